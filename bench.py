@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark: k-bisimulation refinement on the 16M-node / 256M-edge graph.
+
+One step = one full pass of the hot path on a device-resident graph: level 0
+(label grouping) and refinement rounds 1..k (k = 10) until the block count
+stops changing.  Metric: edge-rounds per second = E x rounds run / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank refines its
+own replica of the graph; there is no data-path collective ("replicas only":
+the single-graph path does not shard) and value = N x E x rounds / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edge-rounds/sec (k-bisimulation refinement, 1 GB300)"
+UNIT = "edge-rounds/s"
+K_ROUNDS = 10
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic bytes of one refinement round (implementation-independent):
+# per edge: read dst + label (5 B), write its distinct key (8 B), read that key
+# once for the exact comparison (8 B) = 21 B; per node: offsets 8, pId_{i-1} 4,
+# hash write 8, one read + write of a 16 B grouping record 32, pId_i write 4 = 56 B.
+BYTES_PER_EDGE = 21
+BYTES_PER_NODE = 56
+# Split of those bytes over the kernel classes the library times:
+#   signature kernels: 13 B/edge + 20 B/node (dst+label read, key write;
+#   offsets, pId_{i-1}, hash write), grouping: 16 B/node, verification:
+#   8 B/edge + 16 B/node, renumbering: 4 B/node.
+KERNEL_BYTES = {
+    "sig": (13, 20),
+    "group": (0, 16),
+    "verify": (8, 16),
+    "renumber": (0, 4),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 16M/256M)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--skip-clocks", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index, enabled=True):
+        self.proc = None
+        self.path = None
+        self.device_index = device_index
+        if not enabled:
+            return
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def workload(scale):
+    from paper_1210_0748_gb300 import synth
+    g = synth.config_single_large(scale=scale)
+    return g, {"workload": "powerlaw graph: %d nodes, %d edges, out-degree Pareto alpha=2.1 (hubs "
+                           "to 1M), preferential-attachment targets, 16 node labels Zipf(1.2), "
+                           "32 edge labels Zipf(1.5), k=10 with early stop" % (g.num_nodes, g.num_edges),
+               "nodes": g.num_nodes, "edges": g.num_edges, "k": K_ROUNDS,
+               "l2": "inputs larger than L2 (no flush needed)"}
+
+
+def cpu_baseline(scale_full):
+    """The oracle as it stands, single-threaded, on a bounded sample: the same
+    generator at 1/16 of the size (1M nodes, 16M edges), k = 10."""
+    import oracle
+    from paper_1210_0748_gb300 import synth
+    sc = scale_full / 16.0
+    g = synth.config_single_large(scale=sc)
+    src = g.src()
+    r = oracle.kbisim(g.num_nodes, g.node_label, src, g.dst, g.edge_label, K_ROUNDS)
+    secs = float(np.sum(r.round_seconds))
+    return {"value": g.num_edges * r.rounds_run / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "same generator at %d nodes / %d edges, k=10 with early stop (%d rounds, "
+                      "%.1f s of rounds)" % (g.num_nodes, g.num_edges, r.rounds_run, secs)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1210_0748_gb300 import synth
+    _, cfg = workload(args.scale)
+    sc = args.scale / 64.0  # bounded sample per step: 250K nodes, 4M edges
+    g = synth.config_single_large(scale=sc)
+    src = g.src()
+    for _ in range(args.warmup):
+        oracle.kbisim(g.num_nodes, g.node_label, src, g.dst, g.edge_label, K_ROUNDS)
+    t0 = time.perf_counter()
+    rounds = 0
+    for _ in range(args.steps):
+        r = oracle.kbisim(g.num_nodes, g.node_label, src, g.dst, g.edge_label, K_ROUNDS)
+        rounds += r.rounds_run
+    dt = time.perf_counter() - t0
+    value = g.num_edges * rounds / dt
+    sample = "oracle on the same generator at %d nodes / %d edges per step, k=10" % (
+        g.num_nodes, g.num_edges)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1210_0748_gb300.kbisim import KBisim
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    g, cfg = workload(args.scale)
+    E, N = g.num_edges, g.num_nodes
+    stream = torch.cuda.Stream(device=local_rank)
+    kb = KBisim(device=local_rank, stream=stream, collect_timing=True)
+    kb.load(g)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        res = kb.refine(K_ROUNDS)
+    torch.cuda.synchronize()
+    kb.reset_times()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank, enabled=not args.skip_clocks)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rounds = 0
+    for _ in range(args.steps):
+        res = kb.refine(K_ROUNDS)
+        rounds += res.rounds_run
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ktimes = kb.kernel_times()
+    barrier()
+    ms_max = ms_total
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * E * rounds / (ms_max / 1000.0)
+
+    # roofline: the whole refinement round against the fixed algorithmic bytes,
+    # and the dominant kernel class against its share of those bytes
+    peak, peak_kind = load_peaks()
+    rounds_per_step = rounds / args.steps
+    gpu_launches = int(sum(c for _, c in ktimes.values()))
+    round_ms = (ms_total / args.steps - ktimes["label_group"][0] / args.steps) / max(rounds_per_step, 1)
+    round_bytes = BYTES_PER_EDGE * E + BYTES_PER_NODE * N
+    cls_ms = {
+        "sig": sum(ktimes[k][0] for k in ("sig_small", "sig_medium", "sig_hub")),
+        "group": ktimes["group"][0],
+        "verify": ktimes["verify"][0],
+        "renumber": ktimes["renumber"][0],
+    }
+    dom = max(cls_ms, key=cls_ms.get)
+    be, bn = KERNEL_BYTES[dom]
+    dom_bytes = be * E + bn * N  # per round (one launch sequence of that class)
+    n_rounds_total = rounds
+    dom_ms = cls_ms[dom] / max(n_rounds_total, 1)
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "signature kernels (gather, sort, dedupe, hash)"
+                if dom == "sig" else dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
+    round_achieved = round_bytes / (round_ms / 1000.0) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": cfg, "rounds_per_step": rounds_per_step, "roofline": roofline,
+            "round_roofline": {"achieved": round_achieved, "peak": peak, "unit": "GB/s",
+                               "frac": round_achieved / peak, "avg_round_ms": round_ms,
+                               "algorithmic_bytes": round_bytes},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
+            "gpu_launches": gpu_launches, "clocks": clk}
+
+    # end to end through the public API: pinned host inputs -> build -> level k to host
+    if not args.no_e2e:
+        pin = {"offsets": torch.from_numpy(g.offsets.view(np.int64)).pin_memory(),
+               "dst": torch.from_numpy(g.dst.view(np.int32)).pin_memory(),
+               "edge_label": torch.from_numpy(g.edge_label).pin_memory(),
+               "node_label": torch.from_numpy(g.node_label.view(np.int32)).pin_memory()}
+        host_g = type(g)(N, pin["offsets"].numpy().view(np.uint64), pin["dst"].numpy().view(np.uint32),
+                         pin["edge_label"].numpy(), pin["node_label"].numpy().view(np.uint32))
+        out = torch.empty(N, dtype=torch.int32).pin_memory()
+        out_np = out.numpy()
+        kb2 = KBisim(device=local_rank, stream=stream)
+        r0 = kb2.build(host_g, K_ROUNDS)  # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_rounds = 0
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            r = kb2.build(host_g, K_ROUNDS)
+            kb2._check(kb2._lib.kbisim_pids(kb2._h, K_ROUNDS, out_np.ctypes.data, 0))
+            e2e_rounds += r.rounds_run
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(v.numel() * v.element_size() for v in pin.values())
+        line["e2e"] = {"value": world * E * e2e_rounds / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": N * 4 + 8 * (K_ROUNDS + 1),
+                       "ms_per_step": 1000 * dt / e2e_steps}
+        kb2.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.scale)
+    kb.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

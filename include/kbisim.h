@@ -1,0 +1,238 @@
+/*
+ * kbisim.h -- C ABI of the GB300 k-bisimulation library (libkbisim.so).
+ *
+ * The library computes k-partition identifiers (Definition 2 of "External
+ * memory bisimulation reduction of big graphs"): for a directed graph
+ * <N, E, lambda_N, lambda_E> (Section 2.1) and k >= 0, identifiers
+ * pId_0..pId_k with pId_i(u) == pId_i(v) iff u and v are i-bisimilar
+ * (Definition 1).  Level 0 groups nodes by label (Algorithm 1, k = 0 branch);
+ * level i > 0 groups nodes by the signature
+ *     sig_i(u) = (pId_{i-1}(u), { (lambda_E(u,v), pId_{i-1}(v)) : (u,v) in E })
+ * (Definition 3 and Proposition 2; using pId_{i-1}(u) rather than pId_0(u) as
+ * the first component gives the same partition by Proposition 1).  Rounds stop
+ * early once a level has as many blocks as the one before it (Section 3,
+ * "Early stopping condition"); later levels are then equal to it.
+ *
+ * Numbering is canonical: on every level the blocks are numbered 0, 1, 2, ...
+ * in the order of their smallest node id.  The paper allows any numbering
+ * (Section 3, "Numbering schemes of partition identifier and S"); this one is
+ * unique, so results can be compared bit for bit.
+ *
+ * Edges form a multiset of (source, label, target) triples.  Repeated triples
+ * and several labels on one node pair are allowed; signatures are sets, so
+ * repeats never change a partition.  Self-loops are allowed.
+ *
+ * All work runs in CUDA kernels on the device and stream given at creation;
+ * every host call that returns results waits for that stream.  There is no
+ * CPU fallback: without a usable GPU, kbisim_create fails with
+ * KBISIM_ERR_CUDA.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: KBISIM_OK (0) or one of the KBISIM_ERR_* codes below.
+ *    No C++ exception crosses this boundary.  kbisim_last_error() gives a
+ *    message for the last failure on a handle.
+ *  - A failed call leaves the previous result of the handle intact, except
+ *    KBISIM_ERR_CUDA, after which the handle should be destroyed.
+ *  - Inputs are borrowed for the duration of the call only; the library
+ *    copies what it keeps.  Results live in the handle and stay valid until
+ *    the next call that loads, refines, extends or updates the handle, or
+ *    until kbisim_destroy.
+ *  - A handle is not thread safe: use one handle per host thread.
+ */
+#ifndef KBISIM_H_
+#define KBISIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KBISIM_OK 0
+#define KBISIM_ERR_INVALID_ARG 1   /* bad pointer, size, id or label */
+#define KBISIM_ERR_OUT_OF_MEMORY 2 /* a device allocation failed */
+#define KBISIM_ERR_BUDGET 3        /* the call would exceed options.hbm_budget_bytes */
+#define KBISIM_ERR_CUDA 4          /* a CUDA runtime call or kernel failed */
+#define KBISIM_ERR_TIMEOUT 5       /* a bounded device-side loop gave up */
+#define KBISIM_ERR_CHECKED 6       /* a device bounds check fired (options.checked) */
+#define KBISIM_ERR_STATE 7         /* the call needs a loaded graph or computed levels */
+
+/* Identifier of a deleted node on every level; deleted nodes are not counted. */
+#define KBISIM_DELETED 0xFFFFFFFFu
+
+/* Largest k accepted by the entry points. */
+#define KBISIM_MAX_K 1024u
+
+typedef struct kbisim_handle kbisim_handle;
+
+typedef struct {
+  /* CUDA stream (a cudaStream_t) all work is ordered on; NULL = the legacy
+   * default stream of the device. */
+  void *stream;
+  /* CUDA device ordinal the handle uses. */
+  int device;
+  /* Upper bound on the device bytes the handle may hold; 0 = no bound.
+   * Calls that would need more fail with KBISIM_ERR_BUDGET before allocating. */
+  uint64_t hbm_budget_bytes;
+  /* 1 (default) = stop refining once a level has as many blocks as the level
+   * before it; 0 = always compute k rounds.  Results are identical. */
+  int early_stop;
+  /* Seed of the 64-bit signature hash.  The hash only orders work: equal
+   * signatures are always found by exact comparison, so results do not
+   * depend on it. */
+  uint64_t hash_seed;
+  /* Number of signature-hash bits kept (1..64, default 64).  Values below 64
+   * exist to test the exact collision handling: they make unequal
+   * signatures collide on purpose.  Results do not change, only speed. */
+  uint32_t hash_bits;
+  /* 1 = kernels check their own indices and stop with KBISIM_ERR_CHECKED
+   * instead of touching memory out of range. */
+  int checked;
+  /* 1 = record CUDA events around every kernel and keep per-kernel totals
+   * (see kbisim_kernel_times). */
+  int collect_timing;
+} kbisim_options;
+
+/* Fill *opt with the defaults (stream NULL, device 0, no budget, early stop
+ * on, a fixed seed, 64 hash bits, unchecked, no timing). */
+void kbisim_default_options(kbisim_options *opt);
+
+/* A graph <N, E, lambda_N, lambda_E> (Section 2.1).
+ * Node ids are 0..num_nodes-1 and must be < 2^32 - 1.
+ * Edges are given either in CSR form grouped by source (offsets != NULL:
+ * offsets[u]..offsets[u+1] index dst/edge_label for the out-edges of u,
+ * offsets[0] == 0, non-decreasing, offsets[num_nodes] == num_edges) or as
+ * an unordered COO list (offsets == NULL: src[e], dst[e], edge_label[e]).
+ * Edge labels have edge_label_bytes = 1, 2 or 4 bytes each (unsigned).
+ * With on_device = 1 every pointer is a device pointer on the handle's device;
+ * with 0 they are host pointers (pinned host memory copies faster). */
+typedef struct {
+  uint64_t num_nodes;
+  uint64_t num_edges;
+  const uint32_t *node_label; /* [num_nodes] */
+  const uint64_t *offsets;    /* [num_nodes + 1] or NULL */
+  const uint32_t *src;        /* [num_edges], used when offsets == NULL */
+  const uint32_t *dst;        /* [num_edges] */
+  const void *edge_label;     /* [num_edges] */
+  uint32_t edge_label_bytes;  /* 1, 2 or 4 */
+  int on_device;
+} kbisim_graph;
+
+/* Result of a call that computes levels.  block_count points into the
+ * handle ([k_requested + 1] entries, host memory) and follows the handle's
+ * result lifetime.  rounds_run is the number of signature rounds computed;
+ * with early stop it can be below k_requested, and levels after it repeat
+ * level rounds_run. */
+typedef struct {
+  uint32_t k_requested;
+  uint32_t rounds_run;
+  const uint64_t *block_count;
+} kbisim_result;
+
+/* Per-kernel device time collected when options.collect_timing = 1.
+ * Indices are the KBISIM_KERNEL_* values. */
+enum {
+  KBISIM_KERNEL_LABEL_GROUP = 0, /* level 0 grouping by node label */
+  KBISIM_KERNEL_SIG_SMALL,       /* signatures of out-degree <= 32 */
+  KBISIM_KERNEL_SIG_MEDIUM,      /* signatures of out-degree 33..4096 */
+  KBISIM_KERNEL_SIG_HUB,         /* signatures of larger out-degree (all hub kernels) */
+  KBISIM_KERNEL_GROUP,           /* hash-table grouping of equal signatures */
+  KBISIM_KERNEL_VERIFY,          /* exact signature comparison */
+  KBISIM_KERNEL_RENUMBER,        /* canonical renumbering (scan + gather) */
+  KBISIM_KERNEL_OTHER,           /* clears, collision repair, copies */
+  KBISIM_KERNEL_COUNT
+};
+
+typedef struct {
+  double total_ms[KBISIM_KERNEL_COUNT];
+  uint64_t launches[KBISIM_KERNEL_COUNT];
+} kbisim_kernel_times;
+
+/* Create a handle on options->device (NULL options = defaults).
+ * Errors: INVALID_ARG (h == NULL or bad options), CUDA (no device). */
+int kbisim_create(kbisim_handle **h, const kbisim_options *opt);
+
+/* Release everything the handle holds.  NULL is ignored. */
+void kbisim_destroy(kbisim_handle *h);
+
+/* Message for the last failed call on h (never NULL; "" if none). */
+const char *kbisim_last_error(const kbisim_handle *h);
+
+/* Copy a graph into the handle (building the CSR-by-source edge table when
+ * COO is given) and drop any previous graph and levels.  Validates ids
+ * (INVALID_ARG if a node id >= num_nodes or num_nodes >= 2^32 - 1). */
+int kbisim_load(kbisim_handle *h, const kbisim_graph *g);
+
+/* Compute levels 0..k of the loaded graph (Algorithm 1, Build_Bisim).
+ * Errors: STATE (no graph), INVALID_ARG (k > KBISIM_MAX_K or out == NULL),
+ * OUT_OF_MEMORY, BUDGET, TIMEOUT, CHECKED, CUDA. */
+int kbisim_refine(kbisim_handle *h, uint32_t k, kbisim_result *out);
+
+/* kbisim_load followed by kbisim_refine. */
+int kbisim_build(kbisim_handle *h, const kbisim_graph *g, uint32_t k, kbisim_result *out);
+
+/* Change k (Section 4, "Change k"): a larger k runs the missing rounds from
+ * the kept levels; a smaller k only truncates.  Errors as kbisim_refine. */
+int kbisim_extend(kbisim_handle *h, uint32_t k_new, kbisim_result *out);
+
+/* A maintenance batch (Section 4: Add_Nodes, Add_Edges, deletions).  Applied
+ * in this order: node additions (ids num_nodes, num_nodes+1, ... in batch
+ * order, isolated, with the given labels); edge insertions (one copy of each
+ * triple; endpoints must exist and not be deleted); edge deletions (one copy
+ * of each listed triple; triples that are not present are ignored and
+ * counted); node deletions (every incident edge is removed, then the node
+ * is marked deleted).  Pointers are host or device memory per on_device. */
+typedef struct {
+  const uint32_t *add_node_label; uint64_t n_add_nodes;
+  const uint32_t *ins_src, *ins_dst, *ins_label; uint64_t n_ins;
+  const uint32_t *del_src, *del_dst, *del_label; uint64_t n_del;
+  const uint32_t *del_nodes; uint64_t n_del_nodes;
+  int on_device;
+} kbisim_batch;
+
+/* Apply a batch to the loaded graph and recompute levels 0..k so that the
+ * result equals a build of the updated graph (Theorem 2: the maintained
+ * partition is the k-bisimulation of the new graph).  *missing_deletes (may
+ * be NULL) receives the number of edge deletions that named no edge.
+ * Errors: STATE, INVALID_ARG (bad id, or an edge on a deleted node), and the
+ * errors of kbisim_refine.  On failure the graph and levels are unchanged. */
+int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_result *out,
+                  uint64_t *missing_deletes);
+
+/* Copy level `level` (0..k of the last result) into dst[num_nodes]
+ * (host memory when dst_on_device = 0).  Errors: STATE, INVALID_ARG. */
+int kbisim_pids(kbisim_handle *h, uint32_t level, uint32_t *dst, int dst_on_device);
+
+/* Device pointer to level `level` ([num_nodes] uint32), owned by the handle;
+ * NULL if there is no such level.  Valid until the handle's results change. */
+const uint32_t *kbisim_pids_device(kbisim_handle *h, uint32_t level);
+
+/* Number of nodes of the loaded graph (including deleted ones). */
+uint64_t kbisim_num_nodes(const kbisim_handle *h);
+
+/* Number of edges of the loaded graph. */
+uint64_t kbisim_num_edges(const kbisim_handle *h);
+
+/* Per-kernel device times summed since the last kbisim_reset_times(). */
+int kbisim_get_kernel_times(const kbisim_handle *h, kbisim_kernel_times *out);
+void kbisim_reset_times(kbisim_handle *h);
+
+/* Statistics of the last refine, per computed round r (1-based):
+ * number of distinct (label, child) keys over all nodes, largest signature
+ * size, nodes whose 64-bit hash matched an unequal signature, and nodes on
+ * the hub path.  Errors: STATE, INVALID_ARG (round out of range). */
+typedef struct {
+  uint64_t blocks;
+  uint64_t unique_keys;
+  uint64_t max_signature;
+  uint64_t collided_nodes;
+  uint64_t hub_nodes;
+} kbisim_round_stats;
+int kbisim_get_round_stats(const kbisim_handle *h, uint32_t round, kbisim_round_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KBISIM_H_ */

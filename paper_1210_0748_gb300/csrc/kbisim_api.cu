@@ -1,0 +1,640 @@
+// C ABI of libkbisim (declared in include/kbisim.h): handles, graph loading
+// (CSR build on the device), refinement, extension, copy-out.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kbisim_internal.cuh"
+
+struct kbisim_handle {
+  kb::Store s;
+  std::string last_error;
+};
+
+namespace kb {
+
+Status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return Status::Ok();
+  return Status::Err(e == cudaErrorMemoryAllocation ? KBISIM_ERR_OUT_OF_MEMORY : KBISIM_ERR_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+Status ensure(Store& s, Buf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return Status::Ok();
+  size_t want = std::max<size_t>(bytes, 256);
+  if (s.budget && s.bytes_held - b.cap + want > s.budget)
+    return Status::Err(KBISIM_ERR_BUDGET, "device memory budget exceeded");
+  if (b.p) {
+    cudaStreamSynchronize(s.stream);
+    cudaFree(b.p);
+    s.bytes_held -= b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return Status::Err(KBISIM_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+  }
+  b.p = p;
+  b.cap = want;
+  s.bytes_held += want;
+  return Status::Ok();
+}
+
+void release(Store& s, Buf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    s.bytes_held -= b.cap;
+  }
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+namespace {
+
+template <typename T>
+T* ptr(Buf& b) { return static_cast<T*>(b.p); }
+
+unsigned grid(uint64_t work, unsigned per) {
+  uint64_t g = (work + per - 1) / per;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 65535ull * 16));
+}
+
+// --- load kernels -----------------------------------------------------------
+__global__ void k_check_ids(uint64_t m, uint64_t n, const uint32_t* a, uint32_t* err) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x)
+    if (a[e] >= n) atomicOr(err, kErrBadInput);
+}
+
+__global__ void k_check_offsets(uint64_t n, uint64_t m, const uint64_t* off, uint32_t* err) {
+  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = off[u], b = off[u + 1];
+    if (b < a || b - a > 0x7FFFFFFFull) atomicOr(err, kErrBadInput);
+    if (u == 0 && a != 0) atomicOr(err, kErrBadInput);
+    if (u == n - 1 && b != m) atomicOr(err, kErrBadInput);
+  }
+}
+
+template <typename T>
+__global__ void k_label_max(uint64_t m, const T* lab, unsigned int* mx) {
+  unsigned int v = 0;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x)
+    v = max(v, (unsigned int)lab[e]);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
+}
+
+// Scatter COO edges into their CSR position (with label conversion).
+template <typename TI, typename TO>
+__global__ void k_place_edges(uint64_t m, const uint32_t* src, const uint32_t* dst_in, const TI* lab_in,
+                              unsigned long long* cursor, uint32_t* dst_out, TO* lab_out) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = atomicAdd(&cursor[src[e]], 1ull);
+    dst_out[p] = dst_in[e];
+    lab_out[p] = (TO)lab_in[e];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(uint64_t m, const TI* in, TO* out) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x)
+    out[e] = (TO)in[e];
+}
+
+__global__ void k_degree_count(uint64_t m, const uint32_t* src, unsigned long long* deg) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&deg[src[e]], 1ull);
+}
+
+// Exclusive prefix sum in place: per-tile sums, a one-CTA scan of the tile
+// sums, then tile scans.
+constexpr int kT = 1024, kI = 4, kTile = kT * kI;
+
+__global__ void __launch_bounds__(kT) k_tsum(const unsigned long long* a, uint64_t n, unsigned long long* bs) {
+  __shared__ unsigned long long red[kT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kTile;
+  unsigned long long c = 0;
+  for (int t = 0; t < kI; ++t) {
+    const uint64_t i = base + (uint64_t)t * kT + threadIdx.x;
+    if (i < n) c += a[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kT / 32; ++w) tot += red[w];
+    bs[blockIdx.x] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_tscan1(unsigned long long* bs, uint64_t nb) {
+  __shared__ unsigned long long wt[kT / 32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t base = 0; base < nb; base += kT) {
+    const uint64_t i = base + threadIdx.x;
+    const unsigned long long v = i < nb ? bs[i] : 0ull;
+    unsigned long long x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long t = wt[lane], xx = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, xx, o);
+        if (lane >= o) xx += y;
+      }
+      wt[lane] = xx - t;
+    }
+    __syncthreads();
+    const unsigned long long c0 = carry;
+    if (i < nb) bs[i] = c0 + wt[w] + x - v;
+    __syncthreads();
+    if (threadIdx.x == kT - 1) carry = c0 + wt[w] + x;
+    __syncthreads();
+  }
+}
+
+// exclusive scan of a[0..n) written in place; optional copy
+__global__ void __launch_bounds__(kT) k_tscan2(unsigned long long* a, uint64_t n, const unsigned long long* bs,
+                                              unsigned long long* copy) {
+  __shared__ unsigned long long wt[kT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)threadIdx.x * kI;
+  unsigned long long f[kI], c = 0;
+  for (int t = 0; t < kI; ++t) {
+    f[t] = base + t < n ? a[base + t] : 0ull;
+    c += f[t];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = wt[lane], xx = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, xx, o);
+      if (lane >= o) xx += y;
+    }
+    wt[lane] = xx - t;
+  }
+  __syncthreads();
+  unsigned long long run = bs[blockIdx.x] + wt[w] + (x - c);
+  for (int t = 0; t < kI; ++t) {
+    if (base + t < n) {
+      a[base + t] = run;
+      if (copy) copy[base + t] = run;
+    }
+    run += f[t];
+  }
+}
+
+Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned long long* copy, Buf& tmp) {
+  if (!n) return Status::Ok();
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  Status st = ensure(s, tmp, tiles * 8);
+  if (!st.ok()) return st;
+  unsigned long long* bs = ptr<unsigned long long>(tmp);
+  k_tsum<<<(unsigned)tiles, kT, 0, s.stream>>>(a, n, bs);
+  k_tscan1<<<1, kT, 0, s.stream>>>(bs, tiles);
+  k_tscan2<<<(unsigned)tiles, kT, 0, s.stream>>>(a, n, bs, copy);
+  return cuda_check(cudaGetLastError(), "scan");
+}
+
+void free_graph(Store& s) {
+  Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.alive, &s.small_nodes, &s.warp_nodes,
+                 &s.block_nodes, &s.hub_nodes, &s.hub_bits, &s.hub_bbase, &s.hub_chunks, &s.sigkey,
+                 &s.ucnt, &s.hash, &s.tkey, &s.tmin, &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.bsum,
+                 &s.hub_hist, &s.hub_cursor, &s.hub_ucnt, &s.hub_hpart, &s.hub_tmp, &s.hub_tmp2};
+  for (Buf* b : bufs) release(s, *b);
+  for (Buf& b : s.level) release(s, b);
+  s.level.clear();
+  s.counts.clear();
+  s.stats.clear();
+  s.has_graph = false;
+  s.has_levels = false;
+  s.stable = false;
+  s.computed = 0;
+  s.n = s.m = 0;
+}
+
+Status copy_in(Store& s, void* dstp, const void* srcp, size_t bytes, bool on_device) {
+  if (!bytes) return Status::Ok();
+  return cuda_check(cudaMemcpyAsync(dstp, srcp, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                                  : cudaMemcpyHostToDevice, s.stream),
+                    "copy in");
+}
+
+template <typename TI>
+Status place_edges(Store& s, uint64_t m, const uint32_t* src, const uint32_t* dst_in, const void* lab_in,
+                   unsigned long long* cursor, bool out8) {
+  const unsigned g = grid(m, 256);
+  if (out8)
+    k_place_edges<TI, uint8_t><<<g, 256, 0, s.stream>>>(m, src, dst_in, static_cast<const TI*>(lab_in), cursor,
+                                                         ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel));
+  else
+    k_place_edges<TI, uint32_t><<<g, 256, 0, s.stream>>>(m, src, dst_in, static_cast<const TI*>(lab_in), cursor,
+                                                          ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel));
+  return cuda_check(cudaGetLastError(), "place edges");
+}
+
+Status load_graph(Store& s, const kbisim_graph* g) {
+  if (!g) return Status::Err(KBISIM_ERR_INVALID_ARG, "graph is NULL");
+  const uint64_t n = g->num_nodes, m = g->num_edges;
+  const uint32_t w = g->edge_label_bytes;
+  if (n >= 0xFFFFFFFFull) return Status::Err(KBISIM_ERR_INVALID_ARG, "num_nodes must be < 2^32 - 1");
+  if (w != 1 && w != 2 && w != 4) return Status::Err(KBISIM_ERR_INVALID_ARG, "edge_label_bytes must be 1, 2 or 4");
+  if (n && !g->node_label) return Status::Err(KBISIM_ERR_INVALID_ARG, "node_label is NULL");
+  if (m && (!g->dst || !g->edge_label)) return Status::Err(KBISIM_ERR_INVALID_ARG, "dst/edge_label is NULL");
+  if (m && !g->offsets && !g->src) return Status::Err(KBISIM_ERR_INVALID_ARG, "need offsets or src");
+  if (m && !n) return Status::Err(KBISIM_ERR_INVALID_ARG, "edges without nodes");
+  if (g->offsets && !n && m) return Status::Err(KBISIM_ERR_INVALID_ARG, "offsets without nodes");
+  free_graph(s);
+  Status st;
+  const bool dev = g->on_device != 0;
+  s.n = n;
+  s.m = m;
+  if (!(st = ensure(s, s.d_err, 64)).ok()) return st;
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  uint32_t* err = ptr<uint32_t>(s.d_err);
+  if (!(st = ensure(s, s.nlabel, std::max<uint64_t>(n, 1) * 4)).ok()) return st;
+  if (!(st = ensure(s, s.alive, std::max<uint64_t>(n, 1))).ok()) return st;
+  if (!(st = ensure(s, s.offsets, (n + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, s.dst, std::max<uint64_t>(m, 1) * 4)).ok()) return st;
+  if (!(st = copy_in(s, s.nlabel.p, g->node_label, n * 4, dev)).ok()) return st;
+  cudaMemsetAsync(s.alive.p, 1, std::max<uint64_t>(n, 1), s.stream);
+  s.any_dead = false;
+  // staging for labels (and COO src/dst) when they come from the host
+  Buf lab_stage, src_stage, dst_stage, scan_tmp;
+  const void* lab_in = g->edge_label;
+  const uint32_t* src_in = g->src;
+  const uint32_t* dst_in = g->dst;
+  auto cleanup = [&]() {
+    release(s, lab_stage);
+    release(s, src_stage);
+    release(s, dst_stage);
+    release(s, scan_tmp);
+  };
+  if (m && !dev) {
+    if (!(st = ensure(s, lab_stage, m * w)).ok()) { cleanup(); return st; }
+    if (!(st = copy_in(s, lab_stage.p, g->edge_label, m * w, false)).ok()) { cleanup(); return st; }
+    lab_in = lab_stage.p;
+  }
+  unsigned int* d_max = reinterpret_cast<unsigned int*>(ptr<uint32_t>(s.d_err) + 4);
+  cudaMemsetAsync(d_max, 0, 4, s.stream);
+  if (m) {
+    const unsigned gb = grid(m, 256);
+    if (w == 1) k_label_max<uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), d_max);
+    else if (w == 2) k_label_max<uint16_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), d_max);
+    else k_label_max<uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), d_max);
+  }
+  unsigned int maxlab = 0;
+  if (!(st = cuda_check(cudaMemcpyAsync(&maxlab, d_max, 4, cudaMemcpyDeviceToHost, s.stream), "label max")).ok()) {
+    cleanup();
+    return st;
+  }
+  if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) { cleanup(); return st; }
+  s.label8 = maxlab < 256;
+  if (!(st = ensure(s, s.elabel, std::max<uint64_t>(m, 1) * (s.label8 ? 1 : 4))).ok()) { cleanup(); return st; }
+  unsigned long long* off = ptr<unsigned long long>(s.offsets);
+  if (g->offsets) {
+    if (!(st = copy_in(s, off, g->offsets, (n + 1) * 8, dev)).ok()) { cleanup(); return st; }
+    if (n) k_check_offsets<<<grid(n, 256), 256, 0, s.stream>>>(n, m, ptr<uint64_t>(s.offsets), err);
+    if (!(st = copy_in(s, s.dst.p, g->dst, m * 4, dev)).ok()) { cleanup(); return st; }
+    if (m) {
+      const unsigned gb = grid(m, 256);
+      if (s.label8) {
+        if (w == 1) k_convert<uint8_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), ptr<uint8_t>(s.elabel));
+        else if (w == 2) k_convert<uint16_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), ptr<uint8_t>(s.elabel));
+        else k_convert<uint32_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), ptr<uint8_t>(s.elabel));
+      } else {
+        if (w == 2) k_convert<uint16_t, uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), ptr<uint32_t>(s.elabel));
+        else k_convert<uint32_t, uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), ptr<uint32_t>(s.elabel));
+      }
+      if (!(st = cuda_check(cudaGetLastError(), "convert labels")).ok()) { cleanup(); return st; }
+    }
+  } else {
+    if (m && !dev) {
+      if (!(st = ensure(s, src_stage, m * 4)).ok()) { cleanup(); return st; }
+      if (!(st = ensure(s, dst_stage, m * 4)).ok()) { cleanup(); return st; }
+      if (!(st = copy_in(s, src_stage.p, g->src, m * 4, false)).ok()) { cleanup(); return st; }
+      if (!(st = copy_in(s, dst_stage.p, g->dst, m * 4, false)).ok()) { cleanup(); return st; }
+      src_in = ptr<uint32_t>(src_stage);
+      dst_in = ptr<uint32_t>(dst_stage);
+    }
+    cudaMemsetAsync(off, 0, (n + 1) * 8, s.stream);
+    if (m) {
+      k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
+      uint32_t e0 = 0;
+      cudaMemcpyAsync(&e0, err, 4, cudaMemcpyDeviceToHost, s.stream);
+      if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) { cleanup(); return st; }
+      if (e0) {
+        cleanup();
+        free_graph(s);
+        return Status::Err(KBISIM_ERR_INVALID_ARG, "a source id is >= num_nodes");
+      }
+      k_degree_count<<<grid(m, 256), 256, 0, s.stream>>>(m, src_in, off);
+    }
+    Buf cursor;
+    if (!(st = ensure(s, cursor, (n + 1) * 8)).ok()) { cleanup(); return st; }
+    // off = [d_0, ..., d_{n-1}, 0]; its exclusive scan is the CSR offsets
+    // (off[u] = sum of degrees before u, off[n] = m) and seeds the cursors.
+    if (!(st = exclusive_scan_u64(s, off, n + 1, ptr<unsigned long long>(cursor), scan_tmp)).ok()) {
+      release(s, cursor);
+      cleanup();
+      return st;
+    }
+    if (m) {
+      Status (*fn)(Store&, uint64_t, const uint32_t*, const uint32_t*, const void*, unsigned long long*, bool) =
+          w == 1 ? place_edges<uint8_t> : (w == 2 ? place_edges<uint16_t> : place_edges<uint32_t>);
+      if (!(st = fn(s, m, src_in, dst_in, lab_in, ptr<unsigned long long>(cursor), s.label8)).ok()) {
+        release(s, cursor);
+        cleanup();
+        return st;
+      }
+    }
+    if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) {
+      release(s, cursor);
+      cleanup();
+      return st;
+    }
+    release(s, cursor);
+  }
+  if (m) k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, ptr<uint32_t>(s.dst), err);
+  uint32_t e = 0;
+  cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s.stream);
+  st = cuda_check(cudaStreamSynchronize(s.stream), "load sync");
+  cleanup();
+  if (!st.ok()) return st;
+  if (e) {
+    free_graph(s);
+    return Status::Err(KBISIM_ERR_INVALID_ARG, "invalid graph: node id >= num_nodes or bad offsets");
+  }
+  s.has_graph = true;
+  return prepare_classes(s);
+}
+
+Status ensure_levels(Store& s, uint32_t k) {
+  if (s.level.size() < (size_t)k + 1) s.level.resize(k + 1);
+  for (uint32_t i = 0; i <= k; ++i) {
+    Status st = ensure(s, s.level[i], std::max<uint64_t>(s.n, 1) * 4);
+    if (!st.ok()) return st;
+  }
+  if (s.counts.size() < (size_t)k + 1) s.counts.resize(k + 1, 0);
+  return Status::Ok();
+}
+
+void fill_result(Store& s, uint32_t k, kbisim_result* out) {
+  s.k_requested = k;
+  if (s.counts.size() < (size_t)k + 1) s.counts.resize(k + 1, 0);
+  for (uint32_t j = s.computed + 1; j <= k; ++j) s.counts[j] = s.counts[s.computed];
+  if (out) {
+    out->k_requested = k;
+    out->rounds_run = s.rounds_run;
+    out->block_count = s.counts.data();
+  }
+}
+
+// Run rounds from + 1 .. k (levels up to `from` exist).
+Status run_rounds(Store& s, uint32_t from, uint32_t k) {
+  Status st;
+  for (uint32_t i = from + 1; i <= k; ++i) {
+    if (s.early_stop && s.stable) break;
+    if (!(st = compute_round(s, i)).ok()) return st;
+    s.computed = i;
+    s.rounds_run = i;
+    if (s.counts[i] == s.counts[i - 1]) {
+      s.stable = true;
+      if (s.early_stop) break;
+    }
+  }
+  return Status::Ok();
+}
+
+Status refine(Store& s, uint32_t k, kbisim_result* out) {
+  if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
+  if (k > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+  Status st;
+  if (!(st = ensure_levels(s, s.early_stop ? std::min<uint32_t>(k, 1) : k)).ok()) return st;
+  s.has_levels = false;
+  s.stable = false;
+  s.computed = 0;
+  s.rounds_run = 0;
+  s.stats.clear();
+  if (!(st = compute_level0(s)).ok()) return st;
+  for (uint32_t i = 1; i <= k; ++i) {
+    if (s.early_stop && s.stable) break;
+    if (!(st = ensure_levels(s, i)).ok()) return st;
+    if (!(st = run_rounds(s, i - 1, i)).ok()) return st;
+  }
+  s.has_levels = true;
+  fill_result(s, k, out);
+  return timer_collect(s);
+}
+
+Status extend(Store& s, uint32_t k_new, kbisim_result* out) {
+  if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
+  if (k_new > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+  Status st;
+  const bool need = k_new > s.computed && !(s.early_stop && s.stable);
+  if (need) {
+    for (uint32_t i = s.computed + 1; i <= k_new; ++i) {
+      if (s.early_stop && s.stable) break;
+      if (!(st = ensure_levels(s, i)).ok()) return st;
+      if (!(st = run_rounds(s, i - 1, i)).ok()) return st;
+    }
+  }
+  fill_result(s, k_new, out);
+  return timer_collect(s);
+}
+
+}  // namespace
+}  // namespace kb
+
+using kb::Status;
+
+static int finish(kbisim_handle* h, const Status& st) {
+  if (h) h->last_error = st.ok() ? std::string() : st.msg;
+  return st.code;
+}
+
+extern "C" {
+
+void kbisim_default_options(kbisim_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->stream = nullptr;
+  opt->device = 0;
+  opt->hbm_budget_bytes = 0;
+  opt->early_stop = 1;
+  opt->hash_seed = 0x12100748ull;
+  opt->hash_bits = 64;
+  opt->checked = 0;
+  opt->collect_timing = 0;
+}
+
+int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  *h = nullptr;
+  kbisim_options o;
+  if (opt) o = *opt; else kbisim_default_options(&o);
+  if (o.hash_bits == 0 || o.hash_bits > 64) return KBISIM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return KBISIM_ERR_CUDA;
+  }
+  if (o.device < 0 || o.device >= ndev) return KBISIM_ERR_INVALID_ARG;
+  if (cudaSetDevice(o.device) != cudaSuccess) return KBISIM_ERR_CUDA;
+  kbisim_handle* p = new (std::nothrow) kbisim_handle();
+  if (!p) return KBISIM_ERR_OUT_OF_MEMORY;
+  kb::Store& s = p->s;
+  s.device = o.device;
+  s.stream = static_cast<cudaStream_t>(o.stream);
+  s.budget = o.hbm_budget_bytes;
+  s.early_stop = o.early_stop != 0;
+  s.seed = o.hash_seed;
+  s.hash_mask = o.hash_bits >= 64 ? ~0ull : ((1ull << o.hash_bits) - 1ull);
+  s.checked = o.checked != 0;
+  s.timing = o.collect_timing != 0;
+  void* hp = nullptr;
+  if (cudaMallocHost(&hp, 16 * 8) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return KBISIM_ERR_CUDA;
+  }
+  s.h_scalars.p = hp;
+  s.h_scalars.cap = 16 * 8;
+  Status st = kb::ensure(s, s.d_scalars, 16 * 8);
+  if (st.ok()) st = kb::ensure(s, s.d_err, 64);
+  if (!st.ok()) {
+    cudaFreeHost(hp);
+    delete p;
+    return st.code;
+  }
+  *h = p;
+  return KBISIM_OK;
+}
+
+void kbisim_destroy(kbisim_handle* h) {
+  if (!h) return;
+  kb::Store& s = h->s;
+  cudaSetDevice(s.device);
+  cudaStreamSynchronize(s.stream);
+  kb::free_graph(s);
+  kb::release(s, s.d_scalars);
+  kb::release(s, s.d_err);
+  if (s.h_scalars.p) cudaFreeHost(s.h_scalars.p);
+  kb::timer_destroy(s);
+  delete h;
+}
+
+const char* kbisim_last_error(const kbisim_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+int kbisim_load(kbisim_handle* h, const kbisim_graph* g) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  return finish(h, kb::load_graph(h->s, g));
+}
+
+int kbisim_refine(kbisim_handle* h, uint32_t k, kbisim_result* out) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  return finish(h, kb::refine(h->s, k, out));
+}
+
+int kbisim_build(kbisim_handle* h, const kbisim_graph* g, uint32_t k, kbisim_result* out) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  Status st = kb::load_graph(h->s, g);
+  if (st.ok()) st = kb::refine(h->s, k, out);
+  return finish(h, st);
+}
+
+int kbisim_extend(kbisim_handle* h, uint32_t k_new, kbisim_result* out) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  return finish(h, kb::extend(h->s, k_new, out));
+}
+
+int kbisim_pids(kbisim_handle* h, uint32_t level, uint32_t* dst, int dst_on_device) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  kb::Store& s = h->s;
+  if (!s.has_levels) return finish(h, Status::Err(KBISIM_ERR_STATE, "no computed levels"));
+  if (level > s.k_requested) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "level out of range"));
+  if (!dst && s.n) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "dst is NULL"));
+  cudaSetDevice(s.device);
+  const uint32_t l = std::min(level, s.computed);
+  Status st = kb::cuda_check(cudaMemcpyAsync(dst, s.level[l].p, s.n * 4,
+                                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                             s.stream), "copy out");
+  if (st.ok()) st = kb::cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  return finish(h, st);
+}
+
+const uint32_t* kbisim_pids_device(kbisim_handle* h, uint32_t level) {
+  if (!h || !h->s.has_levels || level > h->s.k_requested) return nullptr;
+  return static_cast<const uint32_t*>(h->s.level[std::min(level, h->s.computed)].p);
+}
+
+uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
+uint64_t kbisim_num_edges(const kbisim_handle* h) { return h ? h->s.m : 0; }
+
+int kbisim_get_kernel_times(const kbisim_handle* h, kbisim_kernel_times* out) {
+  if (!h || !out) return KBISIM_ERR_INVALID_ARG;
+  for (int i = 0; i < KBISIM_KERNEL_COUNT; ++i) {
+    out->total_ms[i] = h->s.total_ms[i];
+    out->launches[i] = h->s.launches[i];
+  }
+  return KBISIM_OK;
+}
+
+void kbisim_reset_times(kbisim_handle* h) {
+  if (!h) return;
+  for (int i = 0; i < KBISIM_KERNEL_COUNT; ++i) {
+    h->s.total_ms[i] = 0;
+    h->s.launches[i] = 0;
+  }
+}
+
+int kbisim_get_round_stats(const kbisim_handle* h, uint32_t round, kbisim_round_stats* out) {
+  if (!h || !out) return KBISIM_ERR_INVALID_ARG;
+  if (!h->s.has_levels) return KBISIM_ERR_STATE;
+  if (round == 0 || round > h->s.stats.size()) return KBISIM_ERR_INVALID_ARG;
+  *out = h->s.stats[round - 1];
+  return KBISIM_OK;
+}
+
+int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_result* out,
+                  uint64_t* missing_deletes) {
+  (void)b;
+  (void)k;
+  (void)out;
+  (void)missing_deletes;
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  return finish(h, Status::Err(KBISIM_ERR_STATE, "kbisim_update is not available yet"));
+}
+
+}  // extern "C"

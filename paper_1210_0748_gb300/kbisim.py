@@ -1,0 +1,373 @@
+"""Python binding of libkbisim (ctypes over the C ABI in include/kbisim.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  PyTorch supplies device memory (for inputs and
+outputs that live on the GPU) and the CUDA stream.  If the library is not
+built, or no GPU is usable, these calls raise; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkbisim.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_OUT_OF_MEMORY = 2
+ERR_BUDGET = 3
+ERR_CUDA = 4
+ERR_TIMEOUT = 5
+ERR_CHECKED = 6
+ERR_STATE = 7
+DELETED = 0xFFFFFFFF
+MAX_K = 1024
+
+KERNEL_NAMES = ["label_group", "sig_small", "sig_medium", "sig_hub", "group", "verify",
+                "renumber", "other"]
+
+_ERR_NAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_OUT_OF_MEMORY: "OUT_OF_MEMORY",
+              ERR_BUDGET: "BUDGET", ERR_CUDA: "CUDA", ERR_TIMEOUT: "TIMEOUT",
+              ERR_CHECKED: "CHECKED", ERR_STATE: "STATE"}
+
+
+class KBisimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_ERR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("early_stop", ctypes.c_int),
+                ("hash_seed", ctypes.c_uint64), ("hash_bits", ctypes.c_uint32),
+                ("checked", ctypes.c_int), ("collect_timing", ctypes.c_int)]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_uint64), ("num_edges", ctypes.c_uint64),
+                ("node_label", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("edge_label", ctypes.c_void_p), ("edge_label_bytes", ctypes.c_uint32),
+                ("on_device", ctypes.c_int)]
+
+
+class ResultDesc(ctypes.Structure):
+    _fields_ = [("k_requested", ctypes.c_uint32), ("rounds_run", ctypes.c_uint32),
+                ("block_count", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("add_node_label", ctypes.c_void_p), ("n_add_nodes", ctypes.c_uint64),
+                ("ins_src", ctypes.c_void_p), ("ins_dst", ctypes.c_void_p),
+                ("ins_label", ctypes.c_void_p), ("n_ins", ctypes.c_uint64),
+                ("del_src", ctypes.c_void_p), ("del_dst", ctypes.c_void_p),
+                ("del_label", ctypes.c_void_p), ("n_del", ctypes.c_uint64),
+                ("del_nodes", ctypes.c_void_p), ("n_del_nodes", ctypes.c_uint64),
+                ("on_device", ctypes.c_int)]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_uint64), ("unique_keys", ctypes.c_uint64),
+                ("max_signature", ctypes.c_uint64), ("collided_nodes", ctypes.c_uint64),
+                ("hub_nodes", ctypes.c_uint64)]
+
+
+_lib = None
+
+# exported symbols and their signatures (checked by the CPU tests)
+SIGNATURES = {
+    "kbisim_default_options": (None, [ctypes.POINTER(Options)]),
+    "kbisim_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
+    "kbisim_destroy": (None, [ctypes.c_void_p]),
+    "kbisim_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "kbisim_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GraphDesc)]),
+    "kbisim_refine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ResultDesc)]),
+    "kbisim_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_uint32,
+                                    ctypes.POINTER(ResultDesc)]),
+    "kbisim_extend": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ResultDesc)]),
+    "kbisim_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchDesc), ctypes.c_uint32,
+                                     ctypes.POINTER(ResultDesc), ctypes.POINTER(ctypes.c_uint64)]),
+    "kbisim_pids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int]),
+    "kbisim_pids_device": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_uint32]),
+    "kbisim_num_nodes": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "kbisim_num_edges": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "kbisim_get_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
+    "kbisim_reset_times": (None, [ctypes.c_void_p]),
+    "kbisim_get_round_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
+                                              ctypes.POINTER(RoundStats)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libkbisim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libkbisim.so is not built (run paper_1210_0748_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _Pinned:
+    """Keeps host arrays alive for the duration of a call."""
+
+    def __init__(self):
+        self.keep = []
+
+    def host(self, a, dtype):
+        arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+        self.keep.append(arr)
+        return arr.ctypes.data if arr.size else None, arr
+
+    def dev(self, t, dtype):
+        torch = _torch()
+        tt = t.to(dtype).contiguous()
+        self.keep.append(tt)
+        return tt.data_ptr() if tt.numel() else None, tt
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except Exception:  # pragma: no cover
+        return False
+
+
+class Result:
+    def __init__(self, desc: ResultDesc):
+        self.k_requested = int(desc.k_requested)
+        self.rounds_run = int(desc.rounds_run)
+        self.counts = [int(desc.block_count[i]) for i in range(self.k_requested + 1)]
+
+    def __repr__(self):
+        return "Result(k=%d, rounds_run=%d, counts=%s)" % (self.k_requested, self.rounds_run, self.counts)
+
+
+class KBisim:
+    """One library handle: a device-resident graph and its partition levels."""
+
+    def __init__(self, device: int = 0, stream=None, early_stop: bool = True,
+                 hash_seed: int = 0x12100748, hash_bits: int = 64, checked: bool = False,
+                 collect_timing: bool = False, hbm_budget_bytes: int = 0):
+        lib = load_library()
+        self._lib = lib
+        opt = Options()
+        lib.kbisim_default_options(ctypes.byref(opt))
+        if stream is None:
+            try:
+                torch = _torch()
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = None
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        opt.stream = stream or None
+        opt.device = device
+        opt.early_stop = 1 if early_stop else 0
+        opt.hash_seed = hash_seed & 0xFFFFFFFFFFFFFFFF
+        opt.hash_bits = hash_bits
+        opt.checked = 1 if checked else 0
+        opt.collect_timing = 1 if collect_timing else 0
+        opt.hbm_budget_bytes = hbm_budget_bytes
+        h = ctypes.c_void_p()
+        rc = lib.kbisim_create(ctypes.byref(h), ctypes.byref(opt))
+        if rc != OK:
+            raise KBisimError(rc, "kbisim_create failed")
+        self._h = h
+        self.device = device
+        self.stream = stream
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            msg = self._lib.kbisim_last_error(self._h)
+            raise KBisimError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kbisim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- graph ----------------------------------------------------------------
+    def _graph_desc(self, keep: _Pinned, num_nodes, node_label, dst, edge_label, offsets=None,
+                    src=None):
+        g = GraphDesc()
+        g.num_nodes = int(num_nodes)
+        on_dev = _is_torch(dst) and dst.is_cuda
+        g.on_device = 1 if on_dev else 0
+        torch = _torch() if on_dev else None
+        if on_dev:
+            g.node_label, _ = keep.dev(node_label, torch.int32)
+            g.dst, dt = keep.dev(dst, torch.int32)
+            g.num_edges = dt.numel()
+            if offsets is not None:
+                g.offsets, _ = keep.dev(offsets, torch.int64)
+            else:
+                g.src, _ = keep.dev(src, torch.int32)
+            el = edge_label
+            if el.dtype == torch.uint8:
+                g.edge_label, _ = keep.dev(el, torch.uint8)
+                g.edge_label_bytes = 1
+            else:
+                g.edge_label, _ = keep.dev(el, torch.int32)
+                g.edge_label_bytes = 4
+        else:
+            g.node_label, _ = keep.host(node_label, np.uint32)
+            g.dst, dt = keep.host(dst, np.uint32)
+            g.num_edges = dt.size
+            if offsets is not None:
+                g.offsets, _ = keep.host(offsets, np.uint64)
+            else:
+                g.src, _ = keep.host(src, np.uint32)
+            el = np.asarray(edge_label)
+            if el.dtype == np.uint8:
+                g.edge_label, _ = keep.host(el, np.uint8)
+                g.edge_label_bytes = 1
+            elif el.dtype == np.uint16:
+                g.edge_label, _ = keep.host(el, np.uint16)
+                g.edge_label_bytes = 2
+            else:
+                g.edge_label, _ = keep.host(el, np.uint32)
+                g.edge_label_bytes = 4
+        return g
+
+    def load(self, graph=None, *, num_nodes=None, node_label=None, dst=None, edge_label=None,
+             offsets=None, src=None):
+        """Load a graph: a ``synth.Graph`` (CSR, host) or explicit arrays
+        (numpy / host tensors, or CUDA tensors for an on-device load)."""
+        keep = _Pinned()
+        if graph is not None:
+            g = self._graph_desc(keep, graph.num_nodes, graph.node_label, graph.dst,
+                                 graph.edge_label, offsets=graph.offsets)
+        else:
+            g = self._graph_desc(keep, num_nodes, node_label, dst, edge_label, offsets=offsets,
+                                 src=src)
+        self._check(self._lib.kbisim_load(self._h, ctypes.byref(g)))
+
+    def refine(self, k: int) -> Result:
+        r = ResultDesc()
+        self._check(self._lib.kbisim_refine(self._h, int(k), ctypes.byref(r)))
+        return Result(r)
+
+    def build(self, graph=None, k: int = 0, **arrays) -> Result:
+        keep = _Pinned()
+        if graph is not None:
+            g = self._graph_desc(keep, graph.num_nodes, graph.node_label, graph.dst,
+                                 graph.edge_label, offsets=graph.offsets)
+        else:
+            g = self._graph_desc(keep, arrays["num_nodes"], arrays["node_label"], arrays["dst"],
+                                 arrays["edge_label"], offsets=arrays.get("offsets"),
+                                 src=arrays.get("src"))
+        r = ResultDesc()
+        self._check(self._lib.kbisim_build(self._h, ctypes.byref(g), int(k), ctypes.byref(r)))
+        return Result(r)
+
+    def extend(self, k_new: int) -> Result:
+        r = ResultDesc()
+        self._check(self._lib.kbisim_extend(self._h, int(k_new), ctypes.byref(r)))
+        return Result(r)
+
+    def update(self, k: int, add_node_label=(), ins=(), dels=(), del_nodes=()):
+        """Apply a maintenance batch (host arrays) and recompute levels 0..k.
+        ins / dels: (src, dst, label) array triples.  Returns (Result, missing)."""
+        keep = _Pinned()
+        b = BatchDesc()
+        b.add_node_label, a = keep.host(add_node_label, np.uint32)
+        b.n_add_nodes = a.size
+        if len(ins):
+            s, d, l = ins
+            b.ins_src, sa = keep.host(s, np.uint32)
+            b.ins_dst, _ = keep.host(d, np.uint32)
+            b.ins_label, _ = keep.host(l, np.uint32)
+            b.n_ins = sa.size
+        if len(dels):
+            s, d, l = dels
+            b.del_src, sa = keep.host(s, np.uint32)
+            b.del_dst, _ = keep.host(d, np.uint32)
+            b.del_label, _ = keep.host(l, np.uint32)
+            b.n_del = sa.size
+        b.del_nodes, dn = keep.host(del_nodes, np.uint32)
+        b.n_del_nodes = dn.size
+        b.on_device = 0
+        r = ResultDesc()
+        miss = ctypes.c_uint64(0)
+        self._check(self._lib.kbisim_update(self._h, ctypes.byref(b), int(k), ctypes.byref(r),
+                                            ctypes.byref(miss)))
+        return Result(r), int(miss.value)
+
+    # -- results ----------------------------------------------------------------
+    @property
+    def num_nodes(self) -> int:
+        return int(self._lib.kbisim_num_nodes(self._h))
+
+    @property
+    def num_edges(self) -> int:
+        return int(self._lib.kbisim_num_edges(self._h))
+
+    def pids(self, level: int, out=None):
+        """Level ``level`` as a host numpy uint32 array, or into ``out`` (a CUDA
+        int32 tensor of num_nodes elements)."""
+        n = self.num_nodes
+        if out is not None:
+            self._check(self._lib.kbisim_pids(self._h, int(level), ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        host = np.empty(n, dtype=np.uint32)
+        self._check(self._lib.kbisim_pids(self._h, int(level),
+                                          host.ctypes.data if n else None, 0))
+        return host
+
+    def pids_device_ptr(self, level: int) -> Optional[int]:
+        p = self._lib.kbisim_pids_device(self._h, int(level))
+        return int(p) if p else None
+
+    def all_pids(self, k: int) -> np.ndarray:
+        return np.stack([self.pids(i) for i in range(k + 1)]) if self.num_nodes else \
+            np.zeros((k + 1, 0), np.uint32)
+
+    def kernel_times(self) -> dict:
+        kt = KernelTimes()
+        self._check(self._lib.kbisim_get_kernel_times(self._h, ctypes.byref(kt)))
+        return {name: (float(kt.total_ms[i]), int(kt.launches[i]))
+                for i, name in enumerate(KERNEL_NAMES)}
+
+    def reset_times(self):
+        self._lib.kbisim_reset_times(self._h)
+
+    def round_stats(self, r: int) -> dict:
+        st = RoundStats()
+        self._check(self._lib.kbisim_get_round_stats(self._h, int(r), ctypes.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in RoundStats._fields_}

@@ -1,0 +1,237 @@
+"""CUDA path (through the C ABI) against the CPU oracle, bit for bit.
+
+Covers the worked examples, random small graphs, every degree tier of the
+signature kernels (warp lanes, warp, CTA, multi-bucket hubs), forced hash
+collisions, COO vs CSR input, device-resident input, wide edge labels,
+early stop, extend, and the full-size 16M-node / 256M-edge workload through
+properties (sampled signatures, canonical order, refinement).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1210_0748_gb300 import synth
+from paper_1210_0748_gb300.kbisim import KBisim, KBisimError, ERR_INVALID_ARG, ERR_STATE
+from tests import golden_io
+from tests.gpu_util import (assert_same, check_properties, gpu_levels, graph_from_edges,
+                            oracle_levels)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_table1_on_gpu():
+    f = golden_io.load("fig1_table1.txt")
+    g = graph_from_edges(len(f.node_names), f.node_label, f.edges)
+    res, pids = gpu_levels(g, 2, early_stop=False)
+    for lev in range(3):
+        assert pids[lev].tolist() == golden_io.canonical(f.pids[lev])
+    assert res.counts == [2, 4, 5]
+
+
+@pytest.mark.parametrize("fix", ["table4_add_edge_2l7.txt", "table5_add_edge_6l5.txt"])
+def test_tables_4_5_on_gpu(fix):
+    base = golden_io.load("fig1_table1.txt")
+    upd = golden_io.Fixture()
+    upd._nlab, upd._elab = base._nlab, base._elab
+    upd = golden_io.load(fix, base=upd)
+    names = list(base.node_names) + [a for a, _ in upd.add_nodes]
+    labels = list(base.node_label) + [l for _, l in upd.add_nodes]
+    edges = list(base.edges) + [(names.index(a), l, names.index(b)) for a, l, b in upd.add_edges]
+    g = graph_from_edges(len(names), labels, edges)
+    res, pids = gpu_levels(g, 2, early_stop=False)
+    for lev in range(3):
+        assert pids[lev].tolist() == golden_io.canonical(upd.pids[lev])
+
+
+def test_random_small_graphs():
+    rng = np.random.default_rng(7)
+    with KBisim() as kb:
+        for it in range(150):
+            n = int(rng.integers(1, 12))
+            m = int(rng.integers(0, 4 * n))
+            g = synth.random_small_graph(n, m, node_labels=int(rng.integers(1, 3)),
+                                         edge_labels=int(rng.integers(1, 3)), seed=it)
+            k = int(rng.integers(0, 7))
+            res = kb.build(g, k)
+            ref = oracle_levels(g, k)
+            assert_same(res, kb.all_pids(k), ref)
+
+
+def _tier_graph(seed):
+    """Nodes in every degree tier: 0..32 (lanes), 33..256 (warp), 257..4096
+    (CTA), and hubs of 5K, 20K and 70K edges (several buckets each)."""
+    rng = np.random.default_rng(seed)
+    n = 6000
+    deg = rng.integers(0, 33, n)
+    deg[:40] = rng.integers(33, 257, 40)
+    deg[40:60] = rng.integers(257, 4097, 20)
+    deg[60] = 5000
+    deg[61] = 20000
+    deg[62] = 70000
+    deg[63] = 70000  # a twin hub: same targets as 62 -> same signature
+    src = np.repeat(np.arange(n), deg)
+    dst = rng.integers(0, n, src.size)
+    lab = rng.integers(0, 3, src.size)
+    # node 63 copies node 62's out-edges in another order
+    s62 = np.nonzero(src == 62)[0]
+    s63 = np.nonzero(src == 63)[0]
+    perm = rng.permutation(s62.size)
+    dst[s63] = dst[s62][perm]
+    lab[s63] = lab[s62][perm]
+    nl = rng.integers(0, 2, n)
+    nl[63] = nl[62]
+    order = rng.permutation(src.size)  # unordered COO
+    return n, src[order], dst[order], lab[order], nl
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_all_degree_tiers(seed):
+    n, s, d, l, nl = _tier_graph(seed)
+    g = synth.from_coo(n, s, d, l, nl)
+    ref = oracle.kbisim(n, nl, s, d, l, 6)
+    res, pids = gpu_levels(g, 6)
+    assert_same(res, pids, ref)
+    assert pids[1][62] == pids[1][63]
+
+
+@pytest.mark.parametrize("bits", [1, 3, 12])
+def test_forced_hash_collisions(bits):
+    # with few hash bits most unequal signatures collide; exact comparison
+    # and the repair passes must still give the oracle's partition
+    n, s, d, l, nl = _tier_graph(3)
+    g = synth.from_coo(n, s, d, l, nl)
+    ref = oracle.kbisim(n, nl, s, d, l, 5)
+    with KBisim(hash_bits=bits) as kb:
+        res = kb.build(g, 5)
+        pids = kb.all_pids(5)
+        assert kb.round_stats(1)["collided_nodes"] > 0
+    assert_same(res, pids, ref)
+
+
+def test_seed_does_not_matter():
+    g = synth.config_single_large(scale=1 / 512, seed=11)
+    a = gpu_levels(g, 6, hash_seed=1)[1]
+    b = gpu_levels(g, 6, hash_seed=0xDEADBEEF)[1]
+    assert np.array_equal(a, b)
+
+
+def test_coo_and_csr_input_agree():
+    n, s, d, l, nl = _tier_graph(5)
+    g = synth.from_coo(n, s, d, l, nl)
+    with KBisim() as kb:
+        r1 = kb.build(g, 4)
+        p1 = kb.all_pids(4)
+        r2 = kb.build(None, 4, num_nodes=n, node_label=nl, dst=d, edge_label=l, src=s)
+        p2 = kb.all_pids(4)
+    assert r1.counts == r2.counts and np.array_equal(p1, p2)
+
+
+def test_device_resident_input_and_output():
+    import torch
+    g = synth.config_single_large(scale=1 / 1024, seed=3)
+    ref = oracle_levels(g, 5)
+    with KBisim() as kb:
+        res = kb.build(None, 5, num_nodes=g.num_nodes,
+                       node_label=torch.from_numpy(g.node_label.astype(np.int32)).cuda(),
+                       dst=torch.from_numpy(g.dst.astype(np.int32)).cuda(),
+                       edge_label=torch.from_numpy(g.edge_label).cuda(),
+                       offsets=torch.from_numpy(g.offsets.astype(np.int64)).cuda())
+        out = torch.empty(g.num_nodes, dtype=torch.int32, device="cuda")
+        got = np.stack([kb.pids(i, out=out).cpu().numpy().view(np.uint32) for i in range(6)])
+    assert_same(res, got, ref)
+
+
+@pytest.mark.parametrize("width,top", [(2, 60000), (4, 3_000_000_000)])
+def test_wide_edge_labels(width, top):
+    rng = np.random.default_rng(width)
+    n, m = 3000, 40000
+    s, d = rng.integers(0, n, m), rng.integers(0, n, m)
+    l = rng.choice(np.array([0, 7, top, top - 1], dtype=np.uint64), m)
+    nl = rng.integers(0, 5, n)
+    g = synth.from_coo(n, s, d, l.astype(np.uint32), nl)
+    g.edge_label = g.edge_label.astype(np.uint16 if width == 2 else np.uint32)
+    ref = oracle.kbisim(n, nl, s, d, l.astype(np.uint32), 5)
+    res, pids = gpu_levels(g, 5)
+    assert_same(res, pids, ref)
+
+
+def test_early_stop_and_extend():
+    g = synth.config_single_large(scale=1 / 512, seed=5)
+    ref_all = oracle_levels(g, 9, early_stop=False)
+    res, pids = gpu_levels(g, 9, early_stop=False)
+    assert_same(res, pids, ref_all)
+    ref = oracle_levels(g, 9)
+    res2, pids2 = gpu_levels(g, 9)
+    assert_same(res2, pids2, ref)
+    assert np.array_equal(pids, pids2)
+    with KBisim() as kb:
+        kb.build(g, 2)
+        r = kb.extend(9)
+        assert r.counts == ref.counts.tolist() and r.rounds_run == ref.rounds_run
+        assert np.array_equal(kb.all_pids(9), ref.pids)
+        r = kb.extend(1)
+        assert r.counts == ref.counts[:2].tolist()
+
+
+def test_degenerate_graphs():
+    with KBisim() as kb:
+        r = kb.build(synth.from_coo(0, [], [], [], []), 3)
+        assert r.counts == [0, 0, 0, 0]
+        g = synth.from_coo(4, [], [], [], [5, 5, 2, 5])
+        r = kb.build(g, 0)
+        assert r.counts == [2] and kb.pids(0).tolist() == [0, 0, 1, 0]
+        r = kb.build(g, 4)
+        assert r.rounds_run == 1 and r.counts == [2] * 5
+        # self loops and repeated triples
+        g = synth.from_coo(3, [0, 0, 0, 1, 1], [0, 0, 1, 1, 1], [1, 1, 1, 1, 1], [0, 0, 0])
+        ref = oracle.kbisim(3, [0, 0, 0], [0, 0, 0, 1, 1], [0, 0, 1, 1, 1], [1] * 5, 3)
+        r = kb.build(g, 3)
+        assert r.counts == ref.counts.tolist()
+        assert np.array_equal(kb.all_pids(3), ref.pids)
+
+
+def test_invalid_inputs_are_rejected():
+    with KBisim() as kb:
+        with pytest.raises(KBisimError) as e:
+            kb.refine(2)
+        assert e.value.code == ERR_STATE
+        with pytest.raises(KBisimError) as e:
+            kb.build(None, 2, num_nodes=3, node_label=[0, 0, 0], dst=[5], edge_label=[0], src=[0])
+        assert e.value.code == ERR_INVALID_ARG
+        with pytest.raises(KBisimError) as e:
+            kb.build(None, 2, num_nodes=3, node_label=[0, 0, 0], dst=[1], edge_label=[0], src=[9])
+        assert e.value.code == ERR_INVALID_ARG
+        g = synth.from_coo(3, [0], [1], [0], [0, 0, 0])
+        kb.build(g, 1)
+        with pytest.raises(KBisimError) as e:
+            kb.pids(2)
+        assert e.value.code == ERR_INVALID_ARG
+
+
+def test_small_workload_full_oracle():
+    # 100K nodes / 1M edges, k = 5 (Zipf out-degrees, uniform targets)
+    g = synth.config_single_small()
+    ref = oracle_levels(g, 5)
+    res, pids = gpu_levels(g, 5)
+    assert_same(res, pids, ref)
+
+
+@pytest.mark.parametrize("scale", [1 / 64, 1 / 16])
+def test_powerlaw_scaled_full_oracle(scale):
+    # the 16M / 256M workload's distributions at 250K / 4M and 1M / 16M
+    g = synth.config_single_large(scale=scale)
+    ref = oracle_levels(g, 10)
+    res, pids = gpu_levels(g, 10)
+    assert_same(res, pids, ref)
+
+
+def test_full_size_properties():
+    # 16M nodes, 256M edges, k = 10 with early stop, as the benchmark runs it
+    g = synth.config_single_large()
+    with KBisim() as kb:
+        res = kb.build(g, 10)
+        pids = kb.all_pids(res.rounds_run)
+    lvl0 = np.empty(g.num_nodes, np.uint32)
+    cnt0 = oracle._load().oracle_level0(g.num_nodes, g.node_label.ctypes.data, None, lvl0.ctypes.data)
+    assert cnt0 == res.counts[0]
+    check_properties(g, pids, res.counts, lvl0, sample=1500)
