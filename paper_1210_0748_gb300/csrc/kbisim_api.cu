@@ -224,8 +224,7 @@ Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned 
 }
 
 void free_graph(Store& s) {
-  Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.alive, &s.small_nodes, &s.warp_nodes,
-                 &s.block_nodes, &s.hub_nodes, &s.hub_bits, &s.hub_bbase, &s.hub_chunks, &s.sigkey,
+  Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.alive, &s.class_nodes, &s.hub_bits, &s.hub_bbase, &s.hub_chunks, &s.sigkey,
                  &s.ucnt, &s.hash, &s.tkey, &s.tmin, &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.bsum,
                  &s.hub_hist, &s.hub_cursor, &s.hub_ucnt, &s.hub_hpart, &s.hub_tmp, &s.hub_tmp2};
   for (Buf* b : bufs) release(s, *b);

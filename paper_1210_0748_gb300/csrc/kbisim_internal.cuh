@@ -107,17 +107,15 @@ struct Store {
   Buf nlabel;                  // uint32 [n]
   Buf alive;                   // uint8 [n] (1 = present)
 
-  // degree classes, fixed per graph
-  Buf small_nodes;             // uint32: nodes with out-degree <= 32, grouped by class
+  // degree classes, fixed per graph: alive nodes ordered by class, then id
+  Buf class_nodes;             // uint32
+  uint64_t class_start[kSmallClasses + 4] = {0};  // classes: P=1..32, warp, CTA, hub
   uint64_t small_count[kSmallClasses] = {0};
   uint64_t small_start[kSmallClasses + 1] = {0};
-  Buf warp_nodes;              // uint32: 33..512
-  uint64_t n_warp = 0;
-  Buf block_nodes;             // uint32: 513..4096
-  uint64_t n_block = 0;
+  uint64_t n_warp = 0;         // out-degree 33..256
+  uint64_t n_block = 0;        // 257..4096
   // hubs: out-degree > 4096
   uint64_t n_hub = 0;
-  Buf hub_nodes;               // uint32 [n_hub]
   Buf hub_bits;                // uint32 [n_hub]  log2(bucket count)
   Buf hub_bbase;               // uint64 [n_hub+1] first bucket of each hub
   Buf hub_chunks;              // uint4 [n_chunks] (hub index, begin lo, begin hi, length)

@@ -181,32 +181,67 @@ __device__ void team_excl_scan(uint32_t* a, int n, uint32_t* warp_tot, int rank)
 struct TeamWs {
   uint64_t* set;    // [hcap] hash set, reused as the sorted output
   uint64_t* uniq;   // [ucap] distinct keys in arrival order
+  uint64_t* bitv;   // [2] OR and AND of the distinct keys
+  uint64_t* red;    // [NT/32] reduction scratch
   uint32_t* cnt;    // [ucap/2] bucket counters
   uint32_t* sh;     // [4] distinct count, saw-empty-key flag, overflow flag
   uint32_t* wtot;   // [NT/32]
   int hcap, ucap;
 };
 
+__host__ __device__ constexpr size_t team_ws_bytes(int hcap, int ucap, int nt) {
+  return ((size_t)hcap * 8 + (size_t)ucap * 8 + 16 + (size_t)(nt / 32) * 8 + (size_t)(ucap / 2) * 4 +
+          16 + (size_t)(nt / 32) * 4 + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ TeamWs carve(char* base, int hcap, int ucap, int nt) {
+  TeamWs ws;
+  ws.set = reinterpret_cast<uint64_t*>(base);
+  ws.uniq = ws.set + hcap;
+  ws.bitv = ws.uniq + ucap;
+  ws.red = ws.bitv + 2;
+  ws.cnt = reinterpret_cast<uint32_t*>(ws.red + nt / 32);
+  ws.sh = ws.cnt + ucap / 2;
+  ws.wtot = ws.sh + 4;
+  ws.hcap = hcap;
+  ws.ucap = ucap;
+  return ws;
+}
+
+// Smallest power of two >= 2 n, clamped to [64, cap].
+__device__ __forceinline__ int set_size_for(uint64_t n, int cap) {
+  int h = 64;
+  while (h < cap && (uint64_t)h < 2 * n) h <<= 1;
+  return h;
+}
+
 // Distinct keys of n inputs, sorted ascending into ws.set[0..U).  Returns U,
 // or 0xFFFFFFFF if more than ucap distinct keys arrived (overflow).
-// Dedupe: open-addressing set in shared memory (keys are already uniformly
-// mixed, so the low bits index it).  Sort: counting sort on the top bits into
-// about U/2 buckets, then insertion sort inside each (tiny) bucket.
+// Dedupe: open-addressing set of `hcap` slots in shared memory (keys are
+// uniformly mixed, so their low bits index it).  Sort: counting sort into
+// about U/2 buckets on the highest bits in which the distinct keys differ
+// (keys that share a prefix -- e.g. one hub bucket -- still spread out),
+// then insertion sort inside each (tiny) bucket.
 template <int NT, class GetKey>
-__device__ uint32_t team_dedupe_sort(const TeamWs& ws, uint64_t n, GetKey get, int rank) {
-  for (int i = rank; i < ws.hcap; i += NT) ws.set[i] = kEmpty64;
+__device__ uint32_t team_dedupe_sort(const TeamWs& ws, int hcap, uint64_t n, GetKey get, int rank) {
+  for (int i = rank; i < hcap; i += NT) ws.set[i] = kEmpty64;
   if (rank < 4) ws.sh[rank] = 0;
+  if (rank == 0) {
+    ws.bitv[0] = 0ull;
+    ws.bitv[1] = ~0ull;
+  }
   team_sync<NT>();
   volatile uint64_t* vset = ws.set;
+  const uint32_t hmask = (uint32_t)(hcap - 1);
   for (uint64_t i = rank; i < n; i += NT) {
     const uint64_t k = get(i);
     bool fresh = false;
     if (k == kEmpty64) {
       fresh = atomicExch(&ws.sh[1], 1u) == 0u;
     } else {
-      uint32_t s = (uint32_t)k & (uint32_t)(ws.hcap - 1);
+      uint32_t s = (uint32_t)k & hmask;
       int t = 0;
-      for (; t < ws.hcap; ++t) {
+      for (; t < hcap; ++t) {
         uint64_t cur = vset[s];
         if (cur == k) break;
         if (cur == kEmpty64) {
@@ -215,13 +250,15 @@ __device__ uint32_t team_dedupe_sort(const TeamWs& ws, uint64_t n, GetKey get, i
           if (old == kEmpty64) { fresh = true; break; }
           if (old == k) break;
         }
-        s = (s + 1) & (uint32_t)(ws.hcap - 1);
+        s = (s + 1) & hmask;
       }
-      if (t == ws.hcap) ws.sh[2] = 1u;
+      if (t == hcap) ws.sh[2] = 1u;
     }
     if (fresh) {
       uint32_t idx = atomicAdd(&ws.sh[0], 1u);
       if (idx < (uint32_t)ws.ucap) ws.uniq[idx] = k; else ws.sh[2] = 1u;
+      atomicOr((unsigned long long*)&ws.bitv[0], (unsigned long long)k);
+      atomicAnd((unsigned long long*)&ws.bitv[1], (unsigned long long)k);
     }
   }
   team_sync<NT>();
@@ -231,18 +268,18 @@ __device__ uint32_t team_dedupe_sort(const TeamWs& ws, uint64_t n, GetKey get, i
   while ((2u << bits) < U) ++bits;  // NB = 2^bits ~ U/2
   if (U <= 2) bits = 0;
   const int NB = 1 << bits;
+  const uint64_t diff = ws.bitv[0] ^ ws.bitv[1];
+  const int top = diff ? 63 - __clzll((long long)diff) : 0;  // highest differing bit
+  const int shift = (top + 1 >= bits) ? top + 1 - bits : 0;
+  const uint64_t bmask = (uint64_t)(NB - 1);
   for (int b = rank; b < NB; b += NT) ws.cnt[b] = 0;
   team_sync<NT>();
-  for (uint32_t i = rank; i < U; i += NT) {
-    uint32_t b = bits ? (uint32_t)(ws.uniq[i] >> (64 - bits)) : 0u;
-    atomicAdd(&ws.cnt[b], 1u);
-  }
+  for (uint32_t i = rank; i < U; i += NT) atomicAdd(&ws.cnt[(ws.uniq[i] >> shift) & bmask], 1u);
   team_sync<NT>();
   team_excl_scan<NT>(ws.cnt, NB, ws.wtot, rank);
   for (uint32_t i = rank; i < U; i += NT) {
-    uint64_t k = ws.uniq[i];
-    uint32_t b = bits ? (uint32_t)(k >> (64 - bits)) : 0u;
-    uint32_t p = atomicAdd(&ws.cnt[b], 1u);
+    const uint64_t k = ws.uniq[i];
+    const uint32_t p = atomicAdd(&ws.cnt[(k >> shift) & bmask], 1u);
     ws.set[p] = k;
   }
   team_sync<NT>();
@@ -377,34 +414,21 @@ __global__ void __launch_bounds__(256) k_sig_small(SigArgs a, const uint32_t* no
 constexpr int kWarpHcap = 2 * kWarpMax;
 constexpr int kWarpUcap = kWarpMax;
 constexpr int kWarpsPerBlock = 8;
-constexpr size_t kWarpWsBytes = kWarpHcap * 8 + kWarpUcap * 8 + (kWarpUcap / 2) * 4 + 4 * 4 + 16;
-
-__device__ __forceinline__ TeamWs carve(char* base, int hcap, int ucap, int nwarps) {
-  TeamWs ws;
-  ws.set = reinterpret_cast<uint64_t*>(base);
-  ws.uniq = ws.set + hcap;
-  ws.cnt = reinterpret_cast<uint32_t*>(ws.uniq + ucap);
-  ws.sh = ws.cnt + ucap / 2;
-  ws.wtot = ws.sh + 4;
-  ws.hcap = hcap;
-  ws.ucap = ucap;
-  (void)nwarps;
-  return ws;
-}
+constexpr size_t kWarpWsBytes = team_ws_bytes(kWarpHcap, kWarpUcap, 32);
 
 template <typename LabelT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sig_warp(SigArgs a, const uint32_t* nodes, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TeamWs ws = carve(smem + w * kWarpWsBytes, kWarpHcap, kWarpUcap, 1);
+  TeamWs ws = carve(smem + w * kWarpWsBytes, kWarpHcap, kWarpUcap, 32);
   for (uint64_t idx = (uint64_t)blockIdx.x * kWarpsPerBlock + w; idx < count;
        idx += (uint64_t)gridDim.x * kWarpsPerBlock) {
     const uint32_t u = nodes[idx];
     const uint64_t off = a.off[u];
     const uint64_t d = a.off[u + 1] - off;
     auto get = [&](uint64_t i) { return edge_key<LabelT>(a, off + i); };
-    const uint32_t U = team_dedupe_sort<32>(ws, d, get, lane);
+    const uint32_t U = team_dedupe_sort<32>(ws, set_size_for(d, kWarpHcap), d, get, lane);
     if (U == 0xFFFFFFFFu) {  // cannot happen: at most d <= ucap distinct keys
       if (lane == 0) atomicOr(a.err, kErrHubOverflow);
       continue;
@@ -422,26 +446,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // Out-degree kWarpMax+1..kBlockMax (one CTA per node) and hub buckets.
 constexpr int kBlkHcap = 2 * kBlockMax;
 constexpr int kBlkUcap = kBlockMax;
-constexpr size_t kBlkWsBytes = kBlkHcap * 8 + kBlkUcap * 8 + (kBlkUcap / 2) * 4 + 4 * 4 +
-                               (kBlockThreads / 32) * 4 + 8 + (kBlockThreads / 32) * 8;
-
-__device__ __forceinline__ uint64_t* blk_red(char* smem) {
-  return reinterpret_cast<uint64_t*>(smem + kBlkHcap * 8 + kBlkUcap * 8 + (kBlkUcap / 2) * 4 + 16 +
-                                     (kBlockThreads / 32) * 4 + 8);
-}
+constexpr size_t kBlkWsBytes = team_ws_bytes(kBlkHcap, kBlkUcap, kBlockThreads);
 
 template <typename LabelT>
 __global__ void __launch_bounds__(kBlockThreads)
     k_sig_block(SigArgs a, const uint32_t* nodes, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads / 32);
-  uint64_t* red = blk_red(smem);
+  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads);
+  uint64_t* red = ws.red;
   for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const uint32_t u = nodes[idx];
     const uint64_t off = a.off[u];
     const uint64_t d = a.off[u + 1] - off;
     auto get = [&](uint64_t i) { return edge_key<LabelT>(a, off + i); };
-    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, d, get, threadIdx.x);
+    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, set_size_for(d, kBlkHcap), d, get, threadIdx.x);
     if (U == 0xFFFFFFFFu) {
       if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
       __syncthreads();
@@ -564,14 +582,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
 __global__ void __launch_bounds__(kBlockThreads)
     k_hub_bucket(HubArgs h, uint64_t n_buckets, uint64_t seed, uint32_t* err) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads / 32);
-  uint64_t* red = blk_red(smem);
+  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads);
+  uint64_t* red = ws.red;
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
     const uint64_t lo = h.hist[b];
     const uint64_t hi = h.cursor[b];  // after the scatter, cursor = end of bucket
     const uint64_t* src = h.tmp + lo;
     auto get = [&](uint64_t i) { return src[i]; };
-    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, hi - lo, get, threadIdx.x);
+    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, set_size_for(hi - lo, kBlkHcap), hi - lo, get,
+                                                       threadIdx.x);
     if (U == 0xFFFFFFFFu) {
       if (threadIdx.x == 0) {
         atomicOr(err, kErrHubOverflow);
@@ -907,32 +926,39 @@ __device__ __forceinline__ int degree_class(uint64_t d) {
   return kClassHub;
 }
 
-__global__ void k_class_count(uint64_t n, const uint64_t* off, const uint8_t* alive,
-                              unsigned long long* cnt) {
+// Stable partition of the alive nodes by degree class, in tiles of 1024 nodes:
+// per-tile class counts, an exclusive scan over (class, tile) on the host,
+// then each tile writes its nodes in id order.
+constexpr int kClassTile = 1024;
+
+__global__ void __launch_bounds__(kClassTile)
+    k_class_tile_count(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
+                       unsigned long long* tcnt) {
   __shared__ unsigned int c[kNumClasses];
   if (threadIdx.x < kNumClasses) c[threadIdx.x] = 0;
   __syncthreads();
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n;
-       u += (uint64_t)gridDim.x * blockDim.x) {
-    if (alive && !alive[u]) continue;
-    atomicAdd(&c[degree_class(off[u + 1] - off[u])], 1u);
-  }
+  const uint64_t u = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
+  if (u < n && (!alive || alive[u])) atomicAdd(&c[degree_class(off[u + 1] - off[u])], 1u);
   __syncthreads();
-  if (threadIdx.x < kNumClasses && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
+  if (threadIdx.x < kNumClasses) tcnt[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = c[threadIdx.x];
 }
 
-__global__ void k_class_scatter(uint64_t n, const uint64_t* off, const uint8_t* alive,
-                                unsigned long long* cursor, uint32_t* small, uint32_t* warp,
-                                uint32_t* block, uint32_t* hub) {
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n;
-       u += (uint64_t)gridDim.x * blockDim.x) {
-    if (alive && !alive[u]) continue;
-    const int c = degree_class(off[u + 1] - off[u]);
-    const unsigned long long p = atomicAdd(&cursor[c], 1ull);
-    if (c < kSmallClasses) small[p] = (uint32_t)u;
-    else if (c == kClassWarp) warp[p] = (uint32_t)u;
-    else if (c == kClassBlock) block[p] = (uint32_t)u;
-    else hub[p] = (uint32_t)u;
+__global__ void __launch_bounds__(kClassTile)
+    k_class_tile_scatter(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
+                         const unsigned long long* tbase, uint32_t* out) {
+  __shared__ unsigned int wcount[kClassTile / 32];
+  const uint64_t u = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
+  const int cls = (u < n && (!alive || alive[u])) ? degree_class(off[u + 1] - off[u]) : -1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < kNumClasses; ++c) {
+    const unsigned m = __ballot_sync(kFull, cls == c);
+    if (lane == 0) wcount[w] = __popc(m);
+    __syncthreads();
+    unsigned before = 0;
+    for (int i = 0; i < w; ++i) before += wcount[i];
+    if (cls == c)
+      out[tbase[(uint64_t)c * ntiles + blockIdx.x] + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)u;
+    __syncthreads();
   }
 }
 
@@ -1119,62 +1145,66 @@ Status prepare_classes(Store& s) {
   if (!st.ok()) return st;
   const uint64_t n = s.n;
   const uint8_t* alive = s.any_dead ? ptr<uint8_t>(s.alive) : nullptr;
-  if (!(st = ensure(s, s.d_scalars, 16 * 8)).ok()) return st;
-  unsigned long long* cnt = ptr<unsigned long long>(s.d_scalars);
-  cudaMemsetAsync(cnt, 0, 16 * 8, s.stream);
-  const int sms = sm_count(s.device);
-  const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 16);
-  if (n) k_class_count<<<blocks, 256, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), alive, cnt);
-  if (!(st = launch_check("k_class_count")).ok()) return st;
-  uint64_t c[16];
-  {
-    Status st2 = cuda_check(cudaMemcpyAsync(s.h_scalars.p, cnt, 16 * 8, cudaMemcpyDeviceToHost, s.stream),
-                            "class counts");
-    if (!st2.ok()) return st2;
-    if (!(st2 = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st2;
-    std::memcpy(c, s.h_scalars.p, 16 * 8);
-  }
-  uint64_t small_total = 0;
-  for (int k = 0; k < kSmallClasses; ++k) {
-    s.small_start[k] = small_total;
-    s.small_count[k] = c[k];
-    small_total += c[k];
-  }
-  s.small_start[kSmallClasses] = small_total;
-  s.n_warp = c[kClassWarp];
-  s.n_block = c[kClassBlock];
-  s.n_hub = c[kClassHub];
-  if (!(st = ensure(s, s.small_nodes, std::max<uint64_t>(1, small_total) * 4)).ok()) return st;
-  if (!(st = ensure(s, s.warp_nodes, std::max<uint64_t>(1, s.n_warp) * 4)).ok()) return st;
-  if (!(st = ensure(s, s.block_nodes, std::max<uint64_t>(1, s.n_block) * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hub_nodes, std::max<uint64_t>(1, s.n_hub) * 4)).ok()) return st;
-  uint64_t cur[16] = {0};
-  for (int k = 0; k < kSmallClasses; ++k) cur[k] = s.small_start[k];
-  std::memcpy(s.h_scalars.p, cur, 16 * 8);
-  cudaMemcpyAsync(cnt, s.h_scalars.p, 16 * 8, cudaMemcpyHostToDevice, s.stream);
+  const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
+  Buf tcnt;
+  if (!(st = ensure(s, tcnt, ntiles * kNumClasses * 8)).ok()) return st;
+  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumClasses * 8, s.stream);
   if (n)
-    k_class_scatter<<<blocks, 256, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), alive, cnt,
-                                                  ptr<uint32_t>(s.small_nodes), ptr<uint32_t>(s.warp_nodes),
-                                                  ptr<uint32_t>(s.block_nodes), ptr<uint32_t>(s.hub_nodes));
-  if (!(st = launch_check("k_class_scatter")).ok()) return st;
-  // hub layout on the host (few nodes)
+    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), alive, ntiles,
+                                                                      ptr<unsigned long long>(tcnt));
+  if (!(st = launch_check("k_class_tile_count")).ok()) { release(s, tcnt); return st; }
+  std::vector<uint64_t> h(ntiles * kNumClasses);
+  st = cuda_check(cudaMemcpyAsync(h.data(), tcnt.p, h.size() * 8, cudaMemcpyDeviceToHost, s.stream), "class counts");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) { release(s, tcnt); return st; }
+  uint64_t run = 0;
+  uint64_t cstart[kNumClasses + 1];
+  for (int c = 0; c < kNumClasses; ++c) {
+    cstart[c] = run;
+    for (uint64_t t = 0; t < ntiles; ++t) {
+      const uint64_t v = h[(uint64_t)c * ntiles + t];
+      h[(uint64_t)c * ntiles + t] = run;
+      run += v;
+    }
+  }
+  cstart[kNumClasses] = run;
+  st = cuda_check(cudaMemcpyAsync(tcnt.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s.stream), "class bases");
+  if (st.ok()) st = ensure(s, s.class_nodes, std::max<uint64_t>(1, run) * 4);
+  if (!st.ok()) { release(s, tcnt); return st; }
+  if (n)
+    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(
+        n, ptr<uint64_t>(s.offsets), alive, ntiles, ptr<unsigned long long>(tcnt), ptr<uint32_t>(s.class_nodes));
+  st = launch_check("k_class_tile_scatter");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  release(s, tcnt);
+  if (!st.ok()) return st;
+  for (int c = 0; c <= kNumClasses; ++c) s.class_start[c] = cstart[c];
+  for (int k = 0; k < kSmallClasses; ++k) {
+    s.small_start[k] = cstart[k];
+    s.small_count[k] = cstart[k + 1] - cstart[k];
+  }
+  s.small_start[kSmallClasses] = cstart[kSmallClasses];
+  s.n_warp = cstart[kClassWarp + 1] - cstart[kClassWarp];
+  s.n_block = cstart[kClassBlock + 1] - cstart[kClassBlock];
+  s.n_hub = cstart[kClassHub + 1] - cstart[kClassHub];
+  // hub layout on the host (few nodes, already in id order)
   s.hub_extra_bits = 0;
   s.h_hub_deg.assign(s.n_hub, 0);
   s.h_hub_degbits.assign(s.n_hub, 0);
   s.hub_edges = 0;
   if (s.n_hub) {
     std::vector<uint32_t> hn(s.n_hub);
-    st = cuda_check(cudaMemcpyAsync(hn.data(), s.hub_nodes.p, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream),
-                    "hub nodes");
+    const uint32_t* hubs = ptr<uint32_t>(s.class_nodes) + cstart[kClassHub];
+    st = cuda_check(cudaMemcpyAsync(hn.data(), hubs, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream), "hub nodes");
     if (!st.ok()) return st;
     if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st;
-    std::sort(hn.begin(), hn.end());
     std::vector<uint64_t> lo(s.n_hub), hi(s.n_hub);
     for (uint64_t i = 0; i < s.n_hub; ++i) {
       cudaMemcpyAsync(&lo[i], ptr<uint64_t>(s.offsets) + hn[i], 8, cudaMemcpyDeviceToHost, s.stream);
       cudaMemcpyAsync(&hi[i], ptr<uint64_t>(s.offsets) + hn[i] + 1, 8, cudaMemcpyDeviceToHost, s.stream);
     }
     if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "hub offsets")).ok()) return st;
+    std::vector<uint4> chunks;
     for (uint64_t i = 0; i < s.n_hub; ++i) {
       const uint64_t d = hi[i] - lo[i];
       s.h_hub_deg[i] = d;
@@ -1182,20 +1212,13 @@ Status prepare_classes(Store& s) {
       while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
       s.h_hub_degbits[i] = bits;
       s.hub_edges += d;
-    }
-    st = cuda_check(cudaMemcpyAsync(s.hub_nodes.p, hn.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream),
-                    "hub nodes");
-    if (!st.ok()) return st;
-    // chunk list
-    std::vector<uint4> chunks;
-    for (uint64_t i = 0; i < s.n_hub; ++i) {
-      for (uint64_t b = 0; b < s.h_hub_deg[i]; b += kHubChunk) {
+      for (uint64_t b = 0; b < d; b += kHubChunk) {
         const uint64_t e = lo[i] + b;
         uint4 q;
         q.x = (uint32_t)i;
         q.y = (uint32_t)(e & 0xFFFFFFFFu);
         q.z = (uint32_t)(e >> 32);
-        q.w = (uint32_t)std::min<uint64_t>(kHubChunk, s.h_hub_deg[i] - b);
+        q.w = (uint32_t)std::min<uint64_t>(kHubChunk, d - b);
         chunks.push_back(q);
       }
     }
@@ -1327,7 +1350,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
   L.bstart[kSmallClasses] = b;
   if (b) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL);
-    k_sig_small<LabelT><<<b, kSmallWarps * 32, 0, s.stream>>>(a, ptr<uint32_t>(s.small_nodes), L);
+    k_sig_small<LabelT><<<b, kSmallWarps * 32, 0, s.stream>>>(a, ptr<uint32_t>(s.class_nodes), L);
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
   if (s.n_warp) {
@@ -1335,21 +1358,21 @@ Status run_signatures(Store& s, const SigArgs& a) {
     const unsigned g = (unsigned)std::min<uint64_t>((s.n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                     (uint64_t)sms * 8);
     k_sig_warp<LabelT><<<g, kWarpsPerBlock * 32, kWarpWsBytes * kWarpsPerBlock, s.stream>>>(
-        a, ptr<uint32_t>(s.warp_nodes), s.n_warp);
+        a, ptr<uint32_t>(s.class_nodes) + s.class_start[kClassWarp], s.n_warp);
   }
   if (!(st = launch_check("k_sig_warp")).ok()) return st;
   if (s.n_block) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>(s.n_block, (uint64_t)sms * 4);
-    k_sig_block<LabelT><<<g, kBlockThreads, kBlkWsBytes, s.stream>>>(a, ptr<uint32_t>(s.block_nodes),
-                                                                     s.n_block);
+    k_sig_block<LabelT><<<g, kBlockThreads, kBlkWsBytes, s.stream>>>(
+        a, ptr<uint32_t>(s.class_nodes) + s.class_start[kClassBlock], s.n_block);
   }
   if (!(st = launch_check("k_sig_block")).ok()) return st;
   if (s.n_hub) {
     for (int attempt = 0;; ++attempt) {
       if (!(st = hub_layout(s)).ok()) return st;
       HubArgs h;
-      h.hub_nodes = ptr<uint32_t>(s.hub_nodes);
+      h.hub_nodes = ptr<uint32_t>(s.class_nodes) + s.class_start[kClassHub];
       h.hub_bits = ptr<uint32_t>(s.hub_bits);
       h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
       h.chunks = ptr<uint4>(s.hub_chunks);
