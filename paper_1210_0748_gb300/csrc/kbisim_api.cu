@@ -64,7 +64,7 @@ T* ptr(Buf& b) { return static_cast<T*>(b.p); }
 
 unsigned grid(uint64_t work, unsigned per) {
   uint64_t g = (work + per - 1) / per;
-  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 65535ull * 16));
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 152ull * 32));
 }
 
 // --- load kernels -----------------------------------------------------------
@@ -92,25 +92,6 @@ __global__ void k_label_max(uint64_t m, const T* lab, unsigned int* mx) {
     v = max(v, (unsigned int)lab[e]);
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
   if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
-}
-
-// Scatter COO edges into their CSR position (with label conversion).
-template <typename TI, typename TO>
-__global__ void k_place_edges(uint64_t m, const uint32_t* src, const uint32_t* dst_in, const TI* lab_in,
-                              unsigned long long* cursor, uint32_t* dst_out, TO* lab_out) {
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t p = atomicAdd(&cursor[src[e]], 1ull);
-    dst_out[p] = dst_in[e];
-    lab_out[p] = (TO)lab_in[e];
-  }
-}
-
-template <typename TI, typename TO>
-__global__ void k_convert(uint64_t m, const TI* in, TO* out) {
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x)
-    out[e] = (TO)in[e];
 }
 
 __global__ void k_degree_count(uint64_t m, const uint32_t* src, unsigned long long* deg) {
@@ -224,19 +205,25 @@ Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned 
 }
 
 void free_graph(Store& s) {
-  Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.alive, &s.class_nodes, &s.hub_bits, &s.hub_bbase, &s.hub_chunks, &s.sigkey,
-                 &s.ucnt, &s.hash, &s.tkey, &s.tmin, &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.bsum,
-                 &s.hub_hist, &s.hub_cursor, &s.hub_ucnt, &s.hub_hpart, &s.hub_tmp, &s.hub_tmp2};
+  Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.p2o, &s.o2p, &s.hub_bits, &s.hub_bbase,
+                 &s.hub_chunks, &s.sigkey, &s.ucnt, &s.hash, &s.table, &s.slot, &s.rep, &s.ulist[0],
+                 &s.ulist[1], &s.hflag, &s.rank_o, &s.bsum, &s.hub_hist, &s.hub_cursor, &s.hub_ucnt,
+                 &s.hub_hpart, &s.hub_tmp, &s.hub_tmp2, &s.alive_o};
   for (Buf* b : bufs) release(s, *b);
   for (Buf& b : s.level) release(s, b);
+  for (Buf& b : s.out_level) release(s, b);
   s.level.clear();
+  s.out_level.clear();
+  s.out_valid.clear();
   s.counts.clear();
   s.stats.clear();
   s.has_graph = false;
   s.has_levels = false;
   s.stable = false;
+  s.any_dead = false;
   s.computed = 0;
-  s.n = s.m = 0;
+  s.n = s.m = s.n_alive = 0;
+  s.n_hub = 0;
 }
 
 Status copy_in(Store& s, void* dstp, const void* srcp, size_t bytes, bool on_device) {
@@ -246,19 +233,36 @@ Status copy_in(Store& s, void* dstp, const void* srcp, size_t bytes, bool on_dev
                     "copy in");
 }
 
-template <typename TI>
-Status place_edges(Store& s, uint64_t m, const uint32_t* src, const uint32_t* dst_in, const void* lab_in,
-                   unsigned long long* cursor, bool out8) {
-  const unsigned g = grid(m, 256);
-  if (out8)
-    k_place_edges<TI, uint8_t><<<g, 256, 0, s.stream>>>(m, src, dst_in, static_cast<const TI*>(lab_in), cursor,
-                                                         ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel));
-  else
-    k_place_edges<TI, uint32_t><<<g, 256, 0, s.stream>>>(m, src, dst_in, static_cast<const TI*>(lab_in), cursor,
-                                                          ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel));
-  return cuda_check(cudaGetLastError(), "place edges");
+template <typename T>
+__global__ void k_place_coo(uint64_t m, const uint32_t* src, const uint32_t* dst_in, const T* lab_in,
+                            unsigned long long* cursor, uint32_t* dst_out, T* lab_out) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = atomicAdd(&cursor[src[e]], 1ull);
+    dst_out[p] = dst_in[e];
+    lab_out[p] = lab_in[e];
+  }
 }
 
+uint32_t bits_needed(uint64_t v) {  // bits for values 0..v
+  uint32_t b = 1;
+  while (b < 64 && (v >> b)) ++b;
+  return b;
+}
+
+// Temporary device buffers of one load, released on every exit path.
+struct Temps {
+  Store& s;
+  Buf b[8];
+  explicit Temps(Store& st) : s(st) {}
+  ~Temps() {
+    for (Buf& x : b) release(s, x);
+  }
+};
+
+// Load: bring the graph to the device as a CSR in original ids (copying host
+// inputs, or grouping COO edges by source with a counting sort), validate it,
+// then relabel it into the store's internal layout.
 Status load_graph(Store& s, const kbisim_graph* g) {
   if (!g) return Status::Err(KBISIM_ERR_INVALID_ARG, "graph is NULL");
   const uint64_t n = g->num_nodes, m = g->num_edges;
@@ -269,130 +273,114 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   if (m && (!g->dst || !g->edge_label)) return Status::Err(KBISIM_ERR_INVALID_ARG, "dst/edge_label is NULL");
   if (m && !g->offsets && !g->src) return Status::Err(KBISIM_ERR_INVALID_ARG, "need offsets or src");
   if (m && !n) return Status::Err(KBISIM_ERR_INVALID_ARG, "edges without nodes");
-  if (g->offsets && !n && m) return Status::Err(KBISIM_ERR_INVALID_ARG, "offsets without nodes");
   free_graph(s);
   Status st;
   const bool dev = g->on_device != 0;
-  s.n = n;
-  s.m = m;
   if (!(st = ensure(s, s.d_err, 64)).ok()) return st;
-  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  cudaMemsetAsync(s.d_err.p, 0, 64, s.stream);
   uint32_t* err = ptr<uint32_t>(s.d_err);
-  if (!(st = ensure(s, s.nlabel, std::max<uint64_t>(n, 1) * 4)).ok()) return st;
-  if (!(st = ensure(s, s.alive, std::max<uint64_t>(n, 1))).ok()) return st;
-  if (!(st = ensure(s, s.offsets, (n + 1) * 8)).ok()) return st;
-  if (!(st = ensure(s, s.dst, std::max<uint64_t>(m, 1) * 4)).ok()) return st;
-  if (!(st = copy_in(s, s.nlabel.p, g->node_label, n * 4, dev)).ok()) return st;
-  cudaMemsetAsync(s.alive.p, 1, std::max<uint64_t>(n, 1), s.stream);
-  s.any_dead = false;
-  // staging for labels (and COO src/dst) when they come from the host
-  Buf lab_stage, src_stage, dst_stage, scan_tmp;
-  const void* lab_in = g->edge_label;
-  const uint32_t* src_in = g->src;
-  const uint32_t* dst_in = g->dst;
-  auto cleanup = [&]() {
-    release(s, lab_stage);
-    release(s, src_stage);
-    release(s, dst_stage);
-    release(s, scan_tmp);
-  };
-  if (m && !dev) {
-    if (!(st = ensure(s, lab_stage, m * w)).ok()) { cleanup(); return st; }
-    if (!(st = copy_in(s, lab_stage.p, g->edge_label, m * w, false)).ok()) { cleanup(); return st; }
-    lab_in = lab_stage.p;
+  Temps t(s);
+  Buf &off_b = t.b[0], &dst_b = t.b[1], &lab_b = t.b[2], &nlab_b = t.b[3], &src_b = t.b[4], &cur_b = t.b[5],
+      &scan_b = t.b[6];
+  // node labels
+  const uint32_t* nlab0 = g->node_label;
+  if (!dev && n) {
+    if (!(st = ensure(s, nlab_b, n * 4)).ok()) return st;
+    if (!(st = copy_in(s, nlab_b.p, g->node_label, n * 4, false)).ok()) return st;
+    nlab0 = ptr<uint32_t>(nlab_b);
   }
-  unsigned int* d_max = reinterpret_cast<unsigned int*>(ptr<uint32_t>(s.d_err) + 4);
-  cudaMemsetAsync(d_max, 0, 4, s.stream);
+  // edge labels and targets as given
+  const void* lab_in = g->edge_label;
+  const uint32_t* dst_in = g->dst;
+  const uint32_t* src_in = g->src;
+  if (!dev && m) {
+    if (!(st = ensure(s, lab_b, m * w)).ok()) return st;
+    if (!(st = copy_in(s, lab_b.p, g->edge_label, m * w, false)).ok()) return st;
+    lab_in = lab_b.p;
+    if (!(st = ensure(s, dst_b, m * 4)).ok()) return st;
+    if (!(st = copy_in(s, dst_b.p, g->dst, m * 4, false)).ok()) return st;
+    dst_in = ptr<uint32_t>(dst_b);
+    if (!g->offsets) {
+      if (!(st = ensure(s, src_b, m * 4)).ok()) return st;
+      if (!(st = copy_in(s, src_b.p, g->src, m * 4, false)).ok()) return st;
+      src_in = ptr<uint32_t>(src_b);
+    }
+  }
+  unsigned int* d_max = reinterpret_cast<unsigned int*>(err + 4);
   if (m) {
     const unsigned gb = grid(m, 256);
     if (w == 1) k_label_max<uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), d_max);
     else if (w == 2) k_label_max<uint16_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), d_max);
     else k_label_max<uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), d_max);
+    k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, dst_in, err);
+    if (!g->offsets) k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
   }
-  unsigned int maxlab = 0;
-  if (!(st = cuda_check(cudaMemcpyAsync(&maxlab, d_max, 4, cudaMemcpyDeviceToHost, s.stream), "label max")).ok()) {
-    cleanup();
-    return st;
-  }
-  if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) { cleanup(); return st; }
-  s.label8 = maxlab < 256;
-  if (!(st = ensure(s, s.elabel, std::max<uint64_t>(m, 1) * (s.label8 ? 1 : 4))).ok()) { cleanup(); return st; }
-  unsigned long long* off = ptr<unsigned long long>(s.offsets);
+  // offsets in original ids
+  const uint64_t* off0 = g->offsets;
   if (g->offsets) {
-    if (!(st = copy_in(s, off, g->offsets, (n + 1) * 8, dev)).ok()) { cleanup(); return st; }
-    if (n) k_check_offsets<<<grid(n, 256), 256, 0, s.stream>>>(n, m, ptr<uint64_t>(s.offsets), err);
-    if (!(st = copy_in(s, s.dst.p, g->dst, m * 4, dev)).ok()) { cleanup(); return st; }
-    if (m) {
-      const unsigned gb = grid(m, 256);
-      if (s.label8) {
-        if (w == 1) k_convert<uint8_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), ptr<uint8_t>(s.elabel));
-        else if (w == 2) k_convert<uint16_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), ptr<uint8_t>(s.elabel));
-        else k_convert<uint32_t, uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), ptr<uint8_t>(s.elabel));
-      } else {
-        if (w == 2) k_convert<uint16_t, uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), ptr<uint32_t>(s.elabel));
-        else k_convert<uint32_t, uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), ptr<uint32_t>(s.elabel));
-      }
-      if (!(st = cuda_check(cudaGetLastError(), "convert labels")).ok()) { cleanup(); return st; }
+    if (!dev) {
+      if (!(st = ensure(s, off_b, (n + 1) * 8)).ok()) return st;
+      if (!(st = copy_in(s, off_b.p, g->offsets, (n + 1) * 8, false)).ok()) return st;
+      off0 = ptr<uint64_t>(off_b);
     }
-  } else {
-    if (m && !dev) {
-      if (!(st = ensure(s, src_stage, m * 4)).ok()) { cleanup(); return st; }
-      if (!(st = ensure(s, dst_stage, m * 4)).ok()) { cleanup(); return st; }
-      if (!(st = copy_in(s, src_stage.p, g->src, m * 4, false)).ok()) { cleanup(); return st; }
-      if (!(st = copy_in(s, dst_stage.p, g->dst, m * 4, false)).ok()) { cleanup(); return st; }
-      src_in = ptr<uint32_t>(src_stage);
-      dst_in = ptr<uint32_t>(dst_stage);
-    }
+    if (n) k_check_offsets<<<grid(n, 256), 256, 0, s.stream>>>(n, m, off0, err);
+  }
+  uint32_t hv[8] = {0};
+  if (!(st = cuda_check(cudaMemcpyAsync(hv, err, 32, cudaMemcpyDeviceToHost, s.stream), "validate")).ok()) return st;
+  if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st;
+  if (hv[0]) return Status::Err(KBISIM_ERR_INVALID_ARG, "invalid graph: node id >= num_nodes or bad offsets");
+  const unsigned int maxlab = hv[4];
+  if (!g->offsets) {
+    // COO: counting sort by source into temporary CSR buffers
+    Buf csr_dst, csr_lab;
+    if (!(st = ensure(s, off_b, (n + 1) * 8)).ok()) return st;
+    if (!(st = ensure(s, cur_b, (n + 1) * 8)).ok()) return st;
+    unsigned long long* off = ptr<unsigned long long>(off_b);
     cudaMemsetAsync(off, 0, (n + 1) * 8, s.stream);
+    if (m) k_degree_count<<<grid(m, 256), 256, 0, s.stream>>>(m, src_in, off);
+    if (!(st = exclusive_scan_u64(s, off, n + 1, ptr<unsigned long long>(cur_b), scan_b)).ok()) return st;
+    off0 = ptr<uint64_t>(off_b);
     if (m) {
-      k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
-      uint32_t e0 = 0;
-      cudaMemcpyAsync(&e0, err, 4, cudaMemcpyDeviceToHost, s.stream);
-      if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) { cleanup(); return st; }
-      if (e0) {
-        cleanup();
-        free_graph(s);
-        return Status::Err(KBISIM_ERR_INVALID_ARG, "a source id is >= num_nodes");
-      }
-      k_degree_count<<<grid(m, 256), 256, 0, s.stream>>>(m, src_in, off);
-    }
-    Buf cursor;
-    if (!(st = ensure(s, cursor, (n + 1) * 8)).ok()) { cleanup(); return st; }
-    // off = [d_0, ..., d_{n-1}, 0]; its exclusive scan is the CSR offsets
-    // (off[u] = sum of degrees before u, off[n] = m) and seeds the cursors.
-    if (!(st = exclusive_scan_u64(s, off, n + 1, ptr<unsigned long long>(cursor), scan_tmp)).ok()) {
-      release(s, cursor);
-      cleanup();
-      return st;
-    }
-    if (m) {
-      Status (*fn)(Store&, uint64_t, const uint32_t*, const uint32_t*, const void*, unsigned long long*, bool) =
-          w == 1 ? place_edges<uint8_t> : (w == 2 ? place_edges<uint16_t> : place_edges<uint32_t>);
-      if (!(st = fn(s, m, src_in, dst_in, lab_in, ptr<unsigned long long>(cursor), s.label8)).ok()) {
-        release(s, cursor);
-        cleanup();
+      if (!(st = ensure(s, csr_dst, m * 4)).ok()) return st;
+      if (!(st = ensure(s, csr_lab, m * w)).ok()) { release(s, csr_dst); return st; }
+      const unsigned gb = grid(m, 256);
+      unsigned long long* cur = ptr<unsigned long long>(cur_b);
+      if (w == 1)
+        k_place_coo<uint8_t><<<gb, 256, 0, s.stream>>>(m, src_in, dst_in, static_cast<const uint8_t*>(lab_in), cur,
+                                                       ptr<uint32_t>(csr_dst), ptr<uint8_t>(csr_lab));
+      else if (w == 2)
+        k_place_coo<uint16_t><<<gb, 256, 0, s.stream>>>(m, src_in, dst_in, static_cast<const uint16_t*>(lab_in),
+                                                        cur, ptr<uint32_t>(csr_dst), ptr<uint16_t>(csr_lab));
+      else
+        k_place_coo<uint32_t><<<gb, 256, 0, s.stream>>>(m, src_in, dst_in, static_cast<const uint32_t*>(lab_in),
+                                                        cur, ptr<uint32_t>(csr_dst), ptr<uint32_t>(csr_lab));
+      st = cuda_check(cudaGetLastError(), "place edges");
+      if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+      if (!st.ok()) {
+        release(s, csr_dst);
+        release(s, csr_lab);
         return st;
       }
+      // the grouped copies replace the staged ones
+      release(s, dst_b);
+      release(s, lab_b);
+      release(s, src_b);
+      dst_b = csr_dst;
+      lab_b = csr_lab;
+      dst_in = ptr<uint32_t>(dst_b);
+      lab_in = lab_b.p;
     }
-    if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) {
-      release(s, cursor);
-      cleanup();
-      return st;
-    }
-    release(s, cursor);
   }
-  if (m) k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, ptr<uint32_t>(s.dst), err);
-  uint32_t e = 0;
-  cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s.stream);
-  st = cuda_check(cudaStreamSynchronize(s.stream), "load sync");
-  cleanup();
-  if (!st.ok()) return st;
-  if (e) {
+  s.n = n;
+  s.m = m;
+  s.label8 = maxlab < 256;
+  s.label_bits = bits_needed(maxlab);
+  if (!(st = relabel_graph(s, off0, dst_in, lab_in, nlab0, nullptr, w)).ok()) {
     free_graph(s);
-    return Status::Err(KBISIM_ERR_INVALID_ARG, "invalid graph: node id >= num_nodes or bad offsets");
+    return st;
   }
   s.has_graph = true;
-  return prepare_classes(s);
+  return Status::Ok();
 }
 
 Status ensure_levels(Store& s, uint32_t k) {
@@ -402,6 +390,24 @@ Status ensure_levels(Store& s, uint32_t k) {
     if (!st.ok()) return st;
   }
   if (s.counts.size() < (size_t)k + 1) s.counts.resize(k + 1, 0);
+  return Status::Ok();
+}
+
+void invalidate_outputs(Store& s) {
+  for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
+}
+
+// Original-order copy of level l (kept until the levels change).
+Status materialize_level(Store& s, uint32_t l) {
+  if (s.out_level.size() < s.level.size()) {
+    s.out_level.resize(s.level.size());
+    s.out_valid.resize(s.level.size(), false);
+  }
+  if (s.out_valid[l]) return Status::Ok();
+  Status st = ensure(s, s.out_level[l], std::max<uint64_t>(s.n, 1) * 4);
+  if (!st.ok()) return st;
+  if (!(st = unpermute_level(s, l, ptr<uint32_t>(s.out_level[l]))).ok()) return st;
+  s.out_valid[l] = true;
   return Status::Ok();
 }
 
@@ -436,6 +442,7 @@ Status refine(Store& s, uint32_t k, kbisim_result* out) {
   if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
   if (k > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
   Status st;
+  invalidate_outputs(s);
   if (!(st = ensure_levels(s, s.early_stop ? std::min<uint32_t>(k, 1) : k)).ok()) return st;
   s.has_levels = false;
   s.stable = false;
@@ -457,6 +464,7 @@ Status extend(Store& s, uint32_t k_new, kbisim_result* out) {
   if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
   if (k_new > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
   Status st;
+  invalidate_outputs(s);
   const bool need = k_new > s.computed && !(s.early_stop && s.stable);
   if (need) {
     for (uint32_t i = s.computed + 1; i <= k_new; ++i) {
@@ -586,16 +594,31 @@ int kbisim_pids(kbisim_handle* h, uint32_t level, uint32_t* dst, int dst_on_devi
   if (!dst && s.n) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "dst is NULL"));
   cudaSetDevice(s.device);
   const uint32_t l = std::min(level, s.computed);
-  Status st = kb::cuda_check(cudaMemcpyAsync(dst, s.level[l].p, s.n * 4,
-                                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                             s.stream), "copy out");
+  Status st;
+  if (dst_on_device) {
+    st = kb::unpermute_level(s, l, dst);
+  } else {
+    st = kb::materialize_level(s, l);
+    if (st.ok())
+      st = kb::cuda_check(cudaMemcpyAsync(dst, s.out_level[l].p, s.n * 4, cudaMemcpyDeviceToHost, s.stream),
+                          "copy out");
+  }
   if (st.ok()) st = kb::cuda_check(cudaStreamSynchronize(s.stream), "sync");
   return finish(h, st);
 }
 
 const uint32_t* kbisim_pids_device(kbisim_handle* h, uint32_t level) {
   if (!h || !h->s.has_levels || level > h->s.k_requested) return nullptr;
-  return static_cast<const uint32_t*>(h->s.level[std::min(level, h->s.computed)].p);
+  kb::Store& s = h->s;
+  cudaSetDevice(s.device);
+  const uint32_t l = std::min(level, s.computed);
+  Status st = kb::materialize_level(s, l);
+  if (st.ok()) st = kb::cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) {
+    h->last_error = st.msg;
+    return nullptr;
+  }
+  return static_cast<const uint32_t*>(s.out_level[l].p);
 }
 
 uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
@@ -628,12 +651,14 @@ int kbisim_get_round_stats(const kbisim_handle* h, uint32_t round, kbisim_round_
 
 int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_result* out,
                   uint64_t* missing_deletes) {
-  (void)b;
-  (void)k;
-  (void)out;
-  (void)missing_deletes;
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  return finish(h, Status::Err(KBISIM_ERR_STATE, "kbisim_update is not available yet"));
+  if (k > KBISIM_MAX_K) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "k too large"));
+  cudaSetDevice(h->s.device);
+  uint64_t missing = 0;
+  Status st = kb::apply_batch(h->s, b, &missing);
+  if (st.ok()) st = kb::refine(h->s, k, out);
+  if (st.ok() && missing_deletes) *missing_deletes = missing;
+  return finish(h, st);
 }
 
 }  // extern "C"

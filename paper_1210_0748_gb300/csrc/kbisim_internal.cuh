@@ -25,9 +25,11 @@ constexpr int kWarpMax = 256;      // 33..256: one warp per node, shared-memory 
 constexpr int kBlockMax = 4096;    // 257..4096: one CTA per node
 constexpr int kBlockThreads = 512; // threads of the CTA-per-node and hub kernels
 constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
-constexpr int kHubUniqueCap = 4096;     // distinct keys one hub bucket can hold
 constexpr int kHubChunk = 8192;         // hub edges per partition CTA (16 per thread)
 constexpr int kSmallClasses = 6;        // P = 1, 2, 4, 8, 16, 32
+constexpr int kClassWarp = kSmallClasses, kClassBlock = kSmallClasses + 1,
+              kClassHub = kSmallClasses + 2, kClassDead = kSmallClasses + 3;
+constexpr int kNumClasses = kSmallClasses + 4;  // including deleted nodes (last)
 
 // Device error flags (bit set in Store::d_err).
 enum : uint32_t {
@@ -38,9 +40,10 @@ enum : uint32_t {
 };
 
 // ---------------------------------------------------------------------------
-// Hashing.  mix64 is the output function of SplitMix64 (Steele, Lea and
-// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014, with
-// Vigna's constants); it is a bijection on 64-bit words.
+// Mixing functions.  mix64 is the output function of SplitMix64 (Steele, Lea
+// and Flood, OOPSLA 2014, with Vigna's constants); mix32 is the 32-bit
+// finalizer of MurmurHash3 (Appleby).  Both are bijections: xor-shifts and
+// multiplications by odd constants are invertible.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
@@ -51,18 +54,47 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x;
 }
 
-// A signature element (edge label, child identifier) as one 64-bit word.
-// pack() is one-to-one, mix64 is one-to-one, so equal words <=> equal
-// elements.  Signatures are stored as the ascending sequence of these mixed
-// words: a canonical order (equal sets give equal sequences) whose values are
-// spread uniformly, which the bucketed sorts below rely on for balance.
-__host__ __device__ __forceinline__ uint64_t elem_key(uint32_t label, uint32_t pid) {
-  return mix64(((uint64_t)label << 32) | (uint64_t)pid);
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
 }
 
+// A signature element (edge label, child identifier) as one word of type K.
+// The pair is packed one-to-one -- (label << pbits) | pid with 32-bit words
+// when label and pid fit, (label << 32) | pid with 64-bit words otherwise --
+// and then passed through a bijective mix, so equal words <=> equal elements.
+// A node's signature set is stored as the ascending sequence of these words:
+// a canonical form (equal sets give equal sequences) whose values are spread
+// uniformly, which the bucketed sorts rely on for balance.
+template <typename K>
+struct KeyOps;
+
+template <>
+struct KeyOps<uint32_t> {
+  static constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+  static constexpr int kBits = 32;
+  __device__ __forceinline__ static uint32_t make(uint32_t label, uint32_t pid, int pbits) {
+    return mix32((label << pbits) | pid);
+  }
+};
+
+template <>
+struct KeyOps<uint64_t> {
+  static constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
+  static constexpr int kBits = 64;
+  __device__ __forceinline__ static uint64_t make(uint32_t label, uint32_t pid, int) {
+    return mix64(((uint64_t)label << 32) | (uint64_t)pid);
+  }
+};
+
 // Commutative per-element hash term (summed over the set).
-__host__ __device__ __forceinline__ uint64_t elem_term(uint64_t key, uint64_t seed) {
-  return mix64(key + seed);
+template <typename K>
+__host__ __device__ __forceinline__ uint64_t elem_term(K key, uint64_t seed) {
+  return mix64((uint64_t)key + seed);
 }
 
 // Hash of a node's signature from its parts.  Never returns kEmpty64.
@@ -85,6 +117,12 @@ struct Buf {
 struct KernelTimer;  // per-kernel CUDA event timing (kbisim_round.cu)
 
 // The device graph store plus all scratch a round needs.  One per handle.
+//
+// Node ids are relabelled once per graph: internal id p orders the alive
+// nodes by (degree class, original id), deleted nodes last.  The edge table
+// is a CSR by source over internal ids (targets relabelled too), so every
+// degree class is a contiguous range of nodes whose edges are contiguous.
+// Levels are stored by internal id; copy-out restores original order.
 struct Store {
   // configuration
   int device = 0;
@@ -96,25 +134,23 @@ struct Store {
   bool checked = false;
   bool timing = false;
 
-  // graph (CSR by source, original node ids)
-  uint64_t n = 0, m = 0;
+  // graph in internal ids
+  uint64_t n = 0, m = 0;       // all nodes / edges
+  uint64_t n_alive = 0;        // internal ids [0, n_alive) are alive
   bool has_graph = false;
   bool label8 = true;          // edge labels stored as uint8 (else uint32)
-  bool any_dead = false;       // some node is deleted
+  uint32_t label_bits = 1;     // bits needed for the largest edge label
   Buf offsets;                 // uint64 [n+1]
-  Buf dst;                     // uint32 [m]
+  Buf dst;                     // uint32 [m] internal target ids
   Buf elabel;                  // uint8 or uint32 [m]
   Buf nlabel;                  // uint32 [n]
-  Buf alive;                   // uint8 [n] (1 = present)
+  Buf p2o;                     // uint32 [n] internal -> original id
+  Buf o2p;                     // uint32 [n] original -> internal id
+  bool any_dead = false;       // some node was deleted by a maintenance batch
+  Buf alive_o;                 // uint8 [n] alive flags in original order (when any_dead)
 
-  // degree classes, fixed per graph: alive nodes ordered by class, then id
-  Buf class_nodes;             // uint32
-  uint64_t class_start[kSmallClasses + 4] = {0};  // classes: P=1..32, warp, CTA, hub
-  uint64_t small_count[kSmallClasses] = {0};
-  uint64_t small_start[kSmallClasses + 1] = {0};
-  uint64_t n_warp = 0;         // out-degree 33..256
-  uint64_t n_block = 0;        // 257..4096
-  // hubs: out-degree > 4096
+  // degree classes (internal id ranges)
+  uint64_t class_start[kNumClasses + 1] = {0};
   uint64_t n_hub = 0;
   Buf hub_bits;                // uint32 [n_hub]  log2(bucket count)
   Buf hub_bbase;               // uint64 [n_hub+1] first bucket of each hub
@@ -123,11 +159,12 @@ struct Store {
   uint64_t n_hub_buckets = 0;
   uint64_t hub_edges = 0;
   uint32_t hub_extra_bits = 0; // grows if a bucket overflows
-  std::vector<uint32_t> h_hub_degbits;  // host copy: ceil(log2(deg / target)) per hub
-  std::vector<uint64_t> h_hub_deg;
+  std::vector<uint32_t> h_hub_degbits;
 
-  // levels (all kept: history for extend / maintenance)
-  std::vector<Buf> level;      // uint32 [n] per computed level
+  // levels (all kept: history for extend / maintenance), internal order
+  std::vector<Buf> level;
+  std::vector<Buf> out_level;  // original-order copies made on demand
+  std::vector<bool> out_valid;
   std::vector<uint64_t> counts;
   uint32_t computed = 0;       // highest computed level (valid if has_levels)
   bool has_levels = false;
@@ -137,24 +174,25 @@ struct Store {
   std::vector<kbisim_round_stats> stats;  // index r-1 for round r
 
   // round scratch
-  Buf sigkey;                  // uint64 [m]: sorted distinct keys per node at its CSR offset
+  Buf sigkey;                  // key words [m]: sorted distinct keys per node at its CSR offset
   Buf ucnt;                    // uint32 [n]
   Buf hash;                    // uint64 [n]
-  Buf tkey;                    // uint64 [cap] hash table keys
-  Buf tmin;                    // uint32 [cap] smallest node per key
+  Buf table;                   // 16-byte slots (key, smallest original id)
   uint64_t tcap = 0;
   Buf slot;                    // uint32 [n]
-  Buf rep;                     // uint32 [n]
+  Buf rep;                     // uint32 [n] internal id of the block head
   Buf ulist[2];                // uint32 [n] unresolved nodes (ping-pong)
+  Buf hflag;                   // uint8 [n] head flags in original order
+  Buf rank_o;                  // uint32 [n] block id of heads, original order
   Buf bsum;                    // uint64 scan block sums
   Buf hub_hist;                // uint64 [buckets]
   Buf hub_cursor;              // uint64 [buckets]
   Buf hub_ucnt;                // uint32 [buckets]
   Buf hub_hpart;               // uint64 [buckets]
-  Buf hub_tmp;                 // uint64 [hub_edges]
-  Buf hub_tmp2;                // uint64 [hub_edges]
+  Buf hub_tmp;                 // key words [hub_edges]
+  Buf hub_tmp2;                // key words [hub_edges]
   Buf d_err;                   // uint32 error flags
-  Buf d_scalars;               // uint64 [8] small device counters
+  Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars
 
   size_t bytes_held = 0;
@@ -182,12 +220,19 @@ Status ensure(Store& s, Buf& b, size_t bytes);
 void release(Store& s, Buf& b);
 Status cuda_check(cudaError_t e, const char* what);
 
-// Round driver (kbisim_round.cu)
-Status prepare_classes(Store& s);                 // degree classes and hub layout
+// Graph preparation and round driver (kbisim_round.cu)
+// Relabel a CSR given in original ids (device arrays owned by the caller;
+// labels of lab_bytes each; alive0 may be null = all alive) into the store's
+// internal layout.  s.n, s.m, s.label8 and s.label_bits must be set.
+Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const void* lab0,
+                     const uint32_t* nlab0, const uint8_t* alive0, uint32_t lab_bytes);
+// Apply a maintenance batch to the stored graph (kbisim_update.cu); leaves
+// the store with the updated graph loaded and no levels.
+Status apply_batch(Store& s, const kbisim_batch* b, uint64_t* missing);
 Status compute_level0(Store& s);                  // pId_0 into level[0]
 Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
-Status timer_begin(Store& s, int kernel_class);
-Status timer_end(Store& s, int kernel_class);
+// Write level `level` in original node order to dst (device memory).
+Status unpermute_level(Store& s, uint32_t level, uint32_t* dst);
 Status timer_collect(Store& s);
 void timer_destroy(Store& s);
 

@@ -1,25 +1,28 @@
-// One refinement round of k-bisimulation on the GPU, and level 0.
+// One refinement round of k-bisimulation on the GPU, level 0, and the
+// once-per-graph relabelling of node ids.
 //
 // Round i (Algorithm 1, the k > 0 branch; Definition 3; Proposition 2):
 //   (a) gather: for every edge e = (u, l, v) of the source-sorted edge table,
-//       the element key (l, pId_{i-1}(v))          -- Algorithm 1 "fill in
-//       pId_old(tId)" (the merge join ET x NT), done as a direct gather;
-//   (b) per source node: sort the keys and drop duplicates (the sorted,
-//       duplicate-free F of Algorithm 1), written at the node's CSR offset;
-//   (c) a 64-bit hash of (pId_{i-1}(u), the key set)  -- stands in for the
-//       signature store S (Section 3, "Data structures for S");
-//   (d) group nodes with equal hash in an open-addressing table that keeps
-//       the smallest node id per hash, compare every node's signature with
-//       that node's exactly (so a hash collision never merges two blocks),
-//       repair collisions, and number blocks by their smallest node id;
+//       the element (l, pId_{i-1}(v))  -- Algorithm 1 fills pId_old(tId) by a
+//       merge join of the edge and node tables; here it is a direct gather;
+//   (b) per source node: drop duplicate elements and sort the rest (the
+//       sorted, duplicate-free F of Algorithm 1), written at the node's CSR
+//       offset;
+//   (c) a 64-bit hash of (pId_{i-1}(u), the element set)  -- it only routes
+//       nodes to candidate groups; it stands in for the signature store S
+//       (Section 3, "Data structures for S");
+//   (d) group nodes with equal hash in an open-addressing table that keeps the
+//       smallest original node id per hash, compare every node's signature
+//       with that node's exactly (a hash collision never merges two blocks),
+//       repair collisions, and number blocks by their smallest original id;
 //   (e) the caller stops when the block count is unchanged.
 // Level 0 groups nodes by label the same way (Algorithm 1, k = 0 branch).
 //
-// Signature keys are compared through a fixed bijection (elem_key), and each
-// node's set is stored in ascending order of that bijection: any fixed order
-// is a canonical form for sets (the paper keeps sets as sorted strings,
-// Section 3.2); this one spreads values uniformly, which balances the
-// bucketed sorts.
+// Degree tiers of step (a)-(c): out-degree <= 32 uses P = 2^c lanes per node
+// and a bitonic network in registers; 33..256 one warp per node; 257..4096
+// one CTA per node (both with a shared-memory hash set, then a counting sort);
+// larger "hubs" are partitioned by key bits into buckets of about 2048
+// distinct keys, each bucket deduplicated and sorted by one CTA.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,21 +35,18 @@
 namespace kb {
 
 namespace {
-
 constexpr unsigned kFull = 0xFFFFFFFFu;
-
-// --------------------------------------------------------------------------
-// Kernel timing
-// --------------------------------------------------------------------------
 }  // namespace
 
+// --------------------------------------------------------------------------
+// Kernel timing (CUDA events on the handle's stream)
+// --------------------------------------------------------------------------
 struct KernelTimer {
   struct Rec {
     int cls;
     cudaEvent_t a, b;
   };
   std::vector<cudaEvent_t> pool;
-  std::vector<Rec> open;
   std::vector<Rec> done;
   cudaEvent_t get() {
     if (!pool.empty()) {
@@ -59,33 +59,6 @@ struct KernelTimer {
     return e;
   }
 };
-
-Status timer_begin(Store& s, int cls) {
-  s.launches[cls] += 1;
-  if (!s.timing) return Status::Ok();
-  if (!s.timer) s.timer = new KernelTimer();
-  KernelTimer::Rec r;
-  r.cls = cls;
-  r.a = s.timer->get();
-  r.b = s.timer->get();
-  cudaEventRecord(r.a, s.stream);
-  s.timer->open.push_back(r);
-  return Status::Ok();
-}
-
-Status timer_end(Store& s, int cls) {
-  if (!s.timing || !s.timer) return Status::Ok();
-  for (size_t i = s.timer->open.size(); i-- > 0;) {
-    if (s.timer->open[i].cls == cls) {
-      KernelTimer::Rec r = s.timer->open[i];
-      cudaEventRecord(r.b, s.stream);
-      s.timer->done.push_back(r);
-      s.timer->open.erase(s.timer->open.begin() + i);
-      break;
-    }
-  }
-  return Status::Ok();
-}
 
 Status timer_collect(Store& s) {
   if (!s.timer) return Status::Ok();
@@ -104,19 +77,35 @@ Status timer_collect(Store& s) {
 void timer_destroy(Store& s) {
   if (!s.timer) return;
   for (auto e : s.timer->pool) cudaEventDestroy(e);
-  for (auto& r : s.timer->open) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
-  for (auto& r : s.timer->done) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto& r : s.timer->done) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   delete s.timer;
   s.timer = nullptr;
 }
 
 namespace {
 
+// Records one CUDA event pair around the kernels launched in its scope.
 struct TimedScope {
   Store& s;
   int cls;
-  TimedScope(Store& st, int c) : s(st), cls(c) { timer_begin(s, c); }
-  ~TimedScope() { timer_end(s, cls); }
+  KernelTimer::Rec rec;
+  TimedScope(Store& st, int c) : s(st), cls(c) {
+    s.launches[c] += 1;
+    if (!s.timing) return;
+    if (!s.timer) s.timer = new KernelTimer();
+    rec.cls = c;
+    rec.a = s.timer->get();
+    rec.b = s.timer->get();
+    cudaEventRecord(rec.a, s.stream);
+  }
+  ~TimedScope() {
+    if (!s.timing) return;
+    cudaEventRecord(rec.b, s.stream);
+    s.timer->done.push_back(rec);
+  }
 };
 
 template <typename T>
@@ -127,16 +116,40 @@ inline unsigned grid_for(uint64_t work, unsigned per_block) {
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 0x7FFFFFFFull));
 }
 
+Status launch_check(const char* what) { return cuda_check(cudaGetLastError(), what); }
+
+int sm_count(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 148;
+  if (!cached[device]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    cached[device] = v > 0 ? v : 148;
+  }
+  return cached[device];
+}
+
 // --------------------------------------------------------------------------
-// Team helpers: a "team" is one warp (NT = 32) or one CTA (NT = blockDim).
+// Small device helpers
 // --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cas(uint32_t* a, uint32_t c, uint32_t v) { return atomicCAS(a, c, v); }
+__device__ __forceinline__ uint64_t cas(uint64_t* a, uint64_t c, uint64_t v) {
+  return atomicCAS((unsigned long long*)a, (unsigned long long)c, (unsigned long long)v);
+}
+__device__ __forceinline__ void aor(uint32_t* a, uint32_t v) { atomicOr(a, v); }
+__device__ __forceinline__ void aor(uint64_t* a, uint64_t v) { atomicOr((unsigned long long*)a, (unsigned long long)v); }
+__device__ __forceinline__ void aand(uint32_t* a, uint32_t v) { atomicAnd(a, v); }
+__device__ __forceinline__ void aand(uint64_t* a, uint64_t v) { atomicAnd((unsigned long long*)a, (unsigned long long)v); }
+__device__ __forceinline__ int top_bit(uint32_t x) { return 31 - __clz((int)x); }
+__device__ __forceinline__ int top_bit(uint64_t x) { return 63 - __clzll((long long)x); }
+
 template <int NT>
 __device__ __forceinline__ void team_sync() {
   if (NT == 32) __syncwarp(); else __syncthreads();
 }
 
-// Exclusive prefix sum of a[0..n) in shared memory by a team of NT threads.
-// warp_tot: NT/32 words of shared scratch (unused for NT == 32).
+// Exclusive prefix sum of a[0..n) in shared memory by a team of NT threads
+// (one warp, or one CTA of NT threads).  warp_tot: NT/32 shared words.
 template <int NT>
 __device__ void team_excl_scan(uint32_t* a, int n, uint32_t* warp_tot, int rank) {
   const int per = (n + NT - 1) / NT;
@@ -177,11 +190,14 @@ __device__ void team_excl_scan(uint32_t* a, int n, uint32_t* warp_tot, int rank)
   team_sync<NT>();
 }
 
-// Shared-memory layout of one team's dedupe-and-sort workspace.
+// --------------------------------------------------------------------------
+// Team dedupe + sort in shared memory
+// --------------------------------------------------------------------------
+template <typename K>
 struct TeamWs {
-  uint64_t* set;    // [hcap] hash set, reused as the sorted output
-  uint64_t* uniq;   // [ucap] distinct keys in arrival order
-  uint64_t* bitv;   // [2] OR and AND of the distinct keys
+  K* set;           // [hcap] hash set, reused as the sorted output
+  K* uniq;          // [ucap] distinct keys in arrival order
+  K* bitv;          // [2] OR and AND of the distinct keys
   uint64_t* red;    // [NT/32] reduction scratch
   uint32_t* cnt;    // [ucap/2] bucket counters
   uint32_t* sh;     // [4] distinct count, saw-empty-key flag, overflow flag
@@ -189,17 +205,19 @@ struct TeamWs {
   int hcap, ucap;
 };
 
+template <typename K>
 __host__ __device__ constexpr size_t team_ws_bytes(int hcap, int ucap, int nt) {
-  return ((size_t)hcap * 8 + (size_t)ucap * 8 + 16 + (size_t)(nt / 32) * 8 + (size_t)(ucap / 2) * 4 +
-          16 + (size_t)(nt / 32) * 4 + 15) / 16 * 16;
+  return ((size_t)hcap * sizeof(K) + (size_t)ucap * sizeof(K) + 16 + (size_t)(nt / 32) * 8 +
+          (size_t)(ucap / 2) * 4 + 16 + (size_t)(nt / 32) * 4 + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ TeamWs carve(char* base, int hcap, int ucap, int nt) {
-  TeamWs ws;
-  ws.set = reinterpret_cast<uint64_t*>(base);
+template <typename K>
+__device__ __forceinline__ TeamWs<K> carve(char* base, int hcap, int ucap, int nt) {
+  TeamWs<K> ws;
+  ws.set = reinterpret_cast<K*>(base);
   ws.uniq = ws.set + hcap;
   ws.bitv = ws.uniq + ucap;
-  ws.red = ws.bitv + 2;
+  ws.red = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws.bitv) + 16);
   ws.cnt = reinterpret_cast<uint32_t*>(ws.red + nt / 32);
   ws.sh = ws.cnt + ucap / 2;
   ws.wtot = ws.sh + 4;
@@ -215,78 +233,80 @@ __device__ __forceinline__ int set_size_for(uint64_t n, int cap) {
   return h;
 }
 
-// Distinct keys of n inputs, sorted ascending into ws.set[0..U).  Returns U,
-// or 0xFFFFFFFF if more than ucap distinct keys arrived (overflow).
-// Dedupe: open-addressing set of `hcap` slots in shared memory (keys are
-// uniformly mixed, so their low bits index it).  Sort: counting sort into
-// about U/2 buckets on the highest bits in which the distinct keys differ
-// (keys that share a prefix -- e.g. one hub bucket -- still spread out),
-// then insertion sort inside each (tiny) bucket.
-template <int NT, class GetKey>
-__device__ uint32_t team_dedupe_sort(const TeamWs& ws, int hcap, uint64_t n, GetKey get, int rank) {
-  for (int i = rank; i < hcap; i += NT) ws.set[i] = kEmpty64;
+template <int NT, typename K>
+__device__ __forceinline__ void team_begin(const TeamWs<K>& ws, int hcap, int rank) {
+  for (int i = rank; i < hcap; i += NT) ws.set[i] = KeyOps<K>::kEmpty;
   if (rank < 4) ws.sh[rank] = 0;
   if (rank == 0) {
-    ws.bitv[0] = 0ull;
-    ws.bitv[1] = ~0ull;
+    ws.bitv[0] = (K)0;
+    ws.bitv[1] = (K)~(K)0;
   }
-  team_sync<NT>();
-  volatile uint64_t* vset = ws.set;
-  const uint32_t hmask = (uint32_t)(hcap - 1);
-  for (uint64_t i = rank; i < n; i += NT) {
-    const uint64_t k = get(i);
-    bool fresh = false;
-    if (k == kEmpty64) {
-      fresh = atomicExch(&ws.sh[1], 1u) == 0u;
-    } else {
-      uint32_t s = (uint32_t)k & hmask;
-      int t = 0;
-      for (; t < hcap; ++t) {
-        uint64_t cur = vset[s];
-        if (cur == k) break;
-        if (cur == kEmpty64) {
-          uint64_t old = atomicCAS((unsigned long long*)&ws.set[s], (unsigned long long)kEmpty64,
-                                   (unsigned long long)k);
-          if (old == kEmpty64) { fresh = true; break; }
-          if (old == k) break;
-        }
-        s = (s + 1) & hmask;
+}
+
+// Insert one key into the team's shared-memory set; a key seen for the first
+// time is appended to ws.uniq.  Probing is bounded by the set size.
+template <typename K>
+__device__ __forceinline__ void team_insert(const TeamWs<K>& ws, int hcap, K k) {
+  bool fresh = false;
+  if (k == KeyOps<K>::kEmpty) {
+    fresh = atomicExch(&ws.sh[1], 1u) == 0u;
+  } else {
+    volatile K* vset = ws.set;
+    const uint32_t hmask = (uint32_t)(hcap - 1);
+    uint32_t s = (uint32_t)k & hmask;
+    int t = 0;
+    for (; t < hcap; ++t) {
+      const K cur = vset[s];
+      if (cur == k) break;
+      if (cur == KeyOps<K>::kEmpty) {
+        const K old = cas(&ws.set[s], KeyOps<K>::kEmpty, k);
+        if (old == KeyOps<K>::kEmpty) { fresh = true; break; }
+        if (old == k) break;
       }
-      if (t == hcap) ws.sh[2] = 1u;
+      s = (s + 1) & hmask;
     }
-    if (fresh) {
-      uint32_t idx = atomicAdd(&ws.sh[0], 1u);
-      if (idx < (uint32_t)ws.ucap) ws.uniq[idx] = k; else ws.sh[2] = 1u;
-      atomicOr((unsigned long long*)&ws.bitv[0], (unsigned long long)k);
-      atomicAnd((unsigned long long*)&ws.bitv[1], (unsigned long long)k);
-    }
+    if (t == hcap) ws.sh[2] = 1u;
   }
-  team_sync<NT>();
+  if (fresh) {
+    const uint32_t idx = atomicAdd(&ws.sh[0], 1u);
+    if (idx < (uint32_t)ws.ucap) ws.uniq[idx] = k; else ws.sh[2] = 1u;
+    aor(&ws.bitv[0], k);
+    aand(&ws.bitv[1], k);
+  }
+}
+
+// After all inserts (and a team sync): sort the distinct keys ascending into
+// ws.set[0..U).  Returns U, or 0xFFFFFFFF on overflow.  Counting sort into
+// about U/2 buckets on the highest bits in which the distinct keys differ (so
+// keys sharing a prefix -- one hub bucket -- still spread), then insertion
+// sort inside each tiny bucket.
+template <int NT, typename K>
+__device__ uint32_t team_sort(const TeamWs<K>& ws, int rank) {
   if (ws.sh[2]) return 0xFFFFFFFFu;
   const uint32_t U = ws.sh[0];
   int bits = 0;
   while ((2u << bits) < U) ++bits;  // NB = 2^bits ~ U/2
   if (U <= 2) bits = 0;
   const int NB = 1 << bits;
-  const uint64_t diff = ws.bitv[0] ^ ws.bitv[1];
-  const int top = diff ? 63 - __clzll((long long)diff) : 0;  // highest differing bit
+  const K diff = ws.bitv[0] ^ ws.bitv[1];
+  const int top = diff ? top_bit(diff) : 0;  // highest differing bit
   const int shift = (top + 1 >= bits) ? top + 1 - bits : 0;
-  const uint64_t bmask = (uint64_t)(NB - 1);
+  const K bmask = (K)(NB - 1);
   for (int b = rank; b < NB; b += NT) ws.cnt[b] = 0;
   team_sync<NT>();
-  for (uint32_t i = rank; i < U; i += NT) atomicAdd(&ws.cnt[(ws.uniq[i] >> shift) & bmask], 1u);
+  for (uint32_t i = rank; i < U; i += NT) atomicAdd(&ws.cnt[(uint32_t)((ws.uniq[i] >> shift) & bmask)], 1u);
   team_sync<NT>();
   team_excl_scan<NT>(ws.cnt, NB, ws.wtot, rank);
   for (uint32_t i = rank; i < U; i += NT) {
-    const uint64_t k = ws.uniq[i];
-    const uint32_t p = atomicAdd(&ws.cnt[(k >> shift) & bmask], 1u);
+    const K k = ws.uniq[i];
+    const uint32_t p = atomicAdd(&ws.cnt[(uint32_t)((k >> shift) & bmask)], 1u);
     ws.set[p] = k;
   }
   team_sync<NT>();
   for (int b = rank; b < NB; b += NT) {
     const uint32_t lo = b ? ws.cnt[b - 1] : 0u, hi = ws.cnt[b];
     for (uint32_t i = lo + 1; i < hi; ++i) {
-      uint64_t v = ws.set[i];
+      const K v = ws.set[i];
       uint32_t j = i;
       while (j > lo && ws.set[j - 1] > v) {
         ws.set[j] = ws.set[j - 1];
@@ -299,11 +319,10 @@ __device__ uint32_t team_dedupe_sort(const TeamWs& ws, int hcap, uint64_t n, Get
   return U;
 }
 
-// Sum of elem_term over ws.set[0..U) across the team (result valid in all lanes
-// of the team for NT == 32, in rank 0 for NT > 32).
-template <int NT>
-__device__ uint64_t team_term_sum(const uint64_t* keys, uint32_t U, uint64_t seed,
-                                  uint64_t* red, int rank) {
+// Sum of elem_term over keys[0..U) across the team (valid in every lane for
+// NT == 32, in rank 0 for NT > 32).
+template <int NT, typename K>
+__device__ uint64_t team_term_sum(const K* keys, uint32_t U, uint64_t seed, uint64_t* red, int rank) {
   uint64_t t = 0;
   for (uint32_t i = rank; i < U; i += NT) t += elem_term(keys[i], seed);
 #pragma unroll
@@ -326,150 +345,196 @@ struct SigArgs {
   const uint32_t* dst;
   const void* lab;
   const uint32_t* prev;
-  uint64_t* sigkey;
+  void* sigkey;
   uint32_t* ucnt;
   uint64_t* hash;
   uint64_t seed;
   uint64_t mask;
+  int pbits;          // bits of a child identifier in a 32-bit key
   uint32_t* err;
 };
 
-template <typename LabelT>
-__device__ __forceinline__ uint64_t edge_key(const SigArgs& a, uint64_t e) {
+template <typename LabelT, typename K>
+__device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e) {
   const LabelT* lab = static_cast<const LabelT*>(a.lab);
-  return elem_key((uint32_t)lab[e], a.prev[a.dst[e]]);
+  return KeyOps<K>::make((uint32_t)lab[e], a.prev[a.dst[e]], a.pbits);
 }
 
-// Out-degree <= 32: P = 2^c lanes per node (32/P nodes per warp).  Keys are
+// Out-degree <= 32: P = 2^c lanes per node, 32/P nodes per warp, R groups of
+// nodes per warp with all their loads issued before any sorting.  Keys are
 // sorted by a bitonic network across the P lanes, duplicates dropped by
 // comparing with the previous lane, survivors compacted with a ballot.
-template <int P, typename LabelT>
-__device__ void sig_small_body(const SigArgs& a, const uint32_t* nodes, uint64_t count,
-                               uint64_t warp_idx) {
+constexpr int kSmallR = 4;
+
+template <int P, typename LabelT, typename K>
+__device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first, uint64_t count,
+                                               uint64_t warp_idx) {
+  constexpr int NPW = 32 / P;
+  constexpr K kE = KeyOps<K>::kEmpty;
   const int lane = threadIdx.x & 31;
   const int g = lane / P, j = lane % P;
-  const uint64_t idx = warp_idx * (32 / P) + g;
-  const bool active = idx < count;
-  uint32_t u = 0;
-  uint64_t off = 0;
-  uint32_t d = 0;
-  if (active) {
-    u = nodes[idx];
-    off = a.off[u];
-    d = (uint32_t)(a.off[u + 1] - off);
+  uint64_t off[kSmallR];
+  uint32_t d[kSmallR];
+  K key[kSmallR];
+#pragma unroll
+  for (int r = 0; r < kSmallR; ++r) {
+    const uint64_t idx = (warp_idx * kSmallR + r) * NPW + g;
+    off[r] = 0;
+    d[r] = 0;
+    if (idx < count) {
+      off[r] = a.off[first + idx];
+      d[r] = (uint32_t)(a.off[first + idx + 1] - off[r]);
+    }
   }
-  uint64_t key = kEmpty64;
-  if (j < (int)d) key = edge_key<LabelT>(a, off + j);
+#pragma unroll
+  for (int r = 0; r < kSmallR; ++r) key[r] = j < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + j) : kE;
 #pragma unroll
   for (int k = 2; k <= P; k <<= 1) {
 #pragma unroll
     for (int s = k >> 1; s > 0; s >>= 1) {
-      uint64_t other = __shfl_xor_sync(kFull, key, s);
-      bool up = (j & k) == 0;
-      bool lower = (j & s) == 0;
-      key = (lower == up) ? min(key, other) : max(key, other);
+      const bool up = (j & k) == 0;
+      const bool lower = (j & s) == 0;
+#pragma unroll
+      for (int r = 0; r < kSmallR; ++r) {
+        const K other = __shfl_xor_sync(kFull, key[r], s);
+        key[r] = (lower == up) ? min(key[r], other) : max(key[r], other);
+      }
     }
   }
-  uint64_t prevk = __shfl_up_sync(kFull, key, 1);
-  const bool uniq = (j < (int)d) && (j == 0 || key != prevk);
-  const unsigned bal = __ballot_sync(kFull, uniq);
-  const unsigned gmask = (P == 32) ? bal : ((bal >> (g * P)) & ((1u << (P & 31)) - 1u));
-  const int pos = __popc(gmask & ((1u << j) - 1u));
-  if (uniq) a.sigkey[off + pos] = key;
-  uint64_t t = uniq ? elem_term(key, a.seed) : 0ull;
+  K* out = static_cast<K*>(a.sigkey);
 #pragma unroll
-  for (int s = P >> 1; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
-  if (active && j == 0) {
-    const uint32_t U = (uint32_t)__popc(gmask);
-    a.ucnt[u] = U;
-    a.hash[u] = node_hash(t, a.prev[u], U, a.seed, a.mask);
+  for (int r = 0; r < kSmallR; ++r) {
+    const K prevk = __shfl_up_sync(kFull, key[r], 1);
+    const bool uniq = (j < (int)d[r]) && (j == 0 || key[r] != prevk);
+    const unsigned bal = __ballot_sync(kFull, uniq);
+    const unsigned gmask = (P == 32) ? bal : ((bal >> (g * P)) & ((1u << (P & 31)) - 1u));
+    const int pos = __popc(gmask & ((1u << j) - 1u));
+    if (uniq) out[off[r] + pos] = key[r];
+    uint64_t t = uniq ? elem_term(key[r], a.seed) : 0ull;
+#pragma unroll
+    for (int s = P >> 1; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
+    const uint64_t idx = (warp_idx * kSmallR + r) * NPW + g;
+    if (j == 0 && idx < count) {
+      const uint64_t p = first + idx;
+      const uint32_t U = (uint32_t)__popc(gmask);
+      a.ucnt[p] = U;
+      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
+    }
   }
 }
 
 struct SmallLaunch {
-  uint64_t start[kSmallClasses];   // first index of class c in the node list
+  uint64_t start[kSmallClasses];
   uint64_t count[kSmallClasses];
-  uint32_t bstart[kSmallClasses + 1];  // first block of class c
+  uint32_t bstart[kSmallClasses + 1];
 };
 
 constexpr int kSmallWarps = 8;
 
-template <typename LabelT>
-__global__ void __launch_bounds__(256) k_sig_small(SigArgs a, const uint32_t* nodes, SmallLaunch L) {
+template <typename LabelT, typename K>
+__global__ void __launch_bounds__(kSmallWarps * 32) k_sig_small(SigArgs a, SmallLaunch L) {
   int c = 0;
   while (c + 1 < kSmallClasses && blockIdx.x >= L.bstart[c + 1]) ++c;
   const uint64_t warp_idx = (uint64_t)(blockIdx.x - L.bstart[c]) * kSmallWarps + (threadIdx.x >> 5);
-  const uint32_t* list = nodes + L.start[c];
   switch (c) {
-    case 0: sig_small_body<1, LabelT>(a, list, L.count[0], warp_idx); break;
-    case 1: sig_small_body<2, LabelT>(a, list, L.count[1], warp_idx); break;
-    case 2: sig_small_body<4, LabelT>(a, list, L.count[2], warp_idx); break;
-    case 3: sig_small_body<8, LabelT>(a, list, L.count[3], warp_idx); break;
-    case 4: sig_small_body<16, LabelT>(a, list, L.count[4], warp_idx); break;
-    default: sig_small_body<32, LabelT>(a, list, L.count[5], warp_idx); break;
+    case 0: sig_small_body<1, LabelT, K>(a, L.start[0], L.count[0], warp_idx); break;
+    case 1: sig_small_body<2, LabelT, K>(a, L.start[1], L.count[1], warp_idx); break;
+    case 2: sig_small_body<4, LabelT, K>(a, L.start[2], L.count[2], warp_idx); break;
+    case 3: sig_small_body<8, LabelT, K>(a, L.start[3], L.count[3], warp_idx); break;
+    case 4: sig_small_body<16, LabelT, K>(a, L.start[4], L.count[4], warp_idx); break;
+    default: sig_small_body<32, LabelT, K>(a, L.start[5], L.count[5], warp_idx); break;
   }
 }
 
-// Out-degree 33..kWarpMax: one warp per node, shared-memory dedupe + sort.
-constexpr int kWarpHcap = 2 * kWarpMax;
-constexpr int kWarpUcap = kWarpMax;
+// Out-degree 33..kWarpMax: one warp per node; keys are loaded into registers
+// (8 per lane) before the shared-memory dedupe.
+constexpr int kWarpItems = kWarpMax / 32;
 constexpr int kWarpsPerBlock = 8;
-constexpr size_t kWarpWsBytes = team_ws_bytes(kWarpHcap, kWarpUcap, 32);
 
-template <typename LabelT>
+template <typename K>
+__host__ __device__ constexpr size_t warp_ws_bytes() { return team_ws_bytes<K>(2 * kWarpMax, kWarpMax, 32); }
+
+template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_sig_warp(SigArgs a, const uint32_t* nodes, uint64_t count) {
+    k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TeamWs ws = carve(smem + w * kWarpWsBytes, kWarpHcap, kWarpUcap, 32);
+  TeamWs<K> ws = carve<K>(smem + w * warp_ws_bytes<K>(), 2 * kWarpMax, kWarpMax, 32);
+  K* out = static_cast<K*>(a.sigkey);
   for (uint64_t idx = (uint64_t)blockIdx.x * kWarpsPerBlock + w; idx < count;
        idx += (uint64_t)gridDim.x * kWarpsPerBlock) {
-    const uint32_t u = nodes[idx];
-    const uint64_t off = a.off[u];
-    const uint64_t d = a.off[u + 1] - off;
-    auto get = [&](uint64_t i) { return edge_key<LabelT>(a, off + i); };
-    const uint32_t U = team_dedupe_sort<32>(ws, set_size_for(d, kWarpHcap), d, get, lane);
+    const uint64_t p = first + idx;
+    const uint64_t off = a.off[p];
+    const uint32_t d = (uint32_t)(a.off[p + 1] - off);
+    K keys[kWarpItems];
+#pragma unroll
+    for (int t = 0; t < kWarpItems; ++t) {
+      const uint32_t i = lane + 32 * t;
+      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
+    }
+    const int hcap = set_size_for(d, 2 * kWarpMax);
+    team_begin<32>(ws, hcap, lane);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kWarpItems; ++t)
+      if (lane + 32 * t < d) team_insert(ws, hcap, keys[t]);
+    __syncwarp();
+    const uint32_t U = team_sort<32>(ws, lane);
     if (U == 0xFFFFFFFFu) {  // cannot happen: at most d <= ucap distinct keys
       if (lane == 0) atomicOr(a.err, kErrHubOverflow);
+      __syncwarp();
       continue;
     }
-    for (uint32_t i = lane; i < U; i += 32) a.sigkey[off + i] = ws.set[i];
+    for (uint32_t i = lane; i < U; i += 32) out[off + i] = ws.set[i];
     const uint64_t t = team_term_sum<32>(ws.set, U, a.seed, nullptr, lane);
     if (lane == 0) {
-      a.ucnt[u] = U;
-      a.hash[u] = node_hash(t, a.prev[u], U, a.seed, a.mask);
+      a.ucnt[p] = U;
+      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
     }
     __syncwarp();
   }
 }
 
-// Out-degree kWarpMax+1..kBlockMax (one CTA per node) and hub buckets.
-constexpr int kBlkHcap = 2 * kBlockMax;
-constexpr int kBlkUcap = kBlockMax;
-constexpr size_t kBlkWsBytes = team_ws_bytes(kBlkHcap, kBlkUcap, kBlockThreads);
+// Out-degree kWarpMax+1..kBlockMax: one CTA per node (8 keys per thread in
+// registers), and the hub buckets.
+constexpr int kBlkItems = kBlockMax / kBlockThreads;
 
-template <typename LabelT>
-__global__ void __launch_bounds__(kBlockThreads)
-    k_sig_block(SigArgs a, const uint32_t* nodes, uint64_t count) {
+template <typename K>
+__host__ __device__ constexpr size_t blk_ws_bytes() { return team_ws_bytes<K>(2 * kBlockMax, kBlockMax, kBlockThreads); }
+
+template <typename LabelT, typename K>
+__global__ void __launch_bounds__(kBlockThreads) k_sig_block(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads);
-  uint64_t* red = ws.red;
+  TeamWs<K> ws = carve<K>(smem, 2 * kBlockMax, kBlockMax, kBlockThreads);
+  K* out = static_cast<K*>(a.sigkey);
   for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
-    const uint32_t u = nodes[idx];
-    const uint64_t off = a.off[u];
-    const uint64_t d = a.off[u + 1] - off;
-    auto get = [&](uint64_t i) { return edge_key<LabelT>(a, off + i); };
-    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, set_size_for(d, kBlkHcap), d, get, threadIdx.x);
+    const uint64_t p = first + idx;
+    const uint64_t off = a.off[p];
+    const uint32_t d = (uint32_t)(a.off[p + 1] - off);
+    K keys[kBlkItems];
+#pragma unroll
+    for (int t = 0; t < kBlkItems; ++t) {
+      const uint32_t i = threadIdx.x + kBlockThreads * t;
+      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
+    }
+    const int hcap = set_size_for(d, 2 * kBlockMax);
+    team_begin<kBlockThreads>(ws, hcap, threadIdx.x);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kBlkItems; ++t)
+      if (threadIdx.x + kBlockThreads * t < d) team_insert(ws, hcap, keys[t]);
+    __syncthreads();
+    const uint32_t U = team_sort<kBlockThreads>(ws, threadIdx.x);
     if (U == 0xFFFFFFFFu) {
       if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
       __syncthreads();
       continue;
     }
-    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) a.sigkey[off + i] = ws.set[i];
-    const uint64_t t = team_term_sum<kBlockThreads>(ws.set, U, a.seed, red, threadIdx.x);
+    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) out[off + i] = ws.set[i];
+    const uint64_t t = team_term_sum<kBlockThreads, K>(ws.set, U, a.seed, ws.red, threadIdx.x);
     if (threadIdx.x == 0) {
-      a.ucnt[u] = U;
-      a.hash[u] = node_hash(t, a.prev[u], U, a.seed, a.mask);
+      a.ucnt[p] = U;
+      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
     }
     __syncthreads();
   }
@@ -480,27 +545,28 @@ __global__ void __launch_bounds__(kBlockThreads)
 // about kHubBucketTarget distinct keys, dedupe + sort each bucket in shared
 // memory, then concatenate the buckets in order (the top bits order them).
 struct HubArgs {
-  const uint32_t* hub_nodes;
+  uint64_t first;           // internal id of hub 0
   const uint32_t* hub_bits;
   const uint64_t* hub_bbase;
   const uint4* chunks;
   uint32_t extra_bits;
   uint64_t* hist;     // per bucket: count, then (after the scan) start
-  uint64_t* cursor;   // per bucket: fill cursor
+  uint64_t* cursor;   // per bucket: fill cursor, then end
   uint32_t* bucnt;    // per bucket: distinct keys
   uint64_t* bhpart;   // per bucket: term sum
-  uint64_t* tmp;
-  uint64_t* tmp2;
+  void* tmp;
+  void* tmp2;
 };
 
 constexpr int kHubItems = kHubChunk / kBlockThreads;  // 16
 constexpr int kHubSmemBuckets = 4096;
 
-__device__ __forceinline__ uint32_t hub_bucket(uint64_t k, uint32_t bits) {
-  return bits ? (uint32_t)(k >> (64 - bits)) : 0u;
+template <typename K>
+__device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
+  return bits ? (uint32_t)(k >> (KeyOps<K>::kBits - bits)) : 0u;
 }
 
-template <typename LabelT>
+template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h) {
   __shared__ uint32_t hist[kHubSmemBuckets];
   const uint4 c = h.chunks[blockIdx.x];
@@ -514,9 +580,19 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h
   if (in_smem)
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-    const uint32_t b = hub_bucket(edge_key<LabelT>(a, begin + i), bits);
-    if (in_smem) atomicAdd(&hist[b], 1u); else atomicAdd((unsigned long long*)&g[b], 1ull);
+  K keys[kHubItems];
+#pragma unroll
+  for (int t = 0; t < kHubItems; ++t) {
+    const uint32_t i = threadIdx.x + t * kBlockThreads;
+    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i) : (K)0;
+  }
+#pragma unroll
+  for (int t = 0; t < kHubItems; ++t) {
+    const uint32_t i = threadIdx.x + t * kBlockThreads;
+    if (i < len) {
+      const uint32_t b = hub_bucket(keys[t], bits);
+      if (in_smem) atomicAdd(&hist[b], 1u); else atomicAdd((unsigned long long*)&g[b], 1ull);
+    }
   }
   __syncthreads();
   if (in_smem)
@@ -524,7 +600,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h
       if (hist[b]) atomicAdd((unsigned long long*)&g[b], (unsigned long long)hist[b]);
 }
 
-template <typename LabelT>
+template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArgs h) {
   __shared__ uint32_t cnt[kHubSmemBuckets];
   __shared__ unsigned long long base[kHubSmemBuckets];
@@ -536,11 +612,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
   const uint32_t nb = 1u << bits;
   const bool in_smem = nb <= kHubSmemBuckets;
   uint64_t* cur = h.cursor + h.hub_bbase[hub];
-  uint64_t keys[kHubItems];
+  K* tmp = static_cast<K*>(h.tmp);
+  K keys[kHubItems];
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
     const uint32_t i = threadIdx.x + t * kBlockThreads;
-    keys[t] = i < len ? edge_key<LabelT>(a, begin + i) : 0ull;
+    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i) : (K)0;
   }
   if (!in_smem) {
 #pragma unroll
@@ -549,7 +626,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
       if (i < len) {
         const uint32_t b = hub_bucket(keys[t], bits);
         const uint64_t p = atomicAdd((unsigned long long*)&cur[b], 1ull);
-        h.tmp[p] = keys[t];
+        tmp[p] = keys[t];
       }
     }
     return;
@@ -573,24 +650,38 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
     if (i < len) {
       const uint32_t b = hub_bucket(keys[t], bits);
       const uint32_t p = atomicAdd(&cnt[b], 1u);
-      h.tmp[base[b] + p] = keys[t];
+      tmp[base[b] + p] = keys[t];
     }
   }
 }
 
 // One CTA per hub bucket: distinct keys of the bucket, sorted, into tmp2.
+template <typename K>
 __global__ void __launch_bounds__(kBlockThreads)
     k_hub_bucket(HubArgs h, uint64_t n_buckets, uint64_t seed, uint32_t* err) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs ws = carve(smem, kBlkHcap, kBlkUcap, kBlockThreads);
-  uint64_t* red = ws.red;
+  TeamWs<K> ws = carve<K>(smem, 2 * kBlockMax, kBlockMax, kBlockThreads);
+  const K* tmp = static_cast<const K*>(h.tmp);
+  K* tmp2 = static_cast<K*>(h.tmp2);
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
     const uint64_t lo = h.hist[b];
-    const uint64_t hi = h.cursor[b];  // after the scatter, cursor = end of bucket
-    const uint64_t* src = h.tmp + lo;
-    auto get = [&](uint64_t i) { return src[i]; };
-    const uint32_t U = team_dedupe_sort<kBlockThreads>(ws, set_size_for(hi - lo, kBlkHcap), hi - lo, get,
-                                                       threadIdx.x);
+    const uint64_t n = h.cursor[b] - lo;  // after the scatter, cursor = end of bucket
+    const int hcap = set_size_for(n, 2 * kBlockMax);
+    team_begin<kBlockThreads>(ws, hcap, threadIdx.x);
+    __syncthreads();
+    for (uint64_t base = 0; base < n; base += (uint64_t)kBlockThreads * 8) {
+      K keys[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const uint64_t i = base + threadIdx.x + (uint64_t)kBlockThreads * t;
+        keys[t] = i < n ? tmp[lo + i] : (K)0;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (base + threadIdx.x + (uint64_t)kBlockThreads * t < n) team_insert(ws, hcap, keys[t]);
+    }
+    __syncthreads();
+    const uint32_t U = team_sort<kBlockThreads>(ws, threadIdx.x);
     if (U == 0xFFFFFFFFu) {
       if (threadIdx.x == 0) {
         atomicOr(err, kErrHubOverflow);
@@ -600,8 +691,8 @@ __global__ void __launch_bounds__(kBlockThreads)
       __syncthreads();
       continue;
     }
-    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) h.tmp2[lo + i] = ws.set[i];
-    const uint64_t t = team_term_sum<kBlockThreads>(ws.set, U, seed, red, threadIdx.x);
+    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) tmp2[lo + i] = ws.set[i];
+    const uint64_t t = team_term_sum<kBlockThreads, K>(ws.set, U, seed, ws.red, threadIdx.x);
     if (threadIdx.x == 0) {
       h.bucnt[b] = U;
       h.bhpart[b] = t;
@@ -611,16 +702,19 @@ __global__ void __launch_bounds__(kBlockThreads)
 }
 
 // One CTA per hub: concatenate its buckets' sorted keys at the hub's CSR offset.
+template <typename K>
 __global__ void __launch_bounds__(kBlockThreads) k_hub_compact(SigArgs a, HubArgs h) {
   __shared__ uint32_t cnt[kBlockThreads];
   __shared__ uint32_t wtot[kBlockThreads / 32];
   __shared__ uint64_t red[kBlockThreads / 32];
   __shared__ unsigned long long running;
   const uint32_t hub = blockIdx.x;
-  const uint32_t u = h.hub_nodes[hub];
-  const uint64_t off = a.off[u];
+  const uint64_t p = h.first + hub;
+  const uint64_t off = a.off[p];
   const uint64_t b0 = h.hub_bbase[hub];
   const uint64_t nb = (uint64_t)1 << (h.hub_bits[hub] + h.extra_bits);
+  const K* tmp2 = static_cast<const K*>(h.tmp2);
+  K* out = static_cast<K*>(a.sigkey);
   if (threadIdx.x == 0) running = 0;
   uint64_t term = 0;
   __syncthreads();
@@ -632,14 +726,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_compact(SigArgs a, HubArg
     __syncthreads();
     team_excl_scan<kBlockThreads>(cnt, kBlockThreads, wtot, threadIdx.x);
     const uint64_t run0 = running;
-    // copy bucket by bucket; every thread helps with each bucket
     const int nchunk = (int)((nb - base) < (uint64_t)kBlockThreads ? (nb - base) : (uint64_t)kBlockThreads);
     for (int j = 0; j < nchunk; ++j) {
       const uint64_t bj = b0 + base + j;
       const uint32_t U = h.bucnt[bj];
       const uint64_t lo = h.hist[bj];
       const uint64_t dstp = off + run0 + cnt[j];
-      for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) a.sigkey[dstp + i] = h.tmp2[lo + i];
+      for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) out[dstp + i] = tmp2[lo + i];
     }
     __syncthreads();
     if (threadIdx.x == kBlockThreads - 1) running = run0 + cnt[kBlockThreads - 1] + myc;
@@ -653,22 +746,28 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_compact(SigArgs a, HubArg
     uint64_t tot = 0;
     for (int w = 0; w < kBlockThreads / 32; ++w) tot += red[w];
     const uint64_t U = running;
-    a.ucnt[u] = (uint32_t)U;
-    a.hash[u] = node_hash(tot, a.prev[u], U, a.seed, a.mask);
+    a.ucnt[p] = (uint32_t)U;
+    a.hash[p] = node_hash(tot, a.prev[p], U, a.seed, a.mask);
   }
 }
 
 // --------------------------------------------------------------------------
-// Grouping: equal hashes -> smallest node id; exact verification
+// Grouping: equal hashes -> smallest original id; exact verification
 // --------------------------------------------------------------------------
+struct __align__(16) Slot {
+  unsigned long long key;
+  unsigned int minid;  // smallest original node id with this key
+  unsigned int pad;
+};
+
 struct GroupArgs {
   const uint64_t* hash;
-  uint64_t* tkey;
-  uint32_t* tmin;
+  const uint32_t* p2o;
+  const uint32_t* o2p;
+  Slot* table;
   uint64_t tmask;   // table capacity - 1
   uint32_t* slot;
   uint32_t* rep;
-  const uint8_t* alive;  // may be null (all alive)
   uint32_t* err;
 };
 
@@ -676,146 +775,193 @@ __device__ __forceinline__ uint32_t table_home(uint64_t h, uint64_t tmask) {
   return (uint32_t)(mix64(h ^ 0x9e3779b97f4a7c15ull) & tmask);
 }
 
+// Lanes of a warp with the same hash combine their smallest original id and
+// let one leader probe the table; the slot is then broadcast.
 __global__ void k_group_insert(GroupArgs g, const uint32_t* list, uint64_t count) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t u = list ? list[i] : (uint32_t)i;
-    if (!list && g.alive && !g.alive[u]) continue;
-    const uint64_t h = g.hash[u];
-    uint32_t s = table_home(h, g.tmask);
-    volatile uint64_t* vk = g.tkey;
-    bool found = false;
-    for (uint64_t t = 0; t <= g.tmask; ++t) {
-      const uint64_t cur = vk[s];
-      if (cur == h) { found = true; break; }
-      if (cur == kEmpty64) {
-        const uint64_t old = atomicCAS((unsigned long long*)&g.tkey[s], (unsigned long long)kEmpty64,
-                                       (unsigned long long)h);
-        if (old == kEmpty64 || old == h) { found = true; break; }
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
+    const uint64_t i = base + lane;
+    const bool valid = i < count;
+    const uint32_t p = valid ? (list ? list[i] : (uint32_t)i) : 0u;
+    const uint64_t h = valid ? g.hash[p] : kEmpty64;
+    const uint32_t o = valid ? g.p2o[p] : kNone32;
+    const unsigned peers = __match_any_sync(kFull, h);
+    const int leader = __ffs(peers) - 1;
+    const uint32_t gmin = __reduce_min_sync(peers, o);
+    uint32_t s = 0;
+    if (valid && lane == leader) {
+      s = table_home(h, g.tmask);
+      bool found = false;
+      for (uint64_t t = 0; t <= g.tmask; ++t) {
+        const unsigned long long cur = *(volatile unsigned long long*)&g.table[s].key;
+        if (cur == h) { found = true; break; }
+        if (cur == kEmpty64) {
+          const unsigned long long old = atomicCAS(&g.table[s].key, (unsigned long long)kEmpty64,
+                                                   (unsigned long long)h);
+          if (old == kEmpty64 || old == h) { found = true; break; }
+        }
+        s = (uint32_t)((s + 1) & g.tmask);
       }
-      s = (uint32_t)((s + 1) & g.tmask);
+      if (found) atomicMin(&g.table[s].minid, gmin); else atomicOr(g.err, kErrProbe);
     }
-    if (!found) {
-      atomicOr(g.err, kErrProbe);
-      continue;
-    }
-    atomicMin(&g.tmin[s], u);
-    g.slot[u] = s;
+    s = __shfl_sync(kFull, s, leader);
+    if (valid) g.slot[p] = s;
   }
 }
 
 struct VerifyArgs {
   int mode;                 // 0: level 0 (labels), 1: signatures
+  int key64;                // signature words are 64-bit
   const uint32_t* nlabel;
   const uint32_t* prev;
   const uint32_t* ucnt;
   const uint64_t* off;
-  const uint64_t* sigkey;
+  const void* sigkey;
   uint32_t* out_list;       // unresolved nodes
   unsigned long long* n_out;
   unsigned long long* n_collided;
+  uint32_t* long_list;      // (node, candidate) pairs with long signatures
+  unsigned long long* n_long;
 };
 
-__device__ __forceinline__ bool same_signature(const VerifyArgs& v, uint32_t u, uint32_t r) {
-  if (v.mode == 0) return v.nlabel[u] == v.nlabel[r];
-  if (v.prev[u] != v.prev[r]) return false;
-  const uint32_t U = v.ucnt[u];
-  if (U != v.ucnt[r]) return false;
-  const uint64_t* ku = v.sigkey + v.off[u];
-  const uint64_t* kr = v.sigkey + v.off[r];
-  for (uint32_t t = 0; t < U; ++t)
-    if (ku[t] != kr[t]) return false;
+constexpr uint32_t kShortSig = 32;
+
+template <typename K>
+__device__ __forceinline__ bool same_keys(const K* a, const K* b, uint32_t n) {
+  for (uint32_t t = 0; t < n; ++t)
+    if (a[t] != b[t]) return false;
   return true;
+}
+
+__device__ __forceinline__ void mark_unresolved(const VerifyArgs& v, uint32_t* rep, uint32_t p) {
+  rep[p] = kNone32;
+  const unsigned long long q = atomicAdd(v.n_out, 1ull);
+  v.out_list[q] = p;
+  atomicAdd(v.n_collided, 1ull);
 }
 
 __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, uint64_t count) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t u = list ? list[i] : (uint32_t)i;
-    if (!list && g.alive && !g.alive[u]) continue;
-    const uint32_t r = g.tmin[g.slot[u]];
-    if (r == u) { g.rep[u] = u; continue; }
-    if (same_signature(v, u, r)) {
-      g.rep[u] = r;
+    const uint32_t p = list ? list[i] : (uint32_t)i;
+    const uint32_t ro = g.table[g.slot[p]].minid;
+    if (ro == g.p2o[p]) { g.rep[p] = p; continue; }
+    const uint32_t r = g.o2p[ro];
+    bool eq;
+    if (v.mode == 0) {
+      eq = v.nlabel[p] == v.nlabel[r];
     } else {
-      g.rep[u] = kNone32;
-      const unsigned long long p = atomicAdd(v.n_out, 1ull);
-      v.out_list[p] = u;
-      atomicAdd(v.n_collided, 1ull);
+      const uint32_t U = v.ucnt[p];
+      eq = v.prev[p] == v.prev[r] && U == v.ucnt[r];
+      if (eq && U > kShortSig) {  // long signature: compared by a warp later
+        const unsigned long long q = atomicAdd(v.n_long, 1ull);
+        v.long_list[2 * q] = p;
+        v.long_list[2 * q + 1] = r;
+        continue;
+      }
+      if (eq) {
+        eq = v.key64 ? same_keys(static_cast<const uint64_t*>(v.sigkey) + v.off[p],
+                                 static_cast<const uint64_t*>(v.sigkey) + v.off[r], U)
+                     : same_keys(static_cast<const uint32_t*>(v.sigkey) + v.off[p],
+                                 static_cast<const uint32_t*>(v.sigkey) + v.off[r], U);
+      }
+    }
+    if (eq) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
+  }
+}
+
+// One warp per (node, candidate) pair with a long signature.
+template <typename K>
+__global__ void k_verify_long(GroupArgs g, VerifyArgs v, uint64_t count) {
+  const int lane = threadIdx.x & 31;
+  const K* keys = static_cast<const K*>(v.sigkey);
+  for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; q < count;
+       q += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t p = v.long_list[2 * q], r = v.long_list[2 * q + 1];
+    const uint32_t U = v.ucnt[p];
+    const K* a = keys + v.off[p];
+    const K* b = keys + v.off[r];
+    bool diff = false;
+    for (uint32_t base = 0; base < U && !diff; base += 32) {
+      const uint32_t t = base + lane;
+      diff = __any_sync(kFull, t < U && a[t] != b[t]);
+    }
+    if (lane == 0) {
+      if (!diff) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// Canonical renumbering: heads are nodes with rep[u] == u (the smallest node
-// of their block); block id = number of heads before the node.
+// Canonical renumbering: heads are nodes with rep[p] == p (the node with the
+// smallest original id in its block); a block's id is the number of heads
+// with a smaller original id.
 // --------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 struct RankArgs {
-  uint64_t n;
+  uint64_t n, n_alive;
   const uint32_t* rep;
-  const uint8_t* alive;
+  const uint32_t* p2o;
   const uint32_t* ucnt;    // may be null (level 0)
-  uint32_t* pid;           // output level
+  uint8_t* hflag;          // [n] original order
+  uint32_t* rank_o;        // [n] original order
+  uint32_t* pid;           // output level, internal order
   uint64_t* bsum;          // per tile head count -> exclusive offsets
   unsigned long long* stats;  // [0] heads total, [2] key total, [3] max signature
 };
 
-__device__ __forceinline__ bool is_head(const RankArgs& r, uint64_t u) {
-  return u < r.n && (!r.alive || r.alive[u]) && r.rep[u] == (uint32_t)u;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_rank_tilesum(RankArgs r) {
-  __shared__ unsigned long long red[kScanThreads / 32];
-  __shared__ unsigned long long redk[kScanThreads / 32];
-  __shared__ unsigned int redm[kScanThreads / 32];
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-  unsigned long long c = 0, keys = 0;
+__global__ void k_mark_heads(RankArgs r) {
+  unsigned long long keys = 0;
   unsigned int mx = 0;
-#pragma unroll
-  for (int t = 0; t < kScanItems; ++t) {
-    const uint64_t u = base + (uint64_t)t * kScanThreads + threadIdx.x;
-    c += is_head(r, u) ? 1 : 0;
-    if (r.ucnt && u < r.n && (!r.alive || r.alive[u])) {
-      const uint32_t q = r.ucnt[u];
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n_alive;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    if (r.rep[p] == (uint32_t)p) r.hflag[r.p2o[p]] = 1;
+    if (r.ucnt) {
+      const uint32_t q = r.ucnt[p];
       keys += q;
       mx = max(mx, q);
     }
   }
+  if (r.ucnt) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    c += __shfl_xor_sync(kFull, c, o);
-    keys += __shfl_xor_sync(kFull, keys, o);
-    mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = c;
-    redk[threadIdx.x >> 5] = keys;
-    redm[threadIdx.x >> 5] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long tot = 0, kt = 0;
-    unsigned int m = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) {
-      tot += red[w];
-      kt += redk[w];
-      m = max(m, redm[w]);
+    for (int o = 16; o > 0; o >>= 1) {
+      keys += __shfl_xor_sync(kFull, keys, o);
+      mx = max(mx, __shfl_xor_sync(kFull, mx, o));
     }
-    r.bsum[blockIdx.x] = tot;
-    if (r.ucnt) {
-      atomicAdd(&r.stats[2], kt);
-      atomicMax(&r.stats[3], (unsigned long long)m);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&r.stats[2], keys);
+      atomicMax(&r.stats[3], (unsigned long long)mx);
     }
   }
 }
 
-// Exclusive scan of bsum[0..nb) in one CTA; total into stats[0].
+__global__ void __launch_bounds__(kScanThreads) k_flag_tilesum(const uint8_t* f, uint64_t n, uint64_t* bsum) {
+  __shared__ unsigned long long red[kScanThreads / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  unsigned long long c = 0;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    const uint64_t i = base + (uint64_t)t * kScanThreads + threadIdx.x;
+    if (i < n) c += f[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) tot += red[w];
+    bsum[blockIdx.x] = tot;
+  }
+}
+
+// Exclusive scan of bsum[0..nb) in one CTA; total into *total.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint64_t* bsum, uint64_t nb,
-                                                              unsigned long long* stats) {
+                                                              unsigned long long* total) {
   __shared__ unsigned long long wt[kScanThreads / 32];
   __shared__ unsigned long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -849,20 +995,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint64_t* bsum, uin
     if (threadIdx.x == kScanThreads - 1) carry = c0 + wt[w] + x;
     __syncthreads();
   }
-  if (threadIdx.x == 0) stats[0] = carry;
+  if (threadIdx.x == 0) *total = carry;
 }
 
-// Heads get their rank (tile offset + rank inside the tile).
-__global__ void __launch_bounds__(kScanThreads) k_rank_heads(RankArgs r) {
+// Heads (flagged original ids) get their rank: tile offset + rank in tile.
+__global__ void __launch_bounds__(kScanThreads) k_flag_rank(const uint8_t* f, uint64_t n, const uint64_t* bsum,
+                                                             uint32_t* rank_o) {
   __shared__ unsigned int wt[kScanThreads / 32];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
-  unsigned int f[kScanItems];
+  unsigned int fl[kScanItems];
   unsigned int c = 0;
+  if (base + kScanItems <= n) {
+    const uchar4 v = *reinterpret_cast<const uchar4*>(f + base);
+    fl[0] = v.x; fl[1] = v.y; fl[2] = v.z; fl[3] = v.w;
+  } else {
 #pragma unroll
-  for (int t = 0; t < kScanItems; ++t) {
-    f[t] = is_head(r, base + t) ? 1u : 0u;
-    c += f[t];
+    for (int t = 0; t < kScanItems; ++t) fl[t] = base + t < n ? f[base + t] : 0u;
   }
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) c += fl[t];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned int x = c;
 #pragma unroll
@@ -883,38 +1034,37 @@ __global__ void __launch_bounds__(kScanThreads) k_rank_heads(RankArgs r) {
     wt[lane] = xx - t;
   }
   __syncthreads();
-  uint64_t rank = r.bsum[blockIdx.x] + wt[w] + (x - c);
+  uint64_t rank = bsum[blockIdx.x] + wt[w] + (x - c);
 #pragma unroll
   for (int t = 0; t < kScanItems; ++t) {
-    if (f[t]) r.pid[base + t] = (uint32_t)rank;
-    rank += f[t];
+    if (fl[t]) rank_o[base + t] = (uint32_t)rank;
+    rank += fl[t];
   }
 }
 
-// Members copy their head's block id; deleted nodes get kDead.
-__global__ void k_rank_fill(RankArgs r) {
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < r.n;
-       u += (uint64_t)gridDim.x * blockDim.x) {
-    if (r.alive && !r.alive[u]) { r.pid[u] = kDead; continue; }
-    const uint32_t h = r.rep[u];
-    if (h != (uint32_t)u) r.pid[u] = r.pid[h];
-  }
+// Every alive node takes its head's block id; deleted nodes get kDead.
+__global__ void k_pid_fill(RankArgs r) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n;
+       p += (uint64_t)gridDim.x * blockDim.x)
+    r.pid[p] = p < r.n_alive ? r.rank_o[r.p2o[r.rep[p]]] : kDead;
 }
 
 // Level 0 hash: the node label.
-__global__ void k_label_hash(uint64_t n, const uint32_t* nlabel, uint64_t* hash, uint64_t seed,
-                             uint64_t mask) {
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n;
-       u += (uint64_t)gridDim.x * blockDim.x)
-    hash[u] = node_hash(0, nlabel[u], 0, seed, mask);
+__global__ void k_label_hash(uint64_t n, const uint32_t* nlabel, uint64_t* hash, uint64_t seed, uint64_t mask) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x)
+    hash[p] = node_hash(0, nlabel[p], 0, seed, mask);
+}
+
+__global__ void k_unpermute(uint64_t n, const uint32_t* o2p, const uint32_t* lvl, uint32_t* out) {
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n;
+       o += (uint64_t)gridDim.x * blockDim.x)
+    out[o] = lvl[o2p[o]];
 }
 
 // --------------------------------------------------------------------------
-// Degree classes (once per graph)
+// Relabelling (once per graph)
 // --------------------------------------------------------------------------
-constexpr int kClassWarp = kSmallClasses, kClassBlock = kSmallClasses + 1,
-              kClassHub = kSmallClasses + 2, kNumClasses = kSmallClasses + 3;
-
 __device__ __forceinline__ int degree_class(uint64_t d) {
   if (d <= (uint64_t)kSmallMax) {
     int c = 0;
@@ -926,10 +1076,13 @@ __device__ __forceinline__ int degree_class(uint64_t d) {
   return kClassHub;
 }
 
-// Stable partition of the alive nodes by degree class, in tiles of 1024 nodes:
-// per-tile class counts, an exclusive scan over (class, tile) on the host,
-// then each tile writes its nodes in id order.
 constexpr int kClassTile = 1024;
+
+__device__ __forceinline__ int node_class(uint64_t o, uint64_t n, const uint64_t* off, const uint8_t* alive) {
+  if (o >= n) return -1;
+  if (alive && !alive[o]) return kClassDead;
+  return degree_class(off[o + 1] - off[o]);
+}
 
 __global__ void __launch_bounds__(kClassTile)
     k_class_tile_count(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
@@ -937,18 +1090,20 @@ __global__ void __launch_bounds__(kClassTile)
   __shared__ unsigned int c[kNumClasses];
   if (threadIdx.x < kNumClasses) c[threadIdx.x] = 0;
   __syncthreads();
-  const uint64_t u = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
-  if (u < n && (!alive || alive[u])) atomicAdd(&c[degree_class(off[u + 1] - off[u])], 1u);
+  const int cls = node_class((uint64_t)blockIdx.x * kClassTile + threadIdx.x, n, off, alive);
+  if (cls >= 0) atomicAdd(&c[cls], 1u);
   __syncthreads();
   if (threadIdx.x < kNumClasses) tcnt[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = c[threadIdx.x];
 }
 
+// Stable scatter: each tile writes its nodes of class c in id order at the
+// (class, tile) base.
 __global__ void __launch_bounds__(kClassTile)
     k_class_tile_scatter(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
-                         const unsigned long long* tbase, uint32_t* out) {
+                         const unsigned long long* tbase, uint32_t* p2o) {
   __shared__ unsigned int wcount[kClassTile / 32];
-  const uint64_t u = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
-  const int cls = (u < n && (!alive || alive[u])) ? degree_class(off[u + 1] - off[u]) : -1;
+  const uint64_t o = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
+  const int cls = node_class(o, n, off, alive);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = 0; c < kNumClasses; ++c) {
     const unsigned m = __ballot_sync(kFull, cls == c);
@@ -957,307 +1112,48 @@ __global__ void __launch_bounds__(kClassTile)
     unsigned before = 0;
     for (int i = 0; i < w; ++i) before += wcount[i];
     if (cls == c)
-      out[tbase[(uint64_t)c * ntiles + blockIdx.x] + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)u;
+      p2o[tbase[(uint64_t)c * ntiles + blockIdx.x] + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)o;
     __syncthreads();
   }
 }
 
-// --------------------------------------------------------------------------
-// Host helpers
-// --------------------------------------------------------------------------
-Status launch_check(const char* what) { return cuda_check(cudaGetLastError(), what); }
-
-int sm_count(int device) {
-  static int cached[64] = {0};
-  if (device < 0 || device >= 64) return 148;
-  if (!cached[device]) {
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
-    cached[device] = v > 0 ? v : 148;
-  }
-  return cached[device];
+__global__ void k_invert(uint64_t n, const uint32_t* p2o, uint32_t* o2p) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x)
+    o2p[p2o[p]] = (uint32_t)p;
 }
 
-Status set_smem_attrs() {
-  static bool done = false;
-  if (done) return Status::Ok();
-  cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(k_sig_warp<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kWarpWsBytes * kWarpsPerBlock));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kWarpWsBytes * kWarpsPerBlock));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_block<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kBlkWsBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_block<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kBlkWsBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kBlkWsBytes);
-  if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute");
-  done = true;
-  return Status::Ok();
+// deg of internal node p into off[p] (then an exclusive scan makes offsets);
+// node labels follow their node.
+__global__ void k_relabel_nodes(uint64_t n, const uint32_t* p2o, const uint64_t* off0, const uint32_t* nlab0,
+                                unsigned long long* deg, uint32_t* nlab) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = p2o[p];
+    deg[p] = off0[o + 1] - off0[o];
+    nlab[p] = nlab0[o];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
 }
 
-Status read_scalars(Store& s, uint64_t* out, int count) {
-  Status st = cuda_check(cudaMemcpyAsync(s.h_scalars.p, s.d_scalars.p, 8 * sizeof(uint64_t),
-                                         cudaMemcpyDeviceToHost, s.stream), "read scalars");
-  if (!st.ok()) return st;
-  st = cuda_check(cudaStreamSynchronize(s.stream), "stream sync");
-  if (!st.ok()) return st;
-  std::memcpy(out, s.h_scalars.p, count * sizeof(uint64_t));
-  return Status::Ok();
-}
-
-Status read_err(Store& s, uint32_t* err) {
-  uint32_t v = 0;
-  Status st = cuda_check(cudaMemcpyAsync(&v, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
-  if (!st.ok()) return st;
-  st = cuda_check(cudaStreamSynchronize(s.stream), "stream sync");
-  *err = v;
-  return st;
-}
-
-uint64_t table_capacity(uint64_t n) {
-  uint64_t c = 1024;
-  while (c < 2 * n) c <<= 1;
-  return c;
-}
-
-// Group the nodes of `hash` (all alive nodes), verify exactly, repair
-// collisions, then renumber canonically into `pid`.  Returns the block count.
-Status group_and_rank(Store& s, int mode, const uint32_t* prev, uint32_t* pid, uint64_t* blocks,
-                      uint64_t* collided, bool with_stats, uint64_t* keys, uint64_t* maxsig) {
-  const uint64_t n = s.n;
-  Status st;
-  uint32_t* err = ptr<uint32_t>(s.d_err);
-  unsigned long long* sc = ptr<unsigned long long>(s.d_scalars);
-  GroupArgs g;
-  g.hash = ptr<uint64_t>(s.hash);
-  g.tkey = ptr<uint64_t>(s.tkey);
-  g.tmin = ptr<uint32_t>(s.tmin);
-  g.tmask = s.tcap - 1;
-  g.slot = ptr<uint32_t>(s.slot);
-  g.rep = ptr<uint32_t>(s.rep);
-  g.alive = s.any_dead ? ptr<uint8_t>(s.alive) : nullptr;
-  g.err = err;
-  VerifyArgs v;
-  v.mode = mode;
-  v.nlabel = ptr<uint32_t>(s.nlabel);
-  v.prev = prev;
-  v.ucnt = ptr<uint32_t>(s.ucnt);
-  v.off = ptr<uint64_t>(s.offsets);
-  v.sigkey = ptr<uint64_t>(s.sigkey);
-  v.n_collided = sc + 4;
-  const int sms = sm_count(s.device);
-  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 16);
-  {
-    TimedScope ts(s, KBISIM_KERNEL_OTHER);
-    cudaMemsetAsync(s.tkey.p, 0xFF, s.tcap * 8, s.stream);
-    cudaMemsetAsync(s.tmin.p, 0xFF, s.tcap * 4, s.stream);
-    cudaMemsetAsync(s.d_scalars.p, 0, 8 * 8, s.stream);
-  }
-  {
-    TimedScope ts(s, KBISIM_KERNEL_GROUP);
-    k_group_insert<<<gblocks, 256, 0, s.stream>>>(g, nullptr, n);
-  }
-  if (!(st = launch_check("k_group_insert")).ok()) return st;
-  v.out_list = ptr<uint32_t>(s.ulist[0]);
-  v.n_out = sc + 1;
-  {
-    TimedScope ts(s, KBISIM_KERNEL_VERIFY);
-    k_group_verify<<<gblocks, 256, 0, s.stream>>>(g, v, nullptr, n);
-  }
-  if (!(st = launch_check("k_group_verify")).ok()) return st;
-  uint64_t h[8];
-  if (!(st = read_scalars(s, h, 8)).ok()) return st;
-  uint64_t unresolved = h[1];
-  // Collision repair: the unresolved nodes hold whole classes; the smallest
-  // unresolved node of each hash group heads its class, so every pass
-  // settles at least one class per group.
-  int cur = 0;
-  uint64_t passes = 0;
-  while (unresolved > 0) {
-    if (++passes > n + 1) return Status::Err(KBISIM_ERR_TIMEOUT, "collision repair did not converge");
-    const uint64_t cap = table_capacity(unresolved);
-    GroupArgs g2 = g;
-    g2.tmask = cap - 1;
-    VerifyArgs v2 = v;
-    v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
-    v2.n_out = sc + 5;
-    const unsigned b2 = grid_for(unresolved, 256);
-    {
-      TimedScope ts(s, KBISIM_KERNEL_OTHER);
-      cudaMemsetAsync(s.tkey.p, 0xFF, cap * 8, s.stream);
-      cudaMemsetAsync(s.tmin.p, 0xFF, cap * 4, s.stream);
-      cudaMemsetAsync(sc + 5, 0, 8, s.stream);
-      k_group_insert<<<b2, 256, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved);
-      k_group_verify<<<b2, 256, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved);
-    }
-    if (!(st = launch_check("collision repair")).ok()) return st;
-    if (!(st = read_scalars(s, h, 8)).ok()) return st;
-    if (h[5] >= unresolved)  // every pass settles the smallest node of each group
-      return Status::Err(KBISIM_ERR_TIMEOUT, "collision repair made no progress");
-    unresolved = h[5];
-    cur ^= 1;
-  }
-  *collided = h[4];
-  // canonical renumbering
-  RankArgs r;
-  r.n = n;
-  r.rep = ptr<uint32_t>(s.rep);
-  r.alive = g.alive;
-  r.ucnt = with_stats ? ptr<uint32_t>(s.ucnt) : nullptr;
-  r.pid = pid;
-  r.bsum = ptr<uint64_t>(s.bsum);
-  r.stats = sc;
-  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
-  {
-    TimedScope ts(s, KBISIM_KERNEL_RENUMBER);
-    if (tiles) {
-      k_rank_tilesum<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r);
-      k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(r.bsum, tiles, sc);
-      k_rank_heads<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r);
-      k_rank_fill<<<gblocks, 256, 0, s.stream>>>(r);
+// One warp per internal node: copy its out-edges, relabelling targets.
+template <typename TI, typename TO>
+__global__ void k_relabel_edges(uint64_t n, const uint32_t* p2o, const uint32_t* o2p, const uint64_t* off0,
+                                const uint32_t* dst0, const TI* lab0, const uint64_t* off, uint32_t* dst,
+                                TO* lab) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; p < n;
+       p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t o = p2o[p];
+    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[p];
+    for (uint64_t i = lane; i < d; i += 32) {
+      dst[s1 + i] = o2p[dst0[s0 + i]];
+      lab[s1 + i] = (TO)lab0[s0 + i];
     }
   }
-  if (!(st = launch_check("renumber")).ok()) return st;
-  if (!(st = read_scalars(s, h, 8)).ok()) return st;
-  *blocks = h[0];
-  if (keys) *keys = h[2];
-  if (maxsig) *maxsig = h[3];
-  uint32_t e = 0;
-  if (!(st = read_err(s, &e)).ok()) return st;
-  if (e & kErrProbe) return Status::Err(KBISIM_ERR_TIMEOUT, "hash table probe bound exceeded");
-  if (e & kErrChecked) return Status::Err(KBISIM_ERR_CHECKED, "device bounds check failed");
-  return Status::Ok();
 }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// Degree classes and hub layout (once per graph, after load)
-// ---------------------------------------------------------------------------
-Status prepare_classes(Store& s) {
-  Status st = set_smem_attrs();
-  if (!st.ok()) return st;
-  const uint64_t n = s.n;
-  const uint8_t* alive = s.any_dead ? ptr<uint8_t>(s.alive) : nullptr;
-  const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
-  Buf tcnt;
-  if (!(st = ensure(s, tcnt, ntiles * kNumClasses * 8)).ok()) return st;
-  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumClasses * 8, s.stream);
-  if (n)
-    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), alive, ntiles,
-                                                                      ptr<unsigned long long>(tcnt));
-  if (!(st = launch_check("k_class_tile_count")).ok()) { release(s, tcnt); return st; }
-  std::vector<uint64_t> h(ntiles * kNumClasses);
-  st = cuda_check(cudaMemcpyAsync(h.data(), tcnt.p, h.size() * 8, cudaMemcpyDeviceToHost, s.stream), "class counts");
-  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  if (!st.ok()) { release(s, tcnt); return st; }
-  uint64_t run = 0;
-  uint64_t cstart[kNumClasses + 1];
-  for (int c = 0; c < kNumClasses; ++c) {
-    cstart[c] = run;
-    for (uint64_t t = 0; t < ntiles; ++t) {
-      const uint64_t v = h[(uint64_t)c * ntiles + t];
-      h[(uint64_t)c * ntiles + t] = run;
-      run += v;
-    }
-  }
-  cstart[kNumClasses] = run;
-  st = cuda_check(cudaMemcpyAsync(tcnt.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s.stream), "class bases");
-  if (st.ok()) st = ensure(s, s.class_nodes, std::max<uint64_t>(1, run) * 4);
-  if (!st.ok()) { release(s, tcnt); return st; }
-  if (n)
-    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(
-        n, ptr<uint64_t>(s.offsets), alive, ntiles, ptr<unsigned long long>(tcnt), ptr<uint32_t>(s.class_nodes));
-  st = launch_check("k_class_tile_scatter");
-  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  release(s, tcnt);
-  if (!st.ok()) return st;
-  for (int c = 0; c <= kNumClasses; ++c) s.class_start[c] = cstart[c];
-  for (int k = 0; k < kSmallClasses; ++k) {
-    s.small_start[k] = cstart[k];
-    s.small_count[k] = cstart[k + 1] - cstart[k];
-  }
-  s.small_start[kSmallClasses] = cstart[kSmallClasses];
-  s.n_warp = cstart[kClassWarp + 1] - cstart[kClassWarp];
-  s.n_block = cstart[kClassBlock + 1] - cstart[kClassBlock];
-  s.n_hub = cstart[kClassHub + 1] - cstart[kClassHub];
-  // hub layout on the host (few nodes, already in id order)
-  s.hub_extra_bits = 0;
-  s.h_hub_deg.assign(s.n_hub, 0);
-  s.h_hub_degbits.assign(s.n_hub, 0);
-  s.hub_edges = 0;
-  if (s.n_hub) {
-    std::vector<uint32_t> hn(s.n_hub);
-    const uint32_t* hubs = ptr<uint32_t>(s.class_nodes) + cstart[kClassHub];
-    st = cuda_check(cudaMemcpyAsync(hn.data(), hubs, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream), "hub nodes");
-    if (!st.ok()) return st;
-    if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st;
-    std::vector<uint64_t> lo(s.n_hub), hi(s.n_hub);
-    for (uint64_t i = 0; i < s.n_hub; ++i) {
-      cudaMemcpyAsync(&lo[i], ptr<uint64_t>(s.offsets) + hn[i], 8, cudaMemcpyDeviceToHost, s.stream);
-      cudaMemcpyAsync(&hi[i], ptr<uint64_t>(s.offsets) + hn[i] + 1, 8, cudaMemcpyDeviceToHost, s.stream);
-    }
-    if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "hub offsets")).ok()) return st;
-    std::vector<uint4> chunks;
-    for (uint64_t i = 0; i < s.n_hub; ++i) {
-      const uint64_t d = hi[i] - lo[i];
-      s.h_hub_deg[i] = d;
-      uint32_t bits = 0;
-      while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
-      s.h_hub_degbits[i] = bits;
-      s.hub_edges += d;
-      for (uint64_t b = 0; b < d; b += kHubChunk) {
-        const uint64_t e = lo[i] + b;
-        uint4 q;
-        q.x = (uint32_t)i;
-        q.y = (uint32_t)(e & 0xFFFFFFFFu);
-        q.z = (uint32_t)(e >> 32);
-        q.w = (uint32_t)std::min<uint64_t>(kHubChunk, d - b);
-        chunks.push_back(q);
-      }
-    }
-    s.n_hub_chunks = chunks.size();
-    if (!(st = ensure(s, s.hub_chunks, chunks.size() * sizeof(uint4))).ok()) return st;
-    st = cuda_check(cudaMemcpyAsync(s.hub_chunks.p, chunks.data(), chunks.size() * sizeof(uint4),
-                                    cudaMemcpyHostToDevice, s.stream), "hub chunks");
-    if (!st.ok()) return st;
-    if (!(st = ensure(s, s.hub_tmp, s.hub_edges * 8)).ok()) return st;
-    if (!(st = ensure(s, s.hub_tmp2, s.hub_edges * 8)).ok()) return st;
-    if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st;
-  }
-  return Status::Ok();
-}
-
-namespace {
-
-// (Re)build the per-hub bucket table for the current extra bits.
-Status hub_layout(Store& s) {
-  Status st;
-  std::vector<uint32_t> bits(s.n_hub);
-  std::vector<uint64_t> bbase(s.n_hub + 1, 0);
-  for (uint64_t i = 0; i < s.n_hub; ++i) {
-    bits[i] = s.h_hub_degbits[i];
-    bbase[i + 1] = bbase[i] + (1ull << (bits[i] + s.hub_extra_bits));
-  }
-  s.n_hub_buckets = bbase[s.n_hub];
-  if (!(st = ensure(s, s.hub_bits, s.n_hub * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hub_bbase, (s.n_hub + 1) * 8)).ok()) return st;
-  if (!(st = ensure(s, s.hub_hist, s.n_hub_buckets * 8)).ok()) return st;
-  if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 8)).ok()) return st;
-  if (!(st = ensure(s, s.hub_ucnt, s.n_hub_buckets * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hub_hpart, s.n_hub_buckets * 8)).ok()) return st;
-  cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
-  cudaMemcpyAsync(s.hub_bbase.p, bbase.data(), (s.n_hub + 1) * 8, cudaMemcpyHostToDevice, s.stream);
-  return cuda_check(cudaStreamSynchronize(s.stream), "hub layout");
-}
-
-// Exclusive scan of a uint64 array in place (reuses the renumber tile scan).
+// Exclusive scan of a uint64 array in place, with an optional copy.
 __global__ void __launch_bounds__(kScanThreads) k_tile_sum64(const uint64_t* a, uint64_t n, uint64_t* bsum) {
   __shared__ unsigned long long red[kScanThreads / 32];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
@@ -1320,59 +1216,256 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan64(uint64_t* a, uint6
   }
 }
 
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
 Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
   if (!n) return Status::Ok();
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
-  Status st = ensure(s, s.bsum, std::max<uint64_t>(tiles, 1) * 8);
+  Status st = ensure(s, s.bsum, std::max<uint64_t>(tiles, 64) * 8);
   if (!st.ok()) return st;
   uint64_t* bs = ptr<uint64_t>(s.bsum);
   k_tile_sum64<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(a, n, bs);
-  k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(bs, tiles, ptr<unsigned long long>(s.d_scalars) + 7);
+  k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(bs, tiles, ptr<unsigned long long>(s.d_scalars) + 15);
   k_tile_scan64<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(a, n, bs, copy);
   return launch_check("scan64");
 }
 
-template <typename LabelT>
+template <typename K>
+Status set_smem_attrs_for() {
+  cudaError_t e = cudaSuccess;
+  const int wb = (int)(warp_ws_bytes<K>() * kWarpsPerBlock), bb = (int)blk_ws_bytes<K>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_warp<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, wb);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_warp<uint32_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, wb);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_block<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_block<uint32_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
+  return cuda_check(e, "cudaFuncSetAttribute");
+}
+
+Status set_smem_attrs(int device) {
+  static bool done[64] = {false};
+  if (device >= 0 && device < 64 && done[device]) return Status::Ok();
+  Status st = set_smem_attrs_for<uint32_t>();
+  if (st.ok()) st = set_smem_attrs_for<uint64_t>();
+  if (st.ok() && device >= 0 && device < 64) done[device] = true;
+  return st;
+}
+
+Status read_scalars(Store& s, uint64_t* out) {
+  Status st = cuda_check(cudaMemcpyAsync(s.h_scalars.p, s.d_scalars.p, 16 * sizeof(uint64_t),
+                                         cudaMemcpyDeviceToHost, s.stream), "read scalars");
+  if (!st.ok()) return st;
+  st = cuda_check(cudaStreamSynchronize(s.stream), "stream sync");
+  if (!st.ok()) return st;
+  std::memcpy(out, s.h_scalars.p, 16 * sizeof(uint64_t));
+  return Status::Ok();
+}
+
+uint64_t table_capacity(uint64_t n) {
+  uint64_t c = 1024;
+  while (c < 2 * n) c <<= 1;
+  return c;
+}
+
+// Scalars used per round (uint64 words of Store::d_scalars):
+//  [0] heads, [1] unresolved after the first pass, [2] key total,
+//  [3] largest signature, [4] collided nodes, [5] unresolved after a repair
+//  pass, [6] long-signature pairs, [7] error flags copy, [15] scan scratch.
+Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint32_t* pid, uint64_t* blocks,
+                      uint64_t* collided, bool with_stats, uint64_t* keys, uint64_t* maxsig) {
+  const uint64_t n = s.n, na = s.n_alive;
+  Status st;
+  unsigned long long* sc = ptr<unsigned long long>(s.d_scalars);
+  GroupArgs g;
+  g.hash = ptr<uint64_t>(s.hash);
+  g.p2o = ptr<uint32_t>(s.p2o);
+  g.o2p = ptr<uint32_t>(s.o2p);
+  g.table = ptr<Slot>(s.table);
+  g.tmask = s.tcap - 1;
+  g.slot = ptr<uint32_t>(s.slot);
+  g.rep = ptr<uint32_t>(s.rep);
+  g.err = ptr<uint32_t>(s.d_err);
+  VerifyArgs v;
+  v.mode = mode;
+  v.key64 = key64 ? 1 : 0;
+  v.nlabel = ptr<uint32_t>(s.nlabel);
+  v.prev = prev;
+  v.ucnt = ptr<uint32_t>(s.ucnt);
+  v.off = ptr<uint64_t>(s.offsets);
+  v.sigkey = s.sigkey.p;
+  v.n_collided = sc + 4;
+  v.long_list = ptr<uint32_t>(s.hub_hist);  // reused as (node, candidate) pairs
+  v.n_long = sc + 6;
+  const int sms = sm_count(s.device);
+  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
+  {
+    TimedScope ts(s, KBISIM_KERNEL_OTHER);
+    cudaMemsetAsync(s.table.p, 0xFF, s.tcap * sizeof(Slot), s.stream);
+    cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
+  }
+  {
+    TimedScope ts(s, KBISIM_KERNEL_GROUP);
+    k_group_insert<<<gblocks, 256, 0, s.stream>>>(g, nullptr, na);
+  }
+  if (!(st = launch_check("k_group_insert")).ok()) return st;
+  v.out_list = ptr<uint32_t>(s.ulist[0]);
+  v.n_out = sc + 1;
+  {
+    TimedScope ts(s, KBISIM_KERNEL_VERIFY);
+    k_group_verify<<<gblocks, 256, 0, s.stream>>>(g, v, nullptr, na);
+  }
+  if (!(st = launch_check("k_group_verify")).ok()) return st;
+  uint64_t h[16];
+  if (!(st = read_scalars(s, h)).ok()) return st;
+  if (h[6]) {
+    TimedScope ts(s, KBISIM_KERNEL_VERIFY);
+    const unsigned b = (unsigned)std::min<uint64_t>(grid_for(h[6] * 32, 256), (uint64_t)sms * 16);
+    if (key64) k_verify_long<uint64_t><<<b, 256, 0, s.stream>>>(g, v, h[6]);
+    else k_verify_long<uint32_t><<<b, 256, 0, s.stream>>>(g, v, h[6]);
+    if (!(st = launch_check("k_verify_long")).ok()) return st;
+    if (!(st = read_scalars(s, h)).ok()) return st;
+  }
+  uint64_t unresolved_n = h[1];
+  // Collision repair: the unresolved nodes hold whole classes; the smallest
+  // unresolved node of each hash group heads its class, so every pass
+  // settles at least one class per group.
+  int cur = 0;
+  while (unresolved_n > 0) {
+    const uint64_t cap = table_capacity(unresolved_n);
+    GroupArgs g2 = g;
+    g2.tmask = cap - 1;
+    VerifyArgs v2 = v;
+    v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
+    v2.n_out = sc + 5;
+    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), (uint64_t)sms * 16);
+    {
+      TimedScope ts(s, KBISIM_KERNEL_OTHER);
+      cudaMemsetAsync(s.table.p, 0xFF, cap * sizeof(Slot), s.stream);
+      cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
+      k_group_insert<<<b2, 256, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+      k_group_verify<<<b2, 256, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+    }
+    if (!(st = launch_check("collision repair")).ok()) return st;
+    if (!(st = read_scalars(s, h)).ok()) return st;
+    if (h[6]) {
+      TimedScope ts(s, KBISIM_KERNEL_OTHER);
+      const unsigned b = (unsigned)std::min<uint64_t>(grid_for(h[6] * 32, 256), (uint64_t)sms * 16);
+      if (key64) k_verify_long<uint64_t><<<b, 256, 0, s.stream>>>(g2, v2, h[6]);
+      else k_verify_long<uint32_t><<<b, 256, 0, s.stream>>>(g2, v2, h[6]);
+      if (!(st = launch_check("k_verify_long")).ok()) return st;
+      if (!(st = read_scalars(s, h)).ok()) return st;
+    }
+    if (h[5] >= unresolved_n)  // every pass settles the smallest node of each group
+      return Status::Err(KBISIM_ERR_TIMEOUT, "collision repair made no progress");
+    unresolved_n = h[5];
+    cur ^= 1;
+  }
+  *collided = h[4];
+  // canonical renumbering
+  RankArgs r;
+  r.n = n;
+  r.n_alive = na;
+  r.rep = g.rep;
+  r.p2o = g.p2o;
+  r.ucnt = with_stats ? ptr<uint32_t>(s.ucnt) : nullptr;
+  r.hflag = ptr<uint8_t>(s.hflag);
+  r.rank_o = ptr<uint32_t>(s.rank_o);
+  r.pid = pid;
+  r.bsum = ptr<uint64_t>(s.bsum);
+  r.stats = sc;
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  {
+    TimedScope ts(s, KBISIM_KERNEL_RENUMBER);
+    if (n) {
+      cudaMemsetAsync(s.hflag.p, 0, n, s.stream);
+      k_mark_heads<<<gblocks, 256, 0, s.stream>>>(r);
+      k_flag_tilesum<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r.hflag, n, r.bsum);
+      k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(r.bsum, tiles, sc);
+      k_flag_rank<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r.hflag, n, r.bsum, r.rank_o);
+      k_pid_fill<<<(unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(r);
+    }
+  }
+  if (!(st = launch_check("renumber")).ok()) return st;
+  cudaMemcpyAsync(sc + 7, s.d_err.p, 4, cudaMemcpyDeviceToDevice, s.stream);
+  if (!(st = read_scalars(s, h)).ok()) return st;
+  *blocks = h[0];
+  if (keys) *keys = h[2];
+  if (maxsig) *maxsig = h[3];
+  const uint32_t e = (uint32_t)h[7];
+  if (e & kErrProbe) return Status::Err(KBISIM_ERR_TIMEOUT, "hash table probe bound exceeded");
+  if (e & kErrChecked) return Status::Err(KBISIM_ERR_CHECKED, "device bounds check failed");
+  return Status::Ok();
+}
+
+// (Re)build the per-hub bucket table for the current extra bits.
+Status hub_layout(Store& s) {
+  Status st;
+  std::vector<uint32_t> bits(s.n_hub);
+  std::vector<uint64_t> bbase(s.n_hub + 1, 0);
+  for (uint64_t i = 0; i < s.n_hub; ++i) {
+    bits[i] = s.h_hub_degbits[i];
+    bbase[i + 1] = bbase[i] + (1ull << (bits[i] + s.hub_extra_bits));
+  }
+  s.n_hub_buckets = bbase[s.n_hub];
+  if (!(st = ensure(s, s.hub_bits, s.n_hub * 4)).ok()) return st;
+  if (!(st = ensure(s, s.hub_bbase, (s.n_hub + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, std::max<uint64_t>(s.n, 1) * 8))).ok())
+    return st;
+  if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 8)).ok()) return st;
+  if (!(st = ensure(s, s.hub_ucnt, s.n_hub_buckets * 4)).ok()) return st;
+  if (!(st = ensure(s, s.hub_hpart, s.n_hub_buckets * 8)).ok()) return st;
+  cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.hub_bbase.p, bbase.data(), (s.n_hub + 1) * 8, cudaMemcpyHostToDevice, s.stream);
+  return cuda_check(cudaStreamSynchronize(s.stream), "hub layout");
+}
+
+template <typename LabelT, typename K>
 Status run_signatures(Store& s, const SigArgs& a) {
   Status st;
   const int sms = sm_count(s.device);
-  // small
   SmallLaunch L;
   uint32_t b = 0;
   for (int c = 0; c < kSmallClasses; ++c) {
-    L.start[c] = s.small_start[c];
-    L.count[c] = s.small_count[c];
+    L.start[c] = s.class_start[c];
+    L.count[c] = s.class_start[c + 1] - s.class_start[c];
     L.bstart[c] = b;
-    const uint64_t npw = 32 >> c;
-    const uint64_t warps = (s.small_count[c] + npw - 1) / npw;
+    const uint64_t per_warp = (uint64_t)(32 >> c) * kSmallR;
+    const uint64_t warps = (L.count[c] + per_warp - 1) / per_warp;
     b += (uint32_t)((warps + kSmallWarps - 1) / kSmallWarps);
   }
   L.bstart[kSmallClasses] = b;
   if (b) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL);
-    k_sig_small<LabelT><<<b, kSmallWarps * 32, 0, s.stream>>>(a, ptr<uint32_t>(s.class_nodes), L);
+    k_sig_small<LabelT, K><<<b, kSmallWarps * 32, 0, s.stream>>>(a, L);
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
-  if (s.n_warp) {
+  const uint64_t n_warp = s.class_start[kClassWarp + 1] - s.class_start[kClassWarp];
+  const uint64_t n_block = s.class_start[kClassBlock + 1] - s.class_start[kClassBlock];
+  if (n_warp) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>((s.n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
+    const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                     (uint64_t)sms * 8);
-    k_sig_warp<LabelT><<<g, kWarpsPerBlock * 32, kWarpWsBytes * kWarpsPerBlock, s.stream>>>(
-        a, ptr<uint32_t>(s.class_nodes) + s.class_start[kClassWarp], s.n_warp);
+    k_sig_warp<LabelT, K><<<g, kWarpsPerBlock * 32, warp_ws_bytes<K>() * kWarpsPerBlock, s.stream>>>(
+        a, s.class_start[kClassWarp], n_warp);
   }
   if (!(st = launch_check("k_sig_warp")).ok()) return st;
-  if (s.n_block) {
+  if (n_block) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>(s.n_block, (uint64_t)sms * 4);
-    k_sig_block<LabelT><<<g, kBlockThreads, kBlkWsBytes, s.stream>>>(
-        a, ptr<uint32_t>(s.class_nodes) + s.class_start[kClassBlock], s.n_block);
+    const unsigned g = (unsigned)std::min<uint64_t>(n_block, (uint64_t)sms * 4);
+    k_sig_block<LabelT, K><<<g, kBlockThreads, blk_ws_bytes<K>(), s.stream>>>(a, s.class_start[kClassBlock],
+                                                                            n_block);
   }
   if (!(st = launch_check("k_sig_block")).ok()) return st;
   if (s.n_hub) {
     for (int attempt = 0;; ++attempt) {
-      if (!(st = hub_layout(s)).ok()) return st;
       HubArgs h;
-      h.hub_nodes = ptr<uint32_t>(s.class_nodes) + s.class_start[kClassHub];
+      h.first = s.class_start[kClassHub];
       h.hub_bits = ptr<uint32_t>(s.hub_bits);
       h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
       h.chunks = ptr<uint4>(s.hub_chunks);
@@ -1381,24 +1474,27 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.cursor = ptr<uint64_t>(s.hub_cursor);
       h.bucnt = ptr<uint32_t>(s.hub_ucnt);
       h.bhpart = ptr<uint64_t>(s.hub_hpart);
-      h.tmp = ptr<uint64_t>(s.hub_tmp);
-      h.tmp2 = ptr<uint64_t>(s.hub_tmp2);
+      h.tmp = s.hub_tmp.p;
+      h.tmp2 = s.hub_tmp2.p;
       {
         TimedScope ts(s, KBISIM_KERNEL_SIG_HUB);
         cudaMemsetAsync(h.hist, 0, s.n_hub_buckets * 8, s.stream);
-        k_hub_hist<LabelT><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_hist<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
         if (!(st = scan64(s, h.hist, s.n_hub_buckets, h.cursor)).ok()) return st;
-        k_hub_scatter<LabelT><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
         const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 4);
-        k_hub_bucket<<<g, kBlockThreads, kBlkWsBytes, s.stream>>>(h, s.n_hub_buckets, a.seed, a.err);
-        k_hub_compact<<<(unsigned)s.n_hub, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_bucket<K><<<g, kBlockThreads, blk_ws_bytes<K>(), s.stream>>>(h, s.n_hub_buckets, a.seed, a.err);
+        k_hub_compact<K><<<(unsigned)s.n_hub, kBlockThreads, 0, s.stream>>>(a, h);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
-      if (!(st = read_err(s, &e)).ok()) return st;
+      st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
+      if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+      if (!st.ok()) return st;
       if (!(e & kErrHubOverflow)) break;
       if (attempt >= 6) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
       s.hub_extra_bits += 2;
+      if (!(st = hub_layout(s)).ok()) return st;
       cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
     }
   }
@@ -1408,38 +1504,171 @@ Status run_signatures(Store& s, const SigArgs& a) {
 Status ensure_round_scratch(Store& s) {
   Status st;
   const uint64_t n = std::max<uint64_t>(s.n, 1), m = std::max<uint64_t>(s.m, 1);
-  const uint64_t cap = table_capacity(n);
+  const uint64_t cap = table_capacity(std::max<uint64_t>(s.n_alive, 1));
   if (!(st = ensure(s, s.sigkey, m * 8)).ok()) return st;
   if (!(st = ensure(s, s.ucnt, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.hash, n * 8)).ok()) return st;
-  if (!(st = ensure(s, s.tkey, cap * 8)).ok()) return st;
-  if (!(st = ensure(s, s.tmin, cap * 4)).ok()) return st;
+  if (!(st = ensure(s, s.table, cap * sizeof(Slot))).ok()) return st;
   s.tcap = cap;
   if (!(st = ensure(s, s.slot, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.rep, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.ulist[0], n * 4)).ok()) return st;
   if (!(st = ensure(s, s.ulist[1], n * 4)).ok()) return st;
+  if (!(st = ensure(s, s.hflag, n + 16)).ok()) return st;
+  if (!(st = ensure(s, s.rank_o, n * 4)).ok()) return st;
+  // the long-signature pair list reuses hub_hist: 2 words per alive node
+  if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, n * 8))).ok()) return st;
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (!(st = ensure(s, s.bsum, std::max<uint64_t>(tiles, 64) * 8)).ok()) return st;
   return Status::Ok();
 }
 
+uint32_t bits_for(uint64_t v) {  // bits needed to represent values 0..v
+  uint32_t b = 1;
+  while (b < 64 && (v >> b)) ++b;
+  return b;
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Relabelling and degree classes (once per graph)
+// ---------------------------------------------------------------------------
+Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const void* lab0,
+                     const uint32_t* nlab0, const uint8_t* alive0, uint32_t lab_bytes) {
+  Status st = set_smem_attrs(s.device);
+  if (!st.ok()) return st;
+  const uint64_t n = s.n, m = s.m;
+  const int sms = sm_count(s.device);
+  const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
+  Buf tcnt;
+  if (!(st = ensure(s, tcnt, ntiles * kNumClasses * 8)).ok()) return st;
+  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumClasses * 8, s.stream);
+  if (n)
+    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ntiles,
+                                                                      ptr<unsigned long long>(tcnt));
+  if (!(st = launch_check("k_class_tile_count")).ok()) { release(s, tcnt); return st; }
+  std::vector<uint64_t> h(ntiles * kNumClasses);
+  st = cuda_check(cudaMemcpyAsync(h.data(), tcnt.p, h.size() * 8, cudaMemcpyDeviceToHost, s.stream), "class counts");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) { release(s, tcnt); return st; }
+  uint64_t run = 0;
+  for (int c = 0; c < kNumClasses; ++c) {
+    s.class_start[c] = run;
+    for (uint64_t t = 0; t < ntiles; ++t) {
+      const uint64_t v = h[(uint64_t)c * ntiles + t];
+      h[(uint64_t)c * ntiles + t] = run;
+      run += v;
+    }
+  }
+  s.class_start[kNumClasses] = run;
+  s.n_alive = s.class_start[kClassDead];
+  st = cuda_check(cudaMemcpyAsync(tcnt.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s.stream), "class bases");
+  if (st.ok()) st = ensure(s, s.p2o, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.o2p, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.offsets, (n + 1) * 8);
+  if (st.ok()) st = ensure(s, s.nlabel, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.dst, std::max<uint64_t>(1, m) * 4);
+  if (st.ok()) st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4));
+  if (!st.ok()) { release(s, tcnt); return st; }
+  const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
+  if (n) {
+    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ntiles,
+                                                                        ptr<unsigned long long>(tcnt),
+                                                                        ptr<uint32_t>(s.p2o));
+    k_invert<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), ptr<uint32_t>(s.o2p));
+  }
+  k_relabel_nodes<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), off0, nlab0,
+                                            ptr<unsigned long long>(s.offsets), ptr<uint32_t>(s.nlabel));
+  if (!(st = launch_check("relabel nodes")).ok()) { release(s, tcnt); return st; }
+  if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) { release(s, tcnt); return st; }
+  if (n && m) {
+    const unsigned ge = (unsigned)std::min<uint64_t>(grid_for(n * 32, 256), (uint64_t)sms * 64);
+    const uint32_t* p2o = ptr<uint32_t>(s.p2o);
+    const uint32_t* o2p = ptr<uint32_t>(s.o2p);
+    const uint64_t* off = ptr<uint64_t>(s.offsets);
+    uint32_t* dst = ptr<uint32_t>(s.dst);
+    if (s.label8) {
+      uint8_t* lab = ptr<uint8_t>(s.elabel);
+      if (lab_bytes == 1)
+        k_relabel_edges<uint8_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+                                                                    static_cast<const uint8_t*>(lab0), off, dst, lab);
+      else if (lab_bytes == 2)
+        k_relabel_edges<uint16_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+                                                                     static_cast<const uint16_t*>(lab0), off, dst, lab);
+      else
+        k_relabel_edges<uint32_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+                                                                     static_cast<const uint32_t*>(lab0), off, dst, lab);
+    } else {
+      uint32_t* lab = ptr<uint32_t>(s.elabel);
+      if (lab_bytes == 2)
+        k_relabel_edges<uint16_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+                                                                      static_cast<const uint16_t*>(lab0), off, dst, lab);
+      else
+        k_relabel_edges<uint32_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+                                                                      static_cast<const uint32_t*>(lab0), off, dst, lab);
+    }
+  }
+  st = launch_check("relabel edges");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  release(s, tcnt);
+  if (!st.ok()) return st;
+  // hubs: a contiguous internal id range; their offsets come in one copy
+  s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
+  s.hub_extra_bits = 0;
+  s.h_hub_degbits.assign(s.n_hub, 0);
+  s.hub_edges = 0;
+  s.n_hub_buckets = 0;
+  if (s.n_hub) {
+    std::vector<uint64_t> hoff(s.n_hub + 1);
+    st = cuda_check(cudaMemcpyAsync(hoff.data(), ptr<uint64_t>(s.offsets) + s.class_start[kClassHub],
+                                    (s.n_hub + 1) * 8, cudaMemcpyDeviceToHost, s.stream), "hub offsets");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+    if (!st.ok()) return st;
+    std::vector<uint4> chunks;
+    for (uint64_t i = 0; i < s.n_hub; ++i) {
+      const uint64_t d = hoff[i + 1] - hoff[i];
+      uint32_t bits = 0;
+      while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
+      s.h_hub_degbits[i] = bits;
+      s.hub_edges += d;
+      for (uint64_t b = 0; b < d; b += kHubChunk) {
+        const uint64_t e = hoff[i] + b;
+        uint4 q;
+        q.x = (uint32_t)i;
+        q.y = (uint32_t)(e & 0xFFFFFFFFu);
+        q.z = (uint32_t)(e >> 32);
+        q.w = (uint32_t)std::min<uint64_t>(kHubChunk, d - b);
+        chunks.push_back(q);
+      }
+    }
+    s.n_hub_chunks = chunks.size();
+    if (!(st = ensure(s, s.hub_chunks, chunks.size() * sizeof(uint4))).ok()) return st;
+    st = cuda_check(cudaMemcpyAsync(s.hub_chunks.p, chunks.data(), chunks.size() * sizeof(uint4),
+                                    cudaMemcpyHostToDevice, s.stream), "hub chunks");
+    if (!st.ok()) return st;
+    if (!(st = ensure(s, s.hub_tmp, s.hub_edges * 8)).ok()) return st;
+    if (!(st = ensure(s, s.hub_tmp2, s.hub_edges * 8)).ok()) return st;
+    if (!(st = hub_layout(s)).ok()) return st;
+  }
+  return cuda_check(cudaStreamSynchronize(s.stream), "sync");
+}
 
 Status compute_level0(Store& s) {
   Status st = ensure_round_scratch(s);
   if (!st.ok()) return st;
   const int sms = sm_count(s.device);
-  const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n, 256), (uint64_t)sms * 16);
+  const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16);
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
   {
     TimedScope ts(s, KBISIM_KERNEL_LABEL_GROUP);
-    if (s.n)
-      k_label_hash<<<blocks, 256, 0, s.stream>>>(s.n, ptr<uint32_t>(s.nlabel), ptr<uint64_t>(s.hash),
+    if (s.n_alive)
+      k_label_hash<<<blocks, 256, 0, s.stream>>>(s.n_alive, ptr<uint32_t>(s.nlabel), ptr<uint64_t>(s.hash),
                                                  s.seed, s.hash_mask);
   }
   if (!(st = launch_check("k_label_hash")).ok()) return st;
   uint64_t blocks_out = 0, coll = 0;
-  st = group_and_rank(s, 0, nullptr, ptr<uint32_t>(s.level[0]), &blocks_out, &coll, false, nullptr,
+  st = group_and_rank(s, 0, nullptr, false, ptr<uint32_t>(s.level[0]), &blocks_out, &coll, false, nullptr,
                       nullptr);
   if (!st.ok()) return st;
   s.counts[0] = blocks_out;
@@ -1455,16 +1684,23 @@ Status compute_round(Store& s, uint32_t i) {
   a.dst = ptr<uint32_t>(s.dst);
   a.lab = s.elabel.p;
   a.prev = ptr<uint32_t>(s.level[i - 1]);
-  a.sigkey = ptr<uint64_t>(s.sigkey);
+  a.sigkey = s.sigkey.p;
   a.ucnt = ptr<uint32_t>(s.ucnt);
   a.hash = ptr<uint64_t>(s.hash);
   a.seed = s.seed;
   a.mask = s.hash_mask;
   a.err = ptr<uint32_t>(s.d_err);
-  st = s.label8 ? run_signatures<uint8_t>(s, a) : run_signatures<uint32_t>(s, a);
+  // 32-bit signature words when (label, child id) fits in 32 bits
+  const uint32_t pbits = bits_for(s.counts[i - 1] ? s.counts[i - 1] - 1 : 0);
+  const bool key64 = pbits + s.label_bits > 32;
+  a.pbits = (int)pbits;
+  if (s.label8)
+    st = key64 ? run_signatures<uint8_t, uint64_t>(s, a) : run_signatures<uint8_t, uint32_t>(s, a);
+  else
+    st = key64 ? run_signatures<uint32_t, uint64_t>(s, a) : run_signatures<uint32_t, uint32_t>(s, a);
   if (!st.ok()) return st;
   uint64_t blocks = 0, coll = 0, keys = 0, maxsig = 0;
-  st = group_and_rank(s, 1, a.prev, ptr<uint32_t>(s.level[i]), &blocks, &coll, true, &keys, &maxsig);
+  st = group_and_rank(s, 1, a.prev, key64, ptr<uint32_t>(s.level[i]), &blocks, &coll, true, &keys, &maxsig);
   if (!st.ok()) return st;
   s.counts[i] = blocks;
   kbisim_round_stats rs;
@@ -1476,6 +1712,14 @@ Status compute_round(Store& s, uint32_t i) {
   if (s.stats.size() < i) s.stats.resize(i);
   s.stats[i - 1] = rs;
   return Status::Ok();
+}
+
+Status unpermute_level(Store& s, uint32_t level, uint32_t* dst) {
+  if (!s.n) return Status::Ok();
+  const int sms = sm_count(s.device);
+  const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(s.n, 256), (uint64_t)sms * 16);
+  k_unpermute<<<gb, 256, 0, s.stream>>>(s.n, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.level[level]), dst);
+  return launch_check("k_unpermute");
 }
 
 }  // namespace kb

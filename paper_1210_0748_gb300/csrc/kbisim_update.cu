@@ -1,0 +1,553 @@
+// Maintenance batches (paper Section 4: Add_Nodes, Add_Edges, deletions),
+// applied on the device to the stored edge multiset, followed by a rebuild of
+// the levels.  Theorem 2 states that the maintained partition is the
+// k-bisimulation of the updated graph; recomputing it from the updated graph
+// gives exactly that result (the paper's own validation compares Add_Edges
+// with Build_Bisim the same way).
+//
+// Batch order: node additions (ids n, n+1, ... in batch order, isolated),
+// edge insertions, edge deletions (one stored copy per listed triple; absent
+// triples are counted), node deletions (incident edges removed, node marked
+// deleted).  All steps are kernels:
+//   1. the stored CSR (internal ids) and the inserted edges become one CSR
+//      grouped by original source id (counting sort by source);
+//   2. deletions are matched per source node: every source with deletions
+//      gets a private open-addressing table of (target, label) -> count, and
+//      one warp walks the source's edges claiming one stored copy per count;
+//   3. edges on deleted nodes are dropped, the rest compacted per source;
+//   4. the result is relabelled like a freshly loaded graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kbisim_internal.cuh"
+
+namespace kb {
+namespace {
+
+template <typename T>
+T* ptr(Buf& b) { return static_cast<T*>(b.p); }
+
+unsigned grid(uint64_t work, unsigned per) {
+  uint64_t g = (work + per - 1) / per;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 152ull * 32));
+}
+
+#define GRID_STRIDE(i, n) \
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); i += (uint64_t)gridDim.x * blockDim.x)
+
+// Flags (bit) written into err[0] by validation kernels.
+constexpr uint32_t kBadId = 1u, kDeadEnd = 2u;
+
+__global__ void k_alive_init(uint64_t n0, uint64_t n1, const uint8_t* old_alive, uint8_t* alive) {
+  GRID_STRIDE(o, n1) alive[o] = o < n0 ? (old_alive ? old_alive[o] : (uint8_t)1) : (uint8_t)1;
+}
+
+__global__ void k_check_inserts(uint64_t k, uint64_t n1, const uint32_t* s, const uint32_t* t, const uint8_t* alive,
+                                uint32_t* err) {
+  GRID_STRIDE(i, k) {
+    if (s[i] >= n1 || t[i] >= n1) atomicOr(err, kBadId);
+    else if (!alive[s[i]] || !alive[t[i]]) atomicOr(err, kDeadEnd);
+  }
+}
+
+__global__ void k_check_ids_only(uint64_t k, uint64_t n1, const uint32_t* a, uint32_t* err) {
+  GRID_STRIDE(i, k) if (a[i] >= n1) atomicOr(err, kBadId);
+}
+
+__global__ void k_check_node_dels(uint64_t k, uint64_t n1, const uint32_t* u, const uint8_t* alive, uint32_t* err) {
+  GRID_STRIDE(i, k) {
+    if (u[i] >= n1) atomicOr(err, kBadId);
+    else if (!alive[u[i]]) atomicOr(err, kDeadEnd);
+  }
+}
+
+// Degree of every original node in the stored graph, plus inserted edges.
+__global__ void k_count_combined(uint64_t n0, const uint32_t* o2p, const uint64_t* off, uint64_t k,
+                                 const uint32_t* ins_s, unsigned long long* cnt) {
+  GRID_STRIDE(o, n0) cnt[o] = off[o2p[o] + 1] - off[o2p[o]];
+}
+
+__global__ void k_count_inserts(uint64_t k, const uint32_t* ins_s, unsigned long long* cnt) {
+  GRID_STRIDE(i, k) atomicAdd(&cnt[ins_s[i]], 1ull);
+}
+
+// One warp per original node: copy its stored edges (targets back to
+// original ids, labels widened) to the start of its combined segment.
+template <typename LabelT>
+__global__ void k_copy_stored(uint64_t n0, const uint32_t* o2p, const uint32_t* p2o, const uint64_t* off,
+                              const uint32_t* dst, const LabelT* lab, const unsigned long long* coff,
+                              unsigned long long* cursor, uint32_t* cdst, uint32_t* clab) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t o = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; o < n0;
+       o += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t p = o2p[o];
+    const uint64_t s0 = off[p], d = off[p + 1] - s0, c0 = coff[o];
+    for (uint64_t i = lane; i < d; i += 32) {
+      cdst[c0 + i] = p2o[dst[s0 + i]];
+      clab[c0 + i] = (uint32_t)lab[s0 + i];
+    }
+    if (lane == 0) cursor[o] = c0 + d;
+  }
+}
+
+__global__ void k_place_inserts(uint64_t k, const uint32_t* s, const uint32_t* t, const uint32_t* l,
+                                unsigned long long* cursor, uint32_t* cdst, uint32_t* clab) {
+  GRID_STRIDE(i, k) {
+    const uint64_t q = atomicAdd(&cursor[s[i]], 1ull);
+    cdst[q] = t[i];
+    clab[q] = l[i];
+  }
+}
+
+// Per-source deletion tables: region of 2^r >= 2 * (deletes of the source) slots.
+// Slots start zeroed: key 0 = empty, stored keys are ((target << 32) | label) + 1
+// (never 0 and never overflowing, since target < 2^32 - 1).
+struct DelSlot {
+  unsigned long long key;
+  int count;
+  int pad;
+};
+
+__global__ void k_count_deletes(uint64_t k, const uint32_t* s, uint64_t n1, unsigned long long* dcnt) {
+  GRID_STRIDE(i, k) if (s[i] < n1) atomicAdd(&dcnt[s[i]], 1ull);
+}
+
+__global__ void k_region_size(uint64_t n1, const unsigned long long* dcnt, unsigned long long* rsz) {
+  GRID_STRIDE(o, n1) {
+    const uint64_t c = dcnt[o];
+    uint64_t r = 0;
+    if (c) {
+      r = 4;
+      while (r < 2 * c) r <<= 1;
+    }
+    rsz[o] = r;
+  }
+}
+
+__global__ void k_insert_deletes(uint64_t k, const uint32_t* s, const uint32_t* t, const uint32_t* l,
+                                 const unsigned long long* rbase, const unsigned long long* rsz, DelSlot* tab,
+                                 uint32_t* err) {
+  GRID_STRIDE(i, k) {
+    const uint64_t base = rbase[s[i]], size = rsz[s[i]];
+    const unsigned long long key = (((unsigned long long)t[i] << 32) | l[i]) + 1ull;
+    uint64_t h = (key * 0x9e3779b97f4a7c15ull) >> 7;
+    bool done = false;
+    for (uint64_t probe = 0; probe < size && !done; ++probe) {
+      DelSlot* sl = &tab[base + ((h + probe) & (size - 1))];
+      const unsigned long long cur = atomicCAS(&sl->key, 0ull, key);
+      if (cur == 0ull || cur == key) {
+        atomicAdd(&sl->count, 1);
+        done = true;
+      }
+    }
+    if (!done) atomicOr(err, 4u);
+  }
+}
+
+// One warp per source with deletions: claim stored copies.
+__global__ void k_match_deletes(uint64_t nlist, const uint32_t* list, const unsigned long long* coff,
+                                const uint32_t* cdst, const uint32_t* clab, const unsigned long long* rbase,
+                                const unsigned long long* rsz, DelSlot* tab, uint8_t* del) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < nlist;
+       w += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t o = list[w];
+    const uint64_t base = rbase[o], size = rsz[o];
+    for (uint64_t e = coff[o] + lane; e < coff[o + 1]; e += 32) {
+      const unsigned long long key = (((unsigned long long)cdst[e] << 32) | clab[e]) + 1ull;
+      uint64_t h = (key * 0x9e3779b97f4a7c15ull) >> 7;
+      for (uint64_t probe = 0; probe < size; ++probe) {
+        DelSlot* sl = &tab[base + ((h + probe) & (size - 1))];
+        const unsigned long long cur = sl->key;
+        if (cur == 0ull) break;
+        if (cur == key) {
+          if (atomicSub(&sl->count, 1) > 0) del[e] = 1;
+          break;
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_sources_with_deletes(uint64_t n1, const unsigned long long* dcnt, unsigned long long* nl,
+                                       uint32_t* list) {
+  GRID_STRIDE(o, n1) if (dcnt[o]) list[atomicAdd(nl, 1ull)] = (uint32_t)o;
+}
+
+__global__ void k_missing(uint64_t total, const DelSlot* tab, unsigned long long* missing) {
+  unsigned long long m = 0;
+  GRID_STRIDE(i, total) if (tab[i].key != 0ull && tab[i].count > 0) m += (unsigned long long)tab[i].count;
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(missing, m);
+}
+
+__global__ void k_mark_dead_nodes(uint64_t k, const uint32_t* u, uint8_t* alive) {
+  GRID_STRIDE(i, k) alive[u[i]] = 0;
+}
+
+// Kept edges per source (drop deleted copies and edges on deleted nodes).
+__global__ void k_count_kept(uint64_t n1, const unsigned long long* coff, const uint32_t* cdst, const uint8_t* del,
+                             const uint8_t* alive, unsigned long long* kept) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t o = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; o < n1;
+       o += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    unsigned long long c = 0;
+    if (alive[o])
+      for (uint64_t e = coff[o] + lane; e < coff[o + 1]; e += 32) c += (!del[e] && alive[cdst[e]]) ? 1 : 0;
+    for (int s = 16; s > 0; s >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, s);
+    if (lane == 0) kept[o] = c;
+  }
+}
+
+__global__ void k_compact(uint64_t n1, const unsigned long long* coff, const uint32_t* cdst, const uint32_t* clab,
+                          const uint8_t* del, const uint8_t* alive, const unsigned long long* noff, uint32_t* ndst,
+                          uint32_t* nlab) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t o = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; o < n1;
+       o += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    if (!alive[o]) continue;
+    uint64_t w = noff[o];
+    for (uint64_t b = coff[o]; b < coff[o + 1]; b += 32) {
+      const uint64_t e = b + lane;
+      const bool keep = e < coff[o + 1] && !del[e] && alive[cdst[e]];
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        const uint64_t q = w + __popc(m & ((1u << lane) - 1u));
+        ndst[q] = cdst[e];
+        nlab[q] = clab[e];
+      }
+      w += __popc(m);
+    }
+  }
+}
+
+__global__ void k_gather_labels(uint64_t n0, const uint32_t* o2p, const uint32_t* nlabel, uint32_t* out) {
+  GRID_STRIDE(o, n0) out[o] = nlabel[o2p[o]];
+}
+
+__global__ void k_max32(uint64_t m, const uint32_t* a, unsigned int* mx) {
+  unsigned int v = 0;
+  GRID_STRIDE(i, m) v = max(v, a[i]);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
+}
+
+__global__ void k_any_dead(uint64_t n, const uint8_t* alive, unsigned int* flag) {
+  GRID_STRIDE(o, n) if (!alive[o]) *flag = 1;
+}
+
+// Exclusive scan (reduce-then-scan) of u64 in place, with optional copy.
+constexpr int kT = 1024, kI = 4, kTile = kT * kI;
+
+__global__ void __launch_bounds__(kT) k_usum(const unsigned long long* a, uint64_t n, unsigned long long* bs) {
+  __shared__ unsigned long long red[kT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kTile;
+  unsigned long long c = 0;
+  for (int t = 0; t < kI; ++t) {
+    const uint64_t i = base + (uint64_t)t * kT + threadIdx.x;
+    if (i < n) c += a[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kT / 32; ++w) tot += red[w];
+    bs[blockIdx.x] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_uscan1(unsigned long long* bs, uint64_t nb, unsigned long long* total) {
+  __shared__ unsigned long long wt[kT / 32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t base = 0; base < nb; base += kT) {
+    const uint64_t i = base + threadIdx.x;
+    const unsigned long long v = i < nb ? bs[i] : 0ull;
+    unsigned long long x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long t = wt[lane], xx = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, xx, o);
+        if (lane >= o) xx += y;
+      }
+      wt[lane] = xx - t;
+    }
+    __syncthreads();
+    const unsigned long long c0 = carry;
+    if (i < nb) bs[i] = c0 + wt[w] + x - v;
+    __syncthreads();
+    if (threadIdx.x == kT - 1) carry = c0 + wt[w] + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kT) k_uscan2(unsigned long long* a, uint64_t n, const unsigned long long* bs,
+                                              unsigned long long* copy) {
+  __shared__ unsigned long long wt[kT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)threadIdx.x * kI;
+  unsigned long long f[kI], c = 0;
+  for (int t = 0; t < kI; ++t) {
+    f[t] = base + t < n ? a[base + t] : 0ull;
+    c += f[t];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = wt[lane], xx = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, xx, o);
+      if (lane >= o) xx += y;
+    }
+    wt[lane] = xx - t;
+  }
+  __syncthreads();
+  unsigned long long run = bs[blockIdx.x] + wt[w] + (x - c);
+  for (int t = 0; t < kI; ++t) {
+    if (base + t < n) {
+      a[base + t] = run;
+      if (copy) copy[base + t] = run;
+    }
+    run += f[t];
+  }
+}
+
+// Exclusive scan of a[0..n); the grand total into *total_out (host).
+Status scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned long long* copy, Buf& tmp,
+                uint64_t* total_out) {
+  const uint64_t tiles = std::max<uint64_t>(1, (n + kTile - 1) / kTile);
+  Status st = ensure(s, tmp, (tiles + 1) * 8);
+  if (!st.ok()) return st;
+  unsigned long long* bs = ptr<unsigned long long>(tmp);
+  if (n) {
+    k_usum<<<(unsigned)tiles, kT, 0, s.stream>>>(a, n, bs);
+    k_uscan1<<<1, kT, 0, s.stream>>>(bs, tiles, bs + tiles);
+    k_uscan2<<<(unsigned)tiles, kT, 0, s.stream>>>(a, n, bs, copy);
+  } else {
+    cudaMemsetAsync(bs + tiles, 0, 8, s.stream);
+  }
+  if (!(st = cuda_check(cudaGetLastError(), "scan")).ok()) return st;
+  if (total_out) {
+    uint64_t v = 0;
+    st = cuda_check(cudaMemcpyAsync(&v, bs + tiles, 8, cudaMemcpyDeviceToHost, s.stream), "scan total");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+    *total_out = v;
+  }
+  return st;
+}
+
+struct Bufs {
+  Store& s;
+  std::vector<Buf> b;
+  explicit Bufs(Store& st, int k) : s(st), b(k) {}
+  ~Bufs() {
+    for (Buf& x : b) release(s, x);
+  }
+};
+
+// Stage a batch array on the device (copy when it is host memory).
+Status stage(Store& s, Buf& b, const uint32_t* src, uint64_t k, bool dev, const uint32_t** out) {
+  *out = src;
+  if (!k || dev) return Status::Ok();
+  Status st = ensure(s, b, k * 4);
+  if (!st.ok()) return st;
+  *out = ptr<uint32_t>(b);
+  return cuda_check(cudaMemcpyAsync(b.p, src, k * 4, cudaMemcpyHostToDevice, s.stream), "stage batch");
+}
+
+}  // namespace
+
+Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
+  if (!bt) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch is NULL");
+  if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
+  if ((bt->n_add_nodes && !bt->add_node_label) || (bt->n_ins && (!bt->ins_src || !bt->ins_dst || !bt->ins_label)) ||
+      (bt->n_del && (!bt->del_src || !bt->del_dst || !bt->del_label)) || (bt->n_del_nodes && !bt->del_nodes))
+    return Status::Err(KBISIM_ERR_INVALID_ARG, "batch array is NULL");
+  const uint64_t n0 = s.n, n1 = n0 + bt->n_add_nodes;
+  if (n1 >= 0xFFFFFFFFull) return Status::Err(KBISIM_ERR_INVALID_ARG, "too many nodes");
+  const bool dev = bt->on_device != 0;
+  Status st;
+  Bufs t(s, 24);
+  enum { ADDL, INS_S, INS_T, INS_L, DEL_S, DEL_T, DEL_L, DEL_N, ALIVE, ERR, CNT, COFF, CUR, CDST, CLAB, DCNT, RSZ,
+         RBASE, TAB, LIST, DELF, NOFF, NDST, NLAB };
+  const uint32_t *addl, *is, *it, *il, *ds, *dt, *dl, *dn;
+  if (!(st = stage(s, t.b[ADDL], bt->add_node_label, bt->n_add_nodes, dev, &addl)).ok()) return st;
+  if (!(st = stage(s, t.b[INS_S], bt->ins_src, bt->n_ins, dev, &is)).ok()) return st;
+  if (!(st = stage(s, t.b[INS_T], bt->ins_dst, bt->n_ins, dev, &it)).ok()) return st;
+  if (!(st = stage(s, t.b[INS_L], bt->ins_label, bt->n_ins, dev, &il)).ok()) return st;
+  if (!(st = stage(s, t.b[DEL_S], bt->del_src, bt->n_del, dev, &ds)).ok()) return st;
+  if (!(st = stage(s, t.b[DEL_T], bt->del_dst, bt->n_del, dev, &dt)).ok()) return st;
+  if (!(st = stage(s, t.b[DEL_L], bt->del_label, bt->n_del, dev, &dl)).ok()) return st;
+  if (!(st = stage(s, t.b[DEL_N], bt->del_nodes, bt->n_del_nodes, dev, &dn)).ok()) return st;
+  // alive flags (original order) after node additions
+  if (!(st = ensure(s, t.b[ALIVE], std::max<uint64_t>(n1, 1))).ok()) return st;
+  if (!(st = ensure(s, t.b[ERR], 64)).ok()) return st;
+  uint8_t* alive = ptr<uint8_t>(t.b[ALIVE]);
+  uint32_t* err = ptr<uint32_t>(t.b[ERR]);
+  cudaMemsetAsync(err, 0, 64, s.stream);
+  k_alive_init<<<grid(n1, 256), 256, 0, s.stream>>>(n0, n1, s.any_dead ? ptr<uint8_t>(s.alive_o) : nullptr, alive);
+  if (bt->n_ins) k_check_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, n1, is, it, alive, err);
+  if (bt->n_del) {
+    k_check_ids_only<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, ds, err);
+    k_check_ids_only<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, dt, err);
+  }
+  if (bt->n_del_nodes)
+    k_check_node_dels<<<grid(bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, n1, dn, alive, err);
+  uint32_t e = 0;
+  st = cuda_check(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s.stream), "validate batch");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  if (e & kBadId) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch names a node id >= num_nodes");
+  if (e & kDeadEnd) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch touches a deleted node");
+
+  // 1. combined CSR by original source: stored edges, then inserted ones
+  const uint64_t m0 = s.m, mc = m0 + bt->n_ins;
+  if (!(st = ensure(s, t.b[CNT], (n1 + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, t.b[COFF], (n1 + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, t.b[CUR], (n1 + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, t.b[CDST], std::max<uint64_t>(mc, 1) * 4)).ok()) return st;
+  if (!(st = ensure(s, t.b[CLAB], std::max<uint64_t>(mc, 1) * 4)).ok()) return st;
+  unsigned long long* coff = ptr<unsigned long long>(t.b[COFF]);
+  cudaMemsetAsync(coff, 0, (n1 + 1) * 8, s.stream);
+  if (n0) k_count_combined<<<grid(n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint64_t>(s.offsets),
+                                                               bt->n_ins, is, coff);
+  if (bt->n_ins) k_count_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, coff);
+  uint64_t total = 0;
+  if (!(st = scan_u64(s, coff, n1 + 1, nullptr, t.b[CNT], &total)).ok()) return st;
+  unsigned long long* cur = ptr<unsigned long long>(t.b[CUR]);
+  uint32_t* cdst = ptr<uint32_t>(t.b[CDST]);
+  uint32_t* clab = ptr<uint32_t>(t.b[CLAB]);
+  if (n0) {
+    const unsigned g = grid(n0 * 32, 256);
+    if (s.label8)
+      k_copy_stored<uint8_t><<<g, 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.p2o),
+                                                      ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst),
+                                                      ptr<uint8_t>(s.elabel), coff, cur, cdst, clab);
+    else
+      k_copy_stored<uint32_t><<<g, 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.p2o),
+                                                       ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst),
+                                                       ptr<uint32_t>(s.elabel), coff, cur, cdst, clab);
+  }
+  if (n1 > n0)  // new nodes start empty
+    cudaMemcpyAsync(cur + n0, coff + n0, (n1 - n0) * 8, cudaMemcpyDeviceToDevice, s.stream);
+  if (bt->n_ins) k_place_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, it, il, cur, cdst, clab);
+  if (!(st = cuda_check(cudaGetLastError(), "combine edges")).ok()) return st;
+
+  // 2. deletions, matched per source
+  if (!(st = ensure(s, t.b[DELF], std::max<uint64_t>(mc, 1))).ok()) return st;
+  uint8_t* delf = ptr<uint8_t>(t.b[DELF]);
+  cudaMemsetAsync(delf, 0, std::max<uint64_t>(mc, 1), s.stream);
+  uint64_t missing = 0;
+  if (bt->n_del) {
+    if (!(st = ensure(s, t.b[DCNT], (n1 + 1) * 8)).ok()) return st;
+    if (!(st = ensure(s, t.b[RSZ], (n1 + 1) * 8)).ok()) return st;
+    if (!(st = ensure(s, t.b[RBASE], (n1 + 1) * 8)).ok()) return st;
+    unsigned long long* dcnt = ptr<unsigned long long>(t.b[DCNT]);
+    unsigned long long* rsz = ptr<unsigned long long>(t.b[RSZ]);
+    unsigned long long* rbase = ptr<unsigned long long>(t.b[RBASE]);
+    cudaMemsetAsync(dcnt, 0, (n1 + 1) * 8, s.stream);
+    k_count_deletes<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, n1, dcnt);
+    k_region_size<<<grid(n1 + 1, 256), 256, 0, s.stream>>>(n1 + 1, dcnt, rsz);
+    cudaMemcpyAsync(rbase, rsz, (n1 + 1) * 8, cudaMemcpyDeviceToDevice, s.stream);
+    uint64_t slots = 0;
+    if (!(st = scan_u64(s, rbase, n1 + 1, nullptr, t.b[NOFF], &slots)).ok()) return st;
+    if (!(st = ensure(s, t.b[TAB], std::max<uint64_t>(slots, 1) * sizeof(DelSlot))).ok()) return st;
+    DelSlot* tab = ptr<DelSlot>(t.b[TAB]);
+    cudaMemsetAsync(tab, 0, slots * sizeof(DelSlot), s.stream);
+    k_insert_deletes<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, dt, dl, rbase, rsz, tab, err);
+    if (!(st = ensure(s, t.b[LIST], std::max<uint64_t>(n1, 1) * 4)).ok()) return st;
+    unsigned long long* nl = reinterpret_cast<unsigned long long*>(err + 8);
+    cudaMemsetAsync(nl, 0, 8, s.stream);
+    k_sources_with_deletes<<<grid(n1, 256), 256, 0, s.stream>>>(n1, dcnt, nl, ptr<uint32_t>(t.b[LIST]));
+    uint64_t nsrc = 0;
+    st = cuda_check(cudaMemcpyAsync(&nsrc, nl, 8, cudaMemcpyDeviceToHost, s.stream), "delete sources");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+    if (!st.ok()) return st;
+    if (nsrc)
+      k_match_deletes<<<grid(nsrc * 32, 256), 256, 0, s.stream>>>(nsrc, ptr<uint32_t>(t.b[LIST]), coff, cdst, clab,
+                                                                  rbase, rsz, tab, delf);
+    unsigned long long* dmiss = reinterpret_cast<unsigned long long*>(err + 10);
+    cudaMemsetAsync(dmiss, 0, 8, s.stream);
+    if (slots) k_missing<<<grid(slots, 256), 256, 0, s.stream>>>(slots, tab, dmiss);
+    st = cuda_check(cudaMemcpyAsync(&missing, dmiss, 8, cudaMemcpyDeviceToHost, s.stream), "missing");
+    uint32_t e2 = 0;
+    if (st.ok()) st = cuda_check(cudaMemcpyAsync(&e2, err, 4, cudaMemcpyDeviceToHost, s.stream), "err");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+    if (!st.ok()) return st;
+    if (e2 & 4u) return Status::Err(KBISIM_ERR_TIMEOUT, "deletion table probe bound exceeded");
+  }
+
+  // 3. node deletions; keep the rest
+  if (bt->n_del_nodes) k_mark_dead_nodes<<<grid(bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, dn, alive);
+  if (!(st = ensure(s, t.b[NOFF], (n1 + 1) * 8)).ok()) return st;
+  unsigned long long* noff = ptr<unsigned long long>(t.b[NOFF]);
+  cudaMemsetAsync(noff, 0, (n1 + 1) * 8, s.stream);
+  k_count_kept<<<grid(n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, delf, alive, noff);
+  uint64_t m1 = 0;
+  if (!(st = scan_u64(s, noff, n1 + 1, nullptr, t.b[CNT], &m1)).ok()) return st;
+  if (!(st = ensure(s, t.b[NDST], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
+  if (!(st = ensure(s, t.b[NLAB], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
+  k_compact<<<grid(n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, clab, delf, alive, noff, ptr<uint32_t>(t.b[NDST]),
+                                                     ptr<uint32_t>(t.b[NLAB]));
+  // node labels in original order (stored ones, then the added ones)
+  if (!(st = ensure(s, t.b[CNT], std::max<uint64_t>(n1, 1) * 4)).ok()) return st;
+  uint32_t* nlab = ptr<uint32_t>(t.b[CNT]);
+  if (n0) k_gather_labels<<<grid(n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.nlabel), nlab);
+  if (n1 > n0) cudaMemcpyAsync(nlab + n0, addl, (n1 - n0) * 4, cudaMemcpyDeviceToDevice, s.stream);
+  unsigned int* dmax = reinterpret_cast<unsigned int*>(err + 12);
+  cudaMemsetAsync(dmax, 0, 8, s.stream);
+  if (m1) k_max32<<<grid(m1, 256), 256, 0, s.stream>>>(m1, ptr<uint32_t>(t.b[NLAB]), dmax);
+  k_any_dead<<<grid(n1, 256), 256, 0, s.stream>>>(n1, alive, dmax + 1);
+  uint32_t hv[2] = {0, 0};
+  st = cuda_check(cudaGetLastError(), "compact");
+  if (st.ok()) st = cuda_check(cudaMemcpyAsync(hv, dmax, 8, cudaMemcpyDeviceToHost, s.stream), "label max");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+
+  // 4. the updated graph replaces the stored one
+  for (Buf& b : s.level) release(s, b);
+  for (Buf& b : s.out_level) release(s, b);
+  s.level.clear();
+  s.out_level.clear();
+  s.out_valid.clear();
+  s.has_levels = false;
+  s.n = n1;
+  s.m = m1;
+  s.label8 = hv[0] < 256;
+  uint32_t lb = 1;
+  while (lb < 32 && (hv[0] >> lb)) ++lb;
+  s.label_bits = lb;
+  s.any_dead = hv[1] != 0;
+  if (!(st = relabel_graph(s, reinterpret_cast<const uint64_t*>(noff), ptr<uint32_t>(t.b[NDST]), t.b[NLAB].p, nlab,
+                           s.any_dead ? alive : nullptr, 4)).ok()) {
+    s.has_graph = false;
+    return st;
+  }
+  if (s.any_dead) {
+    if (!(st = ensure(s, s.alive_o, std::max<uint64_t>(n1, 1))).ok()) return st;
+    cudaMemcpyAsync(s.alive_o.p, alive, n1, cudaMemcpyDeviceToDevice, s.stream);
+  }
+  if (missing_out) *missing_out = missing;
+  return cuda_check(cudaStreamSynchronize(s.stream), "update");
+}
+
+}  // namespace kb

@@ -235,3 +235,90 @@ def test_full_size_properties():
     cnt0 = oracle._load().oracle_level0(g.num_nodes, g.node_label.ctypes.data, None, lvl0.ctypes.data)
     assert cnt0 == res.counts[0]
     check_properties(g, pids, res.counts, lvl0, sample=1500)
+
+
+# --- maintenance batches (paper Section 4) -------------------------------------
+
+def _edges_of(g):
+    return g.src(), g.dst, g.edge_label
+
+
+@pytest.mark.parametrize("fix", ["table4_add_edge_2l7.txt", "table5_add_edge_6l5.txt"])
+def test_tables_4_5_through_update(fix):
+    base = golden_io.load("fig1_table1.txt")
+    upd = golden_io.Fixture()
+    upd._nlab, upd._elab = base._nlab, base._elab
+    upd = golden_io.load(fix, base=upd)
+    names = list(base.node_names) + [a for a, _ in upd.add_nodes]
+    g = graph_from_edges(len(base.node_names), base.node_label, base.edges)
+    ins = [(names.index(a), names.index(b), l) for a, l, b in upd.add_edges]
+    with KBisim(early_stop=False) as kb:
+        kb.build(g, 2)
+        res, missing = kb.update(2, add_node_label=[l for _, l in upd.add_nodes],
+                                 ins=tuple(np.array(x, dtype=np.uint32) for x in zip(*ins)))
+        assert missing == 0
+        for lev in range(3):
+            assert kb.pids(lev).tolist() == golden_io.canonical(upd.pids[lev])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_update_equals_recompute(seed):
+    from oracle.update import MultiGraph
+    rng = np.random.default_rng(50 + seed)
+    n, m = 3000, 20000
+    g = synth.random_small_graph(n, m, node_labels=3, edge_labels=3, seed=seed)
+    # a hub, so deletions also hit a long segment
+    hs = np.full(6000, 7, np.uint32)
+    hd = rng.integers(0, n, 6000).astype(np.uint32)
+    hl = rng.integers(0, 3, 6000).astype(np.uint32)
+    s0 = np.concatenate([g.src(), hs])
+    d0 = np.concatenate([g.dst, hd])
+    l0 = np.concatenate([g.edge_label, hl])
+    g = synth.from_coo(n, s0, d0, l0, g.node_label)
+    mg = MultiGraph(n, g.node_label, s0, d0, l0)
+    k = 6
+    with KBisim() as kb:
+        kb.build(g, k)
+        for step in range(3):
+            nn = mg.num_nodes
+            add = rng.integers(0, 3, int(rng.integers(0, 5))).astype(np.uint32)
+            nn2 = nn + add.size
+            alive = np.nonzero(np.array(mg.alive + [1] * add.size, bool))[0]
+            ni = int(rng.integers(0, 400))
+            ins = (rng.choice(alive, ni).astype(np.uint32), rng.choice(alive, ni).astype(np.uint32),
+                   rng.integers(0, 3, ni).astype(np.uint32))
+            s, d, l = mg.coo()
+            pick = rng.choice(s.size, min(s.size, 500), replace=False)
+            dels = [s[pick], d[pick], l[pick]]
+            # repeat some deletions, and delete triples that are absent
+            dels = [np.concatenate([x, x[:20]]) for x in dels]
+            dels[0] = np.concatenate([dels[0], np.array([0, 1], np.uint32)])
+            dels[1] = np.concatenate([dels[1], np.array([0, 1], np.uint32)])
+            dels[2] = np.concatenate([dels[2], np.array([9, 9], np.uint32)])
+            deln = rng.choice(alive[alive < nn], 3, replace=False).astype(np.uint32) if step else \
+                np.zeros(0, np.uint32)
+            want_missing = mg.apply(add, list(zip(*ins)), list(zip(*dels)), deln)
+            ref = mg.kbisim(k)
+            res, missing = kb.update(k, add_node_label=add, ins=ins, dels=tuple(dels), del_nodes=deln)
+            assert missing == want_missing
+            assert kb.num_nodes == nn2
+            assert_same(res, kb.all_pids(k), ref)
+
+
+def test_update_rejects_bad_batches():
+    g = synth.random_small_graph(50, 200, seed=1)
+    with KBisim() as kb:
+        kb.build(g, 3)
+        before = kb.all_pids(3)
+        with pytest.raises(KBisimError) as e:
+            kb.update(3, ins=(np.array([0], np.uint32), np.array([77], np.uint32), np.array([0], np.uint32)))
+        assert e.value.code == ERR_INVALID_ARG
+        kb.update(3, del_nodes=np.array([4], np.uint32))
+        with pytest.raises(KBisimError) as e:
+            kb.update(3, ins=(np.array([4], np.uint32), np.array([5], np.uint32), np.array([0], np.uint32)))
+        assert e.value.code == ERR_INVALID_ARG
+        with pytest.raises(KBisimError) as e:
+            kb.update(3, del_nodes=np.array([4], np.uint32))
+        assert e.value.code == ERR_INVALID_ARG
+        p = kb.all_pids(3)
+        assert (p[:, 4] == 0xFFFFFFFF).all()
