@@ -177,7 +177,7 @@ struct Store {
   Buf sigkey;                  // key words [m]: sorted distinct keys per node at its CSR offset
   Buf ucnt;                    // uint32 [n]
   Buf hash;                    // uint64 [n]
-  Buf table;                   // 16-byte slots (key, smallest original id)
+  Buf table;                   // 64-bit slots (hash fingerprint, smallest original id)
   uint64_t tcap = 0;
   Buf slot;                    // uint32 [n]
   Buf rep;                     // uint32 [n] internal id of the block head
@@ -187,10 +187,9 @@ struct Store {
   Buf bsum;                    // uint64 scan block sums
   Buf hub_hist;                // uint64 [buckets]
   Buf hub_cursor;              // uint64 [buckets]
-  Buf hub_ucnt;                // uint32 [buckets]
-  Buf hub_hpart;               // uint64 [buckets]
+  Buf bucket_hub;              // uint32 [buckets] hub of each bucket
+  Buf hub_acc;                 // per hub: keys written, term sum (uint64), buckets done (uint32)
   Buf hub_tmp;                 // key words [hub_edges]
-  Buf hub_tmp2;                // key words [hub_edges]
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars

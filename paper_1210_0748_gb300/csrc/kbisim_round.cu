@@ -136,94 +136,41 @@ __device__ __forceinline__ uint32_t cas(uint32_t* a, uint32_t c, uint32_t v) { r
 __device__ __forceinline__ uint64_t cas(uint64_t* a, uint64_t c, uint64_t v) {
   return atomicCAS((unsigned long long*)a, (unsigned long long)c, (unsigned long long)v);
 }
-__device__ __forceinline__ void aor(uint32_t* a, uint32_t v) { atomicOr(a, v); }
-__device__ __forceinline__ void aor(uint64_t* a, uint64_t v) { atomicOr((unsigned long long*)a, (unsigned long long)v); }
-__device__ __forceinline__ void aand(uint32_t* a, uint32_t v) { atomicAnd(a, v); }
-__device__ __forceinline__ void aand(uint64_t* a, uint64_t v) { atomicAnd((unsigned long long*)a, (unsigned long long)v); }
-__device__ __forceinline__ int top_bit(uint32_t x) { return 31 - __clz((int)x); }
-__device__ __forceinline__ int top_bit(uint64_t x) { return 63 - __clzll((long long)x); }
 
 template <int NT>
 __device__ __forceinline__ void team_sync() {
   if (NT == 32) __syncwarp(); else __syncthreads();
 }
 
-// Exclusive prefix sum of a[0..n) in shared memory by a team of NT threads
-// (one warp, or one CTA of NT threads).  warp_tot: NT/32 shared words.
-template <int NT>
-__device__ void team_excl_scan(uint32_t* a, int n, uint32_t* warp_tot, int rank) {
-  const int per = (n + NT - 1) / NT;
-  const int lo = min(rank * per, n), hi = min(lo + per, n);
-  uint32_t sum = 0;
-  for (int i = lo; i < hi; ++i) sum += a[i];
-  const int lane = rank & 31;
-  uint32_t x = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  uint32_t excl = x - sum;
-  if (NT > 32) {
-    const int w = rank >> 5;
-    if (lane == 31) warp_tot[w] = x;
-    team_sync<NT>();
-    if (w == 0) {
-      uint32_t t = lane < NT / 32 ? warp_tot[lane] : 0;
-      uint32_t xx = t;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, xx, o);
-        if (lane >= o) xx += y;
-      }
-      if (lane < NT / 32) warp_tot[lane] = xx - t;
-    }
-    team_sync<NT>();
-    excl += warp_tot[w];
-  }
-  uint32_t run = excl;
-  for (int i = lo; i < hi; ++i) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
-  }
-  team_sync<NT>();
-}
-
 // --------------------------------------------------------------------------
-// Team dedupe + sort in shared memory
+// Team dedupe in shared memory (no sorting)
 // --------------------------------------------------------------------------
+// A team (one warp, or one CTA) inserts keys into an open-addressing set in
+// shared memory.  The first inserter of a key owns it: it writes the key to
+// the node's output at the next free position and adds its hash term.  The
+// order of a node's distinct keys is therefore arbitrary: signatures are
+// compared as sets (see k_group_verify / k_verify_long).
 template <typename K>
-struct TeamWs {
-  K* set;           // [hcap] hash set, reused as the sorted output
-  K* uniq;          // [ucap] distinct keys in arrival order
-  K* bitv;          // [2] OR and AND of the distinct keys
-  uint64_t* red;    // [NT/32] reduction scratch
-  uint32_t* cnt;    // [ucap/2] bucket counters
-  uint32_t* sh;     // [4] distinct count, saw-empty-key flag, overflow flag
-  uint32_t* wtot;   // [NT/32]
-  int hcap, ucap;
+struct TeamSet {
+  K* set;          // [hcap]
+  K* uniq;         // [ucap] distinct keys (hub buckets only)
+  uint32_t* sh;    // [4]: distinct count, saw-the-empty-key flag, overflow flag, spare
+  uint64_t* red;   // [NT/32] reduction scratch
 };
 
 template <typename K>
-__host__ __device__ constexpr size_t team_ws_bytes(int hcap, int ucap, int nt) {
-  return ((size_t)hcap * sizeof(K) + (size_t)ucap * sizeof(K) + 16 + (size_t)(nt / 32) * 8 +
-          (size_t)(ucap / 2) * 4 + 16 + (size_t)(nt / 32) * 4 + 15) / 16 * 16;
+__host__ __device__ constexpr size_t team_set_bytes(int hcap, int ucap, int nt) {
+  return ((size_t)hcap * sizeof(K) + (size_t)ucap * sizeof(K) + 16 + (size_t)(nt / 32) * 8 + 15) / 16 * 16;
 }
 
 template <typename K>
-__device__ __forceinline__ TeamWs<K> carve(char* base, int hcap, int ucap, int nt) {
-  TeamWs<K> ws;
-  ws.set = reinterpret_cast<K*>(base);
-  ws.uniq = ws.set + hcap;
-  ws.bitv = ws.uniq + ucap;
-  ws.red = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws.bitv) + 16);
-  ws.cnt = reinterpret_cast<uint32_t*>(ws.red + nt / 32);
-  ws.sh = ws.cnt + ucap / 2;
-  ws.wtot = ws.sh + 4;
-  ws.hcap = hcap;
-  ws.ucap = ucap;
-  return ws;
+__device__ __forceinline__ TeamSet<K> carve_set(char* base, int hcap, int ucap) {
+  TeamSet<K> t;
+  t.set = reinterpret_cast<K*>(base);
+  t.uniq = t.set + hcap;
+  t.sh = reinterpret_cast<uint32_t*>(t.uniq + ucap);
+  t.red = reinterpret_cast<uint64_t*>(t.sh + 4);
+  return t;
 }
 
 // Smallest power of two >= 2 n, clamped to [64, cap].
@@ -234,97 +181,51 @@ __device__ __forceinline__ int set_size_for(uint64_t n, int cap) {
 }
 
 template <int NT, typename K>
-__device__ __forceinline__ void team_begin(const TeamWs<K>& ws, int hcap, int rank) {
-  for (int i = rank; i < hcap; i += NT) ws.set[i] = KeyOps<K>::kEmpty;
-  if (rank < 4) ws.sh[rank] = 0;
-  if (rank == 0) {
-    ws.bitv[0] = (K)0;
-    ws.bitv[1] = (K)~(K)0;
-  }
+__device__ __forceinline__ void set_clear(const TeamSet<K>& ts, int hcap, int rank) {
+  for (int i = rank; i < hcap; i += NT) ts.set[i] = KeyOps<K>::kEmpty;
+  if (rank < 4) ts.sh[rank] = 0;
 }
 
-// Insert one key into the team's shared-memory set; a key seen for the first
-// time is appended to ws.uniq.  Probing is bounded by the set size.
+// Insert k; true if this call inserted it first.  Probing is bounded by the
+// set size; a full set raises the overflow flag.
 template <typename K>
-__device__ __forceinline__ void team_insert(const TeamWs<K>& ws, int hcap, K k) {
-  bool fresh = false;
-  if (k == KeyOps<K>::kEmpty) {
-    fresh = atomicExch(&ws.sh[1], 1u) == 0u;
-  } else {
-    volatile K* vset = ws.set;
-    const uint32_t hmask = (uint32_t)(hcap - 1);
-    uint32_t s = (uint32_t)k & hmask;
-    int t = 0;
-    for (; t < hcap; ++t) {
-      const K cur = vset[s];
-      if (cur == k) break;
-      if (cur == KeyOps<K>::kEmpty) {
-        const K old = cas(&ws.set[s], KeyOps<K>::kEmpty, k);
-        if (old == KeyOps<K>::kEmpty) { fresh = true; break; }
-        if (old == k) break;
-      }
-      s = (s + 1) & hmask;
+__device__ __forceinline__ bool set_insert(const TeamSet<K>& ts, int hcap, K k) {
+  if (k == KeyOps<K>::kEmpty) return atomicExch(&ts.sh[1], 1u) == 0u;
+  volatile K* vset = ts.set;
+  const uint32_t hmask = (uint32_t)(hcap - 1);
+  uint32_t s = (uint32_t)k & hmask;
+  for (int t = 0; t < hcap; ++t) {
+    const K cur = vset[s];
+    if (cur == k) return false;
+    if (cur == KeyOps<K>::kEmpty) {
+      const K old = cas(&ts.set[s], KeyOps<K>::kEmpty, k);
+      if (old == KeyOps<K>::kEmpty) return true;
+      if (old == k) return false;
     }
-    if (t == hcap) ws.sh[2] = 1u;
+    s = (s + 1) & hmask;
   }
-  if (fresh) {
-    const uint32_t idx = atomicAdd(&ws.sh[0], 1u);
-    if (idx < (uint32_t)ws.ucap) ws.uniq[idx] = k; else ws.sh[2] = 1u;
-    aor(&ws.bitv[0], k);
-    aand(&ws.bitv[1], k);
-  }
+  ts.sh[2] = 1u;
+  return false;
 }
 
-// After all inserts (and a team sync): sort the distinct keys ascending into
-// ws.set[0..U).  Returns U, or 0xFFFFFFFF on overflow.  Counting sort into
-// about U/2 buckets on the highest bits in which the distinct keys differ (so
-// keys sharing a prefix -- one hub bucket -- still spread), then insertion
-// sort inside each tiny bucket.
-template <int NT, typename K>
-__device__ uint32_t team_sort(const TeamWs<K>& ws, int rank) {
-  if (ws.sh[2]) return 0xFFFFFFFFu;
-  const uint32_t U = ws.sh[0];
-  int bits = 0;
-  while ((2u << bits) < U) ++bits;  // NB = 2^bits ~ U/2
-  if (U <= 2) bits = 0;
-  const int NB = 1 << bits;
-  const K diff = ws.bitv[0] ^ ws.bitv[1];
-  const int top = diff ? top_bit(diff) : 0;  // highest differing bit
-  const int shift = (top + 1 >= bits) ? top + 1 - bits : 0;
-  const K bmask = (K)(NB - 1);
-  for (int b = rank; b < NB; b += NT) ws.cnt[b] = 0;
-  team_sync<NT>();
-  for (uint32_t i = rank; i < U; i += NT) atomicAdd(&ws.cnt[(uint32_t)((ws.uniq[i] >> shift) & bmask)], 1u);
-  team_sync<NT>();
-  team_excl_scan<NT>(ws.cnt, NB, ws.wtot, rank);
-  for (uint32_t i = rank; i < U; i += NT) {
-    const K k = ws.uniq[i];
-    const uint32_t p = atomicAdd(&ws.cnt[(uint32_t)((k >> shift) & bmask)], 1u);
-    ws.set[p] = k;
+// Membership test in a set built by set_insert.
+template <typename K>
+__device__ __forceinline__ bool set_find(const TeamSet<K>& ts, int hcap, K k) {
+  if (k == KeyOps<K>::kEmpty) return ts.sh[1] != 0u;
+  const uint32_t hmask = (uint32_t)(hcap - 1);
+  uint32_t s = (uint32_t)k & hmask;
+  for (int t = 0; t < hcap; ++t) {
+    const K cur = ts.set[s];
+    if (cur == k) return true;
+    if (cur == KeyOps<K>::kEmpty) return false;
+    s = (s + 1) & hmask;
   }
-  team_sync<NT>();
-  for (int b = rank; b < NB; b += NT) {
-    const uint32_t lo = b ? ws.cnt[b - 1] : 0u, hi = ws.cnt[b];
-    for (uint32_t i = lo + 1; i < hi; ++i) {
-      const K v = ws.set[i];
-      uint32_t j = i;
-      while (j > lo && ws.set[j - 1] > v) {
-        ws.set[j] = ws.set[j - 1];
-        --j;
-      }
-      ws.set[j] = v;
-    }
-  }
-  team_sync<NT>();
-  return U;
+  return false;
 }
 
-// Sum of elem_term over keys[0..U) across the team (valid in every lane for
-// NT == 32, in rank 0 for NT > 32).
-template <int NT, typename K>
-__device__ uint64_t team_term_sum(const K* keys, uint32_t U, uint64_t seed, uint64_t* red, int rank) {
-  uint64_t t = 0;
-  for (uint32_t i = rank; i < U; i += NT) t += elem_term(keys[i], seed);
+// Sum over the team; valid in every lane for NT == 32, in rank 0 otherwise.
+template <int NT>
+__device__ __forceinline__ uint64_t team_sum(uint64_t t, uint64_t* red, int rank) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
   if (NT == 32) return t;
@@ -361,9 +262,9 @@ __device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e) {
 }
 
 // Out-degree <= 32: P = 2^c lanes per node, 32/P nodes per warp, R groups of
-// nodes per warp with all their loads issued before any sorting.  Keys are
-// sorted by a bitonic network across the P lanes, duplicates dropped by
-// comparing with the previous lane, survivors compacted with a ballot.
+// nodes per warp with all their loads issued first.  Duplicates are found by
+// one warp-wide match: of the lanes of a node holding the same key, the
+// lowest keeps it; keepers are compacted with a ballot.
 constexpr int kSmallR = 4;
 
 template <int P, typename LabelT, typename K>
@@ -373,6 +274,8 @@ __device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first,
   constexpr K kE = KeyOps<K>::kEmpty;
   const int lane = threadIdx.x & 31;
   const int g = lane / P, j = lane % P;
+  const unsigned gbits = (P == 32) ? kFull : (((1u << (P & 31)) - 1u) << (g * P));
+  const unsigned below = (1u << lane) - 1u;
   uint64_t off[kSmallR];
   uint32_t d[kSmallR];
   K key[kSmallR];
@@ -388,35 +291,23 @@ __device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first,
   }
 #pragma unroll
   for (int r = 0; r < kSmallR; ++r) key[r] = j < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + j) : kE;
-#pragma unroll
-  for (int k = 2; k <= P; k <<= 1) {
-#pragma unroll
-    for (int s = k >> 1; s > 0; s >>= 1) {
-      const bool up = (j & k) == 0;
-      const bool lower = (j & s) == 0;
-#pragma unroll
-      for (int r = 0; r < kSmallR; ++r) {
-        const K other = __shfl_xor_sync(kFull, key[r], s);
-        key[r] = (lower == up) ? min(key[r], other) : max(key[r], other);
-      }
-    }
-  }
   K* out = static_cast<K*>(a.sigkey);
 #pragma unroll
   for (int r = 0; r < kSmallR; ++r) {
-    const K prevk = __shfl_up_sync(kFull, key[r], 1);
-    const bool uniq = (j < (int)d[r]) && (j == 0 || key[r] != prevk);
-    const unsigned bal = __ballot_sync(kFull, uniq);
-    const unsigned gmask = (P == 32) ? bal : ((bal >> (g * P)) & ((1u << (P & 31)) - 1u));
-    const int pos = __popc(gmask & ((1u << j) - 1u));
-    if (uniq) out[off[r] + pos] = key[r];
-    uint64_t t = uniq ? elem_term(key[r], a.seed) : 0ull;
+    const bool valid = j < (int)d[r];
+    // padding lanes sit after the node's real lanes, so a real lane is always
+    // the lowest of its peers
+    const unsigned peers = __match_any_sync(kFull, key[r]) & gbits;
+    const bool keep = valid && (__ffs(peers) - 1) == lane;
+    const unsigned bal = __ballot_sync(kFull, keep) & gbits;
+    if (keep) out[off[r] + __popc(bal & below)] = key[r];
+    uint64_t t = keep ? elem_term(key[r], a.seed) : 0ull;
 #pragma unroll
     for (int s = P >> 1; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
     const uint64_t idx = (warp_idx * kSmallR + r) * NPW + g;
     if (j == 0 && idx < count) {
       const uint64_t p = first + idx;
-      const uint32_t U = (uint32_t)__popc(gmask);
+      const uint32_t U = (uint32_t)__popc(bal);
       a.ucnt[p] = U;
       a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
     }
@@ -446,120 +337,99 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_sig_small(SigArgs a, Small
   }
 }
 
-// Out-degree 33..kWarpMax: one warp per node; keys are loaded into registers
-// (8 per lane) before the shared-memory dedupe.
+// Out-degree 33..kWarpMax: one warp per node (8 keys per lane in registers),
+// kWarpMax+1..kBlockMax: one CTA per node (8 keys per thread).  A shared-
+// memory set deduplicates; owners write their key at the next free position.
 constexpr int kWarpItems = kWarpMax / 32;
 constexpr int kWarpsPerBlock = 8;
+constexpr int kBlkItems = kBlockMax / kBlockThreads;
 
 template <typename K>
-__host__ __device__ constexpr size_t warp_ws_bytes() { return team_ws_bytes<K>(2 * kWarpMax, kWarpMax, 32); }
+__host__ __device__ constexpr size_t warp_ws_bytes() { return team_set_bytes<K>(2 * kWarpMax, 0, 32); }
+template <typename K>
+__host__ __device__ constexpr size_t blk_ws_bytes() { return team_set_bytes<K>(2 * kBlockMax, 0, kBlockThreads); }
+
+template <int NT, int ITEMS, typename LabelT, typename K>
+__device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>& ts, int cap, uint64_t p,
+                                              int rank) {
+  const uint64_t off = a.off[p];
+  const uint32_t d = (uint32_t)(a.off[p + 1] - off);
+  K keys[ITEMS];
+#pragma unroll
+  for (int t = 0; t < ITEMS; ++t) {
+    const uint32_t i = rank + NT * t;
+    keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
+  }
+  const int hcap = set_size_for(d, cap);
+  set_clear<NT>(ts, hcap, rank);
+  team_sync<NT>();
+  K* out = static_cast<K*>(a.sigkey);
+  uint64_t term = 0;
+#pragma unroll
+  for (int t = 0; t < ITEMS; ++t) {
+    if (rank + NT * t < d && set_insert(ts, hcap, keys[t])) {
+      const uint32_t pos = atomicAdd(&ts.sh[0], 1u);
+      out[off + pos] = keys[t];
+      term += elem_term(keys[t], a.seed);
+    }
+  }
+  team_sync<NT>();
+  const uint32_t U = ts.sh[0];
+  term = team_sum<NT>(term, ts.red, rank);
+  if (rank == 0) {
+    a.ucnt[p] = U;
+    a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
+  }
+  team_sync<NT>();
+}
 
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TeamWs<K> ws = carve<K>(smem + w * warp_ws_bytes<K>(), 2 * kWarpMax, kWarpMax, 32);
-  K* out = static_cast<K*>(a.sigkey);
+  TeamSet<K> ts = carve_set<K>(smem + w * warp_ws_bytes<K>(), 2 * kWarpMax, 0);
   for (uint64_t idx = (uint64_t)blockIdx.x * kWarpsPerBlock + w; idx < count;
-       idx += (uint64_t)gridDim.x * kWarpsPerBlock) {
-    const uint64_t p = first + idx;
-    const uint64_t off = a.off[p];
-    const uint32_t d = (uint32_t)(a.off[p + 1] - off);
-    K keys[kWarpItems];
-#pragma unroll
-    for (int t = 0; t < kWarpItems; ++t) {
-      const uint32_t i = lane + 32 * t;
-      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
-    }
-    const int hcap = set_size_for(d, 2 * kWarpMax);
-    team_begin<32>(ws, hcap, lane);
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < kWarpItems; ++t)
-      if (lane + 32 * t < d) team_insert(ws, hcap, keys[t]);
-    __syncwarp();
-    const uint32_t U = team_sort<32>(ws, lane);
-    if (U == 0xFFFFFFFFu) {  // cannot happen: at most d <= ucap distinct keys
-      if (lane == 0) atomicOr(a.err, kErrHubOverflow);
-      __syncwarp();
-      continue;
-    }
-    for (uint32_t i = lane; i < U; i += 32) out[off + i] = ws.set[i];
-    const uint64_t t = team_term_sum<32>(ws.set, U, a.seed, nullptr, lane);
-    if (lane == 0) {
-      a.ucnt[p] = U;
-      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
-    }
-    __syncwarp();
-  }
+       idx += (uint64_t)gridDim.x * kWarpsPerBlock)
+    sig_team_node<32, kWarpItems, LabelT, K>(a, ts, 2 * kWarpMax, first + idx, lane);
 }
-
-// Out-degree kWarpMax+1..kBlockMax: one CTA per node (8 keys per thread in
-// registers), and the hub buckets.
-constexpr int kBlkItems = kBlockMax / kBlockThreads;
-
-template <typename K>
-__host__ __device__ constexpr size_t blk_ws_bytes() { return team_ws_bytes<K>(2 * kBlockMax, kBlockMax, kBlockThreads); }
 
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kBlockThreads) k_sig_block(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs<K> ws = carve<K>(smem, 2 * kBlockMax, kBlockMax, kBlockThreads);
-  K* out = static_cast<K*>(a.sigkey);
-  for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
-    const uint64_t p = first + idx;
-    const uint64_t off = a.off[p];
-    const uint32_t d = (uint32_t)(a.off[p + 1] - off);
-    K keys[kBlkItems];
-#pragma unroll
-    for (int t = 0; t < kBlkItems; ++t) {
-      const uint32_t i = threadIdx.x + kBlockThreads * t;
-      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
-    }
-    const int hcap = set_size_for(d, 2 * kBlockMax);
-    team_begin<kBlockThreads>(ws, hcap, threadIdx.x);
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kBlkItems; ++t)
-      if (threadIdx.x + kBlockThreads * t < d) team_insert(ws, hcap, keys[t]);
-    __syncthreads();
-    const uint32_t U = team_sort<kBlockThreads>(ws, threadIdx.x);
-    if (U == 0xFFFFFFFFu) {
-      if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
-      __syncthreads();
-      continue;
-    }
-    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) out[off + i] = ws.set[i];
-    const uint64_t t = team_term_sum<kBlockThreads, K>(ws.set, U, a.seed, ws.red, threadIdx.x);
-    if (threadIdx.x == 0) {
-      a.ucnt[p] = U;
-      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
-    }
-    __syncthreads();
-  }
+  TeamSet<K> ts = carve_set<K>(smem, 2 * kBlockMax, 0);
+  for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x)
+    sig_team_node<kBlockThreads, kBlkItems, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x);
 }
 
 // ---- hubs: out-degree > kBlockMax ----------------------------------------
 // Partition each hub's keys by their top bits into buckets expected to hold
-// about kHubBucketTarget distinct keys, dedupe + sort each bucket in shared
-// memory, then concatenate the buckets in order (the top bits order them).
+// about kHubBucketTarget distinct keys; one CTA deduplicates a bucket in
+// shared memory and appends its distinct keys at the hub's CSR offset.  The
+// last bucket of a hub to finish writes the hub's count and hash.
 struct HubArgs {
   uint64_t first;           // internal id of hub 0
   const uint32_t* hub_bits;
   const uint64_t* hub_bbase;
+  const uint32_t* bucket_hub;
   const uint4* chunks;
   uint32_t extra_bits;
   uint64_t* hist;     // per bucket: count, then (after the scan) start
   uint64_t* cursor;   // per bucket: fill cursor, then end
-  uint32_t* bucnt;    // per bucket: distinct keys
-  uint64_t* bhpart;   // per bucket: term sum
+  unsigned long long* hub_cur;   // per hub: distinct keys written
+  unsigned long long* hub_term;  // per hub: term sum
+  unsigned int* hub_done;        // per hub: buckets finished
   void* tmp;
-  void* tmp2;
 };
 
 constexpr int kHubItems = kHubChunk / kBlockThreads;  // 16
 constexpr int kHubSmemBuckets = 4096;
+constexpr int kHubUcap = kBlockMax;                   // distinct keys per bucket
+
+template <typename K>
+__host__ __device__ constexpr size_t hub_ws_bytes() {
+  return team_set_bytes<K>(2 * kHubUcap, kHubUcap, kBlockThreads);
+}
 
 template <typename K>
 __device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
@@ -655,19 +525,22 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
   }
 }
 
-// One CTA per hub bucket: distinct keys of the bucket, sorted, into tmp2.
+// One CTA per hub bucket.
 template <typename K>
-__global__ void __launch_bounds__(kBlockThreads)
-    k_hub_bucket(HubArgs h, uint64_t n_buckets, uint64_t seed, uint32_t* err) {
+__global__ void __launch_bounds__(kBlockThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem[];
-  TeamWs<K> ws = carve<K>(smem, 2 * kBlockMax, kBlockMax, kBlockThreads);
+  TeamSet<K> ts = carve_set<K>(smem, 2 * kHubUcap, kHubUcap);
+  __shared__ unsigned long long obase;
+  __shared__ unsigned int last;
   const K* tmp = static_cast<const K*>(h.tmp);
-  K* tmp2 = static_cast<K*>(h.tmp2);
+  K* out = static_cast<K*>(a.sigkey);
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
+    const uint32_t hub = h.bucket_hub[b];
+    const uint64_t p = h.first + hub;
     const uint64_t lo = h.hist[b];
     const uint64_t n = h.cursor[b] - lo;  // after the scatter, cursor = end of bucket
-    const int hcap = set_size_for(n, 2 * kBlockMax);
-    team_begin<kBlockThreads>(ws, hcap, threadIdx.x);
+    const int hcap = set_size_for(n, 2 * kHubUcap);
+    set_clear<kBlockThreads>(ts, hcap, threadIdx.x);
     __syncthreads();
     for (uint64_t base = 0; base < n; base += (uint64_t)kBlockThreads * 8) {
       K keys[8];
@@ -677,136 +550,126 @@ __global__ void __launch_bounds__(kBlockThreads)
         keys[t] = i < n ? tmp[lo + i] : (K)0;
       }
 #pragma unroll
-      for (int t = 0; t < 8; ++t)
-        if (base + threadIdx.x + (uint64_t)kBlockThreads * t < n) team_insert(ws, hcap, keys[t]);
+      for (int t = 0; t < 8; ++t) {
+        if (base + threadIdx.x + (uint64_t)kBlockThreads * t < n && set_insert(ts, hcap, keys[t])) {
+          const uint32_t q = atomicAdd(&ts.sh[0], 1u);
+          if (q < (uint32_t)kHubUcap) ts.uniq[q] = keys[t]; else ts.sh[2] = 1u;
+        }
+      }
     }
     __syncthreads();
-    const uint32_t U = team_sort<kBlockThreads>(ws, threadIdx.x);
-    if (U == 0xFFFFFFFFu) {
-      if (threadIdx.x == 0) {
-        atomicOr(err, kErrHubOverflow);
-        h.bucnt[b] = 0;
-        h.bhpart[b] = 0;
-      }
+    if (ts.sh[2]) {  // more distinct keys than the bucket can hold: caller re-partitions
+      if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
       __syncthreads();
       continue;
     }
-    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) tmp2[lo + i] = ws.set[i];
-    const uint64_t t = team_term_sum<kBlockThreads, K>(ws.set, U, seed, ws.red, threadIdx.x);
+    const uint32_t U = ts.sh[0];
+    if (threadIdx.x == 0) obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
+    __syncthreads();
+    const uint64_t off = a.off[p] + obase;
+    uint64_t term = 0;
+    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) {
+      out[off + i] = ts.uniq[i];
+      term += elem_term(ts.uniq[i], a.seed);
+    }
+    term = team_sum<kBlockThreads>(term, ts.red, threadIdx.x);
     if (threadIdx.x == 0) {
-      h.bucnt[b] = U;
-      h.bhpart[b] = t;
+      atomicAdd(&h.hub_term[hub], (unsigned long long)term);
+      __threadfence();
+      const unsigned nb = 1u << (h.hub_bits[hub] + h.extra_bits);
+      last = atomicAdd(&h.hub_done[hub], 1u) == nb - 1u;
     }
     __syncthreads();
-  }
-}
-
-// One CTA per hub: concatenate its buckets' sorted keys at the hub's CSR offset.
-template <typename K>
-__global__ void __launch_bounds__(kBlockThreads) k_hub_compact(SigArgs a, HubArgs h) {
-  __shared__ uint32_t cnt[kBlockThreads];
-  __shared__ uint32_t wtot[kBlockThreads / 32];
-  __shared__ uint64_t red[kBlockThreads / 32];
-  __shared__ unsigned long long running;
-  const uint32_t hub = blockIdx.x;
-  const uint64_t p = h.first + hub;
-  const uint64_t off = a.off[p];
-  const uint64_t b0 = h.hub_bbase[hub];
-  const uint64_t nb = (uint64_t)1 << (h.hub_bits[hub] + h.extra_bits);
-  const K* tmp2 = static_cast<const K*>(h.tmp2);
-  K* out = static_cast<K*>(a.sigkey);
-  if (threadIdx.x == 0) running = 0;
-  uint64_t term = 0;
-  __syncthreads();
-  for (uint64_t base = 0; base < nb; base += kBlockThreads) {
-    const uint64_t b = base + threadIdx.x;
-    const uint32_t myc = b < nb ? h.bucnt[b0 + b] : 0u;
-    if (b < nb) term += h.bhpart[b0 + b];
-    cnt[threadIdx.x] = myc;
-    __syncthreads();
-    team_excl_scan<kBlockThreads>(cnt, kBlockThreads, wtot, threadIdx.x);
-    const uint64_t run0 = running;
-    const int nchunk = (int)((nb - base) < (uint64_t)kBlockThreads ? (nb - base) : (uint64_t)kBlockThreads);
-    for (int j = 0; j < nchunk; ++j) {
-      const uint64_t bj = b0 + base + j;
-      const uint32_t U = h.bucnt[bj];
-      const uint64_t lo = h.hist[bj];
-      const uint64_t dstp = off + run0 + cnt[j];
-      for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) out[dstp + i] = tmp2[lo + i];
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
+      const unsigned long long tsum = atomicAdd(&h.hub_term[hub], 0ull);
+      a.ucnt[p] = (uint32_t)tot;
+      a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
     }
     __syncthreads();
-    if (threadIdx.x == kBlockThreads - 1) running = run0 + cnt[kBlockThreads - 1] + myc;
-    __syncthreads();
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(kFull, term, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t tot = 0;
-    for (int w = 0; w < kBlockThreads / 32; ++w) tot += red[w];
-    const uint64_t U = running;
-    a.ucnt[p] = (uint32_t)U;
-    a.hash[p] = node_hash(tot, a.prev[p], U, a.seed, a.mask);
   }
 }
 
 // --------------------------------------------------------------------------
 // Grouping: equal hashes -> smallest original id; exact verification
 // --------------------------------------------------------------------------
-struct __align__(16) Slot {
-  unsigned long long key;
-  unsigned int minid;  // smallest original node id with this key
-  unsigned int pad;
-};
-
+// Table slots are 64-bit words (hash fingerprint << 32 | smallest original
+// id), empty = all ones.  A slot is claimed by CAS and then lowered with
+// atomicMin; different hashes that meet in one slot with the same
+// fingerprint are merged here and separated again by exact verification.
 struct GroupArgs {
   const uint64_t* hash;
   const uint32_t* p2o;
   const uint32_t* o2p;
-  Slot* table;
+  unsigned long long* table;
   uint64_t tmask;   // table capacity - 1
   uint32_t* slot;
   uint32_t* rep;
   uint32_t* err;
 };
 
-__device__ __forceinline__ uint32_t table_home(uint64_t h, uint64_t tmask) {
-  return (uint32_t)(mix64(h ^ 0x9e3779b97f4a7c15ull) & tmask);
+__device__ __forceinline__ uint32_t table_insert(const GroupArgs& g, uint64_t h, uint32_t minid) {
+  const unsigned long long fp = (unsigned long long)(uint32_t)(h >> 32);
+  const unsigned long long v = (fp << 32) | minid;
+  uint32_t s = (uint32_t)(mix64(h) & g.tmask);
+  for (uint64_t t = 0; t <= g.tmask; ++t) {
+    unsigned long long cur = *(volatile unsigned long long*)&g.table[s];
+    if (cur == kEmpty64) {
+      cur = atomicCAS(&g.table[s], (unsigned long long)kEmpty64, v);
+      if (cur == kEmpty64) return s;
+    }
+    if ((cur >> 32) == fp) {
+      if ((uint32_t)cur > minid) atomicMin(&g.table[s], v);
+      return s;
+    }
+    s = (uint32_t)((s + 1) & g.tmask);
+  }
+  atomicOr(g.err, kErrProbe);
+  return 0;
 }
 
-// Lanes of a warp with the same hash combine their smallest original id and
-// let one leader probe the table; the slot is then broadcast.
-__global__ void k_group_insert(GroupArgs g, const uint32_t* list, uint64_t count) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
-    const uint64_t i = base + lane;
-    const bool valid = i < count;
-    const uint32_t p = valid ? (list ? list[i] : (uint32_t)i) : 0u;
-    const uint64_t h = valid ? g.hash[p] : kEmpty64;
-    const uint32_t o = valid ? g.p2o[p] : kNone32;
-    const unsigned peers = __match_any_sync(kFull, h);
-    const int leader = __ffs(peers) - 1;
-    const uint32_t gmin = __reduce_min_sync(peers, o);
-    uint32_t s = 0;
-    if (valid && lane == leader) {
-      s = table_home(h, g.tmask);
-      bool found = false;
-      for (uint64_t t = 0; t <= g.tmask; ++t) {
-        const unsigned long long cur = *(volatile unsigned long long*)&g.table[s].key;
-        if (cur == h) { found = true; break; }
-        if (cur == kEmpty64) {
-          const unsigned long long old = atomicCAS(&g.table[s].key, (unsigned long long)kEmpty64,
-                                                   (unsigned long long)h);
-          if (old == kEmpty64 || old == h) { found = true; break; }
-        }
-        s = (uint32_t)((s + 1) & g.tmask);
-      }
-      if (found) atomicMin(&g.table[s].minid, gmin); else atomicOr(g.err, kErrProbe);
+// A CTA takes 1024 nodes, combines equal hashes in shared memory (smallest
+// original id per hash), then inserts each distinct hash once.
+constexpr int kInsThreads = 256, kInsItems = 4, kInsChunk = kInsThreads * kInsItems, kInsSlots = 2 * kInsChunk;
+
+__global__ void __launch_bounds__(kInsThreads) k_group_insert(GroupArgs g, const uint32_t* list, uint64_t count) {
+  __shared__ unsigned long long skey[kInsSlots];
+  __shared__ unsigned int smin[kInsSlots];
+  __shared__ unsigned int sglob[kInsSlots];
+  for (uint64_t base = (uint64_t)blockIdx.x * kInsChunk; base < count; base += (uint64_t)gridDim.x * kInsChunk) {
+    for (int i = threadIdx.x; i < kInsSlots; i += kInsThreads) {
+      skey[i] = kEmpty64;
+      smin[i] = kNone32;
     }
-    s = __shfl_sync(kFull, s, leader);
-    if (valid) g.slot[p] = s;
+    __syncthreads();
+    uint32_t ls[kInsItems], pp[kInsItems];
+#pragma unroll
+    for (int t = 0; t < kInsItems; ++t) {
+      const uint64_t i = base + threadIdx.x + (uint64_t)t * kInsThreads;
+      ls[t] = kNone32;
+      if (i < count) {
+        const uint32_t p = list ? list[i] : (uint32_t)i;
+        pp[t] = p;
+        const uint64_t h = g.hash[p];
+        uint32_t s = (uint32_t)(mix64(h) & (kInsSlots - 1));
+        for (int q = 0; q < kInsSlots; ++q) {  // at most kInsChunk distinct hashes: always room
+          const unsigned long long cur = atomicCAS(&skey[s], (unsigned long long)kEmpty64, (unsigned long long)h);
+          if (cur == kEmpty64 || cur == h) break;
+          s = (s + 1) & (kInsSlots - 1);
+        }
+        atomicMin(&smin[s], g.p2o[p]);
+        ls[t] = s;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kInsSlots; i += kInsThreads)
+      if (skey[i] != kEmpty64) sglob[i] = table_insert(g, skey[i], smin[i]);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kInsItems; ++t)
+      if (ls[t] != kNone32) g.slot[pp[t]] = sglob[ls[t]];
+    __syncthreads();
   }
 }
 
@@ -825,12 +688,21 @@ struct VerifyArgs {
   unsigned long long* n_long;
 };
 
-constexpr uint32_t kShortSig = 32;
+constexpr uint32_t kShortSig = 8;
 
+// Set equality of two duplicate-free key lists of the same length n <= kShortSig.
 template <typename K>
-__device__ __forceinline__ bool same_keys(const K* a, const K* b, uint32_t n) {
-  for (uint32_t t = 0; t < n; ++t)
-    if (a[t] != b[t]) return false;
+__device__ __forceinline__ bool same_set_short(const K* a, const K* b, uint32_t n) {
+  K bk[kShortSig];
+#pragma unroll
+  for (uint32_t j = 0; j < kShortSig; ++j) bk[j] = j < n ? b[j] : (K)0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const K x = a[i];
+    bool found = false;
+#pragma unroll
+    for (uint32_t j = 0; j < kShortSig; ++j) found |= (j < n && bk[j] == x);
+    if (!found) return false;
+  }
   return true;
 }
 
@@ -845,7 +717,7 @@ __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, 
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t p = list ? list[i] : (uint32_t)i;
-    const uint32_t ro = g.table[g.slot[p]].minid;
+    const uint32_t ro = (uint32_t)g.table[g.slot[p]];
     if (ro == g.p2o[p]) { g.rep[p] = p; continue; }
     const uint32_t r = g.o2p[ro];
     bool eq;
@@ -854,42 +726,58 @@ __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, 
     } else {
       const uint32_t U = v.ucnt[p];
       eq = v.prev[p] == v.prev[r] && U == v.ucnt[r];
-      if (eq && U > kShortSig) {  // long signature: compared by a warp later
+      if (eq && U > kShortSig) {  // long signature: compared by a CTA later
         const unsigned long long q = atomicAdd(v.n_long, 1ull);
         v.long_list[2 * q] = p;
         v.long_list[2 * q + 1] = r;
         continue;
       }
       if (eq) {
-        eq = v.key64 ? same_keys(static_cast<const uint64_t*>(v.sigkey) + v.off[p],
-                                 static_cast<const uint64_t*>(v.sigkey) + v.off[r], U)
-                     : same_keys(static_cast<const uint32_t*>(v.sigkey) + v.off[p],
-                                 static_cast<const uint32_t*>(v.sigkey) + v.off[r], U);
+        eq = v.key64 ? same_set_short(static_cast<const uint64_t*>(v.sigkey) + v.off[p],
+                                      static_cast<const uint64_t*>(v.sigkey) + v.off[r], U)
+                     : same_set_short(static_cast<const uint32_t*>(v.sigkey) + v.off[p],
+                                      static_cast<const uint32_t*>(v.sigkey) + v.off[r], U);
       }
     }
     if (eq) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
   }
 }
 
-// One warp per (node, candidate) pair with a long signature.
+// One CTA per (node, candidate) pair with a long signature: the candidate's
+// keys go into a shared-memory set, chunk by chunk, and the node's keys are
+// looked up; the sets are equal iff every one of the node's keys is found
+// (both lists are duplicate-free and of equal length).
+constexpr int kVerThreads = 256, kVerChunk = 4096;
+
 template <typename K>
-__global__ void k_verify_long(GroupArgs g, VerifyArgs v, uint64_t count) {
-  const int lane = threadIdx.x & 31;
+__host__ __device__ constexpr size_t verify_ws_bytes() { return team_set_bytes<K>(2 * kVerChunk, 0, kVerThreads); }
+
+template <typename K>
+__global__ void __launch_bounds__(kVerThreads) k_verify_long(GroupArgs g, VerifyArgs v, uint64_t count) {
+  extern __shared__ __align__(16) char smem[];
+  TeamSet<K> ts = carve_set<K>(smem, 2 * kVerChunk, 0);
   const K* keys = static_cast<const K*>(v.sigkey);
-  for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; q < count;
-       q += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+  for (uint64_t q = blockIdx.x; q < count; q += gridDim.x) {
     const uint32_t p = v.long_list[2 * q], r = v.long_list[2 * q + 1];
     const uint32_t U = v.ucnt[p];
-    const K* a = keys + v.off[p];
-    const K* b = keys + v.off[r];
-    bool diff = false;
-    for (uint32_t base = 0; base < U && !diff; base += 32) {
-      const uint32_t t = base + lane;
-      diff = __any_sync(kFull, t < U && a[t] != b[t]);
+    const K* ka = keys + v.off[p];
+    const K* kb = keys + v.off[r];
+    uint64_t found = 0;
+    for (uint32_t c0 = 0; c0 < U; c0 += kVerChunk) {
+      const uint32_t cn = min((uint32_t)kVerChunk, U - c0);
+      const int hcap = set_size_for(cn, 2 * kVerChunk);
+      set_clear<kVerThreads>(ts, hcap, threadIdx.x);
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < cn; i += kVerThreads) set_insert(ts, hcap, kb[c0 + i]);
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < U; i += kVerThreads) found += set_find(ts, hcap, ka[i]) ? 1 : 0;
+      __syncthreads();
     }
-    if (lane == 0) {
-      if (!diff) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
+    found = team_sum<kVerThreads>(found, ts.red, threadIdx.x);
+    if (threadIdx.x == 0) {
+      if (found == U) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
     }
+    __syncthreads();
   }
 }
 
@@ -1235,6 +1123,7 @@ template <typename K>
 Status set_smem_attrs_for() {
   cudaError_t e = cudaSuccess;
   const int wb = (int)(warp_ws_bytes<K>() * kWarpsPerBlock), bb = (int)blk_ws_bytes<K>();
+  const int hb = (int)hub_ws_bytes<K>(), vb = (int)verify_ws_bytes<K>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sig_warp<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, wb);
   if (e == cudaSuccess)
@@ -1243,8 +1132,8 @@ Status set_smem_attrs_for() {
     e = cudaFuncSetAttribute(k_sig_block<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sig_block<uint32_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
   return cuda_check(e, "cudaFuncSetAttribute");
 }
 
@@ -1286,7 +1175,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   g.hash = ptr<uint64_t>(s.hash);
   g.p2o = ptr<uint32_t>(s.p2o);
   g.o2p = ptr<uint32_t>(s.o2p);
-  g.table = ptr<Slot>(s.table);
+  g.table = ptr<unsigned long long>(s.table);
   g.tmask = s.tcap - 1;
   g.slot = ptr<uint32_t>(s.slot);
   g.rep = ptr<uint32_t>(s.rep);
@@ -1306,12 +1195,13 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
   {
     TimedScope ts(s, KBISIM_KERNEL_OTHER);
-    cudaMemsetAsync(s.table.p, 0xFF, s.tcap * sizeof(Slot), s.stream);
+    cudaMemsetAsync(s.table.p, 0xFF, s.tcap * 8, s.stream);
     cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
   }
+  const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8);
   {
     TimedScope ts(s, KBISIM_KERNEL_GROUP);
-    k_group_insert<<<gblocks, 256, 0, s.stream>>>(g, nullptr, na);
+    if (na) k_group_insert<<<iblocks, kInsThreads, 0, s.stream>>>(g, nullptr, na);
   }
   if (!(st = launch_check("k_group_insert")).ok()) return st;
   v.out_list = ptr<uint32_t>(s.ulist[0]);
@@ -1325,9 +1215,9 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   if (!(st = read_scalars(s, h)).ok()) return st;
   if (h[6]) {
     TimedScope ts(s, KBISIM_KERNEL_VERIFY);
-    const unsigned b = (unsigned)std::min<uint64_t>(grid_for(h[6] * 32, 256), (uint64_t)sms * 16);
-    if (key64) k_verify_long<uint64_t><<<b, 256, 0, s.stream>>>(g, v, h[6]);
-    else k_verify_long<uint32_t><<<b, 256, 0, s.stream>>>(g, v, h[6]);
+    const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
+    if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g, v, h[6]);
+    else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g, v, h[6]);
     if (!(st = launch_check("k_verify_long")).ok()) return st;
     if (!(st = read_scalars(s, h)).ok()) return st;
   }
@@ -1346,18 +1236,19 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), (uint64_t)sms * 16);
     {
       TimedScope ts(s, KBISIM_KERNEL_OTHER);
-      cudaMemsetAsync(s.table.p, 0xFF, cap * sizeof(Slot), s.stream);
+      cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
       cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
-      k_group_insert<<<b2, 256, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+      k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8),
+                       kInsThreads, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
       k_group_verify<<<b2, 256, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
     }
     if (!(st = launch_check("collision repair")).ok()) return st;
     if (!(st = read_scalars(s, h)).ok()) return st;
     if (h[6]) {
       TimedScope ts(s, KBISIM_KERNEL_OTHER);
-      const unsigned b = (unsigned)std::min<uint64_t>(grid_for(h[6] * 32, 256), (uint64_t)sms * 16);
-      if (key64) k_verify_long<uint64_t><<<b, 256, 0, s.stream>>>(g2, v2, h[6]);
-      else k_verify_long<uint32_t><<<b, 256, 0, s.stream>>>(g2, v2, h[6]);
+      const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
+      if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g2, v2, h[6]);
+      else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g2, v2, h[6]);
       if (!(st = launch_check("k_verify_long")).ok()) return st;
       if (!(st = read_scalars(s, h)).ok()) return st;
     }
@@ -1413,15 +1304,19 @@ Status hub_layout(Store& s) {
     bbase[i + 1] = bbase[i] + (1ull << (bits[i] + s.hub_extra_bits));
   }
   s.n_hub_buckets = bbase[s.n_hub];
+  std::vector<uint32_t> bhub(s.n_hub_buckets);
+  for (uint64_t i = 0; i < s.n_hub; ++i)
+    for (uint64_t b = bbase[i]; b < bbase[i + 1]; ++b) bhub[b] = (uint32_t)i;
   if (!(st = ensure(s, s.hub_bits, s.n_hub * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_bbase, (s.n_hub + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, s.bucket_hub, s.n_hub_buckets * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, std::max<uint64_t>(s.n, 1) * 8))).ok())
     return st;
   if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 8)).ok()) return st;
-  if (!(st = ensure(s, s.hub_ucnt, s.n_hub_buckets * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hub_hpart, s.n_hub_buckets * 8)).ok()) return st;
+  if (!(st = ensure(s, s.hub_acc, s.n_hub * 24)).ok()) return st;
   cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.hub_bbase.p, bbase.data(), (s.n_hub + 1) * 8, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.bucket_hub.p, bhub.data(), s.n_hub_buckets * 4, cudaMemcpyHostToDevice, s.stream);
   return cuda_check(cudaStreamSynchronize(s.stream), "hub layout");
 }
 
@@ -1468,23 +1363,24 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.first = s.class_start[kClassHub];
       h.hub_bits = ptr<uint32_t>(s.hub_bits);
       h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
+      h.bucket_hub = ptr<uint32_t>(s.bucket_hub);
       h.chunks = ptr<uint4>(s.hub_chunks);
       h.extra_bits = s.hub_extra_bits;
       h.hist = ptr<uint64_t>(s.hub_hist);
       h.cursor = ptr<uint64_t>(s.hub_cursor);
-      h.bucnt = ptr<uint32_t>(s.hub_ucnt);
-      h.bhpart = ptr<uint64_t>(s.hub_hpart);
+      h.hub_cur = ptr<unsigned long long>(s.hub_acc);
+      h.hub_term = h.hub_cur + s.n_hub;
+      h.hub_done = reinterpret_cast<unsigned int*>(h.hub_term + s.n_hub);
       h.tmp = s.hub_tmp.p;
-      h.tmp2 = s.hub_tmp2.p;
       {
         TimedScope ts(s, KBISIM_KERNEL_SIG_HUB);
         cudaMemsetAsync(h.hist, 0, s.n_hub_buckets * 8, s.stream);
+        cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
         k_hub_hist<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
         if (!(st = scan64(s, h.hist, s.n_hub_buckets, h.cursor)).ok()) return st;
         k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
         const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 4);
-        k_hub_bucket<K><<<g, kBlockThreads, blk_ws_bytes<K>(), s.stream>>>(h, s.n_hub_buckets, a.seed, a.err);
-        k_hub_compact<K><<<(unsigned)s.n_hub, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_bucket<K><<<g, kBlockThreads, hub_ws_bytes<K>(), s.stream>>>(a, h, s.n_hub_buckets);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
@@ -1508,7 +1404,7 @@ Status ensure_round_scratch(Store& s) {
   if (!(st = ensure(s, s.sigkey, m * 8)).ok()) return st;
   if (!(st = ensure(s, s.ucnt, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.hash, n * 8)).ok()) return st;
-  if (!(st = ensure(s, s.table, cap * sizeof(Slot))).ok()) return st;
+  if (!(st = ensure(s, s.table, cap * 8)).ok()) return st;
   s.tcap = cap;
   if (!(st = ensure(s, s.slot, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.rep, n * 4)).ok()) return st;
@@ -1648,7 +1544,6 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
                                     cudaMemcpyHostToDevice, s.stream), "hub chunks");
     if (!st.ok()) return st;
     if (!(st = ensure(s, s.hub_tmp, s.hub_edges * 8)).ok()) return st;
-    if (!(st = ensure(s, s.hub_tmp2, s.hub_edges * 8)).ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
   }
   return cuda_check(cudaStreamSynchronize(s.stream), "sync");
