@@ -21,15 +21,17 @@ constexpr uint32_t kDead = KBISIM_DELETED;
 
 // Degree classes of the signature kernels.
 constexpr int kSmallMax = 32;      // out-degree <= 32: lanes of one warp per node
-constexpr int kWarpMax = 256;      // 33..256: one warp per node, shared-memory dedupe
-constexpr int kBlockMax = 4096;    // 257..4096: one CTA per node
-constexpr int kBlockThreads = 512; // threads of the CTA-per-node and hub kernels
+constexpr int kWarpMax = 256;      // 33..256: one warp per node, keys in registers
+constexpr int kWarp2Max = 1024;    // 257..1024: one warp per node, keys in chunks
+constexpr int kBlockMax = 4096;    // 1025..4096: one CTA per node
+constexpr int kBlockThreads = 256; // threads of the CTA-per-node kernel
+constexpr int kHubThreads = 512;   // threads of the hub kernels
 constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
 constexpr int kHubChunk = 8192;         // hub edges per partition CTA (16 per thread)
 constexpr int kSmallClasses = 6;        // P = 1, 2, 4, 8, 16, 32
-constexpr int kClassWarp = kSmallClasses, kClassBlock = kSmallClasses + 1,
-              kClassHub = kSmallClasses + 2, kClassDead = kSmallClasses + 3;
-constexpr int kNumClasses = kSmallClasses + 4;  // including deleted nodes (last)
+constexpr int kClassWarp = kSmallClasses, kClassWarp2 = kSmallClasses + 1, kClassBlock = kSmallClasses + 2,
+              kClassHub = kSmallClasses + 3, kClassDead = kSmallClasses + 4;
+constexpr int kNumClasses = kSmallClasses + 5;  // including deleted nodes (last)
 
 // Device error flags (bit set in Store::d_err).
 enum : uint32_t {
@@ -183,6 +185,8 @@ struct Store {
   Buf rep;                     // uint32 [n] internal id of the block head
   Buf ulist[2];                // uint32 [n] unresolved nodes (ping-pong)
   Buf hflag;                   // uint8 [n] head flags in original order
+  Buf member;                  // uint8 [n] block head has other members (this level)
+  Buf alone;                   // uint8 [n] node is alone in its block at the last computed level
   Buf rank_o;                  // uint32 [n] block id of heads, original order
   Buf bsum;                    // uint64 scan block sums
   Buf hub_hist;                // uint64 [buckets]

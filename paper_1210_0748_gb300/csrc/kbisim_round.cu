@@ -137,6 +137,37 @@ __device__ __forceinline__ uint64_t cas(uint64_t* a, uint64_t c, uint64_t v) {
   return atomicCAS((unsigned long long*)a, (unsigned long long)c, (unsigned long long)v);
 }
 
+// L2 cache policies (sm_90+ createpolicy): streamed edge data and signature
+// words are marked evict-first, the gathered identifier array evict-last, so
+// the random gathers of pId_{i-1}[dst] keep hitting L2 while the edge table
+// streams past.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t* a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint8_t* a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(uint32_t* a, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" :: "l"(a), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(uint64_t* a, uint64_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(a), "l"(v), "l"(pol) : "memory");
+}
+
 template <int NT>
 __device__ __forceinline__ void team_sync() {
   if (NT == 32) __syncwarp(); else __syncthreads();
@@ -255,10 +286,17 @@ struct SigArgs {
   uint32_t* err;
 };
 
+struct Policies {
+  uint64_t stream, keep;
+  __device__ __forceinline__ Policies() : stream(policy_evict_first()), keep(policy_evict_last()) {}
+};
+
 template <typename LabelT, typename K>
-__device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e) {
+__device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e, const Policies& pol) {
   const LabelT* lab = static_cast<const LabelT*>(a.lab);
-  return KeyOps<K>::make((uint32_t)lab[e], a.prev[a.dst[e]], a.pbits);
+  const uint32_t l = ld_hint(lab + e, pol.stream);
+  const uint32_t t = ld_hint(a.dst + e, pol.stream);
+  return KeyOps<K>::make(l, ld_hint(a.prev + t, pol.keep), a.pbits);
 }
 
 // Out-degree <= 32: P = 2^c lanes per node, 32/P nodes per warp, R groups of
@@ -289,8 +327,9 @@ __device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first,
       d[r] = (uint32_t)(a.off[first + idx + 1] - off[r]);
     }
   }
+  const Policies pol;
 #pragma unroll
-  for (int r = 0; r < kSmallR; ++r) key[r] = j < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + j) : kE;
+  for (int r = 0; r < kSmallR; ++r) key[r] = j < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + j, pol) : kE;
   K* out = static_cast<K*>(a.sigkey);
 #pragma unroll
   for (int r = 0; r < kSmallR; ++r) {
@@ -300,7 +339,7 @@ __device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first,
     const unsigned peers = __match_any_sync(kFull, key[r]) & gbits;
     const bool keep = valid && (__ffs(peers) - 1) == lane;
     const unsigned bal = __ballot_sync(kFull, keep) & gbits;
-    if (keep) out[off[r] + __popc(bal & below)] = key[r];
+    if (keep) st_hint(out + off[r] + __popc(bal & below), key[r], pol.stream);
     uint64_t t = keep ? elem_term(key[r], a.seed) : 0ull;
 #pragma unroll
     for (int s = P >> 1; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
@@ -337,40 +376,47 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_sig_small(SigArgs a, Small
   }
 }
 
-// Out-degree 33..kWarpMax: one warp per node (8 keys per lane in registers),
-// kWarpMax+1..kBlockMax: one CTA per node (8 keys per thread).  A shared-
-// memory set deduplicates; owners write their key at the next free position.
-constexpr int kWarpItems = kWarpMax / 32;
+// Out-degree 33..kWarpMax and kWarpMax+1..kWarp2Max: one warp per node;
+// kWarp2Max+1..kBlockMax: one CTA per node.  Keys are loaded ITEMS per thread
+// at a time (all loads of a chunk issued before its inserts); a shared-memory
+// set deduplicates, and a key's owner writes it at the next free position.
+constexpr int kTeamItems = 8;
 constexpr int kWarpsPerBlock = 8;
-constexpr int kBlkItems = kBlockMax / kBlockThreads;
+constexpr int kWarps2PerBlock = 4;
 
 template <typename K>
 __host__ __device__ constexpr size_t warp_ws_bytes() { return team_set_bytes<K>(2 * kWarpMax, 0, 32); }
 template <typename K>
+__host__ __device__ constexpr size_t warp2_ws_bytes() { return team_set_bytes<K>(2 * kWarp2Max, 0, 32); }
+template <typename K>
 __host__ __device__ constexpr size_t blk_ws_bytes() { return team_set_bytes<K>(2 * kBlockMax, 0, kBlockThreads); }
 
-template <int NT, int ITEMS, typename LabelT, typename K>
+template <int NT, typename LabelT, typename K>
 __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>& ts, int cap, uint64_t p,
-                                              int rank) {
+                                              int rank, const Policies& pol) {
   const uint64_t off = a.off[p];
   const uint32_t d = (uint32_t)(a.off[p + 1] - off);
-  K keys[ITEMS];
-#pragma unroll
-  for (int t = 0; t < ITEMS; ++t) {
-    const uint32_t i = rank + NT * t;
-    keys[t] = i < d ? edge_key<LabelT, K>(a, off + i) : (K)0;
-  }
-  const int hcap = set_size_for(d, cap);
-  set_clear<NT>(ts, hcap, rank);
-  team_sync<NT>();
   K* out = static_cast<K*>(a.sigkey);
   uint64_t term = 0;
+  const int hcap = set_size_for(d, cap);
+  for (uint32_t base = 0; base < d; base += NT * kTeamItems) {
+    K keys[kTeamItems];
 #pragma unroll
-  for (int t = 0; t < ITEMS; ++t) {
-    if (rank + NT * t < d && set_insert(ts, hcap, keys[t])) {
-      const uint32_t pos = atomicAdd(&ts.sh[0], 1u);
-      out[off + pos] = keys[t];
-      term += elem_term(keys[t], a.seed);
+    for (int t = 0; t < kTeamItems; ++t) {
+      const uint32_t i = base + rank + NT * t;
+      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i, pol) : (K)0;
+    }
+    if (base == 0) {
+      set_clear<NT>(ts, hcap, rank);
+      team_sync<NT>();
+    }
+#pragma unroll
+    for (int t = 0; t < kTeamItems; ++t) {
+      if (base + rank + NT * t < d && set_insert(ts, hcap, keys[t])) {
+        const uint32_t pos = atomicAdd(&ts.sh[0], 1u);
+        st_hint(out + off + pos, keys[t], pol.stream);
+        term += elem_term(keys[t], a.seed);
+      }
     }
   }
   team_sync<NT>();
@@ -383,23 +429,23 @@ __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>
   team_sync<NT>();
 }
 
-template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
+template <int CAP, int WPB, typename LabelT, typename K>
+__global__ void __launch_bounds__(WPB * 32) k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TeamSet<K> ts = carve_set<K>(smem + w * warp_ws_bytes<K>(), 2 * kWarpMax, 0);
-  for (uint64_t idx = (uint64_t)blockIdx.x * kWarpsPerBlock + w; idx < count;
-       idx += (uint64_t)gridDim.x * kWarpsPerBlock)
-    sig_team_node<32, kWarpItems, LabelT, K>(a, ts, 2 * kWarpMax, first + idx, lane);
+  TeamSet<K> ts = carve_set<K>(smem + w * team_set_bytes<K>(2 * CAP, 0, 32), 2 * CAP, 0);
+  const Policies pol;
+  for (uint64_t idx = (uint64_t)blockIdx.x * WPB + w; idx < count; idx += (uint64_t)gridDim.x * WPB)
+    sig_team_node<32, LabelT, K>(a, ts, 2 * CAP, first + idx, lane, pol);
 }
 
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kBlockThreads) k_sig_block(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   TeamSet<K> ts = carve_set<K>(smem, 2 * kBlockMax, 0);
+  const Policies pol;
   for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x)
-    sig_team_node<kBlockThreads, kBlkItems, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x);
+    sig_team_node<kBlockThreads, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x, pol);
 }
 
 // ---- hubs: out-degree > kBlockMax ----------------------------------------
@@ -422,13 +468,13 @@ struct HubArgs {
   void* tmp;
 };
 
-constexpr int kHubItems = kHubChunk / kBlockThreads;  // 16
+constexpr int kHubItems = kHubChunk / kHubThreads;  // 16
 constexpr int kHubSmemBuckets = 4096;
-constexpr int kHubUcap = kBlockMax;                   // distinct keys per bucket
+constexpr int kHubUcap = 4096;                       // distinct keys per bucket
 
 template <typename K>
 __host__ __device__ constexpr size_t hub_ws_bytes() {
-  return team_set_bytes<K>(2 * kHubUcap, kHubUcap, kBlockThreads);
+  return team_set_bytes<K>(2 * kHubUcap, kHubUcap, kHubThreads);
 }
 
 template <typename K>
@@ -437,7 +483,7 @@ __device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
 }
 
 template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h) {
+__global__ void __launch_bounds__(kHubThreads) k_hub_hist(SigArgs a, HubArgs h) {
   __shared__ uint32_t hist[kHubSmemBuckets];
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
@@ -451,14 +497,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   K keys[kHubItems];
+  const Policies pol;
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kBlockThreads;
-    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i) : (K)0;
+    const uint32_t i = threadIdx.x + t * kHubThreads;
+    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i, pol) : (K)0;
   }
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kBlockThreads;
+    const uint32_t i = threadIdx.x + t * kHubThreads;
     if (i < len) {
       const uint32_t b = hub_bucket(keys[t], bits);
       if (in_smem) atomicAdd(&hist[b], 1u); else atomicAdd((unsigned long long*)&g[b], 1ull);
@@ -471,7 +518,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_hist(SigArgs a, HubArgs h
 }
 
 template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArgs h) {
+__global__ void __launch_bounds__(kHubThreads) k_hub_scatter(SigArgs a, HubArgs h) {
   __shared__ uint32_t cnt[kHubSmemBuckets];
   __shared__ unsigned long long base[kHubSmemBuckets];
   const uint4 c = h.chunks[blockIdx.x];
@@ -484,15 +531,16 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
   uint64_t* cur = h.cursor + h.hub_bbase[hub];
   K* tmp = static_cast<K*>(h.tmp);
   K keys[kHubItems];
+  const Policies pol;
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kBlockThreads;
-    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i) : (K)0;
+    const uint32_t i = threadIdx.x + t * kHubThreads;
+    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i, pol) : (K)0;
   }
   if (!in_smem) {
 #pragma unroll
     for (int t = 0; t < kHubItems; ++t) {
-      const uint32_t i = threadIdx.x + t * kBlockThreads;
+      const uint32_t i = threadIdx.x + t * kHubThreads;
       if (i < len) {
         const uint32_t b = hub_bucket(keys[t], bits);
         const uint64_t p = atomicAdd((unsigned long long*)&cur[b], 1ull);
@@ -505,7 +553,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kBlockThreads;
+    const uint32_t i = threadIdx.x + t * kHubThreads;
     if (i < len) atomicAdd(&cnt[hub_bucket(keys[t], bits)], 1u);
   }
   __syncthreads();
@@ -516,7 +564,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kBlockThreads;
+    const uint32_t i = threadIdx.x + t * kHubThreads;
     if (i < len) {
       const uint32_t b = hub_bucket(keys[t], bits);
       const uint32_t p = atomicAdd(&cnt[b], 1u);
@@ -527,7 +575,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_scatter(SigArgs a, HubArg
 
 // One CTA per hub bucket.
 template <typename K>
-__global__ void __launch_bounds__(kBlockThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
+__global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem[];
   TeamSet<K> ts = carve_set<K>(smem, 2 * kHubUcap, kHubUcap);
   __shared__ unsigned long long obase;
@@ -540,18 +588,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_bucket(SigArgs a, HubArgs
     const uint64_t lo = h.hist[b];
     const uint64_t n = h.cursor[b] - lo;  // after the scatter, cursor = end of bucket
     const int hcap = set_size_for(n, 2 * kHubUcap);
-    set_clear<kBlockThreads>(ts, hcap, threadIdx.x);
+    set_clear<kHubThreads>(ts, hcap, threadIdx.x);
     __syncthreads();
-    for (uint64_t base = 0; base < n; base += (uint64_t)kBlockThreads * 8) {
+    for (uint64_t base = 0; base < n; base += (uint64_t)kHubThreads * 8) {
       K keys[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const uint64_t i = base + threadIdx.x + (uint64_t)kBlockThreads * t;
+        const uint64_t i = base + threadIdx.x + (uint64_t)kHubThreads * t;
         keys[t] = i < n ? tmp[lo + i] : (K)0;
       }
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        if (base + threadIdx.x + (uint64_t)kBlockThreads * t < n && set_insert(ts, hcap, keys[t])) {
+        if (base + threadIdx.x + (uint64_t)kHubThreads * t < n && set_insert(ts, hcap, keys[t])) {
           const uint32_t q = atomicAdd(&ts.sh[0], 1u);
           if (q < (uint32_t)kHubUcap) ts.uniq[q] = keys[t]; else ts.sh[2] = 1u;
         }
@@ -568,11 +616,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_bucket(SigArgs a, HubArgs
     __syncthreads();
     const uint64_t off = a.off[p] + obase;
     uint64_t term = 0;
-    for (uint32_t i = threadIdx.x; i < U; i += kBlockThreads) {
+    for (uint32_t i = threadIdx.x; i < U; i += kHubThreads) {
       out[off + i] = ts.uniq[i];
       term += elem_term(ts.uniq[i], a.seed);
     }
-    term = team_sum<kBlockThreads>(term, ts.red, threadIdx.x);
+    term = team_sum<kHubThreads>(term, ts.red, threadIdx.x);
     if (threadIdx.x == 0) {
       atomicAdd(&h.hub_term[hub], (unsigned long long)term);
       __threadfence();
@@ -607,6 +655,7 @@ struct GroupArgs {
   uint32_t* slot;
   uint32_t* rep;
   uint32_t* err;
+  const uint8_t* alone;  // nodes alone in their previous block (may be null): heads, not grouped
 };
 
 __device__ __forceinline__ uint32_t table_insert(const GroupArgs& g, uint64_t h, uint32_t minid) {
@@ -614,11 +663,8 @@ __device__ __forceinline__ uint32_t table_insert(const GroupArgs& g, uint64_t h,
   const unsigned long long v = (fp << 32) | minid;
   uint32_t s = (uint32_t)(mix64(h) & g.tmask);
   for (uint64_t t = 0; t <= g.tmask; ++t) {
-    unsigned long long cur = *(volatile unsigned long long*)&g.table[s];
-    if (cur == kEmpty64) {
-      cur = atomicCAS(&g.table[s], (unsigned long long)kEmpty64, v);
-      if (cur == kEmpty64) return s;
-    }
+    const unsigned long long cur = atomicCAS(&g.table[s], (unsigned long long)kEmpty64, v);
+    if (cur == kEmpty64) return s;
     if ((cur >> 32) == fp) {
       if ((uint32_t)cur > minid) atomicMin(&g.table[s], v);
       return s;
@@ -651,6 +697,7 @@ __global__ void __launch_bounds__(kInsThreads) k_group_insert(GroupArgs g, const
       if (i < count) {
         const uint32_t p = list ? list[i] : (uint32_t)i;
         pp[t] = p;
+        if (g.alone && g.alone[p]) continue;
         const uint64_t h = g.hash[p];
         uint32_t s = (uint32_t)(mix64(h) & (kInsSlots - 1));
         for (int q = 0; q < kInsSlots; ++q) {  // at most kInsChunk distinct hashes: always room
@@ -717,6 +764,7 @@ __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, 
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t p = list ? list[i] : (uint32_t)i;
+    if (g.alone && g.alone[p]) { g.rep[p] = p; continue; }
     const uint32_t ro = (uint32_t)g.table[g.slot[p]];
     if (ro == g.p2o[p]) { g.rep[p] = p; continue; }
     const uint32_t r = g.o2p[ro];
@@ -796,6 +844,8 @@ struct RankArgs {
   const uint32_t* p2o;
   const uint32_t* ucnt;    // may be null (level 0)
   uint8_t* hflag;          // [n] original order
+  uint8_t* member;         // [n] internal order: the head has other members
+  uint8_t* alone;          // [n] internal order: output, node alone in its block
   uint32_t* rank_o;        // [n] original order
   uint32_t* pid;           // output level, internal order
   uint64_t* bsum;          // per tile head count -> exclusive offsets
@@ -807,7 +857,8 @@ __global__ void k_mark_heads(RankArgs r) {
   unsigned int mx = 0;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n_alive;
        p += (uint64_t)gridDim.x * blockDim.x) {
-    if (r.rep[p] == (uint32_t)p) r.hflag[r.p2o[p]] = 1;
+    const uint32_t h = r.rep[p];
+    if (h == (uint32_t)p) r.hflag[r.p2o[p]] = 1; else r.member[h] = 1;
     if (r.ucnt) {
       const uint32_t q = r.ucnt[p];
       keys += q;
@@ -933,8 +984,15 @@ __global__ void __launch_bounds__(kScanThreads) k_flag_rank(const uint8_t* f, ui
 // Every alive node takes its head's block id; deleted nodes get kDead.
 __global__ void k_pid_fill(RankArgs r) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n;
-       p += (uint64_t)gridDim.x * blockDim.x)
-    r.pid[p] = p < r.n_alive ? r.rank_o[r.p2o[r.rep[p]]] : kDead;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    if (p < r.n_alive) {
+      const uint32_t h = r.rep[p];
+      r.pid[p] = r.rank_o[r.p2o[h]];
+      r.alone[p] = (h == (uint32_t)p && !r.member[p]) ? 1 : 0;
+    } else {
+      r.pid[p] = kDead;
+    }
+  }
 }
 
 // Level 0 hash: the node label.
@@ -960,6 +1018,7 @@ __device__ __forceinline__ int degree_class(uint64_t d) {
     return c;
   }
   if (d <= (uint64_t)kWarpMax) return kClassWarp;
+  if (d <= (uint64_t)kWarp2Max) return kClassWarp2;
   if (d <= (uint64_t)kBlockMax) return kClassBlock;
   return kClassHub;
 }
@@ -1119,21 +1178,29 @@ Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
   return launch_check("scan64");
 }
 
+template <typename LabelT, typename K>
+cudaError_t set_smem_attrs_label() {
+  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpsPerBlock, LabelT, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(warp_ws_bytes<K>() * kWarpsPerBlock));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, LabelT, K>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warp2_ws_bytes<K>() * kWarps2PerBlock));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sig_block<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)blk_ws_bytes<K>());
+  return e;
+}
+
 template <typename K>
 Status set_smem_attrs_for() {
-  cudaError_t e = cudaSuccess;
-  const int wb = (int)(warp_ws_bytes<K>() * kWarpsPerBlock), bb = (int)blk_ws_bytes<K>();
-  const int hb = (int)hub_ws_bytes<K>(), vb = (int)verify_ws_bytes<K>();
+  cudaError_t e = set_smem_attrs_label<uint8_t, K>();
+  if (e == cudaSuccess) e = set_smem_attrs_label<uint32_t, K>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, wb);
+    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_ws_bytes<K>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<uint32_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, wb);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_block<uint8_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_block<uint32_t, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
+    e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)verify_ws_bytes<K>());
   return cuda_check(e, "cudaFuncSetAttribute");
 }
 
@@ -1167,7 +1234,7 @@ uint64_t table_capacity(uint64_t n) {
 //  [3] largest signature, [4] collided nodes, [5] unresolved after a repair
 //  pass, [6] long-signature pairs, [7] error flags copy, [15] scan scratch.
 Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint32_t* pid, uint64_t* blocks,
-                      uint64_t* collided, bool with_stats, uint64_t* keys, uint64_t* maxsig) {
+                      uint64_t* collided, bool with_stats, uint64_t* keys, uint64_t* maxsig, bool use_alone) {
   const uint64_t n = s.n, na = s.n_alive;
   Status st;
   unsigned long long* sc = ptr<unsigned long long>(s.d_scalars);
@@ -1180,6 +1247,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   g.slot = ptr<uint32_t>(s.slot);
   g.rep = ptr<uint32_t>(s.rep);
   g.err = ptr<uint32_t>(s.d_err);
+  g.alone = use_alone ? ptr<uint8_t>(s.alone) : nullptr;
   VerifyArgs v;
   v.mode = mode;
   v.key64 = key64 ? 1 : 0;
@@ -1266,6 +1334,8 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   r.p2o = g.p2o;
   r.ucnt = with_stats ? ptr<uint32_t>(s.ucnt) : nullptr;
   r.hflag = ptr<uint8_t>(s.hflag);
+  r.member = ptr<uint8_t>(s.member);
+  r.alone = ptr<uint8_t>(s.alone);
   r.rank_o = ptr<uint32_t>(s.rank_o);
   r.pid = pid;
   r.bsum = ptr<uint64_t>(s.bsum);
@@ -1275,6 +1345,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     TimedScope ts(s, KBISIM_KERNEL_RENUMBER);
     if (n) {
       cudaMemsetAsync(s.hflag.p, 0, n, s.stream);
+      cudaMemsetAsync(s.member.p, 0, n, s.stream);
       k_mark_heads<<<gblocks, 256, 0, s.stream>>>(r);
       k_flag_tilesum<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r.hflag, n, r.bsum);
       k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(r.bsum, tiles, sc);
@@ -1341,15 +1412,26 @@ Status run_signatures(Store& s, const SigArgs& a) {
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
   const uint64_t n_warp = s.class_start[kClassWarp + 1] - s.class_start[kClassWarp];
+  const uint64_t n_warp2 = s.class_start[kClassWarp2 + 1] - s.class_start[kClassWarp2];
   const uint64_t n_block = s.class_start[kClassBlock + 1] - s.class_start[kClassBlock];
   if (n_warp) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                     (uint64_t)sms * 8);
-    k_sig_warp<LabelT, K><<<g, kWarpsPerBlock * 32, warp_ws_bytes<K>() * kWarpsPerBlock, s.stream>>>(
-        a, s.class_start[kClassWarp], n_warp);
+    k_sig_warp<kWarpMax, kWarpsPerBlock, LabelT, K>
+        <<<g, kWarpsPerBlock * 32, warp_ws_bytes<K>() * kWarpsPerBlock, s.stream>>>(a, s.class_start[kClassWarp],
+                                                                                   n_warp);
   }
   if (!(st = launch_check("k_sig_warp")).ok()) return st;
+  if (n_warp2) {
+    TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
+    const unsigned g = (unsigned)std::min<uint64_t>((n_warp2 + kWarps2PerBlock - 1) / kWarps2PerBlock,
+                                                    (uint64_t)sms * 16);
+    k_sig_warp<kWarp2Max, kWarps2PerBlock, LabelT, K>
+        <<<g, kWarps2PerBlock * 32, warp2_ws_bytes<K>() * kWarps2PerBlock, s.stream>>>(
+            a, s.class_start[kClassWarp2], n_warp2);
+  }
+  if (!(st = launch_check("k_sig_warp2")).ok()) return st;
   if (n_block) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>(n_block, (uint64_t)sms * 4);
@@ -1376,11 +1458,11 @@ Status run_signatures(Store& s, const SigArgs& a) {
         TimedScope ts(s, KBISIM_KERNEL_SIG_HUB);
         cudaMemsetAsync(h.hist, 0, s.n_hub_buckets * 8, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
-        k_hub_hist<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_hist<LabelT, K><<<(unsigned)s.n_hub_chunks, kHubThreads, 0, s.stream>>>(a, h);
         if (!(st = scan64(s, h.hist, s.n_hub_buckets, h.cursor)).ok()) return st;
-        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kBlockThreads, 0, s.stream>>>(a, h);
+        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kHubThreads, 0, s.stream>>>(a, h);
         const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 4);
-        k_hub_bucket<K><<<g, kBlockThreads, hub_ws_bytes<K>(), s.stream>>>(a, h, s.n_hub_buckets);
+        k_hub_bucket<K><<<g, kHubThreads, hub_ws_bytes<K>(), s.stream>>>(a, h, s.n_hub_buckets);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
@@ -1411,6 +1493,8 @@ Status ensure_round_scratch(Store& s) {
   if (!(st = ensure(s, s.ulist[0], n * 4)).ok()) return st;
   if (!(st = ensure(s, s.ulist[1], n * 4)).ok()) return st;
   if (!(st = ensure(s, s.hflag, n + 16)).ok()) return st;
+  if (!(st = ensure(s, s.member, n + 16)).ok()) return st;
+  if (!(st = ensure(s, s.alone, n + 16)).ok()) return st;
   if (!(st = ensure(s, s.rank_o, n * 4)).ok()) return st;
   // the long-signature pair list reuses hub_hist: 2 words per alive node
   if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, n * 8))).ok()) return st;
@@ -1564,7 +1648,7 @@ Status compute_level0(Store& s) {
   if (!(st = launch_check("k_label_hash")).ok()) return st;
   uint64_t blocks_out = 0, coll = 0;
   st = group_and_rank(s, 0, nullptr, false, ptr<uint32_t>(s.level[0]), &blocks_out, &coll, false, nullptr,
-                      nullptr);
+                      nullptr, false);
   if (!st.ok()) return st;
   s.counts[0] = blocks_out;
   return Status::Ok();
@@ -1595,7 +1679,9 @@ Status compute_round(Store& s, uint32_t i) {
     st = key64 ? run_signatures<uint32_t, uint64_t>(s, a) : run_signatures<uint32_t, uint32_t>(s, a);
   if (!st.ok()) return st;
   uint64_t blocks = 0, coll = 0, keys = 0, maxsig = 0;
-  st = group_and_rank(s, 1, a.prev, key64, ptr<uint32_t>(s.level[i]), &blocks, &coll, true, &keys, &maxsig);
+  // nodes alone in their block at level i-1 stay alone (Proposition 1): they
+  // are heads of level i without a table lookup
+  st = group_and_rank(s, 1, a.prev, key64, ptr<uint32_t>(s.level[i]), &blocks, &coll, true, &keys, &maxsig, true);
   if (!st.ok()) return st;
   s.counts[i] = blocks;
   kbisim_round_stats rs;
