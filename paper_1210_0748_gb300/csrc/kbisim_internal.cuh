@@ -93,17 +93,20 @@ struct KeyOps<uint64_t> {
   }
 };
 
-// Commutative per-element hash term (summed over the set).
+// Commutative per-element hash term (summed over the set): a multiply by an
+// odd constant and a xor-shift, both invertible, so distinct keys give
+// distinct terms.
 template <typename K>
 __host__ __device__ __forceinline__ uint64_t elem_term(K key, uint64_t seed) {
-  return mix64((uint64_t)key + seed);
+  const uint64_t x = ((uint64_t)key + seed) * 0x9e3779b97f4a7c15ull;
+  return x ^ (x >> 31);
 }
 
 // Hash of a node's signature from its parts.  Never returns kEmpty64.
 __host__ __device__ __forceinline__ uint64_t node_hash(uint64_t term_sum, uint32_t first,
                                                        uint64_t count, uint64_t seed,
                                                        uint64_t mask) {
-  uint64_t h = mix64(term_sum ^ mix64(((uint64_t)first << 32) + count + seed * 3 + 1));
+  uint64_t h = mix64(term_sum + (uint64_t)first * 0xc2b2ae3d27d4eb4full + count * 0x165667b19e3779f9ull + seed);
   h &= mask;
   return h == kEmpty64 ? kEmpty64 - 1 : h;
 }

@@ -161,12 +161,6 @@ __device__ __forceinline__ uint32_t ld_hint(const uint8_t* a, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
   return v;
 }
-__device__ __forceinline__ void st_hint(uint32_t* a, uint32_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" :: "l"(a), "r"(v), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void st_hint(uint64_t* a, uint64_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(a), "l"(v), "l"(pol) : "memory");
-}
 
 template <int NT>
 __device__ __forceinline__ void team_sync() {
@@ -299,27 +293,50 @@ __device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e, const Polici
   return KeyOps<K>::make(l, ld_hint(a.prev + t, pol.keep), a.pbits);
 }
 
-// Out-degree <= 32: P = 2^c lanes per node, 32/P nodes per warp, R groups of
-// nodes per warp with all their loads issued first.  Duplicates are found by
-// one warp-wide match: of the lanes of a node holding the same key, the
-// lowest keeps it; keepers are compacted with a ballot.
+// Out-degree <= 16: one thread per node, its keys in registers (S = 2^c
+// slots, S >= out-degree).  A key is kept unless an earlier slot holds the
+// same key, so no shuffles, sorting or shared memory are needed.
+template <int S, typename LabelT, typename K>
+__device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, const Policies& pol) {
+  const uint64_t off = a.off[p];
+  const uint32_t d = (uint32_t)(a.off[p + 1] - off);
+  K k[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) k[i] = i < (int)d ? edge_key<LabelT, K>(a, off + i, pol) : (K)0;
+  K* out = static_cast<K*>(a.sigkey) + off;
+  uint64_t term = 0;
+  uint32_t U = 0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    bool keep = i < (int)d;
+#pragma unroll
+    for (int j = 0; j < i; ++j) keep = keep && k[j] != k[i];
+    if (keep) {
+      out[U] = k[i];
+      term += elem_term(k[i], a.seed);
+      ++U;
+    }
+  }
+  a.ucnt[p] = U;
+  a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
+}
+
+// Out-degree 17..32: one warp per node (R nodes per warp, loads issued
+// first).  Duplicates are found by one warp-wide match: of the lanes holding
+// the same key the lowest keeps it; keepers are compacted with a ballot.
 constexpr int kSmallR = 4;
 
-template <int P, typename LabelT, typename K>
-__device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first, uint64_t count,
-                                               uint64_t warp_idx) {
-  constexpr int NPW = 32 / P;
-  constexpr K kE = KeyOps<K>::kEmpty;
+template <typename LabelT, typename K>
+__device__ __forceinline__ void sig_warp32_body(const SigArgs& a, uint64_t first, uint64_t count, uint64_t warp_idx,
+                                                const Policies& pol) {
   const int lane = threadIdx.x & 31;
-  const int g = lane / P, j = lane % P;
-  const unsigned gbits = (P == 32) ? kFull : (((1u << (P & 31)) - 1u) << (g * P));
   const unsigned below = (1u << lane) - 1u;
   uint64_t off[kSmallR];
   uint32_t d[kSmallR];
   K key[kSmallR];
 #pragma unroll
   for (int r = 0; r < kSmallR; ++r) {
-    const uint64_t idx = (warp_idx * kSmallR + r) * NPW + g;
+    const uint64_t idx = warp_idx * kSmallR + r;
     off[r] = 0;
     d[r] = 0;
     if (idx < count) {
@@ -327,24 +344,24 @@ __device__ __forceinline__ void sig_small_body(const SigArgs& a, uint64_t first,
       d[r] = (uint32_t)(a.off[first + idx + 1] - off[r]);
     }
   }
-  const Policies pol;
 #pragma unroll
-  for (int r = 0; r < kSmallR; ++r) key[r] = j < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + j, pol) : kE;
+  for (int r = 0; r < kSmallR; ++r)
+    key[r] = lane < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + lane, pol) : KeyOps<K>::kEmpty;
   K* out = static_cast<K*>(a.sigkey);
 #pragma unroll
   for (int r = 0; r < kSmallR; ++r) {
-    const bool valid = j < (int)d[r];
+    const bool valid = lane < (int)d[r];
     // padding lanes sit after the node's real lanes, so a real lane is always
     // the lowest of its peers
-    const unsigned peers = __match_any_sync(kFull, key[r]) & gbits;
+    const unsigned peers = __match_any_sync(kFull, key[r]);
     const bool keep = valid && (__ffs(peers) - 1) == lane;
-    const unsigned bal = __ballot_sync(kFull, keep) & gbits;
-    if (keep) st_hint(out + off[r] + __popc(bal & below), key[r], pol.stream);
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) out[off[r] + __popc(bal & below)] = key[r];
     uint64_t t = keep ? elem_term(key[r], a.seed) : 0ull;
 #pragma unroll
-    for (int s = P >> 1; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
-    const uint64_t idx = (warp_idx * kSmallR + r) * NPW + g;
-    if (j == 0 && idx < count) {
+    for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
+    const uint64_t idx = warp_idx * kSmallR + r;
+    if (lane == 0 && idx < count) {
       const uint64_t p = first + idx;
       const uint32_t U = (uint32_t)__popc(bal);
       a.ucnt[p] = U;
@@ -359,20 +376,29 @@ struct SmallLaunch {
   uint32_t bstart[kSmallClasses + 1];
 };
 
-constexpr int kSmallWarps = 8;
+constexpr int kSmallThreads = 256;
 
+// Classes 0..4 (out-degree <= 16): one node per thread; class 5 (17..32):
+// kSmallR nodes per warp.
 template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kSmallWarps * 32) k_sig_small(SigArgs a, SmallLaunch L) {
+__global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLaunch L) {
   int c = 0;
   while (c + 1 < kSmallClasses && blockIdx.x >= L.bstart[c + 1]) ++c;
-  const uint64_t warp_idx = (uint64_t)(blockIdx.x - L.bstart[c]) * kSmallWarps + (threadIdx.x >> 5);
+  const uint64_t b = blockIdx.x - L.bstart[c];
+  const Policies pol;
+  if (c == kSmallClasses - 1) {
+    sig_warp32_body<LabelT, K>(a, L.start[c], L.count[c], b * (kSmallThreads / 32) + (threadIdx.x >> 5), pol);
+    return;
+  }
+  const uint64_t idx = b * kSmallThreads + threadIdx.x;
+  if (idx >= L.count[c]) return;
+  const uint64_t p = L.start[c] + idx;
   switch (c) {
-    case 0: sig_small_body<1, LabelT, K>(a, L.start[0], L.count[0], warp_idx); break;
-    case 1: sig_small_body<2, LabelT, K>(a, L.start[1], L.count[1], warp_idx); break;
-    case 2: sig_small_body<4, LabelT, K>(a, L.start[2], L.count[2], warp_idx); break;
-    case 3: sig_small_body<8, LabelT, K>(a, L.start[3], L.count[3], warp_idx); break;
-    case 4: sig_small_body<16, LabelT, K>(a, L.start[4], L.count[4], warp_idx); break;
-    default: sig_small_body<32, LabelT, K>(a, L.start[5], L.count[5], warp_idx); break;
+    case 0: sig_thread_node<1, LabelT, K>(a, p, pol); break;
+    case 1: sig_thread_node<2, LabelT, K>(a, p, pol); break;
+    case 2: sig_thread_node<4, LabelT, K>(a, p, pol); break;
+    case 3: sig_thread_node<8, LabelT, K>(a, p, pol); break;
+    default: sig_thread_node<16, LabelT, K>(a, p, pol); break;
   }
 }
 
@@ -380,7 +406,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_sig_small(SigArgs a, Small
 // kWarp2Max+1..kBlockMax: one CTA per node.  Keys are loaded ITEMS per thread
 // at a time (all loads of a chunk issued before its inserts); a shared-memory
 // set deduplicates, and a key's owner writes it at the next free position.
-constexpr int kTeamItems = 8;
+constexpr int kWarpItems = 4, kWarp2Items = 8, kBlkItems = 4;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kWarps2PerBlock = 4;
 
@@ -391,7 +417,7 @@ __host__ __device__ constexpr size_t warp2_ws_bytes() { return team_set_bytes<K>
 template <typename K>
 __host__ __device__ constexpr size_t blk_ws_bytes() { return team_set_bytes<K>(2 * kBlockMax, 0, kBlockThreads); }
 
-template <int NT, typename LabelT, typename K>
+template <int NT, int ITEMS, typename LabelT, typename K>
 __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>& ts, int cap, uint64_t p,
                                               int rank, const Policies& pol) {
   const uint64_t off = a.off[p];
@@ -399,10 +425,10 @@ __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>
   K* out = static_cast<K*>(a.sigkey);
   uint64_t term = 0;
   const int hcap = set_size_for(d, cap);
-  for (uint32_t base = 0; base < d; base += NT * kTeamItems) {
-    K keys[kTeamItems];
+  for (uint32_t base = 0; base < d; base += NT * ITEMS) {
+    K keys[ITEMS];
 #pragma unroll
-    for (int t = 0; t < kTeamItems; ++t) {
+    for (int t = 0; t < ITEMS; ++t) {
       const uint32_t i = base + rank + NT * t;
       keys[t] = i < d ? edge_key<LabelT, K>(a, off + i, pol) : (K)0;
     }
@@ -411,10 +437,10 @@ __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>
       team_sync<NT>();
     }
 #pragma unroll
-    for (int t = 0; t < kTeamItems; ++t) {
+    for (int t = 0; t < ITEMS; ++t) {
       if (base + rank + NT * t < d && set_insert(ts, hcap, keys[t])) {
         const uint32_t pos = atomicAdd(&ts.sh[0], 1u);
-        st_hint(out + off + pos, keys[t], pol.stream);
+        out[off + pos] = keys[t];
         term += elem_term(keys[t], a.seed);
       }
     }
@@ -429,14 +455,14 @@ __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>
   team_sync<NT>();
 }
 
-template <int CAP, int WPB, typename LabelT, typename K>
+template <int CAP, int WPB, int ITEMS, typename LabelT, typename K>
 __global__ void __launch_bounds__(WPB * 32) k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   TeamSet<K> ts = carve_set<K>(smem + w * team_set_bytes<K>(2 * CAP, 0, 32), 2 * CAP, 0);
   const Policies pol;
   for (uint64_t idx = (uint64_t)blockIdx.x * WPB + w; idx < count; idx += (uint64_t)gridDim.x * WPB)
-    sig_team_node<32, LabelT, K>(a, ts, 2 * CAP, first + idx, lane, pol);
+    sig_team_node<32, ITEMS, LabelT, K>(a, ts, 2 * CAP, first + idx, lane, pol);
 }
 
 template <typename LabelT, typename K>
@@ -445,7 +471,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_sig_block(SigArgs a, uint64_t
   TeamSet<K> ts = carve_set<K>(smem, 2 * kBlockMax, 0);
   const Policies pol;
   for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x)
-    sig_team_node<kBlockThreads, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x, pol);
+    sig_team_node<kBlockThreads, kBlkItems, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x, pol);
 }
 
 // ---- hubs: out-degree > kBlockMax ----------------------------------------
@@ -590,15 +616,15 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h
     const int hcap = set_size_for(n, 2 * kHubUcap);
     set_clear<kHubThreads>(ts, hcap, threadIdx.x);
     __syncthreads();
-    for (uint64_t base = 0; base < n; base += (uint64_t)kHubThreads * 8) {
-      K keys[8];
+    for (uint64_t base = 0; base < n; base += (uint64_t)kHubThreads * 4) {
+      K keys[4];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
+      for (int t = 0; t < 4; ++t) {
         const uint64_t i = base + threadIdx.x + (uint64_t)kHubThreads * t;
         keys[t] = i < n ? tmp[lo + i] : (K)0;
       }
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
+      for (int t = 0; t < 4; ++t) {
         if (base + threadIdx.x + (uint64_t)kHubThreads * t < n && set_insert(ts, hcap, keys[t])) {
           const uint32_t q = atomicAdd(&ts.sh[0], 1u);
           if (q < (uint32_t)kHubUcap) ts.uniq[q] = keys[t]; else ts.sh[2] = 1u;
@@ -1083,16 +1109,15 @@ __global__ void k_relabel_nodes(uint64_t n, const uint32_t* p2o, const uint64_t*
   if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
 }
 
-// One warp per internal node: copy its out-edges, relabelling targets.
+// One warp per original node (reads stream in order): copy its out-edges to
+// the segment of its internal id, relabelling targets.
 template <typename TI, typename TO>
-__global__ void k_relabel_edges(uint64_t n, const uint32_t* p2o, const uint32_t* o2p, const uint64_t* off0,
-                                const uint32_t* dst0, const TI* lab0, const uint64_t* off, uint32_t* dst,
-                                TO* lab) {
+__global__ void k_relabel_edges(uint64_t n, const uint32_t* o2p, const uint64_t* off0, const uint32_t* dst0,
+                                const TI* lab0, const uint64_t* off, uint32_t* dst, TO* lab) {
   const int lane = threadIdx.x & 31;
-  for (uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; p < n;
-       p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-    const uint32_t o = p2o[p];
-    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[p];
+  for (uint64_t o = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; o < n;
+       o += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[o2p[o]];
     for (uint64_t i = lane; i < d; i += 32) {
       dst[s1 + i] = o2p[dst0[s0 + i]];
       lab[s1 + i] = (TO)lab0[s0 + i];
@@ -1180,11 +1205,11 @@ Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
 
 template <typename LabelT, typename K>
 cudaError_t set_smem_attrs_label() {
-  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpsPerBlock, LabelT, K>,
+  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpsPerBlock, kWarpItems, LabelT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(warp_ws_bytes<K>() * kWarpsPerBlock));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, LabelT, K>,
+    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, kWarp2Items, LabelT, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warp2_ws_bytes<K>() * kWarps2PerBlock));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sig_block<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1401,14 +1426,14 @@ Status run_signatures(Store& s, const SigArgs& a) {
     L.start[c] = s.class_start[c];
     L.count[c] = s.class_start[c + 1] - s.class_start[c];
     L.bstart[c] = b;
-    const uint64_t per_warp = (uint64_t)(32 >> c) * kSmallR;
-    const uint64_t warps = (L.count[c] + per_warp - 1) / per_warp;
-    b += (uint32_t)((warps + kSmallWarps - 1) / kSmallWarps);
+    const uint64_t per_block =
+        c == kSmallClasses - 1 ? (uint64_t)(kSmallThreads / 32) * kSmallR : (uint64_t)kSmallThreads;
+    b += (uint32_t)((L.count[c] + per_block - 1) / per_block);
   }
   L.bstart[kSmallClasses] = b;
   if (b) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL);
-    k_sig_small<LabelT, K><<<b, kSmallWarps * 32, 0, s.stream>>>(a, L);
+    k_sig_small<LabelT, K><<<b, kSmallThreads, 0, s.stream>>>(a, L);
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
   const uint64_t n_warp = s.class_start[kClassWarp + 1] - s.class_start[kClassWarp];
@@ -1418,7 +1443,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                     (uint64_t)sms * 8);
-    k_sig_warp<kWarpMax, kWarpsPerBlock, LabelT, K>
+    k_sig_warp<kWarpMax, kWarpsPerBlock, kWarpItems, LabelT, K>
         <<<g, kWarpsPerBlock * 32, warp_ws_bytes<K>() * kWarpsPerBlock, s.stream>>>(a, s.class_start[kClassWarp],
                                                                                    n_warp);
   }
@@ -1427,7 +1452,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>((n_warp2 + kWarps2PerBlock - 1) / kWarps2PerBlock,
                                                     (uint64_t)sms * 16);
-    k_sig_warp<kWarp2Max, kWarps2PerBlock, LabelT, K>
+    k_sig_warp<kWarp2Max, kWarps2PerBlock, kWarp2Items, LabelT, K>
         <<<g, kWarps2PerBlock * 32, warp2_ws_bytes<K>() * kWarps2PerBlock, s.stream>>>(
             a, s.class_start[kClassWarp2], n_warp2);
   }
@@ -1564,28 +1589,27 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) { release(s, tcnt); return st; }
   if (n && m) {
     const unsigned ge = (unsigned)std::min<uint64_t>(grid_for(n * 32, 256), (uint64_t)sms * 64);
-    const uint32_t* p2o = ptr<uint32_t>(s.p2o);
     const uint32_t* o2p = ptr<uint32_t>(s.o2p);
     const uint64_t* off = ptr<uint64_t>(s.offsets);
     uint32_t* dst = ptr<uint32_t>(s.dst);
     if (s.label8) {
       uint8_t* lab = ptr<uint8_t>(s.elabel);
       if (lab_bytes == 1)
-        k_relabel_edges<uint8_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+        k_relabel_edges<uint8_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
                                                                     static_cast<const uint8_t*>(lab0), off, dst, lab);
       else if (lab_bytes == 2)
-        k_relabel_edges<uint16_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+        k_relabel_edges<uint16_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
                                                                      static_cast<const uint16_t*>(lab0), off, dst, lab);
       else
-        k_relabel_edges<uint32_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+        k_relabel_edges<uint32_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
                                                                      static_cast<const uint32_t*>(lab0), off, dst, lab);
     } else {
       uint32_t* lab = ptr<uint32_t>(s.elabel);
       if (lab_bytes == 2)
-        k_relabel_edges<uint16_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+        k_relabel_edges<uint16_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
                                                                       static_cast<const uint16_t*>(lab0), off, dst, lab);
       else
-        k_relabel_edges<uint32_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, p2o, o2p, off0, dst0,
+        k_relabel_edges<uint32_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
                                                                       static_cast<const uint32_t*>(lab0), off, dst, lab);
     }
   }
