@@ -20,15 +20,15 @@ constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 constexpr uint32_t kDead = KBISIM_DELETED;
 
 // Degree classes of the signature kernels.
-constexpr int kSmallMax = 32;      // out-degree <= 32: lanes of one warp per node
-constexpr int kWarpMax = 256;      // 33..256: one warp per node, keys in registers
+constexpr int kSmallMax = 64;      // out-degree <= 64: one thread per node, keys in registers
+constexpr int kWarpMax = 256;      // 65..256: one warp per node
 constexpr int kWarp2Max = 1024;    // 257..1024: one warp per node, keys in chunks
 constexpr int kBlockMax = 4096;    // 1025..4096: one CTA per node
 constexpr int kBlockThreads = 256; // threads of the CTA-per-node kernel
 constexpr int kHubThreads = 512;   // threads of the hub kernels
 constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
 constexpr int kHubChunk = 8192;         // hub edges per partition CTA (16 per thread)
-constexpr int kSmallClasses = 6;        // P = 1, 2, 4, 8, 16, 32
+constexpr int kSmallClasses = 8;        // out-degree 0, 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64
 constexpr int kClassWarp = kSmallClasses, kClassWarp2 = kSmallClasses + 1, kClassBlock = kSmallClasses + 2,
               kClassHub = kSmallClasses + 3, kClassDead = kSmallClasses + 4;
 constexpr int kNumClasses = kSmallClasses + 5;  // including deleted nodes (last)

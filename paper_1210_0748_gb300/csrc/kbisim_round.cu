@@ -162,9 +162,17 @@ __device__ __forceinline__ uint32_t ld_hint(const uint8_t* a, uint64_t pol) {
   return v;
 }
 
+// Lanes of a sub-warp team (NT < 32) or the whole warp.
+template <int NT>
+__device__ __forceinline__ unsigned team_mask() {
+  if (NT >= 32) return kFull;
+  const unsigned lane = threadIdx.x & 31;
+  return ((1u << (NT & 31)) - 1u) << (lane & ~(unsigned)(NT - 1));
+}
+
 template <int NT>
 __device__ __forceinline__ void team_sync() {
-  if (NT == 32) __syncwarp(); else __syncthreads();
+  if (NT <= 32) __syncwarp(team_mask<NT>()); else __syncthreads();
 }
 
 // --------------------------------------------------------------------------
@@ -248,12 +256,13 @@ __device__ __forceinline__ bool set_find(const TeamSet<K>& ts, int hcap, K k) {
   return false;
 }
 
-// Sum over the team; valid in every lane for NT == 32, in rank 0 otherwise.
+// Sum over the team; valid in every lane for NT <= 32, in rank 0 otherwise.
 template <int NT>
 __device__ __forceinline__ uint64_t team_sum(uint64_t t, uint64_t* red, int rank) {
+  const unsigned m = team_mask<NT>();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-  if (NT == 32) return t;
+  for (int o = (NT < 32 ? NT : 32) >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(m, t, o);
+  if (NT <= 32) return t;
   if ((rank & 31) == 0) red[rank >> 5] = t;
   __syncthreads();
   uint64_t tot = 0;
@@ -293,7 +302,7 @@ __device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e, const Polici
   return KeyOps<K>::make(l, ld_hint(a.prev + t, pol.keep), a.pbits);
 }
 
-// Out-degree <= 16: one thread per node, its keys in registers (S = 2^c
+// Out-degree <= 32: one thread per node, its keys in registers (S = 2^c
 // slots, S >= out-degree).  A key is kept unless an earlier slot holds the
 // same key, so no shuffles, sorting or shared memory are needed.
 template <int S, typename LabelT, typename K>
@@ -321,55 +330,6 @@ __device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, co
   a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
 }
 
-// Out-degree 17..32: one warp per node (R nodes per warp, loads issued
-// first).  Duplicates are found by one warp-wide match: of the lanes holding
-// the same key the lowest keeps it; keepers are compacted with a ballot.
-constexpr int kSmallR = 4;
-
-template <typename LabelT, typename K>
-__device__ __forceinline__ void sig_warp32_body(const SigArgs& a, uint64_t first, uint64_t count, uint64_t warp_idx,
-                                                const Policies& pol) {
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  uint64_t off[kSmallR];
-  uint32_t d[kSmallR];
-  K key[kSmallR];
-#pragma unroll
-  for (int r = 0; r < kSmallR; ++r) {
-    const uint64_t idx = warp_idx * kSmallR + r;
-    off[r] = 0;
-    d[r] = 0;
-    if (idx < count) {
-      off[r] = a.off[first + idx];
-      d[r] = (uint32_t)(a.off[first + idx + 1] - off[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kSmallR; ++r)
-    key[r] = lane < (int)d[r] ? edge_key<LabelT, K>(a, off[r] + lane, pol) : KeyOps<K>::kEmpty;
-  K* out = static_cast<K*>(a.sigkey);
-#pragma unroll
-  for (int r = 0; r < kSmallR; ++r) {
-    const bool valid = lane < (int)d[r];
-    // padding lanes sit after the node's real lanes, so a real lane is always
-    // the lowest of its peers
-    const unsigned peers = __match_any_sync(kFull, key[r]);
-    const bool keep = valid && (__ffs(peers) - 1) == lane;
-    const unsigned bal = __ballot_sync(kFull, keep);
-    if (keep) out[off[r] + __popc(bal & below)] = key[r];
-    uint64_t t = keep ? elem_term(key[r], a.seed) : 0ull;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(kFull, t, s);
-    const uint64_t idx = warp_idx * kSmallR + r;
-    if (lane == 0 && idx < count) {
-      const uint64_t p = first + idx;
-      const uint32_t U = (uint32_t)__popc(bal);
-      a.ucnt[p] = U;
-      a.hash[p] = node_hash(t, a.prev[p], U, a.seed, a.mask);
-    }
-  }
-}
-
 struct SmallLaunch {
   uint64_t start[kSmallClasses];
   uint64_t count[kSmallClasses];
@@ -378,27 +338,30 @@ struct SmallLaunch {
 
 constexpr int kSmallThreads = 256;
 
-// Classes 0..4 (out-degree <= 16): one node per thread; class 5 (17..32):
-// kSmallR nodes per warp.
-template <typename LabelT, typename K>
+// Class 0 (no out-edges): signature (pId_{i-1}(u), {}); classes 1..7
+// (out-degree 1..64): one node per thread.  Classes FIRST..LAST per launch,
+// so the 64-slot class (most registers) does not limit the occupancy of the
+// others.
+template <int FIRST, int LAST, typename LabelT, typename K>
 __global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLaunch L) {
-  int c = 0;
-  while (c + 1 < kSmallClasses && blockIdx.x >= L.bstart[c + 1]) ++c;
-  const uint64_t b = blockIdx.x - L.bstart[c];
-  const Policies pol;
-  if (c == kSmallClasses - 1) {
-    sig_warp32_body<LabelT, K>(a, L.start[c], L.count[c], b * (kSmallThreads / 32) + (threadIdx.x >> 5), pol);
-    return;
-  }
-  const uint64_t idx = b * kSmallThreads + threadIdx.x;
+  int c = FIRST;
+  while (c < LAST && blockIdx.x >= L.bstart[c + 1]) ++c;
+  const uint64_t idx = (uint64_t)(blockIdx.x - L.bstart[c]) * kSmallThreads + threadIdx.x;
   if (idx >= L.count[c]) return;
   const uint64_t p = L.start[c] + idx;
+  const Policies pol;
   switch (c) {
-    case 0: sig_thread_node<1, LabelT, K>(a, p, pol); break;
-    case 1: sig_thread_node<2, LabelT, K>(a, p, pol); break;
-    case 2: sig_thread_node<4, LabelT, K>(a, p, pol); break;
-    case 3: sig_thread_node<8, LabelT, K>(a, p, pol); break;
-    default: sig_thread_node<16, LabelT, K>(a, p, pol); break;
+    case 0:
+      a.ucnt[p] = 0;
+      a.hash[p] = node_hash(0, a.prev[p], 0, a.seed, a.mask);
+      break;
+    case 1: if (LAST >= 1) sig_thread_node<1, LabelT, K>(a, p, pol); break;
+    case 2: if (LAST >= 2) sig_thread_node<2, LabelT, K>(a, p, pol); break;
+    case 3: if (LAST >= 3) sig_thread_node<4, LabelT, K>(a, p, pol); break;
+    case 4: if (LAST >= 4) sig_thread_node<8, LabelT, K>(a, p, pol); break;
+    case 5: if (LAST >= 5) sig_thread_node<16, LabelT, K>(a, p, pol); break;
+    case 6: if (LAST >= 6) sig_thread_node<32, LabelT, K>(a, p, pol); break;
+    default: if (LAST >= 7) sig_thread_node<64, LabelT, K>(a, p, pol); break;
   }
 }
 
@@ -406,12 +369,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLau
 // kWarp2Max+1..kBlockMax: one CTA per node.  Keys are loaded ITEMS per thread
 // at a time (all loads of a chunk issued before its inserts); a shared-memory
 // set deduplicates, and a key's owner writes it at the next free position.
-constexpr int kWarpItems = 4, kWarp2Items = 8, kBlkItems = 4;
-constexpr int kWarpsPerBlock = 8;
-constexpr int kWarps2PerBlock = 4;
+// 65..256: warps, 8 per CTA; 257..1024: warps, 4 per CTA
+constexpr int kWarpTeam = 32, kWarpTeams = 8, kWarpItems = 4;
+constexpr int kWarp2Items = 8, kWarps2PerBlock = 4;
+constexpr int kBlkItems = 4;
 
 template <typename K>
-__host__ __device__ constexpr size_t warp_ws_bytes() { return team_set_bytes<K>(2 * kWarpMax, 0, 32); }
+__host__ __device__ constexpr size_t warp_ws_bytes() { return team_set_bytes<K>(2 * kWarpMax, 0, kWarpTeam); }
 template <typename K>
 __host__ __device__ constexpr size_t warp2_ws_bytes() { return team_set_bytes<K>(2 * kWarp2Max, 0, 32); }
 template <typename K>
@@ -455,14 +419,15 @@ __device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>
   team_sync<NT>();
 }
 
-template <int CAP, int WPB, int ITEMS, typename LabelT, typename K>
-__global__ void __launch_bounds__(WPB * 32) k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
+// TPB teams of NT lanes (NT <= 32) per CTA, one node per team at a time.
+template <int CAP, int TPB, int NT, int ITEMS, typename LabelT, typename K>
+__global__ void __launch_bounds__(TPB * NT) k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
   extern __shared__ __align__(16) char smem[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TeamSet<K> ts = carve_set<K>(smem + w * team_set_bytes<K>(2 * CAP, 0, 32), 2 * CAP, 0);
+  const int team = threadIdx.x / NT, rank = threadIdx.x % NT;
+  TeamSet<K> ts = carve_set<K>(smem + team * team_set_bytes<K>(2 * CAP, 0, NT), 2 * CAP, 0);
   const Policies pol;
-  for (uint64_t idx = (uint64_t)blockIdx.x * WPB + w; idx < count; idx += (uint64_t)gridDim.x * WPB)
-    sig_team_node<32, ITEMS, LabelT, K>(a, ts, 2 * CAP, first + idx, lane, pol);
+  for (uint64_t idx = (uint64_t)blockIdx.x * TPB + team; idx < count; idx += (uint64_t)gridDim.x * TPB)
+    sig_team_node<NT, ITEMS, LabelT, K>(a, ts, 2 * CAP, first + idx, rank, pol);
 }
 
 template <typename LabelT, typename K>
@@ -1038,9 +1003,10 @@ __global__ void k_unpermute(uint64_t n, const uint32_t* o2p, const uint32_t* lvl
 // Relabelling (once per graph)
 // --------------------------------------------------------------------------
 __device__ __forceinline__ int degree_class(uint64_t d) {
+  if (d == 0) return 0;
   if (d <= (uint64_t)kSmallMax) {
-    int c = 0;
-    while ((1ull << c) < d) ++c;
+    int c = 1;
+    while ((1ull << (c - 1)) < d) ++c;
     return c;
   }
   if (d <= (uint64_t)kWarpMax) return kClassWarp;
@@ -1109,20 +1075,72 @@ __global__ void k_relabel_nodes(uint64_t n, const uint32_t* p2o, const uint64_t*
   if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
 }
 
-// One warp per original node (reads stream in order): copy its out-edges to
-// the segment of its internal id, relabelling targets.
+// Copy out-edges to the segment of their source's internal id, relabelling
+// targets: one thread per original node of out-degree <= 32 (reads stream in
+// order), one warp per larger node.
 template <typename TI, typename TO>
-__global__ void k_relabel_edges(uint64_t n, const uint32_t* o2p, const uint64_t* off0, const uint32_t* dst0,
-                                const TI* lab0, const uint64_t* off, uint32_t* dst, TO* lab) {
+__global__ void k_relabel_edges_small(uint64_t n, const uint32_t* o2p, const uint64_t* off0, const uint32_t* dst0,
+                                      const TI* lab0, const uint64_t* off, uint32_t* dst, TO* lab) {
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t s0 = off0[o], d = off0[o + 1] - s0;
+    if (d > (uint64_t)kSmallMax) continue;
+    const uint64_t s1 = off[o2p[o]];
+    for (uint64_t i = 0; i < d; ++i) {
+      dst[s1 + i] = o2p[dst0[s0 + i]];
+      lab[s1 + i] = (TO)lab0[s0 + i];
+    }
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_relabel_edges_large(uint64_t p_first, uint64_t p_end, const uint32_t* p2o, const uint32_t* o2p,
+                                      const uint64_t* off0, const uint32_t* dst0, const TI* lab0, const uint64_t* off,
+                                      uint32_t* dst, TO* lab) {
   const int lane = threadIdx.x & 31;
-  for (uint64_t o = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; o < n;
-       o += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[o2p[o]];
+  for (uint64_t p = p_first + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); p < p_end;
+       p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t o = p2o[p];
+    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[p];
     for (uint64_t i = lane; i < d; i += 32) {
       dst[s1 + i] = o2p[dst0[s0 + i]];
       lab[s1 + i] = (TO)lab0[s0 + i];
     }
   }
+}
+
+// Hub edges: one CTA per chunk of kHubChunk edges (chunks as in the hub
+// signature kernels: hub index, first edge in the new table, length).
+template <typename TI, typename TO>
+__global__ void k_relabel_edges_hub(uint64_t hub_first, const uint4* chunks, const uint32_t* p2o, const uint32_t* o2p,
+                                    const uint64_t* off0, const uint32_t* dst0, const TI* lab0, const uint64_t* off,
+                                    uint32_t* dst, TO* lab) {
+  const uint4 c = chunks[blockIdx.x];
+  const uint64_t p = hub_first + c.x;
+  const uint64_t begin = ((uint64_t)c.z << 32) | c.y;
+  const uint64_t src = off0[p2o[p]] + (begin - off[p]);
+  for (uint32_t i = threadIdx.x; i < c.w; i += blockDim.x) {
+    dst[begin + i] = o2p[dst0[src + i]];
+    lab[begin + i] = (TO)lab0[src + i];
+  }
+}
+
+template <typename TI, typename TO>
+void relabel_edges(Store& s, const uint64_t* off0, const uint32_t* dst0, const TI* lab0, TO* lab, int sms) {
+  const uint64_t n = s.n;
+  const uint32_t* o2p = ptr<uint32_t>(s.o2p);
+  const uint64_t* off = ptr<uint64_t>(s.offsets);
+  uint32_t* dst = ptr<uint32_t>(s.dst);
+  const unsigned g1 = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
+  k_relabel_edges_small<TI, TO><<<g1, 256, 0, s.stream>>>(n, o2p, off0, dst0, lab0, off, dst, lab);
+  const uint64_t pf = s.class_start[kClassWarp], pe = s.class_start[kClassHub];
+  if (pe > pf) {
+    const unsigned g2 = (unsigned)std::min<uint64_t>(grid_for((pe - pf) * 32, 256), (uint64_t)sms * 32);
+    k_relabel_edges_large<TI, TO><<<g2, 256, 0, s.stream>>>(pf, pe, ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off,
+                                                           dst, lab);
+  }
+  if (s.n_hub_chunks)
+    k_relabel_edges_hub<TI, TO><<<(unsigned)s.n_hub_chunks, 256, 0, s.stream>>>(
+        s.class_start[kClassHub], ptr<uint4>(s.hub_chunks), ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off, dst, lab);
 }
 
 // Exclusive scan of a uint64 array in place, with an optional copy.
@@ -1205,11 +1223,11 @@ Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
 
 template <typename LabelT, typename K>
 cudaError_t set_smem_attrs_label() {
-  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpsPerBlock, kWarpItems, LabelT, K>,
+  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpTeams, kWarpTeam, kWarpItems, LabelT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(warp_ws_bytes<K>() * kWarpsPerBlock));
+                                       (int)(warp_ws_bytes<K>() * kWarpTeams));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, kWarp2Items, LabelT, K>,
+    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, 32, kWarp2Items, LabelT, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warp2_ws_bytes<K>() * kWarps2PerBlock));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sig_block<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1220,6 +1238,7 @@ cudaError_t set_smem_attrs_label() {
 template <typename K>
 Status set_smem_attrs_for() {
   cudaError_t e = set_smem_attrs_label<uint8_t, K>();
+
   if (e == cudaSuccess) e = set_smem_attrs_label<uint32_t, K>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_ws_bytes<K>());
@@ -1425,15 +1444,20 @@ Status run_signatures(Store& s, const SigArgs& a) {
   for (int c = 0; c < kSmallClasses; ++c) {
     L.start[c] = s.class_start[c];
     L.count[c] = s.class_start[c + 1] - s.class_start[c];
+    if (c == kSmallClasses - 1) b = 0;  // the last class runs as its own launch
     L.bstart[c] = b;
-    const uint64_t per_block =
-        c == kSmallClasses - 1 ? (uint64_t)(kSmallThreads / 32) * kSmallR : (uint64_t)kSmallThreads;
-    b += (uint32_t)((L.count[c] + per_block - 1) / per_block);
+    b += (uint32_t)((L.count[c] + kSmallThreads - 1) / kSmallThreads);
   }
   L.bstart[kSmallClasses] = b;
-  if (b) {
+  {
     TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL);
-    k_sig_small<LabelT, K><<<b, kSmallThreads, 0, s.stream>>>(a, L);
+    // classes 0..6
+    uint32_t nb = 0;
+    for (int c = 0; c < kSmallClasses - 1; ++c) nb += (uint32_t)((L.count[c] + kSmallThreads - 1) / kSmallThreads);
+    if (nb) k_sig_small<0, kSmallClasses - 2, LabelT, K><<<nb, kSmallThreads, 0, s.stream>>>(a, L);
+    // class 7 (out-degree 33..64)
+    const uint32_t n7 = (uint32_t)((L.count[kSmallClasses - 1] + kSmallThreads - 1) / kSmallThreads);
+    if (n7) k_sig_small<kSmallClasses - 1, kSmallClasses - 1, LabelT, K><<<n7, kSmallThreads, 0, s.stream>>>(a, L);
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
   const uint64_t n_warp = s.class_start[kClassWarp + 1] - s.class_start[kClassWarp];
@@ -1441,10 +1465,9 @@ Status run_signatures(Store& s, const SigArgs& a) {
   const uint64_t n_block = s.class_start[kClassBlock + 1] - s.class_start[kClassBlock];
   if (n_warp) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                                    (uint64_t)sms * 8);
-    k_sig_warp<kWarpMax, kWarpsPerBlock, kWarpItems, LabelT, K>
-        <<<g, kWarpsPerBlock * 32, warp_ws_bytes<K>() * kWarpsPerBlock, s.stream>>>(a, s.class_start[kClassWarp],
+    const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpTeams - 1) / kWarpTeams, (uint64_t)sms * 8);
+    k_sig_warp<kWarpMax, kWarpTeams, kWarpTeam, kWarpItems, LabelT, K>
+        <<<g, kWarpTeams * kWarpTeam, warp_ws_bytes<K>() * kWarpTeams, s.stream>>>(a, s.class_start[kClassWarp],
                                                                                    n_warp);
   }
   if (!(st = launch_check("k_sig_warp")).ok()) return st;
@@ -1452,7 +1475,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
     const unsigned g = (unsigned)std::min<uint64_t>((n_warp2 + kWarps2PerBlock - 1) / kWarps2PerBlock,
                                                     (uint64_t)sms * 16);
-    k_sig_warp<kWarp2Max, kWarps2PerBlock, kWarp2Items, LabelT, K>
+    k_sig_warp<kWarp2Max, kWarps2PerBlock, 32, kWarp2Items, LabelT, K>
         <<<g, kWarps2PerBlock * 32, warp2_ws_bytes<K>() * kWarps2PerBlock, s.stream>>>(
             a, s.class_start[kClassWarp2], n_warp2);
   }
@@ -1585,38 +1608,11 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   }
   k_relabel_nodes<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), off0, nlab0,
                                             ptr<unsigned long long>(s.offsets), ptr<uint32_t>(s.nlabel));
-  if (!(st = launch_check("relabel nodes")).ok()) { release(s, tcnt); return st; }
-  if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) { release(s, tcnt); return st; }
-  if (n && m) {
-    const unsigned ge = (unsigned)std::min<uint64_t>(grid_for(n * 32, 256), (uint64_t)sms * 64);
-    const uint32_t* o2p = ptr<uint32_t>(s.o2p);
-    const uint64_t* off = ptr<uint64_t>(s.offsets);
-    uint32_t* dst = ptr<uint32_t>(s.dst);
-    if (s.label8) {
-      uint8_t* lab = ptr<uint8_t>(s.elabel);
-      if (lab_bytes == 1)
-        k_relabel_edges<uint8_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
-                                                                    static_cast<const uint8_t*>(lab0), off, dst, lab);
-      else if (lab_bytes == 2)
-        k_relabel_edges<uint16_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
-                                                                     static_cast<const uint16_t*>(lab0), off, dst, lab);
-      else
-        k_relabel_edges<uint32_t, uint8_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
-                                                                     static_cast<const uint32_t*>(lab0), off, dst, lab);
-    } else {
-      uint32_t* lab = ptr<uint32_t>(s.elabel);
-      if (lab_bytes == 2)
-        k_relabel_edges<uint16_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
-                                                                      static_cast<const uint16_t*>(lab0), off, dst, lab);
-      else
-        k_relabel_edges<uint32_t, uint32_t><<<ge, 256, 0, s.stream>>>(n, o2p, off0, dst0,
-                                                                      static_cast<const uint32_t*>(lab0), off, dst, lab);
-    }
-  }
-  st = launch_check("relabel edges");
+  st = launch_check("relabel nodes");
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  release(s, tcnt);
+  release(s, tcnt);  // the class scatter has finished with the tile bases
   if (!st.ok()) return st;
+  if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
   s.hub_extra_bits = 0;
@@ -1654,6 +1650,21 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
     if (!(st = ensure(s, s.hub_tmp, s.hub_edges * 8)).ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
   }
+  if (n && m) {
+    if (s.label8) {
+      uint8_t* lab = ptr<uint8_t>(s.elabel);
+      if (lab_bytes == 1) relabel_edges(s, off0, dst0, static_cast<const uint8_t*>(lab0), lab, sms);
+      else if (lab_bytes == 2) relabel_edges(s, off0, dst0, static_cast<const uint16_t*>(lab0), lab, sms);
+      else relabel_edges(s, off0, dst0, static_cast<const uint32_t*>(lab0), lab, sms);
+    } else {
+      uint32_t* lab = ptr<uint32_t>(s.elabel);
+      if (lab_bytes == 2) relabel_edges(s, off0, dst0, static_cast<const uint16_t*>(lab0), lab, sms);
+      else relabel_edges(s, off0, dst0, static_cast<const uint32_t*>(lab0), lab, sms);
+    }
+  }
+  st = launch_check("relabel edges");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
   return cuda_check(cudaStreamSynchronize(s.stream), "sync");
 }
 
