@@ -134,8 +134,8 @@ typedef struct {
  * Indices are the KBISIM_KERNEL_* values. */
 enum {
   KBISIM_KERNEL_LABEL_GROUP = 0, /* level 0 grouping by node label */
-  KBISIM_KERNEL_SIG_SMALL,       /* signatures of out-degree <= 32 */
-  KBISIM_KERNEL_SIG_MEDIUM,      /* signatures of out-degree 33..4096 */
+  KBISIM_KERNEL_SIG_SMALL,       /* signatures of out-degree <= 64 */
+  KBISIM_KERNEL_SIG_MEDIUM,      /* signatures of out-degree 65..4096 */
   KBISIM_KERNEL_SIG_HUB,         /* signatures of larger out-degree (all hub kernels) */
   KBISIM_KERNEL_GROUP,           /* hash-table grouping of equal signatures */
   KBISIM_KERNEL_VERIFY,          /* exact signature comparison */
