@@ -231,6 +231,26 @@ typedef struct {
 } kbisim_round_stats;
 int kbisim_get_round_stats(const kbisim_handle *h, uint32_t round, kbisim_round_stats *out);
 
+/* Level 0 (the label partition) for callers that cannot allocate device
+ * memory -- e.g. a serving loop whose device memory is fully reserved up front
+ * by another allocator, or code that must not risk the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  The paper has no counterpart:
+ * it is a packaging of the level-0 step of kbisim_refine.
+ * node_label [num_nodes] and pid0 [num_nodes] are device pointers on the
+ * current device; block_count (device pointer, may be NULL) receives the
+ * number of blocks.  pid0 equals kbisim_pids(h, 0, ...) of a handle holding a
+ * graph with these labels.  Work is queued on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and the call returns without waiting.
+ * Scratch lives in a fixed static device array of about 5 MB that every GPU
+ * loading the library holds until exit; hence num_nodes <= 262144, and larger
+ * inputs fail with KBISIM_ERR_INVALID_ARG.  No device memory is allocated or
+ * freed.  All calls share the scratch array: calls that may overlap on the GPU
+ * (other streams, unordered threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address;
+ * make it before any stream capture.  Errors: INVALID_ARG, CUDA. */
+int kbisim_label_partition_noalloc(const uint32_t *node_label, uint64_t num_nodes, uint32_t *pid0,
+                                   uint32_t *block_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,8 @@ SIGNATURES = {
     "kbisim_reset_times": (None, [ctypes.c_void_p]),
     "kbisim_get_round_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
                                               ctypes.POINTER(RoundStats)]),
+    "kbisim_label_partition_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                                      ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -371,3 +373,18 @@ class KBisim:
         st = RoundStats()
         self._check(self._lib.kbisim_get_round_stats(self._h, int(r), ctypes.byref(st)))
         return {f: int(getattr(st, f)) for f, _ in RoundStats._fields_}
+
+
+def label_partition_noalloc(node_label, pid0, block_count=None, stream=None) -> None:
+    """Level 0 of CUDA int32 tensor ``node_label`` into CUDA int32 tensor
+    ``pid0`` (and the block count into a one-element CUDA int32 tensor),
+    without any device allocation: see kbisim_label_partition_noalloc."""
+    lib = load_library()
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    rc = lib.kbisim_label_partition_noalloc(
+        ctypes.c_void_p(node_label.data_ptr()), node_label.numel(), ctypes.c_void_p(pid0.data_ptr()),
+        ctypes.c_void_p(block_count.data_ptr()) if block_count is not None else None,
+        ctypes.c_void_p(stream) if stream else None)
+    if rc != OK:
+        raise KBisimError(rc, "kbisim_label_partition_noalloc failed")
