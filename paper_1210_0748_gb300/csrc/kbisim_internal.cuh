@@ -21,17 +21,24 @@ constexpr uint32_t kDead = KBISIM_DELETED;
 
 // Degree classes of the signature kernels.
 constexpr int kSmallMax = 64;      // out-degree <= 64: one thread per node, keys in registers
-constexpr int kWarpMax = 256;      // 65..256: one warp per node
-constexpr int kWarp2Max = 1024;    // 257..1024: one warp per node, keys in chunks
-constexpr int kBlockMax = 4096;    // 1025..4096: one CTA per node
-constexpr int kBlockThreads = 256; // threads of the CTA-per-node kernel
-constexpr int kHubThreads = 512;   // threads of the hub kernels
+constexpr int kWarpMax = 256;      // class bounds above kSmallMax (65..256, 257..1024, 1025..4096):
+constexpr int kWarp2Max = 1024;    //   node ordering only; all three run as CTA chunks of whole
+constexpr int kBlockMax = 4096;    //   nodes (at most kChunkEdges edges per chunk)
+constexpr int kChunkThreads = 512; // threads of the chunk kernels for out-degree > kWarp2Max and hubs
+constexpr int kSmallChunkThreads = 128;  // threads of the chunk kernel for out-degree kSmallMax+1..kWarp2Max
+constexpr int kChunkItems = 8;     // edges per thread
+constexpr int kChunkEdges = kChunkThreads * kChunkItems;  // 4096 = kBlockMax
+constexpr int kChunkMaxNodes = 64; // nodes per medium chunk (each has > kSmallMax edges)
+constexpr int kHubThreads = 512;   // threads of the hub bucket kernel
 constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
-constexpr int kHubChunk = 8192;         // hub edges per partition CTA (16 per thread)
+constexpr int kHubChunk = kChunkEdges;  // hub edges per chunk CTA
 constexpr int kSmallClasses = 8;        // out-degree 0, 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64
 constexpr int kClassWarp = kSmallClasses, kClassWarp2 = kSmallClasses + 1, kClassBlock = kSmallClasses + 2,
               kClassHub = kSmallClasses + 3, kClassDead = kSmallClasses + 4;
 constexpr int kNumClasses = kSmallClasses + 5;  // including deleted nodes (last)
+static_assert(kChunkEdges >= kBlockMax, "a medium node must fit one chunk");
+static_assert(kChunkEdges / (kSmallMax + 1) < kChunkMaxNodes, "chunk node table too small");
+static_assert(kSmallChunkThreads * kChunkItems >= kWarp2Max, "a node of out-degree <= kWarp2Max must fit one small chunk");
 
 // Device error flags (bit set in Store::d_err).
 enum : uint32_t {
@@ -69,9 +76,9 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // The pair is packed one-to-one -- (label << pbits) | pid with 32-bit words
 // when label and pid fit, (label << 32) | pid with 64-bit words otherwise --
 // and then passed through a bijective mix, so equal words <=> equal elements.
-// A node's signature set is stored as the ascending sequence of these words:
-// a canonical form (equal sets give equal sequences) whose values are spread
-// uniformly, which the bucketed sorts rely on for balance.
+// A node's signature set is stored as its distinct words in arbitrary order
+// (sets are compared as sets); the mix spreads the words uniformly, which the
+// hash sets and the hub buckets rely on for balance.
 template <typename K>
 struct KeyOps;
 
@@ -93,13 +100,17 @@ struct KeyOps<uint64_t> {
   }
 };
 
-// Commutative per-element hash term (summed over the set): a multiply by an
-// odd constant and a xor-shift, both invertible, so distinct keys give
-// distinct terms.
+// Per-element hash term: the SplitMix64 output function of (key + seed).  A
+// set's term sum adds the two 32-bit halves of the terms separately (each
+// modulo 2^32), so kernels can accumulate it with 32-bit adds in any order.
 template <typename K>
 __host__ __device__ __forceinline__ uint64_t elem_term(K key, uint64_t seed) {
-  const uint64_t x = ((uint64_t)key + seed) * 0x9e3779b97f4a7c15ull;
-  return x ^ (x >> 31);
+  return mix64((uint64_t)key + seed);
+}
+
+// Sum of two packed term sums, half by half.
+__host__ __device__ __forceinline__ uint64_t term_add(uint64_t acc, uint64_t t) {
+  return (uint64_t)((uint32_t)acc + (uint32_t)t) | ((uint64_t)((uint32_t)(acc >> 32) + (uint32_t)(t >> 32)) << 32);
 }
 
 // Hash of a node's signature from its parts.  Never returns kEmpty64.
@@ -157,14 +168,20 @@ struct Store {
   // degree classes (internal id ranges)
   uint64_t class_start[kNumClasses + 1] = {0};
   uint64_t n_hub = 0;
+  Buf mid_chunks;              // uint2 (first node, node count): whole medium nodes, two lists
+  uint64_t n_mid_chunks[2] = {0, 0};  // chunks for 128-thread and for 512-thread CTAs
   Buf hub_bits;                // uint32 [n_hub]  log2(bucket count)
   Buf hub_bbase;               // uint64 [n_hub+1] first bucket of each hub
+  Buf hub_cap;                 // uint32 [n_hub]  key words a bucket of this hub can hold
+  Buf hub_tbase;               // uint64 [n_hub]  start of the hub's buckets in hub_tmp
   Buf hub_chunks;              // uint4 [n_chunks] (hub index, begin lo, begin hi, length)
   uint64_t n_hub_chunks = 0;
+  uint64_t hub_tmp_words = 0;  // key words of all hub buckets
   uint64_t n_hub_buckets = 0;
   uint64_t hub_edges = 0;
   uint32_t hub_extra_bits = 0; // grows if a bucket overflows
   std::vector<uint32_t> h_hub_degbits;
+  std::vector<uint64_t> h_hub_deg;
 
   // levels (all kept: history for extend / maintenance), internal order
   std::vector<Buf> level;
@@ -179,7 +196,7 @@ struct Store {
   std::vector<kbisim_round_stats> stats;  // index r-1 for round r
 
   // round scratch
-  Buf sigkey;                  // key words [m]: sorted distinct keys per node at its CSR offset
+  Buf sigkey;                  // key words [m]: distinct keys per node (any order) at its CSR offset
   Buf ucnt;                    // uint32 [n]
   Buf hash;                    // uint64 [n]
   Buf table;                   // 64-bit slots (hash fingerprint, smallest original id)
@@ -192,11 +209,11 @@ struct Store {
   Buf alone;                   // uint8 [n] node is alone in its block at the last computed level
   Buf rank_o;                  // uint32 [n] block id of heads, original order
   Buf bsum;                    // uint64 scan block sums
-  Buf hub_hist;                // uint64 [buckets]
-  Buf hub_cursor;              // uint64 [buckets]
+  Buf long_pairs;              // uint32 [2n] (node, candidate) pairs with long signatures
+  Buf hub_cursor;              // uint32 [buckets] key words appended to each bucket
   Buf bucket_hub;              // uint32 [buckets] hub of each bucket
   Buf hub_acc;                 // per hub: keys written, term sum (uint64), buckets done (uint32)
-  Buf hub_tmp;                 // key words [hub_edges]
+  Buf hub_tmp;                 // key words [hub_tmp_words]: fixed-capacity hub buckets
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars

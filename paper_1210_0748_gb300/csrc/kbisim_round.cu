@@ -151,14 +151,20 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ uint32_t ld_hint(const uint32_t* a, uint64_t pol) {
+// Loads with an L2 policy, predicated (0 when p is false, no access), so
+// loads of several items are issued back to back without a branch between them.
+__device__ __forceinline__ uint32_t ld_hint_if(const uint32_t* a, uint64_t pol, bool p) {
   uint32_t v;
-  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tmov.u32 %0, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;\n\t}"
+      : "=r"(v) : "l"(a), "l"(pol), "r"((uint32_t)p));
   return v;
 }
-__device__ __forceinline__ uint32_t ld_hint(const uint8_t* a, uint64_t pol) {
+__device__ __forceinline__ uint32_t ld_hint_if(const uint8_t* a, uint64_t pol, bool p) {
   uint32_t v;
-  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tmov.u32 %0, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;\n\t}"
+      : "=r"(v) : "l"(a), "l"(pol), "r"((uint32_t)p));
   return v;
 }
 
@@ -188,7 +194,7 @@ struct TeamSet {
   K* set;          // [hcap]
   K* uniq;         // [ucap] distinct keys (hub buckets only)
   uint32_t* sh;    // [4]: distinct count, saw-the-empty-key flag, overflow flag, spare
-  uint64_t* red;   // [NT/32] reduction scratch
+  uint32_t* red;   // [NT/32] reduction scratch
 };
 
 template <typename K>
@@ -202,7 +208,7 @@ __device__ __forceinline__ TeamSet<K> carve_set(char* base, int hcap, int ucap) 
   t.set = reinterpret_cast<K*>(base);
   t.uniq = t.set + hcap;
   t.sh = reinterpret_cast<uint32_t*>(t.uniq + ucap);
-  t.red = reinterpret_cast<uint64_t*>(t.sh + 4);
+  t.red = t.sh + 4;
   return t;
 }
 
@@ -256,16 +262,16 @@ __device__ __forceinline__ bool set_find(const TeamSet<K>& ts, int hcap, K k) {
   return false;
 }
 
-// Sum over the team; valid in every lane for NT <= 32, in rank 0 otherwise.
+// Sum over the team (modulo 2^32); valid in every lane for NT <= 32, in rank
+// 0 otherwise.
 template <int NT>
-__device__ __forceinline__ uint64_t team_sum(uint64_t t, uint64_t* red, int rank) {
+__device__ __forceinline__ uint32_t team_sum(uint32_t t, uint32_t* red, int rank) {
   const unsigned m = team_mask<NT>();
-#pragma unroll
-  for (int o = (NT < 32 ? NT : 32) >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(m, t, o);
+  t = __reduce_add_sync(m, t);
   if (NT <= 32) return t;
   if ((rank & 31) == 0) red[rank >> 5] = t;
   __syncthreads();
-  uint64_t tot = 0;
+  uint32_t tot = 0;
   if (rank == 0)
     for (int w = 0; w < NT / 32; ++w) tot += red[w];
   __syncthreads();
@@ -289,20 +295,45 @@ struct SigArgs {
   uint32_t* err;
 };
 
+constexpr int kLoadBatch = 16;  // edges whose loads a thread-per-node kernel issues together
+
 struct Policies {
   uint64_t stream, keep;
   __device__ __forceinline__ Policies() : stream(policy_evict_first()), keep(policy_evict_last()) {}
 };
 
-template <typename LabelT, typename K>
-__device__ __forceinline__ K edge_key(const SigArgs& a, uint64_t e, const Policies& pol) {
+// Keys of N edges base + i * stride into key[O + i] (i < N; an edge counts
+// while it is below end): labels and targets first, then the identifier
+// gathers, then the packing, so all loads of the batch are in flight together.
+template <int N, int O, int M, typename LabelT, typename K>
+__device__ __forceinline__ void edge_keys(const SigArgs& a, uint64_t base, uint32_t stride, uint64_t end,
+                                          const Policies& pol, K (&key)[M]) {
+  static_assert(O + N <= M, "batch out of range");
   const LabelT* lab = static_cast<const LabelT*>(a.lab);
-  const uint32_t l = ld_hint(lab + e, pol.stream);
-  const uint32_t t = ld_hint(a.dst + e, pol.stream);
-  return KeyOps<K>::make(l, ld_hint(a.prev + t, pol.keep), a.pbits);
+  uint32_t l[N], t[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint64_t e = base + (uint64_t)i * stride;
+    l[i] = ld_hint_if(lab + e, pol.stream, e < end);
+    t[i] = ld_hint_if(a.dst + e, pol.stream, e < end);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) t[i] = ld_hint_if(a.prev + t[i], pol.keep, base + (uint64_t)i * stride < end);
+#pragma unroll
+  for (int i = 0; i < N; ++i) key[O + i] = KeyOps<K>::make(l[i], t[i], a.pbits);
 }
 
-// Out-degree <= 32: one thread per node, its keys in registers (S = 2^c
+// Keys of edges off .. off + S (those below end) in batches of B.
+template <int O, int B, int S, typename LabelT, typename K>
+__device__ __forceinline__ void edge_key_batches(const SigArgs& a, uint64_t off, uint64_t end, const Policies& pol,
+                                                 K (&key)[S]) {
+  if constexpr (O < S) {
+    edge_keys<B, O, S, LabelT, K>(a, off + O, 1u, end, pol, key);
+    edge_key_batches<O + B, B, S, LabelT, K>(a, off, end, pol, key);
+  }
+}
+
+// Out-degree <= 64: one thread per node, its keys in registers (S = 2^c
 // slots, S >= out-degree).  A key is kept unless an earlier slot holds the
 // same key, so no shuffles, sorting or shared memory are needed.
 template <int S, typename LabelT, typename K>
@@ -310,8 +341,7 @@ __device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, co
   const uint64_t off = a.off[p];
   const uint32_t d = (uint32_t)(a.off[p + 1] - off);
   K k[S];
-#pragma unroll
-  for (int i = 0; i < S; ++i) k[i] = i < (int)d ? edge_key<LabelT, K>(a, off + i, pol) : (K)0;
+  edge_key_batches<0, (S < kLoadBatch ? S : kLoadBatch), S, LabelT, K>(a, off, off + d, pol, k);
   K* out = static_cast<K*>(a.sigkey) + off;
   uint64_t term = 0;
   uint32_t U = 0;
@@ -322,7 +352,7 @@ __device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, co
     for (int j = 0; j < i; ++j) keep = keep && k[j] != k[i];
     if (keep) {
       out[U] = k[i];
-      term += elem_term(k[i], a.seed);
+      term = term_add(term, elem_term(k[i], a.seed));
       ++U;
     }
   }
@@ -365,103 +395,205 @@ __global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLau
   }
 }
 
-// Out-degree 33..kWarpMax and kWarpMax+1..kWarp2Max: one warp per node;
-// kWarp2Max+1..kBlockMax: one CTA per node.  Keys are loaded ITEMS per thread
-// at a time (all loads of a chunk issued before its inserts); a shared-memory
-// set deduplicates, and a key's owner writes it at the next free position.
-// 65..256: warps, 8 per CTA; 257..1024: warps, 4 per CTA
-constexpr int kWarpTeam = 32, kWarpTeams = 8, kWarpItems = 4;
-constexpr int kWarp2Items = 8, kWarps2PerBlock = 4;
-constexpr int kBlkItems = 4;
+// ---- out-degree 65..4096: CTA chunks of whole nodes -----------------------
+// A chunk is a run of consecutive medium nodes with at most kChunkEdges edges
+// in all; their edges are contiguous in the relabelled CSR.  One CTA:
+//  1. loads the chunk's edges coalesced, kChunkItems per thread, and makes
+//     their keys (every load is in flight before the first key is used);
+//  2. inserts each key into its node's region of a shared-memory hash set
+//     (node j owns slots [2 o_j, 2 o_{j+1}), o_j its first edge in the chunk,
+//     so a region is at most half full).  The lane whose insert puts a key
+//     into the set writes it out at once: the 32 consecutive edges of a warp
+//     belong to at most two nodes, so each node's output position is claimed
+//     once per warp step;
+//  3. sums the hash terms of each node's distinct keys, just written, with one
+//     warp per node, and writes the node's distinct-key count and hash.
+// The key equal to the empty-slot marker is kept as a per-node flag.
 
-template <typename K>
-__host__ __device__ constexpr size_t warp_ws_bytes() { return team_set_bytes<K>(2 * kWarpMax, 0, kWarpTeam); }
-template <typename K>
-__host__ __device__ constexpr size_t warp2_ws_bytes() { return team_set_bytes<K>(2 * kWarp2Max, 0, 32); }
-template <typename K>
-__host__ __device__ constexpr size_t blk_ws_bytes() { return team_set_bytes<K>(2 * kBlockMax, 0, kBlockThreads); }
+// A chunk CTA of NT threads takes up to NT * kChunkItems edges.
+template <int NT>
+struct ChunkShape {
+  static constexpr int kEdges = NT * kChunkItems;
+  static constexpr int kSlots = 2 * kEdges;
+  static constexpr int kMaxNodes = kEdges / (kSmallMax + 1) + 1;  // nodes of out-degree > kSmallMax
+};
 
-template <int NT, int ITEMS, typename LabelT, typename K>
-__device__ __forceinline__ void sig_team_node(const SigArgs& a, const TeamSet<K>& ts, int cap, uint64_t p,
-                                              int rank, const Policies& pol) {
-  const uint64_t off = a.off[p];
-  const uint32_t d = (uint32_t)(a.off[p + 1] - off);
-  K* out = static_cast<K*>(a.sigkey);
-  uint64_t term = 0;
-  const int hcap = set_size_for(d, cap);
-  for (uint32_t base = 0; base < d; base += NT * ITEMS) {
-    K keys[ITEMS];
-#pragma unroll
-    for (int t = 0; t < ITEMS; ++t) {
-      const uint32_t i = base + rank + NT * t;
-      keys[t] = i < d ? edge_key<LabelT, K>(a, off + i, pol) : (K)0;
-    }
-    if (base == 0) {
-      set_clear<NT>(ts, hcap, rank);
-      team_sync<NT>();
-    }
-#pragma unroll
-    for (int t = 0; t < ITEMS; ++t) {
-      if (base + rank + NT * t < d && set_insert(ts, hcap, keys[t])) {
-        const uint32_t pos = atomicAdd(&ts.sh[0], 1u);
-        out[off + pos] = keys[t];
-        term += elem_term(keys[t], a.seed);
-      }
-    }
-  }
-  team_sync<NT>();
-  const uint32_t U = ts.sh[0];
-  term = team_sum<NT>(term, ts.red, rank);
-  if (rank == 0) {
-    a.ucnt[p] = U;
-    a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
-  }
-  team_sync<NT>();
+template <typename K, int NT>
+struct ChunkSmem {
+  K slot[ChunkShape<NT>::kSlots];
+  uint32_t off[ChunkShape<NT>::kMaxNodes + 1];  // node starts relative to the chunk's first edge
+  uint32_t cnt[ChunkShape<NT>::kMaxNodes];      // distinct keys written per node
+  uint32_t empty[ChunkShape<NT>::kMaxNodes];    // the node's key equal to KeyOps<K>::kEmpty was seen
+};
+
+__device__ __forceinline__ uint32_t key_h32(uint32_t k) { return k; }
+__device__ __forceinline__ uint32_t key_h32(uint64_t k) { return (uint32_t)(k >> 32) ^ (uint32_t)k; }
+
+// Home slot of k in a region of rs slots: monotone in the key's top bits.
+template <typename K>
+__device__ __forceinline__ uint32_t region_home(K k, uint32_t rs) {
+  return (uint32_t)(((uint64_t)key_h32(k) * rs) >> 32);
 }
 
-// TPB teams of NT lanes (NT <= 32) per CTA, one node per team at a time.
-template <int CAP, int TPB, int NT, int ITEMS, typename LabelT, typename K>
-__global__ void __launch_bounds__(TPB * NT) k_sig_warp(SigArgs a, uint64_t first, uint64_t count) {
-  extern __shared__ __align__(16) char smem[];
-  const int team = threadIdx.x / NT, rank = threadIdx.x % NT;
-  TeamSet<K> ts = carve_set<K>(smem + team * team_set_bytes<K>(2 * CAP, 0, NT), 2 * CAP, 0);
-  const Policies pol;
-  for (uint64_t idx = (uint64_t)blockIdx.x * TPB + team; idx < count; idx += (uint64_t)gridDim.x * TPB)
-    sig_team_node<NT, ITEMS, LabelT, K>(a, ts, 2 * CAP, first + idx, rank, pol);
+// Shared-memory accesses by shared-window address (no generic addressing).
+__device__ __forceinline__ uint32_t lds_volatile(uint32_t a, uint32_t) {
+  uint32_t v;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint64_t lds_volatile(uint32_t a, uint64_t) {
+  uint64_t v;
+  asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t atoms_cas(uint32_t a, uint32_t c, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "r"(a), "r"(c), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint64_t atoms_cas(uint32_t a, uint64_t c, uint64_t v) {
+  uint64_t r;
+  asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(r) : "r"(a), "l"(c), "l"(v) : "memory");
+  return r;
 }
 
-template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kBlockThreads) k_sig_block(SigArgs a, uint64_t first, uint64_t count) {
-  extern __shared__ __align__(16) char smem[];
-  TeamSet<K> ts = carve_set<K>(smem, 2 * kBlockMax, 0);
+// Insert k (!= kEmpty) into the set held in slots [rb, rb + rs) of the slot
+// array at shared-window address `base`; true iff this call put it there.
+// The region has more slots than keys are ever inserted into it, and probing
+// is bounded by its size.
+template <typename K>
+__device__ __forceinline__ bool region_insert(uint32_t base, uint32_t rb, uint32_t rs, K k) {
+  uint32_t s = rb + region_home(k, rs);
+  const uint32_t re = rb + rs;
+  for (uint32_t t = 0; t < rs; ++t) {
+    const uint32_t a = base + s * (uint32_t)sizeof(K);
+    K cur = lds_volatile(a, K());
+    if (cur == k) return false;
+    if (cur == KeyOps<K>::kEmpty) {
+      cur = atoms_cas(a, KeyOps<K>::kEmpty, k);
+      if (cur == KeyOps<K>::kEmpty) return true;
+      if (cur == k) return false;
+    }
+    if (++s == re) s = rb;
+  }
+  return false;
+}
+
+template <typename K, int NT>
+__device__ __forceinline__ void chunk_clear(ChunkSmem<K, NT>& sm, uint32_t slots) {
+  uint4* s4 = reinterpret_cast<uint4*>(sm.slot);
+  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  for (uint32_t i = threadIdx.x; i < slots * sizeof(K) / 16; i += NT) s4[i] = ones;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)ChunkShape<NT>::kMaxNodes; i += NT) {
+    sm.cnt[i] = 0;
+    sm.empty[i] = 0;
+  }
+}
+
+template <int NT, typename LabelT, typename K>
+__device__ __forceinline__ void chunk_keys(const SigArgs& a, uint64_t ebase, uint32_t E, K (&key)[kChunkItems]) {
   const Policies pol;
-  for (uint64_t idx = blockIdx.x; idx < count; idx += gridDim.x)
-    sig_team_node<kBlockThreads, kBlkItems, LabelT, K>(a, ts, 2 * kBlockMax, first + idx, threadIdx.x, pol);
+  edge_keys<kChunkItems, 0, kChunkItems, LabelT, K>(a, ebase + threadIdx.x, NT, ebase + E, pol, key);
+}
+
+// Lanes below `lane`.
+__device__ __forceinline__ unsigned lanes_below(uint32_t lane) { return (1u << lane) - 1u; }
+
+template <int NT, typename LabelT, typename K>
+__global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks) {
+  extern __shared__ __align__(16) char smem_raw[];
+  ChunkSmem<K, NT>& sm = *reinterpret_cast<ChunkSmem<K, NT>*>(smem_raw);
+  const uint2 c = chunks[blockIdx.x];
+  const uint64_t first = c.x;
+  const uint32_t nn = c.y;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint64_t ebase = a.off[first];
+  const uint32_t E = (uint32_t)(a.off[first + nn] - ebase);
+  for (uint32_t i = tid; i <= nn; i += NT) sm.off[i] = (uint32_t)(a.off[first + i] - ebase);
+  chunk_clear(sm, (2 * E + 3) & ~3u);
+  __syncthreads();
+  K key[kChunkItems];
+  chunk_keys<NT, LabelT, K>(a, ebase, E, key);
+  K* out = static_cast<K*>(a.sigkey) + ebase;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.slot);
+  uint32_t j = 0;
+#pragma unroll
+  for (int t = 0; t < kChunkItems; ++t) {
+    const uint32_t e = tid + t * NT;
+    bool fresh = false;
+    if (e < E) {
+      while (sm.off[j + 1] <= e) ++j;
+      fresh = key[t] == KeyOps<K>::kEmpty
+                  ? atomicExch(&sm.empty[j], 1u) == 0u
+                  : region_insert(sbase, 2 * sm.off[j], 2 * (sm.off[j + 1] - sm.off[j]), key[t]);
+    }
+    const unsigned fm = __ballot_sync(kFull, fresh);
+    if (fm == 0u) continue;
+    // valid lanes are a prefix of the warp and span nodes jA and jA + 1
+    const uint32_t jA = __shfl_sync(kFull, j, 0);
+    const bool inA = j == jA;
+    const unsigned fa = fm & __ballot_sync(kFull, inA), fb = fm & ~fa;
+    uint32_t base = 0;
+    if (lane == 0 && fa) base = atomicAdd(&sm.cnt[jA], (uint32_t)__popc(fa));
+    if (lane == 31 && fb) base = atomicAdd(&sm.cnt[jA + 1], (uint32_t)__popc(fb));
+    const uint32_t bA = __shfl_sync(kFull, base, 0), bB = __shfl_sync(kFull, base, 31);
+    if (fresh)
+      out[sm.off[j] + (inA ? bA + __popc(fa & lanes_below(lane)) : bB + __popc(fb & lanes_below(lane)))] = key[t];
+  }
+  __syncthreads();
+  // hash terms: one warp per node over its distinct keys just written
+  for (uint32_t i = tid >> 5; i < nn; i += NT / 32) {
+    const uint32_t U = sm.cnt[i];
+    const K* ko = out + sm.off[i];
+    uint32_t lo = 0, hi = 0;
+    for (uint32_t q = lane; q < U; q += 32) {
+      const uint64_t tm = elem_term(ko[q], a.seed);
+      lo += (uint32_t)tm;
+      hi += (uint32_t)(tm >> 32);
+    }
+    lo = __reduce_add_sync(kFull, lo);
+    hi = __reduce_add_sync(kFull, hi);
+    if (lane == 0) {
+      const uint64_t p = first + i;
+      a.ucnt[p] = U;
+      a.hash[p] = node_hash(((uint64_t)hi << 32) | lo, a.prev[p], U, a.seed, a.mask);
+    }
+  }
 }
 
 // ---- hubs: out-degree > kBlockMax ----------------------------------------
-// Partition each hub's keys by their top bits into buckets expected to hold
-// about kHubBucketTarget distinct keys; one CTA deduplicates a bucket in
-// shared memory and appends its distinct keys at the hub's CSR offset.  The
-// last bucket of a hub to finish writes the hub's count and hash.
+// Pass 1 (k_hub_chunk): a CTA takes kHubChunk edges of one hub, deduplicates
+// their keys in shared memory as above (one region), listing each distinct
+// key once, and appends the list to the hub's buckets; the bucket of a key is
+// its top bits, so equal keys from different chunks meet in one bucket.
+// Buckets have a fixed capacity: an append past it raises kErrHubOverflow and
+// the host repeats the hub passes with more buckets.  Pass 2 (k_hub_bucket):
+// one CTA per bucket deduplicates across chunks and appends the bucket's
+// distinct keys at the hub's CSR offset; the last bucket of a hub to finish
+// writes its count and hash.
 struct HubArgs {
   uint64_t first;           // internal id of hub 0
   const uint32_t* hub_bits;
   const uint64_t* hub_bbase;
+  const uint32_t* hub_cap;
+  const uint64_t* hub_tbase;
   const uint32_t* bucket_hub;
   const uint4* chunks;
   uint32_t extra_bits;
-  uint64_t* hist;     // per bucket: count, then (after the scan) start
-  uint64_t* cursor;   // per bucket: fill cursor, then end
+  uint32_t* cursor;              // per bucket: key words appended
   unsigned long long* hub_cur;   // per hub: distinct keys written
-  unsigned long long* hub_term;  // per hub: term sum
+  uint32_t* hub_term;            // per hub: term sum halves (low, high)
   unsigned int* hub_done;        // per hub: buckets finished
   void* tmp;
 };
 
-constexpr int kHubItems = kHubChunk / kHubThreads;  // 16
-constexpr int kHubSmemBuckets = 4096;
-constexpr int kHubUcap = 4096;                       // distinct keys per bucket
+constexpr int kHubUcap = 4096;         // key words per bucket at most
+constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
+
+template <typename K>
+__host__ __device__ constexpr size_t hub_chunk_smem() {
+  return sizeof(ChunkSmem<K, kChunkThreads>) + (size_t)kHubChunk * sizeof(K) + 2 * kHubSmemBuckets * sizeof(uint32_t);
+}
 
 template <typename K>
 __host__ __device__ constexpr size_t hub_ws_bytes() {
@@ -474,130 +606,98 @@ __device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
 }
 
 template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kHubThreads) k_hub_hist(SigArgs a, HubArgs h) {
-  __shared__ uint32_t hist[kHubSmemBuckets];
+__global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs h) {
+  extern __shared__ __align__(16) char smem_raw[];
+  ChunkSmem<K, kChunkThreads>& sm = *reinterpret_cast<ChunkSmem<K, kChunkThreads>*>(smem_raw);
+  K* list = reinterpret_cast<K*>(smem_raw + sizeof(ChunkSmem<K, kChunkThreads>));
+  uint32_t* bcnt = reinterpret_cast<uint32_t*>(list + kHubChunk);
+  uint32_t* bpos = bcnt + kHubSmemBuckets;
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
-  const uint64_t begin = ((uint64_t)c.z << 32) | c.y;
-  const uint32_t len = c.w;
+  const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
+  const uint32_t E = c.w;
   const uint32_t bits = h.hub_bits[hub] + h.extra_bits;
   const uint32_t nb = 1u << bits;
-  const bool in_smem = nb <= kHubSmemBuckets;
-  uint64_t* g = h.hist + h.hub_bbase[hub];
+  const bool in_smem = nb <= (uint32_t)kHubSmemBuckets;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  chunk_clear(sm, (2 * E + 3) & ~3u);
   if (in_smem)
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    for (uint32_t i = tid; i < nb; i += kChunkThreads) bcnt[i] = 0;
   __syncthreads();
-  K keys[kHubItems];
-  const Policies pol;
+  K key[kChunkItems];
+  chunk_keys<kChunkThreads, LabelT, K>(a, ebase, E, key);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.slot);
 #pragma unroll
-  for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kHubThreads;
-    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i, pol) : (K)0;
+  for (int t = 0; t < kChunkItems; ++t) {
+    bool fresh = false;
+    if (tid + t * kChunkThreads < E)
+      fresh = key[t] == KeyOps<K>::kEmpty ? atomicExch(&sm.empty[0], 1u) == 0u
+                                          : region_insert(sbase, 0u, 2 * E, key[t]);
+    const unsigned fm = __ballot_sync(kFull, fresh);
+    if (fm == 0u) continue;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&sm.cnt[0], (uint32_t)__popc(fm));
+    base = __shfl_sync(kFull, base, 0);
+    if (fresh) list[base + __popc(fm & lanes_below(lane))] = key[t];
   }
-#pragma unroll
-  for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kHubThreads;
-    if (i < len) {
-      const uint32_t b = hub_bucket(keys[t], bits);
-      if (in_smem) atomicAdd(&hist[b], 1u); else atomicAdd((unsigned long long*)&g[b], 1ull);
+  __syncthreads();
+  const uint32_t U = sm.cnt[0];
+  const uint32_t cap = h.hub_cap[hub];
+  uint32_t* cur = h.cursor + h.hub_bbase[hub];
+  K* tmp = static_cast<K*>(h.tmp) + h.hub_tbase[hub];
+  if (in_smem) {
+    for (uint32_t i = tid; i < U; i += kChunkThreads) atomicAdd(&bcnt[hub_bucket(list[i], bits)], 1u);
+    __syncthreads();
+    for (uint32_t b = tid; b < nb; b += kChunkThreads) {
+      const uint32_t n_b = bcnt[b];
+      bpos[b] = n_b ? atomicAdd(&cur[b], n_b) : 0u;
+      bcnt[b] = 0;
     }
+    __syncthreads();
   }
-  __syncthreads();
-  if (in_smem)
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
-      if (hist[b]) atomicAdd((unsigned long long*)&g[b], (unsigned long long)hist[b]);
-}
-
-template <typename LabelT, typename K>
-__global__ void __launch_bounds__(kHubThreads) k_hub_scatter(SigArgs a, HubArgs h) {
-  __shared__ uint32_t cnt[kHubSmemBuckets];
-  __shared__ unsigned long long base[kHubSmemBuckets];
-  const uint4 c = h.chunks[blockIdx.x];
-  const uint32_t hub = c.x;
-  const uint64_t begin = ((uint64_t)c.z << 32) | c.y;
-  const uint32_t len = c.w;
-  const uint32_t bits = h.hub_bits[hub] + h.extra_bits;
-  const uint32_t nb = 1u << bits;
-  const bool in_smem = nb <= kHubSmemBuckets;
-  uint64_t* cur = h.cursor + h.hub_bbase[hub];
-  K* tmp = static_cast<K*>(h.tmp);
-  K keys[kHubItems];
-  const Policies pol;
-#pragma unroll
-  for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kHubThreads;
-    keys[t] = i < len ? edge_key<LabelT, K>(a, begin + i, pol) : (K)0;
-  }
-  if (!in_smem) {
-#pragma unroll
-    for (int t = 0; t < kHubItems; ++t) {
-      const uint32_t i = threadIdx.x + t * kHubThreads;
-      if (i < len) {
-        const uint32_t b = hub_bucket(keys[t], bits);
-        const uint64_t p = atomicAdd((unsigned long long*)&cur[b], 1ull);
-        tmp[p] = keys[t];
-      }
-    }
-    return;
-  }
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kHubThreads;
-    if (i < len) atomicAdd(&cnt[hub_bucket(keys[t], bits)], 1u);
-  }
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-    if (cnt[b]) base[b] = atomicAdd((unsigned long long*)&cur[b], (unsigned long long)cnt[b]);
-    cnt[b] = 0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < kHubItems; ++t) {
-    const uint32_t i = threadIdx.x + t * kHubThreads;
-    if (i < len) {
-      const uint32_t b = hub_bucket(keys[t], bits);
-      const uint32_t p = atomicAdd(&cnt[b], 1u);
-      tmp[base[b] + p] = keys[t];
-    }
+  for (uint32_t i = tid; i < U; i += kChunkThreads) {
+    const K v = list[i];
+    const uint32_t b = hub_bucket(v, bits);
+    const uint32_t q = in_smem ? bpos[b] + atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
+    if (q < cap) tmp[(uint64_t)b * cap + q] = v;
+    else atomicOr(a.err, kErrHubOverflow);
   }
 }
 
-// One CTA per hub bucket.
+// One CTA per hub bucket (grid-stride).
 template <typename K>
 __global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem[];
   TeamSet<K> ts = carve_set<K>(smem, 2 * kHubUcap, kHubUcap);
   __shared__ unsigned long long obase;
   __shared__ unsigned int last;
-  const K* tmp = static_cast<const K*>(h.tmp);
   K* out = static_cast<K*>(a.sigkey);
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
     const uint32_t hub = h.bucket_hub[b];
     const uint64_t p = h.first + hub;
-    const uint64_t lo = h.hist[b];
-    const uint64_t n = h.cursor[b] - lo;  // after the scatter, cursor = end of bucket
+    const uint32_t cap = h.hub_cap[hub];
+    const K* tmp = static_cast<const K*>(h.tmp) + h.hub_tbase[hub] + (b - h.hub_bbase[hub]) * cap;
+    const uint32_t n = min(h.cursor[b], cap);
     const int hcap = set_size_for(n, 2 * kHubUcap);
     set_clear<kHubThreads>(ts, hcap, threadIdx.x);
     __syncthreads();
-    for (uint64_t base = 0; base < n; base += (uint64_t)kHubThreads * 4) {
+    for (uint32_t base = 0; base < n; base += kHubThreads * 4) {
       K keys[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const uint64_t i = base + threadIdx.x + (uint64_t)kHubThreads * t;
-        keys[t] = i < n ? tmp[lo + i] : (K)0;
+        const uint32_t i = base + threadIdx.x + kHubThreads * t;
+        keys[t] = i < n ? tmp[i] : (K)0;
       }
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if (base + threadIdx.x + (uint64_t)kHubThreads * t < n && set_insert(ts, hcap, keys[t])) {
+        if (base + threadIdx.x + kHubThreads * t < n && set_insert(ts, hcap, keys[t])) {
           const uint32_t q = atomicAdd(&ts.sh[0], 1u);
           if (q < (uint32_t)kHubUcap) ts.uniq[q] = keys[t]; else ts.sh[2] = 1u;
         }
       }
     }
     __syncthreads();
-    if (ts.sh[2]) {  // more distinct keys than the bucket can hold: caller re-partitions
+    if (ts.sh[2]) {  // more distinct keys than the bucket can hold: the host re-partitions
       if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
       __syncthreads();
       continue;
@@ -606,14 +706,18 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h
     if (threadIdx.x == 0) obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
     __syncthreads();
     const uint64_t off = a.off[p] + obase;
-    uint64_t term = 0;
+    uint32_t lo = 0, hi = 0;
     for (uint32_t i = threadIdx.x; i < U; i += kHubThreads) {
       out[off + i] = ts.uniq[i];
-      term += elem_term(ts.uniq[i], a.seed);
+      const uint64_t tm = elem_term(ts.uniq[i], a.seed);
+      lo += (uint32_t)tm;
+      hi += (uint32_t)(tm >> 32);
     }
-    term = team_sum<kHubThreads>(term, ts.red, threadIdx.x);
+    lo = team_sum<kHubThreads>(lo, ts.red, threadIdx.x);
+    hi = team_sum<kHubThreads>(hi, ts.red, threadIdx.x);
     if (threadIdx.x == 0) {
-      atomicAdd(&h.hub_term[hub], (unsigned long long)term);
+      atomicAdd(&h.hub_term[2 * hub], lo);
+      atomicAdd(&h.hub_term[2 * hub + 1], hi);
       __threadfence();
       const unsigned nb = 1u << (h.hub_bits[hub] + h.extra_bits);
       last = atomicAdd(&h.hub_done[hub], 1u) == nb - 1u;
@@ -622,7 +726,8 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h
     if (last && threadIdx.x == 0) {
       __threadfence();
       const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
-      const unsigned long long tsum = atomicAdd(&h.hub_term[hub], 0ull);
+      const unsigned long long tsum = ((unsigned long long)atomicAdd(&h.hub_term[2 * hub + 1], 0u) << 32) |
+                                      atomicAdd(&h.hub_term[2 * hub], 0u);
       a.ucnt[p] = (uint32_t)tot;
       a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
     }
@@ -801,7 +906,7 @@ __global__ void __launch_bounds__(kVerThreads) k_verify_long(GroupArgs g, Verify
     const uint32_t U = v.ucnt[p];
     const K* ka = keys + v.off[p];
     const K* kb = keys + v.off[r];
-    uint64_t found = 0;
+    uint32_t found = 0;
     for (uint32_t c0 = 0; c0 < U; c0 += kVerChunk) {
       const uint32_t cn = min((uint32_t)kVerChunk, U - c0);
       const int hcap = set_size_for(cn, 2 * kVerChunk);
@@ -1023,37 +1128,66 @@ __device__ __forceinline__ int node_class(uint64_t o, uint64_t n, const uint64_t
   return degree_class(off[o + 1] - off[o]);
 }
 
-__global__ void __launch_bounds__(kClassTile)
-    k_class_tile_count(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
-                       unsigned long long* tcnt) {
-  __shared__ unsigned int c[kNumClasses];
-  if (threadIdx.x < kNumClasses) c[threadIdx.x] = 0;
-  __syncthreads();
-  const int cls = node_class((uint64_t)blockIdx.x * kClassTile + threadIdx.x, n, off, alive);
-  if (cls >= 0) atomicAdd(&c[cls], 1u);
-  __syncthreads();
-  if (threadIdx.x < kNumClasses) tcnt[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = c[threadIdx.x];
+// Within a degree class, nodes are ordered by popularity as a target (hot
+// first), so the identifiers that most edges gather sit in a few dense cache
+// lines.  Popularity is the in-degree counted on every 2^kHotSampleShift-th
+// edge, put into kHotBuckets buckets; it affects speed only, never results.
+constexpr int kHotBuckets = 8;
+constexpr int kNumOrder = kNumClasses * kHotBuckets;
+constexpr int kHotSampleShift = 4;
+
+__device__ __forceinline__ int hot_bucket(uint32_t c) {
+  return c >= 1024 ? 0 : c >= 256 ? 1 : c >= 64 ? 2 : c >= 16 ? 3 : c >= 4 ? 4 : c >= 2 ? 5 : c >= 1 ? 6 : 7;
 }
 
-// Stable scatter: each tile writes its nodes of class c in id order at the
-// (class, tile) base.
+__device__ __forceinline__ int order_class(uint64_t o, uint64_t n, const uint64_t* off, const uint8_t* alive,
+                                           const uint32_t* hot) {
+  const int c = node_class(o, n, off, alive);
+  if (c < 0) return -1;
+  return c * kHotBuckets + (c == kClassDead ? 0 : hot_bucket(hot[o]));
+}
+
+__global__ void k_hot_sample(uint64_t m, const uint32_t* dst0, uint32_t* hot) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; (i << kHotSampleShift) < m; i += stride)
+    atomicAdd(&hot[dst0[i << kHotSampleShift]], 1u);
+}
+
 __global__ void __launch_bounds__(kClassTile)
-    k_class_tile_scatter(uint64_t n, const uint64_t* off, const uint8_t* alive, uint64_t ntiles,
+    k_class_tile_count(uint64_t n, const uint64_t* off, const uint8_t* alive, const uint32_t* hot, uint64_t ntiles,
+                       unsigned long long* tcnt) {
+  __shared__ unsigned int c[kNumOrder];
+  for (int i = threadIdx.x; i < kNumOrder; i += kClassTile) c[i] = 0;
+  __syncthreads();
+  const int cls = order_class((uint64_t)blockIdx.x * kClassTile + threadIdx.x, n, off, alive, hot);
+  if (cls >= 0) atomicAdd(&c[cls], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNumOrder; i += kClassTile) tcnt[(uint64_t)i * ntiles + blockIdx.x] = c[i];
+}
+
+// Stable scatter: each tile writes its nodes of order class c in id order at
+// the (class, tile) base.
+__global__ void __launch_bounds__(kClassTile)
+    k_class_tile_scatter(uint64_t n, const uint64_t* off, const uint8_t* alive, const uint32_t* hot, uint64_t ntiles,
                          const unsigned long long* tbase, uint32_t* p2o) {
-  __shared__ unsigned int wcount[kClassTile / 32];
+  __shared__ unsigned int wcnt[kClassTile / 32][kNumOrder];
+  for (int i = threadIdx.x; i < (kClassTile / 32) * kNumOrder; i += kClassTile) (&wcnt[0][0])[i] = 0;
   const uint64_t o = (uint64_t)blockIdx.x * kClassTile + threadIdx.x;
-  const int cls = node_class(o, n, off, alive);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = 0; c < kNumClasses; ++c) {
-    const unsigned m = __ballot_sync(kFull, cls == c);
-    if (lane == 0) wcount[w] = __popc(m);
-    __syncthreads();
-    unsigned before = 0;
-    for (int i = 0; i < w; ++i) before += wcount[i];
-    if (cls == c)
-      p2o[tbase[(uint64_t)c * ntiles + blockIdx.x] + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)o;
-    __syncthreads();
+  const int cls = order_class(o, n, off, alive, hot);
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned same = __match_any_sync(kFull, cls);
+  __syncthreads();
+  if (cls >= 0 && lane == (unsigned)__ffs(same) - 1u) wcnt[w][cls] = __popc(same);
+  __syncthreads();
+  if (cls >= 0) {
+    unsigned before = __popc(same & ((1u << lane) - 1u));
+    for (unsigned i = 0; i < w; ++i) before += wcnt[i][cls];
+    p2o[tbase[(uint64_t)cls * ntiles + blockIdx.x] + before] = (uint32_t)o;
   }
+}
+
+__global__ void k_order_starts(const unsigned long long* tbase, uint64_t ntiles, unsigned long long* out) {
+  for (int i = threadIdx.x; i < kNumOrder; i += blockDim.x) out[i] = tbase[(uint64_t)i * ntiles];
 }
 
 __global__ void k_invert(uint64_t n, const uint32_t* p2o, uint32_t* o2p) {
@@ -1223,15 +1357,15 @@ Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
 
 template <typename LabelT, typename K>
 cudaError_t set_smem_attrs_label() {
-  cudaError_t e = cudaFuncSetAttribute(k_sig_warp<kWarpMax, kWarpTeams, kWarpTeam, kWarpItems, LabelT, K>,
+  cudaError_t e = cudaFuncSetAttribute(k_sig_chunk<kChunkThreads, LabelT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(warp_ws_bytes<K>() * kWarpTeams));
+                                       (int)sizeof(ChunkSmem<K, kChunkThreads>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_warp<kWarp2Max, kWarps2PerBlock, 32, kWarp2Items, LabelT, K>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warp2_ws_bytes<K>() * kWarps2PerBlock));
+    e = cudaFuncSetAttribute(k_sig_chunk<kSmallChunkThreads, LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ChunkSmem<K, kSmallChunkThreads>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_block<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)blk_ws_bytes<K>());
+    e = cudaFuncSetAttribute(k_hub_chunk<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hub_chunk_smem<K>());
   return e;
 }
 
@@ -1301,7 +1435,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.off = ptr<uint64_t>(s.offsets);
   v.sigkey = s.sigkey.p;
   v.n_collided = sc + 4;
-  v.long_list = ptr<uint32_t>(s.hub_hist);  // reused as (node, candidate) pairs
+  v.long_list = ptr<uint32_t>(s.long_pairs);
   v.n_long = sc + 6;
   const int sms = sm_count(s.device);
   const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
@@ -1409,28 +1543,39 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   return Status::Ok();
 }
 
-// (Re)build the per-hub bucket table for the current extra bits.
+// (Re)build the per-hub bucket table for the current extra bits: hub i has
+// 2^(bits_i + extra) buckets of cap_i key words each, cap_i twice the mean
+// bucket load plus a margin (at most kHubUcap).
 Status hub_layout(Store& s) {
   Status st;
-  std::vector<uint32_t> bits(s.n_hub);
-  std::vector<uint64_t> bbase(s.n_hub + 1, 0);
+  std::vector<uint32_t> bits(s.n_hub), cap(s.n_hub);
+  std::vector<uint64_t> bbase(s.n_hub + 1, 0), tbase(s.n_hub, 0);
+  uint64_t words = 0;
   for (uint64_t i = 0; i < s.n_hub; ++i) {
     bits[i] = s.h_hub_degbits[i];
-    bbase[i + 1] = bbase[i] + (1ull << (bits[i] + s.hub_extra_bits));
+    const uint64_t nb = 1ull << (bits[i] + s.hub_extra_bits);
+    bbase[i + 1] = bbase[i] + nb;
+    const uint64_t mean = (s.h_hub_deg[i] + nb - 1) / nb;
+    cap[i] = (uint32_t)std::min<uint64_t>(kHubUcap, 2 * mean + 256);
+    tbase[i] = words;
+    words += nb * cap[i];
   }
   s.n_hub_buckets = bbase[s.n_hub];
+  s.hub_tmp_words = words;
   std::vector<uint32_t> bhub(s.n_hub_buckets);
   for (uint64_t i = 0; i < s.n_hub; ++i)
     for (uint64_t b = bbase[i]; b < bbase[i + 1]; ++b) bhub[b] = (uint32_t)i;
   if (!(st = ensure(s, s.hub_bits, s.n_hub * 4)).ok()) return st;
+  if (!(st = ensure(s, s.hub_cap, s.n_hub * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_bbase, (s.n_hub + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, s.hub_tbase, s.n_hub * 8)).ok()) return st;
   if (!(st = ensure(s, s.bucket_hub, s.n_hub_buckets * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, std::max<uint64_t>(s.n, 1) * 8))).ok())
-    return st;
-  if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 8)).ok()) return st;
+  if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_acc, s.n_hub * 24)).ok()) return st;
   cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.hub_cap.p, cap.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.hub_bbase.p, bbase.data(), (s.n_hub + 1) * 8, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.hub_tbase.p, tbase.data(), s.n_hub * 8, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.bucket_hub.p, bhub.data(), s.n_hub_buckets * 4, cudaMemcpyHostToDevice, s.stream);
   return cuda_check(cudaStreamSynchronize(s.stream), "hub layout");
 }
@@ -1460,55 +1605,40 @@ Status run_signatures(Store& s, const SigArgs& a) {
     if (n7) k_sig_small<kSmallClasses - 1, kSmallClasses - 1, LabelT, K><<<n7, kSmallThreads, 0, s.stream>>>(a, L);
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
-  const uint64_t n_warp = s.class_start[kClassWarp + 1] - s.class_start[kClassWarp];
-  const uint64_t n_warp2 = s.class_start[kClassWarp2 + 1] - s.class_start[kClassWarp2];
-  const uint64_t n_block = s.class_start[kClassBlock + 1] - s.class_start[kClassBlock];
-  if (n_warp) {
+  if (s.n_mid_chunks[0] + s.n_mid_chunks[1]) {
     TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>((n_warp + kWarpTeams - 1) / kWarpTeams, (uint64_t)sms * 8);
-    k_sig_warp<kWarpMax, kWarpTeams, kWarpTeam, kWarpItems, LabelT, K>
-        <<<g, kWarpTeams * kWarpTeam, warp_ws_bytes<K>() * kWarpTeams, s.stream>>>(a, s.class_start[kClassWarp],
-                                                                                   n_warp);
+    if (s.n_mid_chunks[0])
+      k_sig_chunk<kSmallChunkThreads, LabelT, K>
+          <<<(unsigned)s.n_mid_chunks[0], kSmallChunkThreads, sizeof(ChunkSmem<K, kSmallChunkThreads>), s.stream>>>(
+              a, ptr<uint2>(s.mid_chunks));
+    if (s.n_mid_chunks[1])
+      k_sig_chunk<kChunkThreads, LabelT, K>
+          <<<(unsigned)s.n_mid_chunks[1], kChunkThreads, sizeof(ChunkSmem<K, kChunkThreads>), s.stream>>>(
+              a, ptr<uint2>(s.mid_chunks) + s.n_mid_chunks[0]);
   }
-  if (!(st = launch_check("k_sig_warp")).ok()) return st;
-  if (n_warp2) {
-    TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>((n_warp2 + kWarps2PerBlock - 1) / kWarps2PerBlock,
-                                                    (uint64_t)sms * 16);
-    k_sig_warp<kWarp2Max, kWarps2PerBlock, 32, kWarp2Items, LabelT, K>
-        <<<g, kWarps2PerBlock * 32, warp2_ws_bytes<K>() * kWarps2PerBlock, s.stream>>>(
-            a, s.class_start[kClassWarp2], n_warp2);
-  }
-  if (!(st = launch_check("k_sig_warp2")).ok()) return st;
-  if (n_block) {
-    TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    const unsigned g = (unsigned)std::min<uint64_t>(n_block, (uint64_t)sms * 4);
-    k_sig_block<LabelT, K><<<g, kBlockThreads, blk_ws_bytes<K>(), s.stream>>>(a, s.class_start[kClassBlock],
-                                                                            n_block);
-  }
-  if (!(st = launch_check("k_sig_block")).ok()) return st;
+  if (!(st = launch_check("k_sig_chunk")).ok()) return st;
   if (s.n_hub) {
     for (int attempt = 0;; ++attempt) {
+      if (!(st = ensure(s, s.hub_tmp, s.hub_tmp_words * sizeof(K))).ok()) return st;
       HubArgs h;
       h.first = s.class_start[kClassHub];
       h.hub_bits = ptr<uint32_t>(s.hub_bits);
       h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
+      h.hub_cap = ptr<uint32_t>(s.hub_cap);
+      h.hub_tbase = ptr<uint64_t>(s.hub_tbase);
       h.bucket_hub = ptr<uint32_t>(s.bucket_hub);
       h.chunks = ptr<uint4>(s.hub_chunks);
       h.extra_bits = s.hub_extra_bits;
-      h.hist = ptr<uint64_t>(s.hub_hist);
-      h.cursor = ptr<uint64_t>(s.hub_cursor);
+      h.cursor = ptr<uint32_t>(s.hub_cursor);
       h.hub_cur = ptr<unsigned long long>(s.hub_acc);
-      h.hub_term = h.hub_cur + s.n_hub;
-      h.hub_done = reinterpret_cast<unsigned int*>(h.hub_term + s.n_hub);
+      h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
+      h.hub_done = h.hub_term + 2 * s.n_hub;
       h.tmp = s.hub_tmp.p;
       {
         TimedScope ts(s, KBISIM_KERNEL_SIG_HUB);
-        cudaMemsetAsync(h.hist, 0, s.n_hub_buckets * 8, s.stream);
+        cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
-        k_hub_hist<LabelT, K><<<(unsigned)s.n_hub_chunks, kHubThreads, 0, s.stream>>>(a, h);
-        if (!(st = scan64(s, h.hist, s.n_hub_buckets, h.cursor)).ok()) return st;
-        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kHubThreads, 0, s.stream>>>(a, h);
+        k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
         const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 4);
         k_hub_bucket<K><<<g, kHubThreads, hub_ws_bytes<K>(), s.stream>>>(a, h, s.n_hub_buckets);
       }
@@ -1518,8 +1648,8 @@ Status run_signatures(Store& s, const SigArgs& a) {
       if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
       if (!st.ok()) return st;
       if (!(e & kErrHubOverflow)) break;
-      if (attempt >= 6) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
-      s.hub_extra_bits += 2;
+      if (attempt >= 8) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
+      s.hub_extra_bits += 1;
       if (!(st = hub_layout(s)).ok()) return st;
       cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
     }
@@ -1544,8 +1674,7 @@ Status ensure_round_scratch(Store& s) {
   if (!(st = ensure(s, s.member, n + 16)).ok()) return st;
   if (!(st = ensure(s, s.alone, n + 16)).ok()) return st;
   if (!(st = ensure(s, s.rank_o, n * 4)).ok()) return st;
-  // the long-signature pair list reuses hub_hist: 2 words per alive node
-  if (!(st = ensure(s, s.hub_hist, std::max<uint64_t>(s.n_hub_buckets * 8, n * 8))).ok()) return st;
+  if (!(st = ensure(s, s.long_pairs, n * 8)).ok()) return st;
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (!(st = ensure(s, s.bsum, std::max<uint64_t>(tiles, 64) * 8)).ok()) return st;
   return Status::Ok();
@@ -1569,39 +1698,44 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   const uint64_t n = s.n, m = s.m;
   const int sms = sm_count(s.device);
   const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
-  Buf tcnt;
-  if (!(st = ensure(s, tcnt, ntiles * kNumClasses * 8)).ok()) return st;
-  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumClasses * 8, s.stream);
+  Buf tcnt, hot, ost;
+  auto fail = [&](Status e) {
+    release(s, tcnt);
+    release(s, hot);
+    release(s, ost);
+    return e;
+  };
+  if (!(st = ensure(s, tcnt, ntiles * kNumOrder * 8)).ok()) return fail(st);
+  if (!(st = ensure(s, hot, std::max<uint64_t>(1, n) * 4)).ok()) return fail(st);
+  if (!(st = ensure(s, ost, kNumOrder * 8)).ok()) return fail(st);
+  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumOrder * 8, s.stream);
+  cudaMemsetAsync(hot.p, 0, std::max<uint64_t>(1, n) * 4, s.stream);
+  if (m >> kHotSampleShift)
+    k_hot_sample<<<(unsigned)std::min<uint64_t>(grid_for(m >> kHotSampleShift, 256), (uint64_t)sms * 32), 256, 0,
+                   s.stream>>>(m, dst0, ptr<uint32_t>(hot));
   if (n)
-    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ntiles,
+    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
                                                                       ptr<unsigned long long>(tcnt));
-  if (!(st = launch_check("k_class_tile_count")).ok()) { release(s, tcnt); return st; }
-  std::vector<uint64_t> h(ntiles * kNumClasses);
-  st = cuda_check(cudaMemcpyAsync(h.data(), tcnt.p, h.size() * 8, cudaMemcpyDeviceToHost, s.stream), "class counts");
+  if (!(st = launch_check("k_class_tile_count")).ok()) return fail(st);
+  if (!(st = scan64(s, ptr<uint64_t>(tcnt), ntiles * kNumOrder, nullptr)).ok()) return fail(st);
+  k_order_starts<<<1, 128, 0, s.stream>>>(ptr<unsigned long long>(tcnt), ntiles, ptr<unsigned long long>(ost));
+  std::vector<uint64_t> hs(kNumOrder);
+  st = cuda_check(cudaMemcpyAsync(hs.data(), ost.p, kNumOrder * 8, cudaMemcpyDeviceToHost, s.stream), "class starts");
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  if (!st.ok()) { release(s, tcnt); return st; }
-  uint64_t run = 0;
-  for (int c = 0; c < kNumClasses; ++c) {
-    s.class_start[c] = run;
-    for (uint64_t t = 0; t < ntiles; ++t) {
-      const uint64_t v = h[(uint64_t)c * ntiles + t];
-      h[(uint64_t)c * ntiles + t] = run;
-      run += v;
-    }
-  }
-  s.class_start[kNumClasses] = run;
+  if (!st.ok()) return fail(st);
+  for (int c = 0; c < kNumClasses; ++c) s.class_start[c] = hs[(size_t)c * kHotBuckets];
+  s.class_start[kNumClasses] = n;
   s.n_alive = s.class_start[kClassDead];
-  st = cuda_check(cudaMemcpyAsync(tcnt.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s.stream), "class bases");
   if (st.ok()) st = ensure(s, s.p2o, std::max<uint64_t>(1, n) * 4);
   if (st.ok()) st = ensure(s, s.o2p, std::max<uint64_t>(1, n) * 4);
   if (st.ok()) st = ensure(s, s.offsets, (n + 1) * 8);
   if (st.ok()) st = ensure(s, s.nlabel, std::max<uint64_t>(1, n) * 4);
   if (st.ok()) st = ensure(s, s.dst, std::max<uint64_t>(1, m) * 4);
   if (st.ok()) st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4));
-  if (!st.ok()) { release(s, tcnt); return st; }
+  if (!st.ok()) return fail(st);
   const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
   if (n) {
-    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ntiles,
+    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
                                                                         ptr<unsigned long long>(tcnt),
                                                                         ptr<uint32_t>(s.p2o));
     k_invert<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), ptr<uint32_t>(s.o2p));
@@ -1610,14 +1744,16 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
                                             ptr<unsigned long long>(s.offsets), ptr<uint32_t>(s.nlabel));
   st = launch_check("relabel nodes");
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  release(s, tcnt);  // the class scatter has finished with the tile bases
+  fail(Status::Ok());  // the class scatter has finished with the tile bases and counts
   if (!st.ok()) return st;
   if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
   s.hub_extra_bits = 0;
   s.h_hub_degbits.assign(s.n_hub, 0);
+  s.h_hub_deg.assign(s.n_hub, 0);
   s.hub_edges = 0;
+  s.n_hub_chunks = 0;
   s.n_hub_buckets = 0;
   if (s.n_hub) {
     std::vector<uint64_t> hoff(s.n_hub + 1);
@@ -1631,6 +1767,7 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
       uint32_t bits = 0;
       while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
       s.h_hub_degbits[i] = bits;
+      s.h_hub_deg[i] = d;
       s.hub_edges += d;
       for (uint64_t b = 0; b < d; b += kHubChunk) {
         const uint64_t e = hoff[i] + b;
@@ -1647,8 +1784,35 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
     st = cuda_check(cudaMemcpyAsync(s.hub_chunks.p, chunks.data(), chunks.size() * sizeof(uint4),
                                     cudaMemcpyHostToDevice, s.stream), "hub chunks");
     if (!st.ok()) return st;
-    if (!(st = ensure(s, s.hub_tmp, s.hub_edges * 8)).ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
+  }
+  // medium nodes: runs of whole nodes; out-degree 65..1024 in chunks of at
+  // most 1024 edges (128-thread CTAs), 1025..4096 in chunks of at most 4096
+  s.n_mid_chunks[0] = s.n_mid_chunks[1] = 0;
+  const uint64_t mf = s.class_start[kClassWarp], mb = s.class_start[kClassBlock], me = s.class_start[kClassHub];
+  if (me > mf) {
+    std::vector<uint64_t> moff(me - mf + 1);
+    st = cuda_check(cudaMemcpyAsync(moff.data(), ptr<uint64_t>(s.offsets) + mf, (me - mf + 1) * 8,
+                                    cudaMemcpyDeviceToHost, s.stream), "medium offsets");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+    if (!st.ok()) return st;
+    std::vector<uint2> mc;
+    auto pack = [&](uint64_t lo, uint64_t hi, uint64_t max_edges, uint64_t max_nodes) {
+      for (uint64_t i = lo; i < hi;) {
+        uint64_t j = i + 1;
+        while (j < hi && j - i < max_nodes && moff[j + 1] - moff[i] <= max_edges) ++j;
+        mc.push_back(make_uint2((uint32_t)(mf + i), (uint32_t)(j - i)));
+        i = j;
+      }
+    };
+    pack(0, mb - mf, ChunkShape<kSmallChunkThreads>::kEdges, ChunkShape<kSmallChunkThreads>::kMaxNodes);
+    s.n_mid_chunks[0] = mc.size();
+    pack(mb - mf, me - mf, ChunkShape<kChunkThreads>::kEdges, ChunkShape<kChunkThreads>::kMaxNodes);
+    s.n_mid_chunks[1] = mc.size() - s.n_mid_chunks[0];
+    if (!(st = ensure(s, s.mid_chunks, mc.size() * sizeof(uint2))).ok()) return st;
+    st = cuda_check(cudaMemcpyAsync(s.mid_chunks.p, mc.data(), mc.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                                    s.stream), "medium chunks");
+    if (!st.ok()) return st;
   }
   if (n && m) {
     if (s.label8) {
