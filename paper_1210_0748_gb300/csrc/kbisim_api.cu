@@ -207,7 +207,7 @@ Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned 
 void free_graph(Store& s) {
   Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.p2o, &s.o2p, &s.mid_chunks, &s.hub_bits,
                  &s.hub_bbase, &s.hub_cap, &s.hub_tbase, &s.hub_chunks, &s.sigkey, &s.ucnt, &s.hash, &s.table,
-                 &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.hflag, &s.member, &s.alone, &s.rank_o, &s.bsum,
+                 &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.hbits, &s.member, &s.alone, &s.hword, &s.bsum,
                  &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_tmp, &s.alive_o};
   for (Buf* b : bufs) release(s, *b);
   for (Buf& b : s.level) release(s, b);

@@ -204,10 +204,11 @@ struct Store {
   Buf slot;                    // uint32 [n]
   Buf rep;                     // uint32 [n] internal id of the block head
   Buf ulist[2];                // uint32 [n] unresolved nodes (ping-pong)
-  Buf hflag;                   // uint8 [n] head flags in original order
+  Buf hbits;                   // uint32 [(n+31)/32] head bitmap over original ids
   Buf member;                  // uint8 [n] block head has other members (this level)
   Buf alone;                   // uint8 [n] node is alone in its block at the last computed level
-  Buf rank_o;                  // uint32 [n] block id of heads, original order
+  Buf hword;                   // uint64 [(n+31)/32] heads before each bitmap word
+  uint64_t n_alone = 0;        // nodes alone in their block at the last computed level
   Buf bsum;                    // uint64 scan block sums
   Buf long_pairs;              // uint32 [2n] (node, candidate) pairs with long signatures
   Buf hub_cursor;              // uint32 [buckets] key words appended to each bucket

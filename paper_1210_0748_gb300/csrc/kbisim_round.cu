@@ -928,7 +928,9 @@ __global__ void __launch_bounds__(kVerThreads) k_verify_long(GroupArgs g, Verify
 // --------------------------------------------------------------------------
 // Canonical renumbering: heads are nodes with rep[p] == p (the node with the
 // smallest original id in its block); a block's id is the number of heads
-// with a smaller original id.
+// with a smaller original id.  Heads are marked in a bitmap over original ids
+// (n/8 bytes, cache resident); an exclusive scan of the per-word head counts
+// then gives each head its rank with one more popcount.
 // --------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -939,13 +941,12 @@ struct RankArgs {
   const uint32_t* rep;
   const uint32_t* p2o;
   const uint32_t* ucnt;    // may be null (level 0)
-  uint8_t* hflag;          // [n] original order
+  uint32_t* hbits;         // [words] head bitmap, original order
+  uint64_t* hword;         // [words] head count per word, then heads before the word
   uint8_t* member;         // [n] internal order: the head has other members
   uint8_t* alone;          // [n] internal order: output, node alone in its block
-  uint32_t* rank_o;        // [n] original order
   uint32_t* pid;           // output level, internal order
-  uint64_t* bsum;          // per tile head count -> exclusive offsets
-  unsigned long long* stats;  // [0] heads total, [2] key total, [3] max signature
+  unsigned long long* stats;  // [2] key total, [3] max signature, [8] nodes alone in their block
 };
 
 __global__ void k_mark_heads(RankArgs r) {
@@ -954,7 +955,12 @@ __global__ void k_mark_heads(RankArgs r) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n_alive;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t h = r.rep[p];
-    if (h == (uint32_t)p) r.hflag[r.p2o[p]] = 1; else r.member[h] = 1;
+    if (h == (uint32_t)p) {
+      const uint32_t o = r.p2o[p];
+      atomicOr(&r.hbits[o >> 5], 1u << (o & 31));
+    } else {
+      r.member[h] = 1;
+    }
     if (r.ucnt) {
       const uint32_t q = r.ucnt[p];
       keys += q;
@@ -974,24 +980,9 @@ __global__ void k_mark_heads(RankArgs r) {
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_flag_tilesum(const uint8_t* f, uint64_t n, uint64_t* bsum) {
-  __shared__ unsigned long long red[kScanThreads / 32];
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-  unsigned long long c = 0;
-#pragma unroll
-  for (int t = 0; t < kScanItems; ++t) {
-    const uint64_t i = base + (uint64_t)t * kScanThreads + threadIdx.x;
-    if (i < n) c += f[i];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long tot = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) tot += red[w];
-    bsum[blockIdx.x] = tot;
-  }
+__global__ void k_word_counts(const uint32_t* hbits, uint64_t words, uint64_t* hword) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x)
+    hword[w] = __popc(hbits[w]);
 }
 
 // Exclusive scan of bsum[0..nb) in one CTA; total into *total.
@@ -1033,62 +1024,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint64_t* bsum, uin
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Heads (flagged original ids) get their rank: tile offset + rank in tile.
-__global__ void __launch_bounds__(kScanThreads) k_flag_rank(const uint8_t* f, uint64_t n, const uint64_t* bsum,
-                                                             uint32_t* rank_o) {
-  __shared__ unsigned int wt[kScanThreads / 32];
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
-  unsigned int fl[kScanItems];
-  unsigned int c = 0;
-  if (base + kScanItems <= n) {
-    const uchar4 v = *reinterpret_cast<const uchar4*>(f + base);
-    fl[0] = v.x; fl[1] = v.y; fl[2] = v.z; fl[3] = v.w;
-  } else {
-#pragma unroll
-    for (int t = 0; t < kScanItems; ++t) fl[t] = base + t < n ? f[base + t] : 0u;
-  }
-#pragma unroll
-  for (int t = 0; t < kScanItems; ++t) c += fl[t];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned int x = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned int y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wt[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    unsigned int t = wt[lane];
-    unsigned int xx = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned int y = __shfl_up_sync(kFull, xx, o);
-      if (lane >= o) xx += y;
-    }
-    wt[lane] = xx - t;
-  }
-  __syncthreads();
-  uint64_t rank = bsum[blockIdx.x] + wt[w] + (x - c);
-#pragma unroll
-  for (int t = 0; t < kScanItems; ++t) {
-    if (fl[t]) rank_o[base + t] = (uint32_t)rank;
-    rank += fl[t];
-  }
-}
-
 // Every alive node takes its head's block id; deleted nodes get kDead.
 __global__ void k_pid_fill(RankArgs r) {
+  unsigned int n_alone = 0;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n;
        p += (uint64_t)gridDim.x * blockDim.x) {
     if (p < r.n_alive) {
       const uint32_t h = r.rep[p];
-      r.pid[p] = r.rank_o[r.p2o[h]];
-      r.alone[p] = (h == (uint32_t)p && !r.member[p]) ? 1 : 0;
+      const uint32_t o = r.p2o[h];
+      const uint32_t w = o >> 5;
+      r.pid[p] = (uint32_t)r.hword[w] + (uint32_t)__popc(r.hbits[w] & ((1u << (o & 31)) - 1u));
+      const bool al = h == (uint32_t)p && !r.member[p];
+      r.alone[p] = al ? 1 : 0;
+      n_alone += al ? 1u : 0u;
     } else {
       r.pid[p] = kDead;
     }
   }
+  n_alone = __reduce_add_sync(kFull, n_alone);
+  if ((threadIdx.x & 31) == 0 && n_alone) atomicAdd(&r.stats[8], (unsigned long long)n_alone);
 }
 
 // Level 0 hash: the node label.
@@ -1408,9 +1362,10 @@ uint64_t table_capacity(uint64_t n) {
 }
 
 // Scalars used per round (uint64 words of Store::d_scalars):
-//  [0] heads, [1] unresolved after the first pass, [2] key total,
-//  [3] largest signature, [4] collided nodes, [5] unresolved after a repair
-//  pass, [6] long-signature pairs, [7] error flags copy, [15] scan scratch.
+//  [1] unresolved after the first pass, [2] key total, [3] largest signature,
+//  [4] collided nodes, [5] unresolved after a repair pass, [6] long-signature
+//  pairs, [7] error flags copy, [8] nodes alone in their block, [15] scan
+//  total (after renumbering: the number of blocks).
 Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint32_t* pid, uint64_t* blocks,
                       uint64_t* collided, bool with_stats, uint64_t* keys, uint64_t* maxsig, bool use_alone) {
   const uint64_t n = s.n, na = s.n_alive;
@@ -1439,9 +1394,12 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.n_long = sc + 6;
   const int sms = sm_count(s.device);
   const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
+  // only nodes not alone in their previous block are inserted
+  const uint64_t tcap = std::min<uint64_t>(s.tcap, table_capacity(use_alone ? na - std::min(na, s.n_alone) : na));
+  g.tmask = tcap - 1;
   {
     TimedScope ts(s, KBISIM_KERNEL_OTHER);
-    cudaMemsetAsync(s.table.p, 0xFF, s.tcap * 8, s.stream);
+    cudaMemsetAsync(s.table.p, 0xFF, tcap * 8, s.stream);
     cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
   }
   const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8);
@@ -1505,36 +1463,36 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   }
   *collided = h[4];
   // canonical renumbering
+  const uint64_t words = (n + 31) / 32;
   RankArgs r;
   r.n = n;
   r.n_alive = na;
   r.rep = g.rep;
   r.p2o = g.p2o;
   r.ucnt = with_stats ? ptr<uint32_t>(s.ucnt) : nullptr;
-  r.hflag = ptr<uint8_t>(s.hflag);
+  r.hbits = ptr<uint32_t>(s.hbits);
+  r.hword = ptr<uint64_t>(s.hword);
   r.member = ptr<uint8_t>(s.member);
   r.alone = ptr<uint8_t>(s.alone);
-  r.rank_o = ptr<uint32_t>(s.rank_o);
   r.pid = pid;
-  r.bsum = ptr<uint64_t>(s.bsum);
   r.stats = sc;
-  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   {
     TimedScope ts(s, KBISIM_KERNEL_RENUMBER);
     if (n) {
-      cudaMemsetAsync(s.hflag.p, 0, n, s.stream);
+      cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
       cudaMemsetAsync(s.member.p, 0, n, s.stream);
       k_mark_heads<<<gblocks, 256, 0, s.stream>>>(r);
-      k_flag_tilesum<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r.hflag, n, r.bsum);
-      k_scan_tiles<<<1, kScanThreads, 0, s.stream>>>(r.bsum, tiles, sc);
-      k_flag_rank<<<(unsigned)tiles, kScanThreads, 0, s.stream>>>(r.hflag, n, r.bsum, r.rank_o);
+      k_word_counts<<<(unsigned)std::min<uint64_t>(grid_for(words, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(
+          r.hbits, words, r.hword);
+      if (!(st = scan64(s, r.hword, words, nullptr)).ok()) return st;
       k_pid_fill<<<(unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(r);
     }
   }
   if (!(st = launch_check("renumber")).ok()) return st;
   cudaMemcpyAsync(sc + 7, s.d_err.p, 4, cudaMemcpyDeviceToDevice, s.stream);
   if (!(st = read_scalars(s, h)).ok()) return st;
-  *blocks = h[0];
+  *blocks = n ? h[15] : 0;  // scan total: heads
+  s.n_alone = h[8];
   if (keys) *keys = h[2];
   if (maxsig) *maxsig = h[3];
   const uint32_t e = (uint32_t)h[7];
@@ -1670,10 +1628,10 @@ Status ensure_round_scratch(Store& s) {
   if (!(st = ensure(s, s.rep, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.ulist[0], n * 4)).ok()) return st;
   if (!(st = ensure(s, s.ulist[1], n * 4)).ok()) return st;
-  if (!(st = ensure(s, s.hflag, n + 16)).ok()) return st;
+  if (!(st = ensure(s, s.hbits, ((n + 31) / 32) * 4 + 16)).ok()) return st;
+  if (!(st = ensure(s, s.hword, std::max<uint64_t>((n + 31) / 32, 1) * 8)).ok()) return st;
   if (!(st = ensure(s, s.member, n + 16)).ok()) return st;
   if (!(st = ensure(s, s.alone, n + 16)).ok()) return st;
-  if (!(st = ensure(s, s.rank_o, n * 4)).ok()) return st;
   if (!(st = ensure(s, s.long_pairs, n * 8)).ok()) return st;
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (!(st = ensure(s, s.bsum, std::max<uint64_t>(tiles, 64) * 8)).ok()) return st;
@@ -1749,6 +1707,7 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
+  s.n_alone = 0;
   s.hub_extra_bits = 0;
   s.h_hub_degbits.assign(s.n_hub, 0);
   s.h_hub_deg.assign(s.n_hub, 0);
