@@ -39,22 +39,55 @@ L2_BYTES = 129 * 1024 * 1024
 # hash write 8, one read + write of a 16 B grouping record 32, pId_i write 4 = 56 B.
 BYTES_PER_EDGE = 21
 BYTES_PER_NODE = 56
-# Split of those bytes over the kernel classes the library times:
+# Split of those bytes over the kernel classes the library times, as
+# (bytes per edge, bytes per node) of the edges and nodes each class covers:
 #   signature kernels: 13 B/edge + 20 B/node (dst+label read, key write;
 #   offsets, pId_{i-1}, hash write), grouping: 16 B/node, verification:
 #   8 B/edge + 16 B/node, renumbering: 4 B/node.
 KERNEL_BYTES = {
-    "sig": (13, 20),
+    "sig_small": (13, 20),
+    "sig_medium": (13, 20),
+    "sig_hub": (13, 20),
     "group": (0, 16),
     "verify": (8, 16),
     "renumber": (0, 4),
 }
+# Out-degree ranges of the signature kernel classes (the library's split).
+SIG_DEGREES = {"sig_small": (0, 64), "sig_medium": (65, 4096), "sig_hub": (4097, None)}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_powerlaw_16m_256m.json")
+
+
+def class_units(g):
+    """(edges, nodes) each kernel class processes per round."""
+    d = np.diff(g.offsets.astype(np.int64))
+    out = {}
+    for k, (lo, hi) in SIG_DEGREES.items():
+        m = (d >= lo) & (d <= hi) if hi is not None else (d >= lo)
+        out[k] = (int(d[m].sum()), int(m.sum()))
+    for k in ("group", "verify", "renumber"):
+        out[k] = (g.num_edges, g.num_nodes)
+    return out
+
+
+def recorded_traffic(cls, scale):
+    """DRAM bytes per round of a kernel class from the committed ncu summary, if it
+    was taken on the current kernel sources and the same workload scale."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    from paper_1210_0748_gb300.ncu_summary import source_digest
+    if t.get("source_sha256") != source_digest() or float(t.get("scale", -1)) != float(scale):
+        return None
+    v = t.get("dram_bytes_per_round", {}).get(cls)
+    return float(v) if v is not None else None
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 16M/256M)")
@@ -239,28 +272,39 @@ def main():
     value = world * E * rounds / (ms_max / 1000.0)
 
     # roofline: the whole refinement round against the fixed algorithmic bytes,
-    # and the dominant kernel class against its share of those bytes
+    # and each kernel class against its share of those bytes (per call of the
+    # class: once per round for the signature classes, once per level -- level
+    # 0 included -- for grouping, verification and renumbering)
     peak, peak_kind = load_peaks()
     rounds_per_step = rounds / args.steps
     gpu_launches = int(sum(c for _, c in ktimes.values()))
     round_ms = (ms_total / args.steps - ktimes["label_group"][0] / args.steps) / max(rounds_per_step, 1)
     round_bytes = BYTES_PER_EDGE * E + BYTES_PER_NODE * N
-    cls_ms = {
-        "sig": sum(ktimes[k][0] for k in ("sig_small", "sig_medium", "sig_hub")),
-        "group": ktimes["group"][0],
-        "verify": ktimes["verify"][0],
-        "renumber": ktimes["renumber"][0],
-    }
-    dom = max(cls_ms, key=cls_ms.get)
-    be, bn = KERNEL_BYTES[dom]
-    dom_bytes = be * E + bn * N  # per round (one launch sequence of that class)
-    n_rounds_total = rounds
-    dom_ms = cls_ms[dom] / max(n_rounds_total, 1)
-    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "signature kernels (gather, sort, dedupe, hash)"
-                if dom == "sig" else dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
+    units = class_units(g)
+    per_class = {}
+    for cls, (be, bn) in KERNEL_BYTES.items():
+        calls = rounds if cls.startswith("sig") else rounds + args.steps
+        ms, launches = ktimes[cls]
+        if calls == 0 or ms <= 0:
+            continue
+        e_c, n_c = units[cls]
+        byts = be * e_c + bn * n_c
+        ms_call = ms / calls
+        per_class[cls] = {"achieved": byts / (ms_call / 1000.0) / 1e9, "frac": byts / (ms_call / 1000.0) / 1e9 / peak,
+                          "algorithmic_bytes_per_call": byts, "ms_per_call": ms_call,
+                          "launches_per_call": launches / calls, "edges": e_c, "nodes": n_c}
+    dom = max(per_class, key=lambda c: ktimes[c][0])
+    d = per_class[dom]
+    traffic = recorded_traffic(dom, args.scale)
+    names = {"sig_small": "k_sig_small (out-degree <= 64, one thread per node)",
+             "sig_medium": "k_sig_chunk (out-degree 65..4096, CTA chunks)",
+             "sig_hub": "k_hub_chunk + k_hub_bucket (out-degree > 4096)",
+             "group": "k_group_insert", "verify": "k_group_verify", "renumber": "renumbering kernels"}
+    roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": d["achieved"], "peak": peak,
+                "unit": "GB/s", "frac": d["frac"], "peak_kind": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_call"] / d["launches_per_call"],
+                "avg_launch_ms": d["ms_per_call"] / d["launches_per_call"],
+                "launches_per_round": d["launches_per_call"]}
     round_achieved = round_bytes / (round_ms / 1000.0) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -270,6 +314,8 @@ def main():
                                "frac": round_achieved / peak, "avg_round_ms": round_ms,
                                "algorithmic_bytes": round_bytes},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
+            "kernel_roofline": {k: {"achieved": v["achieved"], "frac": v["frac"], "ms_per_call": v["ms_per_call"]}
+                                for k, v in per_class.items()},
             "gpu_launches": gpu_launches, "clocks": clk}
 
     # end to end through the public API: pinned host inputs -> build -> level k to host

@@ -131,7 +131,10 @@ typedef struct {
 } kbisim_result;
 
 /* Per-kernel device time collected when options.collect_timing = 1.
- * Indices are the KBISIM_KERNEL_* values. */
+ * Indices are the KBISIM_KERNEL_* values; total_ms is the time between CUDA
+ * events recorded around each group of launches of a class, launches the
+ * number of this library's kernels launched in that class (counted whether or
+ * not timing is on; clears done with cudaMemsetAsync are not counted). */
 enum {
   KBISIM_KERNEL_LABEL_GROUP = 0, /* level 0 grouping by node label */
   KBISIM_KERNEL_SIG_SMALL,       /* signatures of out-degree <= 64 */

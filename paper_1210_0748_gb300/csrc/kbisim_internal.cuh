@@ -29,7 +29,6 @@ constexpr int kSmallChunkThreads = 128;  // threads of the chunk kernel for out-
 constexpr int kChunkItems = 8;     // edges per thread
 constexpr int kChunkEdges = kChunkThreads * kChunkItems;  // 4096 = kBlockMax
 constexpr int kChunkMaxNodes = 64; // nodes per medium chunk (each has > kSmallMax edges)
-constexpr int kHubThreads = 512;   // threads of the hub bucket kernel
 constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
 constexpr int kHubChunk = kChunkEdges;  // hub edges per chunk CTA
 constexpr int kSmallClasses = 8;        // out-degree 0, 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64
@@ -168,8 +167,8 @@ struct Store {
   // degree classes (internal id ranges)
   uint64_t class_start[kNumClasses + 1] = {0};
   uint64_t n_hub = 0;
-  Buf mid_chunks;              // uint2 (first node, node count): whole medium nodes, two lists
-  uint64_t n_mid_chunks[2] = {0, 0};  // chunks for 128-thread and for 512-thread CTAs
+  Buf mid_chunks;              // uint2 (first node, node count): runs of whole nodes, three lists
+  uint64_t n_mid_chunks[3] = {0, 0, 0};  // out-degree 33..64, 65..1024, 1025..4096
   Buf hub_bits;                // uint32 [n_hub]  log2(bucket count)
   Buf hub_bbase;               // uint64 [n_hub+1] first bucket of each hub
   Buf hub_cap;                 // uint32 [n_hub]  key words a bucket of this hub can hold

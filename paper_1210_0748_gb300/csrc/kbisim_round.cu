@@ -88,12 +88,15 @@ void timer_destroy(Store& s) {
 namespace {
 
 // Records one CUDA event pair around the kernels launched in its scope.
+// Events around a group of launches of one kernel class; `kernels` is the
+// number of this library's kernels the group launches (clears by
+// cudaMemsetAsync are not counted).
 struct TimedScope {
   Store& s;
   int cls;
   KernelTimer::Rec rec;
-  TimedScope(Store& st, int c) : s(st), cls(c) {
-    s.launches[c] += 1;
+  TimedScope(Store& st, int c, int kernels) : s(st), cls(c) {
+    s.launches[c] += (uint64_t)kernels;
     if (!s.timing) return;
     if (!s.timer) s.timer = new KernelTimer();
     rec.cls = c;
@@ -410,21 +413,30 @@ __global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLau
 //     warp per node, and writes the node's distinct-key count and hash.
 // The key equal to the empty-slot marker is kept as a per-node flag.
 
-// A chunk CTA of NT threads takes up to NT * kChunkItems edges.
-template <int NT>
+// A chunk CTA of NT threads takes up to NT * kChunkItems edges of nodes with
+// out-degree >= MIN_DEG (> 32, so that 32 consecutive edges meet at most two
+// nodes).
+template <int NT, int MIN_DEG>
 struct ChunkShape {
+  static_assert(MIN_DEG > 32, "a warp step must meet at most two nodes");
   static constexpr int kEdges = NT * kChunkItems;
   static constexpr int kSlots = 2 * kEdges;
-  static constexpr int kMaxNodes = kEdges / (kSmallMax + 1) + 1;  // nodes of out-degree > kSmallMax
+  static constexpr int kMaxNodes = kEdges / MIN_DEG + 1;
 };
 
-template <typename K, int NT>
+template <typename K, int NT, int MIN_DEG>
 struct ChunkSmem {
-  K slot[ChunkShape<NT>::kSlots];
-  uint32_t off[ChunkShape<NT>::kMaxNodes + 1];  // node starts relative to the chunk's first edge
-  uint32_t cnt[ChunkShape<NT>::kMaxNodes];      // distinct keys written per node
-  uint32_t empty[ChunkShape<NT>::kMaxNodes];    // the node's key equal to KeyOps<K>::kEmpty was seen
+  using Shape = ChunkShape<NT, MIN_DEG>;
+  K slot[Shape::kSlots];
+  uint32_t off[Shape::kMaxNodes + 1];  // node starts relative to the chunk's first edge
+  uint32_t cnt[Shape::kMaxNodes];      // distinct keys written per node
+  uint32_t empty[Shape::kMaxNodes];    // the node's key equal to KeyOps<K>::kEmpty was seen
 };
+
+// Chunk kernel shapes: out-degree 33..64 and 65..1024 in 128-thread CTAs,
+// 1025..4096 and hub pieces in 512-thread CTAs.
+constexpr int kChunkMin64 = kSmallMax / 2 + 1, kChunkMin1K = kSmallMax + 1, kChunkMin4K = kWarp2Max + 1;
+constexpr int kChunkMinHub = kBlockMax + 1;
 
 __device__ __forceinline__ uint32_t key_h32(uint32_t k) { return k; }
 __device__ __forceinline__ uint32_t key_h32(uint64_t k) { return (uint32_t)(k >> 32) ^ (uint32_t)k; }
@@ -479,12 +491,12 @@ __device__ __forceinline__ bool region_insert(uint32_t base, uint32_t rb, uint32
   return false;
 }
 
-template <typename K, int NT>
-__device__ __forceinline__ void chunk_clear(ChunkSmem<K, NT>& sm, uint32_t slots) {
+template <typename K, int NT, int MIN_DEG>
+__device__ __forceinline__ void chunk_clear(ChunkSmem<K, NT, MIN_DEG>& sm, uint32_t slots) {
   uint4* s4 = reinterpret_cast<uint4*>(sm.slot);
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
   for (uint32_t i = threadIdx.x; i < slots * sizeof(K) / 16; i += NT) s4[i] = ones;
-  for (uint32_t i = threadIdx.x; i < (uint32_t)ChunkShape<NT>::kMaxNodes; i += NT) {
+  for (uint32_t i = threadIdx.x; i < (uint32_t)ChunkShape<NT, MIN_DEG>::kMaxNodes; i += NT) {
     sm.cnt[i] = 0;
     sm.empty[i] = 0;
   }
@@ -499,10 +511,10 @@ __device__ __forceinline__ void chunk_keys(const SigArgs& a, uint64_t ebase, uin
 // Lanes below `lane`.
 __device__ __forceinline__ unsigned lanes_below(uint32_t lane) { return (1u << lane) - 1u; }
 
-template <int NT, typename LabelT, typename K>
+template <int NT, int MIN_DEG, typename LabelT, typename K>
 __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks) {
   extern __shared__ __align__(16) char smem_raw[];
-  ChunkSmem<K, NT>& sm = *reinterpret_cast<ChunkSmem<K, NT>*>(smem_raw);
+  ChunkSmem<K, NT, MIN_DEG>& sm = *reinterpret_cast<ChunkSmem<K, NT, MIN_DEG>*>(smem_raw);
   const uint2 c = chunks[blockIdx.x];
   const uint64_t first = c.x;
   const uint32_t nn = c.y;
@@ -517,15 +529,19 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
   K* out = static_cast<K*>(a.sigkey) + ebase;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.slot);
   uint32_t j = 0;
-#pragma unroll
+  // one copy of the loop body: the keys rotate through key[0]
+#pragma unroll 1
   for (int t = 0; t < kChunkItems; ++t) {
     const uint32_t e = tid + t * NT;
+    const K kt = key[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kChunkItems; ++q) key[q] = key[q + 1];
     bool fresh = false;
     if (e < E) {
       while (sm.off[j + 1] <= e) ++j;
-      fresh = key[t] == KeyOps<K>::kEmpty
+      fresh = kt == KeyOps<K>::kEmpty
                   ? atomicExch(&sm.empty[j], 1u) == 0u
-                  : region_insert(sbase, 2 * sm.off[j], 2 * (sm.off[j + 1] - sm.off[j]), key[t]);
+                  : region_insert(sbase, 2 * sm.off[j], 2 * (sm.off[j + 1] - sm.off[j]), kt);
     }
     const unsigned fm = __ballot_sync(kFull, fresh);
     if (fm == 0u) continue;
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
     if (lane == 31 && fb) base = atomicAdd(&sm.cnt[jA + 1], (uint32_t)__popc(fb));
     const uint32_t bA = __shfl_sync(kFull, base, 0), bB = __shfl_sync(kFull, base, 31);
     if (fresh)
-      out[sm.off[j] + (inA ? bA + __popc(fa & lanes_below(lane)) : bB + __popc(fb & lanes_below(lane)))] = key[t];
+      out[sm.off[j] + (inA ? bA + __popc(fa & lanes_below(lane)) : bB + __popc(fb & lanes_below(lane)))] = kt;
   }
   __syncthreads();
   // hash terms: one warp per node over its distinct keys just written
@@ -592,13 +608,9 @@ constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memo
 
 template <typename K>
 __host__ __device__ constexpr size_t hub_chunk_smem() {
-  return sizeof(ChunkSmem<K, kChunkThreads>) + (size_t)kHubChunk * sizeof(K) + 2 * kHubSmemBuckets * sizeof(uint32_t);
+  return sizeof(ChunkSmem<K, kChunkThreads, kChunkMinHub>) + (size_t)kHubChunk * sizeof(K) + 2 * kHubSmemBuckets * sizeof(uint32_t);
 }
 
-template <typename K>
-__host__ __device__ constexpr size_t hub_ws_bytes() {
-  return team_set_bytes<K>(2 * kHubUcap, kHubUcap, kHubThreads);
-}
 
 template <typename K>
 __device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
@@ -608,8 +620,8 @@ __device__ __forceinline__ uint32_t hub_bucket(K k, uint32_t bits) {
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs h) {
   extern __shared__ __align__(16) char smem_raw[];
-  ChunkSmem<K, kChunkThreads>& sm = *reinterpret_cast<ChunkSmem<K, kChunkThreads>*>(smem_raw);
-  K* list = reinterpret_cast<K*>(smem_raw + sizeof(ChunkSmem<K, kChunkThreads>));
+  ChunkSmem<K, kChunkThreads, kChunkMinHub>& sm = *reinterpret_cast<ChunkSmem<K, kChunkThreads, kChunkMinHub>*>(smem_raw);
+  K* list = reinterpret_cast<K*>(smem_raw + sizeof(ChunkSmem<K, kChunkThreads, kChunkMinHub>));
   uint32_t* bcnt = reinterpret_cast<uint32_t*>(list + kHubChunk);
   uint32_t* bpos = bcnt + kHubSmemBuckets;
   const uint4 c = h.chunks[blockIdx.x];
@@ -627,18 +639,20 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
   K key[kChunkItems];
   chunk_keys<kChunkThreads, LabelT, K>(a, ebase, E, key);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.slot);
-#pragma unroll
+#pragma unroll 1
   for (int t = 0; t < kChunkItems; ++t) {
+    const K kt = key[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kChunkItems; ++q) key[q] = key[q + 1];
     bool fresh = false;
     if (tid + t * kChunkThreads < E)
-      fresh = key[t] == KeyOps<K>::kEmpty ? atomicExch(&sm.empty[0], 1u) == 0u
-                                          : region_insert(sbase, 0u, 2 * E, key[t]);
+      fresh = kt == KeyOps<K>::kEmpty ? atomicExch(&sm.empty[0], 1u) == 0u : region_insert(sbase, 0u, 2 * E, kt);
     const unsigned fm = __ballot_sync(kFull, fresh);
     if (fm == 0u) continue;
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&sm.cnt[0], (uint32_t)__popc(fm));
     base = __shfl_sync(kFull, base, 0);
-    if (fresh) list[base + __popc(fm & lanes_below(lane))] = key[t];
+    if (fresh) list[base + __popc(fm & lanes_below(lane))] = kt;
   }
   __syncthreads();
   const uint32_t U = sm.cnt[0];
@@ -664,13 +678,45 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
   }
 }
 
-// One CTA per hub bucket (grid-stride).
+// Insert k (!= kEmpty) into a power-of-two set of hmask + 1 slots at
+// shared-window address `base`, home slot from the key's low bits (the keys of
+// one hub bucket share their top bits); true iff this call put it there.
 template <typename K>
-__global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
-  extern __shared__ __align__(16) char smem[];
-  TeamSet<K> ts = carve_set<K>(smem, 2 * kHubUcap, kHubUcap);
-  __shared__ unsigned long long obase;
-  __shared__ unsigned int last;
+__device__ __forceinline__ bool pow2_insert(uint32_t base, uint32_t hmask, K k) {
+  uint32_t s = key_h32(k) & hmask;
+  for (uint32_t t = 0; t <= hmask; ++t) {
+    const uint32_t a = base + s * (uint32_t)sizeof(K);
+    K cur = lds_volatile(a, K());
+    if (cur == k) return false;
+    if (cur == KeyOps<K>::kEmpty) {
+      cur = atoms_cas(a, KeyOps<K>::kEmpty, k);
+      if (cur == KeyOps<K>::kEmpty) return true;
+      if (cur == k) return false;
+    }
+    s = (s + 1) & hmask;
+  }
+  return false;
+}
+
+constexpr int kBucketThreads = 256, kBucketItems = 8;
+
+template <typename K>
+struct BucketSmem {
+  K set[2 * kHubUcap];
+  K uniq[kHubUcap];
+  uint32_t cnt, empty, lo, hi, last;
+  unsigned long long obase;
+};
+
+// One CTA per hub bucket (grid-stride): distinct keys of the bucket into a
+// shared set and list, then appended at the hub's CSR offset with their term
+// sums; the last bucket of a hub writes the hub's count and hash.
+template <typename K>
+__global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
+  extern __shared__ __align__(16) char smem_raw[];
+  BucketSmem<K>& sm = *reinterpret_cast<BucketSmem<K>*>(smem_raw);
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.set);
   K* out = static_cast<K*>(a.sigkey);
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
     const uint32_t hub = h.bucket_hub[b];
@@ -678,58 +724,76 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_bucket(SigArgs a, HubArgs h
     const uint32_t cap = h.hub_cap[hub];
     const K* tmp = static_cast<const K*>(h.tmp) + h.hub_tbase[hub] + (b - h.hub_bbase[hub]) * cap;
     const uint32_t n = min(h.cursor[b], cap);
-    const int hcap = set_size_for(n, 2 * kHubUcap);
-    set_clear<kHubThreads>(ts, hcap, threadIdx.x);
+    uint32_t hcap = 64;
+    while (hcap < 2 * n) hcap <<= 1;
+    {
+      uint4* s4 = reinterpret_cast<uint4*>(sm.set);
+      const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+      for (uint32_t i = tid; i < hcap * sizeof(K) / 16; i += kBucketThreads) s4[i] = ones;
+    }
+    if (tid == 0) {
+      sm.cnt = 0;
+      sm.empty = 0;
+      sm.lo = 0;
+      sm.hi = 0;
+    }
     __syncthreads();
-    for (uint32_t base = 0; base < n; base += kHubThreads * 4) {
-      K keys[4];
+    for (uint32_t i0 = 0; i0 < n; i0 += kBucketThreads * kBucketItems) {
+      K kk[kBucketItems];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t i = base + threadIdx.x + kHubThreads * t;
-        keys[t] = i < n ? tmp[i] : (K)0;
+      for (int t = 0; t < kBucketItems; ++t) {
+        const uint32_t i = i0 + tid + t * kBucketThreads;
+        kk[t] = i < n ? tmp[i] : (K)0;
       }
+#pragma unroll 1
+      for (int t = 0; t < kBucketItems; ++t) {
+        const uint32_t i = i0 + tid + t * kBucketThreads;
+        const K k = kk[0];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (base + threadIdx.x + kHubThreads * t < n && set_insert(ts, hcap, keys[t])) {
-          const uint32_t q = atomicAdd(&ts.sh[0], 1u);
-          if (q < (uint32_t)kHubUcap) ts.uniq[q] = keys[t]; else ts.sh[2] = 1u;
-        }
+        for (int q = 0; q + 1 < kBucketItems; ++q) kk[q] = kk[q + 1];
+        bool fresh = false;
+        if (i < n) fresh = k == KeyOps<K>::kEmpty ? atomicExch(&sm.empty, 1u) == 0u : pow2_insert(sbase, hcap - 1, k);
+        const unsigned fm = __ballot_sync(kFull, fresh);
+        if (fm == 0u) continue;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&sm.cnt, (uint32_t)__popc(fm));
+        base = __shfl_sync(kFull, base, 0);
+        if (fresh) sm.uniq[base + __popc(fm & lanes_below(lane))] = k;
       }
     }
     __syncthreads();
-    if (ts.sh[2]) {  // more distinct keys than the bucket can hold: the host re-partitions
-      if (threadIdx.x == 0) atomicOr(a.err, kErrHubOverflow);
-      __syncthreads();
-      continue;
-    }
-    const uint32_t U = ts.sh[0];
-    if (threadIdx.x == 0) obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
+    const uint32_t U = sm.cnt;
+    if (tid == 0) sm.obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
     __syncthreads();
-    const uint64_t off = a.off[p] + obase;
+    const uint64_t off = a.off[p] + sm.obase;
     uint32_t lo = 0, hi = 0;
-    for (uint32_t i = threadIdx.x; i < U; i += kHubThreads) {
-      out[off + i] = ts.uniq[i];
-      const uint64_t tm = elem_term(ts.uniq[i], a.seed);
+    for (uint32_t i = tid; i < U; i += kBucketThreads) {
+      const K k = sm.uniq[i];
+      out[off + i] = k;
+      const uint64_t tm = elem_term(k, a.seed);
       lo += (uint32_t)tm;
       hi += (uint32_t)(tm >> 32);
     }
-    lo = team_sum<kHubThreads>(lo, ts.red, threadIdx.x);
-    hi = team_sum<kHubThreads>(hi, ts.red, threadIdx.x);
-    if (threadIdx.x == 0) {
-      atomicAdd(&h.hub_term[2 * hub], lo);
-      atomicAdd(&h.hub_term[2 * hub + 1], hi);
-      __threadfence();
-      const unsigned nb = 1u << (h.hub_bits[hub] + h.extra_bits);
-      last = atomicAdd(&h.hub_done[hub], 1u) == nb - 1u;
+    lo = __reduce_add_sync(kFull, lo);
+    hi = __reduce_add_sync(kFull, hi);
+    if (lane == 0) {
+      atomicAdd(&sm.lo, lo);
+      atomicAdd(&sm.hi, hi);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (tid == 0) {
+      atomicAdd(&h.hub_term[2 * hub], sm.lo);
+      atomicAdd(&h.hub_term[2 * hub + 1], sm.hi);
       __threadfence();
-      const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
-      const unsigned long long tsum = ((unsigned long long)atomicAdd(&h.hub_term[2 * hub + 1], 0u) << 32) |
-                                      atomicAdd(&h.hub_term[2 * hub], 0u);
-      a.ucnt[p] = (uint32_t)tot;
-      a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
+      const unsigned nb = 1u << (h.hub_bits[hub] + h.extra_bits);
+      if (atomicAdd(&h.hub_done[hub], 1u) == nb - 1u) {
+        __threadfence();
+        const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
+        const unsigned long long tsum = ((unsigned long long)atomicAdd(&h.hub_term[2 * hub + 1], 0u) << 32) |
+                                        atomicAdd(&h.hub_term[2 * hub], 0u);
+        a.ucnt[p] = (uint32_t)tot;
+        a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
+      }
     }
     __syncthreads();
   }
@@ -752,6 +816,7 @@ struct GroupArgs {
   uint32_t* rep;
   uint32_t* err;
   const uint8_t* alone;  // nodes alone in their previous block (may be null): heads, not grouped
+  int read_first;        // few distinct hashes shared by many nodes (level 0): read a slot before any atomic
 };
 
 __device__ __forceinline__ uint32_t table_insert(const GroupArgs& g, uint64_t h, uint32_t minid) {
@@ -759,6 +824,11 @@ __device__ __forceinline__ uint32_t table_insert(const GroupArgs& g, uint64_t h,
   const unsigned long long v = (fp << 32) | minid;
   uint32_t s = (uint32_t)(mix64(h) & g.tmask);
   for (uint64_t t = 0; t <= g.tmask; ++t) {
+    // a slot already holding this fingerprint with an id no larger needs no atomic
+    if (g.read_first) {
+      const unsigned long long seen = *(volatile unsigned long long*)&g.table[s];
+      if ((seen >> 32) == fp && seen != kEmpty64 && (uint32_t)seen <= minid) return s;
+    }
     const unsigned long long cur = atomicCAS(&g.table[s], (unsigned long long)kEmpty64, v);
     if (cur == kEmpty64) return s;
     if ((cur >> 32) == fp) {
@@ -958,7 +1028,7 @@ __global__ void k_mark_heads(RankArgs r) {
     if (h == (uint32_t)p) {
       const uint32_t o = r.p2o[p];
       atomicOr(&r.hbits[o >> 5], 1u << (o & 31));
-    } else {
+    } else if (!*(volatile uint8_t*)&r.member[h]) {  // large blocks: most members find it set
       r.member[h] = 1;
     }
     if (r.ucnt) {
@@ -1309,14 +1379,17 @@ Status scan64(Store& s, uint64_t* a, uint64_t n, uint64_t* copy) {
   return launch_check("scan64");
 }
 
+template <int NT, int MIN_DEG, typename LabelT, typename K>
+cudaError_t set_chunk_attr() {
+  return cudaFuncSetAttribute(k_sig_chunk<NT, MIN_DEG, LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(ChunkSmem<K, NT, MIN_DEG>));
+}
+
 template <typename LabelT, typename K>
 cudaError_t set_smem_attrs_label() {
-  cudaError_t e = cudaFuncSetAttribute(k_sig_chunk<kChunkThreads, LabelT, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(ChunkSmem<K, kChunkThreads>));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sig_chunk<kSmallChunkThreads, LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(ChunkSmem<K, kSmallChunkThreads>));
+  cudaError_t e = set_chunk_attr<kSmallChunkThreads, kChunkMin64, LabelT, K>();
+  if (e == cudaSuccess) e = set_chunk_attr<kSmallChunkThreads, kChunkMin1K, LabelT, K>();
+  if (e == cudaSuccess) e = set_chunk_attr<kChunkThreads, kChunkMin4K, LabelT, K>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_hub_chunk<LabelT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hub_chunk_smem<K>());
@@ -1329,7 +1402,7 @@ Status set_smem_attrs_for() {
 
   if (e == cudaSuccess) e = set_smem_attrs_label<uint32_t, K>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_ws_bytes<K>());
+    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BucketSmem<K>));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)verify_ws_bytes<K>());
@@ -1381,6 +1454,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   g.rep = ptr<uint32_t>(s.rep);
   g.err = ptr<uint32_t>(s.d_err);
   g.alone = use_alone ? ptr<uint8_t>(s.alone) : nullptr;
+  g.read_first = mode == 0 ? 1 : 0;
   VerifyArgs v;
   v.mode = mode;
   v.key64 = key64 ? 1 : 0;
@@ -1394,31 +1468,35 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.n_long = sc + 6;
   const int sms = sm_count(s.device);
   const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
+  {
+    TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
+    cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
+  }
+  v.out_list = ptr<uint32_t>(s.ulist[0]);
+  v.n_out = sc + 1;
   // only nodes not alone in their previous block are inserted
-  const uint64_t tcap = std::min<uint64_t>(s.tcap, table_capacity(use_alone ? na - std::min(na, s.n_alone) : na));
+  const uint64_t ins = use_alone ? na - std::min(na, s.n_alone) : na;
+  const uint64_t tcap = std::min<uint64_t>(s.tcap, table_capacity(ins));
   g.tmask = tcap - 1;
   {
-    TimedScope ts(s, KBISIM_KERNEL_OTHER);
+    TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
     cudaMemsetAsync(s.table.p, 0xFF, tcap * 8, s.stream);
-    cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
   }
   const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8);
   {
-    TimedScope ts(s, KBISIM_KERNEL_GROUP);
+    TimedScope ts(s, KBISIM_KERNEL_GROUP, na ? 1 : 0);
     if (na) k_group_insert<<<iblocks, kInsThreads, 0, s.stream>>>(g, nullptr, na);
   }
   if (!(st = launch_check("k_group_insert")).ok()) return st;
-  v.out_list = ptr<uint32_t>(s.ulist[0]);
-  v.n_out = sc + 1;
   {
-    TimedScope ts(s, KBISIM_KERNEL_VERIFY);
+    TimedScope ts(s, KBISIM_KERNEL_VERIFY, 1);
     k_group_verify<<<gblocks, 256, 0, s.stream>>>(g, v, nullptr, na);
   }
   if (!(st = launch_check("k_group_verify")).ok()) return st;
   uint64_t h[16];
   if (!(st = read_scalars(s, h)).ok()) return st;
   if (h[6]) {
-    TimedScope ts(s, KBISIM_KERNEL_VERIFY);
+    TimedScope ts(s, KBISIM_KERNEL_VERIFY, 1);
     const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
     if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g, v, h[6]);
     else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g, v, h[6]);
@@ -1439,7 +1517,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     v2.n_out = sc + 5;
     const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), (uint64_t)sms * 16);
     {
-      TimedScope ts(s, KBISIM_KERNEL_OTHER);
+      TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
       cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
       cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
       k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8),
@@ -1449,7 +1527,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     if (!(st = launch_check("collision repair")).ok()) return st;
     if (!(st = read_scalars(s, h)).ok()) return st;
     if (h[6]) {
-      TimedScope ts(s, KBISIM_KERNEL_OTHER);
+      TimedScope ts(s, KBISIM_KERNEL_OTHER, 1);
       const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
       if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g2, v2, h[6]);
       else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g2, v2, h[6]);
@@ -1477,7 +1555,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   r.pid = pid;
   r.stats = sc;
   {
-    TimedScope ts(s, KBISIM_KERNEL_RENUMBER);
+    TimedScope ts(s, KBISIM_KERNEL_RENUMBER, n ? 7 : 0);  // 4 kernels + the 3 of scan64
     if (n) {
       cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
       cudaMemsetAsync(s.member.p, 0, n, s.stream);
@@ -1542,37 +1620,45 @@ template <typename LabelT, typename K>
 Status run_signatures(Store& s, const SigArgs& a) {
   Status st;
   const int sms = sm_count(s.device);
-  SmallLaunch L;
-  uint32_t b = 0;
-  for (int c = 0; c < kSmallClasses; ++c) {
-    L.start[c] = s.class_start[c];
-    L.count[c] = s.class_start[c + 1] - s.class_start[c];
-    if (c == kSmallClasses - 1) b = 0;  // the last class runs as its own launch
-    L.bstart[c] = b;
-    b += (uint32_t)((L.count[c] + kSmallThreads - 1) / kSmallThreads);
-  }
-  L.bstart[kSmallClasses] = b;
+  // thread-per-node classes: 0..4 (out-degree <= 8) in one launch, 5 and 6
+  // (9..16, 17..32) in one launch each, so that each kernel carries only its
+  // own unrolled code; class 7 (33..64) runs as 128-thread chunks
+  auto small_launch = [&](int first, int last) {
+    SmallLaunch L;
+    uint32_t b = 0;
+    for (int c = 0; c < kSmallClasses; ++c) {
+      L.start[c] = s.class_start[c];
+      L.count[c] = s.class_start[c + 1] - s.class_start[c];
+      L.bstart[c] = b;
+      if (c >= first && c <= last) b += (uint32_t)((L.count[c] + kSmallThreads - 1) / kSmallThreads);
+    }
+    L.bstart[kSmallClasses] = b;
+    return L;
+  };
+  const SmallLaunch L04 = small_launch(0, 4), L5 = small_launch(5, 5), L6 = small_launch(6, 6);
+  const uint32_t n04 = L04.bstart[5], n5 = L5.bstart[6] - L5.bstart[5], n6 = L6.bstart[7] - L6.bstart[6];
   {
-    TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL);
-    // classes 0..6
-    uint32_t nb = 0;
-    for (int c = 0; c < kSmallClasses - 1; ++c) nb += (uint32_t)((L.count[c] + kSmallThreads - 1) / kSmallThreads);
-    if (nb) k_sig_small<0, kSmallClasses - 2, LabelT, K><<<nb, kSmallThreads, 0, s.stream>>>(a, L);
-    // class 7 (out-degree 33..64)
-    const uint32_t n7 = (uint32_t)((L.count[kSmallClasses - 1] + kSmallThreads - 1) / kSmallThreads);
-    if (n7) k_sig_small<kSmallClasses - 1, kSmallClasses - 1, LabelT, K><<<n7, kSmallThreads, 0, s.stream>>>(a, L);
+    TimedScope ts(s, KBISIM_KERNEL_SIG_SMALL, (n04 ? 1 : 0) + (n5 ? 1 : 0) + (n6 ? 1 : 0) + (s.n_mid_chunks[0] ? 1 : 0));
+    if (n04) k_sig_small<0, 4, LabelT, K><<<n04, kSmallThreads, 0, s.stream>>>(a, L04);
+    if (n5) k_sig_small<5, 5, LabelT, K><<<n5, kSmallThreads, 0, s.stream>>>(a, L5);
+    if (n6) k_sig_small<6, 6, LabelT, K><<<n6, kSmallThreads, 0, s.stream>>>(a, L6);
+    if (s.n_mid_chunks[0])
+      k_sig_chunk<kSmallChunkThreads, kChunkMin64, LabelT, K>
+          <<<(unsigned)s.n_mid_chunks[0], kSmallChunkThreads,
+             sizeof(ChunkSmem<K, kSmallChunkThreads, kChunkMin64>), s.stream>>>(a, ptr<uint2>(s.mid_chunks));
   }
   if (!(st = launch_check("k_sig_small")).ok()) return st;
-  if (s.n_mid_chunks[0] + s.n_mid_chunks[1]) {
-    TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM);
-    if (s.n_mid_chunks[0])
-      k_sig_chunk<kSmallChunkThreads, LabelT, K>
-          <<<(unsigned)s.n_mid_chunks[0], kSmallChunkThreads, sizeof(ChunkSmem<K, kSmallChunkThreads>), s.stream>>>(
-              a, ptr<uint2>(s.mid_chunks));
+  if (s.n_mid_chunks[1] + s.n_mid_chunks[2]) {
+    TimedScope ts(s, KBISIM_KERNEL_SIG_MEDIUM, (s.n_mid_chunks[1] ? 1 : 0) + (s.n_mid_chunks[2] ? 1 : 0));
     if (s.n_mid_chunks[1])
-      k_sig_chunk<kChunkThreads, LabelT, K>
-          <<<(unsigned)s.n_mid_chunks[1], kChunkThreads, sizeof(ChunkSmem<K, kChunkThreads>), s.stream>>>(
+      k_sig_chunk<kSmallChunkThreads, kChunkMin1K, LabelT, K>
+          <<<(unsigned)s.n_mid_chunks[1], kSmallChunkThreads,
+             sizeof(ChunkSmem<K, kSmallChunkThreads, kChunkMin1K>), s.stream>>>(
               a, ptr<uint2>(s.mid_chunks) + s.n_mid_chunks[0]);
+    if (s.n_mid_chunks[2])
+      k_sig_chunk<kChunkThreads, kChunkMin4K, LabelT, K>
+          <<<(unsigned)s.n_mid_chunks[2], kChunkThreads, sizeof(ChunkSmem<K, kChunkThreads, kChunkMin4K>),
+             s.stream>>>(a, ptr<uint2>(s.mid_chunks) + s.n_mid_chunks[0] + s.n_mid_chunks[1]);
   }
   if (!(st = launch_check("k_sig_chunk")).ok()) return st;
   if (s.n_hub) {
@@ -1593,12 +1679,12 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.hub_done = h.hub_term + 2 * s.n_hub;
       h.tmp = s.hub_tmp.p;
       {
-        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB);
+        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 2);
         cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
         k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
-        const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 4);
-        k_hub_bucket<K><<<g, kHubThreads, hub_ws_bytes<K>(), s.stream>>>(a, h, s.n_hub_buckets);
+        const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 8);
+        k_hub_bucket<K><<<g, kBucketThreads, sizeof(BucketSmem<K>), s.stream>>>(a, h, s.n_hub_buckets);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
@@ -1745,14 +1831,16 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
     if (!st.ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
   }
-  // medium nodes: runs of whole nodes; out-degree 65..1024 in chunks of at
-  // most 1024 edges (128-thread CTAs), 1025..4096 in chunks of at most 4096
-  s.n_mid_chunks[0] = s.n_mid_chunks[1] = 0;
-  const uint64_t mf = s.class_start[kClassWarp], mb = s.class_start[kClassBlock], me = s.class_start[kClassHub];
+  // out-degree 33..4096: runs of whole nodes; 33..64 and 65..1024 in chunks
+  // of at most 1024 edges (128-thread CTAs), 1025..4096 in chunks of at most
+  // 4096 edges (512-thread CTAs)
+  s.n_mid_chunks[0] = s.n_mid_chunks[1] = s.n_mid_chunks[2] = 0;
+  const uint64_t mf = s.class_start[kSmallClasses - 1], mw = s.class_start[kClassWarp],
+                 mb = s.class_start[kClassBlock], me = s.class_start[kClassHub];
   if (me > mf) {
     std::vector<uint64_t> moff(me - mf + 1);
     st = cuda_check(cudaMemcpyAsync(moff.data(), ptr<uint64_t>(s.offsets) + mf, (me - mf + 1) * 8,
-                                    cudaMemcpyDeviceToHost, s.stream), "medium offsets");
+                                    cudaMemcpyDeviceToHost, s.stream), "chunk offsets");
     if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
     if (!st.ok()) return st;
     std::vector<uint2> mc;
@@ -1764,10 +1852,15 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
         i = j;
       }
     };
-    pack(0, mb - mf, ChunkShape<kSmallChunkThreads>::kEdges, ChunkShape<kSmallChunkThreads>::kMaxNodes);
+    using S64 = ChunkShape<kSmallChunkThreads, kChunkMin64>;
+    using S1K = ChunkShape<kSmallChunkThreads, kChunkMin1K>;
+    using S4K = ChunkShape<kChunkThreads, kChunkMin4K>;
+    pack(0, mw - mf, S64::kEdges, S64::kMaxNodes);
     s.n_mid_chunks[0] = mc.size();
-    pack(mb - mf, me - mf, ChunkShape<kChunkThreads>::kEdges, ChunkShape<kChunkThreads>::kMaxNodes);
+    pack(mw - mf, mb - mf, S1K::kEdges, S1K::kMaxNodes);
     s.n_mid_chunks[1] = mc.size() - s.n_mid_chunks[0];
+    pack(mb - mf, me - mf, S4K::kEdges, S4K::kMaxNodes);
+    s.n_mid_chunks[2] = mc.size() - s.n_mid_chunks[0] - s.n_mid_chunks[1];
     if (!(st = ensure(s, s.mid_chunks, mc.size() * sizeof(uint2))).ok()) return st;
     st = cuda_check(cudaMemcpyAsync(s.mid_chunks.p, mc.data(), mc.size() * sizeof(uint2), cudaMemcpyHostToDevice,
                                     s.stream), "medium chunks");
@@ -1798,7 +1891,7 @@ Status compute_level0(Store& s) {
   const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16);
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
   {
-    TimedScope ts(s, KBISIM_KERNEL_LABEL_GROUP);
+    TimedScope ts(s, KBISIM_KERNEL_LABEL_GROUP, s.n_alive ? 1 : 0);
     if (s.n_alive)
       k_label_hash<<<blocks, 256, 0, s.stream>>>(s.n_alive, ptr<uint32_t>(s.nlabel), ptr<uint64_t>(s.hash),
                                                  s.seed, s.hash_mask);

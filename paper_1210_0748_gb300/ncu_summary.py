@@ -1,0 +1,148 @@
+"""Summaries of an ncu launch list of one refinement (``python -m
+paper_1210_0748_gb300.ncu_summary CSV ...``).
+
+The CSV comes from ``ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
+dram__bytes_write.sum --csv`` over ``bench.py --steps 1 --warmup 0``: every
+launch of the graph load and of one refinement (level 0 and each round).
+Launches before the first ``k_label_hash`` belong to the load and are left
+out.  Two outputs:
+
+* a Markdown table per kernel (launches, total time, share, DRAM bytes);
+* a JSON record of DRAM bytes per call of each kernel class (per round for the
+  signature classes, per level for grouping, verification and renumbering),
+  stamped with a digest of the kernel sources, which ``bench.py`` reports as
+  the measured traffic of the dominant class while the sources are unchanged.
+
+Per-launch times under ncu are cold-cache and serialised: compare shares, not
+absolute times.
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import csv
+import hashlib
+import json
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+
+# kernel name -> class of the library's timing (kbisim_kernel_times)
+CLASS_OF = [
+    (r"k_label_hash", "label_group"),
+    (r"k_sig_small", "sig_small"),
+    (r"k_sig_chunk", "sig_medium"),
+    (r"k_hub_chunk|k_hub_bucket", "sig_hub"),
+    (r"k_group_insert", "group"),
+    (r"k_group_verify|k_verify_long", "verify"),
+    (r"k_mark_heads|k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill", "renumber"),
+]
+
+UNITS = {"ns": 1e-9, "nsecond": 1e-9, "us": 1e-6, "usecond": 1e-6, "ms": 1e-3, "msecond": 1e-3,
+         "s": 1.0, "second": 1.0, "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+         "KB": 1e3, "MB": 1e6, "GB": 1e9}
+
+
+def source_digest() -> str:
+    """sha256 over the kernel sources (file names and contents)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(PKG, "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def short_name(name: str) -> str:
+    """Kernel name with its template arguments, without namespaces and parameters."""
+    m = re.search(r"(k_[A-Za-z_0-9]+)(<[^(]*>)?\(", name)
+    return (m.group(1) + (m.group(2) or "")) if m else name[:60]
+
+
+def load(path: str):
+    """Launches in order: list of (id, name, {metric: value in s or bytes})."""
+    rows = list(csv.reader(open(path)))
+    hdr = None
+    out = collections.OrderedDict()
+    for r in rows:
+        if r and r[0] == "ID":
+            hdr = r
+            continue
+        if not hdr or len(r) != len(hdr):
+            continue
+        d = dict(zip(hdr, r))
+        key = int(d["ID"])
+        v = float(d["Metric Value"].replace(",", "")) * UNITS.get(d["Metric Unit"], 1.0)
+        ent = out.setdefault(key, [short_name(d["Kernel Name"]), {}])
+        ent[1][d["Metric Name"]] = v
+    return [(k, v[0], v[1]) for k, v in out.items()]
+
+
+def class_of(name: str):
+    for pat, cls in CLASS_OF:
+        if re.match(pat, name):
+            return cls
+    return None
+
+
+def summarise(launches, rounds: int):
+    first = next((i for i, (_, n, _) in enumerate(launches) if n.startswith("k_label_hash")), 0)
+    refine = launches[first:]
+    per_kernel = collections.OrderedDict()
+    per_class = collections.defaultdict(float)
+    total_t = 0.0
+    for _, name, m in refine:
+        t = m.get("gpu__time_duration.sum", 0.0)
+        b = m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+        k = per_kernel.setdefault(name, [0, 0.0, 0.0])
+        k[0] += 1
+        k[1] += t
+        k[2] += b
+        total_t += t
+        cls = class_of(name)
+        if cls:
+            per_class[cls] += b
+    calls = {c: (rounds if c.startswith("sig") else rounds + 1) for c in per_class}
+    calls["label_group"] = 1
+    per_call = {c: per_class[c] / max(calls[c], 1) for c in per_class}
+    return per_kernel, total_t, per_call
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("csv")
+    ap.add_argument("--rounds", type=int, required=True, help="rounds the profiled refinement ran")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--workload", default="")
+    ap.add_argument("--command", default="")
+    ap.add_argument("--md", help="write the per-kernel table here")
+    ap.add_argument("--traffic", help="write the per-class DRAM bytes record here")
+    a = ap.parse_args()
+    per_kernel, total_t, per_call = summarise(load(a.csv), a.rounds)
+    lines = ["# Launch list: one refinement, %s" % a.workload, "",
+             "Command: `%s`" % a.command, "",
+             "%d rounds; per-launch times are cold-cache and serialised (compare shares)." % a.rounds, "",
+             "| kernel | launches | total ms | share | DRAM MB |", "|---|---:|---:|---:|---:|"]
+    for name, (n, t, b) in sorted(per_kernel.items(), key=lambda kv: -kv[1][1]):
+        lines.append("| `%s` | %d | %.3f | %.1f%% | %.1f |" % (name, n, t * 1e3, 100 * t / total_t, b / 1e6))
+    lines += ["", "DRAM bytes per call of each kernel class (per round for signatures, per level otherwise):", ""]
+    for c, b in sorted(per_call.items()):
+        lines.append("* %s: %.1f MB" % (c, b / 1e6))
+    text = "\n".join(lines) + "\n"
+    if a.md:
+        with open(a.md, "w") as f:
+            f.write(text)
+    else:
+        print(text)
+    if a.traffic:
+        rec = {"source_sha256": source_digest(), "scale": a.scale, "workload": a.workload,
+               "command": a.command, "rounds": a.rounds,
+               "dram_bytes_per_round": {c: round(b) for c, b in per_call.items()}}
+        with open(a.traffic, "w") as f:
+            json.dump(rec, f, indent=1)
+            f.write("\n")
+
+
+if __name__ == "__main__":
+    main()
