@@ -164,7 +164,10 @@ const char *kbisim_last_error(const kbisim_handle *h);
 
 /* Copy a graph into the handle (building the CSR-by-source edge table when
  * COO is given) and drop any previous graph and levels.  Validates ids
- * (INVALID_ARG if a node id >= num_nodes or num_nodes >= 2^32 - 1). */
+ * (INVALID_ARG if a node id >= num_nodes or num_nodes >= 2^32 - 1).  A handle
+ * without an HBM budget keeps its device buffers (including the staging of
+ * host inputs) for the next load, so reloading graphs of similar size
+ * allocates nothing; with a budget they are released and allocated again. */
 int kbisim_load(kbisim_handle *h, const kbisim_graph *g);
 
 /* Compute levels 0..k of the loaded graph (Algorithm 1, Build_Bisim).

@@ -68,10 +68,23 @@ unsigned grid(uint64_t work, unsigned per) {
 }
 
 // --- load kernels -----------------------------------------------------------
+// Every id < n.  Four ids per load when the array is 16-byte aligned.
 __global__ void k_check_ids(uint64_t m, uint64_t n, const uint32_t* a, uint32_t* err) {
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x)
-    if (a[e] >= n) atomicOr(err, kErrBadInput);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  bool bad = false;
+  uint64_t head = 0;
+  if ((reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+    const uint64_t m4 = m / 4;
+    const uint4* a4 = reinterpret_cast<const uint4*>(a);
+    for (uint64_t i = t0; i < m4; i += stride) {
+      const uint4 v = a4[i];
+      bad |= (v.x >= n) | (v.y >= n) | (v.z >= n) | (v.w >= n);
+    }
+    head = m4 * 4;
+  }
+  for (uint64_t e = head + t0; e < m; e += stride) bad |= a[e] >= n;
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrBadInput);
 }
 
 __global__ void k_check_offsets(uint64_t n, uint64_t m, const uint64_t* off, uint32_t* err) {
@@ -84,11 +97,31 @@ __global__ void k_check_offsets(uint64_t n, uint64_t m, const uint64_t* off, uin
   }
 }
 
+// Largest label.  16 bytes per load when the array is 16-byte aligned (byte
+// or half-word maxima by SIMD-in-register max, __vmaxu4 / __vmaxu2).
 template <typename T>
 __global__ void k_label_max(uint64_t m, const T* lab, unsigned int* mx) {
   unsigned int v = 0;
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x)
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint64_t head = 0;
+  if ((reinterpret_cast<uintptr_t>(lab) & 15) == 0) {
+    constexpr uint64_t kPer = 16 / sizeof(T);
+    const uint64_t mv = m / kPer;
+    const uint4* l4 = reinterpret_cast<const uint4*>(lab);
+    unsigned int w = 0;
+    for (uint64_t i = t0; i < mv; i += stride) {
+      const uint4 q = l4[i];
+      if (sizeof(T) == 1) w = __vmaxu4(w, __vmaxu4(__vmaxu4(q.x, q.y), __vmaxu4(q.z, q.w)));
+      else if (sizeof(T) == 2) w = __vmaxu2(w, __vmaxu2(__vmaxu2(q.x, q.y), __vmaxu2(q.z, q.w)));
+      else w = max(w, max(max(q.x, q.y), max(q.z, q.w)));
+    }
+    if (sizeof(T) == 1) v = max(max(w & 0xFF, (w >> 8) & 0xFF), max((w >> 16) & 0xFF, w >> 24));
+    else if (sizeof(T) == 2) v = max(w & 0xFFFF, w >> 16);
+    else v = w;
+    head = mv * kPer;
+  }
+  for (uint64_t e = head + t0; e < m; e += stride)
     v = max(v, (unsigned int)lab[e]);
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
   if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
@@ -204,17 +237,23 @@ Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned 
   return cuda_check(cudaGetLastError(), "scan");
 }
 
-void free_graph(Store& s) {
+// Drop the graph and its levels.  With keep_buffers (a handle without an HBM
+// budget, between loads) the device buffers stay allocated for the next graph.
+void free_graph(Store& s, bool keep_buffers) {
   Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.p2o, &s.o2p, &s.mid_chunks, &s.hub_bits,
                  &s.hub_bbase, &s.hub_cap, &s.hub_tbase, &s.hub_chunks, &s.sigkey, &s.ucnt, &s.hash, &s.table,
                  &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.hbits, &s.member, &s.alone, &s.hword, &s.bsum,
-                 &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_tmp, &s.alive_o};
-  for (Buf* b : bufs) release(s, *b);
-  for (Buf& b : s.level) release(s, b);
-  for (Buf& b : s.out_level) release(s, b);
-  s.level.clear();
-  s.out_level.clear();
-  s.out_valid.clear();
+                 &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_tmp, &s.alive_o,
+                 &s.rl_tcnt, &s.rl_hot, &s.rl_ost};
+  if (!keep_buffers) {
+    for (Buf* b : bufs) release(s, *b);
+    for (Buf& b : s.level) release(s, b);
+    for (Buf& b : s.out_level) release(s, b);
+    for (Buf& b : s.stage) release(s, b);
+    s.level.clear();
+    s.out_level.clear();
+  }
+  for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
   s.counts.clear();
   s.stats.clear();
   s.has_graph = false;
@@ -250,13 +289,16 @@ uint32_t bits_needed(uint64_t v) {  // bits for values 0..v
   return b;
 }
 
-// Temporary device buffers of one load, released on every exit path.
+// Staging buffers of a load (host inputs, COO grouping).  Kept in the store
+// between loads when the handle has no HBM budget, released at the end of the
+// load otherwise.
 struct Temps {
   Store& s;
-  Buf b[8];
-  explicit Temps(Store& st) : s(st) {}
+  Buf* b;
+  explicit Temps(Store& st) : s(st), b(st.stage) {}
   ~Temps() {
-    for (Buf& x : b) release(s, x);
+    if (s.budget)
+      for (int i = 0; i < kStageBufs; ++i) release(s, b[i]);
   }
 };
 
@@ -273,7 +315,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   if (m && (!g->dst || !g->edge_label)) return Status::Err(KBISIM_ERR_INVALID_ARG, "dst/edge_label is NULL");
   if (m && !g->offsets && !g->src) return Status::Err(KBISIM_ERR_INVALID_ARG, "need offsets or src");
   if (m && !n) return Status::Err(KBISIM_ERR_INVALID_ARG, "edges without nodes");
-  free_graph(s);
+  free_graph(s, s.budget == 0);
   Status st;
   const bool dev = g->on_device != 0;
   if (!(st = ensure(s, s.d_err, 64)).ok()) return st;
@@ -332,7 +374,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   const unsigned int maxlab = hv[4];
   if (!g->offsets) {
     // COO: counting sort by source into temporary CSR buffers
-    Buf csr_dst, csr_lab;
+    Buf &csr_dst = t.b[7], &csr_lab = t.b[8];
     if (!(st = ensure(s, off_b, (n + 1) * 8)).ok()) return st;
     if (!(st = ensure(s, cur_b, (n + 1) * 8)).ok()) return st;
     unsigned long long* off = ptr<unsigned long long>(off_b);
@@ -342,7 +384,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
     off0 = ptr<uint64_t>(off_b);
     if (m) {
       if (!(st = ensure(s, csr_dst, m * 4)).ok()) return st;
-      if (!(st = ensure(s, csr_lab, m * w)).ok()) { release(s, csr_dst); return st; }
+      if (!(st = ensure(s, csr_lab, m * w)).ok()) return st;
       const unsigned gb = grid(m, 256);
       unsigned long long* cur = ptr<unsigned long long>(cur_b);
       if (w == 1)
@@ -356,17 +398,10 @@ Status load_graph(Store& s, const kbisim_graph* g) {
                                                         cur, ptr<uint32_t>(csr_dst), ptr<uint32_t>(csr_lab));
       st = cuda_check(cudaGetLastError(), "place edges");
       if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-      if (!st.ok()) {
-        release(s, csr_dst);
-        release(s, csr_lab);
-        return st;
-      }
+      if (!st.ok()) return st;
       // the grouped copies replace the staged ones
-      release(s, dst_b);
-      release(s, lab_b);
-      release(s, src_b);
-      dst_b = csr_dst;
-      lab_b = csr_lab;
+      std::swap(dst_b, csr_dst);
+      std::swap(lab_b, csr_lab);
       dst_in = ptr<uint32_t>(dst_b);
       lab_in = lab_b.p;
     }
@@ -376,7 +411,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   s.label8 = maxlab < 256;
   s.label_bits = bits_needed(maxlab);
   if (!(st = relabel_graph(s, off0, dst_in, lab_in, nlab0, nullptr, w)).ok()) {
-    free_graph(s);
+    free_graph(s, s.budget == 0);
     return st;
   }
   s.has_graph = true;
@@ -550,7 +585,7 @@ void kbisim_destroy(kbisim_handle* h) {
   kb::Store& s = h->s;
   cudaSetDevice(s.device);
   cudaStreamSynchronize(s.stream);
-  kb::free_graph(s);
+  kb::free_graph(s, false);
   kb::release(s, s.d_scalars);
   kb::release(s, s.d_err);
   if (s.h_scalars.p) cudaFreeHost(s.h_scalars.p);

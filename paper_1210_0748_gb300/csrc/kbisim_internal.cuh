@@ -214,6 +214,9 @@ struct Store {
   Buf bucket_hub;              // uint32 [buckets] hub of each bucket
   Buf hub_acc;                 // per hub: keys written, term sum (uint64), buckets done (uint32)
   Buf hub_tmp;                 // key words [hub_tmp_words]: fixed-capacity hub buckets
+  static constexpr int kStageBufsN = 9;
+  Buf stage[kStageBufsN];      // staging of host inputs and COO grouping (kbisim_load)
+  Buf rl_tcnt, rl_hot, rl_ost; // relabelling temporaries
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars
@@ -237,6 +240,8 @@ struct Status {
     return s;
   }
 };
+
+constexpr int kStageBufs = Store::kStageBufsN;
 
 // Allocation helpers (kbisim_api.cu)
 Status ensure(Store& s, Buf& b, size_t bytes);

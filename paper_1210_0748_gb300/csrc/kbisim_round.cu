@@ -1158,7 +1158,7 @@ __device__ __forceinline__ int node_class(uint64_t o, uint64_t n, const uint64_t
 // edge, put into kHotBuckets buckets; it affects speed only, never results.
 constexpr int kHotBuckets = 8;
 constexpr int kNumOrder = kNumClasses * kHotBuckets;
-constexpr int kHotSampleShift = 4;
+constexpr int kHotSampleShift = 6;
 
 __device__ __forceinline__ int hot_bucket(uint32_t c) {
   return c >= 1024 ? 0 : c >= 256 ? 1 : c >= 64 ? 2 : c >= 16 ? 3 : c >= 4 ? 4 : c >= 2 ? 5 : c >= 1 ? 6 : 7;
@@ -1236,13 +1236,18 @@ __global__ void k_relabel_nodes(uint64_t n, const uint32_t* p2o, const uint64_t*
 // Copy out-edges to the segment of their source's internal id, relabelling
 // targets: one thread per original node of out-degree <= 32 (reads stream in
 // order), one warp per larger node.
+// Nodes of out-degree <= kSmallMax (any class, deleted nodes included): one
+// thread per node in internal order, so the writes of a warp fill one
+// contiguous range of the new edge table.
 template <typename TI, typename TO>
-__global__ void k_relabel_edges_small(uint64_t n, const uint32_t* o2p, const uint64_t* off0, const uint32_t* dst0,
-                                      const TI* lab0, const uint64_t* off, uint32_t* dst, TO* lab) {
-  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+__global__ void k_relabel_edges_small(uint64_t n, const uint32_t* p2o, const uint32_t* o2p, const uint64_t* off0,
+                                      const uint32_t* dst0, const TI* lab0, const uint64_t* off, uint32_t* dst,
+                                      TO* lab) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t o = p2o[p];
     const uint64_t s0 = off0[o], d = off0[o + 1] - s0;
     if (d > (uint64_t)kSmallMax) continue;
-    const uint64_t s1 = off[o2p[o]];
+    const uint64_t s1 = off[p];
     for (uint64_t i = 0; i < d; ++i) {
       dst[s1 + i] = o2p[dst0[s0 + i]];
       lab[s1 + i] = (TO)lab0[s0 + i];
@@ -1289,7 +1294,8 @@ void relabel_edges(Store& s, const uint64_t* off0, const uint32_t* dst0, const T
   const uint64_t* off = ptr<uint64_t>(s.offsets);
   uint32_t* dst = ptr<uint32_t>(s.dst);
   const unsigned g1 = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
-  k_relabel_edges_small<TI, TO><<<g1, 256, 0, s.stream>>>(n, o2p, off0, dst0, lab0, off, dst, lab);
+  k_relabel_edges_small<TI, TO><<<g1, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off, dst,
+                                                         lab);
   const uint64_t pf = s.class_start[kClassWarp], pe = s.class_start[kClassHub];
   if (pe > pf) {
     const unsigned g2 = (unsigned)std::min<uint64_t>(grid_for((pe - pf) * 32, 256), (uint64_t)sms * 32);
@@ -1742,11 +1748,15 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   const uint64_t n = s.n, m = s.m;
   const int sms = sm_count(s.device);
   const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
-  Buf tcnt, hot, ost;
+  // temporaries of the relabelling (kept between loads unless the handle has
+  // an HBM budget)
+  Buf &tcnt = s.rl_tcnt, &hot = s.rl_hot, &ost = s.rl_ost;
   auto fail = [&](Status e) {
-    release(s, tcnt);
-    release(s, hot);
-    release(s, ost);
+    if (s.budget) {
+      release(s, tcnt);
+      release(s, hot);
+      release(s, ost);
+    }
     return e;
   };
   if (!(st = ensure(s, tcnt, ntiles * kNumOrder * 8)).ok()) return fail(st);
