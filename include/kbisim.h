@@ -206,6 +206,35 @@ typedef struct {
 int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_result *out,
                   uint64_t *missing_deletes);
 
+/* Batched build: many independent graphs refined together, one sequence of
+ * kernel launches per round for all of them.  The paper has no counterpart
+ * (it builds one graph at a time); each graph's result is that of
+ * kbisim_build on the graph alone.  `g` holds the graphs as one graph whose
+ * node ids are grouped by graph: graph j owns ids graph_start[j] ..
+ * graph_start[j+1] - 1 (graph_start: host memory, num_graphs + 1 entries,
+ * graph_start[0] = 0, non-decreasing, graph_start[num_graphs] =
+ * g->num_nodes; empty graphs are allowed), and every edge joins two nodes of
+ * one graph.  Graph j is refined to k[j] levels (host memory, num_graphs
+ * entries), with the handle's early-stop setting applied to graph j's own
+ * block counts.  Identifiers of graph j are canonical within graph j (blocks
+ * ranked by their smallest node id, counted from graph_start[j]).  The batch
+ * replaces any graph and levels held by the handle (kbisim_pids then returns
+ * levels of the union of the graphs).  Errors: INVALID_ARG (num_graphs == 0,
+ * bad graph_start, k[j] > KBISIM_MAX_K, an edge between two graphs), and the
+ * errors of kbisim_build. */
+int kbisim_build_many(kbisim_handle *h, const kbisim_graph *g, const uint64_t *graph_start,
+                      uint32_t num_graphs, const uint32_t *k);
+
+/* Level `level` (0..k[graph]) of graph `graph` of the last kbisim_build_many,
+ * into dst[graph_start[graph+1] - graph_start[graph]] (host memory when
+ * dst_on_device = 0).  Errors: STATE (no batched result), INVALID_ARG. */
+int kbisim_many_pids(kbisim_handle *h, uint32_t graph, uint32_t level, uint32_t *dst, int dst_on_device);
+
+/* Rounds computed for graph `graph` (its own early stop) into *rounds_run,
+ * and its block counts of levels 0..k[graph] into counts (host memory,
+ * k[graph] + 1 entries); either may be NULL.  Errors: STATE, INVALID_ARG. */
+int kbisim_many_info(kbisim_handle *h, uint32_t graph, uint32_t *rounds_run, uint64_t *counts);
+
 /* Copy level `level` (0..k of the last result) into dst[num_nodes]
  * (host memory when dst_on_device = 0).  Errors: STATE, INVALID_ARG. */
 int kbisim_pids(kbisim_handle *h, uint32_t level, uint32_t *dst, int dst_on_device);

@@ -263,6 +263,8 @@ void free_graph(Store& s, bool keep_buffers) {
   s.computed = 0;
   s.n = s.m = s.n_alive = 0;
   s.n_hub = 0;
+  s.many.valid = false;
+  s.many.levels = 0;
 }
 
 Status copy_in(Store& s, void* dstp, const void* srcp, size_t bytes, bool on_device) {
@@ -465,6 +467,7 @@ Status run_rounds(Store& s, uint32_t from, uint32_t k) {
     if (!(st = compute_round(s, i)).ok()) return st;
     s.computed = i;
     s.rounds_run = i;
+    if (s.level_hook && !(st = s.level_hook(s, i)).ok()) return st;
     if (s.counts[i] == s.counts[i - 1]) {
       s.stable = true;
       if (s.early_stop) break;
@@ -485,6 +488,7 @@ Status refine(Store& s, uint32_t k, kbisim_result* out) {
   s.rounds_run = 0;
   s.stats.clear();
   if (!(st = compute_level0(s)).ok()) return st;
+  if (s.level_hook && !(st = s.level_hook(s, 0)).ok()) return st;
   for (uint32_t i = 1; i <= k; ++i) {
     if (s.early_stop && s.stable) break;
     if (!(st = ensure_levels(s, i)).ok()) return st;
@@ -586,6 +590,7 @@ void kbisim_destroy(kbisim_handle* h) {
   cudaSetDevice(s.device);
   cudaStreamSynchronize(s.stream);
   kb::free_graph(s, false);
+  kb::many_release(s);
   kb::release(s, s.d_scalars);
   kb::release(s, s.d_err);
   if (s.h_scalars.p) cudaFreeHost(s.h_scalars.p);
@@ -605,6 +610,37 @@ int kbisim_refine(kbisim_handle* h, uint32_t k, kbisim_result* out) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
   cudaSetDevice(h->s.device);
   return finish(h, kb::refine(h->s, k, out));
+}
+
+int kbisim_build_many(kbisim_handle* h, const kbisim_graph* g, const uint64_t* graph_start, uint32_t num_graphs,
+                      const uint32_t* k) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  kb::Store& s = h->s;
+  uint32_t kmax = 0;
+  Status st = kb::many_check_args(g, graph_start, num_graphs, k, &kmax);
+  if (st.ok()) st = kb::load_graph(s, g);
+  if (st.ok()) st = kb::many_setup(s, graph_start, num_graphs, k);
+  if (st.ok()) {
+    kbisim_result r;
+    s.level_hook = kb::many_level;
+    st = kb::refine(s, kmax, &r);
+    s.level_hook = nullptr;
+    if (st.ok()) kb::many_finish(s);
+  }
+  if (!st.ok()) s.many.valid = false;
+  return finish(h, st);
+}
+
+int kbisim_many_pids(kbisim_handle* h, uint32_t graph, uint32_t level, uint32_t* dst, int dst_on_device) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  cudaSetDevice(h->s.device);
+  return finish(h, kb::many_pids(h->s, graph, level, dst, dst_on_device != 0));
+}
+
+int kbisim_many_info(kbisim_handle* h, uint32_t graph, uint32_t* rounds_run, uint64_t* counts) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  return finish(h, kb::many_info(h->s, graph, rounds_run, counts));
 }
 
 int kbisim_build(kbisim_handle* h, const kbisim_graph* g, uint32_t k, kbisim_result* out) {

@@ -131,6 +131,27 @@ struct Buf {
 
 struct KernelTimer;  // per-kernel CUDA event timing (kbisim_round.cu)
 
+// Batched build state (kbisim_many.cu): graph j of the batch owns original
+// ids start[j] .. start[j+1]-1 of the loaded union.
+struct ManyState {
+  bool valid = false;
+  uint32_t G = 0;
+  std::vector<uint64_t> start;                 // [G+1]
+  std::vector<uint32_t> k;                     // [G]
+  std::vector<uint32_t> rounds;                // [G] per-graph rounds (own early stop)
+  std::vector<std::vector<uint64_t>> counts;   // [level][G] per-graph block counts
+  uint32_t levels = 0;                         // union levels renumbered per graph
+  std::vector<Buf> lvl;                        // per level: uint32 [n] per-graph ids, original order
+  Buf dstart;                                  // uint64 [G+1]
+  Buf gid, gidp;                               // uint32 [n] graph of each original / internal node
+  Buf tkey, tmin, slot;                        // (graph, union block) -> smallest original id
+  Buf hbits, hword, cnt;                       // head bitmap, per-word prefix, per-graph prefix
+};
+
+struct Store;
+struct Status;
+using LevelHook = Status (*)(Store&, uint32_t);
+
 // The device graph store plus all scratch a round needs.  One per handle.
 //
 // Node ids are relabelled once per graph: internal id p orders the alive
@@ -221,6 +242,9 @@ struct Store {
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars
 
+  ManyState many;               // batched build (kbisim_build_many)
+  LevelHook level_hook = nullptr;  // called after each computed level (batched build)
+
   size_t bytes_held = 0;
   KernelTimer* timer = nullptr;
   double total_ms[KBISIM_KERNEL_COUNT] = {0};
@@ -263,5 +287,18 @@ Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
 Status unpermute_level(Store& s, uint32_t level, uint32_t* dst);
 Status timer_collect(Store& s);
 void timer_destroy(Store& s);
+// Exclusive prefix sum of a uint64 array in place (kbisim_round.cu).
+Status scan_u64(Store& s, uint64_t* a, uint64_t n);
+
+// Batched build (kbisim_many.cu): many_check_args before the union is loaded,
+// many_setup after it, then a refinement with many_level as the level hook.
+Status many_check_args(const kbisim_graph* g, const uint64_t* start, uint32_t G, const uint32_t* k,
+                       uint32_t* kmax);
+Status many_setup(Store& s, const uint64_t* start, uint32_t G, const uint32_t* k);
+Status many_level(Store& s, uint32_t level);
+void many_finish(Store& s);
+Status many_pids(Store& s, uint32_t graph, uint32_t level, uint32_t* dst, bool dst_on_device);
+Status many_info(const Store& s, uint32_t graph, uint32_t* rounds_run, uint64_t* counts);
+void many_release(Store& s);
 
 }  // namespace kb

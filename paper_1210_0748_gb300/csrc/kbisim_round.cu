@@ -1741,6 +1741,8 @@ uint32_t bits_for(uint64_t v) {  // bits needed to represent values 0..v
 // ---------------------------------------------------------------------------
 // Relabelling and degree classes (once per graph)
 // ---------------------------------------------------------------------------
+Status scan_u64(Store& s, uint64_t* a, uint64_t n) { return scan64(s, a, n, nullptr); }
+
 Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const void* lab0,
                      const uint32_t* nlab0, const uint8_t* alive0, uint32_t lab_bytes) {
   Status st = set_smem_attrs(s.device);

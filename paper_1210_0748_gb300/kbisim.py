@@ -106,7 +106,38 @@ SIGNATURES = {
                                               ctypes.POINTER(RoundStats)]),
     "kbisim_label_partition_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "kbisim_build_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_void_p,
+                                         ctypes.c_uint32, ctypes.c_void_p]),
+    "kbisim_many_pids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_int]),
+    "kbisim_many_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.c_void_p]),
 }
+
+
+def concat_graphs(graphs):
+    """Disjoint union of CSR graphs for ``kbisim_build_many``: node ids of graph
+    j shifted by the nodes before it.  Returns (graph, node starts [G+1])."""
+    from .synth import Graph
+    n = np.array([g.num_nodes for g in graphs], dtype=np.int64)
+    m = np.array([g.num_edges for g in graphs], dtype=np.int64)
+    starts = np.zeros(len(graphs) + 1, dtype=np.uint64)
+    starts[1:] = np.cumsum(n)
+    ebase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    ebase[1:] = np.cumsum(m)
+    wide = any(g.edge_label.dtype != np.uint8 for g in graphs)
+    off = np.empty(int(starts[-1]) + 1, dtype=np.uint64)
+    dst = np.empty(int(ebase[-1]), dtype=np.uint32)
+    lab = np.empty(int(ebase[-1]), dtype=np.uint32 if wide else np.uint8)
+    nl = np.empty(int(starts[-1]), dtype=np.uint32)
+    for j, g in enumerate(graphs):
+        a, b = int(starts[j]), int(starts[j + 1])
+        off[a:b] = g.offsets[:-1].astype(np.uint64) + np.uint64(ebase[j])
+        dst[ebase[j]:ebase[j + 1]] = g.dst.astype(np.uint32) + np.uint32(a)
+        lab[ebase[j]:ebase[j + 1]] = g.edge_label
+        nl[a:b] = g.node_label
+    off[-1] = np.uint64(ebase[-1])
+    return Graph(int(starts[-1]), off, dst, lab, nl), starts
 
 
 def load_library(path: str = LIB_PATH):
@@ -279,6 +310,39 @@ class KBisim:
             g = self._graph_desc(keep, num_nodes, node_label, dst, edge_label, offsets=offsets,
                                  src=src)
         self._check(self._lib.kbisim_load(self._h, ctypes.byref(g)))
+
+    def build_many(self, graphs, ks, *, union=None):
+        """Batched build of independent graphs (``synth.Graph`` list) with
+        k = ks[j] for graph j, all refined together.  ``union`` may pass the
+        already concatenated graph and its node starts (``concat_graphs``).
+        Results per graph: ``many_pids(j, level)``, ``many_info(j)``."""
+        g_all, starts = union if union is not None else concat_graphs(graphs)
+        keep = _Pinned()
+        g = self._graph_desc(keep, g_all.num_nodes, g_all.node_label, g_all.dst, g_all.edge_label,
+                             offsets=g_all.offsets)
+        st = np.ascontiguousarray(np.asarray(starts, dtype=np.uint64))
+        kk = np.ascontiguousarray(np.asarray(ks, dtype=np.uint32))
+        if kk.size != st.size - 1:
+            raise ValueError("need one k per graph")
+        self._check(self._lib.kbisim_build_many(self._h, ctypes.byref(g), st.ctypes.data, int(kk.size),
+                                                kk.ctypes.data))
+        self._many_sizes = np.diff(st.astype(np.int64))
+        self._many_k = kk.copy()
+
+    def many_pids(self, j: int, level: int) -> np.ndarray:
+        sizes = getattr(self, "_many_sizes", None)
+        n = int(sizes[j]) if sizes is not None and 0 <= j < sizes.size else 0
+        out = np.empty(max(n, 1), dtype=np.uint32)
+        self._check(self._lib.kbisim_many_pids(self._h, int(j), int(level), out.ctypes.data, 0))
+        return out[:n]
+
+    def many_info(self, j: int):
+        """(rounds_run, block counts of levels 0..k_j) of graph j."""
+        r = ctypes.c_uint32(0)
+        self._check(self._lib.kbisim_many_info(self._h, int(j), ctypes.byref(r), None))
+        counts = np.zeros(int(self._many_k[j]) + 1, dtype=np.uint64)
+        self._check(self._lib.kbisim_many_info(self._h, int(j), ctypes.byref(r), counts.ctypes.data))
+        return int(r.value), counts
 
     def refine(self, k: int) -> Result:
         r = ResultDesc()
