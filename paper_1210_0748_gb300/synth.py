@@ -36,7 +36,7 @@ import numpy as np
 DEFAULT_SEED = 0x12100748
 
 # stream ids keep independent draws apart
-_S_DEG, _S_TGT, _S_ELAB, _S_NLAB, _S_PERM = 1, 2, 3, 4, 5
+_S_DEG, _S_TGT, _S_ELAB, _S_NLAB, _S_PERM, _S_BATCH = 1, 2, 3, 4, 5, 6
 _CHUNK = 1 << 22
 
 
@@ -255,3 +255,17 @@ def config_single_large(seed: int = DEFAULT_SEED + 2, scale: float = 1.0) -> Gra
     m = max(1, int(round(256_000_000 * scale)))
     return powerlaw_graph(n, m, alpha=2.1, hub_cap=1_000_000, node_labels=16, node_zipf=1.2,
                           edge_labels=32, edge_zipf=1.5, seed=seed)
+
+
+def config_batched(seed: int = DEFAULT_SEED + 3, count: int = 4096):
+    """``count`` independent graphs: edge counts log-uniform in [1K, 1M], nodes =
+    edges / 8, out-degrees Zipf(2.0) capped at 10K, uniform targets, 8 node
+    labels and 4 edge labels uniform (the 100K/1M generator's distributions),
+    k uniform in 1..10.  Graph j is drawn with its own seed.  Returns
+    (graphs, ks)."""
+    rng = _rng(seed, _S_BATCH, 0)
+    edges = np.exp(rng.uniform(np.log(1e3), np.log(1e6), count)).astype(np.int64)
+    ks = rng.integers(1, 11, count).astype(np.int64)
+    graphs = [uniform_zipf_graph(int(e // 8), int(e), zipf_s=2.0, dmax=10_000, node_labels=8, edge_labels=4,
+                                 seed=seed * 65_536 + j) for j, e in enumerate(edges.tolist())]
+    return graphs, [int(k) for k in ks]

@@ -38,3 +38,15 @@ def test_from_coo_groups_by_source():
     assert g.offsets.tolist() == [0, 1, 2, 2, 4]
     assert g.dst.tolist() == [1, 3, 0, 2] and g.edge_label.tolist() == [6, 8, 5, 7]
     assert g.src().tolist() == [0, 1, 3, 3]
+
+
+def test_batched_config_shape():
+    graphs, ks = synth.config_batched(count=12)
+    again, ks2 = synth.config_batched(count=12)
+    assert ks == ks2 and all(1 <= k <= 10 for k in ks)
+    for g, h in zip(graphs, again):
+        assert 1_000 <= g.num_edges <= 1_000_000
+        assert g.num_nodes == g.num_edges // 8
+        assert int(g.offsets[-1]) == g.num_edges
+        assert np.array_equal(g.dst, h.dst)
+        assert int(g.node_label.max()) < 8 and int(g.edge_label.max()) < 4
