@@ -94,9 +94,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-clocks", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "large"],
                    help="single: the 16M/256M graph (the headline line); batched: 4096 graphs "
-                        "(times --scale) in one batched build vs one build per graph")
+                        "(times --scale) in one batched build vs one build per graph; large: the "
+                        "256M-node / 2B-edge graph")
     return p.parse_args()
 
 
@@ -165,8 +166,15 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def workload(scale):
+def workload(scale, kind="single"):
     from paper_1210_0748_gb300 import synth
+    if kind == "large":
+        g = synth.config_large_single(scale=scale)
+        return g, {"workload": "powerlaw graph: %d nodes, %d edges, out-degree Pareto alpha=2.0 (hubs to 1M), "
+                               "preferential-attachment targets, 64 node labels and 16 edge labels Zipf(1.3), "
+                               "k=10 with early stop" % (g.num_nodes, g.num_edges),
+                   "nodes": g.num_nodes, "edges": g.num_edges, "k": K_ROUNDS,
+                   "l2": "inputs larger than L2 (no flush needed)"}
     g = synth.config_single_large(scale=scale)
     return g, {"workload": "powerlaw graph: %d nodes, %d edges, out-degree Pareto alpha=2.1 (hubs "
                            "to 1M), preferential-attachment targets, 16 node labels Zipf(1.2), "
@@ -305,7 +313,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    g, cfg = workload(args.scale)
+    g, cfg = workload(args.scale, args.workload)
+    if args.workload == "large":  # a parity-scale case: no host-buffer leg, no CPU sample
+        args.no_e2e = True
+        args.no_cpu_baseline = True
     E, N = g.num_edges, g.num_nodes
     stream = torch.cuda.Stream(device=local_rank)
     kb = KBisim(device=local_rank, stream=stream, collect_timing=True)
@@ -369,7 +380,7 @@ def main():
                           "launches_per_call": launches / calls, "edges": e_c, "nodes": n_c}
     dom = max(per_class, key=lambda c: ktimes[c][0])
     d = per_class[dom]
-    traffic = recorded_traffic(dom, args.scale)
+    traffic = recorded_traffic(dom, args.scale) if args.workload == "single" else None
     names = {"sig_small": "k_sig_small (out-degree <= 64, one thread per node)",
              "sig_medium": "k_sig_chunk (out-degree 65..4096, CTA chunks)",
              "sig_hub": "k_hub_chunk + k_hub_bucket (out-degree > 4096)",

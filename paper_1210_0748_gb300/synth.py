@@ -269,3 +269,13 @@ def config_batched(seed: int = DEFAULT_SEED + 3, count: int = 4096):
     graphs = [uniform_zipf_graph(int(e // 8), int(e), zipf_s=2.0, dmax=10_000, node_labels=8, edge_labels=4,
                                  seed=seed * 65_536 + j) for j, e in enumerate(edges.tolist())]
     return graphs, [int(k) for k in ks]
+
+
+def config_large_single(seed: int = DEFAULT_SEED + 5, scale: float = 1.0) -> Graph:
+    """256M nodes, 2B edges (times ``scale``), power-law alpha = 2.0 out-degrees
+    with hubs to 1M, preferential-attachment targets, 64 node labels and 16
+    edge labels Zipf(1.3) (k = 10)."""
+    n = max(1, int(round(256_000_000 * scale)))
+    m = max(1, int(round(2_000_000_000 * scale)))
+    return powerlaw_graph(n, m, alpha=2.0, hub_cap=1_000_000, node_labels=64, node_zipf=1.3,
+                          edge_labels=16, edge_zipf=1.3, seed=seed)
