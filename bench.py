@@ -94,10 +94,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-clocks", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "large"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "large", "serve"],
                    help="single: the 16M/256M graph (the headline line); batched: 4096 graphs "
                         "(times --scale) in one batched build vs one build per graph; large: the "
-                        "256M-node / 2B-edge graph")
+                        "256M-node / 2B-edge graph; serve: 64 resident graphs under Poisson request "
+                        "streams")
+    p.add_argument("--requests", type=int, default=120, help="requests per arrival rate (serve)")
     return p.parse_args()
 
 
@@ -299,12 +301,65 @@ def run_batched(args):
     return 0
 
 
+def run_serve(args):
+    """Resident graphs under Poisson request streams (70% update batches of
+    1K..1M edges, 30% rebuilds at k 3..10) at several arrival rates: latency
+    percentiles from arrival to result, and throughput."""
+    import torch
+    from paper_1210_0748_gb300 import synth
+    from paper_1210_0748_gb300.serve import Server, make_requests
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    graphs, ks = synth.config_serving(scale=args.scale)
+    srv = Server(graphs, ks, slots=8, device=local_rank)
+    warm = make_requests(graphs, rate=0.0, count=16, seed=99)
+    srv.serve(warm, realtime=False)
+    runs = []
+    for i, rate in enumerate([10.0, 100.0, 1000.0]):
+        reqs = make_requests(graphs, rate=rate, count=args.requests, seed=1 + i)
+        t0 = time.perf_counter()
+        out = srv.serve(reqs, realtime=True)
+        span = time.perf_counter() - t0
+        lat = np.array([o.latency for o in out]) * 1000.0
+        work = float(sum(o.edges * o.rounds_run for o in out))
+        runs.append({"rate_per_s": rate, "requests": len(out), "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "throughput_req_per_s": len(out) / span,
+                     "edge_rounds_per_s": work / span,
+                     "updates": sum(o.kind == "update" for o in out)})
+    # the saturated stream again with one request at a time: what overlap buys
+    srv.slots = 1
+    reqs = make_requests(graphs, rate=1000.0, count=args.requests, seed=3)
+    t0 = time.perf_counter()
+    out = srv.serve(reqs, realtime=True)
+    span1 = time.perf_counter() - t0
+    one_at_a_time = {"throughput_req_per_s": len(out) / span1,
+                     "p50_ms": float(np.percentile([o.latency * 1000 for o in out], 50)),
+                     "p99_ms": float(np.percentile([o.latency * 1000 for o in out], 99))}
+    srv.close()
+    best = max(runs, key=lambda r: r["throughput_req_per_s"])
+    line = {"metric": "serving: requests/s with p50/p99 latency (1 GB300)", "value": best["throughput_req_per_s"],
+            "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "%d resident graphs, edges log-uniform in [1M, 64M] x %g, nodes = edges/10, "
+                                   "100K/1M-generator distributions; Poisson arrivals, 70%% update batches of "
+                                   "1K..1M edges (half inserts, half deletes of generated edges), 30%% rebuilds "
+                                   "at k 3..10; 8 slots" % (len(graphs), args.scale),
+                       "graphs": len(graphs), "edges": int(sum(g.num_edges for g in graphs))},
+            "rates": runs, "one_slot_at_1000_per_s": one_at_a_time,
+            "overlap_speedup": runs[-1]["throughput_req_per_s"] / one_at_a_time["throughput_req_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     import torch
     from paper_1210_0748_gb300.kbisim import KBisim
 

@@ -250,6 +250,7 @@ void free_graph(Store& s, bool keep_buffers) {
     for (Buf& b : s.level) release(s, b);
     for (Buf& b : s.out_level) release(s, b);
     for (Buf& b : s.stage) release(s, b);
+    for (Buf& b : s.upd) release(s, b);
     s.level.clear();
     s.out_level.clear();
   }

@@ -238,6 +238,8 @@ struct Store {
   static constexpr int kStageBufsN = 9;
   Buf stage[kStageBufsN];      // staging of host inputs and COO grouping (kbisim_load)
   Buf rl_tcnt, rl_hot, rl_ost; // relabelling temporaries
+  static constexpr int kUpdBufsN = 24;
+  Buf upd[kUpdBufsN];          // temporaries of a maintenance batch (kbisim_update)
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars
@@ -266,6 +268,7 @@ struct Status {
 };
 
 constexpr int kStageBufs = Store::kStageBufsN;
+constexpr int kUpdBufs = Store::kUpdBufsN;
 
 // Allocation helpers (kbisim_api.cu)
 Status ensure(Store& s, Buf& b, size_t bytes);

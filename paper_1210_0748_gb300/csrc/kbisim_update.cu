@@ -355,12 +355,16 @@ Status scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned long long*
   return st;
 }
 
+// Temporaries of one batch: the store's update buffers, kept for the next
+// batch when the handle has no HBM budget (no cudaFree, which would wait for
+// the whole device), released at the end of the batch otherwise.
 struct Bufs {
   Store& s;
-  std::vector<Buf> b;
-  explicit Bufs(Store& st, int k) : s(st), b(k) {}
+  Buf* b;
+  explicit Bufs(Store& st) : s(st), b(st.upd) {}
   ~Bufs() {
-    for (Buf& x : b) release(s, x);
+    if (s.budget)
+      for (int i = 0; i < kUpdBufs; ++i) release(s, b[i]);
   }
 };
 
@@ -386,7 +390,7 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (n1 >= 0xFFFFFFFFull) return Status::Err(KBISIM_ERR_INVALID_ARG, "too many nodes");
   const bool dev = bt->on_device != 0;
   Status st;
-  Bufs t(s, 24);
+  Bufs t(s);
   enum { ADDL, INS_S, INS_T, INS_L, DEL_S, DEL_T, DEL_L, DEL_N, ALIVE, ERR, CNT, COFF, CUR, CDST, CLAB, DCNT, RSZ,
          RBASE, TAB, LIST, DELF, NOFF, NDST, NLAB };
   const uint32_t *addl, *is, *it, *il, *ds, *dt, *dl, *dn;
@@ -523,12 +527,15 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
   if (!st.ok()) return st;
 
-  // 4. the updated graph replaces the stored one
-  for (Buf& b : s.level) release(s, b);
-  for (Buf& b : s.out_level) release(s, b);
-  s.level.clear();
-  s.out_level.clear();
-  s.out_valid.clear();
+  // 4. the updated graph replaces the stored one (level buffers are reused
+  //    unless the handle has an HBM budget)
+  if (s.budget) {
+    for (Buf& b : s.level) release(s, b);
+    for (Buf& b : s.out_level) release(s, b);
+    s.level.clear();
+    s.out_level.clear();
+  }
+  for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
   s.has_levels = false;
   s.n = n1;
   s.m = m1;

@@ -279,3 +279,15 @@ def config_large_single(seed: int = DEFAULT_SEED + 5, scale: float = 1.0) -> Gra
     m = max(1, int(round(2_000_000_000 * scale)))
     return powerlaw_graph(n, m, alpha=2.0, hub_cap=1_000_000, node_labels=64, node_zipf=1.3,
                           edge_labels=16, edge_zipf=1.3, seed=seed)
+
+
+def config_serving(seed: int = DEFAULT_SEED + 4, count: int = 64, scale: float = 1.0):
+    """``count`` resident graphs: edge counts log-uniform in [1M, 64M] (times
+    ``scale``), nodes = edges / 10, the 100K/1M generator's distributions, and
+    an initial k uniform in 3..10.  Returns (graphs, ks)."""
+    rng = _rng(seed, _S_BATCH, 1)
+    edges = (np.exp(rng.uniform(np.log(1e6), np.log(64e6), count)) * scale).astype(np.int64)
+    ks = rng.integers(3, 11, count).astype(np.int64)
+    graphs = [uniform_zipf_graph(max(1, int(e // 10)), max(1, int(e)), zipf_s=2.0, dmax=10_000, node_labels=8,
+                                 edge_labels=4, seed=seed * 65_536 + j) for j, e in enumerate(edges.tolist())]
+    return graphs, [int(k) for k in ks]

@@ -1,0 +1,49 @@
+"""Serving loop: requests that overlap on the device give, request by request,
+exactly what the same requests give one at a time (tolerance zero: counts,
+rounds and a digest of the level-k identifiers)."""
+import numpy as np
+import pytest
+
+from paper_1210_0748_gb300 import synth
+from paper_1210_0748_gb300.serve import Server, make_requests, run_alone
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    sizes = [2_000, 9_000, 30_000, 60_000, 120_000, 5_000]
+    return [synth.uniform_zipf_graph(m // 10, m, seed=100 + j) for j, m in enumerate(sizes)], [4, 6, 3, 8, 5, 10]
+
+
+@pytest.mark.parametrize("slots", [3, 8])
+def test_results_in_the_mix_equal_alone(slots):
+    graphs, ks = _graphs()
+    reqs = make_requests(graphs, rate=0.0, count=48, seed=7, batch_min=10, batch_max=20_000)
+    srv = Server(graphs, ks, slots=slots)
+    try:
+        mix = srv.serve(reqs, realtime=False)
+    finally:
+        srv.close()
+    alone = run_alone(graphs, ks, reqs)
+    assert [o.rid for o in mix] == [o.rid for o in alone] == list(range(48))
+    for a, b in zip(mix, alone):
+        assert (a.counts, a.rounds_run, a.digest, a.edges) == (b.counts, b.rounds_run, b.digest, b.edges), a.rid
+    assert {o.kind for o in mix} == {"update", "rebuild"}
+
+
+def test_realtime_stream_admits_on_arrival():
+    graphs, ks = _graphs()
+    reqs = make_requests(graphs, rate=400.0, count=30, seed=3, batch_min=10, batch_max=5_000)
+    srv = Server(graphs, ks, slots=4)
+    try:
+        out = srv.serve(reqs, realtime=True)
+    finally:
+        srv.close()
+    assert len(out) == 30
+    for o, r in zip(out, sorted(reqs, key=lambda r: r.rid)):
+        assert o.t_start + 1e-4 >= r.t_arrive and o.t_end >= o.t_start
+    # requests on one graph run in arrival order
+    by_graph = {}
+    for o in sorted(out, key=lambda o: o.t_start):
+        by_graph.setdefault(o.graph, []).append(o.t_arrive)
+    assert all(v == sorted(v) for v in by_graph.values())
