@@ -44,11 +44,15 @@ UNITS = {"ns": 1e-9, "nsecond": 1e-9, "us": 1e-6, "usecond": 1e-6, "ms": 1e-3, "
          "KB": 1e3, "MB": 1e6, "GB": 1e9}
 
 
+# Sources of the kernels a refinement round runs (the timed classes).
+ROUND_SOURCES = ("kbisim_round.cu", "kbisim_internal.cuh")
+
+
 def source_digest() -> str:
-    """sha256 over the kernel sources (file names and contents)."""
+    """sha256 over the sources of the round kernels (file names and contents)."""
     h = hashlib.sha256()
     csrc = os.path.join(PKG, "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in ROUND_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
