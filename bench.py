@@ -103,6 +103,25 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over the ranks of the job (x itself with one rank); the
+    reduction runs on the device for NCCL, on the host for gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank (weak scaling),
+    the job takes as long as its slowest rank."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -402,14 +421,9 @@ def main():
     clk = clocks.stop()
     ktimes = kb.kernel_times()
     barrier()
-    ms_max = ms_total
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_total)
     ms_step = ms_max / args.steps
-    value = world * E * rounds / (ms_max / 1000.0)
+    value = job_value(E * rounds, world, ms_max)
 
     # roofline: the whole refinement round against the fixed algorithmic bytes,
     # and each kernel class against its share of those bytes (per call of the
@@ -479,14 +493,9 @@ def main():
             r = kb2.build(host_g, K_ROUNDS)
             kb2._check(kb2._lib.kbisim_pids(kb2._h, K_ROUNDS, out_np.ctypes.data, 0))
             e2e_rounds += r.rounds_run
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0)
         h2d = sum(v.numel() * v.element_size() for v in pin.values())
-        line["e2e"] = {"value": world * E * e2e_rounds / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        line["e2e"] = {"value": job_value(E * e2e_rounds, world, dt * 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": N * 4 + 8 * (K_ROUNDS + 1),
                        "ms_per_step": 1000 * dt / e2e_steps}
         kb2.close()
