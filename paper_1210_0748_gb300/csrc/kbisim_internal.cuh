@@ -43,7 +43,8 @@ static_assert(kSmallChunkThreads * kChunkItems >= kWarp2Max, "a node of out-degr
 enum : uint32_t {
   kErrChecked = 1u,       // an index check failed
   kErrProbe = 2u,         // a hash probe sequence ran past its bound
-  kErrHubOverflow = 4u,   // a hub bucket held more distinct keys than it can
+  kErrHubOverflow = 4u,   // a hub bucket received more key words than its capacity
+  kErrHubSet = 16u,       // a hub bucket held more distinct keys than its shared set
   kErrBadInput = 8u,      // input validation failed (ids, offsets)
 };
 
@@ -199,7 +200,8 @@ struct Store {
   uint64_t hub_tmp_words = 0;  // key words of all hub buckets
   uint64_t n_hub_buckets = 0;
   uint64_t hub_edges = 0;
-  uint32_t hub_extra_bits = 0; // grows if a bucket overflows
+  uint32_t hub_extra_bits = 0; // more buckets per hub: grows when a bucket's set fills
+  uint32_t hub_cap_shift = 0;  // larger buckets: grows when a bucket's capacity is exceeded
   std::vector<uint32_t> h_hub_degbits;
   std::vector<uint64_t> h_hub_deg;
 

@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
 // key once, and appends the list to the hub's buckets; the bucket of a key is
 // its top bits, so equal keys from different chunks meet in one bucket.
 // Buckets have a fixed capacity: an append past it raises kErrHubOverflow and
-// the host repeats the hub passes with more buckets.  Pass 2 (k_hub_bucket):
+// the host repeats the hub passes with larger buckets (kErrHubSet, from the
+// bucket pass, asks for more buckets instead).  Pass 2 (k_hub_bucket):
 // one CTA per bucket deduplicates across chunks and appends the bucket's
 // distinct keys at the hub's CSR offset; the last bucket of a hub to finish
 // writes its count and hash.
@@ -681,21 +682,22 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
 // Insert k (!= kEmpty) into a power-of-two set of hmask + 1 slots at
 // shared-window address `base`, home slot from the key's low bits (the keys of
 // one hub bucket share their top bits); true iff this call put it there.
+// Returns 1 if this call inserted k, 0 if k was present, -1 if the set is full.
 template <typename K>
-__device__ __forceinline__ bool pow2_insert(uint32_t base, uint32_t hmask, K k) {
+__device__ __forceinline__ int pow2_insert(uint32_t base, uint32_t hmask, K k) {
   uint32_t s = key_h32(k) & hmask;
   for (uint32_t t = 0; t <= hmask; ++t) {
     const uint32_t a = base + s * (uint32_t)sizeof(K);
     K cur = lds_volatile(a, K());
-    if (cur == k) return false;
+    if (cur == k) return 0;
     if (cur == KeyOps<K>::kEmpty) {
       cur = atoms_cas(a, KeyOps<K>::kEmpty, k);
-      if (cur == KeyOps<K>::kEmpty) return true;
-      if (cur == k) return false;
+      if (cur == KeyOps<K>::kEmpty) return 1;
+      if (cur == k) return 0;
     }
     s = (s + 1) & hmask;
   }
-  return false;
+  return -1;
 }
 
 constexpr int kBucketThreads = 256, kBucketItems = 8;
@@ -704,7 +706,7 @@ template <typename K>
 struct BucketSmem {
   K set[2 * kHubUcap];
   K uniq[kHubUcap];
-  uint32_t cnt, empty, lo, hi, last;
+  uint32_t cnt, empty, full, lo, hi, last;
   unsigned long long obase;
 };
 
@@ -725,7 +727,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
     const K* tmp = static_cast<const K*>(h.tmp) + h.hub_tbase[hub] + (b - h.hub_bbase[hub]) * cap;
     const uint32_t n = min(h.cursor[b], cap);
     uint32_t hcap = 64;
-    while (hcap < 2 * n) hcap <<= 1;
+    while (hcap < 2 * n && hcap < 2 * kHubUcap) hcap <<= 1;
     {
       uint4* s4 = reinterpret_cast<uint4*>(sm.set);
       const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -734,6 +736,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
     if (tid == 0) {
       sm.cnt = 0;
       sm.empty = 0;
+      sm.full = 0;
       sm.lo = 0;
       sm.hi = 0;
     }
@@ -752,16 +755,32 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
 #pragma unroll
         for (int q = 0; q + 1 < kBucketItems; ++q) kk[q] = kk[q + 1];
         bool fresh = false;
-        if (i < n) fresh = k == KeyOps<K>::kEmpty ? atomicExch(&sm.empty, 1u) == 0u : pow2_insert(sbase, hcap - 1, k);
+        if (i < n) {
+          if (k == KeyOps<K>::kEmpty) {
+            fresh = atomicExch(&sm.empty, 1u) == 0u;
+          } else {
+            const int r = pow2_insert(sbase, hcap - 1, k);
+            fresh = r > 0;
+            if (r < 0) sm.full = 1u;
+          }
+        }
         const unsigned fm = __ballot_sync(kFull, fresh);
         if (fm == 0u) continue;
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&sm.cnt, (uint32_t)__popc(fm));
         base = __shfl_sync(kFull, base, 0);
-        if (fresh) sm.uniq[base + __popc(fm & lanes_below(lane))] = k;
+        const uint32_t q = base + __popc(fm & lanes_below(lane));
+        if (fresh) {
+          if (q < (uint32_t)kHubUcap) sm.uniq[q] = k; else sm.full = 1u;
+        }
       }
     }
     __syncthreads();
+    if (sm.full) {  // more distinct keys than the set holds: the host adds buckets
+      if (tid == 0) atomicOr(a.err, kErrHubSet);
+      __syncthreads();
+      continue;
+    }
     const uint32_t U = sm.cnt;
     if (tid == 0) sm.obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
     __syncthreads();
@@ -1598,7 +1617,8 @@ Status hub_layout(Store& s) {
     const uint64_t nb = 1ull << (bits[i] + s.hub_extra_bits);
     bbase[i + 1] = bbase[i] + nb;
     const uint64_t mean = (s.h_hub_deg[i] + nb - 1) / nb;
-    cap[i] = (uint32_t)std::min<uint64_t>(kHubUcap, 2 * mean + 256);
+    cap[i] = (uint32_t)std::min<uint64_t>(s.h_hub_deg[i], std::min<uint64_t>(kHubUcap, 2 * mean + 256)
+                                                                << s.hub_cap_shift);
     tbase[i] = words;
     words += nb * cap[i];
   }
@@ -1697,9 +1717,12 @@ Status run_signatures(Store& s, const SigArgs& a) {
       st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
       if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
       if (!st.ok()) return st;
-      if (!(e & kErrHubOverflow)) break;
-      if (attempt >= 8) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
-      s.hub_extra_bits += 1;
+      if (!(e & (kErrHubOverflow | kErrHubSet))) break;
+      if (attempt >= 40) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
+      // too many key words for a bucket (keys repeated across chunks): larger
+      // buckets, up to the hub's degree; too many distinct keys: more buckets
+      if (e & kErrHubOverflow) s.hub_cap_shift += 1;
+      if (e & kErrHubSet) s.hub_extra_bits += 1;
       if (!(st = hub_layout(s)).ok()) return st;
       cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
     }
@@ -1807,6 +1830,7 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
   s.n_alone = 0;
   s.hub_extra_bits = 0;
+  s.hub_cap_shift = 0;
   s.h_hub_degbits.assign(s.n_hub, 0);
   s.h_hub_deg.assign(s.n_hub, 0);
   s.hub_edges = 0;

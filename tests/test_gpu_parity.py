@@ -322,3 +322,60 @@ def test_update_rejects_bad_batches():
         assert e.value.code == ERR_INVALID_ARG
         p = kb.all_pids(3)
         assert (p[:, 4] == 0xFFFFFFFF).all()
+
+
+# --- an element whose packed word equals the empty-slot marker ------------------
+
+def _unmix32(y):
+    """Inverse of the 32-bit MurmurHash3 finalizer (xor-shifts and odd multiplies)."""
+    def unxorshift(x, s):
+        r = x
+        for _ in range(32 // s + 1):
+            r = x ^ (r >> s)
+        return r & 0xFFFFFFFF
+    y = unxorshift(y, 16)
+    y = (y * pow(0xc2b2ae35, -1, 1 << 32)) & 0xFFFFFFFF
+    y = unxorshift(y, 13)
+    y = (y * pow(0x85ebca6b, -1, 1 << 32)) & 0xFFFFFFFF
+    return unxorshift(y, 16)
+
+
+def test_element_equal_to_empty_marker():
+    """Level 0 gives every node its own block (pId_0(v) = v, 2^20 nodes), so
+    round 1 packs elements as (label << 20) | child.  The pair whose packed
+    word mixes to all ones is placed, repeated, in nodes of every degree class
+    (one thread per node, chunks, a hub); results must still equal the oracle."""
+    n = 1 << 20
+    packed = _unmix32(0xFFFFFFFF)
+    lab, child = packed >> 20, packed & (n - 1)
+    rng = np.random.default_rng(17)
+    src, dst, el = [], [], []
+    for u, d in [(0, 5), (1, 40), (2, 300), (3, 2000), (4, 9000), (5, 5)]:
+        src += [u] * d
+        dst += rng.integers(0, n, d).tolist()
+        el += rng.integers(0, 64, d).tolist()
+        for _ in range(2):  # the special element twice (a duplicate)
+            src.append(u)
+            dst.append(child)
+            el.append(lab)
+    g = synth.from_coo(n, np.array(src, np.uint32), np.array(dst, np.uint32), np.array(el, np.uint32),
+                       np.arange(n, dtype=np.uint32))
+    res, pids = gpu_levels(g, 2)
+    assert_same(res, pids, oracle_levels(g, 2))
+
+
+def test_hub_with_one_key_in_every_chunk():
+    """A 20M-edge hub whose edges all carry one element: chunk deduplication
+    leaves one key per 4096-edge chunk, all in one bucket, more than the
+    bucket's first capacity (about twice its mean load); the library must grow
+    the bucket and still match the oracle."""
+    n = 1000
+    m_hub = 20_000_000
+    rng = np.random.default_rng(23)
+    other = 5_000
+    src = np.concatenate([np.zeros(m_hub, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
+    dst = np.concatenate([np.ones(m_hub, np.uint32), rng.integers(0, n, other).astype(np.uint32)])
+    lab = np.concatenate([np.zeros(m_hub, np.uint32), rng.integers(0, 3, other).astype(np.uint32)])
+    g = synth.from_coo(n, src, dst, lab, (np.arange(n) % 3).astype(np.uint32))
+    res, pids = gpu_levels(g, 3)
+    assert_same(res, pids, oracle_levels(g, 3))
