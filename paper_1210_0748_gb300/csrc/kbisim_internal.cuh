@@ -202,6 +202,7 @@ struct Store {
   uint64_t hub_edges = 0;
   uint32_t hub_extra_bits = 0; // more buckets per hub: grows when a bucket's set fills
   uint32_t hub_cap_shift = 0;  // larger buckets: grows when a bucket's capacity is exceeded
+  double hub_distinct_ratio = 0.0;  // distinct keys / edges of the hubs in the last round
   std::vector<uint32_t> h_hub_degbits;
   std::vector<uint64_t> h_hub_deg;
 

@@ -606,6 +606,7 @@ struct HubArgs {
 
 constexpr int kHubUcap = 4096;         // key words per bucket at most
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
+constexpr double kHubScatterRatio = 0.75;  // distinct / edges of the hubs above which chunks skip their set
 
 template <typename K>
 __host__ __device__ constexpr size_t hub_chunk_smem() {
@@ -675,6 +676,52 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
     const uint32_t b = hub_bucket(v, bits);
     const uint32_t q = in_smem ? bpos[b] + atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
     if (q < cap) tmp[(uint64_t)b * cap + q] = v;
+    else atomicOr(a.err, kErrHubOverflow);
+  }
+}
+
+// Hub pieces without the chunk-level set, for rounds in which few hub keys
+// repeat: the keys of a chunk go straight to the hub's buckets (counted per
+// bucket in shared memory first, one global reservation per bucket), and the
+// bucket pass removes every duplicate.
+template <typename LabelT, typename K>
+__global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArgs h) {
+  __shared__ uint32_t bcnt[kHubSmemBuckets];
+  __shared__ uint32_t bpos[kHubSmemBuckets];
+  const uint4 c = h.chunks[blockIdx.x];
+  const uint32_t hub = c.x;
+  const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
+  const uint32_t E = c.w;
+  const uint32_t bits = h.hub_bits[hub] + h.extra_bits;
+  const uint32_t nb = 1u << bits;
+  const bool in_smem = nb <= (uint32_t)kHubSmemBuckets;
+  const uint32_t tid = threadIdx.x;
+  if (in_smem)
+    for (uint32_t i = tid; i < nb; i += kChunkThreads) bcnt[i] = 0;
+  __syncthreads();
+  K key[kChunkItems];
+  chunk_keys<kChunkThreads, LabelT, K>(a, ebase, E, key);
+  const uint32_t cap = h.hub_cap[hub];
+  uint32_t* cur = h.cursor + h.hub_bbase[hub];
+  K* tmp = static_cast<K*>(h.tmp) + h.hub_tbase[hub];
+  if (in_smem) {
+#pragma unroll
+    for (int t = 0; t < kChunkItems; ++t)
+      if (tid + t * kChunkThreads < E) atomicAdd(&bcnt[hub_bucket(key[t], bits)], 1u);
+    __syncthreads();
+    for (uint32_t b = tid; b < nb; b += kChunkThreads) {
+      const uint32_t n_b = bcnt[b];
+      bpos[b] = n_b ? atomicAdd(&cur[b], n_b) : 0u;
+      bcnt[b] = 0;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < kChunkItems; ++t) {
+    if (tid + t * kChunkThreads >= E) continue;
+    const uint32_t b = hub_bucket(key[t], bits);
+    const uint32_t q = in_smem ? bpos[b] + atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
+    if (q < cap) tmp[(uint64_t)b * cap + q] = key[t];
     else atomicOr(a.err, kErrHubOverflow);
   }
 }
@@ -1704,20 +1751,35 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
       h.hub_done = h.hub_term + 2 * s.n_hub;
       h.tmp = s.hub_tmp.p;
+      // chunk-level deduplication pays off while hub keys repeat (round 1, few
+      // blocks); afterwards the keys go straight to the buckets
+      const bool dedupe = s.hub_distinct_ratio < kHubScatterRatio;
       {
         TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 2);
         cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
-        k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
+        if (dedupe)
+          k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
+        else
+          k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
         const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 8);
         k_hub_bucket<K><<<g, kBucketThreads, sizeof(BucketSmem<K>), s.stream>>>(a, h, s.n_hub_buckets);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
+      std::vector<uint64_t> distinct(s.n_hub);
       st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
+      if (st.ok())
+        st = cuda_check(cudaMemcpyAsync(distinct.data(), s.hub_acc.p, s.n_hub * 8, cudaMemcpyDeviceToHost, s.stream),
+                        "hub counts");
       if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
       if (!st.ok()) return st;
-      if (!(e & (kErrHubOverflow | kErrHubSet))) break;
+      if (!(e & (kErrHubOverflow | kErrHubSet))) {
+        uint64_t u = 0;
+        for (uint64_t x : distinct) u += x;
+        s.hub_distinct_ratio = s.hub_edges ? (double)u / (double)s.hub_edges : 1.0;
+        break;
+      }
       if (attempt >= 40) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
       // too many key words for a bucket (keys repeated across chunks): larger
       // buckets, up to the hub's degree; too many distinct keys: more buckets
@@ -1923,6 +1985,7 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
 Status compute_level0(Store& s) {
   Status st = ensure_round_scratch(s);
   if (!st.ok()) return st;
+  s.hub_distinct_ratio = 0.0;  // round 1 packs labels: its hub keys repeat
   const int sms = sm_count(s.device);
   const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16);
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);

@@ -379,3 +379,32 @@ def test_hub_with_one_key_in_every_chunk():
     g = synth.from_coo(n, src, dst, lab, (np.arange(n) % 3).astype(np.uint32))
     res, pids = gpu_levels(g, 3)
     assert_same(res, pids, oracle_levels(g, 3))
+
+
+def test_hubs_with_distinct_keys():
+    """Hubs whose elements are nearly all distinct from round 1 on (each hub
+    edge its own label), so later rounds send hub keys to the buckets without
+    chunk deduplication: two twin hubs list the same elements in other orders,
+    and a third hub repeats each of its elements four times."""
+    rng = np.random.default_rng(31)
+    n = 300_000
+    h = 250_000
+    tgt = rng.permutation(n)[:h].astype(np.uint32)
+    hl = np.arange(h, dtype=np.uint32)
+    p1 = rng.permutation(h)
+    p2 = rng.permutation(40_000)
+    rep_t = np.repeat(rng.permutation(n)[:10_000].astype(np.uint32), 4)[p2]
+    rep_l = np.repeat(np.arange(10_000, dtype=np.uint32), 4)[p2]
+    other = 200_000
+    src = np.concatenate([np.zeros(h, np.uint32), np.ones(h, np.uint32), np.full(40_000, 2, np.uint32),
+                          rng.integers(3, n, other).astype(np.uint32)])
+    dst = np.concatenate([tgt, tgt[p1], rep_t, rng.integers(0, n, other).astype(np.uint32)])
+    lab = np.concatenate([hl, hl[p1], rep_l, rng.integers(0, 2, other).astype(np.uint32)])
+    nl = rng.integers(0, 2, n).astype(np.uint32)
+    nl[1] = nl[0]
+    g = synth.from_coo(n, src, dst, lab, nl)
+    res, pids = gpu_levels(g, 4)
+    ref = oracle_levels(g, 4)
+    assert_same(res, pids, ref)
+    assert ref.rounds_run >= 2
+    assert all(pids[lev][0] == pids[lev][1] for lev in range(pids.shape[0]))
