@@ -447,17 +447,7 @@ __device__ __forceinline__ uint32_t region_home(K k, uint32_t rs) {
   return (uint32_t)(((uint64_t)key_h32(k) * rs) >> 32);
 }
 
-// Shared-memory accesses by shared-window address (no generic addressing).
-__device__ __forceinline__ uint32_t lds_volatile(uint32_t a, uint32_t) {
-  uint32_t v;
-  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint64_t lds_volatile(uint32_t a, uint64_t) {
-  uint64_t v;
-  asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
-  return v;
-}
+// Shared-memory compare-and-swap by shared-window address (no generic addressing).
 __device__ __forceinline__ uint32_t atoms_cas(uint32_t a, uint32_t c, uint32_t v) {
   uint32_t r;
   asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "r"(a), "r"(c), "r"(v) : "memory");
@@ -472,20 +462,15 @@ __device__ __forceinline__ uint64_t atoms_cas(uint32_t a, uint64_t c, uint64_t v
 // Insert k (!= kEmpty) into the set held in slots [rb, rb + rs) of the slot
 // array at shared-window address `base`; true iff this call put it there.
 // The region has more slots than keys are ever inserted into it, and probing
-// is bounded by its size.
+// is bounded by its size; the compare-and-swap is the probe itself.
 template <typename K>
 __device__ __forceinline__ bool region_insert(uint32_t base, uint32_t rb, uint32_t rs, K k) {
   uint32_t s = rb + region_home(k, rs);
   const uint32_t re = rb + rs;
   for (uint32_t t = 0; t < rs; ++t) {
-    const uint32_t a = base + s * (uint32_t)sizeof(K);
-    K cur = lds_volatile(a, K());
+    const K cur = atoms_cas(base + s * (uint32_t)sizeof(K), KeyOps<K>::kEmpty, k);
+    if (cur == KeyOps<K>::kEmpty) return true;
     if (cur == k) return false;
-    if (cur == KeyOps<K>::kEmpty) {
-      cur = atoms_cas(a, KeyOps<K>::kEmpty, k);
-      if (cur == KeyOps<K>::kEmpty) return true;
-      if (cur == k) return false;
-    }
     if (++s == re) s = rb;
   }
   return false;
@@ -704,15 +689,22 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
   const uint32_t cap = h.hub_cap[hub];
   uint32_t* cur = h.cursor + h.hub_bbase[hub];
   K* tmp = static_cast<K*>(h.tmp) + h.hub_tbase[hub];
-  if (in_smem) {
+  // rank of each key within its bucket in this chunk (shared counts), then one
+  // global reservation per bucket
+  uint32_t rank[kChunkItems];
 #pragma unroll
-    for (int t = 0; t < kChunkItems; ++t)
-      if (tid + t * kChunkThreads < E) atomicAdd(&bcnt[hub_bucket(key[t], bits)], 1u);
+  for (int t = 0; t < kChunkItems; ++t) {
+    rank[t] = 0;
+    if (tid + t * kChunkThreads < E) {
+      const uint32_t b = hub_bucket(key[t], bits);
+      rank[t] = in_smem ? atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
+    }
+  }
+  if (in_smem) {
     __syncthreads();
     for (uint32_t b = tid; b < nb; b += kChunkThreads) {
       const uint32_t n_b = bcnt[b];
       bpos[b] = n_b ? atomicAdd(&cur[b], n_b) : 0u;
-      bcnt[b] = 0;
     }
     __syncthreads();
   }
@@ -720,7 +712,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
   for (int t = 0; t < kChunkItems; ++t) {
     if (tid + t * kChunkThreads >= E) continue;
     const uint32_t b = hub_bucket(key[t], bits);
-    const uint32_t q = in_smem ? bpos[b] + atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
+    const uint32_t q = in_smem ? bpos[b] + rank[t] : rank[t];
     if (q < cap) tmp[(uint64_t)b * cap + q] = key[t];
     else atomicOr(a.err, kErrHubOverflow);
   }
@@ -728,20 +720,17 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
 
 // Insert k (!= kEmpty) into a power-of-two set of hmask + 1 slots at
 // shared-window address `base`, home slot from the key's low bits (the keys of
-// one hub bucket share their top bits); true iff this call put it there.
-// Returns 1 if this call inserted k, 0 if k was present, -1 if the set is full.
+// one hub bucket share their top bits).  The compare-and-swap is the probe
+// itself: one shared access per probed slot, whether the slot is empty, holds
+// k or holds another key.  Returns 1 if this call inserted k, 0 if k was
+// present, -1 if the set is full.
 template <typename K>
 __device__ __forceinline__ int pow2_insert(uint32_t base, uint32_t hmask, K k) {
   uint32_t s = key_h32(k) & hmask;
   for (uint32_t t = 0; t <= hmask; ++t) {
-    const uint32_t a = base + s * (uint32_t)sizeof(K);
-    K cur = lds_volatile(a, K());
+    const K cur = atoms_cas(base + s * (uint32_t)sizeof(K), KeyOps<K>::kEmpty, k);
+    if (cur == KeyOps<K>::kEmpty) return 1;
     if (cur == k) return 0;
-    if (cur == KeyOps<K>::kEmpty) {
-      cur = atoms_cas(a, KeyOps<K>::kEmpty, k);
-      if (cur == KeyOps<K>::kEmpty) return 1;
-      if (cur == k) return 0;
-    }
     s = (s + 1) & hmask;
   }
   return -1;
@@ -1085,7 +1074,14 @@ struct RankArgs {
   unsigned long long* stats;  // [2] key total, [3] max signature, [8] nodes alone in their block
 };
 
-__global__ void k_mark_heads(RankArgs r) {
+constexpr int kMarkThreads = 256, kMarkSeen = 256;
+
+__global__ void __launch_bounds__(kMarkThreads) k_mark_heads(RankArgs r) {
+  // heads this CTA has marked as having members: large blocks (a few blocks
+  // of millions of nodes at level 0) then cost no global access per member
+  __shared__ uint32_t seen[kMarkSeen];
+  for (int i = threadIdx.x; i < kMarkSeen; i += kMarkThreads) seen[i] = kNone32;
+  __syncthreads();
   unsigned long long keys = 0;
   unsigned int mx = 0;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n_alive;
@@ -1094,8 +1090,9 @@ __global__ void k_mark_heads(RankArgs r) {
     if (h == (uint32_t)p) {
       const uint32_t o = r.p2o[p];
       atomicOr(&r.hbits[o >> 5], 1u << (o & 31));
-    } else if (!*(volatile uint8_t*)&r.member[h]) {  // large blocks: most members find it set
-      r.member[h] = 1;
+    } else if (seen[h % kMarkSeen] != h) {
+      if (!*(volatile uint8_t*)&r.member[h]) r.member[h] = 1;
+      seen[h % kMarkSeen] = h;  // any value left here is a head already marked
     }
     if (r.ucnt) {
       const uint32_t q = r.ucnt[p];
@@ -1631,7 +1628,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     if (n) {
       cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
       cudaMemsetAsync(s.member.p, 0, n, s.stream);
-      k_mark_heads<<<gblocks, 256, 0, s.stream>>>(r);
+      k_mark_heads<<<gblocks, kMarkThreads, 0, s.stream>>>(r);
       k_word_counts<<<(unsigned)std::min<uint64_t>(grid_for(words, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(
           r.hbits, words, r.hword);
       if (!(st = scan64(s, r.hword, words, nullptr)).ok()) return st;
