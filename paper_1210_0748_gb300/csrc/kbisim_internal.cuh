@@ -296,6 +296,18 @@ void timer_destroy(Store& s);
 // Exclusive prefix sum of a uint64 array in place (kbisim_round.cu).
 Status scan_u64(Store& s, uint64_t* a, uint64_t n);
 
+// Thread blocks of `kernel` (threads each, dyn_smem dynamic shared bytes) that
+// are resident on all `sms` multiprocessors at once: the grid of a grid-stride
+// loop, which then runs as one full wave (a larger grid that is not a whole
+// number of waves leaves most multiprocessors idle in its last wave).
+template <typename F>
+inline unsigned resident_blocks(F kernel, int threads, size_t dyn_smem, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return (unsigned)per_sm * (unsigned)(sms > 0 ? sms : 1);
+}
+
 // Batched build (kbisim_many.cu): many_check_args before the union is loaded,
 // many_setup after it, then a refinement with many_level as the level hook.
 Status many_check_args(const kbisim_graph* g, const uint64_t* start, uint32_t G, const uint32_t* k,

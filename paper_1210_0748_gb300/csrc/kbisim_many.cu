@@ -213,7 +213,8 @@ Status many_level(Store& s, uint32_t l) {
   cudaMemsetAsync(m.tmin.p, 0xFF, cap * 4, s.stream);
   cudaMemsetAsync(m.hbits.p, 0, words * 4, s.stream);
   if (na) {
-    k_many_insert<<<grid_for(na, kAggChunk, sms * 8), kThreads, 0, s.stream>>>(a);
+    k_many_insert<<<grid_for(na, kAggChunk, (int)resident_blocks(k_many_insert, kThreads, 0, sms)), kThreads, 0,
+                    s.stream>>>(a);
     k_many_heads<<<grid_for(na, kThreads, sms * 16), kThreads, 0, s.stream>>>(a);
   }
   k_many_word_counts<<<grid_for(words, kThreads, sms * 16), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.hbits), words,

@@ -1551,7 +1551,8 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
     cudaMemsetAsync(s.table.p, 0xFF, tcap * 8, s.stream);
   }
-  const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8);
+  const unsigned ins_grid = resident_blocks(k_group_insert, kInsThreads, 0, sms);
+  const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, ins_grid);
   {
     TimedScope ts(s, KBISIM_KERNEL_GROUP, na ? 1 : 0);
     if (na) k_group_insert<<<iblocks, kInsThreads, 0, s.stream>>>(g, nullptr, na);
@@ -1589,7 +1590,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
       TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
       cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
       cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
-      k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, (uint64_t)sms * 8),
+      k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, ins_grid),
                        kInsThreads, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
       k_group_verify<<<b2, 256, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
     }
