@@ -200,9 +200,9 @@ struct Store {
   uint64_t hub_tmp_words = 0;  // key words of all hub buckets
   uint64_t n_hub_buckets = 0;
   uint64_t hub_edges = 0;
-  uint32_t hub_extra_bits = 0; // more buckets per hub: grows when a bucket's set fills
-  uint32_t hub_cap_shift = 0;  // larger buckets: grows when a bucket's capacity is exceeded
-  double hub_distinct_ratio = 0.0;  // distinct keys / edges of the hubs in the last round
+  std::vector<uint32_t> h_hub_xbits;  // per hub: more buckets, after a bucket's set filled
+  std::vector<uint32_t> h_hub_shift;  // per hub: larger buckets, after a bucket's capacity was exceeded
+  std::vector<uint8_t> h_hub_force;   // per hub: deduplicating chunk pass, after a scatter overflowed
   std::vector<uint32_t> h_hub_degbits;
   std::vector<uint64_t> h_hub_deg;
 
@@ -237,6 +237,9 @@ struct Store {
   Buf hub_cursor;              // uint32 [buckets] key words appended to each bucket
   Buf bucket_hub;              // uint32 [buckets] hub of each bucket
   Buf hub_acc;                 // per hub: keys written, term sum (uint64), buckets done (uint32)
+  Buf hub_mode;                // uint8 [hubs]: chunk pass of each hub this round (1 = no chunk set)
+  Buf hub_force;               // uint8 [hubs]: copy of h_hub_force
+  Buf hub_err;                 // uint32 [hubs]: overflow flags of the last hub pass
   Buf hub_tmp;                 // key words [hub_tmp_words]: fixed-capacity hub buckets
   static constexpr int kStageBufsN = 9;
   Buf stage[kStageBufsN];      // staging of host inputs and COO grouping (kbisim_load)

@@ -567,9 +567,13 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
 // their keys in shared memory as above (one region), listing each distinct
 // key once, and appends the list to the hub's buckets; the bucket of a key is
 // its top bits, so equal keys from different chunks meet in one bucket.
-// Buckets have a fixed capacity: an append past it raises kErrHubOverflow and
-// the host repeats the hub passes with larger buckets (kErrHubSet, from the
-// bucket pass, asks for more buckets instead).  Pass 2 (k_hub_bucket):
+// Hubs whose keys rarely repeat (k_hub_sample) skip the chunk set
+// (k_hub_scatter).  Buckets have a fixed capacity: an append past it flags the
+// hub (kErrHubOverflow) and the host repeats the hub passes with larger
+// buckets for that hub, or, for a scattering hub whose buckets have grown
+// twice already, with the deduplicating pass (a key repeated that often stays
+// repeated in later rounds); a bucket with more distinct keys than its set
+// (kErrHubSet) gives its hub more buckets.  Pass 2 (k_hub_bucket):
 // one CTA per bucket deduplicates across chunks and appends the bucket's
 // distinct keys at the hub's CSR offset; the last bucket of a hub to finish
 // writes its count and hash.
@@ -581,17 +585,26 @@ struct HubArgs {
   const uint64_t* hub_tbase;
   const uint32_t* bucket_hub;
   const uint4* chunks;
-  uint32_t extra_bits;
   uint32_t* cursor;              // per bucket: key words appended
   unsigned long long* hub_cur;   // per hub: distinct keys written
   uint32_t* hub_term;            // per hub: term sum halves (low, high)
   unsigned int* hub_done;        // per hub: buckets finished
   void* tmp;
+  uint8_t* mode;                 // per hub: 1 = chunks skip their set (few repeated keys)
+  const uint8_t* force;          // per hub: 1 = always the deduplicating chunk pass
+  uint32_t* hub_err;             // per hub: kErrHubOverflow / kErrHubSet raised for it
 };
+
+__device__ __forceinline__ void hub_fail(const SigArgs& a, const HubArgs& h, uint32_t hub, uint32_t e) {
+  atomicOr(&h.hub_err[hub], e);
+  atomicOr(a.err, e);
+}
 
 constexpr int kHubUcap = 4096;         // key words per bucket at most
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
-constexpr double kHubScatterRatio = 0.75;  // distinct / edges of the hubs above which chunks skip their set
+constexpr int kHubSample = 128;        // keys sampled per hub to choose its chunk pass
+constexpr int kHubSamplePairs = 4;     // equal sampled pairs from which a hub keeps the chunk set
+constexpr uint32_t kHubScatterShiftMax = 2;  // bucket growth of a scattering hub before it takes the set
 
 template <typename K>
 __host__ __device__ constexpr size_t hub_chunk_smem() {
@@ -613,9 +626,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
   uint32_t* bpos = bcnt + kHubSmemBuckets;
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
+  if (h.mode[hub]) return;  // this hub's chunks run k_hub_scatter
   const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
   const uint32_t E = c.w;
-  const uint32_t bits = h.hub_bits[hub] + h.extra_bits;
+  const uint32_t bits = h.hub_bits[hub];
   const uint32_t nb = 1u << bits;
   const bool in_smem = nb <= (uint32_t)kHubSmemBuckets;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
@@ -661,23 +675,57 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
     const uint32_t b = hub_bucket(v, bits);
     const uint32_t q = in_smem ? bpos[b] + atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
     if (q < cap) tmp[(uint64_t)b * cap + q] = v;
-    else atomicOr(a.err, kErrHubOverflow);
+    else hub_fail(a, h, hub, kErrHubOverflow);
   }
 }
 
-// Hub pieces without the chunk-level set, for rounds in which few hub keys
-// repeat: the keys of a chunk go straight to the hub's buckets (counted per
-// bucket in shared memory first, one global reservation per bucket), and the
-// bucket pass removes every duplicate.
+// Hub pieces without the chunk-level set, for hubs whose keys rarely repeat
+// (k_hub_sample): the keys of a chunk go straight to the hub's buckets
+// (ranked per bucket in shared memory, one global reservation per bucket), and
+// the bucket pass removes every duplicate.
+
+// One warp per hub: kHubSample keys at an even stride over the hub's edges.
+// Among S samples from U equally frequent distinct keys about S(S-1)/2 / U
+// pairs are equal: kHubSamplePairs or more equal pairs mean a few thousand
+// distinct keys or fewer (the few blocks of an early level), or a key that
+// makes up several percent of the hub's edges, and the hub keeps the chunk
+// set, which sends each distinct key of a chunk to the buckets once.  Other
+// hubs skip it, unless an earlier overflow forced the set on them.
+template <typename LabelT, typename K>
+__global__ void __launch_bounds__(256) k_hub_sample(SigArgs a, HubArgs h, uint64_t n_hub) {
+  constexpr int kPer = kHubSample / 32;
+  __shared__ K sk[256 / 32][kHubSample];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t hub = (uint64_t)blockIdx.x * (256 / 32) + w;
+  if (hub >= n_hub) return;
+  const uint64_t p = h.first + hub;
+  const uint64_t e0 = a.off[p], D = a.off[p + 1] - e0;
+  const uint32_t st = (uint32_t)(D / kHubSample);  // >= 1: hubs have more than 4096 edges
+  const Policies pol;
+  K key[kPer];
+  edge_keys<kPer, 0, kPer, LabelT, K>(a, e0 + (uint64_t)lane * st, 32u * st, e0 + D, pol, key);
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) sk[w][lane + 32 * t] = key[t];
+  __syncwarp();
+  uint32_t pairs = 0;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const uint32_t i = lane + 32 * t;
+    for (uint32_t j = i + 1; j < (uint32_t)kHubSample; ++j) pairs += sk[w][j] == key[t] ? 1u : 0u;
+  }
+  pairs = __reduce_add_sync(kFull, pairs);
+  if (lane == 0) h.mode[hub] = (!h.force[hub] && pairs < (uint32_t)kHubSamplePairs) ? 1 : 0;
+}
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArgs h) {
   __shared__ uint32_t bcnt[kHubSmemBuckets];
   __shared__ uint32_t bpos[kHubSmemBuckets];
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
+  if (!h.mode[hub]) return;  // this hub's chunks run k_hub_chunk
   const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
   const uint32_t E = c.w;
-  const uint32_t bits = h.hub_bits[hub] + h.extra_bits;
+  const uint32_t bits = h.hub_bits[hub];
   const uint32_t nb = 1u << bits;
   const bool in_smem = nb <= (uint32_t)kHubSmemBuckets;
   const uint32_t tid = threadIdx.x;
@@ -714,7 +762,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
     const uint32_t b = hub_bucket(key[t], bits);
     const uint32_t q = in_smem ? bpos[b] + rank[t] : rank[t];
     if (q < cap) tmp[(uint64_t)b * cap + q] = key[t];
-    else atomicOr(a.err, kErrHubOverflow);
+    else hub_fail(a, h, hub, kErrHubOverflow);
   }
 }
 
@@ -756,12 +804,28 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
   const uint32_t tid = threadIdx.x, lane = tid & 31;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.set);
   K* out = static_cast<K*>(a.sigkey);
+  // a bucket's hub, key count and first kBucketThreads * kBucketItems keys are
+  // loaded one bucket ahead, so that their latency overlaps the work on the
+  // bucket before
+  uint32_t nx_hub = 0, nx_n = 0;
+  const K* nx_tmp = nullptr;
+  K kk[kBucketItems];
+  auto fetch = [&](uint64_t bb) {
+    nx_hub = h.bucket_hub[bb];
+    const uint32_t cap = h.hub_cap[nx_hub];
+    nx_tmp = static_cast<const K*>(h.tmp) + h.hub_tbase[nx_hub] + (bb - h.hub_bbase[nx_hub]) * cap;
+    nx_n = min(h.cursor[bb], cap);
+#pragma unroll
+    for (int t = 0; t < kBucketItems; ++t) {
+      const uint32_t i = tid + t * kBucketThreads;
+      kk[t] = i < nx_n ? nx_tmp[i] : (K)0;
+    }
+  };
+  if (blockIdx.x < n_buckets) fetch(blockIdx.x);
   for (uint64_t b = blockIdx.x; b < n_buckets; b += gridDim.x) {
-    const uint32_t hub = h.bucket_hub[b];
+    const uint32_t hub = nx_hub, n = nx_n;
     const uint64_t p = h.first + hub;
-    const uint32_t cap = h.hub_cap[hub];
-    const K* tmp = static_cast<const K*>(h.tmp) + h.hub_tbase[hub] + (b - h.hub_bbase[hub]) * cap;
-    const uint32_t n = min(h.cursor[b], cap);
+    const K* tmp = nx_tmp;
     uint32_t hcap = 64;
     while (hcap < 2 * n && hcap < 2 * kHubUcap) hcap <<= 1;
     {
@@ -778,11 +842,12 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
     }
     __syncthreads();
     for (uint32_t i0 = 0; i0 < n; i0 += kBucketThreads * kBucketItems) {
-      K kk[kBucketItems];
+      if (i0) {
 #pragma unroll
-      for (int t = 0; t < kBucketItems; ++t) {
-        const uint32_t i = i0 + tid + t * kBucketThreads;
-        kk[t] = i < n ? tmp[i] : (K)0;
+        for (int t = 0; t < kBucketItems; ++t) {
+          const uint32_t i = i0 + tid + t * kBucketThreads;
+          kk[t] = i < n ? tmp[i] : (K)0;
+        }
       }
 #pragma unroll 1
       for (int t = 0; t < kBucketItems; ++t) {
@@ -811,9 +876,10 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
         }
       }
     }
+    if (b + gridDim.x < n_buckets) fetch(b + gridDim.x);
     __syncthreads();
     if (sm.full) {  // more distinct keys than the set holds: the host adds buckets
-      if (tid == 0) atomicOr(a.err, kErrHubSet);
+      if (tid == 0) hub_fail(a, h, hub, kErrHubSet);
       __syncthreads();
       continue;
     }
@@ -840,7 +906,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       atomicAdd(&h.hub_term[2 * hub], sm.lo);
       atomicAdd(&h.hub_term[2 * hub + 1], sm.hi);
       __threadfence();
-      const unsigned nb = 1u << (h.hub_bits[hub] + h.extra_bits);
+      const unsigned nb = 1u << h.hub_bits[hub];
       if (atomicAdd(&h.hub_done[hub], 1u) == nb - 1u) {
         __threadfence();
         const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
@@ -1658,12 +1724,12 @@ Status hub_layout(Store& s) {
   std::vector<uint64_t> bbase(s.n_hub + 1, 0), tbase(s.n_hub, 0);
   uint64_t words = 0;
   for (uint64_t i = 0; i < s.n_hub; ++i) {
-    bits[i] = s.h_hub_degbits[i];
-    const uint64_t nb = 1ull << (bits[i] + s.hub_extra_bits);
+    bits[i] = s.h_hub_degbits[i] + s.h_hub_xbits[i];
+    const uint64_t nb = 1ull << bits[i];
     bbase[i + 1] = bbase[i] + nb;
     const uint64_t mean = (s.h_hub_deg[i] + nb - 1) / nb;
     cap[i] = (uint32_t)std::min<uint64_t>(s.h_hub_deg[i], std::min<uint64_t>(kHubUcap, 2 * mean + 256)
-                                                                << s.hub_cap_shift);
+                                                                << s.h_hub_shift[i]);
     tbase[i] = words;
     words += nb * cap[i];
   }
@@ -1679,7 +1745,10 @@ Status hub_layout(Store& s) {
   if (!(st = ensure(s, s.bucket_hub, s.n_hub_buckets * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_cursor, s.n_hub_buckets * 4)).ok()) return st;
   if (!(st = ensure(s, s.hub_acc, s.n_hub * 24)).ok()) return st;
-  cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
+  if (!(st = ensure(s, s.hub_mode, s.n_hub)).ok()) return st;
+  if (!(st = ensure(s, s.hub_force, s.n_hub)).ok()) return st;
+  if (!(st = ensure(s, s.hub_err, s.n_hub * 4)).ok()) return st;
+  cudaMemcpyAsync(s.hub_force.p, s.h_hub_force.data(), s.n_hub, cudaMemcpyHostToDevice, s.stream);  cudaMemcpyAsync(s.hub_bits.p, bits.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.hub_cap.p, cap.data(), s.n_hub * 4, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.hub_bbase.p, bbase.data(), (s.n_hub + 1) * 8, cudaMemcpyHostToDevice, s.stream);
   cudaMemcpyAsync(s.hub_tbase.p, tbase.data(), s.n_hub * 8, cudaMemcpyHostToDevice, s.stream);
@@ -1743,46 +1812,56 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.hub_tbase = ptr<uint64_t>(s.hub_tbase);
       h.bucket_hub = ptr<uint32_t>(s.bucket_hub);
       h.chunks = ptr<uint4>(s.hub_chunks);
-      h.extra_bits = s.hub_extra_bits;
       h.cursor = ptr<uint32_t>(s.hub_cursor);
       h.hub_cur = ptr<unsigned long long>(s.hub_acc);
       h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
       h.hub_done = h.hub_term + 2 * s.n_hub;
       h.tmp = s.hub_tmp.p;
-      // chunk-level deduplication pays off while hub keys repeat (round 1, few
-      // blocks); afterwards the keys go straight to the buckets
-      const bool dedupe = s.hub_distinct_ratio < kHubScatterRatio;
+      h.mode = ptr<uint8_t>(s.hub_mode);
+      h.force = ptr<uint8_t>(s.hub_force);
+      h.hub_err = ptr<uint32_t>(s.hub_err);
       {
-        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 2);
+        // each hub's chunks run either the deduplicating pass or the plain
+        // scatter, as its key sample says; both kernels cover all chunks and
+        // skip those of the other kind
+        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 4);
         cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
-        if (dedupe)
-          k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
-        else
-          k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
-        const unsigned g = (unsigned)std::min<uint64_t>(s.n_hub_buckets, (uint64_t)sms * 8);
+        cudaMemsetAsync(s.hub_err.p, 0, s.n_hub * 4, s.stream);
+        k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(a, h, s.n_hub);
+        k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
+        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
+        const unsigned g = (unsigned)std::min<uint64_t>(
+            s.n_hub_buckets, resident_blocks(k_hub_bucket<K>, kBucketThreads, sizeof(BucketSmem<K>), sms));
         k_hub_bucket<K><<<g, kBucketThreads, sizeof(BucketSmem<K>), s.stream>>>(a, h, s.n_hub_buckets);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;
-      std::vector<uint64_t> distinct(s.n_hub);
       st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
-      if (st.ok())
-        st = cuda_check(cudaMemcpyAsync(distinct.data(), s.hub_acc.p, s.n_hub * 8, cudaMemcpyDeviceToHost, s.stream),
-                        "hub counts");
       if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
       if (!st.ok()) return st;
-      if (!(e & (kErrHubOverflow | kErrHubSet))) {
-        uint64_t u = 0;
-        for (uint64_t x : distinct) u += x;
-        s.hub_distinct_ratio = s.hub_edges ? (double)u / (double)s.hub_edges : 1.0;
-        break;
-      }
+      if (!(e & (kErrHubOverflow | kErrHubSet))) break;
       if (attempt >= 40) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
-      // too many key words for a bucket (keys repeated across chunks): larger
-      // buckets, up to the hub's degree; too many distinct keys: more buckets
-      if (e & kErrHubOverflow) s.hub_cap_shift += 1;
-      if (e & kErrHubSet) s.hub_extra_bits += 1;
+      std::vector<uint32_t> herr(s.n_hub);
+      std::vector<uint8_t> hmode(s.n_hub);
+      st = cuda_check(cudaMemcpyAsync(herr.data(), s.hub_err.p, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream),
+                      "hub flags");
+      if (st.ok())
+        st = cuda_check(cudaMemcpyAsync(hmode.data(), s.hub_mode.p, s.n_hub, cudaMemcpyDeviceToHost, s.stream),
+                        "hub modes");
+      if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+      if (!st.ok()) return st;
+      for (uint64_t i = 0; i < s.n_hub; ++i) {
+        // a bucket overflowed (a key repeated many times): larger buckets for
+        // the hub, up to its degree, or, once the scatter has overflowed
+        // buckets kHubScatterShiftMax times larger than the first, the
+        // deduplicating pass; too many distinct keys in a bucket: more buckets
+        if (herr[i] & kErrHubOverflow) {
+          if (hmode[i] && s.h_hub_shift[i] >= kHubScatterShiftMax) s.h_hub_force[i] = 1;
+          else s.h_hub_shift[i] += 1;
+        }
+        if (herr[i] & kErrHubSet) s.h_hub_xbits[i] += 1;
+      }
       if (!(st = hub_layout(s)).ok()) return st;
       cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
     }
@@ -1889,8 +1968,9 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
   s.n_alone = 0;
-  s.hub_extra_bits = 0;
-  s.hub_cap_shift = 0;
+  s.h_hub_xbits.assign(s.n_hub, 0);
+  s.h_hub_shift.assign(s.n_hub, 0);
+  s.h_hub_force.assign(s.n_hub, 0);
   s.h_hub_degbits.assign(s.n_hub, 0);
   s.h_hub_deg.assign(s.n_hub, 0);
   s.hub_edges = 0;
@@ -1983,7 +2063,6 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
 Status compute_level0(Store& s) {
   Status st = ensure_round_scratch(s);
   if (!st.ok()) return st;
-  s.hub_distinct_ratio = 0.0;  // round 1 packs labels: its hub keys repeat
   const int sms = sm_count(s.device);
   const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16);
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);

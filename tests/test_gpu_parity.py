@@ -408,3 +408,24 @@ def test_hubs_with_distinct_keys():
     assert_same(res, pids, ref)
     assert ref.rounds_run >= 2
     assert all(pids[lev][0] == pids[lev][1] for lev in range(pids.shape[0]))
+
+
+def test_hub_with_one_heavy_key_among_distinct_keys():
+    """A 1M-edge hub whose keys are all distinct but one, which makes up 1% of
+    its edges: a key sample finds few repeats, so the hub skips the chunk set,
+    the heavy key overflows its bucket, and the hub must be redone with the
+    chunk set; the result must still equal the oracle."""
+    rng = np.random.default_rng(41)
+    n = 100_000
+    nl = (np.arange(n) % 1000).astype(np.uint32)
+    c = np.arange(990_000)
+    hub_dst = np.concatenate([(c % 1000) + 1000 * rng.integers(0, n // 1000, c.size), np.full(10_000, 5)])
+    hub_lab = np.concatenate([c // 1000, np.zeros(10_000, np.int64)])
+    perm = rng.permutation(hub_dst.size)
+    other = 200_000
+    src = np.concatenate([np.zeros(hub_dst.size, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
+    dst = np.concatenate([hub_dst[perm], rng.integers(0, n, other)]).astype(np.uint32)
+    lab = np.concatenate([hub_lab[perm], rng.integers(0, 3, other)]).astype(np.uint32)
+    g = synth.from_coo(n, src, dst, lab, nl)
+    res, pids = gpu_levels(g, 3)
+    assert_same(res, pids, oracle_levels(g, 3))
