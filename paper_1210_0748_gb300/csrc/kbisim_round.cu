@@ -1020,6 +1020,8 @@ struct VerifyArgs {
   unsigned long long* n_collided;
   uint32_t* long_list;      // (node, candidate) pairs with long signatures
   unsigned long long* n_long;
+  uint32_t* hbits;          // head bitmap over original ids (canonical numbering)
+  uint8_t* member;          // per internal id: this head has other members
 };
 
 constexpr uint32_t kShortSig = 8;
@@ -1040,6 +1042,18 @@ __device__ __forceinline__ bool same_set_short(const K* a, const K* b, uint32_t 
   return true;
 }
 
+// Marks for the canonical numbering, set where a node's representative is
+// settled: a head sets the bit of its original id; a member sets its head's
+// member flag (read first: in a large block most members find it set).
+__device__ __forceinline__ void mark_head(const VerifyArgs& v, uint32_t o) {
+  atomicOr(&v.hbits[o >> 5], 1u << (o & 31));
+}
+__device__ __forceinline__ void mark_member(const VerifyArgs& v, uint32_t r) {
+  if (!*(volatile uint8_t*)&v.member[r]) v.member[r] = 1;
+}
+
+constexpr int kMarkSeen = 256;  // heads a verification CTA remembers as marked
+
 __device__ __forceinline__ void mark_unresolved(const VerifyArgs& v, uint32_t* rep, uint32_t p) {
   rep[p] = kNone32;
   const unsigned long long q = atomicAdd(v.n_out, 1ull);
@@ -1048,12 +1062,25 @@ __device__ __forceinline__ void mark_unresolved(const VerifyArgs& v, uint32_t* r
 }
 
 __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, uint64_t count) {
+  // heads this CTA has marked as having members: a block of millions of
+  // nodes (level 0) then costs one global access per CTA, not per member
+  __shared__ uint32_t seen[kMarkSeen];
+  for (int i = threadIdx.x; i < kMarkSeen; i += blockDim.x) seen[i] = kNone32;
+  __syncthreads();
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t p = list ? list[i] : (uint32_t)i;
-    if (g.alone && g.alone[p]) { g.rep[p] = p; continue; }
+    if (g.alone && g.alone[p]) {
+      g.rep[p] = p;
+      mark_head(v, g.p2o[p]);
+      continue;
+    }
     const uint32_t ro = (uint32_t)g.table[g.slot[p]];
-    if (ro == g.p2o[p]) { g.rep[p] = p; continue; }
+    if (ro == g.p2o[p]) {
+      g.rep[p] = p;
+      mark_head(v, ro);
+      continue;
+    }
     const uint32_t r = g.o2p[ro];
     bool eq;
     if (v.mode == 0) {
@@ -1074,7 +1101,12 @@ __global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, 
                                       static_cast<const uint32_t*>(v.sigkey) + v.off[r], U);
       }
     }
-    if (eq) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
+    if (eq) {
+      g.rep[p] = r;
+      if (atomicCAS(&seen[r % kMarkSeen], kNone32, r) != r) mark_member(v, r);
+    } else {
+      mark_unresolved(v, g.rep, p);
+    }
   }
 }
 
@@ -1110,7 +1142,12 @@ __global__ void __launch_bounds__(kVerThreads) k_verify_long(GroupArgs g, Verify
     }
     found = team_sum<kVerThreads>(found, ts.red, threadIdx.x);
     if (threadIdx.x == 0) {
-      if (found == U) g.rep[p] = r; else mark_unresolved(v, g.rep, p);
+      if (found == U) {
+        g.rep[p] = r;
+        mark_member(v, r);
+      } else {
+        mark_unresolved(v, g.rep, p);
+      }
     }
     __syncthreads();
   }
@@ -1139,45 +1176,6 @@ struct RankArgs {
   uint32_t* pid;           // output level, internal order
   unsigned long long* stats;  // [2] key total, [3] max signature, [8] nodes alone in their block
 };
-
-constexpr int kMarkThreads = 256, kMarkSeen = 256;
-
-__global__ void __launch_bounds__(kMarkThreads) k_mark_heads(RankArgs r) {
-  // heads this CTA has marked as having members: large blocks (a few blocks
-  // of millions of nodes at level 0) then cost no global access per member
-  __shared__ uint32_t seen[kMarkSeen];
-  for (int i = threadIdx.x; i < kMarkSeen; i += kMarkThreads) seen[i] = kNone32;
-  __syncthreads();
-  unsigned long long keys = 0;
-  unsigned int mx = 0;
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n_alive;
-       p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t h = r.rep[p];
-    if (h == (uint32_t)p) {
-      const uint32_t o = r.p2o[p];
-      atomicOr(&r.hbits[o >> 5], 1u << (o & 31));
-    } else if (seen[h % kMarkSeen] != h) {
-      if (!*(volatile uint8_t*)&r.member[h]) r.member[h] = 1;
-      seen[h % kMarkSeen] = h;  // any value left here is a head already marked
-    }
-    if (r.ucnt) {
-      const uint32_t q = r.ucnt[p];
-      keys += q;
-      mx = max(mx, q);
-    }
-  }
-  if (r.ucnt) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      keys += __shfl_xor_sync(kFull, keys, o);
-      mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&r.stats[2], keys);
-      atomicMax(&r.stats[3], (unsigned long long)mx);
-    }
-  }
-}
 
 __global__ void k_word_counts(const uint32_t* hbits, uint64_t words, uint64_t* hword) {
   for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x)
@@ -1225,10 +1223,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint64_t* bsum, uin
 
 // Every alive node takes its head's block id; deleted nodes get kDead.
 __global__ void k_pid_fill(RankArgs r) {
-  unsigned int n_alone = 0;
+  unsigned int n_alone = 0, mx = 0;
+  unsigned long long keys = 0;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n;
        p += (uint64_t)gridDim.x * blockDim.x) {
     if (p < r.n_alive) {
+      if (r.ucnt) {
+        const uint32_t q = r.ucnt[p];
+        keys += q;
+        mx = max(mx, q);
+      }
       const uint32_t h = r.rep[p];
       const uint32_t o = r.p2o[h];
       const uint32_t w = o >> 5;
@@ -1242,6 +1246,17 @@ __global__ void k_pid_fill(RankArgs r) {
   }
   n_alone = __reduce_add_sync(kFull, n_alone);
   if ((threadIdx.x & 31) == 0 && n_alone) atomicAdd(&r.stats[8], (unsigned long long)n_alone);
+  if (r.ucnt) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      keys += __shfl_xor_sync(kFull, keys, o);
+      mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&r.stats[2], keys);
+      atomicMax(&r.stats[3], (unsigned long long)mx);
+    }
+  }
 }
 
 // Level 0 hash: the node label.
@@ -1601,11 +1616,18 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.n_collided = sc + 4;
   v.long_list = ptr<uint32_t>(s.long_pairs);
   v.n_long = sc + 6;
+  v.hbits = ptr<uint32_t>(s.hbits);
+  v.member = ptr<uint8_t>(s.member);
+  const uint64_t words = (n + 31) / 32;
   const int sms = sm_count(s.device);
-  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), (uint64_t)sms * 16);
+  const unsigned ver_grid = resident_blocks(k_group_verify, 256, 0, sms);
+  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), ver_grid);
   {
     TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
     cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
+    // marks of the canonical numbering, set as representatives are settled
+    cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
+    cudaMemsetAsync(s.member.p, 0, n, s.stream);
   }
   v.out_list = ptr<uint32_t>(s.ulist[0]);
   v.n_out = sc + 1;
@@ -1651,7 +1673,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     VerifyArgs v2 = v;
     v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
     v2.n_out = sc + 5;
-    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), (uint64_t)sms * 16);
+    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), ver_grid);
     {
       TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
       cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
@@ -1677,7 +1699,6 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   }
   *collided = h[4];
   // canonical renumbering
-  const uint64_t words = (n + 31) / 32;
   RankArgs r;
   r.n = n;
   r.n_alive = na;
@@ -1691,11 +1712,8 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   r.pid = pid;
   r.stats = sc;
   {
-    TimedScope ts(s, KBISIM_KERNEL_RENUMBER, n ? 7 : 0);  // 4 kernels + the 3 of scan64
+    TimedScope ts(s, KBISIM_KERNEL_RENUMBER, n ? 5 : 0);  // 2 kernels + the 3 of scan64
     if (n) {
-      cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
-      cudaMemsetAsync(s.member.p, 0, n, s.stream);
-      k_mark_heads<<<gblocks, kMarkThreads, 0, s.stream>>>(r);
       k_word_counts<<<(unsigned)std::min<uint64_t>(grid_for(words, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(
           r.hbits, words, r.hword);
       if (!(st = scan64(s, r.hword, words, nullptr)).ok()) return st;

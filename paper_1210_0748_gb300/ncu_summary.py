@@ -36,7 +36,7 @@ CLASS_OF = [
     (r"k_hub_sample|k_hub_chunk|k_hub_scatter|k_hub_bucket", "sig_hub"),
     (r"k_group_insert", "group"),
     (r"k_group_verify|k_verify_long", "verify"),
-    (r"k_mark_heads|k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill", "renumber"),
+    (r"k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill", "renumber"),
 ]
 
 UNITS = {"ns": 1e-9, "nsecond": 1e-9, "us": 1e-6, "usecond": 1e-6, "ms": 1e-3, "msecond": 1e-3,
