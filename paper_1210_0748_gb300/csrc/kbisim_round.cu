@@ -970,39 +970,76 @@ __global__ void __launch_bounds__(kInsThreads) k_group_insert(GroupArgs g, const
   __shared__ unsigned long long skey[kInsSlots];
   __shared__ unsigned int smin[kInsSlots];
   __shared__ unsigned int sglob[kInsSlots];
+  __shared__ unsigned short used[kInsChunk];  // slots taken in this chunk (one per distinct hash)
+  __shared__ unsigned int n_used;
+  const uint32_t lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kInsSlots; i += kInsThreads) {
+    skey[i] = kEmpty64;
+    smin[i] = kNone32;
+  }
+  if (threadIdx.x == 0) n_used = 0;
+  __syncthreads();
   for (uint64_t base = (uint64_t)blockIdx.x * kInsChunk; base < count; base += (uint64_t)gridDim.x * kInsChunk) {
-    for (int i = threadIdx.x; i < kInsSlots; i += kInsThreads) {
-      skey[i] = kEmpty64;
-      smin[i] = kNone32;
-    }
-    __syncthreads();
-    uint32_t ls[kInsItems], pp[kInsItems];
+    // loads of all items first (node ids, then alone flags, then hashes and
+    // original ids of the nodes that are grouped), so that they overlap
+    uint32_t ls[kInsItems], pp[kInsItems], oo[kInsItems];
+    uint64_t hh[kInsItems];
 #pragma unroll
     for (int t = 0; t < kInsItems; ++t) {
       const uint64_t i = base + threadIdx.x + (uint64_t)t * kInsThreads;
-      ls[t] = kNone32;
-      if (i < count) {
-        const uint32_t p = list ? list[i] : (uint32_t)i;
-        pp[t] = p;
-        if (g.alone && g.alone[p]) continue;
-        const uint64_t h = g.hash[p];
+      pp[t] = i < count ? (list ? list[i] : (uint32_t)i) : kNone32;
+    }
+#pragma unroll
+    for (int t = 0; t < kInsItems; ++t)
+      ls[t] = (pp[t] != kNone32 && !(g.alone && g.alone[pp[t]])) ? 0u : kNone32;
+#pragma unroll
+    for (int t = 0; t < kInsItems; ++t) {
+      if (ls[t] != kNone32) {
+        hh[t] = g.hash[pp[t]];
+        oo[t] = g.p2o[pp[t]];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kInsItems; ++t) {
+      bool took = false;
+      if (ls[t] != kNone32) {
+        const uint64_t h = hh[t];
         uint32_t s = (uint32_t)(mix64(h) & (kInsSlots - 1));
         for (int q = 0; q < kInsSlots; ++q) {  // at most kInsChunk distinct hashes: always room
           const unsigned long long cur = atomicCAS(&skey[s], (unsigned long long)kEmpty64, (unsigned long long)h);
-          if (cur == kEmpty64 || cur == h) break;
+          if (cur == kEmpty64) { took = true; break; }
+          if (cur == h) break;
           s = (s + 1) & (kInsSlots - 1);
         }
-        atomicMin(&smin[s], g.p2o[p]);
+        atomicMin(&smin[s], oo[t]);
         ls[t] = s;
+      }
+      const unsigned tm = __ballot_sync(kFull, took);
+      if (tm) {
+        uint32_t b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&n_used, (unsigned)__popc(tm));
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (took) used[b0 + __popc(tm & lanes_below(lane))] = (unsigned short)ls[t];
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kInsSlots; i += kInsThreads)
-      if (skey[i] != kEmpty64) sglob[i] = table_insert(g, skey[i], smin[i]);
+    const uint32_t nu = n_used;
+    for (uint32_t i = threadIdx.x; i < nu; i += kInsThreads) {
+      const uint32_t sl = used[i];
+      sglob[sl] = table_insert(g, skey[sl], smin[sl]);
+    }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kInsItems; ++t)
       if (ls[t] != kNone32) g.slot[pp[t]] = sglob[ls[t]];
+    __syncthreads();
+    // only the slots this chunk took are cleared for the next one
+    for (uint32_t i = threadIdx.x; i < nu; i += kInsThreads) {
+      const uint32_t sl = used[i];
+      skey[sl] = kEmpty64;
+      smin[sl] = kNone32;
+    }
+    if (threadIdx.x == 0) n_used = 0;
     __syncthreads();
   }
 }
