@@ -1098,51 +1098,88 @@ __device__ __forceinline__ void mark_unresolved(const VerifyArgs& v, uint32_t* r
   atomicAdd(v.n_collided, 1ull);
 }
 
-__global__ void k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list, uint64_t count) {
+// Each thread takes kVerItems nodes of a tile at a time, and every step's
+// loads for all of them are issued together (node ids; alone flags; original
+// ids and table slots; representatives; their fields; the short key lists).
+constexpr int kVerNodeThreads = 256, kVerItems = 4, kVerTile = kVerNodeThreads * kVerItems;
+
+__global__ void __launch_bounds__(kVerNodeThreads) k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list,
+                                                                   uint64_t count) {
   // heads this CTA has marked as having members: a block of millions of
   // nodes (level 0) then costs one global access per CTA, not per member
   __shared__ uint32_t seen[kMarkSeen];
-  for (int i = threadIdx.x; i < kMarkSeen; i += blockDim.x) seen[i] = kNone32;
+  for (int i = threadIdx.x; i < kMarkSeen; i += kVerNodeThreads) seen[i] = kNone32;
   __syncthreads();
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = list ? list[i] : (uint32_t)i;
-    if (g.alone && g.alone[p]) {
-      g.rep[p] = p;
-      mark_head(v, g.p2o[p]);
-      continue;
+  for (uint64_t base = (uint64_t)blockIdx.x * kVerTile; base < count; base += (uint64_t)gridDim.x * kVerTile) {
+    uint32_t p[kVerItems], o[kVerItems], x[kVerItems], r[kVerItems], U[kVerItems];
+    bool act[kVerItems], eq[kVerItems];
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t) {
+      const uint64_t i = base + threadIdx.x + (uint64_t)t * kVerNodeThreads;
+      p[t] = i < count ? (list ? list[i] : (uint32_t)i) : kNone32;
     }
-    const uint32_t ro = (uint32_t)g.table[g.slot[p]];
-    if (ro == g.p2o[p]) {
-      g.rep[p] = p;
-      mark_head(v, ro);
-      continue;
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t) act[t] = p[t] != kNone32 && !(g.alone && g.alone[p[t]]);
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t) {
+      if (p[t] != kNone32) o[t] = g.p2o[p[t]];
+      if (act[t]) x[t] = g.slot[p[t]];
     }
-    const uint32_t r = g.o2p[ro];
-    bool eq;
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t)
+      if (act[t]) x[t] = (uint32_t)g.table[x[t]];  // smallest original id of the node's hash
+    // heads: alone in the previous block, or the smallest id of their hash
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t) {
+      if (p[t] != kNone32 && (!act[t] || x[t] == o[t])) {
+        g.rep[p[t]] = p[t];
+        mark_head(v, o[t]);
+        act[t] = false;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t)
+      if (act[t]) r[t] = g.o2p[x[t]];
     if (v.mode == 0) {
-      eq = v.nlabel[p] == v.nlabel[r];
+#pragma unroll
+      for (int t = 0; t < kVerItems; ++t)
+        if (act[t]) eq[t] = v.nlabel[p[t]] == v.nlabel[r[t]];
     } else {
-      const uint32_t U = v.ucnt[p];
-      eq = v.prev[p] == v.prev[r] && U == v.ucnt[r];
-      if (eq && U > kShortSig) {  // long signature: compared by a CTA later
-        const unsigned long long q = atomicAdd(v.n_long, 1ull);
-        v.long_list[2 * q] = p;
-        v.long_list[2 * q + 1] = r;
-        continue;
+#pragma unroll
+      for (int t = 0; t < kVerItems; ++t) {
+        if (act[t]) {
+          U[t] = v.ucnt[p[t]];
+          eq[t] = v.prev[p[t]] == v.prev[r[t]] && U[t] == v.ucnt[r[t]];
+        }
       }
-      if (eq) {
-        eq = v.key64 ? same_set_short(static_cast<const uint64_t*>(v.sigkey) + v.off[p],
-                                      static_cast<const uint64_t*>(v.sigkey) + v.off[r], U)
-                     : same_set_short(static_cast<const uint32_t*>(v.sigkey) + v.off[p],
-                                      static_cast<const uint32_t*>(v.sigkey) + v.off[r], U);
+#pragma unroll
+      for (int t = 0; t < kVerItems; ++t) {
+        if (act[t] && eq[t] && U[t] > kShortSig) {  // long signature: compared by a CTA later
+          const unsigned long long q = atomicAdd(v.n_long, 1ull);
+          v.long_list[2 * q] = p[t];
+          v.long_list[2 * q + 1] = r[t];
+          act[t] = false;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kVerItems; ++t) {
+        if (act[t] && eq[t]) {
+          eq[t] = v.key64 ? same_set_short(static_cast<const uint64_t*>(v.sigkey) + v.off[p[t]],
+                                           static_cast<const uint64_t*>(v.sigkey) + v.off[r[t]], U[t])
+                          : same_set_short(static_cast<const uint32_t*>(v.sigkey) + v.off[p[t]],
+                                           static_cast<const uint32_t*>(v.sigkey) + v.off[r[t]], U[t]);
+        }
       }
     }
-    if (eq) {
-      g.rep[p] = r;
-      if (atomicCAS(&seen[r % kMarkSeen], kNone32, r) != r) mark_member(v, r);
-    } else {
-      mark_unresolved(v, g.rep, p);
+#pragma unroll
+    for (int t = 0; t < kVerItems; ++t) {
+      if (!act[t]) continue;
+      if (eq[t]) {
+        g.rep[p[t]] = r[t];
+        if (atomicCAS(&seen[r[t] % kMarkSeen], kNone32, r[t]) != r[t]) mark_member(v, r[t]);
+      } else {
+        mark_unresolved(v, g.rep, p[t]);
+      }
     }
   }
 }
@@ -1657,8 +1694,8 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.member = ptr<uint8_t>(s.member);
   const uint64_t words = (n + 31) / 32;
   const int sms = sm_count(s.device);
-  const unsigned ver_grid = resident_blocks(k_group_verify, 256, 0, sms);
-  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, 256), ver_grid);
+  const unsigned ver_grid = resident_blocks(k_group_verify, kVerNodeThreads, 0, sms);
+  const unsigned gblocks = (unsigned)std::min<uint64_t>(grid_for(na, kVerTile), ver_grid);
   {
     TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
     cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
@@ -1685,7 +1722,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   if (!(st = launch_check("k_group_insert")).ok()) return st;
   {
     TimedScope ts(s, KBISIM_KERNEL_VERIFY, 1);
-    k_group_verify<<<gblocks, 256, 0, s.stream>>>(g, v, nullptr, na);
+    k_group_verify<<<gblocks, kVerNodeThreads, 0, s.stream>>>(g, v, nullptr, na);
   }
   if (!(st = launch_check("k_group_verify")).ok()) return st;
   uint64_t h[16];
@@ -1710,14 +1747,14 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     VerifyArgs v2 = v;
     v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
     v2.n_out = sc + 5;
-    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, 256), ver_grid);
+    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, kVerTile), ver_grid);
     {
       TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
       cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
       cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
       k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, ins_grid),
                        kInsThreads, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
-      k_group_verify<<<b2, 256, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+      k_group_verify<<<b2, kVerNodeThreads, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
     }
     if (!(st = launch_check("collision repair")).ok()) return st;
     if (!(st = read_scalars(s, h)).ok()) return st;
