@@ -452,7 +452,7 @@ def main():
     traffic = recorded_traffic(dom, args.scale) if args.workload == "single" else None
     names = {"sig_small": "k_sig_small (out-degree <= 64, one thread per node)",
              "sig_medium": "k_sig_chunk (out-degree 65..4096, CTA chunks)",
-             "sig_hub": "k_hub_sample, k_hub_chunk or k_hub_scatter per hub, then k_hub_bucket (out-degree > 4096)",
+             "sig_hub": "k_hub_sample, k_hub_chunk or k_hub_scatter per hub, k_hub_bucket, k_hub_finish (out-degree > 4096)",
              "group": "k_group_insert", "verify": "k_group_verify", "renumber": "renumbering kernels"}
     roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": d["achieved"], "peak": peak,
                 "unit": "GB/s", "frac": d["frac"], "peak_kind": peak_kind, "traffic": traffic,

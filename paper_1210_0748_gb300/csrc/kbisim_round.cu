@@ -575,8 +575,8 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
 // repeated in later rounds); a bucket with more distinct keys than its set
 // (kErrHubSet) gives its hub more buckets.  Pass 2 (k_hub_bucket):
 // one CTA per bucket deduplicates across chunks and appends the bucket's
-// distinct keys at the hub's CSR offset; the last bucket of a hub to finish
-// writes its count and hash.
+// distinct keys at the hub's CSR offset, adding to the hub's count and term
+// sums; k_hub_finish then writes each hub's count and hash.
 struct HubArgs {
   uint64_t first;           // internal id of hub 0
   const uint32_t* hub_bits;
@@ -588,7 +588,6 @@ struct HubArgs {
   uint32_t* cursor;              // per bucket: key words appended
   unsigned long long* hub_cur;   // per hub: distinct keys written
   uint32_t* hub_term;            // per hub: term sum halves (low, high)
-  unsigned int* hub_done;        // per hub: buckets finished
   void* tmp;
   uint8_t* mode;                 // per hub: 1 = chunks skip their set (few repeated keys)
   const uint8_t* force;          // per hub: 1 = always the deduplicating chunk pass
@@ -795,8 +794,8 @@ struct BucketSmem {
 };
 
 // One CTA per hub bucket (grid-stride): distinct keys of the bucket into a
-// shared set and list, then appended at the hub's CSR offset with their term
-// sums; the last bucket of a hub writes the hub's count and hash.
+// shared set and list, then appended at the hub's CSR offset, their term
+// sums added to the hub's.
 template <typename K>
 __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -883,15 +882,13 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       __syncthreads();
       continue;
     }
+    // the output reservation is in flight while the term sums are formed;
+    // the hub's count and hash are written by k_hub_finish
     const uint32_t U = sm.cnt;
     if (tid == 0) sm.obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
-    __syncthreads();
-    const uint64_t off = a.off[p] + sm.obase;
     uint32_t lo = 0, hi = 0;
     for (uint32_t i = tid; i < U; i += kBucketThreads) {
-      const K k = sm.uniq[i];
-      out[off + i] = k;
-      const uint64_t tm = elem_term(k, a.seed);
+      const uint64_t tm = elem_term(sm.uniq[i], a.seed);
       lo += (uint32_t)tm;
       hi += (uint32_t)(tm >> 32);
     }
@@ -902,21 +899,26 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       atomicAdd(&sm.hi, hi);
     }
     __syncthreads();
+    const uint64_t off = a.off[p] + sm.obase;
+    for (uint32_t i = tid; i < U; i += kBucketThreads) out[off + i] = sm.uniq[i];
     if (tid == 0) {
       atomicAdd(&h.hub_term[2 * hub], sm.lo);
       atomicAdd(&h.hub_term[2 * hub + 1], sm.hi);
-      __threadfence();
-      const unsigned nb = 1u << h.hub_bits[hub];
-      if (atomicAdd(&h.hub_done[hub], 1u) == nb - 1u) {
-        __threadfence();
-        const unsigned long long tot = atomicAdd(&h.hub_cur[hub], 0ull);
-        const unsigned long long tsum = ((unsigned long long)atomicAdd(&h.hub_term[2 * hub + 1], 0u) << 32) |
-                                        atomicAdd(&h.hub_term[2 * hub], 0u);
-        a.ucnt[p] = (uint32_t)tot;
-        a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
-      }
     }
-    __syncthreads();
+    // no barrier here: the next bucket's first barrier comes before anything
+    // this bucket's output reads is written again
+  }
+}
+
+// Count and hash of every hub from its buckets' totals.
+__global__ void k_hub_finish(SigArgs a, HubArgs h, uint64_t n_hub) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_hub;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = h.first + i;
+    const unsigned long long tot = h.hub_cur[i];
+    const uint64_t tsum = ((uint64_t)h.hub_term[2 * i + 1] << 32) | h.hub_term[2 * i];
+    a.ucnt[p] = (uint32_t)tot;
+    a.hash[p] = node_hash(tsum, a.prev[p], tot, a.seed, a.mask);
   }
 }
 
@@ -1907,8 +1909,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
       h.cursor = ptr<uint32_t>(s.hub_cursor);
       h.hub_cur = ptr<unsigned long long>(s.hub_acc);
       h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
-      h.hub_done = h.hub_term + 2 * s.n_hub;
-      h.tmp = s.hub_tmp.p;
+        h.tmp = s.hub_tmp.p;
       h.mode = ptr<uint8_t>(s.hub_mode);
       h.force = ptr<uint8_t>(s.hub_force);
       h.hub_err = ptr<uint32_t>(s.hub_err);
@@ -1916,7 +1917,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
         // each hub's chunks run either the deduplicating pass or the plain
         // scatter, as its key sample says; both kernels cover all chunks and
         // skip those of the other kind
-        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 4);
+        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 5);
         cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
         cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
         cudaMemsetAsync(s.hub_err.p, 0, s.n_hub * 4, s.stream);
@@ -1926,6 +1927,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
         const unsigned g = (unsigned)std::min<uint64_t>(
             s.n_hub_buckets, resident_blocks(k_hub_bucket<K>, kBucketThreads, sizeof(BucketSmem<K>), sms));
         k_hub_bucket<K><<<g, kBucketThreads, sizeof(BucketSmem<K>), s.stream>>>(a, h, s.n_hub_buckets);
+        k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(a, h, s.n_hub);
       }
       if (!(st = launch_check("hub kernels")).ok()) return st;
       uint32_t e = 0;

@@ -33,7 +33,7 @@ CLASS_OF = [
     (r"k_label_hash", "label_group"),
     (r"k_sig_small", "sig_small"),
     (r"k_sig_chunk", "sig_medium"),
-    (r"k_hub_sample|k_hub_chunk|k_hub_scatter|k_hub_bucket", "sig_hub"),
+    (r"k_hub_sample|k_hub_chunk|k_hub_scatter|k_hub_bucket|k_hub_finish", "sig_hub"),
     (r"k_group_insert", "group"),
     (r"k_group_verify|k_verify_long", "verify"),
     (r"k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill", "renumber"),
