@@ -1378,7 +1378,7 @@ __device__ __forceinline__ int node_class(uint64_t o, uint64_t n, const uint64_t
 // edge, put into kHotBuckets buckets; it affects speed only, never results.
 constexpr int kHotBuckets = 8;
 constexpr int kNumOrder = kNumClasses * kHotBuckets;
-constexpr int kHotSampleShift = 6;
+constexpr int kHotSampleShift = 8;
 
 __device__ __forceinline__ int hot_bucket(uint32_t c) {
   return c >= 1024 ? 0 : c >= 256 ? 1 : c >= 64 ? 2 : c >= 16 ? 3 : c >= 4 ? 4 : c >= 2 ? 5 : c >= 1 ? 6 : 7;
@@ -1454,16 +1454,72 @@ __global__ void k_relabel_nodes(uint64_t n, const uint32_t* p2o, const uint64_t*
 }
 
 // Copy out-edges to the segment of their source's internal id, relabelling
-// targets: one thread per original node of out-degree <= 32 (reads stream in
-// order), one warp per larger node.
-// Nodes of out-degree <= kSmallMax (any class, deleted nodes included): one
-// thread per node in internal order, so the writes of a warp fill one
-// contiguous range of the new edge table.
+// targets.  Every lane handles kRelItems edges at a time, all their loads in
+// flight together (targets and labels, then the identifier gathers).
+constexpr int kRelItems = 4;
+
+// Out-degree <= kSmallMax: one warp per 32 consecutive internal nodes, whose
+// edges form one contiguous range of the new table.  Lane k copies edges k,
+// k + 32, ... of that range; an edge's node is found by a binary search over
+// the 32 new offsets the lanes hold, so reads follow each node's edges in
+// order and writes fill the range coalesced.
 template <typename TI, typename TO>
-__global__ void k_relabel_edges_small(uint64_t n, const uint32_t* p2o, const uint32_t* o2p, const uint64_t* off0,
-                                      const uint32_t* dst0, const TI* lab0, const uint64_t* off, uint32_t* dst,
-                                      TO* lab) {
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+__global__ void k_relabel_edges_small(uint64_t n_small, const uint32_t* p2o, const uint32_t* o2p,
+                                      const uint64_t* off0, const uint32_t* dst0, const TI* lab0, const uint64_t* off,
+                                      uint32_t* dst, TO* lab) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < n_small; w += warps) {
+    const uint64_t p = w * 32 + lane;
+    const uint64_t base = off[w * 32];
+    const uint64_t end = off[min(w * 32 + 32, n_small)];
+    // lanes past the last node hold the range's end: an empty node there
+    const uint32_t r1 = (uint32_t)((p < n_small ? off[p] : end) - base);
+    const uint64_t s0 = p < n_small ? off0[p2o[p]] : 0;
+    const uint32_t T = (uint32_t)(end - base);  // at most 32 * kSmallMax
+    for (uint32_t k0 = 0; k0 < T; k0 += 32 * kRelItems) {
+      uint64_t src[kRelItems];
+#pragma unroll
+      for (int t = 0; t < kRelItems; ++t) {
+        const uint32_t k = min(k0 + lane + 32u * t, T - 1);
+        uint32_t j = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1)
+          if (__shfl_sync(kFull, r1, j + step) <= k) j += step;
+        src[t] = __shfl_sync(kFull, s0, j) + (k - __shfl_sync(kFull, r1, j));
+      }
+      uint32_t dv[kRelItems];
+      TI lv[kRelItems];
+#pragma unroll
+      for (int t = 0; t < kRelItems; ++t) {
+        if (k0 + lane + 32u * t < T) {
+          dv[t] = dst0[src[t]];
+          lv[t] = lab0[src[t]];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kRelItems; ++t)
+        if (k0 + lane + 32u * t < T) dv[t] = o2p[dv[t]];
+#pragma unroll
+      for (int t = 0; t < kRelItems; ++t) {
+        const uint32_t k = k0 + lane + 32u * t;
+        if (k < T) {
+          dst[base + k] = dv[t];
+          lab[base + k] = (TO)lv[t];
+        }
+      }
+    }
+  }
+}
+
+// Deleted nodes (their own class, last): one thread per node; those of
+// out-degree <= kSmallMax keep their edges in the new table.
+template <typename TI, typename TO>
+__global__ void k_relabel_edges_dead(uint64_t p_first, uint64_t p_end, const uint32_t* p2o, const uint32_t* o2p,
+                                     const uint64_t* off0, const uint32_t* dst0, const TI* lab0, const uint64_t* off,
+                                     uint32_t* dst, TO* lab) {
+  for (uint64_t p = p_first + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < p_end;
+       p += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t o = p2o[p];
     const uint64_t s0 = off0[o], d = off0[o + 1] - s0;
     if (d > (uint64_t)kSmallMax) continue;
@@ -1475,19 +1531,48 @@ __global__ void k_relabel_edges_small(uint64_t n, const uint32_t* p2o, const uin
   }
 }
 
+// Copy d edges from src to dst_at in the new table, kRelItems per lane at a
+// time, `lane` of `lanes` threads.
+template <typename TI, typename TO>
+__device__ __forceinline__ void relabel_run(uint64_t src, uint64_t at, uint64_t d, uint32_t lane, uint32_t lanes,
+                                            const uint32_t* o2p, const uint32_t* dst0, const TI* lab0, uint32_t* dst,
+                                            TO* lab) {
+  for (uint64_t i0 = 0; i0 < d; i0 += (uint64_t)lanes * kRelItems) {
+    uint32_t dv[kRelItems];
+    TI lv[kRelItems];
+#pragma unroll
+    for (int t = 0; t < kRelItems; ++t) {
+      const uint64_t i = i0 + lane + (uint64_t)t * lanes;
+      if (i < d) {
+        dv[t] = dst0[src + i];
+        lv[t] = lab0[src + i];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kRelItems; ++t)
+      if (i0 + lane + (uint64_t)t * lanes < d) dv[t] = o2p[dv[t]];
+#pragma unroll
+    for (int t = 0; t < kRelItems; ++t) {
+      const uint64_t i = i0 + lane + (uint64_t)t * lanes;
+      if (i < d) {
+        dst[at + i] = dv[t];
+        lab[at + i] = (TO)lv[t];
+      }
+    }
+  }
+}
+
+// Out-degree 65..4096: one warp per node.
 template <typename TI, typename TO>
 __global__ void k_relabel_edges_large(uint64_t p_first, uint64_t p_end, const uint32_t* p2o, const uint32_t* o2p,
                                       const uint64_t* off0, const uint32_t* dst0, const TI* lab0, const uint64_t* off,
                                       uint32_t* dst, TO* lab) {
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31;
   for (uint64_t p = p_first + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); p < p_end;
        p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
     const uint32_t o = p2o[p];
-    const uint64_t s0 = off0[o], d = off0[o + 1] - s0, s1 = off[p];
-    for (uint64_t i = lane; i < d; i += 32) {
-      dst[s1 + i] = o2p[dst0[s0 + i]];
-      lab[s1 + i] = (TO)lab0[s0 + i];
-    }
+    const uint64_t s0 = off0[o];
+    relabel_run(s0, off[p], off0[o + 1] - s0, lane, 32u, o2p, dst0, lab0, dst, lab);
   }
 }
 
@@ -1501,10 +1586,7 @@ __global__ void k_relabel_edges_hub(uint64_t hub_first, const uint4* chunks, con
   const uint64_t p = hub_first + c.x;
   const uint64_t begin = ((uint64_t)c.z << 32) | c.y;
   const uint64_t src = off0[p2o[p]] + (begin - off[p]);
-  for (uint32_t i = threadIdx.x; i < c.w; i += blockDim.x) {
-    dst[begin + i] = o2p[dst0[src + i]];
-    lab[begin + i] = (TO)lab0[src + i];
-  }
+  relabel_run(src, begin, c.w, threadIdx.x, blockDim.x, o2p, dst0, lab0, dst, lab);
 }
 
 template <typename TI, typename TO>
@@ -1513,9 +1595,16 @@ void relabel_edges(Store& s, const uint64_t* off0, const uint32_t* dst0, const T
   const uint32_t* o2p = ptr<uint32_t>(s.o2p);
   const uint64_t* off = ptr<uint64_t>(s.offsets);
   uint32_t* dst = ptr<uint32_t>(s.dst);
-  const unsigned g1 = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
-  k_relabel_edges_small<TI, TO><<<g1, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off, dst,
-                                                         lab);
+  const uint64_t n_small = s.class_start[kClassWarp];
+  if (n_small) {
+    const unsigned g1 = (unsigned)std::min<uint64_t>(grid_for(n_small, 256), (uint64_t)sms * 32);
+    k_relabel_edges_small<TI, TO><<<g1, 256, 0, s.stream>>>(n_small, ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off,
+                                                           dst, lab);
+  }
+  const uint64_t dead = s.class_start[kClassDead];
+  if (n > dead)
+    k_relabel_edges_dead<TI, TO><<<(unsigned)std::min<uint64_t>(grid_for(n - dead, 256), (uint64_t)sms * 8), 256, 0,
+                                   s.stream>>>(dead, n, ptr<uint32_t>(s.p2o), o2p, off0, dst0, lab0, off, dst, lab);
   const uint64_t pf = s.class_start[kClassWarp], pe = s.class_start[kClassHub];
   if (pe > pf) {
     const unsigned g2 = (unsigned)std::min<uint64_t>(grid_for((pe - pf) * 32, 256), (uint64_t)sms * 32);
