@@ -2,10 +2,11 @@
 paper_1210_0748_gb300.ncu_summary CSV ...``).
 
 The CSV comes from ``ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
-dram__bytes_write.sum --csv`` over ``bench.py --steps 1 --warmup 0``: every
-launch of the graph load and of one refinement (level 0 and each round).
-Launches before the first ``k_label_hash`` belong to the load and are left
-out.  Two outputs:
+dram__bytes_write.sum --csv`` over ``bench.py --steps 1 --warmup 2``: every
+launch of the graph load and of three refinements (level 0 and each round).
+Only the last refinement is summarised (from the last ``k_label_hash`` on):
+the warm-up refinements have already grown any hub bucket that overflows, as
+in the timed steps.  Two outputs:
 
 * a Markdown table per kernel (launches, total time, share, DRAM bytes);
 * a JSON record of DRAM bytes per call of each kernel class (per round for the
@@ -91,7 +92,7 @@ def class_of(name: str):
 
 
 def summarise(launches, rounds: int):
-    first = next((i for i, (_, n, _) in enumerate(launches) if n.startswith("k_label_hash")), 0)
+    first = max((i for i, (_, n, _) in enumerate(launches) if n.startswith("k_label_hash")), default=0)
     refine = launches[first:]
     per_kernel = collections.OrderedDict()
     per_class = collections.defaultdict(float)
