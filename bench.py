@@ -449,13 +449,16 @@ def main():
                           "launches_per_call": launches / calls, "edges": e_c, "nodes": n_c}
     dom = max(per_class, key=lambda c: ktimes[c][0])
     d = per_class[dom]
-    traffic = recorded_traffic(dom, args.scale) if args.workload == "single" else None
+    # measured DRAM bytes of the class per round (ncu), per launch like the algorithmic bytes
+    traffic_round = recorded_traffic(dom, args.scale) if args.workload == "single" else None
+    traffic = traffic_round / d["launches_per_call"] if traffic_round is not None else None
     names = {"sig_small": "k_sig_small (out-degree <= 64, one thread per node)",
              "sig_medium": "k_sig_chunk (out-degree 65..4096, CTA chunks)",
              "sig_hub": "k_hub_sample, k_hub_chunk or k_hub_scatter per hub, k_hub_bucket, k_hub_finish (out-degree > 4096)",
              "group": "k_group_insert", "verify": "k_group_verify", "renumber": "renumbering kernels"}
     roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": d["achieved"], "peak": peak,
                 "unit": "GB/s", "frac": d["frac"], "peak_kind": peak_kind, "traffic": traffic,
+                "traffic_per_round": traffic_round, "algorithmic_bytes_per_round": d["algorithmic_bytes_per_call"],
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_call"] / d["launches_per_call"],
                 "avg_launch_ms": d["ms_per_call"] / d["launches_per_call"],
                 "launches_per_round": d["launches_per_call"]}
