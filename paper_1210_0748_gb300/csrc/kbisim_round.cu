@@ -363,6 +363,80 @@ __device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, co
   a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
 }
 
+// The same for the 32 nodes of a warp (consecutive internal ids, so their
+// edges are one contiguous range of at most 32 * S edges), with the edges
+// staged through the warp's shared-memory buffer: the warp loads the range
+// coalesced (lane l takes edges l, l + 32, ...) and makes the keys, each
+// thread reads its node's keys back, keeps the distinct ones as above and
+// writes them over its own keys, and the warp stores the whole range
+// coalesced (slots past a node's distinct count keep leftovers that nothing
+// reads).  Lanes past the class end take part without a node.
+template <int S, typename LabelT, typename K>
+__device__ __forceinline__ void sig_warp_staged(const SigArgs& a, uint64_t p_first, uint32_t nvalid, K* wsm,
+                                                const Policies& pol) {
+  const uint32_t lane = threadIdx.x & 31;
+  const bool valid = lane < nvalid;
+  const uint64_t p = p_first + lane;
+  const uint64_t base = a.off[p_first];
+  const uint64_t end = a.off[p_first + nvalid];
+  const uint32_t T = (uint32_t)(end - base);  // at most 32 * S
+  {
+    K kk[S];
+    edge_keys<S, 0, S, LabelT, K>(a, base + lane, 32u, end, pol, kk);
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (lane + 32u * t < T) wsm[lane + 32u * t] = kk[t];
+  }
+  __syncwarp();
+  uint32_t r0 = 0, d = 0;
+  if (valid) {
+    const uint64_t o = a.off[p];
+    r0 = (uint32_t)(o - base);
+    d = (uint32_t)(a.off[p + 1] - o);
+  }
+  K k[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) k[i] = i < (int)d ? wsm[r0 + i] : (K)0;
+  __syncwarp();  // every read is done before the distinct keys go back
+  uint64_t term = 0;
+  uint32_t U = 0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    bool keep = i < (int)d;
+#pragma unroll
+    for (int j = 0; j < i; ++j) keep = keep && k[j] != k[i];
+    if (keep) {
+      wsm[r0 + U] = k[i];
+      term = term_add(term, elem_term(k[i], a.seed));
+      ++U;
+    }
+  }
+  __syncwarp();
+  K* out = static_cast<K*>(a.sigkey) + base;
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (lane + 32u * t < T) out[lane + 32u * t] = wsm[lane + 32u * t];
+  if (valid) {
+    a.ucnt[p] = U;
+    a.hash[p] = node_hash(term, a.prev[p], U, a.seed, a.mask);
+  }
+}
+
+// Largest S staged through shared memory (out-degree 9..16); the 17..32 class
+// keeps one node per thread, whose registers a staged copy would double.
+template <typename K>
+__host__ __device__ constexpr int staged_max_s() {
+  return 16;
+}
+
+// Resident CTAs per multiprocessor the small-class kernels are compiled for:
+// all 8 (32 registers) for out-degree <= 8 with 32-bit keys, fewer where more
+// keys sit in registers.
+template <int LAST, typename K>
+__host__ __device__ constexpr int small_min_blocks() {
+  return LAST <= 4 ? (sizeof(K) == 4 ? 8 : 6) : (LAST == 5 ? 4 : (sizeof(K) == 4 ? 4 : 2));
+}
+
 struct SmallLaunch {
   uint64_t start[kSmallClasses];
   uint64_t count[kSmallClasses];
@@ -376,26 +450,48 @@ constexpr int kSmallThreads = 256;
 // so the 64-slot class (most registers) does not limit the occupancy of the
 // others.
 template <int FIRST, int LAST, typename LabelT, typename K>
-__global__ void __launch_bounds__(kSmallThreads) k_sig_small(SigArgs a, SmallLaunch L) {
+__global__ void __launch_bounds__(kSmallThreads, small_min_blocks<LAST, K>()) k_sig_small(SigArgs a, SmallLaunch L) {
+  // per-warp staging buffer for the largest class of this launch that is staged
+  constexpr int kSLast = LAST == 0 ? 1 : (1 << (LAST - 1));
+  constexpr int kSBuf = kSLast <= staged_max_s<K>() ? kSLast : 1;
+  __shared__ K stage[kSmallThreads / 32][32 * kSBuf];
   int c = FIRST;
   while (c < LAST && blockIdx.x >= L.bstart[c + 1]) ++c;
+  const uint32_t lane = threadIdx.x & 31;
   const uint64_t idx = (uint64_t)(blockIdx.x - L.bstart[c]) * kSmallThreads + threadIdx.x;
-  if (idx >= L.count[c]) return;
+  const uint64_t widx = idx - lane;
+  if (widx >= L.count[c]) return;  // the whole warp is past the class end
+  const uint64_t left = L.count[c] - widx;
+  const uint32_t nvalid = left < 32 ? (uint32_t)left : 32u;
   const uint64_t p = L.start[c] + idx;
   const Policies pol;
+  K* wsm = stage[threadIdx.x >> 5];
+#define KB_SMALL_CLASS(C, S)                                                                  \
+  case C:                                                                                     \
+    if constexpr (LAST >= C) {                                                                \
+      if constexpr (S <= kSBuf) sig_warp_staged<S, LabelT, K>(a, L.start[c] + widx, nvalid, wsm, pol); \
+      else if (idx < L.count[c]) sig_thread_node<S, LabelT, K>(a, p, pol);                    \
+    }                                                                                         \
+    break;
   switch (c) {
     case 0:
-      a.ucnt[p] = 0;
-      a.hash[p] = node_hash(0, a.prev[p], 0, a.seed, a.mask);
+      if (idx < L.count[c]) {
+        a.ucnt[p] = 0;
+        a.hash[p] = node_hash(0, a.prev[p], 0, a.seed, a.mask);
+      }
       break;
-    case 1: if (LAST >= 1) sig_thread_node<1, LabelT, K>(a, p, pol); break;
-    case 2: if (LAST >= 2) sig_thread_node<2, LabelT, K>(a, p, pol); break;
-    case 3: if (LAST >= 3) sig_thread_node<4, LabelT, K>(a, p, pol); break;
-    case 4: if (LAST >= 4) sig_thread_node<8, LabelT, K>(a, p, pol); break;
-    case 5: if (LAST >= 5) sig_thread_node<16, LabelT, K>(a, p, pol); break;
-    case 6: if (LAST >= 6) sig_thread_node<32, LabelT, K>(a, p, pol); break;
-    default: if (LAST >= 7) sig_thread_node<64, LabelT, K>(a, p, pol); break;
+    KB_SMALL_CLASS(1, 1)
+    KB_SMALL_CLASS(2, 2)
+    KB_SMALL_CLASS(3, 4)
+    KB_SMALL_CLASS(4, 8)
+    KB_SMALL_CLASS(5, 16)
+    KB_SMALL_CLASS(6, 32)
+    default:
+      if constexpr (LAST >= 7)
+        if (idx < L.count[c]) sig_thread_node<64, LabelT, K>(a, p, pol);
+      break;
   }
+#undef KB_SMALL_CLASS
 }
 
 // ---- out-degree 65..4096: CTA chunks of whole nodes -----------------------
