@@ -698,7 +698,7 @@ __device__ __forceinline__ void hub_fail(const SigArgs& a, const HubArgs& h, uin
 constexpr int kHubUcap = 4096;         // key words per bucket at most
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
 constexpr int kHubSample = 128;        // keys sampled per hub to choose its chunk pass
-constexpr int kHubSamplePairs = 4;     // equal sampled pairs from which a hub keeps the chunk set
+constexpr int kHubSamplePairs = 8;     // equal sampled pairs from which a hub keeps the chunk set
 constexpr uint32_t kHubScatterShiftMax = 2;  // bucket growth of a scattering hub before it takes the set
 
 template <typename K>
@@ -781,9 +781,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
 
 // One warp per hub: kHubSample keys at an even stride over the hub's edges.
 // Among S samples from U equally frequent distinct keys about S(S-1)/2 / U
-// pairs are equal: kHubSamplePairs or more equal pairs mean a few thousand
+// pairs are equal: kHubSamplePairs or more equal pairs mean about a thousand
 // distinct keys or fewer (the few blocks of an early level), or a key that
-// makes up several percent of the hub's edges, and the hub keeps the chunk
+// makes up some 5% of the hub's edges or more, and the hub keeps the chunk
 // set, which sends each distinct key of a chunk to the buckets once.  Other
 // hubs skip it, unless an earlier overflow forced the set on them.
 template <typename LabelT, typename K>
@@ -1199,7 +1199,7 @@ __device__ __forceinline__ void mark_unresolved(const VerifyArgs& v, uint32_t* r
 // Each thread takes kVerItems nodes of a tile at a time, and every step's
 // loads for all of them are issued together (node ids; alone flags; original
 // ids and table slots; representatives; their fields; the short key lists).
-constexpr int kVerNodeThreads = 256, kVerItems = 4, kVerTile = kVerNodeThreads * kVerItems;
+constexpr int kVerNodeThreads = 256, kVerItems = 2, kVerTile = kVerNodeThreads * kVerItems;
 
 __global__ void __launch_bounds__(kVerNodeThreads) k_group_verify(GroupArgs g, VerifyArgs v, const uint32_t* list,
                                                                    uint64_t count) {
