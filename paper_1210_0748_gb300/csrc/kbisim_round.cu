@@ -698,7 +698,7 @@ __device__ __forceinline__ void hub_fail(const SigArgs& a, const HubArgs& h, uin
 constexpr int kHubUcap = 4096;         // key words per bucket at most
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
 constexpr int kHubSample = 128;        // keys sampled per hub to choose its chunk pass
-constexpr int kHubSamplePairs = 8;     // equal sampled pairs from which a hub keeps the chunk set
+constexpr int kHubSamplePairs = 16;    // equal sampled pairs from which a hub keeps the chunk set
 constexpr uint32_t kHubScatterShiftMax = 2;  // bucket growth of a scattering hub before it takes the set
 
 template <typename K>
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
 
 // One warp per hub: kHubSample keys at an even stride over the hub's edges.
 // Among S samples from U equally frequent distinct keys about S(S-1)/2 / U
-// pairs are equal: kHubSamplePairs or more equal pairs mean about a thousand
+// pairs are equal: kHubSamplePairs or more equal pairs mean about 500
 // distinct keys or fewer (the few blocks of an early level), or a key that
 // makes up some 5% of the hub's edges or more, and the hub keeps the chunk
 // set, which sends each distinct key of a chunk to the buckets once.  Other
