@@ -141,8 +141,8 @@ enum {
   KBISIM_KERNEL_SIG_MEDIUM,      /* signatures of out-degree 65..4096 */
   KBISIM_KERNEL_SIG_HUB,         /* signatures of larger out-degree (all hub kernels) */
   KBISIM_KERNEL_GROUP,           /* hash-table grouping of equal signatures */
-  KBISIM_KERNEL_VERIFY,          /* exact signature comparison */
-  KBISIM_KERNEL_RENUMBER,        /* canonical renumbering (scan + gather) */
+  KBISIM_KERNEL_VERIFY,          /* exact signature comparison, marking block heads */
+  KBISIM_KERNEL_RENUMBER,        /* canonical renumbering (scan of head counts + ranks) */
   KBISIM_KERNEL_OTHER,           /* clears, collision repair, copies */
   KBISIM_KERNEL_COUNT
 };
