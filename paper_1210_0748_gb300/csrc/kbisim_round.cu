@@ -505,8 +505,9 @@ __global__ void __launch_bounds__(kSmallThreads, small_min_blocks<LAST, K>()) k_
 //     into the set writes it out at once: the 32 consecutive edges of a warp
 //     belong to at most two nodes, so each node's output position is claimed
 //     once per warp step;
-//  3. sums the hash terms of each node's distinct keys, just written, with one
-//     warp per node, and writes the node's distinct-key count and hash.
+//  3. adds the hash terms of the keys a warp step inserted to their node's
+//     sums as it claims their output positions, and at the end writes each
+//     node's distinct-key count and hash.
 // The key equal to the empty-slot marker is kept as a per-node flag.
 
 // A chunk CTA of NT threads takes up to NT * kChunkItems edges of nodes with
@@ -527,6 +528,8 @@ struct ChunkSmem {
   uint32_t off[Shape::kMaxNodes + 1];  // node starts relative to the chunk's first edge
   uint32_t cnt[Shape::kMaxNodes];      // distinct keys written per node
   uint32_t empty[Shape::kMaxNodes];    // the node's key equal to KeyOps<K>::kEmpty was seen
+  uint32_t lo[Shape::kMaxNodes];       // term sum halves of the node's distinct keys
+  uint32_t hi[Shape::kMaxNodes];
 };
 
 // Chunk kernel shapes: out-degree 33..64 and 65..1024 in 128-thread CTAs,
@@ -580,6 +583,8 @@ __device__ __forceinline__ void chunk_clear(ChunkSmem<K, NT, MIN_DEG>& sm, uint3
   for (uint32_t i = threadIdx.x; i < (uint32_t)ChunkShape<NT, MIN_DEG>::kMaxNodes; i += NT) {
     sm.cnt[i] = 0;
     sm.empty[i] = 0;
+    sm.lo[i] = 0;
+    sm.hi[i] = 0;
   }
 }
 
@@ -630,31 +635,34 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
     const uint32_t jA = __shfl_sync(kFull, j, 0);
     const bool inA = j == jA;
     const unsigned fa = fm & __ballot_sync(kFull, inA), fb = fm & ~fa;
+    // the fresh keys' term sums, per node of the step, go with their count
+    const uint64_t tm = fresh ? elem_term(kt, a.seed) : 0ull;
+    const uint32_t loA = __reduce_add_sync(kFull, inA ? (uint32_t)tm : 0u);
+    const uint32_t hiA = __reduce_add_sync(kFull, inA ? (uint32_t)(tm >> 32) : 0u);
+    const uint32_t loB = __reduce_add_sync(kFull, inA ? 0u : (uint32_t)tm);
+    const uint32_t hiB = __reduce_add_sync(kFull, inA ? 0u : (uint32_t)(tm >> 32));
     uint32_t base = 0;
-    if (lane == 0 && fa) base = atomicAdd(&sm.cnt[jA], (uint32_t)__popc(fa));
-    if (lane == 31 && fb) base = atomicAdd(&sm.cnt[jA + 1], (uint32_t)__popc(fb));
+    if (lane == 0 && fa) {
+      base = atomicAdd(&sm.cnt[jA], (uint32_t)__popc(fa));
+      atomicAdd(&sm.lo[jA], loA);
+      atomicAdd(&sm.hi[jA], hiA);
+    }
+    if (lane == 31 && fb) {
+      base = atomicAdd(&sm.cnt[jA + 1], (uint32_t)__popc(fb));
+      atomicAdd(&sm.lo[jA + 1], loB);
+      atomicAdd(&sm.hi[jA + 1], hiB);
+    }
     const uint32_t bA = __shfl_sync(kFull, base, 0), bB = __shfl_sync(kFull, base, 31);
     if (fresh)
       out[sm.off[j] + (inA ? bA + __popc(fa & lanes_below(lane)) : bB + __popc(fb & lanes_below(lane)))] = kt;
   }
   __syncthreads();
-  // hash terms: one warp per node over its distinct keys just written
-  for (uint32_t i = tid >> 5; i < nn; i += NT / 32) {
+  // count and hash of each node of the chunk
+  for (uint32_t i = tid; i < nn; i += NT) {
+    const uint64_t p = first + i;
     const uint32_t U = sm.cnt[i];
-    const K* ko = out + sm.off[i];
-    uint32_t lo = 0, hi = 0;
-    for (uint32_t q = lane; q < U; q += 32) {
-      const uint64_t tm = elem_term(ko[q], a.seed);
-      lo += (uint32_t)tm;
-      hi += (uint32_t)(tm >> 32);
-    }
-    lo = __reduce_add_sync(kFull, lo);
-    hi = __reduce_add_sync(kFull, hi);
-    if (lane == 0) {
-      const uint64_t p = first + i;
-      a.ucnt[p] = U;
-      a.hash[p] = node_hash(((uint64_t)hi << 32) | lo, a.prev[p], U, a.seed, a.mask);
-    }
+    a.ucnt[p] = U;
+    a.hash[p] = node_hash(((uint64_t)sm.hi[i] << 32) | sm.lo[i], a.prev[p], U, a.seed, a.mask);
   }
 }
 
