@@ -410,17 +410,19 @@ def test_hubs_with_distinct_keys():
     assert all(pids[lev][0] == pids[lev][1] for lev in range(pids.shape[0]))
 
 
-def test_hub_with_one_heavy_key_among_distinct_keys():
-    """A 1M-edge hub whose keys are all distinct but one, which makes up 1% of
-    its edges: a key sample finds few repeats, so the hub skips the chunk set,
-    the heavy key overflows its bucket, and the hub must be redone with the
-    chunk set; the result must still equal the oracle."""
+@pytest.mark.parametrize("heavy", [10_000, 30_000])
+def test_hub_with_one_heavy_key_among_distinct_keys(heavy):
+    """A 1M-edge hub whose keys are all distinct but one, which makes up 1% or
+    3% of its edges: a key sample finds few repeats, so the hub skips the chunk
+    set and the heavy key overflows its bucket.  With 1% the bucket grows until
+    it fits; with 3% it outgrows the growth a scattering hub is allowed and the
+    hub is redone with the chunk set.  Results must equal the oracle."""
     rng = np.random.default_rng(41)
     n = 100_000
     nl = (np.arange(n) % 1000).astype(np.uint32)
     c = np.arange(990_000)
-    hub_dst = np.concatenate([(c % 1000) + 1000 * rng.integers(0, n // 1000, c.size), np.full(10_000, 5)])
-    hub_lab = np.concatenate([c // 1000, np.zeros(10_000, np.int64)])
+    hub_dst = np.concatenate([(c % 1000) + 1000 * rng.integers(0, n // 1000, c.size), np.full(heavy, 5)])
+    hub_lab = np.concatenate([c // 1000, np.zeros(heavy, np.int64)])
     perm = rng.permutation(hub_dst.size)
     other = 200_000
     src = np.concatenate([np.zeros(hub_dst.size, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
