@@ -54,7 +54,7 @@ extern "C" {
 #define KBISIM_ERR_OUT_OF_MEMORY 2 /* a device allocation failed */
 #define KBISIM_ERR_BUDGET 3        /* the call would exceed options.hbm_budget_bytes */
 #define KBISIM_ERR_CUDA 4          /* a CUDA runtime call or kernel failed */
-#define KBISIM_ERR_TIMEOUT 5       /* a bounded device-side loop gave up */
+#define KBISIM_ERR_TIMEOUT 5       /* a bounded loop gave up (table probe, hub bucket growth, collision repair) */
 #define KBISIM_ERR_CHECKED 6       /* a device bounds check fired (options.checked) */
 #define KBISIM_ERR_STATE 7         /* the call needs a loaded graph or computed levels */
 
