@@ -31,8 +31,20 @@
  *  - Return value: KBISIM_OK (0) or one of the KBISIM_ERR_* codes below.
  *    No C++ exception crosses this boundary.  kbisim_last_error() gives a
  *    message for the last failure on a handle.
- *  - A failed call leaves the previous result of the handle intact, except
- *    KBISIM_ERR_CUDA, after which the handle should be destroyed.
+ *  - A failed kbisim_refine or kbisim_extend leaves the previous result of
+ *    the handle readable and unchanged: new levels are computed into spare
+ *    buffers and replace the old ones only when the call succeeds.  For
+ *    kbisim_load, kbisim_build, kbisim_build_many and kbisim_update see their
+ *    own comments (they replace the graph).  After KBISIM_ERR_CUDA the handle
+ *    should be destroyed.
+ *  - Test hooks (host-side fault injection; read from the environment at the
+ *    start of each call that computes, and applied to that call only):
+ *    KBISIM_FAULT_ALLOC=N makes the call's (N+1)-th device allocation fail
+ *    with KBISIM_ERR_OUT_OF_MEMORY; KBISIM_FAULT_TIMEOUT_ROUND=r makes round r
+ *    report KBISIM_ERR_TIMEOUT; KBISIM_FAULT_CORRUPT_DST=1 (checked mode only)
+ *    sets one stored edge target to num_nodes before each round, which the
+ *    checked-mode index check reports as KBISIM_ERR_CHECKED (the value is put
+ *    back before the call returns).
  *  - Inputs are borrowed for the duration of the call only; the library
  *    copies what it keeps.  Results live in the handle and stay valid until
  *    the next call that loads, refines, extends or updates the handle, or
@@ -86,8 +98,11 @@ typedef struct {
    * exist to test the exact collision handling: they make unequal
    * signatures collide on purpose.  Results do not change, only speed. */
   uint32_t hash_bits;
-  /* 1 = kernels check their own indices and stop with KBISIM_ERR_CHECKED
-   * instead of touching memory out of range. */
+  /* 1 = checked mode: before a kernel indexes with a device array, a check
+   * kernel verifies every index in it (edge offsets and targets, the previous
+   * level's identifiers, block heads, identifiers) and the call stops with
+   * KBISIM_ERR_CHECKED, without launching the kernel, if one is out of range.
+   * Results are identical; each check costs one pass over the array. */
   int checked;
   /* 1 = record CUDA events around every kernel and keep per-kernel totals
    * (see kbisim_kernel_times). */
@@ -163,7 +178,8 @@ void kbisim_destroy(kbisim_handle *h);
 const char *kbisim_last_error(const kbisim_handle *h);
 
 /* Copy a graph into the handle (building the CSR-by-source edge table when
- * COO is given) and drop any previous graph and levels.  Validates ids
+ * COO is given) and drop any previous graph and levels (also when the load
+ * fails after validation: then the handle holds no graph).  Validates ids
  * (INVALID_ARG if a node id >= num_nodes or num_nodes >= 2^32 - 1).  A handle
  * without an HBM budget keeps its device buffers (including the staging of
  * host inputs) for the next load, so reloading graphs of similar size
@@ -175,7 +191,8 @@ int kbisim_load(kbisim_handle *h, const kbisim_graph *g);
  * OUT_OF_MEMORY, BUDGET, TIMEOUT, CHECKED, CUDA. */
 int kbisim_refine(kbisim_handle *h, uint32_t k, kbisim_result *out);
 
-/* kbisim_load followed by kbisim_refine. */
+/* kbisim_load followed by kbisim_refine.  If the refinement fails, the new
+ * graph stays loaded without levels (KBISIM_ERR_STATE on read). */
 int kbisim_build(kbisim_handle *h, const kbisim_graph *g, uint32_t k, kbisim_result *out);
 
 /* Change k (Section 4, "Change k"): a larger k runs the missing rounds from
@@ -202,7 +219,12 @@ typedef struct {
  * partition is the k-bisimulation of the new graph).  *missing_deletes (may
  * be NULL) receives the number of edge deletions that named no edge.
  * Errors: STATE, INVALID_ARG (bad id, or an edge on a deleted node), and the
- * errors of kbisim_refine.  On failure the graph and levels are unchanged. */
+ * errors of kbisim_refine.  A batch that is rejected (INVALID_ARG), or whose
+ * staging or matching fails (OUT_OF_MEMORY, BUDGET, TIMEOUT), leaves the graph
+ * and levels unchanged.  Once the updated graph has been stored the old levels
+ * no longer describe it: a failure of that step leaves no graph, and a failure
+ * of the recomputation leaves the updated graph loaded without levels
+ * (KBISIM_ERR_STATE on read; kbisim_refine computes them). */
 int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_result *out,
                   uint64_t *missing_deletes);
 
@@ -248,6 +270,10 @@ uint64_t kbisim_num_nodes(const kbisim_handle *h);
 
 /* Number of edges of the loaded graph. */
 uint64_t kbisim_num_edges(const kbisim_handle *h);
+
+/* Device bytes the handle holds now (graph, levels, scratch, spares); the
+ * quantity options.hbm_budget_bytes bounds.  0 for NULL. */
+uint64_t kbisim_device_bytes(const kbisim_handle *h);
 
 /* Per-kernel device times summed since the last kbisim_reset_times(). */
 int kbisim_get_kernel_times(const kbisim_handle *h, kbisim_kernel_times *out);

@@ -1,5 +1,5 @@
-"""Summaries of an ncu launch list of one refinement (``python -m
-paper_1210_0748_gb300.ncu_summary CSV ...``).
+"""Benchmark helper: summaries of an ncu launch list of one refinement
+(``python ncu_summary.py CSV ...``).
 
 The CSV comes from ``ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
 dram__bytes_write.sum --csv`` over ``bench.py --steps 1 --warmup 2``: every
@@ -27,7 +27,7 @@ import json
 import os
 import re
 
-PKG = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1210_0748_gb300", "csrc")
 
 # kernel name -> class of the library's timing (kbisim_kernel_times)
 CLASS_OF = [
@@ -52,9 +52,8 @@ ROUND_SOURCES = ("kbisim_round.cu", "kbisim_internal.cuh")
 def source_digest() -> str:
     """sha256 over the sources of the round kernels (file names and contents)."""
     h = hashlib.sha256()
-    csrc = os.path.join(PKG, "csrc")
     for name in ROUND_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 

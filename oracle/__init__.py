@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kbisim_oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "check_levels.cpp")]
 _LIB = os.path.join(_HERE, "libkbisim_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,9 +30,9 @@ DEAD = 0xFFFFFFFF
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with the host C++ compiler."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -51,6 +52,8 @@ def _load():
             lib.oracle_full_bisim.restype = ctypes.c_int
             lib.oracle_level0.argtypes = [U64, P, P, P]
             lib.oracle_level0.restype = U64
+            lib.oracle_check_level.argtypes = [U64, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P, P]
+            lib.oracle_check_level.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -117,3 +120,27 @@ def full_bisim(num_nodes, node_label, src, dst, edge_label):
     if rc != 0:
         raise ValueError("oracle rejected the input")
     return out, int(cnt[0])
+
+
+def check_level(g, prev, cur, threads=None):
+    """Check candidate level ``cur`` of CSR graph ``g`` (a ``synth.Graph``)
+    against the previous level ``prev`` through Proposition 2 (check_levels.cpp):
+    returns (code, blocks, bad_node); code 0 means cur is the canonical next
+    level, 1 not canonical, 2 a node whose signature differs from its block
+    head's, 3 two blocks with equal signatures."""
+    lib = _load()
+    n = int(g.num_nodes)
+    off = np.ascontiguousarray(g.offsets, dtype=np.uint64)
+    dst = np.ascontiguousarray(g.dst, dtype=np.uint32)
+    lab = np.ascontiguousarray(g.edge_label)
+    if lab.dtype != np.uint8:
+        lab = np.ascontiguousarray(lab, dtype=np.uint32)
+    p, c = _u32(prev), _u32(cur)
+    if p.size != n or c.size != n:
+        raise ValueError("level sizes disagree with the graph")
+    cnt = np.zeros(1, np.uint64)
+    bad = np.zeros(1, np.uint64)
+    rc = lib.oracle_check_level(n, _ptr(off), _ptr(dst), _ptr(lab), 1 if lab.dtype == np.uint8 else 4,
+                                _ptr(p), _ptr(c), int(threads or os.cpu_count() or 1),
+                                cnt.ctypes.data_as(ctypes.c_void_p), bad.ctypes.data_as(ctypes.c_void_p))
+    return int(rc), int(cnt[0]), int(bad[0])

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -24,11 +25,33 @@ Status cuda_check(cudaError_t e, const char* what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Test hooks, read from the environment at the start of every call that
+// computes (the library's own fault injection: nothing here touches a GPU
+// setting or makes a kernel fail):
+//   KBISIM_FAULT_ALLOC=N          the call's (N+1)-th device allocation fails
+//                                 with KBISIM_ERR_OUT_OF_MEMORY;
+//   KBISIM_FAULT_TIMEOUT_ROUND=r  round r reports KBISIM_ERR_TIMEOUT, as a
+//                                 bounded device loop that gave up would;
+//   KBISIM_FAULT_CORRUPT_DST=1    with options.checked only: one stored edge
+//                                 target is set to num_nodes (one past the
+//                                 last node) before each round, which the
+//                                 checked-mode index check must report.
+void read_fault_hooks(Store& s) {
+  const char* a = std::getenv("KBISIM_FAULT_ALLOC");
+  s.fault_alloc = (a && *a) ? std::strtol(a, nullptr, 10) : -1;
+  const char* t = std::getenv("KBISIM_FAULT_TIMEOUT_ROUND");
+  s.fault_timeout_round = (t && *t) ? (uint32_t)std::strtoul(t, nullptr, 10) : 0u;
+  const char* c = std::getenv("KBISIM_FAULT_CORRUPT_DST");
+  s.fault_corrupt_dst = s.checked && c && *c == '1';
+}
+
 Status ensure(Store& s, Buf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return Status::Ok();
   size_t want = std::max<size_t>(bytes, 256);
   if (s.budget && s.bytes_held - b.cap + want > s.budget)
     return Status::Err(KBISIM_ERR_BUDGET, "device memory budget exceeded");
+  if (s.fault_alloc >= 0 && s.fault_alloc-- == 0)
+    return Status::Err(KBISIM_ERR_OUT_OF_MEMORY, "injected allocation failure (KBISIM_FAULT_ALLOC)");
   if (b.p) {
     cudaStreamSynchronize(s.stream);
     cudaFree(b.p);
@@ -62,9 +85,11 @@ namespace {
 template <typename T>
 T* ptr(Buf& b) { return static_cast<T*>(b.p); }
 
-unsigned grid(uint64_t work, unsigned per) {
+// Grid of a grid-stride loop over `work` items, `per` per CTA: at most 32
+// CTAs per multiprocessor of the handle's device.
+unsigned grid(const Store& s, uint64_t work, unsigned per) {
   uint64_t g = (work + per - 1) / per;
-  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 152ull * 32));
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)s.sms * 32));
 }
 
 // --- load kernels -----------------------------------------------------------
@@ -247,6 +272,9 @@ void free_graph(Store& s, bool keep_buffers) {
                  &s.rl_tcnt, &s.rl_hot, &s.rl_ost};
   if (!keep_buffers) {
     for (Buf* b : bufs) release(s, *b);
+    release(s, s.spare_alone);
+    for (Buf& b : s.spare_level) release(s, b);
+    s.spare_level.clear();
     for (Buf& b : s.level) release(s, b);
     for (Buf& b : s.out_level) release(s, b);
     for (Buf& b : s.stage) release(s, b);
@@ -353,12 +381,12 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   }
   unsigned int* d_max = reinterpret_cast<unsigned int*>(err + 4);
   if (m) {
-    const unsigned gb = grid(m, 256);
+    const unsigned gb = grid(s, m, 256);
     if (w == 1) k_label_max<uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), d_max);
     else if (w == 2) k_label_max<uint16_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), d_max);
     else k_label_max<uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), d_max);
-    k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, dst_in, err);
-    if (!g->offsets) k_check_ids<<<grid(m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
+    k_check_ids<<<grid(s, m, 256), 256, 0, s.stream>>>(m, n, dst_in, err);
+    if (!g->offsets) k_check_ids<<<grid(s, m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
   }
   // offsets in original ids
   const uint64_t* off0 = g->offsets;
@@ -368,7 +396,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
       if (!(st = copy_in(s, off_b.p, g->offsets, (n + 1) * 8, false)).ok()) return st;
       off0 = ptr<uint64_t>(off_b);
     }
-    if (n) k_check_offsets<<<grid(n, 256), 256, 0, s.stream>>>(n, m, off0, err);
+    if (n) k_check_offsets<<<grid(s, n, 256), 256, 0, s.stream>>>(n, m, off0, err);
   }
   uint32_t hv[8] = {0};
   if (!(st = cuda_check(cudaMemcpyAsync(hv, err, 32, cudaMemcpyDeviceToHost, s.stream), "validate")).ok()) return st;
@@ -382,13 +410,13 @@ Status load_graph(Store& s, const kbisim_graph* g) {
     if (!(st = ensure(s, cur_b, (n + 1) * 8)).ok()) return st;
     unsigned long long* off = ptr<unsigned long long>(off_b);
     cudaMemsetAsync(off, 0, (n + 1) * 8, s.stream);
-    if (m) k_degree_count<<<grid(m, 256), 256, 0, s.stream>>>(m, src_in, off);
+    if (m) k_degree_count<<<grid(s, m, 256), 256, 0, s.stream>>>(m, src_in, off);
     if (!(st = exclusive_scan_u64(s, off, n + 1, ptr<unsigned long long>(cur_b), scan_b)).ok()) return st;
     off0 = ptr<uint64_t>(off_b);
     if (m) {
       if (!(st = ensure(s, csr_dst, m * 4)).ok()) return st;
       if (!(st = ensure(s, csr_lab, m * w)).ok()) return st;
-      const unsigned gb = grid(m, 256);
+      const unsigned gb = grid(s, m, 256);
       unsigned long long* cur = ptr<unsigned long long>(cur_b);
       if (w == 1)
         k_place_coo<uint8_t><<<gb, 256, 0, s.stream>>>(m, src_in, dst_in, static_cast<const uint8_t*>(lab_in), cur,
@@ -477,17 +505,35 @@ Status run_rounds(Store& s, uint32_t from, uint32_t k) {
   return Status::Ok();
 }
 
-Status refine(Store& s, uint32_t k, kbisim_result* out) {
-  if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
-  if (k > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+// Host side of a computed result; with the level buffers and the alone flags
+// it is what a failed call puts back.
+struct LevelSnapshot {
+  std::vector<uint64_t> counts;
+  std::vector<kbisim_round_stats> stats;
+  uint32_t computed, rounds_run, k_requested;
+  bool stable, has_levels;
+  uint64_t n_alone;
+};
+
+LevelSnapshot take_snapshot(const Store& s) {
+  return LevelSnapshot{s.counts, s.stats, s.computed, s.rounds_run, s.k_requested, s.stable, s.has_levels,
+                       s.n_alone};
+}
+
+void put_back(Store& s, LevelSnapshot& p) {
+  s.counts.swap(p.counts);
+  s.stats.swap(p.stats);
+  s.computed = p.computed;
+  s.rounds_run = p.rounds_run;
+  s.k_requested = p.k_requested;
+  s.stable = p.stable;
+  s.has_levels = p.has_levels;
+  s.n_alone = p.n_alone;
+}
+
+Status refine_levels(Store& s, uint32_t k) {
   Status st;
-  invalidate_outputs(s);
   if (!(st = ensure_levels(s, s.early_stop ? std::min<uint32_t>(k, 1) : k)).ok()) return st;
-  s.has_levels = false;
-  s.stable = false;
-  s.computed = 0;
-  s.rounds_run = 0;
-  s.stats.clear();
   if (!(st = compute_level0(s)).ok()) return st;
   if (s.level_hook && !(st = s.level_hook(s, 0)).ok()) return st;
   for (uint32_t i = 1; i <= k; ++i) {
@@ -495,23 +541,69 @@ Status refine(Store& s, uint32_t k, kbisim_result* out) {
     if (!(st = ensure_levels(s, i)).ok()) return st;
     if (!(st = run_rounds(s, i - 1, i)).ok()) return st;
   }
+  return Status::Ok();
+}
+
+// Levels 0..k of the loaded graph.  The new levels are computed into spare
+// buffers; the current result (level buffers, alone flags, counts) is set
+// aside and put back if the call fails, so a failed refinement leaves the
+// previous result readable.
+Status refine(Store& s, uint32_t k, kbisim_result* out) {
+  if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
+  if (k > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+  LevelSnapshot snap = take_snapshot(s);
+  std::swap(s.level, s.spare_level);
+  std::swap(s.alone, s.spare_alone);
+  s.has_levels = false;
+  s.stable = false;
+  s.computed = 0;
+  s.rounds_run = 0;
+  s.stats.clear();
+  s.counts.assign(std::max<size_t>(snap.counts.size(), 1), 0);
+  Status st = refine_levels(s, k);
+  if (!st.ok()) {
+    std::swap(s.level, s.spare_level);
+    std::swap(s.alone, s.spare_alone);
+    put_back(s, snap);
+    timer_collect(s);
+    return st;
+  }
+  invalidate_outputs(s);
+  if (s.budget) {  // a budget handle keeps no spares between calls
+    for (Buf& b : s.spare_level) release(s, b);
+    s.spare_level.clear();
+    release(s, s.spare_alone);
+  }
   s.has_levels = true;
   fill_result(s, k, out);
   return timer_collect(s);
 }
 
+// Change k.  Rounds past the computed level write new level buffers only; the
+// alone flags and the host side are copied first and restored on failure.
 Status extend(Store& s, uint32_t k_new, kbisim_result* out) {
   if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
   if (k_new > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
   Status st;
-  invalidate_outputs(s);
   const bool need = k_new > s.computed && !(s.early_stop && s.stable);
   if (need) {
-    for (uint32_t i = s.computed + 1; i <= k_new; ++i) {
+    if (!(st = ensure(s, s.spare_alone, s.n + 16)).ok()) return st;
+    if (!(st = cuda_check(cudaMemcpyAsync(s.spare_alone.p, s.alone.p, s.n + 16, cudaMemcpyDeviceToDevice,
+                                          s.stream), "save alone flags")).ok())
+      return st;
+    LevelSnapshot snap = take_snapshot(s);
+    for (uint32_t i = s.computed + 1; i <= k_new && st.ok(); ++i) {
       if (s.early_stop && s.stable) break;
-      if (!(st = ensure_levels(s, i)).ok()) return st;
-      if (!(st = run_rounds(s, i - 1, i)).ok()) return st;
+      st = ensure_levels(s, i);
+      if (st.ok()) st = run_rounds(s, i - 1, i);
     }
+    if (!st.ok()) {
+      cudaMemcpyAsync(s.alone.p, s.spare_alone.p, s.n + 16, cudaMemcpyDeviceToDevice, s.stream);
+      put_back(s, snap);
+      timer_collect(s);
+      return st;
+    }
+    invalidate_outputs(s);
   }
   fill_result(s, k_new, out);
   return timer_collect(s);
@@ -523,8 +615,19 @@ Status extend(Store& s, uint32_t k_new, kbisim_result* out) {
 using kb::Status;
 
 static int finish(kbisim_handle* h, const Status& st) {
-  if (h) h->last_error = st.ok() ? std::string() : st.msg;
+  if (h) {
+    h->last_error = st.ok() ? std::string() : st.msg;
+    h->s.fault_alloc = -1;  // test hooks apply to one call only
+    h->s.fault_timeout_round = 0;
+    h->s.fault_corrupt_dst = false;
+  }
   return st.code;
+}
+
+// Entry of a call that computes: device current, test hooks read.
+static void enter(kbisim_handle* h) {
+  cudaSetDevice(h->s.device);
+  kb::read_fault_hooks(h->s);
 }
 
 extern "C" {
@@ -559,6 +662,10 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   if (!p) return KBISIM_ERR_OUT_OF_MEMORY;
   kb::Store& s = p->s;
   s.device = o.device;
+  if (cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess || s.sms < 1) {
+    cudaGetLastError();
+    s.sms = 1;
+  }
   s.stream = static_cast<cudaStream_t>(o.stream);
   s.budget = o.hbm_budget_bytes;
   s.early_stop = o.early_stop != 0;
@@ -603,20 +710,20 @@ const char* kbisim_last_error(const kbisim_handle* h) { return h ? h->last_error
 
 int kbisim_load(kbisim_handle* h, const kbisim_graph* g) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  cudaSetDevice(h->s.device);
+  enter(h);
   return finish(h, kb::load_graph(h->s, g));
 }
 
 int kbisim_refine(kbisim_handle* h, uint32_t k, kbisim_result* out) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  cudaSetDevice(h->s.device);
+  enter(h);
   return finish(h, kb::refine(h->s, k, out));
 }
 
 int kbisim_build_many(kbisim_handle* h, const kbisim_graph* g, const uint64_t* graph_start, uint32_t num_graphs,
                       const uint32_t* k) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  cudaSetDevice(h->s.device);
+  enter(h);
   kb::Store& s = h->s;
   uint32_t kmax = 0;
   Status st = kb::many_check_args(g, graph_start, num_graphs, k, &kmax);
@@ -646,7 +753,7 @@ int kbisim_many_info(kbisim_handle* h, uint32_t graph, uint32_t* rounds_run, uin
 
 int kbisim_build(kbisim_handle* h, const kbisim_graph* g, uint32_t k, kbisim_result* out) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  cudaSetDevice(h->s.device);
+  enter(h);
   Status st = kb::load_graph(h->s, g);
   if (st.ok()) st = kb::refine(h->s, k, out);
   return finish(h, st);
@@ -654,7 +761,7 @@ int kbisim_build(kbisim_handle* h, const kbisim_graph* g, uint32_t k, kbisim_res
 
 int kbisim_extend(kbisim_handle* h, uint32_t k_new, kbisim_result* out) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
-  cudaSetDevice(h->s.device);
+  enter(h);
   return finish(h, kb::extend(h->s, k_new, out));
 }
 
@@ -695,6 +802,7 @@ const uint32_t* kbisim_pids_device(kbisim_handle* h, uint32_t level) {
 
 uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
 uint64_t kbisim_num_edges(const kbisim_handle* h) { return h ? h->s.m : 0; }
+uint64_t kbisim_device_bytes(const kbisim_handle* h) { return h ? (uint64_t)h->s.bytes_held : 0; }
 
 int kbisim_get_kernel_times(const kbisim_handle* h, kbisim_kernel_times* out) {
   if (!h || !out) return KBISIM_ERR_INVALID_ARG;
@@ -725,7 +833,7 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
                   uint64_t* missing_deletes) {
   if (!h) return KBISIM_ERR_INVALID_ARG;
   if (k > KBISIM_MAX_K) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "k too large"));
-  cudaSetDevice(h->s.device);
+  enter(h);
   uint64_t missing = 0;
   Status st = kb::apply_batch(h->s, b, &missing);
   if (st.ok()) st = kb::refine(h->s, k, out);

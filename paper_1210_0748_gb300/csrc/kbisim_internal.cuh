@@ -163,6 +163,7 @@ using LevelHook = Status (*)(Store&, uint32_t);
 struct Store {
   // configuration
   int device = 0;
+  int sms = 1;                 // multiprocessors of the device (grid sizes)
   cudaStream_t stream = nullptr;
   uint64_t budget = 0;
   bool early_stop = true;
@@ -208,6 +209,8 @@ struct Store {
 
   // levels (all kept: history for extend / maintenance), internal order
   std::vector<Buf> level;
+  std::vector<Buf> spare_level;  // a refinement computes into these; the levels it replaces
+  Buf spare_alone;               //   come back here if it fails (and are its spares next time)
   std::vector<Buf> out_level;  // original-order copies made on demand
   std::vector<bool> out_valid;
   std::vector<uint64_t> counts;
@@ -253,6 +256,14 @@ struct Store {
   ManyState many;               // batched build (kbisim_build_many)
   LevelHook level_hook = nullptr;  // called after each computed level (batched build)
 
+  // Host-side fault injection for tests (read from the environment at every
+  // mutating call, see read_fault_hooks): allocations that succeed before one
+  // fails (-1 = off), the round that reports a timeout (0 = off), and, in
+  // checked mode only, one edge target set out of range before each round.
+  long fault_alloc = -1;
+  uint32_t fault_timeout_round = 0;
+  bool fault_corrupt_dst = false;
+
   size_t bytes_held = 0;
   KernelTimer* timer = nullptr;
   double total_ms[KBISIM_KERNEL_COUNT] = {0};
@@ -278,6 +289,7 @@ constexpr int kUpdBufs = Store::kUpdBufsN;
 
 // Allocation helpers (kbisim_api.cu)
 Status ensure(Store& s, Buf& b, size_t bytes);
+void read_fault_hooks(Store& s);
 void release(Store& s, Buf& b);
 Status cuda_check(cudaError_t e, const char* what);
 

@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "kbisim_internal.cuh"
@@ -1439,6 +1440,23 @@ __global__ void k_pid_fill(RankArgs r) {
   }
 }
 
+// Checked mode: every a[i] (i < n) must be below `bound`.  The kernels that
+// index with an array run only after this check has passed on it.
+__global__ void k_check_below(const uint32_t* a, uint64_t n, uint64_t bound, uint32_t* err) {
+  bool bad = false;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    bad |= (uint64_t)a[i] >= bound;
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrChecked);
+}
+
+// Checked mode: offsets non-decreasing from 0 to m.
+__global__ void k_check_offsets_mono(const uint64_t* off, uint64_t n, uint64_t m, uint32_t* err) {
+  bool bad = false;
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x)
+    bad |= off[p] > off[p + 1] || off[p + 1] > m || (p == 0 && off[0] != 0);
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrChecked);
+}
+
 // Level 0 hash: the node label.
 __global__ void k_label_hash(uint64_t n, const uint32_t* nlabel, uint64_t* hash, uint64_t seed, uint64_t mask) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
@@ -1847,6 +1865,25 @@ Status read_scalars(Store& s, uint64_t* out) {
   return Status::Ok();
 }
 
+// Checked mode: run a check kernel's verdict to the host.  Returns CHECKED if
+// an index check failed (the kernels that would use the array are not run).
+Status checked_verdict(Store& s, const char* what) {
+  uint32_t e = 0;
+  Status st = launch_check(what);
+  if (st.ok()) st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), what);
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), what);
+  if (!st.ok()) return st;
+  if (e & kErrChecked) return Status::Err(KBISIM_ERR_CHECKED, std::string("index check failed: ") + what);
+  return Status::Ok();
+}
+
+Status check_below(Store& s, const uint32_t* a, uint64_t n, uint64_t bound, const char* what) {
+  if (!n) return Status::Ok();
+  const unsigned g = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sm_count(s.device) * 16);
+  k_check_below<<<g, 256, 0, s.stream>>>(a, n, bound, ptr<uint32_t>(s.d_err));
+  return checked_verdict(s, what);
+}
+
 uint64_t table_capacity(uint64_t n) {
   uint64_t c = 1024;
   while (c < 2 * n) c <<= 1;
@@ -1967,6 +2004,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
     cur ^= 1;
   }
   *collided = h[4];
+  if (s.checked && !(st = check_below(s, g.rep, na, n, "block heads")).ok()) return st;
   // canonical renumbering
   RankArgs r;
   r.n = n;
@@ -1993,6 +2031,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   cudaMemcpyAsync(sc + 7, s.d_err.p, 4, cudaMemcpyDeviceToDevice, s.stream);
   if (!(st = read_scalars(s, h)).ok()) return st;
   *blocks = n ? h[15] : 0;  // scan total: heads
+  if (s.checked && !(st = check_below(s, pid, na, *blocks, "identifiers")).ok()) return st;
   s.n_alone = h[8];
   if (keys) *keys = h[2];
   if (maxsig) *maxsig = h[3];
@@ -2368,10 +2407,45 @@ Status compute_level0(Store& s) {
   return Status::Ok();
 }
 
+// Checked mode, before a round: the edge table's offsets and targets and the
+// previous level's identifiers (the indices and the packed values of the
+// signature kernels).  With the KBISIM_FAULT_CORRUPT_DST test hook one target
+// is set to n first (and put back after the check reports it).
+Status check_round_inputs(Store& s, uint32_t i) {
+  Status st;
+  uint32_t saved = 0;
+  const uint64_t at = s.m / 2;
+  uint32_t* dst = ptr<uint32_t>(s.dst);
+  if (s.fault_corrupt_dst && s.m) {
+    const uint32_t bad = (uint32_t)s.n;
+    st = cuda_check(cudaMemcpyAsync(&saved, dst + at, 4, cudaMemcpyDeviceToHost, s.stream), "corrupt");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "corrupt");
+    if (st.ok()) st = cuda_check(cudaMemcpyAsync(dst + at, &bad, 4, cudaMemcpyHostToDevice, s.stream), "corrupt");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "corrupt");
+    if (!st.ok()) return st;
+  }
+  if (s.n) {
+    const unsigned g = (unsigned)std::min<uint64_t>(grid_for(s.n, 256), (uint64_t)sm_count(s.device) * 16);
+    k_check_offsets_mono<<<g, 256, 0, s.stream>>>(ptr<uint64_t>(s.offsets), s.n, s.m, ptr<uint32_t>(s.d_err));
+    st = checked_verdict(s, "edge offsets");
+  }
+  if (st.ok()) st = check_below(s, dst, s.m, s.n, "edge targets");
+  if (s.fault_corrupt_dst && s.m) {
+    Status st2 = cuda_check(cudaMemcpyAsync(dst + at, &saved, 4, cudaMemcpyHostToDevice, s.stream), "restore");
+    if (st2.ok()) st2 = cuda_check(cudaStreamSynchronize(s.stream), "restore");
+    if (!st2.ok()) return st2;
+  }
+  if (st.ok()) st = check_below(s, ptr<uint32_t>(s.level[i - 1]), s.n_alive, s.counts[i - 1], "previous level");
+  return st;
+}
+
 Status compute_round(Store& s, uint32_t i) {
+  if (s.fault_timeout_round && i == s.fault_timeout_round)
+    return Status::Err(KBISIM_ERR_TIMEOUT, "injected timeout (KBISIM_FAULT_TIMEOUT_ROUND)");
   Status st = ensure_round_scratch(s);
   if (!st.ok()) return st;
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  if (s.checked && !(st = check_round_inputs(s, i)).ok()) return st;
   SigArgs a;
   a.off = ptr<uint64_t>(s.offsets);
   a.dst = ptr<uint32_t>(s.dst);

@@ -31,9 +31,11 @@ namespace {
 template <typename T>
 T* ptr(Buf& b) { return static_cast<T*>(b.p); }
 
-unsigned grid(uint64_t work, unsigned per) {
+// Grid of a grid-stride loop over `work` items, `per` per CTA: at most 32
+// CTAs per multiprocessor of the handle's device.
+unsigned grid(const Store& s, uint64_t work, unsigned per) {
   uint64_t g = (work + per - 1) / per;
-  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 152ull * 32));
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)s.sms * 32));
 }
 
 #define GRID_STRIDE(i, n) \
@@ -408,14 +410,14 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   uint8_t* alive = ptr<uint8_t>(t.b[ALIVE]);
   uint32_t* err = ptr<uint32_t>(t.b[ERR]);
   cudaMemsetAsync(err, 0, 64, s.stream);
-  k_alive_init<<<grid(n1, 256), 256, 0, s.stream>>>(n0, n1, s.any_dead ? ptr<uint8_t>(s.alive_o) : nullptr, alive);
-  if (bt->n_ins) k_check_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, n1, is, it, alive, err);
+  k_alive_init<<<grid(s, n1, 256), 256, 0, s.stream>>>(n0, n1, s.any_dead ? ptr<uint8_t>(s.alive_o) : nullptr, alive);
+  if (bt->n_ins) k_check_inserts<<<grid(s, bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, n1, is, it, alive, err);
   if (bt->n_del) {
-    k_check_ids_only<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, ds, err);
-    k_check_ids_only<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, dt, err);
+    k_check_ids_only<<<grid(s, bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, ds, err);
+    k_check_ids_only<<<grid(s, bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, n1, dt, err);
   }
   if (bt->n_del_nodes)
-    k_check_node_dels<<<grid(bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, n1, dn, alive, err);
+    k_check_node_dels<<<grid(s, bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, n1, dn, alive, err);
   uint32_t e = 0;
   st = cuda_check(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s.stream), "validate batch");
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
@@ -432,16 +434,16 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (!(st = ensure(s, t.b[CLAB], std::max<uint64_t>(mc, 1) * 4)).ok()) return st;
   unsigned long long* coff = ptr<unsigned long long>(t.b[COFF]);
   cudaMemsetAsync(coff, 0, (n1 + 1) * 8, s.stream);
-  if (n0) k_count_combined<<<grid(n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint64_t>(s.offsets),
+  if (n0) k_count_combined<<<grid(s, n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint64_t>(s.offsets),
                                                                bt->n_ins, is, coff);
-  if (bt->n_ins) k_count_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, coff);
+  if (bt->n_ins) k_count_inserts<<<grid(s, bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, coff);
   uint64_t total = 0;
   if (!(st = scan_u64(s, coff, n1 + 1, nullptr, t.b[CNT], &total)).ok()) return st;
   unsigned long long* cur = ptr<unsigned long long>(t.b[CUR]);
   uint32_t* cdst = ptr<uint32_t>(t.b[CDST]);
   uint32_t* clab = ptr<uint32_t>(t.b[CLAB]);
   if (n0) {
-    const unsigned g = grid(n0 * 32, 256);
+    const unsigned g = grid(s, n0 * 32, 256);
     if (s.label8)
       k_copy_stored<uint8_t><<<g, 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.p2o),
                                                       ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst),
@@ -453,7 +455,7 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   }
   if (n1 > n0)  // new nodes start empty
     cudaMemcpyAsync(cur + n0, coff + n0, (n1 - n0) * 8, cudaMemcpyDeviceToDevice, s.stream);
-  if (bt->n_ins) k_place_inserts<<<grid(bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, it, il, cur, cdst, clab);
+  if (bt->n_ins) k_place_inserts<<<grid(s, bt->n_ins, 256), 256, 0, s.stream>>>(bt->n_ins, is, it, il, cur, cdst, clab);
   if (!(st = cuda_check(cudaGetLastError(), "combine edges")).ok()) return st;
 
   // 2. deletions, matched per source
@@ -469,29 +471,29 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
     unsigned long long* rsz = ptr<unsigned long long>(t.b[RSZ]);
     unsigned long long* rbase = ptr<unsigned long long>(t.b[RBASE]);
     cudaMemsetAsync(dcnt, 0, (n1 + 1) * 8, s.stream);
-    k_count_deletes<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, n1, dcnt);
-    k_region_size<<<grid(n1 + 1, 256), 256, 0, s.stream>>>(n1 + 1, dcnt, rsz);
+    k_count_deletes<<<grid(s, bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, n1, dcnt);
+    k_region_size<<<grid(s, n1 + 1, 256), 256, 0, s.stream>>>(n1 + 1, dcnt, rsz);
     cudaMemcpyAsync(rbase, rsz, (n1 + 1) * 8, cudaMemcpyDeviceToDevice, s.stream);
     uint64_t slots = 0;
     if (!(st = scan_u64(s, rbase, n1 + 1, nullptr, t.b[NOFF], &slots)).ok()) return st;
     if (!(st = ensure(s, t.b[TAB], std::max<uint64_t>(slots, 1) * sizeof(DelSlot))).ok()) return st;
     DelSlot* tab = ptr<DelSlot>(t.b[TAB]);
     cudaMemsetAsync(tab, 0, slots * sizeof(DelSlot), s.stream);
-    k_insert_deletes<<<grid(bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, dt, dl, rbase, rsz, tab, err);
+    k_insert_deletes<<<grid(s, bt->n_del, 256), 256, 0, s.stream>>>(bt->n_del, ds, dt, dl, rbase, rsz, tab, err);
     if (!(st = ensure(s, t.b[LIST], std::max<uint64_t>(n1, 1) * 4)).ok()) return st;
     unsigned long long* nl = reinterpret_cast<unsigned long long*>(err + 8);
     cudaMemsetAsync(nl, 0, 8, s.stream);
-    k_sources_with_deletes<<<grid(n1, 256), 256, 0, s.stream>>>(n1, dcnt, nl, ptr<uint32_t>(t.b[LIST]));
+    k_sources_with_deletes<<<grid(s, n1, 256), 256, 0, s.stream>>>(n1, dcnt, nl, ptr<uint32_t>(t.b[LIST]));
     uint64_t nsrc = 0;
     st = cuda_check(cudaMemcpyAsync(&nsrc, nl, 8, cudaMemcpyDeviceToHost, s.stream), "delete sources");
     if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
     if (!st.ok()) return st;
     if (nsrc)
-      k_match_deletes<<<grid(nsrc * 32, 256), 256, 0, s.stream>>>(nsrc, ptr<uint32_t>(t.b[LIST]), coff, cdst, clab,
+      k_match_deletes<<<grid(s, nsrc * 32, 256), 256, 0, s.stream>>>(nsrc, ptr<uint32_t>(t.b[LIST]), coff, cdst, clab,
                                                                   rbase, rsz, tab, delf);
     unsigned long long* dmiss = reinterpret_cast<unsigned long long*>(err + 10);
     cudaMemsetAsync(dmiss, 0, 8, s.stream);
-    if (slots) k_missing<<<grid(slots, 256), 256, 0, s.stream>>>(slots, tab, dmiss);
+    if (slots) k_missing<<<grid(s, slots, 256), 256, 0, s.stream>>>(slots, tab, dmiss);
     st = cuda_check(cudaMemcpyAsync(&missing, dmiss, 8, cudaMemcpyDeviceToHost, s.stream), "missing");
     uint32_t e2 = 0;
     if (st.ok()) st = cuda_check(cudaMemcpyAsync(&e2, err, 4, cudaMemcpyDeviceToHost, s.stream), "err");
@@ -501,26 +503,26 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   }
 
   // 3. node deletions; keep the rest
-  if (bt->n_del_nodes) k_mark_dead_nodes<<<grid(bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, dn, alive);
+  if (bt->n_del_nodes) k_mark_dead_nodes<<<grid(s, bt->n_del_nodes, 256), 256, 0, s.stream>>>(bt->n_del_nodes, dn, alive);
   if (!(st = ensure(s, t.b[NOFF], (n1 + 1) * 8)).ok()) return st;
   unsigned long long* noff = ptr<unsigned long long>(t.b[NOFF]);
   cudaMemsetAsync(noff, 0, (n1 + 1) * 8, s.stream);
-  k_count_kept<<<grid(n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, delf, alive, noff);
+  k_count_kept<<<grid(s, n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, delf, alive, noff);
   uint64_t m1 = 0;
   if (!(st = scan_u64(s, noff, n1 + 1, nullptr, t.b[CNT], &m1)).ok()) return st;
   if (!(st = ensure(s, t.b[NDST], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
   if (!(st = ensure(s, t.b[NLAB], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
-  k_compact<<<grid(n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, clab, delf, alive, noff, ptr<uint32_t>(t.b[NDST]),
+  k_compact<<<grid(s, n1 * 32, 256), 256, 0, s.stream>>>(n1, coff, cdst, clab, delf, alive, noff, ptr<uint32_t>(t.b[NDST]),
                                                      ptr<uint32_t>(t.b[NLAB]));
   // node labels in original order (stored ones, then the added ones)
   if (!(st = ensure(s, t.b[CNT], std::max<uint64_t>(n1, 1) * 4)).ok()) return st;
   uint32_t* nlab = ptr<uint32_t>(t.b[CNT]);
-  if (n0) k_gather_labels<<<grid(n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.nlabel), nlab);
+  if (n0) k_gather_labels<<<grid(s, n0, 256), 256, 0, s.stream>>>(n0, ptr<uint32_t>(s.o2p), ptr<uint32_t>(s.nlabel), nlab);
   if (n1 > n0) cudaMemcpyAsync(nlab + n0, addl, (n1 - n0) * 4, cudaMemcpyDeviceToDevice, s.stream);
   unsigned int* dmax = reinterpret_cast<unsigned int*>(err + 12);
   cudaMemsetAsync(dmax, 0, 8, s.stream);
-  if (m1) k_max32<<<grid(m1, 256), 256, 0, s.stream>>>(m1, ptr<uint32_t>(t.b[NLAB]), dmax);
-  k_any_dead<<<grid(n1, 256), 256, 0, s.stream>>>(n1, alive, dmax + 1);
+  if (m1) k_max32<<<grid(s, m1, 256), 256, 0, s.stream>>>(m1, ptr<uint32_t>(t.b[NLAB]), dmax);
+  k_any_dead<<<grid(s, n1, 256), 256, 0, s.stream>>>(n1, alive, dmax + 1);
   uint32_t hv[2] = {0, 0};
   st = cuda_check(cudaGetLastError(), "compact");
   if (st.ok()) st = cuda_check(cudaMemcpyAsync(hv, dmax, 8, cudaMemcpyDeviceToHost, s.stream), "label max");

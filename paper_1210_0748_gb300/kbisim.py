@@ -100,6 +100,7 @@ SIGNATURES = {
     "kbisim_pids_device": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_uint32]),
     "kbisim_num_nodes": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_num_edges": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "kbisim_device_bytes": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_get_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
     "kbisim_reset_times": (None, [ctypes.c_void_p]),
     "kbisim_get_round_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
@@ -404,11 +405,17 @@ class KBisim:
     def num_edges(self) -> int:
         return int(self._lib.kbisim_num_edges(self._h))
 
+    @property
+    def device_bytes(self) -> int:
+        """Device bytes the handle holds (what hbm_budget_bytes bounds)."""
+        return int(self._lib.kbisim_device_bytes(self._h))
+
     def pids(self, level: int, out=None):
         """Level ``level`` as a host numpy uint32 array, or into ``out`` (a CUDA
         int32 tensor of num_nodes elements)."""
         n = self.num_nodes
         if out is not None:
+            check_device_tensor(out, "out", n, device=self.device)
             self._check(self._lib.kbisim_pids(self._h, int(level), ctypes.c_void_p(out.data_ptr()), 1))
             return out
         host = np.empty(n, dtype=np.uint32)
@@ -439,10 +446,37 @@ class KBisim:
         return {f: int(getattr(st, f)) for f, _ in RoundStats._fields_}
 
 
+def check_device_tensor(t, name: str, min_numel: int, device=None) -> None:
+    """Raise ValueError unless ``t`` is a contiguous CUDA int32 tensor on
+    ``device`` (default: the current CUDA device) with at least ``min_numel``
+    elements.  Runs before any pointer reaches the library, so a host tensor,
+    a wrong dtype or a short buffer never becomes an out-of-range device write."""
+    if not _is_torch(t):
+        raise ValueError("%s must be a torch tensor" % name)
+    torch = _torch()
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    want = torch.cuda.current_device() if device is None else int(device)
+    if t.device.index != want:
+        raise ValueError("%s is on cuda:%s, expected cuda:%d" % (name, t.device.index, want))
+    if t.dtype != torch.int32:
+        raise ValueError("%s must be int32, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < min_numel:
+        raise ValueError("%s has %d elements, needs at least %d" % (name, t.numel(), min_numel))
+
+
 def label_partition_noalloc(node_label, pid0, block_count=None, stream=None) -> None:
     """Level 0 of CUDA int32 tensor ``node_label`` into CUDA int32 tensor
     ``pid0`` (and the block count into a one-element CUDA int32 tensor),
     without any device allocation: see kbisim_label_partition_noalloc."""
+    if not _is_torch(node_label):
+        raise ValueError("node_label must be a torch tensor")
+    check_device_tensor(node_label, "node_label", 0)
+    check_device_tensor(pid0, "pid0", node_label.numel())
+    if block_count is not None:
+        check_device_tensor(block_count, "block_count", 1)
     lib = load_library()
     if stream is None:
         stream = _torch().cuda.current_stream().cuda_stream

@@ -43,3 +43,20 @@ def test_create_without_gpu_fails_loudly():
         assert e.code == kbisim.ERR_CUDA
     else:  # pragma: no cover
         raise AssertionError("created a handle without a GPU")
+
+
+def test_binding_rejects_bad_tensors_before_the_library():
+    """The binding checks device buffers (CUDA, current device, int32,
+    contiguous, large enough) before any pointer reaches the library; these
+    checks run on the host, so they are tested on the CPU."""
+    import pytest
+    import torch
+    ok = torch.zeros(4, dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):
+        kbisim.label_partition_noalloc(ok, ok)
+    with pytest.raises(ValueError, match="torch tensor"):
+        kbisim.label_partition_noalloc([0, 1], ok)
+    with pytest.raises(ValueError):
+        kbisim.check_device_tensor(torch.zeros(4, dtype=torch.int64), "x", 1)
+    with pytest.raises(ValueError):
+        kbisim.check_device_tensor(ok, "x", 8)

@@ -1,6 +1,8 @@
 """Serving loop: requests that overlap on the device give, request by request,
-exactly what the same requests give one at a time (tolerance zero: counts,
-rounds and a digest of the level-k identifiers)."""
+exactly what the oracle gives for the same request sequence replayed on the
+host (oracle.update.MultiGraph: apply each batch to the edge multiset, then
+Algorithm 1), and what the same requests give one at a time (tolerance zero:
+counts, rounds, a digest of the level-k identifiers, edge count)."""
 import numpy as np
 import pytest
 
@@ -8,6 +10,26 @@ from paper_1210_0748_gb300 import synth
 from paper_1210_0748_gb300.serve import Server, make_requests, run_alone
 
 pytestmark = pytest.mark.gpu
+
+
+def oracle_replay(graphs, requests):
+    """Each request's result from the oracle: per graph, the requests in
+    arrival order, each update applied to the graph's edge multiset before
+    its levels are recomputed."""
+    from oracle.update import MultiGraph
+    from paper_1210_0748_gb300.serve import _digest
+    mgs = [MultiGraph(g.num_nodes, g.node_label, g.src(), g.dst, g.edge_label) for g in graphs]
+    out = {}
+    for r in sorted(requests, key=lambda r: (r.t_arrive, r.rid)):
+        mg = mgs[r.graph]
+        if r.kind == "update":
+            ins = list(zip(*r.ins)) if r.ins is not None else []
+            dels = list(zip(*r.dels)) if r.dels is not None else []
+            mg.apply(ins=ins, dels=dels)
+        ref = mg.kbisim(r.k)
+        out[r.rid] = ([int(c) for c in ref.counts], ref.rounds_run, _digest(ref.pids[r.k]),
+                      sum(mg.edges.values()))
+    return out
 
 
 def _graphs():
@@ -25,9 +47,11 @@ def test_results_in_the_mix_equal_alone(slots):
     finally:
         srv.close()
     alone = run_alone(graphs, ks, reqs)
+    ref = oracle_replay(graphs, reqs)
     assert [o.rid for o in mix] == [o.rid for o in alone] == list(range(48))
     for a, b in zip(mix, alone):
         assert (a.counts, a.rounds_run, a.digest, a.edges) == (b.counts, b.rounds_run, b.digest, b.edges), a.rid
+        assert (a.counts, a.rounds_run, a.digest, a.edges) == ref[a.rid], a.rid
     assert {o.kind for o in mix} == {"update", "rebuild"}
 
 

@@ -4,7 +4,7 @@ call divide by rounds (signature classes) or levels (the others)."""
 import csv
 import json
 
-from paper_1210_0748_gb300 import ncu_summary
+import ncu_summary
 
 HDR = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
        "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]

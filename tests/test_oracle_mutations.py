@@ -81,3 +81,21 @@ def test_pins_catch_planted_mistake(tmp_path, name):
     finally:
         oracle._lib = real
     assert failures > 0, "no pin caught mutation %s" % name
+
+
+def test_delete_pin_catches_deleting_every_copy(monkeypatch):
+    """A planted mistake in the update oracle: a deletion that removes every
+    copy of its triple instead of one.  The hand-worked delete pin fails."""
+    from oracle import update
+
+    def apply_all_copies(self, add_node_label=(), ins=(), dels=(), del_nodes=()):
+        missing = 0
+        for s, t, l in dels:
+            key = (int(s), int(l), int(t))
+            if self.edges.pop(key, 0) == 0:
+                missing += 1
+        return missing
+
+    monkeypatch.setattr(update.MultiGraph, "apply", apply_all_copies)
+    with pytest.raises(AssertionError):
+        pins.test_delete_removes_one_copy_of_a_repeated_triple()

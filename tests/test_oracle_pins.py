@@ -302,3 +302,38 @@ def test_update_recompute_with_deletes():
     # the same graph built directly, with the dead node's edges gone
     s2, d2, l2 = mg.coo()
     assert not ((s2 == 5) | (d2 == 5)).any()
+
+
+def _figure1_with_doubled_works_edge():
+    """The Figure 1 graph with its edge (1, w, 2) given twice."""
+    f = golden_io.load("fig1_table1.txt")
+    one, w, two = f.node("1"), f.elab("w"), f.node("2")
+    assert (one, w, two) in f.edges
+    s, d, l = f.coo(list(f.edges) + [(one, w, two)])
+    return f, MultiGraph(len(f.node_names), f.node_label, s, d, l), (one, two, w)
+
+
+def test_delete_removes_one_copy_of_a_repeated_triple():
+    """A deletion removes one stored copy of its triple.  With (1, w, 2) stored
+    twice, deleting it once leaves the Figure 1 graph (Table 1 unchanged);
+    deleting it twice leaves the graph without that edge, worked by hand from
+    Definitions 1-3 (nodes 1..6 as ids 0..5, canonical numbering):
+      level 0: M = {1, 2}, P = {3, 4, 5, 6}              -> 0 0 1 1 1 1
+      level 1: 1 (M, {l P}); 2 (M, {w M, l P}); 3 and 5 (P, {l M});
+               4 (P, {l P}); 6 (P, {})                     -> 0 1 2 3 2 4
+      level 2: 3 -> child 1 (block 0), 5 -> child 2 (block 1): split
+                                                           -> 0 1 2 3 4 5
+    A third deletion names an absent triple and is only counted."""
+    f, mg, (one, two, w) = _figure1_with_doubled_works_edge()
+    assert mg.apply(dels=[(one, two, w)]) == 0
+    r = mg.kbisim(2, early_stop=False)
+    for lev in (0, 1, 2):
+        assert r.pids[lev].tolist() == golden_io.canonical(f.pids[lev]), lev
+    assert mg.apply(dels=[(one, two, w)]) == 0
+    r = mg.kbisim(2, early_stop=False)
+    assert r.pids[0].tolist() == [0, 0, 1, 1, 1, 1]
+    assert r.pids[1].tolist() == [0, 1, 2, 3, 2, 4]
+    assert r.pids[2].tolist() == [0, 1, 2, 3, 4, 5]
+    assert r.counts.tolist() == [2, 5, 6]
+    assert mg.apply(dels=[(one, two, w)]) == 1
+    assert mg.kbisim(2, early_stop=False).pids[2].tolist() == [0, 1, 2, 3, 4, 5]
