@@ -258,7 +258,10 @@ int kbisim_many_pids(kbisim_handle *h, uint32_t graph, uint32_t level, uint32_t 
 int kbisim_many_info(kbisim_handle *h, uint32_t graph, uint32_t *rounds_run, uint64_t *counts);
 
 /* Copy level `level` (0..k of the last result) into dst[num_nodes]
- * (host memory when dst_on_device = 0).  Errors: STATE, INVALID_ARG. */
+ * (host memory when dst_on_device = 0).  A handle without an HBM budget keeps
+ * an original-order copy of each level it has returned (until the levels
+ * change); a handle with a budget allocates nothing here.
+ * Errors: STATE, INVALID_ARG, OUT_OF_MEMORY. */
 int kbisim_pids(kbisim_handle *h, uint32_t level, uint32_t *dst, int dst_on_device);
 
 /* Device pointer to level `level` ([num_nodes] uint32), owned by the handle;

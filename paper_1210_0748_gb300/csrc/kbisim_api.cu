@@ -776,6 +776,12 @@ int kbisim_pids(kbisim_handle* h, uint32_t level, uint32_t* dst, int dst_on_devi
   Status st;
   if (dst_on_device) {
     st = kb::unpermute_level(s, l, dst);
+  } else if (s.budget && s.hash.cap >= s.n * 4) {
+    // a budget handle allocates nothing to read a level: the original-order
+    // copy goes through the round scratch (the hash array, idle between calls)
+    st = kb::unpermute_level(s, l, static_cast<uint32_t*>(s.hash.p));
+    if (st.ok())
+      st = kb::cuda_check(cudaMemcpyAsync(dst, s.hash.p, s.n * 4, cudaMemcpyDeviceToHost, s.stream), "copy out");
   } else {
     st = kb::materialize_level(s, l);
     if (st.ok())

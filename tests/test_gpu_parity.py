@@ -448,3 +448,40 @@ def test_hub_with_one_heavy_key_among_distinct_keys(heavy):
     g = synth.from_coo(n, src, dst, lab, nl)
     res, pids = gpu_levels(g, 3)
     assert_same(res, pids, oracle_levels(g, 3))
+
+
+def _mix32(x):
+    """MurmurHash3's 32-bit finalizer on uint64 arrays (values < 2^32)."""
+    x = x.astype(np.uint64)
+    m = np.uint64(0xFFFFFFFF)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85ebca6b)) & m
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xc2b2ae35)) & m
+    x ^= x >> np.uint64(16)
+    return x
+
+
+def test_hub_whose_keys_crowd_one_set_part():
+    """Level 0 gives every node its own block (pId_0(v) = v over 2^17 nodes),
+    so round 1 packs an element as (label << 17) | child before the mix.  A
+    100K-edge hub gets only elements whose mixed word has its two top bits
+    clear: the top bits pick the CTA that owns a key, so every key lands in
+    one part of the hub's set, which holds a third of them.  The part
+    overflows, the library regroups the hub's keys (by their low bits) and
+    must still equal the oracle."""
+    n = 1 << 17
+    rng = np.random.default_rng(61)
+    lab = rng.integers(0, 1 << 15, 2_000_000, dtype=np.uint64)
+    child = rng.integers(0, n, 2_000_000, dtype=np.uint64)
+    packed = np.unique((lab << np.uint64(17)) | child)
+    packed = packed[(_mix32(packed) >> np.uint64(30)) == 0]
+    packed = rng.permutation(packed)[:100_000]
+    assert packed.size == 100_000
+    other = 50_000
+    src = np.concatenate([np.zeros(packed.size, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
+    dst = np.concatenate([(packed & np.uint64(n - 1)).astype(np.uint32), rng.integers(0, n, other).astype(np.uint32)])
+    el = np.concatenate([(packed >> np.uint64(17)).astype(np.uint32), rng.integers(0, 3, other).astype(np.uint32)])
+    g = synth.from_coo(n, src, dst, el, np.arange(n, dtype=np.uint32))
+    res, pids = gpu_levels(g, 2)
+    assert_same(res, pids, oracle_levels(g, 2))
