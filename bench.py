@@ -98,11 +98,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-clocks", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "large", "serve"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "large", "serve", "update"],
                    help="single: the 16M/256M graph (the headline line); batched: 4096 graphs "
                         "(times --scale) in one batched build vs one build per graph; large: the "
                         "256M-node / 2B-edge graph; serve: 64 resident graphs under Poisson request "
-                        "streams")
+                        "streams; update: maintenance batches on the 16M/256M graph, incremental "
+                        "against recomputation")
+    p.add_argument("--batch", type=int, default=1000, help="edges per maintenance batch (update)")
+    p.add_argument("--k", type=int, default=3, help="levels kept by maintenance (update)")
     p.add_argument("--requests", type=int, default=120, help="requests per arrival rate (serve)")
     return p.parse_args()
 
@@ -330,6 +333,66 @@ def run_batched(args):
     return 0
 
 
+def run_update(args):
+    """Maintenance batches (half inserts of random edges, half deletions of
+    stored edges) on the 16M/256M graph with k levels: the same sequence of
+    batches through the incremental frontier path (options.maintain = 1) and
+    through recomputation (maintain = 0), each timed per update (host wall
+    clock around kbisim_update, which waits for its stream), with the levels of
+    both handles compared after every batch."""
+    import torch
+    from paper_1210_0748_gb300.kbisim import KBisim
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    g, cfg = workload(args.scale)
+    rng = np.random.default_rng(77)
+    src = g.src()
+    nb = max(2, args.batch)
+    batches = []
+    for _ in range(args.warmup + args.steps):
+        ni, nd = nb // 2, nb - nb // 2
+        ins = (rng.integers(0, g.num_nodes, ni).astype(np.uint32), rng.integers(0, g.num_nodes, ni).astype(np.uint32),
+               rng.integers(0, 32, ni).astype(np.uint32))
+        e = rng.integers(0, g.num_edges, nd)
+        dels = (src[e], g.dst[e], g.edge_label[e].astype(np.uint32))
+        batches.append((ins, dels))
+    out = {}
+    levels = {}
+    for name, maintain in (("incremental", True), ("recompute", False)):
+        stream = torch.cuda.Stream(device=local_rank)
+        kb = KBisim(device=local_rank, stream=stream, maintain=maintain)
+        kb.build(g, args.k)
+        times, paths, nodes = [], [], []
+        for i, (ins, dels) in enumerate(batches):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kb.update(args.k, ins=ins, dels=dels)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt * 1000.0)
+                info = kb.update_info()
+                paths.append(info["reason"])
+                nodes.append(info["frontier_nodes"])
+            levels.setdefault(i, []).append(kb.pids(args.k))
+        out[name] = {"ms_per_update_median": float(np.median(times)), "ms_per_update_mean": float(np.mean(times)),
+                     "paths": {p: paths.count(p) for p in set(paths)},
+                     "frontier_nodes_median": float(np.median(nodes)) if nodes else 0.0}
+        kb.close()
+    same = all(np.array_equal(v[0], v[1]) for v in levels.values())
+    line = {"metric": "maintenance: ms per update batch of %d edges, k=%d (1 GB300)" % (nb, args.k),
+            "value": out["incremental"]["ms_per_update_median"], "unit": "ms", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(cfg, batch_edges=nb, k=args.k),
+            "incremental": out["incremental"], "recompute": out["recompute"],
+            "speedup": out["recompute"]["ms_per_update_median"] / out["incremental"]["ms_per_update_median"],
+            "levels_equal": same,
+            "timing": "host wall clock around each kbisim_update (the call waits for its stream)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def run_serve(args):
     """Resident graphs under Poisson request streams (70% update batches of
     1K..1M edges, 30% rebuilds at k 3..10) at several arrival rates: latency
@@ -394,6 +457,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "update":
+        return run_update(args)
     import torch
     from paper_1210_0748_gb300.kbisim import KBisim
 

@@ -107,10 +107,19 @@ typedef struct {
   /* 1 = record CUDA events around every kernel and keep per-kernel totals
    * (see kbisim_kernel_times). */
   int collect_timing;
+  /* 1 (default) = kbisim_update maintains the levels incrementally (Section
+   * 4, Algorithm 3): only nodes whose signature may have changed are signed
+   * again, level by level, against per-level signature stores kept in the
+   * handle; 0 = kbisim_update recomputes every level.  Results are identical.
+   * The stores are made at the first update after a build (a cost of about
+   * one signature pass per level) and take about 12 bytes per edge and 16 per
+   * node per maintained level. */
+  int maintain;
 } kbisim_options;
 
 /* Fill *opt with the defaults (stream NULL, device 0, no budget, early stop
- * on, a fixed seed, 64 hash bits, unchecked, no timing). */
+ * on, a fixed seed, 64 hash bits, unchecked, no timing, incremental
+ * maintenance). */
 void kbisim_default_options(kbisim_options *opt);
 
 /* A graph <N, E, lambda_N, lambda_E> (Section 2.1).
@@ -214,10 +223,20 @@ typedef struct {
   int on_device;
 } kbisim_batch;
 
-/* Apply a batch to the loaded graph and recompute levels 0..k so that the
- * result equals a build of the updated graph (Theorem 2: the maintained
- * partition is the k-bisimulation of the new graph).  *missing_deletes (may
- * be NULL) receives the number of edge deletions that named no edge.
+/* Apply a batch to the loaded graph and bring levels 0..k up to date, so
+ * that the result equals a build of the updated graph (Theorem 2: the
+ * maintained partition is the k-bisimulation of the new graph).  With
+ * options.maintain the levels are maintained incrementally (Algorithm 3): the
+ * frontier of level 1 is the sources of the batch's edges and the new nodes;
+ * a node is signed again at level j only if it is such a source, or its own
+ * level-(j-1) label changed, or a child's did; its signature is looked up in
+ * the level's signature store, which keeps labels of unchanged signatures.
+ * The update switches back to a full recomputation (Section 4, "When to
+ * switch back to Algorithm 1") when a level's frontier holds more than a
+ * quarter of the nodes (and more than 4096), when a store runs out of room, when the batch deletes
+ * nodes, or when k exceeds the levels the stores hold; kbisim_update_info
+ * tells which path the last update took.  *missing_deletes (may be NULL)
+ * receives the number of edge deletions that named no edge.
  * Errors: STATE, INVALID_ARG (bad id, or an edge on a deleted node), and the
  * errors of kbisim_refine.  A batch that is rejected (INVALID_ARG), or whose
  * staging or matching fails (OUT_OF_MEMORY, BUDGET, TIMEOUT), leaves the graph
@@ -227,6 +246,22 @@ typedef struct {
  * (KBISIM_ERR_STATE on read; kbisim_refine computes them). */
 int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_result *out,
                   uint64_t *missing_deletes);
+
+/* How the last kbisim_update ran.  incremental = 1: the frontier path, with
+ * frontier_nodes nodes signed over `levels` levels; 0: every level was
+ * recomputed, for the reason in `reason` (KBISIM_MAINT_*). */
+#define KBISIM_MAINT_OFF 1        /* options.maintain = 0 */
+#define KBISIM_MAINT_NO_STORE 2   /* no stores yet (first update after a build), or k above them */
+#define KBISIM_MAINT_FRONTIER 3   /* a level's frontier held more than a quarter of the nodes (and > 4096) */
+#define KBISIM_MAINT_CAPACITY 4   /* a signature store ran out of room */
+#define KBISIM_MAINT_DELETES 5    /* the batch deletes nodes */
+typedef struct {
+  int incremental;
+  int reason;
+  uint64_t frontier_nodes;
+  uint64_t levels;
+} kbisim_update_info;
+int kbisim_get_update_info(const kbisim_handle *h, kbisim_update_info *out);
 
 /* Batched build: many independent graphs refined together, one sequence of
  * kernel launches per round for all of them.  The paper has no counterpart

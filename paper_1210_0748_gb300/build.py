@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libkbisim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kbisim_api.cu", "kbisim_round.cu", "kbisim_update.cu", "kbisim_many.cu", "kbisim_noalloc.cu"]
+SOURCES = ["kbisim_api.cu", "kbisim_round.cu", "kbisim_update.cu", "kbisim_many.cu", "kbisim_noalloc.cu",
+           "kbisim_maint.cu"]
 
 
 def nvcc() -> str:

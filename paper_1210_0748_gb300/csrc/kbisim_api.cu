@@ -292,6 +292,7 @@ void free_graph(Store& s, bool keep_buffers) {
   s.computed = 0;
   s.n = s.m = s.n_alive = 0;
   s.n_hub = 0;
+  kb::maint_release(s);
   s.many.valid = false;
   s.many.levels = 0;
 }
@@ -531,6 +532,13 @@ void put_back(Store& s, LevelSnapshot& p) {
   s.n_alone = p.n_alone;
 }
 
+// The levels of an incremental update are in place: result and outputs.
+Status finish_incremental(Store& s, uint32_t k, kbisim_result* out) {
+  invalidate_outputs(s);
+  fill_result(s, k, out);
+  return timer_collect(s);
+}
+
 Status refine_levels(Store& s, uint32_t k) {
   Status st;
   if (!(st = ensure_levels(s, s.early_stop ? std::min<uint32_t>(k, 1) : k)).ok()) return st;
@@ -643,6 +651,7 @@ void kbisim_default_options(kbisim_options* opt) {
   opt->hash_bits = 64;
   opt->checked = 0;
   opt->collect_timing = 0;
+  opt->maintain = 1;
 }
 
 int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
@@ -673,6 +682,7 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   s.hash_mask = o.hash_bits >= 64 ? ~0ull : ((1ull << o.hash_bits) - 1ull);
   s.checked = o.checked != 0;
   s.timing = o.collect_timing != 0;
+  s.maintain = o.maintain != 0;
   void* hp = nullptr;
   if (cudaMallocHost(&hp, 16 * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -810,6 +820,15 @@ uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
 uint64_t kbisim_num_edges(const kbisim_handle* h) { return h ? h->s.m : 0; }
 uint64_t kbisim_device_bytes(const kbisim_handle* h) { return h ? (uint64_t)h->s.bytes_held : 0; }
 
+int kbisim_get_update_info(const kbisim_handle* h, kbisim_update_info* out) {
+  if (!h || !out) return KBISIM_ERR_INVALID_ARG;
+  out->incremental = h->s.mt.incremental;
+  out->reason = h->s.mt.reason;
+  out->frontier_nodes = h->s.mt.frontier_nodes;
+  out->levels = h->s.mt.levels;
+  return KBISIM_OK;
+}
+
 int kbisim_get_kernel_times(const kbisim_handle* h, kbisim_kernel_times* out) {
   if (!h || !out) return KBISIM_ERR_INVALID_ARG;
   for (int i = 0; i < KBISIM_KERNEL_COUNT; ++i) {
@@ -840,9 +859,33 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
   if (!h) return KBISIM_ERR_INVALID_ARG;
   if (k > KBISIM_MAX_K) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "k too large"));
   enter(h);
+  kb::Store& s = h->s;
   uint64_t missing = 0;
-  Status st = kb::apply_batch(h->s, b, &missing);
-  if (st.ok()) st = kb::refine(h->s, k, out);
+  Status st;
+  bool done = false;
+  s.mt.incremental = 0;
+  s.mt.frontier_nodes = 0;
+  s.mt.levels = 0;
+  if (!s.maintain) {
+    s.mt.reason = KBISIM_MAINT_OFF;
+  } else if (b && b->n_del_nodes) {
+    s.mt.reason = KBISIM_MAINT_DELETES;
+  } else {
+    // stores made from the current levels when there are none for this k yet
+    if ((!s.mt.valid || k > s.mt.k) && s.has_levels && (s.k_requested >= k || s.stable)) {
+      if (!kb::maint_build(s, k).ok()) kb::maint_release(s);
+    }
+    if (s.mt.valid && k <= s.mt.k) st = kb::maint_update(s, b, k, &missing, &done);
+    else s.mt.reason = KBISIM_MAINT_NO_STORE;
+  }
+  if (st.ok() && !done) {
+    kb::maint_release(s);  // the graph changes under the stores
+    st = kb::apply_batch(s, b, &missing);
+  }
+  if (st.ok()) st = s.mt.incremental ? kb::finish_incremental(s, k, out) : kb::refine(s, k, out);
+  // after a full recomputation, stores for the next update
+  if (st.ok() && s.maintain && !s.mt.incremental && s.has_levels && !kb::maint_build(s, k).ok())
+    kb::maint_release(s);
   if (st.ok() && missing_deletes) *missing_deletes = missing;
   return finish(h, st);
 }

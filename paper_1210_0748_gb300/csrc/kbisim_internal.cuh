@@ -149,6 +149,44 @@ struct ManyState {
   Buf hbits, hword, cnt;                       // head bitmap, per-word prefix, per-graph prefix
 };
 
+// Incremental maintenance state (kbisim_maint.cu).  Level j of the
+// maintained partition gives every node a stable label L_j: level 0 the node
+// label itself, level j > 0 the label its signature
+//   sig_j(u) = (L_{j-1}(u), { (edge label, L_{j-1}(v)) : (u, v) in E })
+// has in the signature store S_j (the paper's S, one per level): a hash
+// table from signature hash to label plus, per label, the signature itself
+// (first component, element count, element words in a pool).  A label keeps
+// its meaning across updates, so a node whose signature does not change keeps
+// its label, and only changed labels propagate to parents (Algorithm 3).
+struct MaintLevel {
+  Buf lab;                  // uint32 [n] label of each node, original order (kDead: deleted)
+  Buf tkey;                 // uint64 [tcap] signature hash of each slot (all ones: empty)
+  Buf tval;                 // uint32 [tcap] label of each slot (kNone32 while being written)
+  Buf sfirst, scount;       // uint32 [lcap] first component and element count of each label's signature
+  Buf soff;                 // uint64 [lcap] first element word of each label in pool
+  Buf pool;                 // uint64 [pcap] element words of the stored signatures
+  Buf ctr;                  // uint64 [2] labels handed out, pool words used
+  uint64_t tcap = 0, lcap = 0, pcap = 0;
+};
+
+struct MaintState {
+  bool valid = false;
+  uint32_t k = 0;                   // levels 1..k are maintained
+  std::vector<MaintLevel> lv;       // [k + 1]; level 0 keeps only lab
+  Buf fmask, fnext, changed, seeds; // bitmaps over internal ids
+  Buf list, pend;                   // uint32 frontier list; pending head lookups
+  Buf prev_int;                     // uint32 [n] labels of the level below, internal order
+  Buf newlab;                       // uint32 [n] label found for each frontier head (internal id)
+  Buf minid, cnt;                   // uint32 [lcap] canonical renumbering from labels
+  Buf src;                          // uint32 staged sources of the batch's edges
+  Buf misc;                         // uint64 scalars
+  // last update
+  int incremental = 0;              // 1 = frontier path, 0 = full recomputation
+  int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)
+  uint64_t frontier_nodes = 0;      // nodes signed over all levels
+  uint64_t levels = 0;              // levels processed
+};
+
 struct Store;
 struct Status;
 using LevelHook = Status (*)(Store&, uint32_t);
@@ -254,6 +292,9 @@ struct Store {
   Buf h_scalars;               // pinned host mirror of d_scalars
 
   ManyState many;               // batched build (kbisim_build_many)
+  MaintState mt;                // incremental maintenance (kbisim_update with options.maintain)
+  bool maintain = true;
+  double maint_frontier_max = 0.25;  // switch back to a rebuild above this fraction of the nodes
   LevelHook level_hook = nullptr;  // called after each computed level (batched build)
 
   // Host-side fault injection for tests (read from the environment at every
@@ -304,12 +345,31 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
 Status apply_batch(Store& s, const kbisim_batch* b, uint64_t* missing);
 Status compute_level0(Store& s);                  // pId_0 into level[0]
 Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
+// Signatures of the nodes whose bit is set in fmask (bitmap over internal ids;
+// NULL = every node) from identifiers prev (internal order), as 64-bit
+// element words: each node's distinct words at its CSR offset in sigkey, its
+// count in ucnt and its hash in hash (first component prev[p]).
+Status masked_signatures(Store& s, const uint32_t* prev, const uint32_t* fmask);
+// Group the nodes of list (internal ids) by exact signature, as left in
+// sigkey / ucnt / hash by masked_signatures: rep[p] = the node of the list
+// with the smallest original id that has p's signature.
+Status group_list(Store& s, const uint32_t* list, uint64_t count, const uint32_t* prev);
 // Write level `level` in original node order to dst (device memory).
 Status unpermute_level(Store& s, uint32_t level, uint32_t* dst);
 Status timer_collect(Store& s);
 void timer_destroy(Store& s);
 // Exclusive prefix sum of a uint64 array in place (kbisim_round.cu).
 Status scan_u64(Store& s, uint64_t* a, uint64_t n);
+
+// Incremental maintenance (kbisim_maint.cu).  maint_build makes the state for
+// levels 1..k of the loaded graph from its canonical levels (which must be
+// computed up to k, or be stable before).  maint_update applies a batch and
+// brings levels and state up to date; *done = false means the batch was not
+// applied because this path does not take it (node deletions, no state for
+// k), and the caller recomputes.
+Status maint_build(Store& s, uint32_t k);
+Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missing, bool* done);
+void maint_release(Store& s);
 
 // Thread blocks of `kernel` (threads each, dyn_smem dynamic shared bytes) that
 // are resident on all `sms` multiprocessors at once: the grid of a grid-stride

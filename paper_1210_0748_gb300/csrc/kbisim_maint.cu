@@ -1,0 +1,850 @@
+// Incremental maintenance of the k-partition (paper Section 4: Algorithm 2
+// Add_Nodes, Algorithm 3 Add_Edges, and deletions of edges handled like
+// insertions), on the GPU.
+//
+// Algorithm 3 keeps, per level, the signature storage S across updates: a
+// node's identifier is what S returns for its signature, so a node whose
+// signature does not change keeps its identifier, and only nodes whose
+// identifier changed put their parents on the queue of the next level.
+// Here S_j is a device hash table from a 64-bit signature hash to a stable
+// label, with the signature of each label kept exactly (first component,
+// element count, element words) so that a hash collision never merges two
+// signatures.  Level 0 labels are the node labels themselves.
+//
+// One update (edge insertions, edge deletions, node additions):
+//   1. the batch is applied to the stored edge multiset (kbisim_update.cu);
+//   2. the frontier of level 1 is the set of nodes whose out-edges changed and
+//      the new nodes (the paper enqueues (j, s) for every level j and every
+//      source s of a new edge);
+//   3. for j = 1..k: if the frontier holds more than a fixed fraction of the
+//      nodes, switch back to the full computation (the paper's "When to switch
+//      back to Algorithm 1": check the queue size at the start of an
+//      iteration).  Otherwise sign the frontier nodes from the labels of level
+//      j-1, group them by exact signature, look each group's signature up in
+//      S_j (inserting it with a new label when absent), and give the nodes
+//      their labels.  The frontier of level j+1 is the update's sources, the
+//      nodes whose level-j label changed (their own first component changed)
+//      and the parents of those nodes;
+//   4. every level's canonical identifiers (blocks ranked by their smallest
+//      node id) are formed from the labels.
+// The result equals a full recomputation (Theorem 2); the tests check it
+// against the oracle after every batch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kbisim_internal.cuh"
+
+namespace kb {
+namespace {
+
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+constexpr int kThreads = 256;
+constexpr uint64_t kFrontierFloor = 4096;  // frontiers this small never switch back
+
+template <typename T>
+T* ptr(const Buf& b) {
+  return static_cast<T*>(b.p);
+}
+
+unsigned grid_for(const Store& s, uint64_t n, int per) {
+  const uint64_t g = (n + per - 1) / per;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)s.sms * 16));
+}
+
+#define GRID_STRIDE(i, n) \
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); i += (uint64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ bool bit(const uint32_t* m, uint64_t i) { return (m[i >> 5] >> (i & 31)) & 1u; }
+__device__ __forceinline__ void set_bit(uint32_t* m, uint64_t i) { atomicOr(&m[i >> 5], 1u << (i & 31)); }
+
+// Home slot of a signature hash in a table of mask + 1 slots.
+__device__ __forceinline__ uint64_t home_slot(uint64_t h, uint64_t mask) { return mix64(h ^ 0x6a09e667f3bcc909ull) & mask; }
+
+// --- labels -----------------------------------------------------------------
+// Level 0 labels: the node label of every alive node, original order.
+__global__ void k_lab0(uint64_t n, uint64_t n_alive, const uint32_t* o2p, const uint32_t* nlabel, uint32_t* lab) {
+  GRID_STRIDE(o, n) {
+    const uint32_t p = o2p[o];
+    lab[o] = p < n_alive ? nlabel[p] : kDead;
+  }
+}
+
+// Labels from a canonical level (internal order), original order.
+__global__ void k_lab_from_level(uint64_t n, const uint32_t* o2p, const uint32_t* level, uint32_t* lab) {
+  GRID_STRIDE(o, n) lab[o] = level[o2p[o]];
+}
+
+// Original-order labels to internal order.
+__global__ void k_to_internal(uint64_t n, const uint32_t* p2o, const uint32_t* lab, uint32_t* out) {
+  GRID_STRIDE(p, n) out[p] = lab[p2o[p]];
+}
+
+// Smallest original id and member count of every label (labels < lcap).
+__global__ void k_label_heads(uint64_t n, const uint32_t* lab, uint32_t* minid, uint32_t* cnt) {
+  GRID_STRIDE(o, n) {
+    const uint32_t b = lab[o];
+    if (b == kDead) continue;
+    atomicMin(&minid[b], (uint32_t)o);
+    if (cnt) atomicAdd(&cnt[b], 1u);
+  }
+}
+
+// Head bitmap over original ids: o is the smallest node of its label.
+__global__ void k_label_head_bits(uint64_t n, const uint32_t* lab, const uint32_t* minid, uint32_t* hbits) {
+  GRID_STRIDE(o, n) {
+    const uint32_t b = lab[o];
+    if (b != kDead && minid[b] == (uint32_t)o) set_bit(hbits, o);
+  }
+}
+
+__global__ void k_word_popc(const uint32_t* bits, uint64_t words, uint64_t* out) {
+  GRID_STRIDE(w, words) out[w] = __popc(bits[w]);
+}
+
+// Canonical identifier of every node (internal order): the rank of its
+// label's head among all heads; alone flags (label with one member).
+__global__ void k_label_pid(uint64_t n, uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab,
+                            const uint32_t* minid, const uint32_t* cnt, const uint32_t* hbits, const uint64_t* hword,
+                            uint32_t* pid, uint8_t* alone, unsigned long long* n_alone) {
+  unsigned int na = 0;
+  GRID_STRIDE(p, n) {
+    if (p >= n_alive) {
+      pid[p] = kDead;
+      if (alone) alone[p] = 0;
+      continue;
+    }
+    const uint32_t b = lab[p2o[p]];
+    const uint32_t h = minid[b];
+    const uint32_t w = h >> 5;
+    pid[p] = (uint32_t)hword[w] + (uint32_t)__popc(hbits[w] & ((1u << (h & 31)) - 1u));
+    if (alone) {
+      const bool al = cnt[b] == 1u;
+      alone[p] = al ? 1 : 0;
+      na += al ? 1u : 0u;
+    }
+  }
+  if (alone) {
+    na = __reduce_add_sync(kFullMask, na);
+    if ((threadIdx.x & 31) == 0 && na) atomicAdd(n_alone, (unsigned long long)na);
+  }
+}
+
+// --- the signature store ----------------------------------------------------
+struct StoreArgs {
+  unsigned long long* tkey;
+  uint32_t* tval;
+  uint64_t tmask;
+  uint32_t* sfirst;
+  uint32_t* scount;
+  unsigned long long* soff;
+  unsigned long long* pool;
+  unsigned long long* ctr;  // [0] labels handed out, [1] pool words used
+  uint64_t lcap, pcap;
+  uint32_t* err;            // bit 1: a capacity was exceeded
+};
+
+struct NodeSig {
+  const uint64_t* off;      // CSR offsets (internal ids)
+  const uint64_t* sigkey;   // element words of each node at its CSR offset
+  const uint32_t* ucnt;
+  const uint64_t* hash;
+  const uint32_t* prev;     // labels of the level below, internal order (first component)
+};
+
+// Claim a table slot for hash h and label b (the signature is already stored).
+__device__ bool store_slot(const StoreArgs& a, uint64_t h, uint32_t b) {
+  uint64_t s = home_slot(h, a.tmask);
+  for (uint64_t t = 0; t <= a.tmask; ++t) {
+    if (atomicCAS(&a.tkey[s], kEmpty64, (unsigned long long)h) == kEmpty64) {
+      a.tval[s] = b;
+      return true;
+    }
+    s = (s + 1) & a.tmask;
+  }
+  return false;
+}
+
+// The warp stores node p's signature under label b (all lanes take part).
+__device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p, uint32_t b) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t U = g.ucnt[p];
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&a.ctr[1], (unsigned long long)U);
+  base = __shfl_sync(kFullMask, base, 0);
+  if (base + U > a.pcap || b >= a.lcap) {
+    if (lane == 0) atomicOr(a.err, 1u);
+    return;
+  }
+  const uint64_t* src = g.sigkey + g.off[p];
+  for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
+  if (lane == 0) {
+    a.sfirst[b] = g.prev[p];
+    a.scount[b] = U;
+    a.soff[b] = base;
+  }
+  __threadfence();  // the signature is visible before its slot names it
+  __syncwarp();
+  if (lane == 0 && !store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
+}
+
+// Build: the heads of every label (smallest original id) store their
+// signatures under their canonical id.  One warp per node.
+__global__ void k_store_heads(StoreArgs a, NodeSig g, uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab,
+                              const uint32_t* minid) {
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; p < n_alive; p += warps) {
+    const uint32_t o = p2o[p];
+    const uint32_t b = lab[o];
+    if (minid[b] != o) continue;
+    store_signature(a, g, p, b);
+  }
+}
+
+// Words the heads' signatures take (the pool's size at build).
+__global__ void k_head_words(uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab, const uint32_t* minid,
+                             const uint32_t* ucnt, unsigned long long* total) {
+  unsigned long long w = 0;
+  GRID_STRIDE(p, n_alive) {
+    const uint32_t o = p2o[p];
+    if (minid[lab[o]] == o) w += ucnt[p];
+  }
+  for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFullMask, w, d);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+}
+
+// Set equality of node p's elements and stored signature b (same count U <=
+// 32), by the warp: lane i holds the node's element i and checks that it is
+// among the stored ones (both lists are duplicate-free).
+__device__ bool warp_same_set(const StoreArgs& a, const NodeSig& g, uint64_t p, uint32_t b, uint32_t U) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t mine = lane < U ? g.sigkey[g.off[p] + lane] : 0ull;
+  const uint64_t stored = lane < U ? a.pool[a.soff[b] + lane] : 0ull;
+  bool found = lane >= U;
+  for (uint32_t j = 0; j < U; ++j) found |= __shfl_sync(kFullMask, stored, j) == mine;
+  return __all_sync(kFullMask, found);
+}
+
+// Look up the signature of every frontier head in S_j (one warp per head).
+// heads: (node, first slot to probe).  A stored signature with the same hash,
+// first component and count is compared here when it has at most 32 elements;
+// longer ones go to `pend` (node, label, slot) for k_long_compare.  A head
+// whose probe reaches an empty slot stores its signature under a new label.
+struct LookupArgs {
+  const uint32_t* heads;    // node ids
+  const unsigned long long* start;  // per head: slot to start at, or all ones for the home slot
+  uint64_t count;
+  uint32_t* newlab;         // per node (internal id): the label found
+  uint4* pend;              // (head index, label, slot lo, slot hi)
+  unsigned long long* n_pend;
+};
+
+__global__ void k_lookup(StoreArgs a, NodeSig g, LookupArgs l) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < l.count; i += warps) {
+    const uint32_t p = l.heads[i];
+    const uint64_t h = g.hash[p];
+    const uint32_t U = g.ucnt[p], first = g.prev[p];
+    uint64_t s = l.start && l.start[i] != kEmpty64 ? l.start[i] : home_slot(h, a.tmask);
+    bool done = false;
+    for (uint64_t t = 0; t <= a.tmask && !done; ++t, s = (s + 1) & a.tmask) {
+      const unsigned long long key = *(volatile unsigned long long*)&a.tkey[s];
+      if (key == kEmpty64) break;
+      if (key != h) continue;
+      const uint32_t b = *(volatile uint32_t*)&a.tval[s];
+      if (b == kNone32) continue;  // being written by another head: another signature
+      if (a.sfirst[b] != first || a.scount[b] != U) continue;
+      if (U > 32) {
+        if (lane == 0) {
+          const unsigned long long q = atomicAdd(l.n_pend, 1ull);
+          l.pend[q] = make_uint4((uint32_t)i, b, (uint32_t)s, (uint32_t)(s >> 32));
+        }
+        done = true;
+        break;
+      }
+      if (warp_same_set(a, g, p, b, U)) {
+        if (lane == 0) l.newlab[p] = b;
+        done = true;
+      }
+    }
+    if (done) continue;
+    // not in S_j: a new label
+    uint32_t b = 0;
+    if (lane == 0) b = (uint32_t)atomicAdd(&a.ctr[0], 1ull);
+    b = __shfl_sync(kFullMask, b, 0);
+    store_signature(a, g, p, b);
+    if (lane == 0) l.newlab[p] = b;
+  }
+}
+
+// One CTA per pending (head, label): equal sets iff every element of the
+// head is among the label's stored elements (equal counts, both duplicate
+// free).  The stored elements go into a shared-memory set chunk by chunk.
+constexpr int kCmpThreads = 256, kCmpChunk = 4096, kCmpSlots = 2 * kCmpChunk;
+
+__global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeSig g, LookupArgs l,
+                                                               uint64_t n_pend, uint32_t* match) {
+  __shared__ unsigned long long set[kCmpSlots];
+  __shared__ unsigned int found_sh;
+  for (uint64_t q = blockIdx.x; q < n_pend; q += gridDim.x) {
+    const uint4 e = l.pend[q];
+    const uint32_t p = l.heads[e.x], b = e.y;
+    const uint32_t U = g.ucnt[p];
+    const uint64_t* mine = g.sigkey + g.off[p];
+    const unsigned long long* stored = a.pool + a.soff[b];
+    uint32_t found = 0;
+    for (uint32_t c0 = 0; c0 < U; c0 += kCmpChunk) {
+      const uint32_t cn = min((uint32_t)kCmpChunk, U - c0);
+      for (int i = threadIdx.x; i < kCmpSlots; i += kCmpThreads) set[i] = kEmpty64;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < cn; i += kCmpThreads) {
+        const unsigned long long k = stored[c0 + i];
+        uint32_t s = (uint32_t)(mix64(k) & (kCmpSlots - 1));
+        for (int t = 0; t < kCmpSlots; ++t) {  // a chunk fills at most half the set
+          const unsigned long long old = atomicCAS(&set[s], kEmpty64, k);
+          if (old == kEmpty64 || old == k) break;
+          s = (s + 1) & (kCmpSlots - 1);
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < U; i += kCmpThreads) {
+        const unsigned long long k = mine[i];
+        uint32_t s = (uint32_t)(mix64(k) & (kCmpSlots - 1));
+        for (int t = 0; t < kCmpSlots; ++t) {
+          const unsigned long long cur = set[s];
+          if (cur == k) {
+            ++found;
+            break;
+          }
+          if (cur == kEmpty64) break;
+          s = (s + 1) & (kCmpSlots - 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) found_sh = 0;
+    __syncthreads();
+    found = __reduce_add_sync(kFullMask, found);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&found_sh, found);
+    __syncthreads();
+    // the element equal to the empty marker cannot sit in the set: compare it apart
+    if (threadIdx.x == 0) {
+      uint32_t extra = 0;
+      bool mine_has = false, stored_has = false;
+      for (uint32_t i = 0; i < U; ++i) {
+        mine_has |= mine[i] == kEmpty64;
+        stored_has |= stored[i] == kEmpty64;
+      }
+      if (mine_has && stored_has) extra = 1;
+      match[q] = (found_sh + extra == U) ? 1u : 0u;
+    }
+    __syncthreads();
+  }
+}
+
+// After a long compare: matched heads take the label, the others probe on
+// from the next slot (a new pending list for k_lookup).
+__global__ void k_resolve(LookupArgs l, uint64_t n_pend, const uint32_t* match, uint32_t* retry_heads,
+                          unsigned long long* retry_start, unsigned long long* n_retry, uint64_t tmask) {
+  GRID_STRIDE(q, n_pend) {
+    const uint4 e = l.pend[q];
+    const uint32_t p = l.heads[e.x];
+    if (match[q]) {
+      l.newlab[p] = e.y;
+    } else {
+      const unsigned long long r = atomicAdd(n_retry, 1ull);
+      retry_heads[r] = p;
+      retry_start[r] = ((((uint64_t)e.w << 32) | e.z) + 1) & tmask;
+    }
+  }
+}
+
+// --- frontier -----------------------------------------------------------------
+// List of the set bits of a bitmap over internal ids (order free).
+__global__ void k_bits_to_list(const uint32_t* bits, uint64_t words, uint64_t n, uint32_t* list,
+                               unsigned long long* count) {
+  GRID_STRIDE(w, words) {
+    uint32_t m = bits[w];
+    if (!m) continue;
+    const unsigned long long base = atomicAdd(count, (unsigned long long)__popc(m));
+    uint32_t k = 0;
+    while (m) {
+      const uint32_t b = __ffs(m) - 1;
+      m &= m - 1;
+      const uint64_t p = (w << 5) + b;
+      if (p < n) list[base + k] = (uint32_t)p;
+      ++k;
+    }
+  }
+}
+
+// Sources of the batch's edges (original ids) and the new nodes into the
+// seed bitmap (internal ids).
+__global__ void k_seed_sources(uint64_t k, const uint32_t* src, const uint32_t* o2p, uint32_t* seeds) {
+  GRID_STRIDE(i, k) set_bit(seeds, o2p[src[i]]);
+}
+__global__ void k_seed_new(uint64_t n0, uint64_t n1, const uint32_t* o2p, uint32_t* seeds) {
+  GRID_STRIDE(o, n1 - n0) set_bit(seeds, o2p[n0 + o]);
+}
+
+// Labels of level j for the frontier: a head's new label goes to every node
+// of its group; nodes whose label changed are marked.
+__global__ void k_assign(const uint32_t* list, uint64_t count, const uint32_t* rep, const uint32_t* newlab,
+                         const uint32_t* p2o, uint32_t* lab, uint32_t* changed) {
+  GRID_STRIDE(i, count) {
+    const uint32_t p = list[i];
+    const uint32_t b = newlab[rep[p]];
+    const uint32_t o = p2o[p];
+    if (lab[o] != b) {
+      lab[o] = b;
+      set_bit(changed, p);
+    }
+  }
+}
+
+// Next frontier: seeds | changed | parents of changed nodes.  Out-degree <=
+// 64: one thread per node; larger: one warp per node.
+__global__ void k_frontier_small(uint64_t n_small, const uint64_t* off, const uint32_t* dst, const uint32_t* changed,
+                                 uint32_t* next) {
+  GRID_STRIDE(p, n_small) {
+    bool hit = false;
+    for (uint64_t e = off[p]; e < off[p + 1] && !hit; ++e) hit = bit(changed, dst[e]);
+    if (hit) set_bit(next, p);
+  }
+}
+__global__ void k_frontier_large(uint64_t p0, uint64_t p1, const uint64_t* off, const uint32_t* dst,
+                                 const uint32_t* changed, uint32_t* next) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t p = p0 + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); p < p1; p += warps) {
+    bool hit = false;
+    for (uint64_t e = off[p] + lane; e < off[p + 1]; e += 32) {
+      hit |= bit(changed, dst[e]);
+      if (__any_sync(kFullMask, hit)) break;
+    }
+    if (__any_sync(kFullMask, hit) && lane == 0) set_bit(next, p);
+  }
+}
+__global__ void k_or3(uint64_t words, const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  GRID_STRIDE(w, words) out[w] |= a[w] | b[w];
+}
+__global__ void k_popc_sum(const uint32_t* bits, uint64_t words, unsigned long long* total) {
+  unsigned long long c = 0;
+  GRID_STRIDE(w, words) c += __popc(bits[w]);
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFullMask, c, d);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
+}
+
+// Labels of added nodes: their node label at level 0, "none" above (a new
+// node is always in the frontier, so it gets a label at every level).
+__global__ void k_lab_grow(uint64_t n0, uint64_t n1, const uint32_t* o2p, const uint32_t* nlabel, int level0,
+                           uint32_t* lab) {
+  GRID_STRIDE(i, n1 - n0) lab[n0 + i] = level0 ? nlabel[o2p[n0 + i]] : kNone32;
+}
+
+// --- host ---------------------------------------------------------------------
+Status sync_read(Store& s, void* dst, const void* src, size_t bytes, const char* what) {
+  Status st = cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s.stream), what);
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), what);
+  return st;
+}
+
+// Grow b to at least `bytes`, keeping its first `keep` bytes.
+Status grow_keep(Store& s, Buf& b, size_t bytes, size_t keep) {
+  if (bytes <= b.cap && b.p) return Status::Ok();
+  Buf nb;
+  Status st = ensure(s, nb, bytes);
+  if (!st.ok()) return st;
+  if (keep && b.p)
+    st = cuda_check(cudaMemcpyAsync(nb.p, b.p, std::min(keep, b.cap), cudaMemcpyDeviceToDevice, s.stream), "grow");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "grow");
+  release(s, b);
+  b = nb;
+  return st;
+}
+
+uint64_t pow2_at_least(uint64_t v) {
+  uint64_t c = 1024;
+  while (c < v) c <<= 1;
+  return c;
+}
+
+StoreArgs store_args(Store& s, MaintLevel& L) {
+  StoreArgs a;
+  a.tkey = ptr<unsigned long long>(L.tkey);
+  a.tval = ptr<uint32_t>(L.tval);
+  a.tmask = L.tcap - 1;
+  a.sfirst = ptr<uint32_t>(L.sfirst);
+  a.scount = ptr<uint32_t>(L.scount);
+  a.soff = ptr<unsigned long long>(L.soff);
+  a.pool = ptr<unsigned long long>(L.pool);
+  a.ctr = ptr<unsigned long long>(L.ctr);
+  a.lcap = L.lcap;
+  a.pcap = L.pcap;
+  a.err = ptr<uint32_t>(s.d_err);
+  return a;
+}
+
+NodeSig node_sig(Store& s) {
+  NodeSig g;
+  g.off = ptr<uint64_t>(s.offsets);
+  g.sigkey = ptr<uint64_t>(s.sigkey);
+  g.ucnt = ptr<uint32_t>(s.ucnt);
+  g.hash = ptr<uint64_t>(s.hash);
+  g.prev = ptr<uint32_t>(s.mt.prev_int);
+  return g;
+}
+
+Status ensure_common(Store& s) {
+  MaintState& m = s.mt;
+  const uint64_t n = std::max<uint64_t>(s.n, 1), words = (n + 31) / 32 + 1;
+  Status st;
+  Buf* bits[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds};
+  for (Buf* b : bits)
+    if (!(st = ensure(s, *b, words * 4)).ok()) return st;
+  if (!(st = ensure(s, m.list, n * 4)).ok()) return st;
+  if (!(st = ensure(s, m.prev_int, n * 4)).ok()) return st;
+  if (!(st = ensure(s, m.newlab, n * 4)).ok()) return st;
+  if (!(st = ensure(s, m.misc, 16 * 8)).ok()) return st;
+  return Status::Ok();
+}
+
+// Canonical identifiers of level j (internal order) from its labels; the
+// number of blocks; alone flags when `alone` is set.
+Status canonical_from_labels(Store& s, uint32_t j, uint32_t* pid, uint64_t* blocks, bool alone) {
+  MaintState& m = s.mt;
+  MaintLevel& L = m.lv[j];
+  const uint64_t n = s.n, words = n / 32 + 1;
+  Status st;
+  if (!(st = ensure(s, m.minid, L.lcap * 4)).ok()) return st;
+  if (!(st = ensure(s, m.cnt, L.lcap * 4)).ok()) return st;
+  if (!(st = ensure(s, s.hbits, words * 4 + 16)).ok()) return st;
+  if (!(st = ensure(s, s.hword, words * 8)).ok()) return st;
+  cudaMemsetAsync(m.minid.p, 0xFF, L.lcap * 4, s.stream);
+  cudaMemsetAsync(m.cnt.p, 0, L.lcap * 4, s.stream);
+  cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
+  unsigned long long* sc = ptr<unsigned long long>(m.misc);
+  cudaMemsetAsync(sc + 4, 0, 8, s.stream);
+  const uint32_t* lab = ptr<uint32_t>(L.lab);
+  k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, lab, ptr<uint32_t>(m.minid),
+                                                                      ptr<uint32_t>(m.cnt));
+  k_label_head_bits<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, lab, ptr<uint32_t>(m.minid),
+                                                                          ptr<uint32_t>(s.hbits));
+  k_word_popc<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(s.hbits), words,
+                                                                        ptr<uint64_t>(s.hword));
+  if (!(st = cuda_check(cudaGetLastError(), "canonical ids")).ok()) return st;
+  if (!(st = scan_u64(s, ptr<uint64_t>(s.hword), words)).ok()) return st;
+  k_label_pid<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(
+      n, s.n_alive, ptr<uint32_t>(s.p2o), lab, ptr<uint32_t>(m.minid), ptr<uint32_t>(m.cnt), ptr<uint32_t>(s.hbits),
+      ptr<uint64_t>(s.hword), pid, alone ? ptr<uint8_t>(s.alone) : nullptr, sc + 4);
+  if (!(st = cuda_check(cudaGetLastError(), "canonical ids")).ok()) return st;
+  uint64_t tail[2] = {0, 0};
+  // blocks = heads before the spare word past the last node
+  if (!(st = sync_read(s, tail, ptr<uint64_t>(s.hword) + (words - 1), 8, "block count")).ok()) return st;
+  uint32_t lastw = 0;
+  if (!(st = sync_read(s, &lastw, ptr<uint32_t>(s.hbits) + (words - 1), 4, "block count")).ok()) return st;
+  *blocks = tail[0] + (uint64_t)__builtin_popcount(lastw);
+  if (alone && !(st = sync_read(s, &s.n_alone, sc + 4, 8, "alone")).ok()) return st;
+  return Status::Ok();
+}
+
+// S_j for level j from the current labels of levels j-1 and j (canonical at
+// build time): every label's head stores its signature.
+Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
+  MaintState& m = s.mt;
+  MaintLevel& L = m.lv[j];
+  const uint64_t n = s.n, na = s.n_alive;
+  Status st;
+  k_to_internal<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o),
+                                                                      ptr<uint32_t>(m.lv[j - 1].lab),
+                                                                      ptr<uint32_t>(m.prev_int));
+  if (!(st = masked_signatures(s, ptr<uint32_t>(m.prev_int), nullptr)).ok()) return st;
+  L.lcap = pow2_at_least(2 * labels + 1024);
+  if (!(st = ensure(s, m.minid, L.lcap * 4)).ok()) return st;
+  cudaMemsetAsync(m.minid.p, 0xFF, L.lcap * 4, s.stream);
+  k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(L.lab), ptr<uint32_t>(m.minid),
+                                                                      nullptr);
+  unsigned long long* sc = ptr<unsigned long long>(m.misc);
+  cudaMemsetAsync(sc, 0, 8, s.stream);
+  k_head_words<<<grid_for(s, na, kThreads), kThreads, 0, s.stream>>>(na, ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
+                                                                      ptr<uint32_t>(m.minid), ptr<uint32_t>(s.ucnt), sc);
+  uint64_t words = 0;
+  if (!(st = sync_read(s, &words, sc, 8, "store size")).ok()) return st;
+  L.pcap = words + words / 2 + (1u << 20);
+  L.tcap = pow2_at_least(2 * L.lcap);
+  if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
+  if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
+  if (!(st = ensure(s, L.sfirst, L.lcap * 4)).ok()) return st;
+  if (!(st = ensure(s, L.scount, L.lcap * 4)).ok()) return st;
+  if (!(st = ensure(s, L.soff, L.lcap * 8)).ok()) return st;
+  if (!(st = ensure(s, L.pool, L.pcap * 8)).ok()) return st;
+  if (!(st = ensure(s, L.ctr, 16)).ok()) return st;
+  cudaMemsetAsync(L.tkey.p, 0xFF, L.tcap * 8, s.stream);
+  cudaMemsetAsync(L.tval.p, 0xFF, L.tcap * 4, s.stream);
+  uint64_t c0[2] = {labels, 0};
+  if (!(st = cuda_check(cudaMemcpyAsync(L.ctr.p, c0, 16, cudaMemcpyHostToDevice, s.stream), "store")).ok()) return st;
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  k_store_heads<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(store_args(s, L), node_sig(s), na,
+                                                                ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
+                                                                ptr<uint32_t>(m.minid));
+  uint32_t e = 0;
+  if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
+  if (!(st = sync_read(s, &e, s.d_err.p, 4, "store heads")).ok()) return st;
+  if (e & 1u) return Status::Err(KBISIM_ERR_TIMEOUT, "signature store capacity exceeded at build");
+  return Status::Ok();
+}
+
+// Heads of the frontier groups (rep[p] == p), listed.
+__global__ void k_group_heads(const uint32_t* list, uint64_t count, const uint32_t* rep, uint32_t* heads,
+                              unsigned long long* n) {
+  GRID_STRIDE(i, count) {
+    const uint32_t p = list[i];
+    if (rep[p] == p) heads[atomicAdd(n, 1ull)] = p;
+  }
+}
+
+// One level of an update: the frontier (fmask) gets its labels of level j.
+// Returns false in *fits when a store capacity ran out (the caller recomputes).
+Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
+  MaintState& m = s.mt;
+  MaintLevel& L = m.lv[j];
+  Status st;
+  *fits = true;
+  uint32_t* list = ptr<uint32_t>(m.list);
+  if (!(st = masked_signatures(s, ptr<uint32_t>(m.prev_int), ptr<uint32_t>(m.fmask))).ok()) return st;
+  if (!(st = group_list(s, list, count, ptr<uint32_t>(m.prev_int))).ok()) return st;
+  // heads of the frontier groups (rep[p] == p) look up S_j; scratch of the
+  // lookup: pending long compares, restart slots, results, heads, retries
+  const size_t cnt = std::max<uint64_t>(count, 1);
+  if (!(st = ensure(s, m.pend, cnt * (sizeof(uint4) + 8 + 4 + 4 + 4))).ok()) return st;
+  uint4* pend = ptr<uint4>(m.pend);
+  unsigned long long* start = reinterpret_cast<unsigned long long*>(pend + cnt);
+  uint32_t* match = reinterpret_cast<uint32_t*>(start + cnt);
+  uint32_t* heads = match + cnt;
+  uint32_t* retry = heads + cnt;
+  unsigned long long* sc = ptr<unsigned long long>(m.misc);
+  cudaMemsetAsync(sc, 0, 32, s.stream);
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  k_group_heads<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep), heads, sc);
+  uint64_t nheads = 0;
+  if (!(st = cuda_check(cudaGetLastError(), "group heads")).ok()) return st;
+  if (!(st = sync_read(s, &nheads, sc, 8, "group heads")).ok()) return st;
+  LookupArgs la;
+  la.heads = heads;
+  la.start = nullptr;
+  la.count = nheads;
+  la.newlab = ptr<uint32_t>(m.newlab);
+  la.pend = pend;
+  la.n_pend = sc + 1;
+  const StoreArgs sa = store_args(s, L);
+  const NodeSig ns = node_sig(s);
+  for (int pass = 0; la.count; ++pass) {
+    if (pass > 64) return Status::Err(KBISIM_ERR_TIMEOUT, "signature lookup made no progress");
+    cudaMemsetAsync(sc + 1, 0, 16, s.stream);
+    k_lookup<<<(unsigned)std::min<uint64_t>((la.count + 7) / 8, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(sa, ns,
+                                                                                                            la);
+    uint64_t np = 0;
+    if (!(st = cuda_check(cudaGetLastError(), "lookup")).ok()) return st;
+    if (!(st = sync_read(s, &np, sc + 1, 8, "lookup")).ok()) return st;
+    if (!np) break;
+    k_long_compare<<<(unsigned)std::min<uint64_t>(np, (uint64_t)s.sms * 4), kCmpThreads, 0, s.stream>>>(sa, ns, la, np,
+                                                                                                      match);
+    k_resolve<<<grid_for(s, np, kThreads), kThreads, 0, s.stream>>>(la, np, match, retry, start, sc + 2, L.tcap - 1);
+    uint64_t nr = 0;
+    if (!(st = cuda_check(cudaGetLastError(), "long compare")).ok()) return st;
+    if (!(st = sync_read(s, &nr, sc + 2, 8, "long compare")).ok()) return st;
+    // the heads still unmatched probe on from their next slot
+    if (nr) {
+      cudaMemcpyAsync(heads, retry, nr * 4, cudaMemcpyDeviceToDevice, s.stream);
+    }
+    la.start = start;
+    la.count = nr;
+  }
+  uint32_t e = 0;
+  if (!(st = sync_read(s, &e, s.d_err.p, 4, "store")).ok()) return st;
+  if (e & 1u) {
+    *fits = false;
+    return Status::Ok();
+  }
+  const uint64_t words = s.n / 32 + 1;
+  cudaMemsetAsync(m.changed.p, 0, words * 4, s.stream);
+  k_assign<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep),
+                                                                    ptr<uint32_t>(m.newlab), ptr<uint32_t>(s.p2o),
+                                                                    ptr<uint32_t>(L.lab), ptr<uint32_t>(m.changed));
+  return cuda_check(cudaGetLastError(), "assign labels");
+}
+
+}  // namespace
+
+void maint_release(Store& s) {
+  MaintState& m = s.mt;
+  for (MaintLevel& L : m.lv) {
+    Buf* b[] = {&L.lab, &L.tkey, &L.tval, &L.sfirst, &L.scount, &L.soff, &L.pool, &L.ctr};
+    for (Buf* x : b) release(s, *x);
+  }
+  m.lv.clear();
+  Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
+              &m.minid, &m.cnt, &m.src, &m.misc};
+  for (Buf* x : b) release(s, *x);
+  m.valid = false;
+  m.k = 0;
+}
+
+Status maint_build(Store& s, uint32_t k) {
+  MaintState& m = s.mt;
+  m.valid = false;
+  if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
+  Status st;
+  if (!(st = ensure_common(s)).ok()) return st;
+  m.lv.resize(k + 1);
+  const uint64_t n = s.n;
+  for (uint32_t j = 0; j <= k; ++j)
+    if (!(st = ensure(s, m.lv[j].lab, std::max<uint64_t>(n, 1) * 4)).ok()) return st;
+  k_lab0<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, s.n_alive, ptr<uint32_t>(s.o2p),
+                                                              ptr<uint32_t>(s.nlabel), ptr<uint32_t>(m.lv[0].lab));
+  for (uint32_t j = 1; j <= k; ++j) {
+    const uint32_t l = std::min(j, s.computed);
+    k_lab_from_level<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(s.o2p),
+                                                                          ptr<uint32_t>(s.level[l]),
+                                                                          ptr<uint32_t>(m.lv[j].lab));
+    if (!(st = build_level_store(s, j, s.counts[l])).ok()) return st;
+  }
+  m.k = k;
+  m.valid = true;
+  return Status::Ok();
+}
+
+Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missing, bool* done) {
+  MaintState& m = s.mt;
+  *done = false;
+  if (!m.valid || k > m.k || !b || b->n_del_nodes) return Status::Ok();
+  Status st;
+  // the batch's edge sources, staged before the graph changes (original ids)
+  const uint64_t ns = b->n_ins + b->n_del;
+  if (!(st = ensure(s, m.src, std::max<uint64_t>(ns, 1) * 4)).ok()) return st;
+  const cudaMemcpyKind kind = b->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (b->n_ins && !(st = cuda_check(cudaMemcpyAsync(m.src.p, b->ins_src, b->n_ins * 4, kind, s.stream), "stage")).ok())
+    return st;
+  if (b->n_del && !(st = cuda_check(cudaMemcpyAsync(ptr<uint32_t>(m.src) + b->n_ins, b->del_src, b->n_del * 4, kind,
+                                                    s.stream), "stage")).ok())
+    return st;
+  const uint64_t n0 = s.n;
+  if (!(st = apply_batch(s, b, missing)).ok()) return st;
+  *done = true;  // from here on the graph is the updated one
+  m.incremental = 0;
+  m.frontier_nodes = 0;
+  m.levels = 0;
+  const uint64_t n = s.n, words = n / 32 + 1;
+  if (!(st = ensure_common(s)).ok()) return st;
+  // labels of added nodes
+  for (uint32_t j = 0; j <= m.k; ++j) {
+    if (!(st = grow_keep(s, m.lv[j].lab, std::max<uint64_t>(n, 1) * 4, n0 * 4)).ok()) return st;
+    if (n > n0)
+      k_lab_grow<<<grid_for(s, n - n0, kThreads), kThreads, 0, s.stream>>>(n0, n, ptr<uint32_t>(s.o2p),
+                                                                           ptr<uint32_t>(s.nlabel), j == 0,
+                                                                           ptr<uint32_t>(m.lv[j].lab));
+  }
+  // seeds: sources of the batch's edges and the new nodes
+  cudaMemsetAsync(m.seeds.p, 0, words * 4, s.stream);
+  if (ns) k_seed_sources<<<grid_for(s, ns, kThreads), kThreads, 0, s.stream>>>(ns, ptr<uint32_t>(m.src),
+                                                                               ptr<uint32_t>(s.o2p),
+                                                                               ptr<uint32_t>(m.seeds));
+  if (n > n0) k_seed_new<<<grid_for(s, n - n0, kThreads), kThreads, 0, s.stream>>>(n0, n, ptr<uint32_t>(s.o2p),
+                                                                                  ptr<uint32_t>(m.seeds));
+  cudaMemcpyAsync(m.fmask.p, m.seeds.p, words * 4, cudaMemcpyDeviceToDevice, s.stream);
+  k_to_internal<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o),
+                                                                      ptr<uint32_t>(m.lv[0].lab),
+                                                                      ptr<uint32_t>(m.prev_int));
+  if (!(st = cuda_check(cudaGetLastError(), "seeds")).ok()) return st;
+  unsigned long long* sc = ptr<unsigned long long>(m.misc);
+  bool fits = true;
+  uint64_t nodes = 0;
+  for (uint32_t j = 1; j <= m.k && fits; ++j) {
+    // frontier of level j: count, switch back when large, list
+    cudaMemsetAsync(sc + 8, 0, 16, s.stream);
+    k_popc_sum<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.fmask), words, sc + 8);
+    uint64_t count = 0;
+    if (!(st = cuda_check(cudaGetLastError(), "frontier")).ok()) return st;
+    if (!(st = sync_read(s, &count, sc + 8, 8, "frontier")).ok()) return st;
+    if (count > kFrontierFloor && (double)count > s.maint_frontier_max * (double)std::max<uint64_t>(s.n_alive, 1)) {
+      fits = false;
+      m.reason = KBISIM_MAINT_FRONTIER;
+      break;
+    }
+    nodes += count;
+    if (count) {
+      k_bits_to_list<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.fmask), words, n,
+                                                                              ptr<uint32_t>(m.list), sc + 9);
+      if (!(st = cuda_check(cudaGetLastError(), "frontier list")).ok()) return st;
+      if (!(st = update_level(s, j, count, &fits)).ok()) return st;
+      if (!fits) {
+        m.reason = KBISIM_MAINT_CAPACITY;
+        break;
+      }
+    } else {
+      cudaMemsetAsync(m.changed.p, 0, words * 4, s.stream);
+    }
+    if (j == m.k) break;
+    // next frontier: seeds | changed | parents of changed
+    cudaMemsetAsync(m.fnext.p, 0, words * 4, s.stream);
+    const uint64_t n_small = s.class_start[kClassWarp];
+    if (n_small)
+      k_frontier_small<<<grid_for(s, n_small, kThreads), kThreads, 0, s.stream>>>(
+          n_small, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
+    if (s.n_alive > n_small)
+      k_frontier_large<<<(unsigned)s.sms * 16, kThreads, 0, s.stream>>>(n_small, s.n_alive, ptr<uint64_t>(s.offsets),
+                                                                       ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
+                                                                       ptr<uint32_t>(m.fnext));
+    k_or3<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(words, ptr<uint32_t>(m.seeds),
+                                                                    ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
+    std::swap(m.fmask, m.fnext);
+    k_to_internal<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o),
+                                                                        ptr<uint32_t>(m.lv[j].lab),
+                                                                        ptr<uint32_t>(m.prev_int));
+    if (!(st = cuda_check(cudaGetLastError(), "next frontier")).ok()) return st;
+  }
+  if (!fits) {
+    // switch back: the caller recomputes every level and rebuilds the state
+    m.valid = false;
+    return Status::Ok();
+  }
+  m.frontier_nodes = nodes;
+  m.levels = m.k;
+  m.incremental = 1;
+  m.reason = 0;
+  // canonical identifiers of levels 0..k: level 0 by its own grouping, the
+  // others from their labels; rounds and early stop as a full computation
+  // decides them
+  if (s.level.size() < (size_t)m.k + 1) s.level.resize(m.k + 1);
+  for (uint32_t j = 0; j <= m.k; ++j)
+    if (!(st = ensure(s, s.level[j], std::max<uint64_t>(n, 1) * 4)).ok()) return st;
+  if (s.counts.size() < (size_t)m.k + 1) s.counts.resize(m.k + 1, 0);
+  if (!(st = compute_level0(s)).ok()) return st;
+  uint32_t rounds = k;
+  for (uint32_t j = 1; j <= k; ++j) {
+    uint64_t blocks = 0;
+    if (!(st = canonical_from_labels(s, j, ptr<uint32_t>(s.level[j]), &blocks, false)).ok()) return st;
+    s.counts[j] = blocks;
+    if (s.early_stop && blocks == s.counts[j - 1]) {
+      rounds = j;
+      break;
+    }
+  }
+  if (k == 0) rounds = 0;
+  if (rounds > 0) {  // alone flags of the last computed level (level 0 has its own)
+    uint64_t blocks = 0;
+    if (!(st = canonical_from_labels(s, rounds, ptr<uint32_t>(s.level[rounds]), &blocks, true)).ok()) return st;
+  }
+  s.computed = rounds;
+  s.rounds_run = rounds;
+  s.stable = rounds > 0 && s.counts[rounds] == s.counts[rounds - 1];
+  s.stats.assign(rounds, kbisim_round_stats());
+  for (uint32_t r = 1; r <= rounds; ++r) s.stats[r - 1].blocks = s.counts[r];
+  s.has_levels = true;
+  return cuda_check(cudaStreamSynchronize(s.stream), "maintenance");
+}
+
+}  // namespace kb

@@ -297,7 +297,13 @@ struct SigArgs {
   uint64_t mask;
   int pbits;          // bits of a child identifier in a 32-bit key
   uint32_t* err;
+  const uint32_t* fmask;  // bitmap over internal ids of the nodes to sign (NULL = all)
 };
+
+// The node is to be signed this pass (every node unless a frontier mask is set).
+__device__ __forceinline__ bool in_mask(const SigArgs& a, uint64_t p) {
+  return !a.fmask || ((a.fmask[p >> 5] >> (p & 31)) & 1u);
+}
 
 constexpr int kLoadBatch = 16;  // edges whose loads a thread-per-node kernel issues together
 
@@ -342,6 +348,7 @@ __device__ __forceinline__ void edge_key_batches(const SigArgs& a, uint64_t off,
 // same key, so no shuffles, sorting or shared memory are needed.
 template <int S, typename LabelT, typename K>
 __device__ __forceinline__ void sig_thread_node(const SigArgs& a, uint64_t p, const Policies& pol) {
+  if (!in_mask(a, p)) return;
   const uint64_t off = a.off[p];
   const uint32_t d = (uint32_t)(a.off[p + 1] - off);
   K k[S];
@@ -378,6 +385,7 @@ __device__ __forceinline__ void sig_warp_staged(const SigArgs& a, uint64_t p_fir
   const uint32_t lane = threadIdx.x & 31;
   const bool valid = lane < nvalid;
   const uint64_t p = p_first + lane;
+  if (a.fmask && !__any_sync(0xFFFFFFFFu, valid && in_mask(a, p))) return;
   const uint64_t base = a.off[p_first];
   const uint64_t end = a.off[p_first + nvalid];
   const uint32_t T = (uint32_t)(end - base);  // at most 32 * S
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(kSmallThreads, small_min_blocks<LAST, K>()) k_
     break;
   switch (c) {
     case 0:
-      if (idx < L.count[c]) {
+      if (idx < L.count[c] && in_mask(a, p)) {
         a.ucnt[p] = 0;
         a.hash[p] = node_hash(0, a.prev[p], 0, a.seed, a.mask);
       }
@@ -606,6 +614,7 @@ __global__ void __launch_bounds__(NT) k_sig_chunk(SigArgs a, const uint2* chunks
   const uint64_t first = c.x;
   const uint32_t nn = c.y;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
+  if (a.fmask && !__syncthreads_or(tid < nn && in_mask(a, first + tid))) return;
   const uint64_t ebase = a.off[first];
   const uint32_t E = (uint32_t)(a.off[first + nn] - ebase);
   for (uint32_t i = tid; i <= nn; i += NT) sm.off[i] = (uint32_t)(a.off[first + i] - ebase);
@@ -731,6 +740,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
   if (h.mode[hub]) return;  // this hub's chunks run k_hub_scatter
+  if (!in_mask(a, h.first + hub)) return;
   const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
   const uint32_t E = c.w;
   const uint32_t bits = h.hub_bits[hub];
@@ -827,6 +837,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
   if (!h.mode[hub]) return;  // this hub's chunks run k_hub_chunk
+  if (!in_mask(a, h.first + hub)) return;
   const uint64_t ebase = ((uint64_t)c.z << 32) | c.y;
   const uint32_t E = c.w;
   const uint32_t bits = h.hub_bits[hub];
@@ -1890,6 +1901,61 @@ uint64_t table_capacity(uint64_t n) {
   return c;
 }
 
+// After a first insert + verify pass (scalars in h): compare the long
+// signatures, then regroup the nodes a hash collision left unresolved until
+// none is left.  The unresolved nodes hold whole classes; the smallest
+// unresolved node of each hash group heads its class, so every pass settles
+// at least one class per group (a pass that settles nothing is an error).
+Status settle_unresolved(Store& s, const GroupArgs& g, const VerifyArgs& v, bool key64, uint64_t* h, int long_cls) {
+  Status st;
+  unsigned long long* sc = ptr<unsigned long long>(s.d_scalars);
+  const int sms = sm_count(s.device);
+  const unsigned ver_grid = resident_blocks(k_group_verify, kVerNodeThreads, 0, sms);
+  const unsigned ins_grid = resident_blocks(k_group_insert, kInsThreads, 0, sms);
+  if (h[6]) {
+    TimedScope ts(s, long_cls, 1);
+    const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
+    if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g, v, h[6]);
+    else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g, v, h[6]);
+    if (!(st = launch_check("k_verify_long")).ok()) return st;
+    if (!(st = read_scalars(s, h)).ok()) return st;
+  }
+  uint64_t unresolved_n = h[1];
+  int cur = 0;
+  while (unresolved_n > 0) {
+    const uint64_t cap = table_capacity(unresolved_n);
+    GroupArgs g2 = g;
+    g2.tmask = cap - 1;
+    VerifyArgs v2 = v;
+    v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
+    v2.n_out = sc + 5;
+    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, kVerTile), ver_grid);
+    {
+      TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
+      cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
+      cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
+      k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, ins_grid),
+                       kInsThreads, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+      k_group_verify<<<b2, kVerNodeThreads, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
+    }
+    if (!(st = launch_check("collision repair")).ok()) return st;
+    if (!(st = read_scalars(s, h)).ok()) return st;
+    if (h[6]) {
+      TimedScope ts(s, KBISIM_KERNEL_OTHER, 1);
+      const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
+      if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g2, v2, h[6]);
+      else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g2, v2, h[6]);
+      if (!(st = launch_check("k_verify_long")).ok()) return st;
+      if (!(st = read_scalars(s, h)).ok()) return st;
+    }
+    if (h[5] >= unresolved_n)
+      return Status::Err(KBISIM_ERR_TIMEOUT, "collision repair made no progress");
+    unresolved_n = h[5];
+    cur ^= 1;
+  }
+  return Status::Ok();
+}
+
 // Scalars used per round (uint64 words of Store::d_scalars):
 //  [1] unresolved after the first pass, [2] key total, [3] largest signature,
 //  [4] collided nodes, [5] unresolved after a repair pass, [6] long-signature
@@ -1959,50 +2025,7 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   if (!(st = launch_check("k_group_verify")).ok()) return st;
   uint64_t h[16];
   if (!(st = read_scalars(s, h)).ok()) return st;
-  if (h[6]) {
-    TimedScope ts(s, KBISIM_KERNEL_VERIFY, 1);
-    const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
-    if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g, v, h[6]);
-    else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g, v, h[6]);
-    if (!(st = launch_check("k_verify_long")).ok()) return st;
-    if (!(st = read_scalars(s, h)).ok()) return st;
-  }
-  uint64_t unresolved_n = h[1];
-  // Collision repair: the unresolved nodes hold whole classes; the smallest
-  // unresolved node of each hash group heads its class, so every pass
-  // settles at least one class per group.
-  int cur = 0;
-  while (unresolved_n > 0) {
-    const uint64_t cap = table_capacity(unresolved_n);
-    GroupArgs g2 = g;
-    g2.tmask = cap - 1;
-    VerifyArgs v2 = v;
-    v2.out_list = ptr<uint32_t>(s.ulist[cur ^ 1]);
-    v2.n_out = sc + 5;
-    const unsigned b2 = (unsigned)std::min<uint64_t>(grid_for(unresolved_n, kVerTile), ver_grid);
-    {
-      TimedScope ts(s, KBISIM_KERNEL_OTHER, 2);
-      cudaMemsetAsync(s.table.p, 0xFF, cap * 8, s.stream);
-      cudaMemsetAsync(sc + 5, 0, 16, s.stream);  // [5] and [6]
-      k_group_insert<<<(unsigned)std::min<uint64_t>((unresolved_n + kInsChunk - 1) / kInsChunk, ins_grid),
-                       kInsThreads, 0, s.stream>>>(g2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
-      k_group_verify<<<b2, kVerNodeThreads, 0, s.stream>>>(g2, v2, ptr<uint32_t>(s.ulist[cur]), unresolved_n);
-    }
-    if (!(st = launch_check("collision repair")).ok()) return st;
-    if (!(st = read_scalars(s, h)).ok()) return st;
-    if (h[6]) {
-      TimedScope ts(s, KBISIM_KERNEL_OTHER, 1);
-      const unsigned b = (unsigned)std::min<uint64_t>(h[6], (uint64_t)sms * 8);
-      if (key64) k_verify_long<uint64_t><<<b, kVerThreads, verify_ws_bytes<uint64_t>(), s.stream>>>(g2, v2, h[6]);
-      else k_verify_long<uint32_t><<<b, kVerThreads, verify_ws_bytes<uint32_t>(), s.stream>>>(g2, v2, h[6]);
-      if (!(st = launch_check("k_verify_long")).ok()) return st;
-      if (!(st = read_scalars(s, h)).ok()) return st;
-    }
-    if (h[5] >= unresolved_n)  // every pass settles the smallest node of each group
-      return Status::Err(KBISIM_ERR_TIMEOUT, "collision repair made no progress");
-    unresolved_n = h[5];
-    cur ^= 1;
-  }
+  if (!(st = settle_unresolved(s, g, v, key64, h, KBISIM_KERNEL_VERIFY)).ok()) return st;
   *collided = h[4];
   if (s.checked && !(st = check_below(s, g.rep, na, n, "block heads")).ok()) return st;
   // canonical renumbering
@@ -2457,6 +2480,7 @@ Status compute_round(Store& s, uint32_t i) {
   a.seed = s.seed;
   a.mask = s.hash_mask;
   a.err = ptr<uint32_t>(s.d_err);
+  a.fmask = nullptr;
   // 32-bit signature words when (label, child id) fits in 32 bits
   const uint32_t pbits = bits_for(s.counts[i - 1] ? s.counts[i - 1] - 1 : 0);
   const bool key64 = pbits + s.label_bits > 32;
@@ -2481,6 +2505,80 @@ Status compute_round(Store& s, uint32_t i) {
   if (s.stats.size() < i) s.stats.resize(i);
   s.stats[i - 1] = rs;
   return Status::Ok();
+}
+
+Status masked_signatures(Store& s, const uint32_t* prev, const uint32_t* fmask) {
+  Status st = ensure_round_scratch(s);
+  if (!st.ok()) return st;
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  SigArgs a;
+  a.off = ptr<uint64_t>(s.offsets);
+  a.dst = ptr<uint32_t>(s.dst);
+  a.lab = s.elabel.p;
+  a.prev = prev;
+  a.sigkey = s.sigkey.p;
+  a.ucnt = ptr<uint32_t>(s.ucnt);
+  a.hash = ptr<uint64_t>(s.hash);
+  a.seed = s.seed;
+  a.mask = s.hash_mask;
+  a.err = ptr<uint32_t>(s.d_err);
+  a.fmask = fmask;
+  a.pbits = 32;
+  return s.label8 ? run_signatures<uint8_t, uint64_t>(s, a) : run_signatures<uint32_t, uint64_t>(s, a);
+}
+
+Status group_list(Store& s, const uint32_t* list, uint64_t count, const uint32_t* prev) {
+  Status st = ensure_round_scratch(s);
+  if (!st.ok() || !count) return st;
+  unsigned long long* sc = ptr<unsigned long long>(s.d_scalars);
+  GroupArgs g;
+  g.hash = ptr<uint64_t>(s.hash);
+  g.p2o = ptr<uint32_t>(s.p2o);
+  g.o2p = ptr<uint32_t>(s.o2p);
+  g.table = ptr<unsigned long long>(s.table);
+  g.slot = ptr<uint32_t>(s.slot);
+  g.rep = ptr<uint32_t>(s.rep);
+  g.err = ptr<uint32_t>(s.d_err);
+  g.alone = nullptr;
+  g.read_first = 0;
+  VerifyArgs v;
+  v.mode = 1;
+  v.key64 = 1;
+  v.nlabel = ptr<uint32_t>(s.nlabel);
+  v.prev = prev;
+  v.ucnt = ptr<uint32_t>(s.ucnt);
+  v.off = ptr<uint64_t>(s.offsets);
+  v.sigkey = s.sigkey.p;
+  v.n_collided = sc + 4;
+  v.long_list = ptr<uint32_t>(s.long_pairs);
+  v.n_long = sc + 6;
+  v.hbits = ptr<uint32_t>(s.hbits);  // marks of the canonical numbering: not used here
+  v.member = ptr<uint8_t>(s.member);
+  v.out_list = ptr<uint32_t>(s.ulist[0]);
+  v.n_out = sc + 1;
+  const uint64_t tcap = std::min<uint64_t>(s.tcap, table_capacity(count));
+  g.tmask = tcap - 1;
+  const int sms = sm_count(s.device);
+  cudaMemsetAsync(s.d_scalars.p, 0, 15 * 8, s.stream);
+  cudaMemsetAsync(s.table.p, 0xFF, tcap * 8, s.stream);
+  {
+    TimedScope ts(s, KBISIM_KERNEL_GROUP, 2);
+    k_group_insert<<<(unsigned)std::min<uint64_t>((count + kInsChunk - 1) / kInsChunk,
+                                                  resident_blocks(k_group_insert, kInsThreads, 0, sms)),
+                     kInsThreads, 0, s.stream>>>(g, list, count);
+    k_group_verify<<<(unsigned)std::min<uint64_t>(grid_for(count, kVerTile),
+                                                  resident_blocks(k_group_verify, kVerNodeThreads, 0, sms)),
+                     kVerNodeThreads, 0, s.stream>>>(g, v, list, count);
+  }
+  if (!(st = launch_check("group list")).ok()) return st;
+  uint64_t h[16];
+  if (!(st = read_scalars(s, h)).ok()) return st;
+  if (!(st = settle_unresolved(s, g, v, true, h, KBISIM_KERNEL_VERIFY)).ok()) return st;
+  uint32_t e = 0;
+  st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "group list");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "group list");
+  if (st.ok() && (e & kErrProbe)) return Status::Err(KBISIM_ERR_TIMEOUT, "hash table probe bound exceeded");
+  return st;
 }
 
 Status unpermute_level(Store& s, uint32_t level, uint32_t* dst) {

@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("early_stop", ctypes.c_int),
                 ("hash_seed", ctypes.c_uint64), ("hash_bits", ctypes.c_uint32),
-                ("checked", ctypes.c_int), ("collect_timing", ctypes.c_int)]
+                ("checked", ctypes.c_int), ("collect_timing", ctypes.c_int), ("maintain", ctypes.c_int)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -75,6 +75,14 @@ class KernelTimes(ctypes.Structure):
     _fields_ = [("total_ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
 
 
+class UpdateInfo(ctypes.Structure):
+    _fields_ = [("incremental", ctypes.c_int), ("reason", ctypes.c_int),
+                ("frontier_nodes", ctypes.c_uint64), ("levels", ctypes.c_uint64)]
+
+
+MAINT_REASONS = {0: "incremental", 1: "off", 2: "no_store", 3: "frontier", 4: "capacity", 5: "deletes"}
+
+
 class RoundStats(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_uint64), ("unique_keys", ctypes.c_uint64),
                 ("max_signature", ctypes.c_uint64), ("collided_nodes", ctypes.c_uint64),
@@ -101,6 +109,7 @@ SIGNATURES = {
     "kbisim_num_nodes": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_num_edges": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_device_bytes": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "kbisim_get_update_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(UpdateInfo)]),
     "kbisim_get_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
     "kbisim_reset_times": (None, [ctypes.c_void_p]),
     "kbisim_get_round_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
@@ -203,7 +212,7 @@ class KBisim:
 
     def __init__(self, device: int = 0, stream=None, early_stop: bool = True,
                  hash_seed: int = 0x12100748, hash_bits: int = 64, checked: bool = False,
-                 collect_timing: bool = False, hbm_budget_bytes: int = 0):
+                 collect_timing: bool = False, hbm_budget_bytes: int = 0, maintain: bool = True):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -225,6 +234,7 @@ class KBisim:
         opt.checked = 1 if checked else 0
         opt.collect_timing = 1 if collect_timing else 0
         opt.hbm_budget_bytes = hbm_budget_bytes
+        opt.maintain = 1 if maintain else 0
         h = ctypes.c_void_p()
         rc = lib.kbisim_create(ctypes.byref(h), ctypes.byref(opt))
         if rc != OK:
@@ -439,6 +449,14 @@ class KBisim:
 
     def reset_times(self):
         self._lib.kbisim_reset_times(self._h)
+
+    def update_info(self) -> dict:
+        """How the last update ran: incremental (frontier path) or recomputed,
+        the reason for a recomputation, and the nodes signed over the levels."""
+        ui = UpdateInfo()
+        self._check(self._lib.kbisim_get_update_info(self._h, ctypes.byref(ui)))
+        return {"incremental": bool(ui.incremental), "reason": MAINT_REASONS.get(int(ui.reason), str(ui.reason)),
+                "frontier_nodes": int(ui.frontier_nodes), "levels": int(ui.levels)}
 
     def round_stats(self, r: int) -> dict:
         st = RoundStats()

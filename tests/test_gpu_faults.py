@@ -133,11 +133,13 @@ def test_checked_mode_reports_a_bad_index(env):
 
 
 def test_update_failure_after_the_batch_is_stored(env):
+    """The recomputing update (maintain=False): a round that fails after the
+    batch was stored leaves the updated graph without levels."""
     from oracle.update import MultiGraph
     g = _graph()
     mg = MultiGraph(g.num_nodes, g.node_label, g.src(), g.dst, g.edge_label)
     ins = (np.array([1, 2], np.uint32), np.array([3, 4], np.uint32), np.array([0, 1], np.uint32))
-    with KBisim() as kb:
+    with KBisim(maintain=False) as kb:
         kb.build(g, 3)
         env.set(KBISIM_FAULT_TIMEOUT_ROUND=1)
         with pytest.raises(KBisimError) as e:

@@ -1,0 +1,121 @@
+"""Incremental maintenance (Section 4, Algorithm 3) through kbisim_update:
+after every batch the levels equal the oracle's recomputation of the updated
+graph (oracle.update.MultiGraph: apply the batch to the edge multiset, then
+Algorithm 1), bit for bit, and the update takes the frontier path when the
+frontier is small (kbisim_update_info)."""
+import numpy as np
+import pytest
+
+from paper_1210_0748_gb300 import synth
+from paper_1210_0748_gb300.kbisim import KBisim
+from tests import golden_io
+from tests.gpu_util import assert_same, graph_from_edges
+
+pytestmark = pytest.mark.gpu
+
+
+def _mg(g):
+    from oracle.update import MultiGraph
+    return MultiGraph(g.num_nodes, g.node_label, g.src(), g.dst, g.edge_label)
+
+
+def _random_batch(rng, mg, n_ins, n_del, n_add=0, labels=3, node_labels=3):
+    add = rng.integers(0, node_labels, n_add).astype(np.uint32)
+    alive = np.nonzero(np.array(mg.alive + [1] * n_add, bool))[0]
+    ins = (rng.choice(alive, n_ins).astype(np.uint32), rng.choice(alive, n_ins).astype(np.uint32),
+           rng.integers(0, labels, n_ins).astype(np.uint32))
+    s, d, l = mg.coo()
+    pick = rng.choice(s.size, min(s.size, n_del), replace=False)
+    dels = (s[pick], d[pick], l[pick])
+    return add, ins, dels
+
+
+@pytest.mark.parametrize("early_stop", [True, False])
+def test_incremental_updates_equal_the_oracle(early_stop):
+    """Small batches of edge inserts, edge deletes (some repeated or absent)
+    and node additions on a 5000-node multigraph with out-degree hubs: every
+    batch after the first runs on the frontier path."""
+    rng = np.random.default_rng(5)
+    n = 5000
+    g = synth.random_small_graph(n, 12_000, node_labels=3, edge_labels=3, seed=9)
+    hub_s = np.full(8000, 11, np.uint32)
+    hub_d = rng.integers(0, n, 8000).astype(np.uint32)
+    hub_l = rng.integers(0, 3, 8000).astype(np.uint32)
+    g = synth.from_coo(n, np.concatenate([g.src(), hub_s]), np.concatenate([g.dst, hub_d]),
+                       np.concatenate([g.edge_label, hub_l]), g.node_label)
+    mg = _mg(g)
+    k = 4
+    paths = []
+    with KBisim(early_stop=early_stop) as kb:
+        kb.build(g, k)
+        for step in range(8):
+            add, ins, dels = _random_batch(rng, mg, int(rng.integers(1, 12)), int(rng.integers(0, 8)),
+                                           n_add=int(step % 3 == 1))
+            dl = [np.concatenate([x, x[:1]]) for x in dels]  # one repeated deletion
+            want_missing = mg.apply(add, list(zip(*ins)), list(zip(*dl)))
+            res, missing = kb.update(k, add_node_label=add, ins=ins, dels=tuple(dl))
+            assert missing == want_missing
+            assert_same(res, kb.all_pids(k), mg.kbisim(k, early_stop=early_stop))
+            paths.append(kb.update_info())
+    assert sum(p["incremental"] for p in paths) >= 6, paths
+    assert all(p["frontier_nodes"] < n for p in paths if p["incremental"])
+
+
+def test_tables_4_and_5_on_the_frontier_path():
+    """The paper's Add_Edges examples: Figure 1 plus edge (2, l, 7) with node 7
+    added (Table 4), and plus edge (6, l, 5) (Table 5), each as an update of a
+    built handle, against the tables as printed."""
+    for fix in ("table4_add_edge_2l7.txt", "table5_add_edge_6l5.txt"):
+        base = golden_io.load("fig1_table1.txt")
+        upd = golden_io.Fixture()
+        upd._nlab, upd._elab = base._nlab, base._elab
+        upd = golden_io.load(fix, base=upd)
+        names = list(base.node_names) + [a for a, _ in upd.add_nodes]
+        g = graph_from_edges(len(base.node_names), base.node_label, base.edges)
+        ins = [(names.index(a), names.index(b), l) for a, l, b in upd.add_edges]
+        with KBisim(early_stop=False) as kb:
+            kb.build(g, 2)
+            kb.update(2, add_node_label=[l for _, l in upd.add_nodes],
+                      ins=tuple(np.array(x, dtype=np.uint32) for x in zip(*ins)))
+            assert kb.update_info()["incremental"], kb.update_info()
+            for lev in range(3):
+                assert kb.pids(lev).tolist() == golden_io.canonical(upd.pids[lev]), (fix, lev)
+
+
+def test_switch_back_and_recompute_agree():
+    """A batch that touches most nodes switches back to the full computation;
+    a batch with a node deletion recomputes; maintain=False always recomputes.
+    All three give the oracle's levels, and later small batches go back to the
+    frontier path."""
+    rng = np.random.default_rng(8)
+    g = synth.config_single_large(scale=1 / 2048, seed=4)  # 7.8K nodes, 125K edges
+    mg = _mg(g)
+    k = 3
+    with KBisim() as kb, KBisim(maintain=False) as plain:
+        kb.build(g, k)
+        plain.build(g, k)
+        batches = [_random_batch(rng, mg, 4000, 500, labels=32, node_labels=16),
+                   _random_batch(rng, mg, 3, 2, labels=32, node_labels=16),
+                   _random_batch(rng, mg, 5, 1, labels=32, node_labels=16)]
+        for i, (add, ins, dels) in enumerate(batches):
+            mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+            ref = mg.kbisim(k)
+            r1, _ = kb.update(k, ins=ins, dels=dels)
+            info = kb.update_info()
+            r2, _ = plain.update(k, ins=ins, dels=dels)
+            assert plain.update_info()["reason"] == "off"
+            assert_same(r1, kb.all_pids(k), ref)
+            assert_same(r2, plain.all_pids(k), ref)
+            if i == 0:
+                assert not info["incremental"] and info["reason"] == "frontier", info
+        # a node deletion recomputes, then the next small batch is incremental again
+        victim = int(np.nonzero(np.array(mg.alive))[0][3])
+        mg.apply(del_nodes=[victim])
+        r, _ = kb.update(k, del_nodes=np.array([victim], np.uint32))
+        assert kb.update_info()["reason"] == "deletes"
+        assert_same(r, kb.all_pids(k), mg.kbisim(k))
+        add, ins, dels = _random_batch(rng, mg, 2, 1, labels=32, node_labels=16)
+        mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+        r, _ = kb.update(k, ins=ins, dels=dels)
+        assert kb.update_info()["incremental"]
+        assert_same(r, kb.all_pids(k), mg.kbisim(k))
