@@ -249,7 +249,9 @@ int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_re
 
 /* How the last kbisim_update ran.  incremental = 1: the frontier path, with
  * frontier_nodes nodes signed over `levels` levels; 0: every level was
- * recomputed, for the reason in `reason` (KBISIM_MAINT_*). */
+ * recomputed, for the reason in `reason` (KBISIM_MAINT_*).  The paper has no
+ * counterpart: this reports which of its two paths (Algorithm 3 or a rebuild)
+ * ran. */
 #define KBISIM_MAINT_OFF 1        /* options.maintain = 0 */
 #define KBISIM_MAINT_NO_STORE 2   /* no stores yet (first update after a build), or k above them */
 #define KBISIM_MAINT_FRONTIER 3   /* a level's frontier held more than a quarter of the nodes (and > 4096) */
@@ -260,6 +262,10 @@ typedef struct {
   int reason;
   uint64_t frontier_nodes;
   uint64_t levels;
+  /* 1 = the batch was applied to the edge table in place (edge insertions and
+   * deletions that keep every node in its out-degree class: node ids keep
+   * their internal order); 0 = the updated graph was laid out again. */
+  int in_place;
 } kbisim_update_info;
 int kbisim_get_update_info(const kbisim_handle *h, kbisim_update_info *out);
 

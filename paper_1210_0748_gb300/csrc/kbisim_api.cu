@@ -279,6 +279,7 @@ void free_graph(Store& s, bool keep_buffers) {
     for (Buf& b : s.out_level) release(s, b);
     for (Buf& b : s.stage) release(s, b);
     for (Buf& b : s.upd) release(s, b);
+    for (Buf& b : s.inplace) release(s, b);
     s.level.clear();
     s.out_level.clear();
   }
@@ -744,6 +745,7 @@ int kbisim_build_many(kbisim_handle* h, const kbisim_graph* g, const uint64_t* g
     s.level_hook = kb::many_level;
     st = kb::refine(s, kmax, &r);
     s.level_hook = nullptr;
+    s.round_mask = nullptr;
     if (st.ok()) kb::many_finish(s);
   }
   if (!st.ok()) s.many.valid = false;
@@ -826,6 +828,7 @@ int kbisim_get_update_info(const kbisim_handle* h, kbisim_update_info* out) {
   out->reason = h->s.mt.reason;
   out->frontier_nodes = h->s.mt.frontier_nodes;
   out->levels = h->s.mt.levels;
+  out->in_place = h->s.mt.in_place;
   return KBISIM_OK;
 }
 
@@ -866,6 +869,7 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
   s.mt.incremental = 0;
   s.mt.frontier_nodes = 0;
   s.mt.levels = 0;
+  s.mt.in_place = 0;
   if (!s.maintain) {
     s.mt.reason = KBISIM_MAINT_OFF;
   } else if (b && b->n_del_nodes) {

@@ -39,6 +39,21 @@ static_assert(kChunkEdges >= kBlockMax, "a medium node must fit one chunk");
 static_assert(kChunkEdges / (kSmallMax + 1) < kChunkMaxNodes, "chunk node table too small");
 static_assert(kSmallChunkThreads * kChunkItems >= kWarp2Max, "a node of out-degree <= kWarp2Max must fit one small chunk");
 
+// Degree class of a node of out-degree d: 0, 1, 2, 3-4, 5-8, 9-16, 17-32,
+// 33-64, then 65..kWarpMax, ..kWarp2Max, ..kBlockMax, hubs.
+__host__ __device__ __forceinline__ int degree_class_of(uint64_t d) {
+  if (d == 0) return 0;
+  if (d <= (uint64_t)kSmallMax) {
+    int c = 1;
+    while ((1ull << (c - 1)) < d) ++c;
+    return c;
+  }
+  if (d <= (uint64_t)kWarpMax) return kClassWarp;
+  if (d <= (uint64_t)kWarp2Max) return kClassWarp2;
+  if (d <= (uint64_t)kBlockMax) return kClassBlock;
+  return kClassHub;
+}
+
 // Device error flags (bit set in Store::d_err).
 enum : uint32_t {
   kErrChecked = 1u,       // an index check failed
@@ -147,6 +162,8 @@ struct ManyState {
   Buf gid, gidp;                               // uint32 [n] graph of each original / internal node
   Buf tkey, tmin, slot;                        // (graph, union block) -> smallest original id
   Buf hbits, hword, cnt;                       // head bitmap, per-word prefix, per-graph prefix
+  Buf live, live_mask;                         // uint8 [G] graph still refined; bitmap over internal ids
+  uint64_t live_graphs = 0;                    // graphs refined in the next round
 };
 
 // Incremental maintenance state (kbisim_maint.cu).  Level j of the
@@ -180,11 +197,13 @@ struct MaintState {
   Buf minid, cnt;                   // uint32 [lcap] canonical renumbering from labels
   Buf src;                          // uint32 staged sources of the batch's edges
   Buf misc;                         // uint64 scalars
+  Buf woff;                         // uint64 [n + 1] pool offsets of the heads' signatures (build)
   // last update
   int incremental = 0;              // 1 = frontier path, 0 = full recomputation
   int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)
   uint64_t frontier_nodes = 0;      // nodes signed over all levels
   uint64_t levels = 0;              // levels processed
+  int in_place = 0;                 // the batch was applied to the edge table in place
 };
 
 struct Store;
@@ -287,6 +306,8 @@ struct Store {
   Buf rl_tcnt, rl_hot, rl_ost; // relabelling temporaries
   static constexpr int kUpdBufsN = 24;
   Buf upd[kUpdBufsN];          // temporaries of a maintenance batch (kbisim_update)
+  static constexpr int kInplaceBufsN = 11;
+  Buf inplace[kInplaceBufsN];  // a batch applied in place: claims, degrees, the other edge table
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters
   Buf h_scalars;               // pinned host mirror of d_scalars
@@ -296,6 +317,8 @@ struct Store {
   bool maintain = true;
   double maint_frontier_max = 0.25;  // switch back to a rebuild above this fraction of the nodes
   LevelHook level_hook = nullptr;  // called after each computed level (batched build)
+  const uint32_t* round_mask = nullptr;  // nodes signed in the next round (NULL = all); the
+                                         // others keep their block (batched build work list)
 
   // Host-side fault injection for tests (read from the environment at every
   // mutating call, see read_fault_hooks): allocations that succeed before one
@@ -344,6 +367,9 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
 // the store with the updated graph loaded and no levels.
 Status apply_batch(Store& s, const kbisim_batch* b, uint64_t* missing);
 Status compute_level0(Store& s);                  // pId_0 into level[0]
+// Work lists of the degree classes from s.offsets (after a relabel, or after
+// a batch applied in place); `fresh` drops what hub buckets learned.
+Status build_chunk_lists(Store& s, bool fresh);
 Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
 // Signatures of the nodes whose bit is set in fmask (bitmap over internal ids;
 // NULL = every node) from identifiers prev (internal order), as 64-bit

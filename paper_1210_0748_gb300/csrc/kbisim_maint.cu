@@ -191,28 +191,40 @@ __device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p
 }
 
 // Build: the heads of every label (smallest original id) store their
-// signatures under their canonical id.  One warp per node.
+// signatures under their canonical id, at pool offsets from a prefix sum of
+// the heads' element counts (woff).  One warp per node.
 __global__ void k_store_heads(StoreArgs a, NodeSig g, uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab,
-                              const uint32_t* minid) {
+                              const uint32_t* minid, const unsigned long long* woff) {
+  const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; p < n_alive; p += warps) {
     const uint32_t o = p2o[p];
     const uint32_t b = lab[o];
     if (minid[b] != o) continue;
-    store_signature(a, g, p, b);
+    const uint32_t U = g.ucnt[p];
+    const unsigned long long base = woff[p];
+    const uint64_t* src = g.sigkey + g.off[p];
+    for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
+    if (lane == 0) {
+      a.sfirst[b] = g.prev[p];
+      a.scount[b] = U;
+      a.soff[b] = base;
+      if (!store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
+    }
   }
 }
 
-// Words the heads' signatures take (the pool's size at build).
-__global__ void k_head_words(uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab, const uint32_t* minid,
-                             const uint32_t* ucnt, unsigned long long* total) {
-  unsigned long long w = 0;
-  GRID_STRIDE(p, n_alive) {
-    const uint32_t o = p2o[p];
-    if (minid[lab[o]] == o) w += ucnt[p];
+// Element words of every head (0 for the other nodes), for the pool offsets.
+__global__ void k_head_words(uint64_t n_alive, uint64_t n, const uint32_t* p2o, const uint32_t* lab,
+                             const uint32_t* minid, const uint32_t* ucnt, unsigned long long* w) {
+  GRID_STRIDE(p, n + 1) {
+    unsigned long long v = 0;
+    if (p < n_alive) {
+      const uint32_t o = p2o[p];
+      if (minid[lab[o]] == o) v = ucnt[p];
+    }
+    w[p] = v;
   }
-  for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFullMask, w, d);
-  if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
 }
 
 // Set equality of node p's elements and stored signature b (same count U <=
@@ -567,13 +579,16 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   cudaMemsetAsync(m.minid.p, 0xFF, L.lcap * 4, s.stream);
   k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(L.lab), ptr<uint32_t>(m.minid),
                                                                       nullptr);
-  unsigned long long* sc = ptr<unsigned long long>(m.misc);
-  cudaMemsetAsync(sc, 0, 8, s.stream);
-  k_head_words<<<grid_for(s, na, kThreads), kThreads, 0, s.stream>>>(na, ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
-                                                                      ptr<uint32_t>(m.minid), ptr<uint32_t>(s.ucnt), sc);
+  if (!(st = ensure(s, m.woff, (n + 1) * 8)).ok()) return st;
+  unsigned long long* woff = ptr<unsigned long long>(m.woff);
+  k_head_words<<<grid_for(s, n + 1, kThreads), kThreads, 0, s.stream>>>(na, n, ptr<uint32_t>(s.p2o),
+                                                                          ptr<uint32_t>(L.lab), ptr<uint32_t>(m.minid),
+                                                                          ptr<uint32_t>(s.ucnt), woff);
+  if (!(st = cuda_check(cudaGetLastError(), "store size")).ok()) return st;
+  if (!(st = scan_u64(s, reinterpret_cast<uint64_t*>(woff), n + 1)).ok()) return st;
   uint64_t words = 0;
-  if (!(st = sync_read(s, &words, sc, 8, "store size")).ok()) return st;
-  L.pcap = words + words / 2 + (1u << 20);
+  if (!(st = sync_read(s, &words, woff + n, 8, "store size")).ok()) return st;
+  L.pcap = 2 * words + (16u << 20);  // room for the signatures later updates add
   L.tcap = pow2_at_least(2 * L.lcap);
   if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
   if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
@@ -584,12 +599,12 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = ensure(s, L.ctr, 16)).ok()) return st;
   cudaMemsetAsync(L.tkey.p, 0xFF, L.tcap * 8, s.stream);
   cudaMemsetAsync(L.tval.p, 0xFF, L.tcap * 4, s.stream);
-  uint64_t c0[2] = {labels, 0};
+  uint64_t c0[2] = {labels, words};
   if (!(st = cuda_check(cudaMemcpyAsync(L.ctr.p, c0, 16, cudaMemcpyHostToDevice, s.stream), "store")).ok()) return st;
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
   k_store_heads<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(store_args(s, L), node_sig(s), na,
                                                                 ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
-                                                                ptr<uint32_t>(m.minid));
+                                                                ptr<uint32_t>(m.minid), woff);
   uint32_t e = 0;
   if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
   if (!(st = sync_read(s, &e, s.d_err.p, 4, "store heads")).ok()) return st;
@@ -687,7 +702,7 @@ void maint_release(Store& s) {
   }
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc};
+              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff};
   for (Buf* x : b) release(s, *x);
   m.valid = false;
   m.k = 0;

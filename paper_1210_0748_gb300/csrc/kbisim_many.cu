@@ -172,7 +172,51 @@ __global__ void k_many_counts(ManyArgs a, const uint64_t* start, uint32_t G, uns
     cnt[j] = heads_before(a, start[j]);
 }
 
+// Work list of the next round: nodes of the graphs still refined.
+__global__ void k_many_live_mask(uint64_t n_alive, const uint32_t* gidp, const uint8_t* live, uint32_t* mask) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w * 32 < n_alive;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t bits = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+      const uint64_t p = w * 32 + b;
+      if (p < n_alive && live[gidp[p]]) bits |= 1u << b;
+    }
+    mask[w] = bits;
+  }
+}
+
 }  // namespace
+
+// After level l: the graphs that still need a round (l < k_j, and with early
+// stop not yet stable) form the next round's work list; the others keep their
+// blocks (their nodes are not signed again).  Only set while some graph has
+// stopped and others go on.
+Status many_work_list(Store& s, uint32_t l) {
+  ManyState& m = s.many;
+  s.round_mask = nullptr;
+  std::vector<uint8_t> live(m.G, 0);
+  uint64_t nlive = 0;
+  for (uint32_t j = 0; j < m.G; ++j) {
+    bool go = l < m.k[j];
+    if (go && s.early_stop && l >= 1 && m.counts[l][j] == m.counts[l - 1][j]) go = false;
+    live[j] = go ? 1 : 0;
+    nlive += go ? 1 : 0;
+  }
+  m.live_graphs = nlive;
+  if (nlive == 0 || nlive == m.G) return Status::Ok();
+  Status st;
+  const uint64_t words = s.n_alive / 32 + 1;
+  if (!(st = ensure(s, m.live, m.G)).ok()) return st;
+  if (!(st = ensure(s, m.live_mask, words * 4)).ok()) return st;
+  st = cuda_check(cudaMemcpyAsync(m.live.p, live.data(), m.G, cudaMemcpyHostToDevice, s.stream), "live graphs");
+  if (!st.ok()) return st;
+  k_many_live_mask<<<grid_for(words, kThreads, s.sms * 16), kThreads, 0, s.stream>>>(
+      s.n_alive, ptr<uint32_t>(m.gidp), ptr<uint8_t>(m.live), ptr<uint32_t>(m.live_mask));
+  st = cuda_check(cudaGetLastError(), "live mask");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "live mask");  // the host vector goes away
+  if (st.ok()) s.round_mask = ptr<uint32_t>(m.live_mask);
+  return st;
+}
 
 // Per-graph renumbering of level l (called right after the union computed it).
 Status many_level(Store& s, uint32_t l) {
@@ -238,7 +282,7 @@ Status many_level(Store& s, uint32_t l) {
   m.counts[l].resize(m.G);
   for (uint32_t j = 0; j < m.G; ++j) m.counts[l][j] = c[j + 1] - c[j];
   m.levels = l + 1;
-  return Status::Ok();
+  return many_work_list(s, l);
 }
 
 Status many_check_args(const kbisim_graph* g, const uint64_t* start, uint32_t G, const uint32_t* k,
@@ -337,7 +381,8 @@ void many_release(Store& s) {
   ManyState& m = s.many;
   for (Buf& b : m.lvl) release(s, b);
   m.lvl.clear();
-  Buf* bufs[] = {&m.dstart, &m.gid, &m.gidp, &m.tkey, &m.tmin, &m.slot, &m.hbits, &m.hword, &m.cnt};
+  Buf* bufs[] = {&m.dstart, &m.gid, &m.gidp, &m.tkey, &m.tmin, &m.slot, &m.hbits, &m.hword, &m.cnt, &m.live,
+                 &m.live_mask};
   for (Buf* b : bufs) release(s, *b);
   m.valid = false;
 }

@@ -1451,6 +1451,18 @@ __global__ void k_pid_fill(RankArgs r) {
   }
 }
 
+// Nodes outside the round's mask keep their block: signature (pId_{i-1}(u), {})
+// -- a node of a graph that has stopped (batched build) then stays with the
+// nodes it was grouped with at the level before.
+__global__ void k_freeze(uint64_t n_alive, const uint32_t* mask, const uint32_t* prev, uint32_t* ucnt,
+                         uint64_t* hash, uint64_t seed, uint64_t hmask) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n_alive; p += (uint64_t)gridDim.x * blockDim.x) {
+    if ((mask[p >> 5] >> (p & 31)) & 1u) continue;
+    ucnt[p] = 0;
+    hash[p] = node_hash(0, prev[p], 0, seed, hmask);
+  }
+}
+
 // Checked mode: every a[i] (i < n) must be below `bound`.  The kernels that
 // index with an array run only after this check has passed on it.
 __global__ void k_check_below(const uint32_t* a, uint64_t n, uint64_t bound, uint32_t* err) {
@@ -1484,18 +1496,7 @@ __global__ void k_unpermute(uint64_t n, const uint32_t* o2p, const uint32_t* lvl
 // --------------------------------------------------------------------------
 // Relabelling (once per graph)
 // --------------------------------------------------------------------------
-__device__ __forceinline__ int degree_class(uint64_t d) {
-  if (d == 0) return 0;
-  if (d <= (uint64_t)kSmallMax) {
-    int c = 1;
-    while ((1ull << (c - 1)) < d) ++c;
-    return c;
-  }
-  if (d <= (uint64_t)kWarpMax) return kClassWarp;
-  if (d <= (uint64_t)kWarp2Max) return kClassWarp2;
-  if (d <= (uint64_t)kBlockMax) return kClassBlock;
-  return kClassHub;
-}
+__device__ __forceinline__ int degree_class(uint64_t d) { return degree_class_of(d); }
 
 constexpr int kClassTile = 1024;
 
@@ -2252,74 +2253,18 @@ uint32_t bits_for(uint64_t v) {  // bits needed to represent values 0..v
 // ---------------------------------------------------------------------------
 // Relabelling and degree classes (once per graph)
 // ---------------------------------------------------------------------------
-Status scan_u64(Store& s, uint64_t* a, uint64_t n) { return scan64(s, a, n, nullptr); }
-
-Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const void* lab0,
-                     const uint32_t* nlab0, const uint8_t* alive0, uint32_t lab_bytes) {
-  Status st = set_smem_attrs(s.device);
-  if (!st.ok()) return st;
-  const uint64_t n = s.n, m = s.m;
-  const int sms = sm_count(s.device);
-  const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
-  // temporaries of the relabelling (kept between loads unless the handle has
-  // an HBM budget)
-  Buf &tcnt = s.rl_tcnt, &hot = s.rl_hot, &ost = s.rl_ost;
-  auto fail = [&](Status e) {
-    if (s.budget) {
-      release(s, tcnt);
-      release(s, hot);
-      release(s, ost);
-    }
-    return e;
-  };
-  if (!(st = ensure(s, tcnt, ntiles * kNumOrder * 8)).ok()) return fail(st);
-  if (!(st = ensure(s, hot, std::max<uint64_t>(1, n) * 4)).ok()) return fail(st);
-  if (!(st = ensure(s, ost, kNumOrder * 8)).ok()) return fail(st);
-  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumOrder * 8, s.stream);
-  cudaMemsetAsync(hot.p, 0, std::max<uint64_t>(1, n) * 4, s.stream);
-  if (m >> kHotSampleShift)
-    k_hot_sample<<<(unsigned)std::min<uint64_t>(grid_for(m >> kHotSampleShift, 256), (uint64_t)sms * 32), 256, 0,
-                   s.stream>>>(m, dst0, ptr<uint32_t>(hot));
-  if (n)
-    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
-                                                                      ptr<unsigned long long>(tcnt));
-  if (!(st = launch_check("k_class_tile_count")).ok()) return fail(st);
-  if (!(st = scan64(s, ptr<uint64_t>(tcnt), ntiles * kNumOrder, nullptr)).ok()) return fail(st);
-  k_order_starts<<<1, 128, 0, s.stream>>>(ptr<unsigned long long>(tcnt), ntiles, ptr<unsigned long long>(ost));
-  std::vector<uint64_t> hs(kNumOrder);
-  st = cuda_check(cudaMemcpyAsync(hs.data(), ost.p, kNumOrder * 8, cudaMemcpyDeviceToHost, s.stream), "class starts");
-  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  if (!st.ok()) return fail(st);
-  for (int c = 0; c < kNumClasses; ++c) s.class_start[c] = hs[(size_t)c * kHotBuckets];
-  s.class_start[kNumClasses] = n;
-  s.n_alive = s.class_start[kClassDead];
-  if (st.ok()) st = ensure(s, s.p2o, std::max<uint64_t>(1, n) * 4);
-  if (st.ok()) st = ensure(s, s.o2p, std::max<uint64_t>(1, n) * 4);
-  if (st.ok()) st = ensure(s, s.offsets, (n + 1) * 8);
-  if (st.ok()) st = ensure(s, s.nlabel, std::max<uint64_t>(1, n) * 4);
-  if (st.ok()) st = ensure(s, s.dst, std::max<uint64_t>(1, m) * 4);
-  if (st.ok()) st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4));
-  if (!st.ok()) return fail(st);
-  const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
-  if (n) {
-    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
-                                                                        ptr<unsigned long long>(tcnt),
-                                                                        ptr<uint32_t>(s.p2o));
-    k_invert<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), ptr<uint32_t>(s.o2p));
-  }
-  k_relabel_nodes<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), off0, nlab0,
-                                            ptr<unsigned long long>(s.offsets), ptr<uint32_t>(s.nlabel));
-  st = launch_check("relabel nodes");
-  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  fail(Status::Ok());  // the class scatter has finished with the tile bases and counts
-  if (!st.ok()) return st;
-  if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
+// Work lists made from the offsets of the degree classes: hub chunks and the
+// hubs' bucket layout, and the chunks of whole nodes for out-degree 33..4096.
+// `fresh`: a new graph (bucket growth learned on the previous one is dropped).
+Status build_chunk_lists(Store& s, bool fresh) {
+  Status st;
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
-  s.n_alone = 0;
-  s.h_hub_xbits.assign(s.n_hub, 0);
-  s.h_hub_shift.assign(s.n_hub, 0);
-  s.h_hub_force.assign(s.n_hub, 0);
+  if (fresh || s.h_hub_xbits.size() != s.n_hub) {  // bucket growth learned on this graph is kept otherwise
+    s.h_hub_xbits.assign(s.n_hub, 0);
+    s.h_hub_shift.assign(s.n_hub, 0);
+    s.h_hub_force.assign(s.n_hub, 0);
+  }
   s.h_hub_degbits.assign(s.n_hub, 0);
   s.h_hub_deg.assign(s.n_hub, 0);
   s.hub_edges = 0;
@@ -2391,6 +2336,74 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
                                     s.stream), "medium chunks");
     if (!st.ok()) return st;
   }
+  return Status::Ok();
+}
+
+
+Status scan_u64(Store& s, uint64_t* a, uint64_t n) { return scan64(s, a, n, nullptr); }
+
+Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const void* lab0,
+                     const uint32_t* nlab0, const uint8_t* alive0, uint32_t lab_bytes) {
+  Status st = set_smem_attrs(s.device);
+  if (!st.ok()) return st;
+  const uint64_t n = s.n, m = s.m;
+  const int sms = sm_count(s.device);
+  const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
+  // temporaries of the relabelling (kept between loads unless the handle has
+  // an HBM budget)
+  Buf &tcnt = s.rl_tcnt, &hot = s.rl_hot, &ost = s.rl_ost;
+  auto fail = [&](Status e) {
+    if (s.budget) {
+      release(s, tcnt);
+      release(s, hot);
+      release(s, ost);
+    }
+    return e;
+  };
+  if (!(st = ensure(s, tcnt, ntiles * kNumOrder * 8)).ok()) return fail(st);
+  if (!(st = ensure(s, hot, std::max<uint64_t>(1, n) * 4)).ok()) return fail(st);
+  if (!(st = ensure(s, ost, kNumOrder * 8)).ok()) return fail(st);
+  cudaMemsetAsync(tcnt.p, 0, ntiles * kNumOrder * 8, s.stream);
+  cudaMemsetAsync(hot.p, 0, std::max<uint64_t>(1, n) * 4, s.stream);
+  if (m >> kHotSampleShift)
+    k_hot_sample<<<(unsigned)std::min<uint64_t>(grid_for(m >> kHotSampleShift, 256), (uint64_t)sms * 32), 256, 0,
+                   s.stream>>>(m, dst0, ptr<uint32_t>(hot));
+  if (n)
+    k_class_tile_count<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
+                                                                      ptr<unsigned long long>(tcnt));
+  if (!(st = launch_check("k_class_tile_count")).ok()) return fail(st);
+  if (!(st = scan64(s, ptr<uint64_t>(tcnt), ntiles * kNumOrder, nullptr)).ok()) return fail(st);
+  k_order_starts<<<1, 128, 0, s.stream>>>(ptr<unsigned long long>(tcnt), ntiles, ptr<unsigned long long>(ost));
+  std::vector<uint64_t> hs(kNumOrder);
+  st = cuda_check(cudaMemcpyAsync(hs.data(), ost.p, kNumOrder * 8, cudaMemcpyDeviceToHost, s.stream), "class starts");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return fail(st);
+  for (int c = 0; c < kNumClasses; ++c) s.class_start[c] = hs[(size_t)c * kHotBuckets];
+  s.class_start[kNumClasses] = n;
+  s.n_alive = s.class_start[kClassDead];
+  if (st.ok()) st = ensure(s, s.p2o, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.o2p, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.offsets, (n + 1) * 8);
+  if (st.ok()) st = ensure(s, s.nlabel, std::max<uint64_t>(1, n) * 4);
+  if (st.ok()) st = ensure(s, s.dst, std::max<uint64_t>(1, m) * 4);
+  if (st.ok()) st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4));
+  if (!st.ok()) return fail(st);
+  const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
+  if (n) {
+    k_class_tile_scatter<<<(unsigned)ntiles, kClassTile, 0, s.stream>>>(n, off0, alive0, ptr<uint32_t>(hot), ntiles,
+                                                                        ptr<unsigned long long>(tcnt),
+                                                                        ptr<uint32_t>(s.p2o));
+    k_invert<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), ptr<uint32_t>(s.o2p));
+  }
+  k_relabel_nodes<<<gb, 256, 0, s.stream>>>(n, ptr<uint32_t>(s.p2o), off0, nlab0,
+                                            ptr<unsigned long long>(s.offsets), ptr<uint32_t>(s.nlabel));
+  st = launch_check("relabel nodes");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  fail(Status::Ok());  // the class scatter has finished with the tile bases and counts
+  if (!st.ok()) return st;
+  if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
+  s.n_alone = 0;
+  if (!(st = build_chunk_lists(s, true)).ok()) return st;
   if (n && m) {
     if (s.label8) {
       uint8_t* lab = ptr<uint8_t>(s.elabel);
@@ -2480,7 +2493,7 @@ Status compute_round(Store& s, uint32_t i) {
   a.seed = s.seed;
   a.mask = s.hash_mask;
   a.err = ptr<uint32_t>(s.d_err);
-  a.fmask = nullptr;
+  a.fmask = s.round_mask;
   // 32-bit signature words when (label, child id) fits in 32 bits
   const uint32_t pbits = bits_for(s.counts[i - 1] ? s.counts[i - 1] - 1 : 0);
   const bool key64 = pbits + s.label_bits > 32;
@@ -2490,6 +2503,12 @@ Status compute_round(Store& s, uint32_t i) {
   else
     st = key64 ? run_signatures<uint32_t, uint64_t>(s, a) : run_signatures<uint32_t, uint32_t>(s, a);
   if (!st.ok()) return st;
+  if (s.round_mask && s.n_alive) {
+    const int sms = sm_count(s.device);
+    k_freeze<<<(unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16), 256, 0, s.stream>>>(
+        s.n_alive, s.round_mask, a.prev, a.ucnt, a.hash, s.seed, s.hash_mask);
+    if (!(st = launch_check("k_freeze")).ok()) return st;
+  }
   uint64_t blocks = 0, coll = 0, keys = 0, maxsig = 0;
   // nodes alone in their block at level i-1 stay alone (Proposition 1): they
   // are heads of level i without a table lookup

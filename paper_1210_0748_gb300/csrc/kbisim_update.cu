@@ -382,6 +382,303 @@ Status stage(Store& s, Buf& b, const uint32_t* src, uint64_t k, bool dev, const 
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// In-place application of a batch of edge insertions and deletions that keeps
+// every node in its degree class (no node additions or deletions): internal
+// ids and the class layout stay, only the touched nodes' segments change.
+// Deletions claim one stored copy each (a claim bit per edge), the new
+// offsets are the old ones shifted by the degree changes, untouched segments
+// move as blocks and touched ones are rewritten.  Costs a few passes over the
+// edge table instead of the relabelling a general batch needs.
+// ---------------------------------------------------------------------------
+
+// Internal ids of the batch's endpoints.
+__global__ void k_to_internal_ids(uint64_t k, const uint32_t* o2p, const uint32_t* a, uint32_t* out) {
+  GRID_STRIDE(i, k) out[i] = o2p[a[i]];
+}
+
+// One warp per deletion: claim the first unclaimed stored copy of (t, l) in
+// the segment of s.  Claims are bits over the edge table.
+template <typename LabelT>
+__global__ void k_claim_deletes(uint64_t k, const uint32_t* ds, const uint32_t* dt, const uint32_t* dl,
+                                const uint64_t* off, const uint32_t* dst, const LabelT* lab, uint32_t* claimed,
+                                int* delta, uint32_t* touched, unsigned long long* missing) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < k; i += warps) {
+    const uint32_t p = ds[i], t = dt[i], l = dl[i];
+    bool done = false;
+    for (uint64_t e0 = off[p]; e0 < off[p + 1] && !done; e0 += 32) {
+      const uint64_t e = e0 + lane;
+      unsigned cand = __ballot_sync(0xFFFFFFFFu, e < off[p + 1] && dst[e] == t && (uint32_t)lab[e] == l);
+      while (cand && !done) {
+        const int j = __ffs(cand) - 1;
+        cand &= cand - 1;
+        uint32_t won = 0;
+        if (lane == (uint32_t)j) {
+          const uint64_t ej = e0 + j;
+          won = (atomicOr(&claimed[ej >> 5], 1u << (ej & 31)) >> (ej & 31)) & 1u ? 0u : 1u;
+        }
+        done = __shfl_sync(0xFFFFFFFFu, won, j) != 0;
+      }
+    }
+    if (lane == 0) {
+      if (done) {
+        atomicSub(&delta[p], 1);
+        atomicOr(&touched[p >> 5], 1u << (p & 31));
+      } else {
+        atomicAdd(missing, 1ull);
+      }
+    }
+  }
+}
+
+__global__ void k_count_inserts_internal(uint64_t k, const uint32_t* is, int* delta, uint32_t* touched) {
+  GRID_STRIDE(i, k) {
+    atomicAdd(&delta[is[i]], 1);
+    atomicOr(&touched[is[i] >> 5], 1u << (is[i] & 31));
+  }
+}
+
+// Touched nodes whose degree class would change (then the batch is applied by
+// relabelling), and the new degrees of all nodes.
+__global__ void k_new_degrees(uint64_t n, const uint64_t* off, const int* delta, unsigned long long* deg,
+                              unsigned int* class_moved) {
+  GRID_STRIDE(p, n) {
+    const uint64_t d0 = off[p + 1] - off[p];
+    const int dd = delta[p];
+    const uint64_t d1 = (uint64_t)((int64_t)d0 + dd);
+    deg[p] = d1;
+    if (dd && degree_class_of(d0) != degree_class_of(d1)) *class_moved = 1u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
+}
+
+// Untouched segments move to their new offsets.  Out-degree <= 64: one warp
+// per 32 consecutive nodes, edges found by a binary search over the 32
+// offsets (as in the relabelling); larger: one warp per node.
+template <typename LabelT>
+__global__ void k_move_small(uint64_t n_small, const uint64_t* off, const uint64_t* noff, const uint32_t* touched,
+                             const uint32_t* dst, const LabelT* lab, uint32_t* ndst, LabelT* nlab) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < n_small; w += warps) {
+    const uint64_t p = w * 32 + lane;
+    const uint64_t base = off[w * 32];
+    const uint64_t end = off[min(w * 32 + 32, n_small)];
+    const uint32_t r1 = (uint32_t)((p < n_small ? off[p] : end) - base);
+    const uint64_t to = p < n_small ? noff[p] : 0;
+    const bool skip = p >= n_small || ((touched[p >> 5] >> (p & 31)) & 1u);
+    const uint32_t T = (uint32_t)(end - base);
+    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
+      const uint32_t kk = k0 + lane;
+      const uint32_t ks = min(kk, T - 1);
+      uint32_t j = 0;
+#pragma unroll
+      for (uint32_t step = 16; step; step >>= 1)
+        if (__shfl_sync(0xFFFFFFFFu, r1, j + step) <= ks) j += step;
+      const bool sk = __shfl_sync(0xFFFFFFFFu, skip, j);
+      const uint64_t tj = __shfl_sync(0xFFFFFFFFu, to, j);
+      const uint32_t rj = __shfl_sync(0xFFFFFFFFu, r1, j);
+      if (kk < T && !sk) {
+        ndst[tj + (kk - rj)] = dst[base + kk];
+        nlab[tj + (kk - rj)] = lab[base + kk];
+      }
+    }
+  }
+}
+
+template <typename LabelT>
+__global__ void k_move_large(uint64_t p0, uint64_t p1, const uint64_t* off, const uint64_t* noff,
+                             const uint32_t* touched, const uint32_t* dst, const LabelT* lab, uint32_t* ndst,
+                             LabelT* nlab) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t p = p0 + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); p < p1; p += warps) {
+    if ((touched[p >> 5] >> (p & 31)) & 1u) continue;
+    const uint64_t a = off[p], d = off[p + 1] - a, b = noff[p];
+    for (uint64_t i = lane; i < d; i += 32) {
+      ndst[b + i] = dst[a + i];
+      nlab[b + i] = lab[a + i];
+    }
+  }
+}
+
+// Touched nodes (one warp each): kept edges first, then a cursor for the
+// inserted ones.
+template <typename LabelT>
+__global__ void k_rewrite_touched(const uint32_t* list, uint64_t count, const uint64_t* off, const uint64_t* noff,
+                                  const uint32_t* claimed, const uint32_t* dst, const LabelT* lab, uint32_t* ndst,
+                                  LabelT* nlab, unsigned long long* cursor) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
+    const uint32_t p = list[i];
+    uint64_t w = noff[p];
+    for (uint64_t e0 = off[p]; e0 < off[p + 1]; e0 += 32) {
+      const uint64_t e = e0 + lane;
+      const bool keep = e < off[p + 1] && !((claimed[e >> 5] >> (e & 31)) & 1u);
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        const uint64_t q = w + __popc(m & ((1u << lane) - 1u));
+        ndst[q] = dst[e];
+        nlab[q] = lab[e];
+      }
+      w += __popc(m);
+    }
+    if (lane == 0) cursor[p] = w;
+  }
+}
+
+template <typename LabelT>
+__global__ void k_place_inserts_internal(uint64_t k, const uint32_t* is, const uint32_t* it, const uint32_t* il,
+                                         unsigned long long* cursor, uint32_t* ndst, LabelT* nlab) {
+  GRID_STRIDE(i, k) {
+    const uint64_t q = atomicAdd(&cursor[is[i]], 1ull);
+    ndst[q] = it[i];
+    nlab[q] = (LabelT)il[i];
+  }
+}
+
+__global__ void k_bits_list(const uint32_t* bits, uint64_t words, uint32_t* list, unsigned long long* count) {
+  GRID_STRIDE(w, words) {
+    uint32_t m = bits[w];
+    if (!m) continue;
+    const unsigned long long b = atomicAdd(count, (unsigned long long)__popc(m));
+    uint32_t j = 0;
+    while (m) {
+      const uint32_t x = __ffs(m) - 1;
+      m &= m - 1;
+      list[b + j++] = (uint32_t)((w << 5) + x);
+    }
+  }
+}
+
+template <typename LabelT>
+Status move_edges(Store& s, const uint64_t* noff, const uint32_t* touched, const uint32_t* claimed,
+                  const uint32_t* tlist, uint64_t ntouched, unsigned long long* cursor, const uint32_t* is,
+                  const uint32_t* it, const uint32_t* il, uint64_t nins, uint32_t* ndst, LabelT* nlab) {
+  const uint64_t* off = ptr<uint64_t>(s.offsets);
+  const uint32_t* dst = ptr<uint32_t>(s.dst);
+  const LabelT* lab = static_cast<const LabelT*>(s.elabel.p);
+  const uint64_t n_small = s.class_start[kClassWarp];
+  if (n_small)
+    k_move_small<LabelT><<<grid(s, n_small, 256), 256, 0, s.stream>>>(n_small, off, noff, touched, dst, lab, ndst,
+                                                                       nlab);
+  if (s.n_alive > n_small)
+    k_move_large<LabelT><<<grid(s, (s.n_alive - n_small) * 32, 256), 256, 0, s.stream>>>(
+        n_small, s.n_alive, off, noff, touched, dst, lab, ndst, nlab);
+  if (ntouched)
+    k_rewrite_touched<LabelT><<<grid(s, ntouched * 32, 256), 256, 0, s.stream>>>(tlist, ntouched, off, noff, claimed,
+                                                                                 dst, lab, ndst, nlab, cursor);
+  if (nins)
+    k_place_inserts_internal<LabelT><<<grid(s, nins, 256), 256, 0, s.stream>>>(nins, is, it, il, cursor, ndst, nlab);
+  return cuda_check(cudaGetLastError(), "move edges");
+}
+
+// Try the in-place path.  *taken = false leaves the graph as it was.
+Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, const uint32_t* it, const uint32_t* il,
+                      const uint32_t* ds, const uint32_t* dt, const uint32_t* dl, uint64_t* missing_out,
+                      bool* taken) {
+  *taken = false;
+  const uint64_t n = s.n, m = s.m, ni = bt->n_ins, nd = bt->n_del;
+  if (bt->n_add_nodes || bt->n_del_nodes || !n || !s.has_graph || s.budget) return Status::Ok();
+  if (ni + nd > std::max<uint64_t>(m / 16, 1ull << 16)) return Status::Ok();  // large batches relabel
+  Status st;
+  Buf* B = s.inplace;
+  enum { IDS, DELTA, TOUCH, CLAIM, DEG, CUR, LIST, NDST, NLAB, SC, TMP };
+  const uint64_t words = n / 32 + 1, cwords = m / 32 + 1;
+  if (!(st = ensure(s, B[IDS], std::max<uint64_t>(2 * ni + 2 * nd, 1) * 4)).ok()) return st;
+  if (!(st = ensure(s, B[DELTA], n * 4)).ok()) return st;
+  if (!(st = ensure(s, B[TOUCH], words * 4)).ok()) return st;
+  if (!(st = ensure(s, B[CLAIM], cwords * 4)).ok()) return st;
+  if (!(st = ensure(s, B[DEG], (n + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, B[SC], 64)).ok()) return st;
+  uint32_t* ids = ptr<uint32_t>(B[IDS]);
+  uint32_t *isp = ids, *itp = ids + ni, *dsp = ids + 2 * ni, *dtp = ids + 2 * ni + nd;
+  int* delta = ptr<int>(B[DELTA]);
+  uint32_t* touched = ptr<uint32_t>(B[TOUCH]);
+  uint32_t* claimed = ptr<uint32_t>(B[CLAIM]);
+  unsigned long long* deg = ptr<unsigned long long>(B[DEG]);
+  unsigned long long* sc = ptr<unsigned long long>(B[SC]);
+  cudaMemsetAsync(delta, 0, n * 4, s.stream);
+  cudaMemsetAsync(touched, 0, words * 4, s.stream);
+  cudaMemsetAsync(claimed, 0, cwords * 4, s.stream);
+  cudaMemsetAsync(sc, 0, 64, s.stream);
+  const uint32_t* o2p = ptr<uint32_t>(s.o2p);
+  if (ni) {
+    k_to_internal_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, is, isp);
+    k_to_internal_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, it, itp);
+    k_count_inserts_internal<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, isp, delta, touched);
+  }
+  if (nd) {
+    k_to_internal_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, ds, dsp);
+    k_to_internal_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, dt, dtp);
+    if (s.label8)
+      k_claim_deletes<uint8_t><<<grid(s, nd * 32, 256), 256, 0, s.stream>>>(
+          nd, dsp, dtp, dl, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel), claimed, delta,
+          touched, sc);
+    else
+      k_claim_deletes<uint32_t><<<grid(s, nd * 32, 256), 256, 0, s.stream>>>(
+          nd, dsp, dtp, dl, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel), claimed, delta,
+          touched, sc);
+  }
+  unsigned int* moved = reinterpret_cast<unsigned int*>(sc + 1);
+  unsigned int* maxlab = moved + 1;
+  k_new_degrees<<<grid(s, n, 256), 256, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), delta, deg, moved);
+  if (ni) k_max32<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, il, maxlab);
+  uint64_t h[2] = {0, 0};
+  st = cuda_check(cudaGetLastError(), "in-place batch");
+  if (st.ok()) st = cuda_check(cudaMemcpyAsync(h, sc, 16, cudaMemcpyDeviceToHost, s.stream), "in-place batch");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  const uint32_t moved_v = (uint32_t)h[1], maxlab_v = (uint32_t)(h[1] >> 32);
+  if (moved_v) return Status::Ok();  // a node changes degree class: relabel
+  if (s.label8 && maxlab_v >= 256) return Status::Ok();  // wider labels: relabel
+  // a deletion with no stored copy may name an edge inserted by this batch
+  // (insertions come first): the general path decides those
+  if (h[0]) return Status::Ok();
+  const uint64_t missing = 0;
+  const uint64_t m1 = m + ni - (nd - missing);
+  // new offsets, touched list, then the edges
+  if (!(st = scan_u64(s, deg, n + 1, nullptr, B[TMP], nullptr)).ok()) return st;
+  if (!(st = ensure(s, B[CUR], (n + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, B[LIST], n * 4)).ok()) return st;
+  if (!(st = ensure(s, B[NDST], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
+  if (!(st = ensure(s, B[NLAB], std::max<uint64_t>(m1, 1) * (s.label8 ? 1 : 4))).ok()) return st;
+  cudaMemsetAsync(sc + 2, 0, 8, s.stream);
+  k_bits_list<<<grid(s, words, 256), 256, 0, s.stream>>>(touched, words, ptr<uint32_t>(B[LIST]), sc + 2);
+  uint64_t ntouched = 0;
+  st = cuda_check(cudaMemcpyAsync(&ntouched, sc + 2, 8, cudaMemcpyDeviceToHost, s.stream), "touched");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  unsigned long long* cur = ptr<unsigned long long>(B[CUR]);
+  if (s.label8)
+    st = move_edges<uint8_t>(s, reinterpret_cast<const uint64_t*>(deg), touched, claimed, ptr<uint32_t>(B[LIST]),
+                             ntouched, cur, isp, itp, il, ni, ptr<uint32_t>(B[NDST]), ptr<uint8_t>(B[NLAB]));
+  else
+    st = move_edges<uint32_t>(s, reinterpret_cast<const uint64_t*>(deg), touched, claimed, ptr<uint32_t>(B[LIST]),
+                              ntouched, cur, isp, itp, il, ni, ptr<uint32_t>(B[NDST]), ptr<uint32_t>(B[NLAB]));
+  if (!st.ok()) return st;
+  // the new table replaces the old one (buffers swap, so both stay allocated)
+  std::swap(s.dst, B[NDST]);
+  std::swap(s.elabel, B[NLAB]);
+  std::swap(s.offsets, B[DEG]);
+  s.m = m1;
+  if (maxlab_v) {
+    uint32_t lb = 1;
+    while (lb < 32 && (maxlab_v >> lb)) ++lb;
+    s.label_bits = std::max(s.label_bits, lb);
+  }
+  for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
+  s.has_levels = false;
+  s.many.valid = false;
+  if (!(st = build_chunk_lists(s, false)).ok()) return st;
+  *taken = true;
+  if (missing_out) *missing_out = missing;
+  return cuda_check(cudaStreamSynchronize(s.stream), "in-place batch");
+}
+
 Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (!bt) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch is NULL");
   if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
@@ -424,6 +721,12 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (!st.ok()) return st;
   if (e & kBadId) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch names a node id >= num_nodes");
   if (e & kDeadEnd) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch touches a deleted node");
+  {
+    bool taken = false;
+    if (!(st = apply_in_place(s, bt, is, it, il, ds, dt, dl, missing_out, &taken)).ok()) return st;
+    s.mt.in_place = taken ? 1 : 0;
+    if (taken) return Status::Ok();
+  }
 
   // 1. combined CSR by original source: stored edges, then inserted ones
   const uint64_t m0 = s.m, mc = m0 + bt->n_ins;

@@ -77,7 +77,7 @@ class KernelTimes(ctypes.Structure):
 
 class UpdateInfo(ctypes.Structure):
     _fields_ = [("incremental", ctypes.c_int), ("reason", ctypes.c_int),
-                ("frontier_nodes", ctypes.c_uint64), ("levels", ctypes.c_uint64)]
+                ("frontier_nodes", ctypes.c_uint64), ("levels", ctypes.c_uint64), ("in_place", ctypes.c_int)]
 
 
 MAINT_REASONS = {0: "incremental", 1: "off", 2: "no_store", 3: "frontier", 4: "capacity", 5: "deletes"}
@@ -456,7 +456,8 @@ class KBisim:
         ui = UpdateInfo()
         self._check(self._lib.kbisim_get_update_info(self._h, ctypes.byref(ui)))
         return {"incremental": bool(ui.incremental), "reason": MAINT_REASONS.get(int(ui.reason), str(ui.reason)),
-                "frontier_nodes": int(ui.frontier_nodes), "levels": int(ui.levels)}
+                "frontier_nodes": int(ui.frontier_nodes), "levels": int(ui.levels),
+                "in_place": bool(ui.in_place)}
 
     def round_stats(self, r: int) -> dict:
         st = RoundStats()

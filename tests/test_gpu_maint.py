@@ -61,6 +61,44 @@ def test_incremental_updates_equal_the_oracle(early_stop):
     assert all(p["frontier_nodes"] < n for p in paths if p["incremental"])
 
 
+def test_in_place_batches_on_a_large_graph():
+    """Batches of edge inserts and deletes on the 250K-node power-law graph,
+    applied to the edge table in place (every touched node keeps its degree
+    class, hubs included), with and without incremental maintenance."""
+    rng = np.random.default_rng(12)
+    g = synth.config_single_large(scale=1 / 64, seed=6)
+    mg = _mg(g)
+    k = 3
+    with KBisim() as kb, KBisim(maintain=False) as plain:
+        kb.build(g, k)
+        plain.build(g, k)
+        d = np.diff(g.offsets.astype(np.int64))
+        hubs = np.nonzero(d > 5000)[0]
+        assert hubs.size > 0
+        for step in range(4):
+            # insertions into distinct nodes of out-degree 10..12 (at most one
+            # per batch and four in all, so they stay in class 9..16) and
+            # hubs; deletions of hub edges (hubs stay hubs)
+            small = np.nonzero((d >= 10) & (d <= 12))[0]
+            s_ins = np.concatenate([rng.choice(small, 40, replace=False), rng.choice(hubs, 10)]).astype(np.uint32)
+            ins = (s_ins, rng.integers(0, g.num_nodes, 50).astype(np.uint32), rng.integers(0, 32, 50).astype(np.uint32))
+            s, dd, l = mg.coo()
+            cand_e = np.nonzero(np.isin(s, hubs))[0]
+            pick = rng.choice(cand_e, 50, replace=False)
+            dels = (s[pick], dd[pick], l[pick])
+            mg.apply(ins=list(zip(*ins)), dels=list(zip(*dels)))
+            ref = mg.kbisim(k)
+            r1, miss = kb.update(k, ins=ins, dels=dels)
+            assert miss == 0
+            info = kb.update_info()
+            assert info["in_place"], info
+            r2, _ = plain.update(k, ins=ins, dels=dels)
+            assert plain.update_info()["in_place"]
+            assert_same(r1, kb.all_pids(k), ref)
+            assert_same(r2, plain.all_pids(k), ref)
+            d = d + np.bincount(s_ins, minlength=g.num_nodes)
+
+
 def test_tables_4_and_5_on_the_frontier_path():
     """The paper's Add_Edges examples: Figure 1 plus edge (2, l, 7) with node 7
     added (Table 4), and plus edge (6, l, 5) (Table 5), each as an update of a
