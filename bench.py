@@ -105,6 +105,9 @@ def parse():
                         "streams; update: maintenance batches on the 16M/256M graph, incremental "
                         "against recomputation")
     p.add_argument("--batch", type=int, default=1000, help="edges per maintenance batch (update)")
+    p.add_argument("--graph", default="powerlaw", choices=["powerlaw", "uniform"],
+                   help="update: the 16M/256M power-law graph, or a 6.4M-node / 64M-edge graph with the "
+                        "100K/1M generator's distributions (uniform targets), the largest serving graph")
     p.add_argument("--k", type=int, default=3, help="levels kept by maintenance (update)")
     p.add_argument("--requests", type=int, default=120, help="requests per arrival rate (serve)")
     return p.parse_args()
@@ -344,7 +347,17 @@ def run_update(args):
     from paper_1210_0748_gb300.kbisim import KBisim
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
-    g, cfg = workload(args.scale)
+    if args.graph == "uniform":
+        from paper_1210_0748_gb300 import synth
+        m = int(64_000_000 * args.scale)
+        g = synth.uniform_zipf_graph(m // 10, m, zipf_s=2.0, dmax=10_000, node_labels=8, edge_labels=4)
+        cfg = {"workload": "graph of %d nodes, %d edges: out-degree Zipf(2.0) capped at 10K, uniform targets, "
+                           "8 node labels and 4 edge labels uniform" % (g.num_nodes, g.num_edges),
+               "nodes": g.num_nodes, "edges": g.num_edges}
+        n_labels = 4
+    else:
+        g, cfg = workload(args.scale)
+        n_labels = 32
     rng = np.random.default_rng(77)
     src = g.src()
     nb = max(2, args.batch)
@@ -352,7 +365,7 @@ def run_update(args):
     for _ in range(args.warmup + args.steps):
         ni, nd = nb // 2, nb - nb // 2
         ins = (rng.integers(0, g.num_nodes, ni).astype(np.uint32), rng.integers(0, g.num_nodes, ni).astype(np.uint32),
-               rng.integers(0, 32, ni).astype(np.uint32))
+               rng.integers(0, n_labels, ni).astype(np.uint32))
         e = rng.integers(0, g.num_edges, nd)
         dels = (src[e], g.dst[e], g.edge_label[e].astype(np.uint32))
         batches.append((ins, dels))

@@ -233,7 +233,8 @@ typedef struct {
  * the level's signature store, which keeps labels of unchanged signatures.
  * The update switches back to a full recomputation (Section 4, "When to
  * switch back to Algorithm 1") when a level's frontier holds more than a
- * quarter of the nodes (and more than 4096), when a store runs out of room, when the batch deletes
+ * quarter of the nodes (and more than 4096; later batches of at least that
+ * many edges at the same k then recompute at once), when a store runs out of room, when the batch deletes
  * nodes, or when k exceeds the levels the stores hold; kbisim_update_info
  * tells which path the last update took.  *missing_deletes (may be NULL)
  * receives the number of edge deletions that named no edge.
@@ -318,6 +319,12 @@ uint64_t kbisim_num_edges(const kbisim_handle *h);
 /* Device bytes the handle holds now (graph, levels, scratch, spares); the
  * quantity options.hbm_budget_bytes bounds.  0 for NULL. */
 uint64_t kbisim_device_bytes(const kbisim_handle *h);
+
+/* Change the handle's HBM budget (options.hbm_budget_bytes; 0 = none) for
+ * later calls.  A budget below what the handle holds now is allowed: calls
+ * that would allocate fail with KBISIM_ERR_BUDGET until memory is released.
+ * The paper has no counterpart (a serving loop sets it when it admits work). */
+int kbisim_set_hbm_budget(kbisim_handle *h, uint64_t bytes);
 
 /* Per-kernel device times summed since the last kbisim_reset_times(). */
 int kbisim_get_kernel_times(const kbisim_handle *h, kbisim_kernel_times *out);

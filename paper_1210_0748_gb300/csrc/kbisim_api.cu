@@ -266,7 +266,7 @@ Status exclusive_scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned 
 // budget, between loads) the device buffers stay allocated for the next graph.
 void free_graph(Store& s, bool keep_buffers) {
   Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.p2o, &s.o2p, &s.mid_chunks, &s.hub_bits,
-                 &s.hub_bbase, &s.hub_cap, &s.hub_tbase, &s.hub_chunks, &s.sigkey, &s.ucnt, &s.hash, &s.table,
+                 &s.hub_bbase, &s.hub_cap, &s.hub_tbase, &s.hub_chunks, &s.hub_cstart, &s.sigkey, &s.ucnt, &s.hash, &s.table,
                  &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.hbits, &s.member, &s.alone, &s.hword, &s.bsum,
                  &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_mode, &s.hub_force, &s.hub_err, &s.hub_tmp, &s.alive_o,
                  &s.rl_tcnt, &s.rl_hot, &s.rl_ost};
@@ -822,6 +822,12 @@ uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
 uint64_t kbisim_num_edges(const kbisim_handle* h) { return h ? h->s.m : 0; }
 uint64_t kbisim_device_bytes(const kbisim_handle* h) { return h ? (uint64_t)h->s.bytes_held : 0; }
 
+int kbisim_set_hbm_budget(kbisim_handle* h, uint64_t bytes) {
+  if (!h) return KBISIM_ERR_INVALID_ARG;
+  h->s.budget = bytes;
+  return KBISIM_OK;
+}
+
 int kbisim_get_update_info(const kbisim_handle* h, kbisim_update_info* out) {
   if (!h || !out) return KBISIM_ERR_INVALID_ARG;
   out->incremental = h->s.mt.incremental;
@@ -870,10 +876,16 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
   s.mt.frontier_nodes = 0;
   s.mt.levels = 0;
   s.mt.in_place = 0;
+  const uint64_t batch_edges = b ? b->n_ins + b->n_del : 0;
+  const bool suspended = s.mt.suspend_edges && k == s.mt.suspend_k && batch_edges >= s.mt.suspend_edges;
   if (!s.maintain) {
     s.mt.reason = KBISIM_MAINT_OFF;
   } else if (b && b->n_del_nodes) {
     s.mt.reason = KBISIM_MAINT_DELETES;
+  } else if (suspended) {
+    // a batch at least this large already switched back at this k: recompute
+    s.mt.reason = KBISIM_MAINT_FRONTIER;
+    kb::maint_release(s);
   } else {
     // stores made from the current levels when there are none for this k yet
     if ((!s.mt.valid || k > s.mt.k) && s.has_levels && (s.k_requested >= k || s.stable)) {
@@ -887,8 +899,16 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
     st = kb::apply_batch(s, b, &missing);
   }
   if (st.ok()) st = s.mt.incremental ? kb::finish_incremental(s, k, out) : kb::refine(s, k, out);
-  // after a full recomputation, stores for the next update
-  if (st.ok() && s.maintain && !s.mt.incremental && s.has_levels && !kb::maint_build(s, k).ok())
+  if (s.mt.incremental) {
+    s.mt.suspend_edges = 0;
+  } else if (s.mt.reason == KBISIM_MAINT_FRONTIER) {
+    s.mt.suspend_edges = std::max<uint64_t>(batch_edges, 1);
+    s.mt.suspend_k = k;
+  }
+  // after a full recomputation, stores for the next update (not while large
+  // batches are known to switch back: the next smaller batch makes them)
+  if (st.ok() && s.maintain && !s.mt.incremental && s.has_levels && s.mt.reason != KBISIM_MAINT_FRONTIER &&
+      !kb::maint_build(s, k).ok())
     kb::maint_release(s);
   if (st.ok() && missing_deletes) *missing_deletes = missing;
   return finish(h, st);

@@ -198,12 +198,19 @@ struct MaintState {
   Buf src;                          // uint32 staged sources of the batch's edges
   Buf misc;                         // uint64 scalars
   Buf woff;                         // uint64 [n + 1] pool offsets of the heads' signatures (build)
+  Buf cmp;                          // hash set comparing one long signature with a stored one
+  Buf cmp_info;                     // uint64 x 3 per pending comparison
+  Buf big;                          // uint2 (node, label): long signatures copied by their own CTA
   // last update
   int incremental = 0;              // 1 = frontier path, 0 = full recomputation
   int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)
   uint64_t frontier_nodes = 0;      // nodes signed over all levels
   uint64_t levels = 0;              // levels processed
   int in_place = 0;                 // the batch was applied to the edge table in place
+  // after a switch back for a large frontier: batches of at least this many
+  // edges (same k) recompute at once, without stores (0 = none)
+  uint64_t suspend_edges = 0;
+  uint32_t suspend_k = 0;
 };
 
 struct Store;
@@ -254,6 +261,7 @@ struct Store {
   Buf hub_cap;                 // uint32 [n_hub]  key words a bucket of this hub can hold
   Buf hub_tbase;               // uint64 [n_hub]  start of the hub's buckets in hub_tmp
   Buf hub_chunks;              // uint4 [n_chunks] (hub index, begin lo, begin hi, length)
+  Buf hub_cstart;              // uint32 [n_hub + 1] first chunk of each hub
   uint64_t n_hub_chunks = 0;
   uint64_t hub_tmp_words = 0;  // key words of all hub buckets
   uint64_t n_hub_buckets = 0;
@@ -306,7 +314,7 @@ struct Store {
   Buf rl_tcnt, rl_hot, rl_ost; // relabelling temporaries
   static constexpr int kUpdBufsN = 24;
   Buf upd[kUpdBufsN];          // temporaries of a maintenance batch (kbisim_update)
-  static constexpr int kInplaceBufsN = 11;
+  static constexpr int kInplaceBufsN = 15;
   Buf inplace[kInplaceBufsN];  // a batch applied in place: claims, degrees, the other edge table
   Buf d_err;                   // uint32 error flags
   Buf d_scalars;               // uint64 [16] small device counters

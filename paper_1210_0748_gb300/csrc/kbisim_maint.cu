@@ -168,7 +168,14 @@ __device__ bool store_slot(const StoreArgs& a, uint64_t h, uint32_t b) {
 }
 
 // The warp stores node p's signature under label b (all lanes take part).
-__device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p, uint32_t b) {
+// Signatures of more than kInlineCopy elements are only reserved here and
+// listed in `big` (node, pool offset); k_copy_big copies them before any
+// comparison reads them (only signatures of at most 32 elements are compared
+// inside k_lookup, and those are copied here, before their slot is named).
+constexpr uint32_t kInlineCopy = 32;
+
+__device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p, uint32_t b, uint2* big,
+                                unsigned long long* n_big) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t U = g.ucnt[p];
   unsigned long long base = 0;
@@ -178,8 +185,12 @@ __device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p
     if (lane == 0) atomicOr(a.err, 1u);
     return;
   }
-  const uint64_t* src = g.sigkey + g.off[p];
-  for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
+  if (U <= kInlineCopy) {
+    const uint64_t* src = g.sigkey + g.off[p];
+    for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
+  } else if (lane == 0) {
+    big[atomicAdd(n_big, 1ull)] = make_uint2((uint32_t)p, b);
+  }
   if (lane == 0) {
     a.sfirst[b] = g.prev[p];
     a.scount[b] = U;
@@ -190,27 +201,44 @@ __device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p
   if (lane == 0 && !store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
 }
 
+// Element words of the long new signatures (one CTA per signature).
+__global__ void k_copy_big(StoreArgs a, NodeSig g, const uint2* big, uint64_t n_big) {
+  for (uint64_t q = blockIdx.x; q < n_big; q += gridDim.x) {
+    const uint2 e = big[q];
+    const uint32_t U = a.scount[e.y];
+    const uint64_t* src = g.sigkey + g.off[e.x];
+    unsigned long long* dstp = a.pool + a.soff[e.y];
+    for (uint32_t i = threadIdx.x; i < U; i += blockDim.x) dstp[i] = src[i];
+  }
+}
+
 // Build: the heads of every label (smallest original id) store their
 // signatures under their canonical id, at pool offsets from a prefix sum of
 // the heads' element counts (woff).  One warp per node.
+constexpr uint32_t kBuildInlineCopy = 8;  // longer signatures: k_copy_big, one CTA each
+
+// One thread per node: a head (smallest original id of its label) stores its
+// signature's first component, count and offset, copies short signatures
+// itself, lists long ones for k_copy_big, and names its label in the table.
 __global__ void k_store_heads(StoreArgs a, NodeSig g, uint64_t n_alive, const uint32_t* p2o, const uint32_t* lab,
-                              const uint32_t* minid, const unsigned long long* woff) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; p < n_alive; p += warps) {
+                              const uint32_t* minid, const unsigned long long* woff, uint2* big,
+                              unsigned long long* n_big) {
+  GRID_STRIDE(p, n_alive) {
     const uint32_t o = p2o[p];
     const uint32_t b = lab[o];
     if (minid[b] != o) continue;
     const uint32_t U = g.ucnt[p];
     const unsigned long long base = woff[p];
-    const uint64_t* src = g.sigkey + g.off[p];
-    for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
-    if (lane == 0) {
-      a.sfirst[b] = g.prev[p];
-      a.scount[b] = U;
-      a.soff[b] = base;
-      if (!store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
+    if (U <= kBuildInlineCopy) {
+      const uint64_t* src = g.sigkey + g.off[p];
+      for (uint32_t i = 0; i < U; ++i) a.pool[base + i] = src[i];
+    } else {
+      big[atomicAdd(n_big, 1ull)] = make_uint2((uint32_t)p, b);
     }
+    a.sfirst[b] = g.prev[p];
+    a.scount[b] = U;
+    a.soff[b] = base;
+    if (!store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
   }
 }
 
@@ -251,6 +279,8 @@ struct LookupArgs {
   uint32_t* newlab;         // per node (internal id): the label found
   uint4* pend;              // (head index, label, slot lo, slot hi)
   unsigned long long* n_pend;
+  uint2* big;               // new signatures copied by k_copy_big (node, label)
+  unsigned long long* n_big;
 };
 
 __global__ void k_lookup(StoreArgs a, NodeSig g, LookupArgs l) {
@@ -287,7 +317,7 @@ __global__ void k_lookup(StoreArgs a, NodeSig g, LookupArgs l) {
     uint32_t b = 0;
     if (lane == 0) b = (uint32_t)atomicAdd(&a.ctr[0], 1ull);
     b = __shfl_sync(kFullMask, b, 0);
-    store_signature(a, g, p, b);
+    store_signature(a, g, p, b, l.big, l.n_big);
     if (lane == 0) l.newlab[p] = b;
   }
 }
@@ -305,6 +335,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeS
     const uint4 e = l.pend[q];
     const uint32_t p = l.heads[e.x], b = e.y;
     const uint32_t U = g.ucnt[p];
+    if (U > kCmpChunk) continue;  // compared by k_big_* through a set in global memory
     const uint64_t* mine = g.sigkey + g.off[p];
     const unsigned long long* stored = a.pool + a.soff[b];
     uint32_t found = 0;
@@ -355,6 +386,67 @@ __global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeS
     }
     __syncthreads();
   }
+}
+
+// Long signatures (more than kCmpChunk elements), one pair at a time over the
+// whole grid: the stored elements go into a hash set in global memory of 2U
+// slots, then the node's elements are looked up.
+__global__ void k_big_insert(const unsigned long long* stored, uint32_t U, unsigned long long* set, uint64_t smask,
+                             unsigned int* flags) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < U; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = stored[i];
+    if (k == kEmpty64) {
+      flags[0] = 1u;
+      continue;
+    }
+    uint64_t s = mix64(k) & smask;
+    for (uint64_t t = 0; t <= smask; ++t) {
+      const unsigned long long old = atomicCAS(&set[s], kEmpty64, k);
+      if (old == kEmpty64 || old == k) break;
+      s = (s + 1) & smask;
+    }
+  }
+}
+
+__global__ void k_big_lookup(const uint64_t* mine, uint32_t U, const unsigned long long* set, uint64_t smask,
+                             unsigned int* flags) {
+  unsigned int found = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < U; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = mine[i];
+    if (k == kEmpty64) {
+      found += flags[0];
+      continue;
+    }
+    uint64_t s = mix64(k) & smask;
+    for (uint64_t t = 0; t <= smask; ++t) {
+      const unsigned long long cur = set[s];
+      if (cur == k) {
+        ++found;
+        break;
+      }
+      if (cur == kEmpty64) break;
+      s = (s + 1) & smask;
+    }
+  }
+  found = __reduce_add_sync(kFullMask, found);
+  if ((threadIdx.x & 31) == 0 && found) atomicAdd(&flags[1], found);
+}
+
+// Per pending pair: element count, the node's first element word, the
+// stored signature's first pool word (for the host to route long pairs).
+__global__ void k_pending_info(const uint4* pend, const uint32_t* heads, uint64_t np, const uint32_t* ucnt,
+                               const uint64_t* off, const unsigned long long* soff, unsigned long long* info) {
+  GRID_STRIDE(q, np) {
+    const uint4 e = pend[q];
+    const uint32_t p = heads[e.x];
+    info[3 * q] = ucnt[p];
+    info[3 * q + 1] = off[p];
+    info[3 * q + 2] = soff[e.y];
+  }
+}
+
+__global__ void k_big_result(const unsigned int* flags, uint32_t U, uint32_t* match) {
+  *match = flags[1] == U ? 1u : 0u;
 }
 
 // After a long compare: matched heads take the label, the others probe on
@@ -440,6 +532,18 @@ __global__ void k_frontier_large(uint64_t p0, uint64_t p1, const uint64_t* off, 
     if (__any_sync(kFullMask, hit) && lane == 0) set_bit(next, p);
   }
 }
+// Hubs, one CTA per chunk of the hub's edges.
+__global__ void k_frontier_hub(const uint4* chunks, uint64_t nchunks, uint64_t hub_first, const uint32_t* dst,
+                               const uint32_t* changed, uint32_t* next) {
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint4 q = chunks[c];
+    const uint64_t b = ((uint64_t)q.z << 32) | q.y;
+    bool hit = false;
+    for (uint32_t i = threadIdx.x; i < q.w; i += blockDim.x) hit |= bit(changed, dst[b + i]);
+    if (__syncthreads_or(hit) && threadIdx.x == 0) set_bit(next, hub_first + q.x);
+  }
+}
+
 __global__ void k_or3(uint64_t words, const uint32_t* a, const uint32_t* b, uint32_t* out) {
   GRID_STRIDE(w, words) out[w] |= a[w] | b[w];
 }
@@ -588,7 +692,7 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = scan_u64(s, reinterpret_cast<uint64_t*>(woff), n + 1)).ok()) return st;
   uint64_t words = 0;
   if (!(st = sync_read(s, &words, woff + n, 8, "store size")).ok()) return st;
-  L.pcap = 2 * words + (16u << 20);  // room for the signatures later updates add
+  L.pcap = 4 * words + (64u << 20);  // room for the signatures later updates add
   L.tcap = pow2_at_least(2 * L.lcap);
   if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
   if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
@@ -602,9 +706,20 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   uint64_t c0[2] = {labels, words};
   if (!(st = cuda_check(cudaMemcpyAsync(L.ctr.p, c0, 16, cudaMemcpyHostToDevice, s.stream), "store")).ok()) return st;
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
-  k_store_heads<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(store_args(s, L), node_sig(s), na,
+  const uint64_t nbig = std::max<uint64_t>(s.n_alive - std::min(s.n_alive, s.class_start[kSmallClasses - 3]), 1);
+  if (!(st = ensure(s, m.big, nbig * sizeof(uint2))).ok()) return st;
+  unsigned long long* sc = ptr<unsigned long long>(m.misc);
+  cudaMemsetAsync(sc + 12, 0, 8, s.stream);
+  k_store_heads<<<grid_for(s, na, kThreads), kThreads, 0, s.stream>>>(store_args(s, L), node_sig(s), na,
                                                                 ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
-                                                                ptr<uint32_t>(m.minid), woff);
+                                                                ptr<uint32_t>(m.minid), woff, ptr<uint2>(m.big),
+                                                                sc + 12);
+  uint64_t hb = 0;
+  if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
+  if (!(st = sync_read(s, &hb, sc + 12, 8, "store heads")).ok()) return st;
+  if (hb)
+    k_copy_big<<<(unsigned)std::min<uint64_t>(hb, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
+        store_args(s, L), node_sig(s), ptr<uint2>(m.big), hb);
   uint32_t e = 0;
   if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
   if (!(st = sync_read(s, &e, s.d_err.p, 4, "store heads")).ok()) return st;
@@ -634,10 +749,11 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   // heads of the frontier groups (rep[p] == p) look up S_j; scratch of the
   // lookup: pending long compares, restart slots, results, heads, retries
   const size_t cnt = std::max<uint64_t>(count, 1);
-  if (!(st = ensure(s, m.pend, cnt * (sizeof(uint4) + 8 + 4 + 4 + 4))).ok()) return st;
+  if (!(st = ensure(s, m.pend, cnt * (sizeof(uint4) + 8 + 8 + 4 + 4 + 4))).ok()) return st;
   uint4* pend = ptr<uint4>(m.pend);
   unsigned long long* start = reinterpret_cast<unsigned long long*>(pend + cnt);
-  uint32_t* match = reinterpret_cast<uint32_t*>(start + cnt);
+  uint2* big = reinterpret_cast<uint2*>(start + cnt);
+  uint32_t* match = reinterpret_cast<uint32_t*>(big + cnt);
   uint32_t* heads = match + cnt;
   uint32_t* retry = heads + cnt;
   unsigned long long* sc = ptr<unsigned long long>(m.misc);
@@ -654,19 +770,50 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   la.newlab = ptr<uint32_t>(m.newlab);
   la.pend = pend;
   la.n_pend = sc + 1;
+  la.big = big;
+  la.n_big = sc + 3;
   const StoreArgs sa = store_args(s, L);
   const NodeSig ns = node_sig(s);
   for (int pass = 0; la.count; ++pass) {
     if (pass > 64) return Status::Err(KBISIM_ERR_TIMEOUT, "signature lookup made no progress");
-    cudaMemsetAsync(sc + 1, 0, 16, s.stream);
+    cudaMemsetAsync(sc + 1, 0, 24, s.stream);  // [1] pending, [2] retries, [3] long copies
     k_lookup<<<(unsigned)std::min<uint64_t>((la.count + 7) / 8, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(sa, ns,
                                                                                                             la);
-    uint64_t np = 0;
+    uint64_t hv[3] = {0, 0, 0};
     if (!(st = cuda_check(cudaGetLastError(), "lookup")).ok()) return st;
-    if (!(st = sync_read(s, &np, sc + 1, 8, "lookup")).ok()) return st;
+    if (!(st = sync_read(s, hv, sc + 1, 24, "lookup")).ok()) return st;
+    if (hv[2])
+      k_copy_big<<<(unsigned)std::min<uint64_t>(hv[2], (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(sa, ns, big,
+                                                                                                     hv[2]);
+    const uint64_t np = hv[0];
     if (!np) break;
     k_long_compare<<<(unsigned)std::min<uint64_t>(np, (uint64_t)s.sms * 4), kCmpThreads, 0, s.stream>>>(sa, ns, la, np,
                                                                                                       match);
+    // pairs above kCmpChunk elements: one at a time through a set in global memory
+    if (!(st = ensure(s, m.cmp_info, np * 24)).ok()) return st;
+    k_pending_info<<<grid_for(s, np, kThreads), kThreads, 0, s.stream>>>(
+        pend, heads, np, ptr<uint32_t>(s.ucnt), ptr<uint64_t>(s.offsets), ptr<unsigned long long>(L.soff),
+        ptr<unsigned long long>(m.cmp_info));
+    std::vector<uint64_t> info(3 * np);
+    if (!(st = cuda_check(cudaGetLastError(), "pending")).ok()) return st;
+    if (!(st = sync_read(s, info.data(), m.cmp_info.p, np * 24, "pending")).ok()) return st;
+    for (uint64_t q = 0; q < np; ++q) {
+      const uint32_t U = (uint32_t)info[3 * q];
+      if (U <= (uint32_t)kCmpChunk) continue;
+      uint64_t slots = 1024;
+      while (slots < 2ull * U) slots <<= 1;
+      if (!(st = ensure(s, m.cmp, slots * 8 + 64)).ok()) return st;
+      unsigned long long* set = ptr<unsigned long long>(m.cmp);
+      unsigned int* flags = reinterpret_cast<unsigned int*>(set + slots);
+      const uint64_t noff = info[3 * q + 1], soff = info[3 * q + 2];
+      cudaMemsetAsync(set, 0xFF, slots * 8, s.stream);
+      cudaMemsetAsync(flags, 0, 8, s.stream);
+      const unsigned gb = grid_for(s, U, kThreads);
+      k_big_insert<<<gb, kThreads, 0, s.stream>>>(ptr<unsigned long long>(L.pool) + soff, U, set, slots - 1, flags);
+      k_big_lookup<<<gb, kThreads, 0, s.stream>>>(ptr<uint64_t>(s.sigkey) + noff, U, set, slots - 1, flags);
+      k_big_result<<<1, 1, 0, s.stream>>>(flags, U, match + q);
+      if (!(st = cuda_check(cudaGetLastError(), "long compare")).ok()) return st;
+    }
     k_resolve<<<grid_for(s, np, kThreads), kThreads, 0, s.stream>>>(la, np, match, retry, start, sc + 2, L.tcap - 1);
     uint64_t nr = 0;
     if (!(st = cuda_check(cudaGetLastError(), "long compare")).ok()) return st;
@@ -702,7 +849,7 @@ void maint_release(Store& s) {
   }
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff};
+              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big};
   for (Buf* x : b) release(s, *x);
   m.valid = false;
   m.k = 0;
@@ -809,10 +956,15 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
     if (n_small)
       k_frontier_small<<<grid_for(s, n_small, kThreads), kThreads, 0, s.stream>>>(
           n_small, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
-    if (s.n_alive > n_small)
-      k_frontier_large<<<(unsigned)s.sms * 16, kThreads, 0, s.stream>>>(n_small, s.n_alive, ptr<uint64_t>(s.offsets),
+    const uint64_t hub_first = s.class_start[kClassHub];
+    if (hub_first > n_small)
+      k_frontier_large<<<(unsigned)s.sms * 16, kThreads, 0, s.stream>>>(n_small, hub_first, ptr<uint64_t>(s.offsets),
                                                                        ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
                                                                        ptr<uint32_t>(m.fnext));
+    if (s.n_hub_chunks)
+      k_frontier_hub<<<(unsigned)std::min<uint64_t>(s.n_hub_chunks, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
+          ptr<uint4>(s.hub_chunks), s.n_hub_chunks, hub_first, ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
+          ptr<uint32_t>(m.fnext));
     k_or3<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(words, ptr<uint32_t>(m.seeds),
                                                                     ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
     std::swap(m.fmask, m.fnext);

@@ -941,6 +941,10 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
     const uint32_t hub = nx_hub, n = nx_n;
     const uint64_t p = h.first + hub;
     const K* tmp = nx_tmp;
+    if (n == 0) {  // nothing appended (a hub outside a frontier mask): no barrier, no output
+      if (b + gridDim.x < n_buckets) fetch(b + gridDim.x);
+      continue;
+    }
     uint32_t hcap = 64;
     while (hcap < 2 * n && hcap < 2 * kHubUcap) hcap <<= 1;
     {
@@ -2277,7 +2281,9 @@ Status build_chunk_lists(Store& s, bool fresh) {
     if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
     if (!st.ok()) return st;
     std::vector<uint4> chunks;
+    std::vector<uint32_t> cstart(s.n_hub + 1, 0);
     for (uint64_t i = 0; i < s.n_hub; ++i) {
+      cstart[i] = (uint32_t)chunks.size();
       const uint64_t d = hoff[i + 1] - hoff[i];
       uint32_t bits = 0;
       while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
@@ -2295,9 +2301,15 @@ Status build_chunk_lists(Store& s, bool fresh) {
       }
     }
     s.n_hub_chunks = chunks.size();
+    cstart[s.n_hub] = (uint32_t)chunks.size();
     if (!(st = ensure(s, s.hub_chunks, chunks.size() * sizeof(uint4))).ok()) return st;
+    if (!(st = ensure(s, s.hub_cstart, (s.n_hub + 1) * 4)).ok()) return st;
     st = cuda_check(cudaMemcpyAsync(s.hub_chunks.p, chunks.data(), chunks.size() * sizeof(uint4),
                                     cudaMemcpyHostToDevice, s.stream), "hub chunks");
+    if (st.ok())
+      st = cuda_check(cudaMemcpyAsync(s.hub_cstart.p, cstart.data(), (s.n_hub + 1) * 4, cudaMemcpyHostToDevice,
+                                      s.stream), "hub chunks");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "hub chunks");
     if (!st.ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
   }

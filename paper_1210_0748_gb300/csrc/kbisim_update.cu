@@ -400,17 +400,19 @@ __global__ void k_to_internal_ids(uint64_t k, const uint32_t* o2p, const uint32_
 // One warp per deletion: claim the first unclaimed stored copy of (t, l) in
 // the segment of s.  Claims are bits over the edge table.
 template <typename LabelT>
-__global__ void k_claim_deletes(uint64_t k, const uint32_t* ds, const uint32_t* dt, const uint32_t* dl,
+__global__ void k_claim_deletes(uint64_t k, const uint32_t* ds, const uint32_t* dt, const uint32_t* dl, uint64_t n0,
                                 const uint64_t* off, const uint32_t* dst, const LabelT* lab, uint32_t* claimed,
                                 int* delta, uint32_t* touched, unsigned long long* missing) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < k; i += warps) {
     const uint32_t p = ds[i], t = dt[i], l = dl[i];
+    if (p < n0 && off[p + 1] - off[p] > (uint64_t)kBlockMax) continue;  // hubs: k_claim_deletes_hub
     bool done = false;
-    for (uint64_t e0 = off[p]; e0 < off[p + 1] && !done; e0 += 32) {
+    // an added node has no stored edge
+    for (uint64_t e0 = p < n0 ? off[p] : 0, e1 = p < n0 ? off[p + 1] : 0; e0 < e1 && !done; e0 += 32) {
       const uint64_t e = e0 + lane;
-      unsigned cand = __ballot_sync(0xFFFFFFFFu, e < off[p + 1] && dst[e] == t && (uint32_t)lab[e] == l);
+      unsigned cand = __ballot_sync(0xFFFFFFFFu, e < e1 && dst[e] == t && (uint32_t)lab[e] == l);
       while (cand && !done) {
         const int j = __ffs(cand) - 1;
         cand &= cand - 1;
@@ -433,6 +435,58 @@ __global__ void k_claim_deletes(uint64_t k, const uint32_t* ds, const uint32_t* 
   }
 }
 
+// Deletions whose source is a hub: one CTA per deletion scans the hub's
+// segment a block of edges at a time.
+template <typename LabelT>
+__global__ void __launch_bounds__(1024) k_claim_deletes_hub(uint64_t k, const uint32_t* ds, const uint32_t* dt,
+                                                            const uint32_t* dl, uint64_t n0, const uint64_t* off,
+                                                            const uint32_t* dst, const LabelT* lab, uint32_t* claimed,
+                                                            int* delta, uint32_t* touched,
+                                                            unsigned long long* missing) {
+  __shared__ unsigned int done;
+  for (uint64_t i = blockIdx.x; i < k; i += gridDim.x) {
+    const uint32_t p = ds[i], t = dt[i], l = dl[i];
+    if (!(p < n0 && off[p + 1] - off[p] > (uint64_t)kBlockMax)) continue;
+    if (threadIdx.x == 0) done = 0;
+    __syncthreads();
+    const uint64_t e1 = off[p + 1];
+    for (uint64_t e0 = off[p]; e0 < e1; e0 += blockDim.x) {
+      const uint64_t e = e0 + threadIdx.x;
+      const bool cand = e < e1 && dst[e] == t && (uint32_t)lab[e] == l;
+      // candidates take turns in lane order within the block until one claims
+      if (__syncthreads_or(cand)) {
+        for (uint32_t w = 0; w < blockDim.x; w += 32) {
+          if (done) break;
+          if (threadIdx.x >= w && threadIdx.x < w + 32) {
+            unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+            while (m && !done) {
+              const int j = __ffs(m) - 1;
+              m &= m - 1;
+              if ((threadIdx.x & 31) == (uint32_t)j) {
+                const uint64_t ej = e;
+                if (!((atomicOr(&claimed[ej >> 5], 1u << (ej & 31)) >> (ej & 31)) & 1u)) done = 1;
+              }
+              __syncwarp();
+            }
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      if (done) break;
+    }
+    if (threadIdx.x == 0) {
+      if (done) {
+        atomicSub(&delta[p], 1);
+        atomicOr(&touched[p >> 5], 1u << (p & 31));
+      } else {
+        atomicAdd(missing, 1ull);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_count_inserts_internal(uint64_t k, const uint32_t* is, int* delta, uint32_t* touched) {
   GRID_STRIDE(i, k) {
     atomicAdd(&delta[is[i]], 1);
@@ -442,10 +496,10 @@ __global__ void k_count_inserts_internal(uint64_t k, const uint32_t* is, int* de
 
 // Touched nodes whose degree class would change (then the batch is applied by
 // relabelling), and the new degrees of all nodes.
-__global__ void k_new_degrees(uint64_t n, const uint64_t* off, const int* delta, unsigned long long* deg,
+__global__ void k_new_degrees(uint64_t n0, uint64_t n, const uint64_t* off, const int* delta, unsigned long long* deg,
                               unsigned int* class_moved) {
   GRID_STRIDE(p, n) {
-    const uint64_t d0 = off[p + 1] - off[p];
+    const uint64_t d0 = p < n0 ? off[p + 1] - off[p] : 0;
     const int dd = delta[p];
     const uint64_t d1 = (uint64_t)((int64_t)d0 + dd);
     deg[p] = d1;
@@ -507,17 +561,20 @@ __global__ void k_move_large(uint64_t p0, uint64_t p1, const uint64_t* off, cons
 // Touched nodes (one warp each): kept edges first, then a cursor for the
 // inserted ones.
 template <typename LabelT>
-__global__ void k_rewrite_touched(const uint32_t* list, uint64_t count, const uint64_t* off, const uint64_t* noff,
+__global__ void k_rewrite_touched(const uint32_t* list, uint64_t count, uint64_t n0, const uint64_t* off,
+                                  const uint64_t* noff,
                                   const uint32_t* claimed, const uint32_t* dst, const LabelT* lab, uint32_t* ndst,
                                   LabelT* nlab, unsigned long long* cursor) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
     const uint32_t p = list[i];
+    if (p < n0 && off[p + 1] - off[p] > (uint64_t)kBlockMax) continue;  // hubs: k_hub_chunk_move
     uint64_t w = noff[p];
-    for (uint64_t e0 = off[p]; e0 < off[p + 1]; e0 += 32) {
+    const uint64_t a = p < n0 ? off[p] : 0, b = p < n0 ? off[p + 1] : 0;  // added nodes: no stored edge
+    for (uint64_t e0 = a; e0 < b; e0 += 32) {
       const uint64_t e = e0 + lane;
-      const bool keep = e < off[p + 1] && !((claimed[e >> 5] >> (e & 31)) & 1u);
+      const bool keep = e < b && !((claimed[e >> 5] >> (e & 31)) & 1u);
       const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
       if (keep) {
         const uint64_t q = w + __popc(m & ((1u << lane) - 1u));
@@ -554,6 +611,80 @@ __global__ void k_bits_list(const uint32_t* bits, uint64_t words, uint32_t* list
   }
 }
 
+// Hubs, one CTA per chunk of the hub's edges (the chunk list of the current
+// layout): claimed copies in the chunk, then per hub a prefix over its chunks
+// and the cursor for its inserted edges, then the chunk's kept edges at their
+// new places (a block scan of the claim flags).
+constexpr int kHubMoveThreads = 256;
+constexpr int kHubCntBuf = 14;  // index of the per-chunk claim counts in Store::inplace
+
+__global__ void k_hub_chunk_claims(const uint4* chunks, uint64_t nchunks, const uint32_t* claimed, uint32_t* cnt) {
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint4 q = chunks[c];
+    const uint64_t b = ((uint64_t)q.z << 32) | q.y;
+    uint32_t tot = 0;
+    for (uint32_t i0 = 0; i0 < q.w; i0 += kHubMoveThreads) {
+      const uint64_t e = b + i0 + threadIdx.x;
+      const bool cl = i0 + threadIdx.x < q.w && ((claimed[e >> 5] >> (e & 31)) & 1u);
+      tot += __syncthreads_count(cl);
+    }
+    if (threadIdx.x == 0) cnt[c] = tot;
+  }
+}
+
+__global__ void k_hub_chunk_prefix(uint64_t n_hub, uint64_t hub_first, const uint32_t* cstart, const uint4* chunks,
+                                   const uint64_t* off, const uint64_t* noff, uint32_t* cnt,
+                                   unsigned long long* cursor) {
+  for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n_hub; h += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t run = 0;
+    for (uint32_t c = cstart[h]; c < cstart[h + 1]; ++c) {
+      const uint32_t v = cnt[c];
+      cnt[c] = run;
+      run += v;
+    }
+    const uint64_t p = hub_first + h;
+    cursor[p] = noff[p] + (off[p + 1] - off[p]) - run;
+  }
+}
+
+template <typename LabelT>
+__global__ void __launch_bounds__(kHubMoveThreads) k_hub_chunk_move(const uint4* chunks, uint64_t nchunks,
+                                                                   uint64_t hub_first, const uint64_t* off,
+                                                                   const uint64_t* noff, const uint32_t* claimed,
+                                                                   const uint32_t* before, const uint32_t* dst,
+                                                                   const LabelT* lab, uint32_t* ndst, LabelT* nlab) {
+  __shared__ uint32_t wsum[kHubMoveThreads / 32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint4 q = chunks[c];
+    const uint64_t p = hub_first + q.x;
+    const uint64_t b = ((uint64_t)q.z << 32) | q.y;
+    const uint64_t to = noff[p] + (b - off[p]);
+    uint32_t run = before[c];  // claims before this chunk in the hub
+    for (uint32_t i0 = 0; i0 < q.w; i0 += kHubMoveThreads) {
+      const uint32_t i = i0 + threadIdx.x;
+      const uint64_t e = b + i;
+      const bool valid = i < q.w;
+      const bool cl = valid && ((claimed[e >> 5] >> (e & 31)) & 1u);
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, cl);
+      if (lane == 0) wsum[warp] = __popc(m);
+      __syncthreads();
+      uint32_t wb = 0, tot = 0;
+      for (int w = 0; w < kHubMoveThreads / 32; ++w) {
+        if (w < (int)warp) wb += wsum[w];
+        tot += wsum[w];
+      }
+      const uint32_t claims_before = run + wb + __popc(m & ((1u << lane) - 1u));
+      if (valid && !cl) {
+        ndst[to + i - claims_before] = dst[e];
+        nlab[to + i - claims_before] = lab[e];
+      }
+      run += tot;
+      __syncthreads();
+    }
+  }
+}
+
 template <typename LabelT>
 Status move_edges(Store& s, const uint64_t* noff, const uint32_t* touched, const uint32_t* claimed,
                   const uint32_t* tlist, uint64_t ntouched, unsigned long long* cursor, const uint32_t* is,
@@ -565,34 +696,115 @@ Status move_edges(Store& s, const uint64_t* noff, const uint32_t* touched, const
   if (n_small)
     k_move_small<LabelT><<<grid(s, n_small, 256), 256, 0, s.stream>>>(n_small, off, noff, touched, dst, lab, ndst,
                                                                        nlab);
-  if (s.n_alive > n_small)
-    k_move_large<LabelT><<<grid(s, (s.n_alive - n_small) * 32, 256), 256, 0, s.stream>>>(
-        n_small, s.n_alive, off, noff, touched, dst, lab, ndst, nlab);
+  const uint64_t hub_first = s.class_start[kClassHub];
+  if (hub_first > n_small)
+    k_move_large<LabelT><<<grid(s, (hub_first - n_small) * 32, 256), 256, 0, s.stream>>>(
+        n_small, hub_first, off, noff, touched, dst, lab, ndst, nlab);
+  if (s.n_hub_chunks) {
+    Status st = ensure(s, s.inplace[kHubCntBuf], s.n_hub_chunks * 4);
+    if (!st.ok()) return st;
+    uint32_t* cnt = ptr<uint32_t>(s.inplace[kHubCntBuf]);
+    const unsigned gc = (unsigned)std::min<uint64_t>(s.n_hub_chunks, (uint64_t)s.sms * 8);
+    const uint4* chunks = ptr<uint4>(s.hub_chunks);
+    k_hub_chunk_claims<<<gc, kHubMoveThreads, 0, s.stream>>>(chunks, s.n_hub_chunks, claimed, cnt);
+    k_hub_chunk_prefix<<<grid(s, s.n_hub, 256), 256, 0, s.stream>>>(s.n_hub, hub_first, ptr<uint32_t>(s.hub_cstart),
+                                                                     chunks, off, noff, cnt, cursor);
+    k_hub_chunk_move<LabelT><<<gc, kHubMoveThreads, 0, s.stream>>>(chunks, s.n_hub_chunks, hub_first, off, noff,
+                                                                    claimed, cnt, dst, lab, ndst, nlab);
+  }
   if (ntouched)
-    k_rewrite_touched<LabelT><<<grid(s, ntouched * 32, 256), 256, 0, s.stream>>>(tlist, ntouched, off, noff, claimed,
-                                                                                 dst, lab, ndst, nlab, cursor);
+    k_rewrite_touched<LabelT><<<grid(s, ntouched * 32, 256), 256, 0, s.stream>>>(tlist, ntouched, s.n, off, noff,
+                                                                                 claimed, dst, lab, ndst, nlab, cursor);
   if (nins)
     k_place_inserts_internal<LabelT><<<grid(s, nins, 256), 256, 0, s.stream>>>(nins, is, it, il, cursor, ndst, nlab);
   return cuda_check(cudaGetLastError(), "move edges");
 }
 
-// Try the in-place path.  *taken = false leaves the graph as it was.
+// Original-order alive flags grown by the added nodes (alive).
+Status ensure_keep_alive(Store& s, uint64_t n0, uint64_t n1) {
+  Buf nb;
+  Status st = ensure(s, nb, std::max<uint64_t>(n1, 1));
+  if (!st.ok()) return st;
+  cudaMemcpyAsync(nb.p, s.alive_o.p, n0, cudaMemcpyDeviceToDevice, s.stream);
+  cudaMemsetAsync(static_cast<uint8_t*>(nb.p) + n0, 1, n1 - n0, s.stream);
+  st = cuda_check(cudaStreamSynchronize(s.stream), "alive flags");
+  release(s, s.alive_o);
+  s.alive_o = nb;
+  return st;
+}
+
+// Endpoints of the batch in the current internal ids; a node added by the
+// batch (original id >= n0) keeps its original id as its provisional one.
+__global__ void k_to_current_ids(uint64_t k, const uint32_t* o2p, uint64_t n0, const uint32_t* a, uint32_t* out) {
+  GRID_STRIDE(i, k) out[i] = a[i] < n0 ? o2p[a[i]] : a[i];
+}
+
+// Provisional ids -> original ids (the current p2o, extended by the added
+// nodes), node labels and alive flags by provisional id, for the relabelling.
+__global__ void k_provisional_maps(uint64_t n0, uint64_t n1, uint64_t n_alive0, const uint32_t* p2o,
+                                   const uint32_t* nlabel, const uint32_t* add_label, uint32_t* orig, uint32_t* nlab,
+                                   uint8_t* alive) {
+  GRID_STRIDE(q, n1) {
+    orig[q] = q < n0 ? p2o[q] : (uint32_t)q;
+    nlab[q] = q < n0 ? nlabel[q] : add_label[q - n0];
+    alive[q] = (q < n_alive0 || q >= n0) ? 1 : 0;
+  }
+}
+
+// After relabelling by provisional ids: p2o[p] = the original id of the
+// provisional id the relabelling gave node p; then o2p is its inverse.
+__global__ void k_compose_p2o(uint64_t n, const uint32_t* orig, uint32_t* p2o) {
+  GRID_STRIDE(p, n) p2o[p] = orig[p2o[p]];
+}
+__global__ void k_invert_p2o(uint64_t n, const uint32_t* p2o, uint32_t* o2p) {
+  GRID_STRIDE(p, n) o2p[p2o[p]] = (uint32_t)p;
+}
+
+// The fast path for edge insertions and deletions and node additions (no node
+// deletions, every deletion names a stored copy, labels keep their width):
+// the new edge table is built in the current internal ids (deletions claim
+// stored copies, untouched segments move as blocks, touched ones are
+// rewritten).  If every node keeps its degree class and no node is added, the
+// table replaces the old one in place; otherwise the new table is laid out
+// again from these ids by the usual relabelling, whose order is then mapped
+// back to original ids.  *taken = false leaves the graph as it was (the
+// general path runs).
+Status apply_in_place_body(Store& s, const kbisim_batch* bt, const uint32_t* is, const uint32_t* it,
+                           const uint32_t* il, const uint32_t* ds, const uint32_t* dt, const uint32_t* dl,
+                           const uint32_t* addl, uint64_t* missing_out, bool* taken);
+
+// With an HBM budget the fast path's buffers (the second edge table, claims,
+// degrees) count against it: if they do not fit, the general path runs, and
+// after the batch they are released again.
 Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, const uint32_t* it, const uint32_t* il,
-                      const uint32_t* ds, const uint32_t* dt, const uint32_t* dl, uint64_t* missing_out,
-                      bool* taken) {
+                      const uint32_t* ds, const uint32_t* dt, const uint32_t* dl, const uint32_t* addl,
+                      uint64_t* missing_out, bool* taken) {
+  Status st = apply_in_place_body(s, bt, is, it, il, ds, dt, dl, addl, missing_out, taken);
+  if (s.budget) {
+    const bool graph_intact = *taken || s.has_graph;
+    for (Buf& b : s.inplace) release(s, b);
+    if (st.code == KBISIM_ERR_BUDGET && !*taken && graph_intact) return Status::Ok();
+  }
+  return st;
+}
+
+Status apply_in_place_body(Store& s, const kbisim_batch* bt, const uint32_t* is, const uint32_t* it,
+                           const uint32_t* il, const uint32_t* ds, const uint32_t* dt, const uint32_t* dl,
+                           const uint32_t* addl, uint64_t* missing_out, bool* taken) {
   *taken = false;
-  const uint64_t n = s.n, m = s.m, ni = bt->n_ins, nd = bt->n_del;
-  if (bt->n_add_nodes || bt->n_del_nodes || !n || !s.has_graph || s.budget) return Status::Ok();
-  if (ni + nd > std::max<uint64_t>(m / 16, 1ull << 16)) return Status::Ok();  // large batches relabel
+  const uint64_t n0 = s.n, m = s.m, ni = bt->n_ins, nd = bt->n_del, na = bt->n_add_nodes;
+  const uint64_t n1 = n0 + na;
+  if (bt->n_del_nodes || !n0 || !s.has_graph) return Status::Ok();
+  if (ni + nd > std::max<uint64_t>(m / 16, 1ull << 16)) return Status::Ok();  // large batches: general path
   Status st;
   Buf* B = s.inplace;
-  enum { IDS, DELTA, TOUCH, CLAIM, DEG, CUR, LIST, NDST, NLAB, SC, TMP };
-  const uint64_t words = n / 32 + 1, cwords = m / 32 + 1;
+  enum { IDS, DELTA, TOUCH, CLAIM, DEG, CUR, LIST, NDST, NLAB, SC, TMP, ORIG, PNLAB, PALIVE };
+  const uint64_t words = n1 / 32 + 1, cwords = m / 32 + 1;
   if (!(st = ensure(s, B[IDS], std::max<uint64_t>(2 * ni + 2 * nd, 1) * 4)).ok()) return st;
-  if (!(st = ensure(s, B[DELTA], n * 4)).ok()) return st;
+  if (!(st = ensure(s, B[DELTA], n1 * 4)).ok()) return st;
   if (!(st = ensure(s, B[TOUCH], words * 4)).ok()) return st;
   if (!(st = ensure(s, B[CLAIM], cwords * 4)).ok()) return st;
-  if (!(st = ensure(s, B[DEG], (n + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, B[DEG], (n1 + 1) * 8)).ok()) return st;
   if (!(st = ensure(s, B[SC], 64)).ok()) return st;
   uint32_t* ids = ptr<uint32_t>(B[IDS]);
   uint32_t *isp = ids, *itp = ids + ni, *dsp = ids + 2 * ni, *dtp = ids + 2 * ni + nd;
@@ -601,49 +813,59 @@ Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, cons
   uint32_t* claimed = ptr<uint32_t>(B[CLAIM]);
   unsigned long long* deg = ptr<unsigned long long>(B[DEG]);
   unsigned long long* sc = ptr<unsigned long long>(B[SC]);
-  cudaMemsetAsync(delta, 0, n * 4, s.stream);
+  cudaMemsetAsync(delta, 0, n1 * 4, s.stream);
   cudaMemsetAsync(touched, 0, words * 4, s.stream);
   cudaMemsetAsync(claimed, 0, cwords * 4, s.stream);
   cudaMemsetAsync(sc, 0, 64, s.stream);
   const uint32_t* o2p = ptr<uint32_t>(s.o2p);
   if (ni) {
-    k_to_internal_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, is, isp);
-    k_to_internal_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, it, itp);
+    k_to_current_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, n0, is, isp);
+    k_to_current_ids<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, o2p, n0, it, itp);
     k_count_inserts_internal<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, isp, delta, touched);
   }
   if (nd) {
-    k_to_internal_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, ds, dsp);
-    k_to_internal_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, dt, dtp);
+    k_to_current_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, n0, ds, dsp);
+    k_to_current_ids<<<grid(s, nd, 256), 256, 0, s.stream>>>(nd, o2p, n0, dt, dtp);
     if (s.label8)
       k_claim_deletes<uint8_t><<<grid(s, nd * 32, 256), 256, 0, s.stream>>>(
-          nd, dsp, dtp, dl, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel), claimed, delta,
-          touched, sc);
+          nd, dsp, dtp, dl, n0, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel), claimed,
+          delta, touched, sc);
     else
       k_claim_deletes<uint32_t><<<grid(s, nd * 32, 256), 256, 0, s.stream>>>(
-          nd, dsp, dtp, dl, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel), claimed, delta,
-          touched, sc);
+          nd, dsp, dtp, dl, n0, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel), claimed,
+          delta, touched, sc);
+    if (s.n_hub) {
+      const unsigned gh = (unsigned)std::min<uint64_t>(nd, (uint64_t)s.sms * 2);
+      if (s.label8)
+        k_claim_deletes_hub<uint8_t><<<gh, 1024, 0, s.stream>>>(nd, dsp, dtp, dl, n0, ptr<uint64_t>(s.offsets),
+                                                              ptr<uint32_t>(s.dst), ptr<uint8_t>(s.elabel), claimed,
+                                                              delta, touched, sc);
+      else
+        k_claim_deletes_hub<uint32_t><<<gh, 1024, 0, s.stream>>>(nd, dsp, dtp, dl, n0, ptr<uint64_t>(s.offsets),
+                                                               ptr<uint32_t>(s.dst), ptr<uint32_t>(s.elabel), claimed,
+                                                               delta, touched, sc);
+    }
   }
   unsigned int* moved = reinterpret_cast<unsigned int*>(sc + 1);
   unsigned int* maxlab = moved + 1;
-  k_new_degrees<<<grid(s, n, 256), 256, 0, s.stream>>>(n, ptr<uint64_t>(s.offsets), delta, deg, moved);
+  k_new_degrees<<<grid(s, n1, 256), 256, 0, s.stream>>>(n0, n1, ptr<uint64_t>(s.offsets), delta, deg, moved);
   if (ni) k_max32<<<grid(s, ni, 256), 256, 0, s.stream>>>(ni, il, maxlab);
   uint64_t h[2] = {0, 0};
-  st = cuda_check(cudaGetLastError(), "in-place batch");
-  if (st.ok()) st = cuda_check(cudaMemcpyAsync(h, sc, 16, cudaMemcpyDeviceToHost, s.stream), "in-place batch");
+  st = cuda_check(cudaGetLastError(), "batch");
+  if (st.ok()) st = cuda_check(cudaMemcpyAsync(h, sc, 16, cudaMemcpyDeviceToHost, s.stream), "batch");
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
   if (!st.ok()) return st;
   const uint32_t moved_v = (uint32_t)h[1], maxlab_v = (uint32_t)(h[1] >> 32);
-  if (moved_v) return Status::Ok();  // a node changes degree class: relabel
-  if (s.label8 && maxlab_v >= 256) return Status::Ok();  // wider labels: relabel
+  if (s.label8 && maxlab_v >= 256) return Status::Ok();  // wider labels: general path
   // a deletion with no stored copy may name an edge inserted by this batch
   // (insertions come first): the general path decides those
   if (h[0]) return Status::Ok();
-  const uint64_t missing = 0;
-  const uint64_t m1 = m + ni - (nd - missing);
-  // new offsets, touched list, then the edges
-  if (!(st = scan_u64(s, deg, n + 1, nullptr, B[TMP], nullptr)).ok()) return st;
-  if (!(st = ensure(s, B[CUR], (n + 1) * 8)).ok()) return st;
-  if (!(st = ensure(s, B[LIST], n * 4)).ok()) return st;
+  const uint64_t m1 = m + ni - nd;
+  const bool relabel = moved_v || na;
+  // new offsets (current ids), touched list, then the edges
+  if (!(st = scan_u64(s, deg, n1 + 1, nullptr, B[TMP], nullptr)).ok()) return st;
+  if (!(st = ensure(s, B[CUR], (n1 + 1) * 8)).ok()) return st;
+  if (!(st = ensure(s, B[LIST], n1 * 4)).ok()) return st;
   if (!(st = ensure(s, B[NDST], std::max<uint64_t>(m1, 1) * 4)).ok()) return st;
   if (!(st = ensure(s, B[NLAB], std::max<uint64_t>(m1, 1) * (s.label8 ? 1 : 4))).ok()) return st;
   cudaMemsetAsync(sc + 2, 0, 8, s.stream);
@@ -660,11 +882,6 @@ Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, cons
     st = move_edges<uint32_t>(s, reinterpret_cast<const uint64_t*>(deg), touched, claimed, ptr<uint32_t>(B[LIST]),
                               ntouched, cur, isp, itp, il, ni, ptr<uint32_t>(B[NDST]), ptr<uint32_t>(B[NLAB]));
   if (!st.ok()) return st;
-  // the new table replaces the old one (buffers swap, so both stay allocated)
-  std::swap(s.dst, B[NDST]);
-  std::swap(s.elabel, B[NLAB]);
-  std::swap(s.offsets, B[DEG]);
-  s.m = m1;
   if (maxlab_v) {
     uint32_t lb = 1;
     while (lb < 32 && (maxlab_v >> lb)) ++lb;
@@ -673,10 +890,44 @@ Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, cons
   for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
   s.has_levels = false;
   s.many.valid = false;
-  if (!(st = build_chunk_lists(s, false)).ok()) return st;
+  if (!relabel) {
+    // the new table replaces the old one (buffers swap, so both stay allocated)
+    std::swap(s.dst, B[NDST]);
+    std::swap(s.elabel, B[NLAB]);
+    std::swap(s.offsets, B[DEG]);
+    s.m = m1;
+    if (!(st = build_chunk_lists(s, false)).ok()) return st;
+  } else {
+    // lay the new table out again; its ids are the current internal ones (and
+    // the added nodes'), so the relabelling's order is mapped back to
+    // original ids afterwards
+    if (!(st = ensure(s, B[ORIG], n1 * 4)).ok()) return st;
+    if (!(st = ensure(s, B[PNLAB], n1 * 4)).ok()) return st;
+    if (!(st = ensure(s, B[PALIVE], n1)).ok()) return st;
+    k_provisional_maps<<<grid(s, n1, 256), 256, 0, s.stream>>>(n0, n1, s.n_alive, ptr<uint32_t>(s.p2o),
+                                                               ptr<uint32_t>(s.nlabel), addl, ptr<uint32_t>(B[ORIG]),
+                                                               ptr<uint32_t>(B[PNLAB]), ptr<uint8_t>(B[PALIVE]));
+    if (!(st = cuda_check(cudaGetLastError(), "provisional ids")).ok()) return st;
+    const bool any_dead = s.n_alive < n0;
+    s.n = n1;
+    s.m = m1;
+    if (!(st = relabel_graph(s, reinterpret_cast<const uint64_t*>(deg), ptr<uint32_t>(B[NDST]), B[NLAB].p,
+                             ptr<uint32_t>(B[PNLAB]), any_dead ? ptr<uint8_t>(B[PALIVE]) : nullptr,
+                             s.label8 ? 1 : 4)).ok()) {
+      s.has_graph = false;
+      return st;
+    }
+    k_compose_p2o<<<grid(s, n1, 256), 256, 0, s.stream>>>(n1, ptr<uint32_t>(B[ORIG]), ptr<uint32_t>(s.p2o));
+    k_invert_p2o<<<grid(s, n1, 256), 256, 0, s.stream>>>(n1, ptr<uint32_t>(s.p2o), ptr<uint32_t>(s.o2p));
+    if (!(st = cuda_check(cudaGetLastError(), "compose ids")).ok()) return st;
+    if (s.any_dead && na) {  // alive flags in original order: the added nodes are alive
+      if (!(st = ensure_keep_alive(s, n0, n1)).ok()) return st;
+    }
+  }
   *taken = true;
-  if (missing_out) *missing_out = missing;
-  return cuda_check(cudaStreamSynchronize(s.stream), "in-place batch");
+  s.mt.in_place = relabel ? 0 : 1;
+  if (missing_out) *missing_out = 0;
+  return cuda_check(cudaStreamSynchronize(s.stream), "batch");
 }
 
 Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
@@ -723,8 +974,8 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (e & kDeadEnd) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch touches a deleted node");
   {
     bool taken = false;
-    if (!(st = apply_in_place(s, bt, is, it, il, ds, dt, dl, missing_out, &taken)).ok()) return st;
-    s.mt.in_place = taken ? 1 : 0;
+    s.mt.in_place = 0;
+    if (!(st = apply_in_place(s, bt, is, it, il, ds, dt, dl, addl, missing_out, &taken)).ok()) return st;
     if (taken) return Status::Ok();
   }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
     "kbisim_num_edges": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_device_bytes": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_get_update_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(UpdateInfo)]),
+    "kbisim_set_hbm_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "kbisim_get_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
     "kbisim_reset_times": (None, [ctypes.c_void_p]),
     "kbisim_get_round_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
@@ -419,6 +420,10 @@ class KBisim:
     def device_bytes(self) -> int:
         """Device bytes the handle holds (what hbm_budget_bytes bounds)."""
         return int(self._lib.kbisim_device_bytes(self._h))
+
+    def set_hbm_budget(self, nbytes: int) -> None:
+        """Bound the device bytes later calls may hold (0 = no bound)."""
+        self._check(self._lib.kbisim_set_hbm_budget(self._h, int(nbytes)))
 
     def pids(self, level: int, out=None):
         """Level ``level`` as a host numpy uint32 array, or into ``out`` (a CUDA

@@ -1,14 +1,17 @@
 """Serving loop: build and update requests on device-resident graphs.
 
-Each resident graph lives in its own library handle with its own CUDA stream.
-Requests arrive over time (``Request.t_arrive``, seconds from the start); the
-loop admits a request as soon as
+Each resident graph lives in its own library handle with its own CUDA stream
+and its own HBM budget, which the library enforces (kbisim_set_hbm_budget: a
+call that would hold more fails with KBISIM_ERR_BUDGET instead of
+allocating).  Requests arrive over time (``Request.t_arrive``, seconds from
+the start); the loop admits a request as soon as
 
 * its graph has no request in flight (requests on one graph run in arrival
   order, so each result is the one the same sequence gives one at a time),
 * a slot is free (at most ``slots`` requests in flight), and
-* the device memory it may need fits under the budget beside the requests
-  already in flight,
+* the server's HBM budget holds the bytes the idle handles hold now, plus the
+  budgets of the handles with a request in flight (each may grow up to its
+  budget, never past it), plus the budget of the request's own handle,
 
 and runs it on a worker thread (the library call releases the interpreter
 lock), so requests on different graphs overlap on the device.  A request
@@ -31,7 +34,7 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from .kbisim import KBisim
+from .kbisim import ERR_BUDGET, KBisim, KBisimError
 
 
 @dataclasses.dataclass
@@ -57,6 +60,7 @@ class Outcome:
     counts: List[int]
     digest: str
     edges: int
+    error: str = ""                # "budget": the handle's HBM budget refused the request
 
     @property
     def latency(self) -> float:
@@ -67,10 +71,26 @@ def _digest(pids: np.ndarray) -> str:
     return hashlib.sha256(pids.tobytes()).hexdigest()[:16]
 
 
-def graph_bytes(num_nodes: int, num_edges: int) -> int:
-    """Device bytes a graph's handle holds, and a bound for what a request on it
-    may add (edge table, levels, round scratch)."""
-    return int(num_edges) * 24 + int(num_nodes) * 80
+class HbmAdmission:
+    """Admission by HBM budget (host logic).  Every handle h has a budget
+    B_h that the library enforces, so a handle with a request in flight never
+    holds more than B_h and an idle one holds what it holds now (H_h).  A
+    request on handle r is admitted iff
+        sum(H_h, h idle) + sum(B_h, h in flight) + B_r <= total,
+    so the device never holds more than `total` for the handles."""
+
+    def __init__(self, total: int):
+        self.total = int(total)
+
+    def fits(self, held_idle: int, budgets_in_flight: int, budget: int) -> bool:
+        return held_idle + budgets_in_flight + budget <= self.total
+
+
+def handle_budget(held_after_build: int) -> int:
+    """Budget of a resident graph's handle: room for an update's second edge
+    table and the signature stores of incremental maintenance beside what the
+    handle holds after its build."""
+    return 4 * int(held_after_build) + (64 << 20)
 
 
 class Server:
@@ -83,17 +103,20 @@ class Server:
         self.device = device
         self.slots = max(1, int(slots))
         self.handles: List[KBisim] = []
-        self.sizes = []
+        self.budgets: List[int] = []
         self.k = list(int(x) for x in ks)
         for g, k in zip(graphs, self.k):
             stream = torch.cuda.Stream(device=device)
             h = KBisim(device=device, stream=stream)
             h.build(g, k)
+            b = handle_budget(h.device_bytes)
+            h.set_hbm_budget(b)
             self.handles.append(h)
-            self.sizes.append((g.num_nodes, g.num_edges))
+            self.budgets.append(b)
         torch.cuda.synchronize(device)
         free, _ = torch.cuda.mem_get_info(device)
-        self.budget = int(hbm_budget) if hbm_budget is not None else int(free * 0.8)
+        held = sum(h.device_bytes for h in self.handles)
+        self.admission = HbmAdmission(int(hbm_budget) if hbm_budget is not None else held + int(free * 0.8))
 
     def close(self):
         for h in self.handles:
@@ -104,22 +127,22 @@ class Server:
     def _run(self, req: Request, t0: float) -> Outcome:
         h = self.handles[req.graph]
         t_start = time.perf_counter() - t0
-        if req.kind == "update":
-            res, _ = h.update(req.k, ins=req.ins if req.ins is not None else (),
-                              dels=req.dels if req.dels is not None else ())
-        else:
-            res = h.refine(req.k)
-        pids = h.pids(req.k)
+        try:
+            if req.kind == "update":
+                res, _ = h.update(req.k, ins=req.ins if req.ins is not None else (),
+                                  dels=req.dels if req.dels is not None else ())
+            else:
+                res = h.refine(req.k)
+            pids = h.pids(req.k)
+        except KBisimError as e:
+            if e.code != ERR_BUDGET:
+                raise
+            t_end = time.perf_counter() - t0
+            return Outcome(req.rid, req.graph, req.kind, req.t_arrive, t_start, t_end, 0, [], "", h.num_edges,
+                           error="budget")
         t_end = time.perf_counter() - t0
-        n, m = h.num_nodes, h.num_edges
-        self.sizes[req.graph] = (n, m)
         return Outcome(req.rid, req.graph, req.kind, req.t_arrive, t_start, t_end, res.rounds_run,
-                       list(res.counts), _digest(pids), m)
-
-    def _need(self, req: Request) -> int:
-        n, m = self.sizes[req.graph]
-        extra = 0 if req.ins is None else len(req.ins[0])
-        return graph_bytes(n, m + extra) if req.kind == "update" else graph_bytes(n, m) // 4
+                       list(res.counts), _digest(pids), h.num_edges)
 
     # -- the loop ----------------------------------------------------------------
     def serve(self, requests: Sequence[Request], realtime: bool = True) -> List[Outcome]:
@@ -129,7 +152,6 @@ class Server:
         pending: List[Request] = []
         busy: Dict[int, bool] = {}
         inflight: Dict[cf.Future, Request] = {}
-        reserved = 0
         done: List[Outcome] = []
         nxt = 0
         t0 = time.perf_counter()
@@ -144,14 +166,16 @@ class Server:
                 # a slot and memory
                 kept = []
                 for r in pending:
-                    need = self._need(r)
-                    if (len(inflight) < self.slots and not busy.get(r.graph) and
-                            (reserved + need <= self.budget or not inflight)):
-                        busy[r.graph] = True
-                        reserved += need
-                        inflight[pool.submit(self._run, r, t0)] = r
-                    else:
-                        kept.append(r)
+                    if len(inflight) < self.slots and not busy.get(r.graph):
+                        flying = {x.graph for x in inflight.values()}
+                        held_idle = sum(h.device_bytes for i, h in enumerate(self.handles) if i not in flying)
+                        in_flight = sum(self.budgets[i] for i in flying)
+                        if self.admission.fits(held_idle - self.handles[r.graph].device_bytes, in_flight,
+                                               self.budgets[r.graph]) or not inflight:
+                            busy[r.graph] = True
+                            inflight[pool.submit(self._run, r, t0)] = r
+                            continue
+                    kept.append(r)
                 pending = kept
                 timeout = None
                 if nxt < len(reqs) and realtime:
@@ -161,7 +185,6 @@ class Server:
                     for f in fin:
                         r = inflight.pop(f)
                         busy[r.graph] = False
-                        reserved -= self._need(r)
                         with lock:
                             done.append(f.result())
                 elif timeout:

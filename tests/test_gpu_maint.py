@@ -157,3 +157,34 @@ def test_switch_back_and_recompute_agree():
         r, _ = kb.update(k, ins=ins, dels=dels)
         assert kb.update_info()["incremental"]
         assert_same(r, kb.all_pids(k), mg.kbisim(k))
+
+
+def test_long_signatures_in_the_store():
+    """A 12K-edge hub through the signature stores: a new edge gives it a new
+    long signature (stored after the lookup pass), a duplicate of one of its
+    edges leaves its signature as stored (compared element by element through
+    a set in global memory), and deleting the duplicate again too.  Every
+    step equals the oracle and runs on the frontier path."""
+    rng = np.random.default_rng(21)
+    n = 20_000
+    hub_t = rng.permutation(n)[:12_000].astype(np.uint32)
+    hub_l = rng.integers(0, 3, hub_t.size).astype(np.uint32)
+    other = 40_000
+    src = np.concatenate([np.zeros(hub_t.size, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
+    dst = np.concatenate([hub_t, rng.integers(0, n, other).astype(np.uint32)])
+    lab = np.concatenate([hub_l, rng.integers(0, 3, other).astype(np.uint32)])
+    nl = rng.integers(0, 2, n).astype(np.uint32)
+    g = synth.from_coo(n, src, dst, lab, nl)
+    mg = _mg(g)
+    k = 3
+    dup = (np.array([0], np.uint32), hub_t[:1].copy(), hub_l[:1].copy())
+    steps = [dict(ins=(np.array([0], np.uint32), np.array([int(hub_t[5]) ^ 1], np.uint32), np.array([2], np.uint32))),
+             dict(ins=dup), dict(dels=dup)]
+    with KBisim() as kb:
+        kb.build(g, k)
+        for st in steps:
+            ins, dels = st.get("ins", ()), st.get("dels", ())
+            mg.apply(ins=list(zip(*ins)) if len(ins) else [], dels=list(zip(*dels)) if len(dels) else [])
+            res, _ = kb.update(k, ins=ins, dels=dels)
+            assert kb.update_info()["incremental"], kb.update_info()
+            assert_same(res, kb.all_pids(k), mg.kbisim(k))

@@ -26,3 +26,14 @@ def test_request_stream_shape_and_determinism():
             for x in range(min(5, ds.size)):
                 lo, hi = int(g.offsets[ds[x]]), int(g.offsets[ds[x] + 1])
                 assert ((g.dst[lo:hi] == dd[x]) & (g.edge_label[lo:hi] == dl[x])).any()
+
+
+def test_admission_by_library_enforced_budgets():
+    """Idle handles count what they hold, handles with a request in flight
+    count their whole budget (the library keeps them within it), and a
+    request is admitted only if its own handle's budget fits beside those."""
+    from paper_1210_0748_gb300.serve import HbmAdmission, handle_budget
+    a = HbmAdmission(total=1000)
+    assert a.fits(held_idle=300, budgets_in_flight=400, budget=300)
+    assert not a.fits(held_idle=300, budgets_in_flight=400, budget=301)
+    assert handle_budget(100) == 400 + (64 << 20)
