@@ -85,7 +85,12 @@ typedef struct {
   /* CUDA device ordinal the handle uses. */
   int device;
   /* Upper bound on the device bytes the handle may hold; 0 = no bound.
-   * Calls that would need more fail with KBISIM_ERR_BUDGET before allocating. */
+   * A handle keeps its scratch between calls (so that steady-state calls
+   * neither allocate nor free: cudaFree waits for the whole device).  When an
+   * allocation would pass the budget, the handle first releases the scratch
+   * no running step uses (staging, batch temporaries, spare levels, the
+   * signature stores of maintenance, stale copy-out buffers); a call that
+   * still does not fit fails with KBISIM_ERR_BUDGET before allocating. */
   uint64_t hbm_budget_bytes;
   /* 1 (default) = stop refining once a level has as many blocks as the level
    * before it; 0 = always compute k rounds.  Results are identical. */
@@ -113,7 +118,11 @@ typedef struct {
    * handle; 0 = kbisim_update recomputes every level.  Results are identical.
    * The stores are made at the first update after a build (a cost of about
    * one signature pass per level) and take about 12 bytes per edge and 16 per
-   * node per maintained level. */
+   * node per maintained level.  The handle times both paths (host clock, per
+   * maintained level): after one update on each, it takes the frontier path
+   * only while that measured cheaper, and otherwise recomputes for the next 16
+   * updates (reason KBISIM_MAINT_COST) before trying the frontier path again.
+   * 2 = the frontier path whenever it applies, without timing. */
   int maintain;
 } kbisim_options;
 
@@ -258,6 +267,7 @@ int kbisim_update(kbisim_handle *h, const kbisim_batch *b, uint32_t k, kbisim_re
 #define KBISIM_MAINT_FRONTIER 3   /* a level's frontier held more than a quarter of the nodes (and > 4096) */
 #define KBISIM_MAINT_CAPACITY 4   /* a signature store ran out of room */
 #define KBISIM_MAINT_DELETES 5    /* the batch deletes nodes */
+#define KBISIM_MAINT_COST 6       /* recomputation measured cheaper on this handle (options.maintain = 1) */
 typedef struct {
   int incremental;
   int reason;

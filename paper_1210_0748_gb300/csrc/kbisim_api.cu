@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -48,8 +49,11 @@ void read_fault_hooks(Store& s) {
 Status ensure(Store& s, Buf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return Status::Ok();
   size_t want = std::max<size_t>(bytes, 256);
-  if (s.budget && s.bytes_held - b.cap + want > s.budget)
-    return Status::Err(KBISIM_ERR_BUDGET, "device memory budget exceeded");
+  if (s.budget && s.bytes_held - b.cap + want > s.budget) {
+    trim_caches(s);  // may release b too: it is reallocated below
+    if (s.bytes_held - b.cap + want > s.budget)
+      return Status::Err(KBISIM_ERR_BUDGET, "device memory budget exceeded");
+  }
   if (s.fault_alloc >= 0 && s.fault_alloc-- == 0)
     return Status::Err(KBISIM_ERR_OUT_OF_MEMORY, "injected allocation failure (KBISIM_FAULT_ALLOC)");
   if (b.p) {
@@ -78,6 +82,30 @@ void release(Store& s, Buf& b) {
   }
   b.p = nullptr;
   b.cap = 0;
+}
+
+void trim_caches(Store& s) {
+  const uint32_t u = s.busy;
+  if (!(u & kCacheStage))
+    for (Buf& b : s.stage) release(s, b);
+  if (!(u & kCacheUpd))
+    for (Buf& b : s.upd) release(s, b);
+  if (!(u & kCacheInplace))
+    for (Buf& b : s.inplace) release(s, b);
+  if (!(u & kCacheRelabel)) {
+    release(s, s.rl_tcnt);
+    release(s, s.rl_hot);
+    release(s, s.rl_ost);
+  }
+  if (!(u & kCacheSpare)) {
+    for (Buf& b : s.spare_level) release(s, b);
+    s.spare_level.clear();
+    release(s, s.spare_alone);
+  }
+  // copies in original order whose results are no longer valid
+  for (size_t l = 0; l < s.out_level.size(); ++l)
+    if (!(l < s.out_valid.size() && s.out_valid[l])) release(s, s.out_level[l]);
+  if (!(u & kCacheMaint)) maint_release(s);
 }
 
 namespace {
@@ -322,17 +350,12 @@ uint32_t bits_needed(uint64_t v) {  // bits for values 0..v
   return b;
 }
 
-// Staging buffers of a load (host inputs, COO grouping).  Kept in the store
-// between loads when the handle has no HBM budget, released at the end of the
-// load otherwise.
+// Staging buffers of a load (host inputs, COO grouping), kept in the store
+// between loads.
 struct Temps {
-  Store& s;
+  InUse use;
   Buf* b;
-  explicit Temps(Store& st) : s(st), b(st.stage) {}
-  ~Temps() {
-    if (s.budget)
-      for (int i = 0; i < kStageBufs; ++i) release(s, b[i]);
-  }
+  explicit Temps(Store& st) : use(st, kCacheStage), b(st.stage) {}
 };
 
 // Load: bring the graph to the device as a CSR in original ids (copying host
@@ -560,6 +583,7 @@ Status refine_levels(Store& s, uint32_t k) {
 Status refine(Store& s, uint32_t k, kbisim_result* out) {
   if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
   if (k > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+  InUse use(s, kCacheSpare);
   LevelSnapshot snap = take_snapshot(s);
   std::swap(s.level, s.spare_level);
   std::swap(s.alone, s.spare_alone);
@@ -578,11 +602,6 @@ Status refine(Store& s, uint32_t k, kbisim_result* out) {
     return st;
   }
   invalidate_outputs(s);
-  if (s.budget) {  // a budget handle keeps no spares between calls
-    for (Buf& b : s.spare_level) release(s, b);
-    s.spare_level.clear();
-    release(s, s.spare_alone);
-  }
   s.has_levels = true;
   fill_result(s, k, out);
   return timer_collect(s);
@@ -593,6 +612,7 @@ Status refine(Store& s, uint32_t k, kbisim_result* out) {
 Status extend(Store& s, uint32_t k_new, kbisim_result* out) {
   if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
   if (k_new > KBISIM_MAX_K) return Status::Err(KBISIM_ERR_INVALID_ARG, "k too large");
+  InUse use(s, kCacheSpare);
   Status st;
   const bool need = k_new > s.computed && !(s.early_stop && s.stable);
   if (need) {
@@ -661,6 +681,7 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   kbisim_options o;
   if (opt) o = *opt; else kbisim_default_options(&o);
   if (o.hash_bits == 0 || o.hash_bits > 64) return KBISIM_ERR_INVALID_ARG;
+  if (o.maintain < 0 || o.maintain > 2) return KBISIM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -683,7 +704,7 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   s.hash_mask = o.hash_bits >= 64 ? ~0ull : ((1ull << o.hash_bits) - 1ull);
   s.checked = o.checked != 0;
   s.timing = o.collect_timing != 0;
-  s.maintain = o.maintain != 0;
+  s.maintain = o.maintain;
   void* hp = nullptr;
   if (cudaMallocHost(&hp, 16 * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -869,47 +890,92 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
   if (k > KBISIM_MAX_K) return finish(h, Status::Err(KBISIM_ERR_INVALID_ARG, "k too large"));
   enter(h);
   kb::Store& s = h->s;
+  kb::MaintState& m = s.mt;
+  kb::InUse use(s, kb::kCacheMaint);
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms_since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+  };
   uint64_t missing = 0;
   Status st;
   bool done = false;
-  s.mt.incremental = 0;
-  s.mt.frontier_nodes = 0;
-  s.mt.levels = 0;
-  s.mt.in_place = 0;
+  m.incremental = 0;
+  m.frontier_nodes = 0;
+  m.levels = 0;
+  m.in_place = 0;
   const uint64_t batch_edges = b ? b->n_ins + b->n_del : 0;
-  const bool suspended = s.mt.suspend_edges && k == s.mt.suspend_k && batch_edges >= s.mt.suspend_edges;
+  const bool suspended = m.suspend_edges && k == m.suspend_k && batch_edges >= m.suspend_edges;
+  // timed choice: after one update on each path, the frontier path runs only
+  // while it measured cheaper; otherwise the next 16 updates recompute
+  bool timed = s.maintain == 1;
+  bool cost_off = false;
+  if (timed && m.n_inc && m.n_rec && m.ms_inc > m.ms_rec) {
+    if (m.cost_skip == 0) m.cost_skip = 16;
+    cost_off = --m.cost_skip > 0;
+  } else if (timed && m.n_inc && !m.n_rec) {
+    cost_off = true;  // one recomputation to compare with
+  }
+  bool tried = false;  // the frontier path was attempted (its cost is charged to it)
   if (!s.maintain) {
-    s.mt.reason = KBISIM_MAINT_OFF;
+    m.reason = KBISIM_MAINT_OFF;
   } else if (b && b->n_del_nodes) {
-    s.mt.reason = KBISIM_MAINT_DELETES;
+    m.reason = KBISIM_MAINT_DELETES;
   } else if (suspended) {
     // a batch at least this large already switched back at this k: recompute
-    s.mt.reason = KBISIM_MAINT_FRONTIER;
-    kb::maint_release(s);
+    m.reason = KBISIM_MAINT_FRONTIER;
+    kb::maint_invalidate(s);
+  } else if (cost_off) {
+    m.reason = KBISIM_MAINT_COST;
+    kb::maint_invalidate(s);
   } else {
     // stores made from the current levels when there are none for this k yet
-    if ((!s.mt.valid || k > s.mt.k) && s.has_levels && (s.k_requested >= k || s.stable)) {
+    if ((!m.valid || k > m.k) && s.has_levels && (s.k_requested >= k || s.stable)) {
       if (!kb::maint_build(s, k).ok()) kb::maint_release(s);
     }
-    if (s.mt.valid && k <= s.mt.k) st = kb::maint_update(s, b, k, &missing, &done);
-    else s.mt.reason = KBISIM_MAINT_NO_STORE;
+    if (m.valid && k <= m.k) {
+      tried = true;
+      st = kb::maint_update(s, b, k, &missing, &done);
+    } else {
+      m.reason = KBISIM_MAINT_NO_STORE;
+    }
   }
   if (st.ok() && !done) {
-    kb::maint_release(s);  // the graph changes under the stores
+    kb::maint_invalidate(s);  // the graph changes under the stores
     st = kb::apply_batch(s, b, &missing);
   }
-  if (st.ok()) st = s.mt.incremental ? kb::finish_incremental(s, k, out) : kb::refine(s, k, out);
-  if (s.mt.incremental) {
-    s.mt.suspend_edges = 0;
-  } else if (s.mt.reason == KBISIM_MAINT_FRONTIER) {
-    s.mt.suspend_edges = std::max<uint64_t>(batch_edges, 1);
-    s.mt.suspend_k = k;
+  if (st.ok()) st = m.incremental ? kb::finish_incremental(s, k, out) : kb::refine(s, k, out);
+  if (m.incremental) {
+    m.suspend_edges = 0;
+  } else if (m.reason == KBISIM_MAINT_FRONTIER) {
+    m.suspend_edges = std::max<uint64_t>(batch_edges, 1);
+    m.suspend_k = k;
   }
+  const double call_ms = ms_since(t0);
   // after a full recomputation, stores for the next update (not while large
-  // batches are known to switch back: the next smaller batch makes them)
-  if (st.ok() && s.maintain && !s.mt.incremental && s.has_levels && s.mt.reason != KBISIM_MAINT_FRONTIER &&
-      !kb::maint_build(s, k).ok())
-    kb::maint_release(s);
+  // batches are known to switch back, nor while recomputation measures
+  // cheaper: the update before the next trial of the frontier path makes them)
+  const bool next_tries = !(m.reason == KBISIM_MAINT_COST && m.cost_skip > 1);
+  double build_ms = 0;
+  if (st.ok() && s.maintain && !m.incremental && s.has_levels && m.reason != KBISIM_MAINT_FRONTIER &&
+      next_tries) {
+    const auto tb = std::chrono::steady_clock::now();
+    if (!kb::maint_build(s, k).ok()) kb::maint_release(s);
+    build_ms = ms_since(tb);
+  }
+  if (st.ok() && timed) {
+    const double per = 1.0 / std::max<uint32_t>(k, 1);
+    auto fold = [](double& avg, uint32_t& n, double x) {
+      avg = n ? 0.5 * (avg + x) : x;
+      ++n;
+    };
+    if (tried || m.incremental) {
+      fold(m.ms_inc, m.n_inc, (call_ms + m.build_ms) * per);
+      m.build_ms = 0;
+    } else if (m.reason == KBISIM_MAINT_COST || m.reason == KBISIM_MAINT_NO_STORE) {
+      fold(m.ms_rec, m.n_rec, call_ms * per);
+    }
+    m.build_ms += build_ms;
+  }
   if (st.ok() && missing_deletes) *missing_deletes = missing;
   return finish(h, st);
 }

@@ -211,6 +211,13 @@ struct MaintState {
   // edges (same k) recompute at once, without stores (0 = none)
   uint64_t suspend_edges = 0;
   uint32_t suspend_k = 0;
+  // measured cost of the two paths (host ms per maintained level, averaged
+  // with weight 1/2 on the newest sample) and how many more updates
+  // recompute because the frontier path measured dearer
+  double ms_inc = 0, ms_rec = 0;
+  uint32_t n_inc = 0, n_rec = 0;
+  uint32_t cost_skip = 0;
+  double build_ms = 0;  // store build after a recomputation, charged to the next frontier update
 };
 
 struct Store;
@@ -322,7 +329,7 @@ struct Store {
 
   ManyState many;               // batched build (kbisim_build_many)
   MaintState mt;                // incremental maintenance (kbisim_update with options.maintain)
-  bool maintain = true;
+  int maintain = 1;            // options.maintain: 0 off, 1 timed choice, 2 always when it applies
   double maint_frontier_max = 0.25;  // switch back to a rebuild above this fraction of the nodes
   LevelHook level_hook = nullptr;  // called after each computed level (batched build)
   const uint32_t* round_mask = nullptr;  // nodes signed in the next round (NULL = all); the
@@ -337,6 +344,7 @@ struct Store {
   bool fault_corrupt_dst = false;
 
   size_t bytes_held = 0;
+  uint32_t busy = 0;           // scratch groups (kCache*) in use by the running call
   KernelTimer* timer = nullptr;
   double total_ms[KBISIM_KERNEL_COUNT] = {0};
   uint64_t launches[KBISIM_KERNEL_COUNT] = {0};
@@ -363,6 +371,30 @@ constexpr int kUpdBufs = Store::kUpdBufsN;
 Status ensure(Store& s, Buf& b, size_t bytes);
 void read_fault_hooks(Store& s);
 void release(Store& s, Buf& b);
+
+// Scratch groups a handle keeps between calls (so that a call allocates and
+// frees nothing in the steady state: cudaFree waits for the whole device).
+// With an HBM budget, an allocation that would pass the budget first drops
+// the groups no running code uses (trim_caches), then fails if it still does
+// not fit.  Code that uses a group marks it with an InUse guard.
+enum : uint32_t {
+  kCacheStage = 1,    // stage[]: host inputs and COO grouping of a load
+  kCacheUpd = 2,      // upd[]: a maintenance batch
+  kCacheInplace = 4,  // inplace[]: a batch applied in place
+  kCacheSpare = 8,    // spare_level / spare_alone: the levels a refinement replaces
+  kCacheRelabel = 16, // rl_*: relabelling
+  kCacheMaint = 32,   // the signature stores of incremental maintenance
+};
+struct InUse {
+  Store& s;
+  uint32_t bit;
+  bool was;
+  InUse(Store& st, uint32_t b) : s(st), bit(b), was((st.busy & b) != 0) { st.busy |= b; }
+  ~InUse() {
+    if (!was) s.busy &= ~bit;
+  }
+};
+void trim_caches(Store& s);
 Status cuda_check(cudaError_t e, const char* what);
 
 // Graph preparation and round driver (kbisim_round.cu)
@@ -403,7 +435,8 @@ Status scan_u64(Store& s, uint64_t* a, uint64_t n);
 // k), and the caller recomputes.
 Status maint_build(Store& s, uint32_t k);
 Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missing, bool* done);
-void maint_release(Store& s);
+void maint_release(Store& s);     // frees the stores and their scratch
+void maint_invalidate(Store& s);  // marks them stale, keeping the buffers
 
 // Thread blocks of `kernel` (threads each, dyn_smem dynamic shared bytes) that
 // are resident on all `sms` multiprocessors at once: the grid of a grid-stride

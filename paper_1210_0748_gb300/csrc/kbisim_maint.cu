@@ -692,7 +692,7 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = scan_u64(s, reinterpret_cast<uint64_t*>(woff), n + 1)).ok()) return st;
   uint64_t words = 0;
   if (!(st = sync_read(s, &words, woff + n, 8, "store size")).ok()) return st;
-  L.pcap = 4 * words + (64u << 20);  // room for the signatures later updates add
+  L.pcap = 3 * words + (4u << 20);  // room for the signatures later updates add
   L.tcap = pow2_at_least(2 * L.lcap);
   if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
   if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
@@ -841,12 +841,19 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
 
 }  // namespace
 
+void release_level(Store& s, MaintLevel& L) {
+  Buf* b[] = {&L.lab, &L.tkey, &L.tval, &L.sfirst, &L.scount, &L.soff, &L.pool, &L.ctr};
+  for (Buf* x : b) release(s, *x);
+}
+
+void maint_invalidate(Store& s) {
+  s.mt.valid = false;
+  s.mt.k = 0;
+}
+
 void maint_release(Store& s) {
   MaintState& m = s.mt;
-  for (MaintLevel& L : m.lv) {
-    Buf* b[] = {&L.lab, &L.tkey, &L.tval, &L.sfirst, &L.scount, &L.soff, &L.pool, &L.ctr};
-    for (Buf* x : b) release(s, *x);
-  }
+  for (MaintLevel& L : m.lv) release_level(s, L);
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
               &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big};
@@ -861,6 +868,7 @@ Status maint_build(Store& s, uint32_t k) {
   if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
   Status st;
   if (!(st = ensure_common(s)).ok()) return st;
+  for (size_t j = k + 1; j < m.lv.size(); ++j) release_level(s, m.lv[j]);
   m.lv.resize(k + 1);
   const uint64_t n = s.n;
   for (uint32_t j = 0; j <= k; ++j)

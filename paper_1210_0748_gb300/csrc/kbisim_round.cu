@@ -2361,17 +2361,10 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   const uint64_t n = s.n, m = s.m;
   const int sms = sm_count(s.device);
   const uint64_t ntiles = std::max<uint64_t>(1, (n + kClassTile - 1) / kClassTile);
-  // temporaries of the relabelling (kept between loads unless the handle has
-  // an HBM budget)
+  // temporaries of the relabelling (kept between loads)
+  InUse use(s, kCacheRelabel);
   Buf &tcnt = s.rl_tcnt, &hot = s.rl_hot, &ost = s.rl_ost;
-  auto fail = [&](Status e) {
-    if (s.budget) {
-      release(s, tcnt);
-      release(s, hot);
-      release(s, ost);
-    }
-    return e;
-  };
+  auto fail = [&](Status e) { return e; };
   if (!(st = ensure(s, tcnt, ntiles * kNumOrder * 8)).ok()) return fail(st);
   if (!(st = ensure(s, hot, std::max<uint64_t>(1, n) * 4)).ok()) return fail(st);
   if (!(st = ensure(s, ost, kNumOrder * 8)).ok()) return fail(st);

@@ -358,16 +358,11 @@ Status scan_u64(Store& s, unsigned long long* a, uint64_t n, unsigned long long*
 }
 
 // Temporaries of one batch: the store's update buffers, kept for the next
-// batch when the handle has no HBM budget (no cudaFree, which would wait for
-// the whole device), released at the end of the batch otherwise.
+// batch.
 struct Bufs {
-  Store& s;
+  InUse use;
   Buf* b;
-  explicit Bufs(Store& st) : s(st), b(st.upd) {}
-  ~Bufs() {
-    if (s.budget)
-      for (int i = 0; i < kUpdBufs; ++i) release(s, b[i]);
-  }
+  explicit Bufs(Store& st) : use(st, kCacheUpd), b(st.upd) {}
 };
 
 // Stage a batch array on the device (copy when it is host memory).
@@ -774,16 +769,18 @@ Status apply_in_place_body(Store& s, const kbisim_batch* bt, const uint32_t* is,
                            const uint32_t* addl, uint64_t* missing_out, bool* taken);
 
 // With an HBM budget the fast path's buffers (the second edge table, claims,
-// degrees) count against it: if they do not fit, the general path runs, and
-// after the batch they are released again.
+// degrees) count against it: if they do not fit, the general path runs.
 Status apply_in_place(Store& s, const kbisim_batch* bt, const uint32_t* is, const uint32_t* it, const uint32_t* il,
                       const uint32_t* ds, const uint32_t* dt, const uint32_t* dl, const uint32_t* addl,
                       uint64_t* missing_out, bool* taken) {
-  Status st = apply_in_place_body(s, bt, is, it, il, ds, dt, dl, addl, missing_out, taken);
-  if (s.budget) {
-    const bool graph_intact = *taken || s.has_graph;
-    for (Buf& b : s.inplace) release(s, b);
-    if (st.code == KBISIM_ERR_BUDGET && !*taken && graph_intact) return Status::Ok();
+  Status st;
+  {
+    InUse use(s, kCacheInplace);
+    st = apply_in_place_body(s, bt, is, it, il, ds, dt, dl, addl, missing_out, taken);
+  }
+  if (s.budget && st.code == KBISIM_ERR_BUDGET && !*taken && s.has_graph) {
+    for (Buf& b : s.inplace) release(s, b);  // room for the general path
+    return Status::Ok();
   }
   return st;
 }
@@ -1083,14 +1080,7 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
   if (!st.ok()) return st;
 
-  // 4. the updated graph replaces the stored one (level buffers are reused
-  //    unless the handle has an HBM budget)
-  if (s.budget) {
-    for (Buf& b : s.level) release(s, b);
-    for (Buf& b : s.out_level) release(s, b);
-    s.level.clear();
-    s.out_level.clear();
-  }
+  // 4. the updated graph replaces the stored one (level buffers are reused)
   for (size_t i = 0; i < s.out_valid.size(); ++i) s.out_valid[i] = false;
   s.has_levels = false;
   s.n = n1;

@@ -80,7 +80,7 @@ class UpdateInfo(ctypes.Structure):
                 ("frontier_nodes", ctypes.c_uint64), ("levels", ctypes.c_uint64), ("in_place", ctypes.c_int)]
 
 
-MAINT_REASONS = {0: "incremental", 1: "off", 2: "no_store", 3: "frontier", 4: "capacity", 5: "deletes"}
+MAINT_REASONS = {0: "incremental", 1: "off", 2: "no_store", 3: "frontier", 4: "capacity", 5: "deletes", 6: "cost"}
 
 
 class RoundStats(ctypes.Structure):
@@ -213,7 +213,7 @@ class KBisim:
 
     def __init__(self, device: int = 0, stream=None, early_stop: bool = True,
                  hash_seed: int = 0x12100748, hash_bits: int = 64, checked: bool = False,
-                 collect_timing: bool = False, hbm_budget_bytes: int = 0, maintain: bool = True):
+                 collect_timing: bool = False, hbm_budget_bytes: int = 0, maintain=True):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -235,7 +235,9 @@ class KBisim:
         opt.checked = 1 if checked else 0
         opt.collect_timing = 1 if collect_timing else 0
         opt.hbm_budget_bytes = hbm_budget_bytes
-        opt.maintain = 1 if maintain else 0
+        # False/0: recompute; True/1: frontier path while it measures cheaper;
+        # "always"/2: frontier path whenever it applies
+        opt.maintain = 2 if maintain in ("always", 2) else (1 if maintain else 0)
         h = ctypes.c_void_p()
         rc = lib.kbisim_create(ctypes.byref(h), ctypes.byref(opt))
         if rc != OK:

@@ -22,6 +22,12 @@ Request kinds: ``update`` (a maintenance batch, then levels 0..k of the
 updated graph, Section 4) and ``rebuild`` (levels 0..k from scratch,
 Algorithm 1).  Each result records the block counts and a digest of the
 level-k identifiers.
+
+Handles recompute on update by default (``maintain=False``): a stream that
+spreads its updates over many graphs at varying k gives each handle few
+updates in a row, so the signature stores of the frontier path (built once
+per graph and k, about one signature pass per level) would rarely pay off;
+``Server(maintain=True)`` turns the timed choice of the library on.
 """
 from __future__ import annotations
 
@@ -97,7 +103,7 @@ class Server:
     """Resident graphs (``synth.Graph`` list) with an initial k each."""
 
     def __init__(self, graphs: Sequence, ks: Sequence[int], *, slots: int = 4, device: int = 0,
-                 hbm_budget: Optional[int] = None):
+                 hbm_budget: Optional[int] = None, maintain=False):
         import torch
         self.torch = torch
         self.device = device
@@ -107,7 +113,7 @@ class Server:
         self.k = list(int(x) for x in ks)
         for g, k in zip(graphs, self.k):
             stream = torch.cuda.Stream(device=device)
-            h = KBisim(device=device, stream=stream)
+            h = KBisim(device=device, stream=stream, maintain=maintain)
             h.build(g, k)
             b = handle_budget(h.device_bytes)
             h.set_hbm_budget(b)

@@ -101,7 +101,7 @@ def test_budget_is_enforced_and_keeps_previous_levels():
         assert kb.device_bytes <= need + 4096
         before = _snapshot(kb, 2)
         with pytest.raises(KBisimError) as e:
-            kb.refine(8)  # eight more levels do not fit
+            kb.refine(200)  # 198 more levels do not fit, even without the idle scratch
         assert e.value.code == ERR_BUDGET
         assert np.array_equal(_snapshot(kb, 2), before)
         assert kb.device_bytes <= need + 4096
@@ -109,6 +109,23 @@ def test_budget_is_enforced_and_keeps_previous_levels():
         with pytest.raises(KBisimError) as e:
             kb.build(synth.config_single_large(scale=1 / 256, seed=3), 3)
         assert e.value.code == ERR_BUDGET
+
+
+def test_budget_drops_idle_scratch_before_failing():
+    """A handle keeps its scratch between calls (the staging of its load,
+    here); when a call needs more than the budget allows, the scratch no
+    running step uses is released first, so the call succeeds."""
+    g = _graph()
+    with KBisim(early_stop=False) as kb:
+        kb.build(g, 2)
+        kb.refine(2)  # the levels the build made become this call's spares
+        held = kb.device_bytes
+        kb.refine(2)
+        assert kb.device_bytes == held  # a repeated call allocates nothing
+        kb.set_hbm_budget(held)
+        res = kb.refine(3)  # one more level: fits once the load's staging is gone
+        assert kb.device_bytes <= held
+        assert_same(res, kb.all_pids(3), oracle_levels(g, 3, early_stop=False))
 
 
 def test_checked_mode_reports_a_bad_index(env):

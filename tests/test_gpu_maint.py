@@ -46,7 +46,7 @@ def test_incremental_updates_equal_the_oracle(early_stop):
     mg = _mg(g)
     k = 4
     paths = []
-    with KBisim(early_stop=early_stop) as kb:
+    with KBisim(early_stop=early_stop, maintain="always") as kb:
         kb.build(g, k)
         for step in range(8):
             add, ins, dels = _random_batch(rng, mg, int(rng.integers(1, 12)), int(rng.integers(0, 8)),
@@ -111,7 +111,7 @@ def test_tables_4_and_5_on_the_frontier_path():
         names = list(base.node_names) + [a for a, _ in upd.add_nodes]
         g = graph_from_edges(len(base.node_names), base.node_label, base.edges)
         ins = [(names.index(a), names.index(b), l) for a, l, b in upd.add_edges]
-        with KBisim(early_stop=False) as kb:
+        with KBisim(early_stop=False, maintain="always") as kb:
             kb.build(g, 2)
             kb.update(2, add_node_label=[l for _, l in upd.add_nodes],
                       ins=tuple(np.array(x, dtype=np.uint32) for x in zip(*ins)))
@@ -129,7 +129,7 @@ def test_switch_back_and_recompute_agree():
     g = synth.config_single_large(scale=1 / 2048, seed=4)  # 7.8K nodes, 125K edges
     mg = _mg(g)
     k = 3
-    with KBisim() as kb, KBisim(maintain=False) as plain:
+    with KBisim(maintain="always") as kb, KBisim(maintain=False) as plain:
         kb.build(g, k)
         plain.build(g, k)
         batches = [_random_batch(rng, mg, 4000, 500, labels=32, node_labels=16),
@@ -180,7 +180,7 @@ def test_long_signatures_in_the_store():
     dup = (np.array([0], np.uint32), hub_t[:1].copy(), hub_l[:1].copy())
     steps = [dict(ins=(np.array([0], np.uint32), np.array([int(hub_t[5]) ^ 1], np.uint32), np.array([2], np.uint32))),
              dict(ins=dup), dict(dels=dup)]
-    with KBisim() as kb:
+    with KBisim(maintain="always") as kb:
         kb.build(g, k)
         for st in steps:
             ins, dels = st.get("ins", ()), st.get("dels", ())
@@ -188,3 +188,36 @@ def test_long_signatures_in_the_store():
             res, _ = kb.update(k, ins=ins, dels=dels)
             assert kb.update_info()["incremental"], kb.update_info()
             assert_same(res, kb.all_pids(k), mg.kbisim(k))
+
+
+def test_timed_choice_between_the_paths():
+    """maintain=True times both paths on the handle: the first update takes
+    the frontier path, the second recomputes to compare (reason "cost"), and
+    later ones take whichever measured cheaper, trying the frontier path again
+    after 16 recomputations.  Every level equals a handle that always
+    recomputes, and the last ones the oracle."""
+    rng = np.random.default_rng(31)
+    g = synth.config_single_large(scale=1 / 512, seed=8)  # 31K nodes, 500K edges
+    mg = _mg(g)
+    k = 3
+    reasons = []
+    with KBisim() as kb, KBisim(maintain=False) as plain:
+        kb.build(g, k)
+        plain.build(g, k)
+        for step in range(24):
+            add, ins, dels = _random_batch(rng, mg, 20, 10, labels=32, node_labels=16)
+            mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+            r1, _ = kb.update(k, ins=ins, dels=dels)
+            r2, _ = plain.update(k, ins=ins, dels=dels)
+            reasons.append(kb.update_info()["reason"])
+            assert list(r1.counts) == list(r2.counts)
+            for lev in range(k + 1):
+                assert np.array_equal(kb.pids(lev), plain.pids(lev)), (step, lev)
+        assert_same(r1, kb.all_pids(k), mg.kbisim(k))
+    assert reasons[0] in ("incremental", "frontier"), reasons
+    assert reasons[1] == "cost", reasons
+    assert set(reasons) <= {"incremental", "frontier", "cost"}, reasons
+    run = 0
+    for r in reasons[2:]:  # never more than 15 recomputations in a row on cost
+        run = run + 1 if r == "cost" else 0
+        assert run <= 15, reasons
