@@ -58,7 +58,7 @@ KERNEL_BYTES = {
 }
 # Out-degree ranges of the signature kernel classes (the library's split).
 SIG_DEGREES = {"sig_small": (0, 64), "sig_medium": (65, 4096), "sig_hub": (4097, None)}
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_powerlaw_16m_256m.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_powerlaw_4m_64m.json")
 
 
 def class_units(g):
@@ -75,17 +75,20 @@ def class_units(g):
 
 def recorded_traffic(cls, scale):
     """DRAM bytes per round of a kernel class from the committed ncu summary, if it
-    was taken on the current kernel sources and the same workload scale."""
+    was taken on the current kernel sources.  The capture is of the same
+    generator at a smaller scale (4M nodes / 64M edges: inputs larger than L2,
+    a few GB on the device); nodes and edges both grow with the scale, and so
+    does every class's traffic, so it is scaled by scale / captured scale."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
     from ncu_summary import source_digest
-    if t.get("source_sha256") != source_digest() or float(t.get("scale", -1)) != float(scale):
+    if t.get("source_sha256") != source_digest() or float(t.get("scale", 0)) <= 0:
         return None
     v = t.get("dram_bytes_per_round", {}).get(cls)
-    return float(v) if v is not None else None
+    return float(v) * float(scale) / float(t["scale"]) if v is not None else None
 
 
 def parse():
@@ -98,6 +101,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-clocks", action="store_true")
+    p.add_argument("--hub-bucket-keys", type=int, default=0, choices=[0, 2048, 4096],
+                   help="hub bucket size (0 = tuned by the library on the first refinement)")
     p.add_argument("--workload", default="single", choices=["single", "batched", "large", "serve", "update"],
                    help="single: the 16M/256M graph (the headline line); batched: 4096 graphs "
                         "(times --scale) in one batched build vs one build per graph; large: the "
@@ -489,7 +494,7 @@ def main():
         args.no_cpu_baseline = True
     E, N = g.num_edges, g.num_nodes
     stream = torch.cuda.Stream(device=local_rank)
-    kb = KBisim(device=local_rank, stream=stream, collect_timing=True)
+    kb = KBisim(device=local_rank, stream=stream, collect_timing=True, hub_bucket_keys=args.hub_bucket_keys)
     kb.load(g)
 
     def barrier():
@@ -569,7 +574,7 @@ def main():
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
             "kernel_roofline": {k: {"achieved": v["achieved"], "frac": v["frac"], "ms_per_call": v["ms_per_call"]}
                                 for k, v in per_class.items()},
-            "gpu_launches": gpu_launches, "clocks": clk}
+            "hub_bucket_keys": kb.hub_bucket_keys, "gpu_launches": gpu_launches, "clocks": clk}
 
     # end to end through the public API: pinned host inputs -> build -> level k to host
     if not args.no_e2e:

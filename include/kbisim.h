@@ -124,6 +124,12 @@ typedef struct {
    * updates (reason KBISIM_MAINT_COST) before trying the frontier path again.
    * 2 = the frontier path whenever it applies, without timing. */
   int maintain;
+  /* Key words a hub bucket holds at most (out-degree > 4096: the hub's keys
+   * are split into buckets by key bits, each deduplicated by one CTA in
+   * shared memory): 2048 or 4096; 0 (default) = tuned once per handle, in the
+   * first full round from level 2 on, by timing the hub pass with each size
+   * (kbisim_hub_bucket_keys reports the choice).  Results do not depend on it. */
+  uint32_t hub_bucket_keys;
 } kbisim_options;
 
 /* Fill *opt with the defaults (stream NULL, device 0, no budget, early stop
@@ -329,6 +335,10 @@ uint64_t kbisim_num_edges(const kbisim_handle *h);
 /* Device bytes the handle holds now (graph, levels, scratch, spares); the
  * quantity options.hbm_budget_bytes bounds.  0 for NULL. */
 uint64_t kbisim_device_bytes(const kbisim_handle *h);
+
+/* Hub bucket size in use (options.hub_bucket_keys, or the tuned choice; 4096
+ * before tuning).  0 for NULL. */
+uint32_t kbisim_hub_bucket_keys(const kbisim_handle *h);
 
 /* Change the handle's HBM budget (options.hbm_budget_bytes; 0 = none) for
  * later calls.  A budget below what the handle holds now is allowed: calls

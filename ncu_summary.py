@@ -4,7 +4,7 @@
 The CSV comes from ``ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
 dram__bytes_write.sum --csv`` over ``bench.py --steps 1 --warmup 2``: every
 launch of the graph load and of three refinements (level 0 and each round).
-Only the last refinement is summarised (from the last ``k_label_hash`` on):
+Only the last refinement is summarised (from its level-0 kernel on):
 the warm-up refinements have already grown any hub bucket that overflows, as
 in the timed steps.  Two outputs:
 
@@ -31,13 +31,13 @@ CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1210_0748
 
 # kernel name -> class of the library's timing (kbisim_kernel_times)
 CLASS_OF = [
-    (r"k_label_hash", "label_group"),
+    (r"k_label_hash|k_l0_collect", "label_group"),
     (r"k_sig_small", "sig_small"),
     (r"k_sig_chunk", "sig_medium"),
     (r"k_hub_sample|k_hub_chunk|k_hub_scatter|k_hub_bucket|k_hub_finish", "sig_hub"),
     (r"k_group_insert", "group"),
     (r"k_group_verify|k_verify_long", "verify"),
-    (r"k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill", "renumber"),
+    (r"k_word_counts|k_tile_sum64|k_scan_tiles|k_tile_scan64|k_pid_fill|k_l0_fill", "renumber"),
 ]
 
 UNITS = {"ns": 1e-9, "nsecond": 1e-9, "us": 1e-6, "usecond": 1e-6, "ms": 1e-3, "msecond": 1e-3,
@@ -91,7 +91,8 @@ def class_of(name: str):
 
 
 def summarise(launches, rounds: int):
-    first = max((i for i, (_, n, _) in enumerate(launches) if n.startswith("k_label_hash")), default=0)
+    first = max((i for i, (_, n, _) in enumerate(launches) if n.startswith(("k_label_hash", "k_l0_collect"))),
+                default=0)
     refine = launches[first:]
     per_kernel = collections.OrderedDict()
     per_class = collections.defaultdict(float)
@@ -123,16 +124,22 @@ def main():
     ap.add_argument("--md", help="write the per-kernel table here")
     ap.add_argument("--traffic", help="write the per-class DRAM bytes record here")
     a = ap.parse_args()
-    per_kernel, total_t, per_call = summarise(load(a.csv), a.rounds)
+    launches = load(a.csv)
+    per_kernel, total_t, per_call = summarise(launches, a.rounds)
+    dram = any("dram__bytes_read.sum" in m for _, _, m in launches)
     lines = ["# Launch list: one refinement, %s" % a.workload, "",
              "Command: `%s`" % a.command, "",
              "%d rounds; per-launch times are cold-cache and serialised (compare shares)." % a.rounds, "",
-             "| kernel | launches | total ms | share | DRAM MB |", "|---|---:|---:|---:|---:|"]
+             "| kernel | launches | total ms | share |" + (" DRAM MB |" if dram else ""),
+             "|---|---:|---:|---:|" + ("---:|" if dram else "")]
     for name, (n, t, b) in sorted(per_kernel.items(), key=lambda kv: -kv[1][1]):
-        lines.append("| `%s` | %d | %.3f | %.1f%% | %.1f |" % (name, n, t * 1e3, 100 * t / total_t, b / 1e6))
-    lines += ["", "DRAM bytes per call of each kernel class (per round for signatures, per level otherwise):", ""]
-    for c, b in sorted(per_call.items()):
-        lines.append("* %s: %.1f MB" % (c, b / 1e6))
+        lines.append("| `%s` | %d | %.3f | %.1f%% |" % (name, n, t * 1e3, 100 * t / total_t) +
+                     (" %.1f |" % (b / 1e6) if dram else ""))
+    if dram:
+        lines += ["", "DRAM bytes per call of each kernel class (per round for signatures, per level otherwise):",
+                  ""]
+        for c, b in sorted(per_call.items()):
+            lines.append("* %s: %.1f MB" % (c, b / 1e6))
     text = "\n".join(lines) + "\n"
     if a.md:
         with open(a.md, "w") as f:

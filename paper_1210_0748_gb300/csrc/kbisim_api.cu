@@ -673,6 +673,7 @@ void kbisim_default_options(kbisim_options* opt) {
   opt->checked = 0;
   opt->collect_timing = 0;
   opt->maintain = 1;
+  opt->hub_bucket_keys = 0;
 }
 
 int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
@@ -682,6 +683,7 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   if (opt) o = *opt; else kbisim_default_options(&o);
   if (o.hash_bits == 0 || o.hash_bits > 64) return KBISIM_ERR_INVALID_ARG;
   if (o.maintain < 0 || o.maintain > 2) return KBISIM_ERR_INVALID_ARG;
+  if (o.hub_bucket_keys != 0 && o.hub_bucket_keys != 2048 && o.hub_bucket_keys != 4096) return KBISIM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -705,6 +707,10 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   s.checked = o.checked != 0;
   s.timing = o.collect_timing != 0;
   s.maintain = o.maintain;
+  if (o.hub_bucket_keys) {
+    s.hub_ucap = o.hub_bucket_keys;
+    s.hub_tune = 2;
+  }
   void* hp = nullptr;
   if (cudaMallocHost(&hp, 16 * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -842,6 +848,8 @@ const uint32_t* kbisim_pids_device(kbisim_handle* h, uint32_t level) {
 uint64_t kbisim_num_nodes(const kbisim_handle* h) { return h ? h->s.n : 0; }
 uint64_t kbisim_num_edges(const kbisim_handle* h) { return h ? h->s.m : 0; }
 uint64_t kbisim_device_bytes(const kbisim_handle* h) { return h ? (uint64_t)h->s.bytes_held : 0; }
+
+uint32_t kbisim_hub_bucket_keys(const kbisim_handle* h) { return h ? h->s.hub_ucap : 0u; }
 
 int kbisim_set_hbm_budget(kbisim_handle* h, uint64_t bytes) {
   if (!h) return KBISIM_ERR_INVALID_ARG;

@@ -29,7 +29,6 @@ constexpr int kSmallChunkThreads = 128;  // threads of the chunk kernel for out-
 constexpr int kChunkItems = 8;     // edges per thread
 constexpr int kChunkEdges = kChunkThreads * kChunkItems;  // 4096 = kBlockMax
 constexpr int kChunkMaxNodes = 64; // nodes per medium chunk (each has > kSmallMax edges)
-constexpr int kHubBucketTarget = 2048;  // expected distinct keys per hub bucket
 constexpr int kHubChunk = kChunkEdges;  // hub edges per chunk CTA
 constexpr int kSmallClasses = 8;        // out-degree 0, 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64
 constexpr int kClassWarp = kSmallClasses, kClassWarp2 = kSmallClasses + 1, kClassBlock = kSmallClasses + 2,
@@ -276,7 +275,6 @@ struct Store {
   std::vector<uint32_t> h_hub_xbits;  // per hub: more buckets, after a bucket's set filled
   std::vector<uint32_t> h_hub_shift;  // per hub: larger buckets, after a bucket's capacity was exceeded
   std::vector<uint8_t> h_hub_force;   // per hub: deduplicating chunk pass, after a scatter overflowed
-  std::vector<uint32_t> h_hub_degbits;
   std::vector<uint64_t> h_hub_deg;
 
   // levels (all kept: history for extend / maintenance), internal order
@@ -342,6 +340,14 @@ struct Store {
   long fault_alloc = -1;
   uint32_t fault_timeout_round = 0;
   bool fault_corrupt_dst = false;
+
+  // hub bucket size (key words at most per bucket: 2048 or 4096) and its
+  // tuning: 1 = the next full round from level 2 on times both sizes and
+  // keeps the faster, 2 = chosen (tuned, or fixed by options.hub_bucket_keys)
+  uint32_t hub_ucap = 4096;
+  int hub_tune = 1;
+  bool tune_now = false;
+  float hub_tune_ms[2] = {0, 0};  // measured hub pass of each size (4096, 2048)
 
   size_t bytes_held = 0;
   uint32_t busy = 0;           // scratch groups (kCache*) in use by the running call
@@ -410,6 +416,12 @@ Status compute_level0(Store& s);                  // pId_0 into level[0]
 // Work lists of the degree classes from s.offsets (after a relabel, or after
 // a batch applied in place); `fresh` drops what hub buckets learned.
 Status build_chunk_lists(Store& s, bool fresh);
+struct HubGrowth {
+  std::vector<uint32_t> orig, xbits, shift;
+  std::vector<uint8_t> force;
+};
+Status save_hub_growth(Store& s, HubGrowth* g);
+Status restore_hub_growth(Store& s, const HubGrowth& g);
 Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
 // Signatures of the nodes whose bit is set in fmask (bitmap over internal ids;
 // NULL = every node) from identifiers prev (internal order), as 64-bit

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kbisim_internal.cuh"
@@ -713,7 +714,7 @@ __device__ __forceinline__ void hub_fail(const SigArgs& a, const HubArgs& h, uin
   atomicOr(a.err, e);
 }
 
-constexpr int kHubUcap = 4096;         // key words per bucket at most
+constexpr int kHubUcapMax = 4096;      // key words per bucket at most (the larger bucket variant)
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
 constexpr int kHubSample = 128;        // keys sampled per hub to choose its chunk pass
 constexpr int kHubSamplePairs = 16;    // equal sampled pairs from which a hub keeps the chunk set
@@ -901,10 +902,10 @@ __device__ __forceinline__ int pow2_insert(uint32_t base, uint32_t hmask, K k) {
 
 constexpr int kBucketThreads = 256, kBucketItems = 8;
 
-template <typename K>
+template <typename K, int UCAP>
 struct BucketSmem {
-  K set[2 * kHubUcap];
-  K uniq[kHubUcap];
+  K set[2 * UCAP];
+  K uniq[UCAP];
   uint32_t cnt, empty, full, lo, hi, last;
   unsigned long long obase;
 };
@@ -912,10 +913,10 @@ struct BucketSmem {
 // One CTA per hub bucket (grid-stride): distinct keys of the bucket into a
 // shared set and list, then appended at the hub's CSR offset, their term
 // sums added to the hub's.
-template <typename K>
+template <typename K, int UCAP>
 __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem_raw[];
-  BucketSmem<K>& sm = *reinterpret_cast<BucketSmem<K>*>(smem_raw);
+  BucketSmem<K, UCAP>& sm = *reinterpret_cast<BucketSmem<K, UCAP>*>(smem_raw);
   const uint32_t tid = threadIdx.x, lane = tid & 31;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm.set);
   K* out = static_cast<K*>(a.sigkey);
@@ -946,7 +947,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       continue;
     }
     uint32_t hcap = 64;
-    while (hcap < 2 * n && hcap < 2 * kHubUcap) hcap <<= 1;
+    while (hcap < 2 * n && hcap < 2 * UCAP) hcap <<= 1;
     {
       uint4* s4 = reinterpret_cast<uint4*>(sm.set);
       const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -970,6 +971,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       }
 #pragma unroll 1
       for (int t = 0; t < kBucketItems; ++t) {
+        if (i0 + (uint32_t)t * kBucketThreads >= n) break;  // the same for the whole CTA
         const uint32_t i = i0 + tid + t * kBucketThreads;
         const K k = kk[0];
 #pragma unroll
@@ -991,7 +993,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
         base = __shfl_sync(kFull, base, 0);
         const uint32_t q = base + __popc(fm & lanes_below(lane));
         if (fresh) {
-          if (q < (uint32_t)kHubUcap) sm.uniq[q] = k; else sm.full = 1u;
+          if (q < (uint32_t)UCAP) sm.uniq[q] = k; else sm.full = 1u;
         }
       }
     }
@@ -1855,7 +1857,11 @@ Status set_smem_attrs_for() {
 
   if (e == cudaSuccess) e = set_smem_attrs_label<uint32_t, K>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BucketSmem<K>));
+    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcapMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BucketSmem<K, kHubUcapMax>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcapMax / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BucketSmem<K, kHubUcapMax / 2>));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)verify_ws_bytes<K>());
@@ -2010,13 +2016,13 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   v.n_out = sc + 1;
   // only nodes not alone in their previous block are inserted
   const uint64_t ins = use_alone ? na - std::min(na, s.n_alone) : na;
+  const unsigned ins_grid = resident_blocks(k_group_insert, kInsThreads, 0, sms);
   const uint64_t tcap = std::min<uint64_t>(s.tcap, table_capacity(ins));
   g.tmask = tcap - 1;
   {
     TimedScope ts(s, KBISIM_KERNEL_OTHER, 0);
     cudaMemsetAsync(s.table.p, 0xFF, tcap * 8, s.stream);
   }
-  const unsigned ins_grid = resident_blocks(k_group_insert, kInsThreads, 0, sms);
   const unsigned iblocks = (unsigned)std::min<uint64_t>((na + kInsChunk - 1) / kInsChunk, ins_grid);
   {
     TimedScope ts(s, KBISIM_KERNEL_GROUP, na ? 1 : 0);
@@ -2069,20 +2075,24 @@ Status group_and_rank(Store& s, int mode, const uint32_t* prev, bool key64, uint
   return Status::Ok();
 }
 
-// (Re)build the per-hub bucket table for the current extra bits: hub i has
-// 2^(bits_i + extra) buckets of cap_i key words each, cap_i twice the mean
-// bucket load plus a margin (at most kHubUcap).
+// (Re)build the per-hub bucket table for the bucket size s.hub_ucap and the
+// current extra bits: hub i has 2^(bits_i + extra) buckets of cap_i key words
+// each, bits_i the least with degree <= (hub_ucap / 2) << bits_i, cap_i twice
+// the mean bucket load plus a margin (at most hub_ucap).
 Status hub_layout(Store& s) {
   Status st;
   std::vector<uint32_t> bits(s.n_hub), cap(s.n_hub);
   std::vector<uint64_t> bbase(s.n_hub + 1, 0), tbase(s.n_hub, 0);
   uint64_t words = 0;
+  const uint64_t target = s.hub_ucap / 2;
   for (uint64_t i = 0; i < s.n_hub; ++i) {
-    bits[i] = s.h_hub_degbits[i] + s.h_hub_xbits[i];
+    uint32_t db = 0;
+    while ((target << db) < s.h_hub_deg[i]) ++db;
+    bits[i] = db + s.h_hub_xbits[i];
     const uint64_t nb = 1ull << bits[i];
     bbase[i + 1] = bbase[i] + nb;
     const uint64_t mean = (s.h_hub_deg[i] + nb - 1) / nb;
-    cap[i] = (uint32_t)std::min<uint64_t>(s.h_hub_deg[i], std::min<uint64_t>(kHubUcap, 2 * mean + 256)
+    cap[i] = (uint32_t)std::min<uint64_t>(s.h_hub_deg[i], std::min<uint64_t>(s.hub_ucap, 2 * mean + 256)
                                                                 << s.h_hub_shift[i]);
     tbase[i] = words;
     words += nb * cap[i];
@@ -2156,68 +2166,126 @@ Status run_signatures(Store& s, const SigArgs& a) {
   }
   if (!(st = launch_check("k_sig_chunk")).ok()) return st;
   if (s.n_hub) {
-    for (int attempt = 0;; ++attempt) {
-      if (!(st = ensure(s, s.hub_tmp, s.hub_tmp_words * sizeof(K))).ok()) return st;
-      HubArgs h;
-      h.first = s.class_start[kClassHub];
-      h.hub_bits = ptr<uint32_t>(s.hub_bits);
-      h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
-      h.hub_cap = ptr<uint32_t>(s.hub_cap);
-      h.hub_tbase = ptr<uint64_t>(s.hub_tbase);
-      h.bucket_hub = ptr<uint32_t>(s.bucket_hub);
-      h.chunks = ptr<uint4>(s.hub_chunks);
-      h.cursor = ptr<uint32_t>(s.hub_cursor);
-      h.hub_cur = ptr<unsigned long long>(s.hub_acc);
-      h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
+    auto run_hubs = [&]() -> Status {
+      Status st;
+      for (int attempt = 0;; ++attempt) {
+        if (!(st = ensure(s, s.hub_tmp, s.hub_tmp_words * sizeof(K))).ok()) return st;
+        HubArgs h;
+        h.first = s.class_start[kClassHub];
+        h.hub_bits = ptr<uint32_t>(s.hub_bits);
+        h.hub_bbase = ptr<uint64_t>(s.hub_bbase);
+        h.hub_cap = ptr<uint32_t>(s.hub_cap);
+        h.hub_tbase = ptr<uint64_t>(s.hub_tbase);
+        h.bucket_hub = ptr<uint32_t>(s.bucket_hub);
+        h.chunks = ptr<uint4>(s.hub_chunks);
+        h.cursor = ptr<uint32_t>(s.hub_cursor);
+        h.hub_cur = ptr<unsigned long long>(s.hub_acc);
+        h.hub_term = reinterpret_cast<uint32_t*>(h.hub_cur + s.n_hub);
         h.tmp = s.hub_tmp.p;
-      h.mode = ptr<uint8_t>(s.hub_mode);
-      h.force = ptr<uint8_t>(s.hub_force);
-      h.hub_err = ptr<uint32_t>(s.hub_err);
-      {
-        // each hub's chunks run either the deduplicating pass or the plain
-        // scatter, as its key sample says; both kernels cover all chunks and
-        // skip those of the other kind
-        TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 5);
-        cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
-        cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
-        cudaMemsetAsync(s.hub_err.p, 0, s.n_hub * 4, s.stream);
-        k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(a, h, s.n_hub);
-        k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
-        k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
-        const unsigned g = (unsigned)std::min<uint64_t>(
-            s.n_hub_buckets, resident_blocks(k_hub_bucket<K>, kBucketThreads, sizeof(BucketSmem<K>), sms));
-        k_hub_bucket<K><<<g, kBucketThreads, sizeof(BucketSmem<K>), s.stream>>>(a, h, s.n_hub_buckets);
-        k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(a, h, s.n_hub);
-      }
-      if (!(st = launch_check("hub kernels")).ok()) return st;
-      uint32_t e = 0;
-      st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
-      if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-      if (!st.ok()) return st;
-      if (!(e & (kErrHubOverflow | kErrHubSet))) break;
-      if (attempt >= 40) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
-      std::vector<uint32_t> herr(s.n_hub);
-      std::vector<uint8_t> hmode(s.n_hub);
-      st = cuda_check(cudaMemcpyAsync(herr.data(), s.hub_err.p, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream),
-                      "hub flags");
-      if (st.ok())
-        st = cuda_check(cudaMemcpyAsync(hmode.data(), s.hub_mode.p, s.n_hub, cudaMemcpyDeviceToHost, s.stream),
-                        "hub modes");
-      if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-      if (!st.ok()) return st;
-      for (uint64_t i = 0; i < s.n_hub; ++i) {
-        // a bucket overflowed (a key repeated many times): larger buckets for
-        // the hub, up to its degree, or, once the scatter has overflowed
-        // buckets kHubScatterShiftMax times larger than the first, the
-        // deduplicating pass; too many distinct keys in a bucket: more buckets
-        if (herr[i] & kErrHubOverflow) {
-          if (hmode[i] && s.h_hub_shift[i] >= kHubScatterShiftMax) s.h_hub_force[i] = 1;
-          else s.h_hub_shift[i] += 1;
+        h.mode = ptr<uint8_t>(s.hub_mode);
+        h.force = ptr<uint8_t>(s.hub_force);
+        h.hub_err = ptr<uint32_t>(s.hub_err);
+        {
+          // each hub's chunks run either the deduplicating pass or the plain
+          // scatter, as its key sample says; both kernels cover all chunks and
+          // skip those of the other kind
+          TimedScope ts(s, KBISIM_KERNEL_SIG_HUB, 5);
+          cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
+          cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
+          cudaMemsetAsync(s.hub_err.p, 0, s.n_hub * 4, s.stream);
+          k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(a, h, s.n_hub);
+          k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
+          k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
+          if (s.hub_ucap == (uint32_t)kHubUcapMax) {
+            constexpr int U = kHubUcapMax;
+            const unsigned g = (unsigned)std::min<uint64_t>(
+                s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
+            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(a, h, s.n_hub_buckets);
+          } else {
+            constexpr int U = kHubUcapMax / 2;
+            const unsigned g = (unsigned)std::min<uint64_t>(
+                s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
+            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(a, h, s.n_hub_buckets);
+          }
+          k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(a, h, s.n_hub);
         }
-        if (herr[i] & kErrHubSet) s.h_hub_xbits[i] += 1;
+        if (!(st = launch_check("hub kernels")).ok()) return st;
+        uint32_t e = 0;
+        st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), "read err");
+        if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+        if (!st.ok()) return st;
+        if (!(e & (kErrHubOverflow | kErrHubSet))) return Status::Ok();
+        if (attempt >= 40) return Status::Err(KBISIM_ERR_TIMEOUT, "hub bucket overflow persists");
+        std::vector<uint32_t> herr(s.n_hub);
+        std::vector<uint8_t> hmode(s.n_hub);
+        st = cuda_check(cudaMemcpyAsync(herr.data(), s.hub_err.p, s.n_hub * 4, cudaMemcpyDeviceToHost, s.stream),
+                        "hub flags");
+        if (st.ok())
+          st = cuda_check(cudaMemcpyAsync(hmode.data(), s.hub_mode.p, s.n_hub, cudaMemcpyDeviceToHost, s.stream),
+                          "hub modes");
+        if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+        if (!st.ok()) return st;
+        for (uint64_t i = 0; i < s.n_hub; ++i) {
+          // a bucket overflowed (a key repeated many times): larger buckets for
+          // the hub, up to its degree, or, once the scatter has overflowed
+          // buckets kHubScatterShiftMax times larger than the first, the
+          // deduplicating pass; too many distinct keys in a bucket: more buckets
+          if (herr[i] & kErrHubOverflow) {
+            if (hmode[i] && s.h_hub_shift[i] >= kHubScatterShiftMax) s.h_hub_force[i] = 1;
+            else s.h_hub_shift[i] += 1;
+          }
+          if (herr[i] & kErrHubSet) s.h_hub_xbits[i] += 1;
+        }
+        if (!(st = hub_layout(s)).ok()) return st;
+        cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
       }
+    };
+    if (!s.tune_now) return run_hubs();
+    // tuning (once per handle, on a full round from level 2 on): each bucket
+    // size runs the hub pass twice, the second time timed (the first settles
+    // bucket growth); the faster size is kept.  Every pass writes the same
+    // signatures, so the round's result is the last pass's.
+    const uint32_t sizes[2] = {(uint32_t)kHubUcapMax, (uint32_t)kHubUcapMax / 2};
+    // bucket growth is learned per size: each starts from the growth before
+    // tuning, and the chosen size keeps its own
+    const std::vector<uint32_t> x0 = s.h_hub_xbits, sh0 = s.h_hub_shift;
+    const std::vector<uint8_t> f0 = s.h_hub_force;
+    std::vector<uint32_t> x1, sh1;
+    std::vector<uint8_t> f1;
+    cudaEvent_t ev[2];
+    if (!(st = cuda_check(cudaEventCreate(&ev[0]), "event")).ok()) return st;
+    if (!(st = cuda_check(cudaEventCreate(&ev[1]), "event")).ok()) {
+      cudaEventDestroy(ev[0]);
+      return st;
+    }
+    for (int c = 0; c < 2 && st.ok(); ++c) {
+      if (c == 1) {
+        x1.swap(s.h_hub_xbits);
+        sh1.swap(s.h_hub_shift);
+        f1.swap(s.h_hub_force);
+        s.h_hub_xbits = x0;
+        s.h_hub_shift = sh0;
+        s.h_hub_force = f0;
+      }
+      s.hub_ucap = sizes[c];
+      if (!(st = hub_layout(s)).ok()) break;
+      if (!(st = run_hubs()).ok()) break;
+      cudaEventRecord(ev[0], s.stream);
+      if (!(st = run_hubs()).ok()) break;
+      cudaEventRecord(ev[1], s.stream);
+      if (!(st = cuda_check(cudaEventSynchronize(ev[1]), "event")).ok()) break;
+      cudaEventElapsedTime(&s.hub_tune_ms[c], ev[0], ev[1]);
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (!st.ok()) return st;
+    s.hub_tune = 2;
+    if (s.hub_tune_ms[0] <= s.hub_tune_ms[1]) {
+      s.hub_ucap = sizes[0];
+      s.h_hub_xbits.swap(x1);
+      s.h_hub_shift.swap(sh1);
+      s.h_hub_force.swap(f1);
       if (!(st = hub_layout(s)).ok()) return st;
-      cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
     }
   }
   return Status::Ok();
@@ -2254,6 +2322,58 @@ uint32_t bits_for(uint64_t v) {  // bits needed to represent values 0..v
 
 }  // namespace
 
+// Bucket growth of the hubs, keyed by original node id: a graph laid out
+// again after an update keeps what its hubs' buckets learned, instead of
+// overflowing and growing them again in the next refinement.
+Status save_hub_growth(Store& s, HubGrowth* g) {
+  g->orig.clear();
+  g->xbits.clear();
+  g->shift.clear();
+  g->force.clear();
+  if (!s.has_graph || !s.n_hub || s.h_hub_xbits.size() != s.n_hub) return Status::Ok();
+  bool any = false;
+  for (uint64_t i = 0; i < s.n_hub && !any; ++i) any = s.h_hub_xbits[i] || s.h_hub_shift[i] || s.h_hub_force[i];
+  if (!any) return Status::Ok();
+  std::vector<uint32_t> p2o(s.n_hub);
+  Status st = cuda_check(cudaMemcpyAsync(p2o.data(), ptr<uint32_t>(s.p2o) + s.class_start[kClassHub], s.n_hub * 4,
+                                         cudaMemcpyDeviceToHost, s.stream), "hub ids");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  for (uint64_t i = 0; i < s.n_hub; ++i)
+    if (s.h_hub_xbits[i] || s.h_hub_shift[i] || s.h_hub_force[i]) {
+      g->orig.push_back(p2o[i]);
+      g->xbits.push_back(s.h_hub_xbits[i]);
+      g->shift.push_back(s.h_hub_shift[i]);
+      g->force.push_back(s.h_hub_force[i]);
+    }
+  return Status::Ok();
+}
+
+Status restore_hub_growth(Store& s, const HubGrowth& g) {
+  if (g.orig.empty() || !s.has_graph || !s.n_hub) return Status::Ok();
+  std::vector<uint32_t> p2o(s.n_hub);
+  Status st = cuda_check(cudaMemcpyAsync(p2o.data(), ptr<uint32_t>(s.p2o) + s.class_start[kClassHub], s.n_hub * 4,
+                                         cudaMemcpyDeviceToHost, s.stream), "hub ids");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  std::unordered_map<uint32_t, size_t> at;
+  at.reserve(g.orig.size() * 2);
+  for (size_t j = 0; j < g.orig.size(); ++j) at[g.orig[j]] = j;
+  s.h_hub_xbits.resize(s.n_hub, 0);
+  s.h_hub_shift.resize(s.n_hub, 0);
+  s.h_hub_force.resize(s.n_hub, 0);
+  bool changed = false;
+  for (uint64_t i = 0; i < s.n_hub; ++i) {
+    const auto it = at.find(p2o[i]);
+    if (it == at.end()) continue;
+    s.h_hub_xbits[i] = std::max(s.h_hub_xbits[i], g.xbits[it->second]);
+    s.h_hub_shift[i] = std::max(s.h_hub_shift[i], g.shift[it->second]);
+    s.h_hub_force[i] = std::max(s.h_hub_force[i], g.force[it->second]);
+    changed = true;
+  }
+  return changed ? hub_layout(s) : Status::Ok();
+}
+
 // ---------------------------------------------------------------------------
 // Relabelling and degree classes (once per graph)
 // ---------------------------------------------------------------------------
@@ -2269,7 +2389,6 @@ Status build_chunk_lists(Store& s, bool fresh) {
     s.h_hub_shift.assign(s.n_hub, 0);
     s.h_hub_force.assign(s.n_hub, 0);
   }
-  s.h_hub_degbits.assign(s.n_hub, 0);
   s.h_hub_deg.assign(s.n_hub, 0);
   s.hub_edges = 0;
   s.n_hub_chunks = 0;
@@ -2285,9 +2404,6 @@ Status build_chunk_lists(Store& s, bool fresh) {
     for (uint64_t i = 0; i < s.n_hub; ++i) {
       cstart[i] = (uint32_t)chunks.size();
       const uint64_t d = hoff[i + 1] - hoff[i];
-      uint32_t bits = 0;
-      while (((uint64_t)kHubBucketTarget << bits) < d) ++bits;
-      s.h_hub_degbits[i] = bits;
       s.h_hub_deg[i] = d;
       s.hub_edges += d;
       for (uint64_t b = 0; b < d; b += kHubChunk) {
@@ -2427,9 +2543,163 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   return cuda_check(cudaStreamSynchronize(s.stream), "sync");
 }
 
+// ---- level 0 when few labels occur (Definition 2: pId_0 groups nodes by
+// label) ------------------------------------------------------------------
+// A table of kL0Slots 64-bit slots (label << 32 | smallest original id) and a
+// node count per slot.  Each CTA first gathers the labels of its node range in
+// a shared copy, so the global table sees one update per label per CTA.  If a
+// shared or the global table fills (more labels than it holds) the general
+// path (hash, grouping, exact check, renumbering) computes the level instead.
+constexpr int kL0Slots = 4096;        // global table: labels at most kL0Slots / 2
+constexpr int kL0SmemSlots = 1024;    // per CTA
+constexpr int kL0Threads = 256;
+constexpr unsigned long long kL0Empty = ~0ull;  // (0xFFFFFFFF, 0xFFFFFFFF): no original id is 0xFFFFFFFF
+
+__device__ __forceinline__ uint32_t l0_home(uint32_t label, uint32_t mask) {
+  return (label * 0x9E3779B1u >> 7) & mask;  // Fibonacci hashing, then the slot bits
+}
+
+// Insert (label, id) into a table of 64-bit slots: the slot of the label keeps
+// the smallest id; returns the slot, or -1 if the table is full (shared or
+// global memory, through generic addressing).
+__device__ __forceinline__ int l0_insert(unsigned long long* tab, uint32_t mask, uint32_t label, uint32_t id) {
+  const unsigned long long v = ((unsigned long long)label << 32) | id;
+  uint32_t at = l0_home(label, mask);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    const unsigned long long cur = atomicCAS(tab + at, kL0Empty, v);
+    if (cur == kL0Empty) return (int)at;
+    if ((uint32_t)(cur >> 32) == label) {
+      if ((uint32_t)cur > id) atomicMin(tab + at, v);
+      return (int)at;
+    }
+    at = (at + 1) & mask;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kL0Threads) k_l0_collect(uint64_t n_alive, const uint32_t* nlabel, const uint32_t* p2o,
+                                                           unsigned long long* gtab, uint32_t* gcnt, uint32_t* err) {
+  __shared__ unsigned long long tab[kL0SmemSlots];
+  __shared__ uint32_t cnt[kL0SmemSlots];
+  __shared__ uint32_t full;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kL0SmemSlots; i += kL0Threads) {
+    tab[i] = kL0Empty;
+    cnt[i] = 0;
+  }
+  if (threadIdx.x == 0) full = 0;
+  __syncthreads();
+  const uint64_t per = (n_alive + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo0 = (uint64_t)blockIdx.x * per;
+  const uint64_t lo = lo0 < n_alive ? lo0 : n_alive, hi = lo + per < n_alive ? lo + per : n_alive;
+  for (uint64_t p = lo + threadIdx.x; p < hi; p += kL0Threads) {
+    const int at = l0_insert(tab, kL0SmemSlots - 1, nlabel[p], p2o[p]);
+    if (at < 0) full = 1;
+    else atomicAdd(&cnt[at], 1u);
+  }
+  __syncthreads();
+  if (full) {
+    if (threadIdx.x == 0) atomicOr(err, 1u);
+    return;
+  }
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kL0SmemSlots; i += kL0Threads) {
+    const unsigned long long v = tab[i];
+    if (v == kL0Empty) continue;
+    const int at = l0_insert(gtab, kL0Slots - 1, (uint32_t)(v >> 32), (uint32_t)v);
+    if (at < 0) atomicOr(err, 1u);
+    else atomicAdd(&gcnt[at], cnt[i]);
+  }
+}
+
+// pId_0 of every node from the ranked table: rank[slot] = block id, and the
+// node is alone in its block when its label's count is 1.
+__global__ void __launch_bounds__(kL0Threads) k_l0_fill(uint64_t n, uint64_t n_alive, const uint32_t* nlabel,
+                                                        const unsigned long long* gtab, const uint32_t* rank,
+                                                        const uint32_t* gcnt, uint32_t* pid, uint8_t* alone) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+    if (p >= n_alive) {
+      pid[p] = kDead;
+      continue;
+    }
+    const uint32_t label = nlabel[p];
+    uint32_t at = l0_home(label, kL0Slots - 1);
+    for (uint32_t t = 0; t < (uint32_t)kL0Slots; ++t) {  // the label is in the table: the loop ends at its slot
+      const unsigned long long v = __ldg(gtab + at);
+      if (v != kL0Empty && (uint32_t)(v >> 32) == label) break;
+      at = (at + 1) & (kL0Slots - 1);
+    }
+    pid[p] = __ldg(rank + at);
+    alone[p] = __ldg(gcnt + at) == 1u ? 1 : 0;
+  }
+}
+
+// Level 0 by the label table; *done = false when there are too many labels
+// (the general path then runs).
+Status level0_few_labels(Store& s, bool* done) {
+  *done = false;
+  const uint64_t n = s.n, na = s.n_alive;
+  if (!na) return Status::Ok();
+  Status st;
+  // the table, counts and ranks in the grouping table's buffer (sized for n
+  // nodes, so large enough whenever there are nodes)
+  const size_t bytes = kL0Slots * 8 + kL0Slots * 4 + kL0Slots * 4 + 16;
+  if (s.table.cap < bytes) return Status::Ok();
+  unsigned long long* gtab = ptr<unsigned long long>(s.table);
+  uint32_t* gcnt = reinterpret_cast<uint32_t*>(gtab + kL0Slots);
+  uint32_t* grank = gcnt + kL0Slots;
+  uint32_t* err = grank + kL0Slots;
+  const int sms = sm_count(s.device);
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+  {
+    TimedScope ts(s, KBISIM_KERNEL_LABEL_GROUP, 1);
+    cudaMemsetAsync(gtab, 0xFF, kL0Slots * 8, s.stream);
+    cudaMemsetAsync(gcnt, 0, kL0Slots * 4 * 2 + 16, s.stream);
+    const unsigned g = (unsigned)std::min<uint64_t>(grid_for(na, 2048), (uint64_t)sms * 8);
+    k_l0_collect<<<g, kL0Threads, 0, s.stream>>>(na, ptr<uint32_t>(s.nlabel), ptr<uint32_t>(s.p2o), gtab, gcnt, err);
+  }
+  if (!(st = launch_check("k_l0_collect")).ok()) return st;
+  std::vector<unsigned long long> tab(kL0Slots);
+  std::vector<uint32_t> cnt(kL0Slots + 1);
+  st = cuda_check(cudaMemcpyAsync(tab.data(), gtab, kL0Slots * 8, cudaMemcpyDeviceToHost, s.stream), "level 0");
+  if (st.ok())
+    st = cuda_check(cudaMemcpyAsync(cnt.data(), gcnt, kL0Slots * 4, cudaMemcpyDeviceToHost, s.stream), "level 0");
+  if (st.ok()) st = cuda_check(cudaMemcpyAsync(&cnt[kL0Slots], err, 4, cudaMemcpyDeviceToHost, s.stream), "level 0");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok() || cnt[kL0Slots]) return st;  // too many labels: the general path
+  // blocks ranked by their smallest original id
+  std::vector<std::pair<uint32_t, uint32_t>> heads;  // (smallest id, slot)
+  uint64_t alone = 0;
+  for (uint32_t i = 0; i < (uint32_t)kL0Slots; ++i)
+    if (tab[i] != kL0Empty) {
+      heads.push_back({(uint32_t)tab[i], i});
+      alone += cnt[i] == 1 ? 1 : 0;
+    }
+  if (heads.size() > (size_t)kL0Slots / 2) return Status::Ok();  // long probe runs: the general path
+  std::sort(heads.begin(), heads.end());
+  std::vector<uint32_t> rank(kL0Slots, 0);
+  for (size_t r = 0; r < heads.size(); ++r) rank[heads[r].second] = (uint32_t)r;
+  st = cuda_check(cudaMemcpyAsync(grank, rank.data(), kL0Slots * 4, cudaMemcpyHostToDevice, s.stream), "level 0");
+  if (!st.ok()) return st;
+  {
+    TimedScope ts(s, KBISIM_KERNEL_RENUMBER, 1);
+    const unsigned g = (unsigned)std::min<uint64_t>(grid_for(n, kL0Threads), (uint64_t)sms * 16);
+    k_l0_fill<<<g, kL0Threads, 0, s.stream>>>(n, na, ptr<uint32_t>(s.nlabel), gtab, grank, gcnt,
+                                             ptr<uint32_t>(s.level[0]), ptr<uint8_t>(s.alone));
+  }
+  if (!(st = launch_check("k_l0_fill")).ok()) return st;
+  if (s.checked && !(st = check_below(s, ptr<uint32_t>(s.level[0]), na, heads.size(), "identifiers")).ok())
+    return st;
+  s.counts[0] = heads.size();
+  s.n_alone = alone;
+  *done = true;
+  return Status::Ok();
+}
+
 Status compute_level0(Store& s) {
   Status st = ensure_round_scratch(s);
   if (!st.ok()) return st;
+  bool done = false;
+  if (!(st = level0_few_labels(s, &done)).ok()) return st;
+  if (done) return Status::Ok();
   const int sms = sm_count(s.device);
   const unsigned blocks = (unsigned)std::min<uint64_t>(grid_for(s.n_alive, 256), (uint64_t)sms * 16);
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
@@ -2503,10 +2773,12 @@ Status compute_round(Store& s, uint32_t i) {
   const uint32_t pbits = bits_for(s.counts[i - 1] ? s.counts[i - 1] - 1 : 0);
   const bool key64 = pbits + s.label_bits > 32;
   a.pbits = (int)pbits;
+  s.tune_now = s.hub_tune == 1 && i >= 2 && !s.round_mask && s.n_hub;
   if (s.label8)
     st = key64 ? run_signatures<uint8_t, uint64_t>(s, a) : run_signatures<uint8_t, uint32_t>(s, a);
   else
     st = key64 ? run_signatures<uint32_t, uint64_t>(s, a) : run_signatures<uint32_t, uint32_t>(s, a);
+  s.tune_now = false;
   if (!st.ok()) return st;
   if (s.round_mask && s.n_alive) {
     const int sms = sm_count(s.device);

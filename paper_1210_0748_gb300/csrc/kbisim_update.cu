@@ -927,7 +927,18 @@ Status apply_in_place_body(Store& s, const kbisim_batch* bt, const uint32_t* is,
   return cuda_check(cudaStreamSynchronize(s.stream), "batch");
 }
 
+Status apply_batch_body(Store& s, const kbisim_batch* bt, uint64_t* missing_out);
+
+// The batch, with the hubs' bucket growth carried over to the new layout.
 Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
+  HubGrowth g;
+  Status st = save_hub_growth(s, &g);
+  if (st.ok()) st = apply_batch_body(s, bt, missing_out);
+  if (st.ok()) st = restore_hub_growth(s, g);
+  return st;
+}
+
+Status apply_batch_body(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   if (!bt) return Status::Err(KBISIM_ERR_INVALID_ARG, "batch is NULL");
   if (!s.has_graph) return Status::Err(KBISIM_ERR_STATE, "no graph loaded");
   if ((bt->n_add_nodes && !bt->add_node_label) || (bt->n_ins && (!bt->ins_src || !bt->ins_dst || !bt->ins_label)) ||

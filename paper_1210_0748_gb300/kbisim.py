@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("early_stop", ctypes.c_int),
                 ("hash_seed", ctypes.c_uint64), ("hash_bits", ctypes.c_uint32),
-                ("checked", ctypes.c_int), ("collect_timing", ctypes.c_int), ("maintain", ctypes.c_int)]
+                ("checked", ctypes.c_int), ("collect_timing", ctypes.c_int), ("maintain", ctypes.c_int),
+                ("hub_bucket_keys", ctypes.c_uint32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -109,6 +110,7 @@ SIGNATURES = {
     "kbisim_num_nodes": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_num_edges": (ctypes.c_uint64, [ctypes.c_void_p]),
     "kbisim_device_bytes": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "kbisim_hub_bucket_keys": (ctypes.c_uint32, [ctypes.c_void_p]),
     "kbisim_get_update_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(UpdateInfo)]),
     "kbisim_set_hbm_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "kbisim_get_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
@@ -213,7 +215,8 @@ class KBisim:
 
     def __init__(self, device: int = 0, stream=None, early_stop: bool = True,
                  hash_seed: int = 0x12100748, hash_bits: int = 64, checked: bool = False,
-                 collect_timing: bool = False, hbm_budget_bytes: int = 0, maintain=True):
+                 collect_timing: bool = False, hbm_budget_bytes: int = 0, maintain=True,
+                 hub_bucket_keys: int = 0):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -238,6 +241,7 @@ class KBisim:
         # False/0: recompute; True/1: frontier path while it measures cheaper;
         # "always"/2: frontier path whenever it applies
         opt.maintain = 2 if maintain in ("always", 2) else (1 if maintain else 0)
+        opt.hub_bucket_keys = int(hub_bucket_keys)
         h = ctypes.c_void_p()
         rc = lib.kbisim_create(ctypes.byref(h), ctypes.byref(opt))
         if rc != OK:
@@ -417,6 +421,11 @@ class KBisim:
     @property
     def num_edges(self) -> int:
         return int(self._lib.kbisim_num_edges(self._h))
+
+    @property
+    def hub_bucket_keys(self) -> int:
+        """Hub bucket size in use (fixed by the option, or tuned)."""
+        return int(self._lib.kbisim_hub_bucket_keys(self._h))
 
     @property
     def device_bytes(self) -> int:

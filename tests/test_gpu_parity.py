@@ -427,8 +427,8 @@ def test_hubs_with_distinct_keys():
     assert all(pids[lev][0] == pids[lev][1] for lev in range(pids.shape[0]))
 
 
-@pytest.mark.parametrize("heavy", [10_000, 30_000])
-def test_hub_with_one_heavy_key_among_distinct_keys(heavy):
+@pytest.mark.parametrize("heavy,ucap", [(10_000, 0), (30_000, 0), (10_000, 2048), (30_000, 2048), (30_000, 4096)])
+def test_hub_with_one_heavy_key_among_distinct_keys(heavy, ucap):
     """A 1M-edge hub whose keys are all distinct but one, which makes up 1% or
     3% of its edges: a key sample finds few repeats, so the hub skips the chunk
     set and the heavy key overflows its bucket.  With 1% the bucket grows until
@@ -446,8 +446,60 @@ def test_hub_with_one_heavy_key_among_distinct_keys(heavy):
     dst = np.concatenate([hub_dst[perm], rng.integers(0, n, other)]).astype(np.uint32)
     lab = np.concatenate([hub_lab[perm], rng.integers(0, 3, other)]).astype(np.uint32)
     g = synth.from_coo(n, src, dst, lab, nl)
+    res, pids = gpu_levels(g, 3, hub_bucket_keys=ucap)
+    assert_same(res, pids, oracle_levels(g, 3))
+
+
+@pytest.mark.parametrize("labels", [1, 16, 600, 1500, 3000])
+def test_level0_label_table_and_general_path(labels):
+    """Level 0 through the label table (few labels) and through the general
+    path (more labels than the table or a CTA's shared copy holds), with the
+    extreme labels 0 and 0xFFFFFFFF and labels carried by one node only (alone
+    in their block, which the next round relies on)."""
+    rng = np.random.default_rng(labels)
+    n = 40_000
+    pool = np.unique(np.concatenate([[0, 0xFFFFFFFF], rng.integers(1, 2**32 - 1, labels)]))[:labels]
+    nl = pool[rng.integers(0, pool.size, n)].astype(np.uint32)
+    nl[rng.choice(n, 5, replace=False)] = rng.integers(1, 2**32 - 1, 5).astype(np.uint32)  # single-node labels
+    g = synth.random_small_graph(n, 200_000, node_labels=2, edge_labels=3, seed=labels)
+    g = synth.from_coo(n, g.src(), g.dst, g.edge_label, nl)
     res, pids = gpu_levels(g, 3)
     assert_same(res, pids, oracle_levels(g, 3))
+
+
+def test_grouping_with_a_block_of_a_million_nodes():
+    """2.4M nodes to group in round 1, half of them in one block (no out-edges,
+    one label: one signature, and so one hash, shared by 1.2M nodes).  Every
+    level equals the oracle's."""
+    rng = np.random.default_rng(77)
+    n, heavy = 2_400_000, 1_200_000
+    m = 5_000_000
+    src = rng.integers(heavy, n, m).astype(np.uint32)  # nodes below `heavy` have no out-edges
+    dst = rng.integers(0, n, m).astype(np.uint32)
+    lab = rng.integers(0, 3, m).astype(np.uint32)
+    nl = np.zeros(n, np.uint32)
+    nl[heavy:] = rng.integers(0, 4, n - heavy).astype(np.uint32)
+    g = synth.from_coo(n, src, dst, lab, nl)
+    res, pids = gpu_levels(g, 3)
+    assert_same(res, pids, oracle_levels(g, 3))
+
+
+@pytest.mark.parametrize("ucap", [0, 2048, 4096])
+def test_hub_bucket_sizes(ucap):
+    """Both hub bucket sizes (2048 and 4096 key words), and the size tuned in
+    the first round from level 2 on (which runs the hub pass with each size,
+    the round keeping the last pass's signatures), give the oracle's levels on
+    every degree tier, and a later refinement of the handle too."""
+    n, s, d, l, nl = _tier_graph(5)
+    g = synth.from_coo(n, s, d, l, nl)
+    ref = oracle_levels(g, 5, early_stop=False)
+    with KBisim(hub_bucket_keys=ucap, early_stop=False) as kb:
+        assert kb.hub_bucket_keys == (ucap or 4096)
+        res = kb.build(g, 5)
+        assert_same(res, kb.all_pids(5), ref)
+        assert kb.hub_bucket_keys in ((ucap,) if ucap else (2048, 4096))
+        res = kb.refine(5)
+        assert_same(res, kb.all_pids(5), ref)
 
 
 def _mix32(x):
