@@ -32,7 +32,7 @@ CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1210_0748
 # kernel name -> class of the library's timing (kbisim_kernel_times)
 CLASS_OF = [
     (r"k_label_hash|k_l0_collect", "label_group"),
-    (r"k_sig_small", "sig_small"),
+    (r"k_sig_small|k_sig_chunk<128, 33,", "sig_small"),  # the library times out-degree 33..64 with <= 32
     (r"k_sig_chunk", "sig_medium"),
     (r"k_hub_sample|k_hub_chunk|k_hub_scatter|k_hub_bucket|k_hub_finish", "sig_hub"),
     (r"k_group_insert", "group"),

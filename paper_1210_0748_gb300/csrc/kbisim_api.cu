@@ -296,7 +296,7 @@ void free_graph(Store& s, bool keep_buffers) {
   Buf* bufs[] = {&s.offsets, &s.dst, &s.elabel, &s.nlabel, &s.p2o, &s.o2p, &s.mid_chunks, &s.hub_bits,
                  &s.hub_bbase, &s.hub_cap, &s.hub_tbase, &s.hub_chunks, &s.hub_cstart, &s.sigkey, &s.ucnt, &s.hash, &s.table,
                  &s.slot, &s.rep, &s.ulist[0], &s.ulist[1], &s.hbits, &s.member, &s.alone, &s.hword, &s.bsum,
-                 &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_mode, &s.hub_force, &s.hub_err, &s.hub_tmp, &s.alive_o,
+                 &s.long_pairs, &s.hub_cursor, &s.bucket_hub, &s.hub_acc, &s.hub_mode, &s.hub_force, &s.hub_err, &s.hub_retry, &s.hub_tmp, &s.alive_o,
                  &s.rl_tcnt, &s.rl_hot, &s.rl_ost};
   if (!keep_buffers) {
     for (Buf* b : bufs) release(s, *b);

@@ -200,6 +200,7 @@ struct MaintState {
   Buf cmp;                          // hash set comparing one long signature with a stored one
   Buf cmp_info;                     // uint64 x 3 per pending comparison
   Buf big;                          // uint2 (node, label): long signatures copied by their own CTA
+  Buf huge;                         // uint2 (node, label): the longest, copied by every CTA of a grid
   // last update
   int incremental = 0;              // 1 = frontier path, 0 = full recomputation
   int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)
@@ -313,6 +314,7 @@ struct Store {
   Buf hub_mode;                // uint8 [hubs]: chunk pass of each hub this round (1 = no chunk set)
   Buf hub_force;               // uint8 [hubs]: copy of h_hub_force
   Buf hub_err;                 // uint32 [hubs]: overflow flags of the last hub pass
+  Buf hub_retry;               // bitmap over internal ids: the hubs a repeated hub pass runs
   Buf hub_tmp;                 // key words [hub_tmp_words]: fixed-capacity hub buckets
   static constexpr int kStageBufsN = 9;
   Buf stage[kStageBufsN];      // staging of host inputs and COO grouping (kbisim_load)

@@ -201,15 +201,52 @@ __device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p
   if (lane == 0 && !store_slot(a, g.hash[p], b)) atomicOr(a.err, 1u);
 }
 
-// Element words of the long new signatures (one CTA per signature).
-__global__ void k_copy_big(StoreArgs a, NodeSig g, const uint2* big, uint64_t n_big) {
+// Element words of the long new signatures (one CTA per signature); the
+// longest (hubs: more than kHugeCopy words) are listed for k_copy_huge, so
+// that no CTA copies a million words while the others wait.
+constexpr uint32_t kHugeCopy = 1u << 15;
+
+__global__ void k_copy_big(StoreArgs a, NodeSig g, const uint2* big, uint64_t n_big, uint2* huge,
+                           unsigned long long* n_huge) {
   for (uint64_t q = blockIdx.x; q < n_big; q += gridDim.x) {
     const uint2 e = big[q];
     const uint32_t U = a.scount[e.y];
+    if (U > kHugeCopy) {
+      if (threadIdx.x == 0) huge[atomicAdd(n_huge, 1ull)] = e;
+      continue;
+    }
     const uint64_t* src = g.sigkey + g.off[e.x];
     unsigned long long* dstp = a.pool + a.soff[e.y];
     for (uint32_t i = threadIdx.x; i < U; i += blockDim.x) dstp[i] = src[i];
   }
+}
+
+// Each listed signature split evenly over all CTAs of the grid.
+__global__ void k_copy_huge(StoreArgs a, NodeSig g, const uint2* huge, const unsigned long long* n_huge) {
+  const uint64_t nh = *n_huge;
+  for (uint64_t q = 0; q < nh; ++q) {
+    const uint2 e = huge[q];
+    const uint64_t U = a.scount[e.y];
+    const uint64_t lo = U * blockIdx.x / gridDim.x, hi = U * (blockIdx.x + 1) / gridDim.x;
+    const uint64_t* src = g.sigkey + g.off[e.x];
+    unsigned long long* dstp = a.pool + a.soff[e.y];
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dstp[i] = src[i];
+  }
+}
+
+// Copies of the listed long signatures (big: n_big entries, known on the
+// host), the longest split over the whole grid.
+Status copy_long_signatures(Store& s, const StoreArgs& sa, const NodeSig& ns, const uint2* big, uint64_t n_big) {
+  MaintState& m = s.mt;
+  Status st;
+  if (!n_big) return Status::Ok();
+  if (!(st = ensure(s, m.huge, (std::max<uint64_t>(s.n_hub, 1) + 1) * sizeof(uint2))).ok()) return st;
+  unsigned long long* n_huge = ptr<unsigned long long>(m.misc) + 14;
+  cudaMemsetAsync(n_huge, 0, 8, s.stream);
+  k_copy_big<<<(unsigned)std::min<uint64_t>(n_big, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
+      sa, ns, big, n_big, ptr<uint2>(m.huge), n_huge);
+  k_copy_huge<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(sa, ns, ptr<uint2>(m.huge), n_huge);
+  return cuda_check(cudaGetLastError(), "copy signatures");
 }
 
 // Build: the heads of every label (smallest original id) store their
@@ -717,9 +754,7 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   uint64_t hb = 0;
   if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
   if (!(st = sync_read(s, &hb, sc + 12, 8, "store heads")).ok()) return st;
-  if (hb)
-    k_copy_big<<<(unsigned)std::min<uint64_t>(hb, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
-        store_args(s, L), node_sig(s), ptr<uint2>(m.big), hb);
+  if (!(st = copy_long_signatures(s, store_args(s, L), node_sig(s), ptr<uint2>(m.big), hb)).ok()) return st;
   uint32_t e = 0;
   if (!(st = cuda_check(cudaGetLastError(), "store heads")).ok()) return st;
   if (!(st = sync_read(s, &e, s.d_err.p, 4, "store heads")).ok()) return st;
@@ -782,9 +817,7 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
     uint64_t hv[3] = {0, 0, 0};
     if (!(st = cuda_check(cudaGetLastError(), "lookup")).ok()) return st;
     if (!(st = sync_read(s, hv, sc + 1, 24, "lookup")).ok()) return st;
-    if (hv[2])
-      k_copy_big<<<(unsigned)std::min<uint64_t>(hv[2], (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(sa, ns, big,
-                                                                                                     hv[2]);
+    if (!(st = copy_long_signatures(s, sa, ns, big, hv[2])).ok()) return st;
     const uint64_t np = hv[0];
     if (!np) break;
     k_long_compare<<<(unsigned)std::min<uint64_t>(np, (uint64_t)s.sms * 4), kCmpThreads, 0, s.stream>>>(sa, ns, la, np,
@@ -856,7 +889,7 @@ void maint_release(Store& s) {
   for (MaintLevel& L : m.lv) release_level(s, L);
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big};
+              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge};
   for (Buf* x : b) release(s, *x);
   m.valid = false;
   m.k = 0;

@@ -1032,11 +1032,12 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
   }
 }
 
-// Count and hash of every hub from its buckets' totals.
+// Count and hash of every hub (of the mask) from its buckets' totals.
 __global__ void k_hub_finish(SigArgs a, HubArgs h, uint64_t n_hub) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_hub;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t p = h.first + i;
+    if (!in_mask(a, p)) continue;
     const unsigned long long tot = h.hub_cur[i];
     const uint64_t tsum = ((uint64_t)h.hub_term[2 * i + 1] << 32) | h.hub_term[2 * i];
     a.ucnt[p] = (uint32_t)tot;
@@ -2168,6 +2169,9 @@ Status run_signatures(Store& s, const SigArgs& a) {
   if (s.n_hub) {
     auto run_hubs = [&]() -> Status {
       Status st;
+      // a repeat after an overflow runs only the hubs that overflowed (the
+      // others' signatures are written): a mask over their internal ids
+      SigArgs ah = a;
       for (int attempt = 0;; ++attempt) {
         if (!(st = ensure(s, s.hub_tmp, s.hub_tmp_words * sizeof(K))).ok()) return st;
         HubArgs h;
@@ -2193,21 +2197,21 @@ Status run_signatures(Store& s, const SigArgs& a) {
           cudaMemsetAsync(h.cursor, 0, s.n_hub_buckets * 4, s.stream);
           cudaMemsetAsync(s.hub_acc.p, 0, s.n_hub * 24, s.stream);
           cudaMemsetAsync(s.hub_err.p, 0, s.n_hub * 4, s.stream);
-          k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(a, h, s.n_hub);
-          k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(a, h);
-          k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(a, h);
+          k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(ah, h, s.n_hub);
+          k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(ah, h);
+          k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(ah, h);
           if (s.hub_ucap == (uint32_t)kHubUcapMax) {
             constexpr int U = kHubUcapMax;
             const unsigned g = (unsigned)std::min<uint64_t>(
                 s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
-            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(a, h, s.n_hub_buckets);
+            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(ah, h, s.n_hub_buckets);
           } else {
             constexpr int U = kHubUcapMax / 2;
             const unsigned g = (unsigned)std::min<uint64_t>(
                 s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
-            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(a, h, s.n_hub_buckets);
+            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(ah, h, s.n_hub_buckets);
           }
-          k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(a, h, s.n_hub);
+          k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(ah, h, s.n_hub);
         }
         if (!(st = launch_check("hub kernels")).ok()) return st;
         uint32_t e = 0;
@@ -2237,6 +2241,16 @@ Status run_signatures(Store& s, const SigArgs& a) {
           if (herr[i] & kErrHubSet) s.h_hub_xbits[i] += 1;
         }
         if (!(st = hub_layout(s)).ok()) return st;
+        // the repeat's mask: the words of the hub id range, bits of the failed hubs
+        const uint64_t first = s.class_start[kClassHub], w0 = first >> 5, w1 = (first + s.n_hub + 31) >> 5;
+        std::vector<uint32_t> bits(w1 - w0, 0u);
+        for (uint64_t i = 0; i < s.n_hub; ++i)
+          if (herr[i]) bits[((first + i) >> 5) - w0] |= 1u << ((first + i) & 31);
+        if (!(st = ensure(s, s.hub_retry, (w1 + 1) * 4)).ok()) return st;
+        st = cuda_check(cudaMemcpyAsync(ptr<uint32_t>(s.hub_retry) + w0, bits.data(), bits.size() * 4,
+                                        cudaMemcpyHostToDevice, s.stream), "hub repeat mask");
+        if (!st.ok()) return st;
+        ah.fmask = ptr<uint32_t>(s.hub_retry);
         cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
       }
     };

@@ -467,6 +467,31 @@ def test_level0_label_table_and_general_path(labels):
     assert_same(res, pids, oracle_levels(g, 3))
 
 
+def test_hub_repeat_keeps_the_other_hubs():
+    """A hub whose heavy key overflows its bucket is redone alone (the repeat
+    runs only the hubs that overflowed); two other hubs, finished in the first
+    pass, keep their signatures.  Equal to the oracle."""
+    rng = np.random.default_rng(43)
+    n = 100_000
+    nl = (np.arange(n) % 1000).astype(np.uint32)
+    c = np.arange(600_000)
+    a_dst = np.concatenate([(c % 1000) + 1000 * rng.integers(0, n // 1000, c.size), np.full(20_000, 5)])
+    a_lab = np.concatenate([c // 1000, np.zeros(20_000, np.int64)])
+    b = np.arange(300_000)
+    b_dst = (b % 1000) + 1000 * rng.integers(0, n // 1000, b.size)
+    b_lab = b // 1000
+    other = 200_000
+    src = np.concatenate([np.zeros(a_dst.size, np.uint32), np.ones(b_dst.size, np.uint32),
+                          np.full(b_dst.size, 2, np.uint32), rng.integers(3, n, other).astype(np.uint32)])
+    dst = np.concatenate([a_dst, b_dst, b_dst[::-1], rng.integers(0, n, other)]).astype(np.uint32)
+    lab = np.concatenate([a_lab, b_lab, b_lab[::-1], rng.integers(0, 3, other)]).astype(np.uint32)
+    nl[2] = nl[1]
+    g = synth.from_coo(n, src, dst, lab, nl)
+    res, pids = gpu_levels(g, 3)
+    assert_same(res, pids, oracle_levels(g, 3))
+    assert all(pids[lev][1] == pids[lev][2] for lev in range(pids.shape[0]))  # twin hubs
+
+
 def test_grouping_with_a_block_of_a_million_nodes():
     """2.4M nodes to group in round 1, half of them in one block (no out-edges,
     one label: one signature, and so one hash, shared by 1.2M nodes).  Every
