@@ -73,22 +73,29 @@ def class_units(g):
     return out
 
 
-def recorded_traffic(cls, scale):
+def recorded_traffic(cls, units):
     """DRAM bytes per round of a kernel class from the committed ncu summary, if it
     was taken on the current kernel sources.  The capture is of the same
     generator at a smaller scale (4M nodes / 64M edges: inputs larger than L2,
-    a few GB on the device); nodes and edges both grow with the scale, and so
-    does every class's traffic, so it is scaled by scale / captured scale."""
+    a few GB on the device), which records the units each class processed
+    there; the traffic is scaled by this workload's units over those (edges for
+    the signature classes, nodes for the per-node classes).  `units`: this
+    workload's (edges, nodes) of the class."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
     from ncu_summary import source_digest
-    if t.get("source_sha256") != source_digest() or float(t.get("scale", 0)) <= 0:
+    if t.get("source_sha256") != source_digest():
         return None
     v = t.get("dram_bytes_per_round", {}).get(cls)
-    return float(v) * float(scale) / float(t["scale"]) if v is not None else None
+    cu = t.get("class_units", {}).get(cls)
+    if v is None or not cu:
+        return None
+    if cls.startswith("sig"):
+        return float(v) * units[0] / max(cu["edges"], 1)
+    return float(v) * units[1] / max(cu["nodes"], 1)
 
 
 def parse():
@@ -551,7 +558,7 @@ def main():
     dom = max(per_class, key=lambda c: ktimes[c][0])
     d = per_class[dom]
     # measured DRAM bytes of the class per round (ncu), per launch like the algorithmic bytes
-    traffic_round = recorded_traffic(dom, args.scale) if args.workload == "single" else None
+    traffic_round = recorded_traffic(dom, units[dom]) if args.workload == "single" else None
     traffic = traffic_round / d["launches_per_call"] if traffic_round is not None else None
     names = {"sig_small": "k_sig_small (out-degree <= 64, one thread per node)",
              "sig_medium": "k_sig_chunk (out-degree 65..4096, CTA chunks)",

@@ -119,8 +119,9 @@ typedef struct {
    * The stores are made at the first update after a build (a cost of about
    * one signature pass per level) and take about 12 bytes per edge and 16 per
    * node per maintained level.  The handle times both paths (host clock, per
-   * maintained level): after one update on each, it takes the frontier path
-   * only while that measured cheaper, and otherwise recomputes for the next 16
+   * maintained level, building the stores not included: they serve every
+   * later update): after one update on each, it takes the frontier path only
+   * while that measured cheaper, and otherwise recomputes for the next 16
    * updates (reason KBISIM_MAINT_COST) before trying the frontier path again.
    * 2 = the frontier path whenever it applies, without timing. */
   int maintain;

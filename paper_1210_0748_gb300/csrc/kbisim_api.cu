@@ -924,6 +924,7 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
     cost_off = true;  // one recomputation to compare with
   }
   bool tried = false;  // the frontier path was attempted (its cost is charged to it)
+  double entry_build_ms = 0;  // stores built for this update (a one-time cost, not charged)
   if (!s.maintain) {
     m.reason = KBISIM_MAINT_OFF;
   } else if (b && b->n_del_nodes) {
@@ -938,7 +939,9 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
   } else {
     // stores made from the current levels when there are none for this k yet
     if ((!m.valid || k > m.k) && s.has_levels && (s.k_requested >= k || s.stable)) {
+      const auto tb = std::chrono::steady_clock::now();
       if (!kb::maint_build(s, k).ok()) kb::maint_release(s);
+      entry_build_ms = ms_since(tb);
     }
     if (m.valid && k <= m.k) {
       tried = true;
@@ -958,17 +961,16 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
     m.suspend_edges = std::max<uint64_t>(batch_edges, 1);
     m.suspend_k = k;
   }
-  const double call_ms = ms_since(t0);
+  // per-update cost of the path taken; building the stores is a one-time
+  // cost of the frontier path that later updates reuse, so it is not charged
+  const double call_ms = ms_since(t0) - entry_build_ms;
   // after a full recomputation, stores for the next update (not while large
   // batches are known to switch back, nor while recomputation measures
   // cheaper: the update before the next trial of the frontier path makes them)
   const bool next_tries = !(m.reason == KBISIM_MAINT_COST && m.cost_skip > 1);
-  double build_ms = 0;
   if (st.ok() && s.maintain && !m.incremental && s.has_levels && m.reason != KBISIM_MAINT_FRONTIER &&
       next_tries) {
-    const auto tb = std::chrono::steady_clock::now();
     if (!kb::maint_build(s, k).ok()) kb::maint_release(s);
-    build_ms = ms_since(tb);
   }
   if (st.ok() && timed) {
     const double per = 1.0 / std::max<uint32_t>(k, 1);
@@ -976,13 +978,8 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
       avg = n ? 0.5 * (avg + x) : x;
       ++n;
     };
-    if (tried || m.incremental) {
-      fold(m.ms_inc, m.n_inc, (call_ms + m.build_ms) * per);
-      m.build_ms = 0;
-    } else if (m.reason == KBISIM_MAINT_COST || m.reason == KBISIM_MAINT_NO_STORE) {
-      fold(m.ms_rec, m.n_rec, call_ms * per);
-    }
-    m.build_ms += build_ms;
+    if (tried || m.incremental) fold(m.ms_inc, m.n_inc, call_ms * per);
+    else if (m.reason == KBISIM_MAINT_COST || m.reason == KBISIM_MAINT_NO_STORE) fold(m.ms_rec, m.n_rec, call_ms * per);
   }
   if (st.ok() && missing_deletes) *missing_deletes = missing;
   return finish(h, st);

@@ -217,7 +217,6 @@ struct MaintState {
   double ms_inc = 0, ms_rec = 0;
   uint32_t n_inc = 0, n_rec = 0;
   uint32_t cost_skip = 0;
-  double build_ms = 0;  // store build after a recomputation, charged to the next frontier update
 };
 
 struct Store;

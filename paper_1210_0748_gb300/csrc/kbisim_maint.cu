@@ -1031,10 +1031,12 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
     if (!(st = ensure(s, s.level[j], std::max<uint64_t>(n, 1) * 4)).ok()) return st;
   if (s.counts.size() < (size_t)m.k + 1) s.counts.resize(m.k + 1, 0);
   if (!(st = compute_level0(s)).ok()) return st;
+  // (every level writes its alone flags, so they are those of the last
+  // computed level when the loop ends; with k = 0, level 0's own)
   uint32_t rounds = k;
   for (uint32_t j = 1; j <= k; ++j) {
     uint64_t blocks = 0;
-    if (!(st = canonical_from_labels(s, j, ptr<uint32_t>(s.level[j]), &blocks, false)).ok()) return st;
+    if (!(st = canonical_from_labels(s, j, ptr<uint32_t>(s.level[j]), &blocks, true)).ok()) return st;
     s.counts[j] = blocks;
     if (s.early_stop && blocks == s.counts[j - 1]) {
       rounds = j;
@@ -1042,10 +1044,6 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
     }
   }
   if (k == 0) rounds = 0;
-  if (rounds > 0) {  // alone flags of the last computed level (level 0 has its own)
-    uint64_t blocks = 0;
-    if (!(st = canonical_from_labels(s, rounds, ptr<uint32_t>(s.level[rounds]), &blocks, true)).ok()) return st;
-  }
   s.computed = rounds;
   s.rounds_run = rounds;
   s.stable = rounds > 0 && s.counts[rounds] == s.counts[rounds - 1];
