@@ -120,9 +120,11 @@ typedef struct {
    * one signature pass per level) and take about 12 bytes per edge and 16 per
    * node per maintained level.  The handle times both paths (host clock, per
    * maintained level, building the stores not included: they serve every
-   * later update): after one update on each, it takes the frontier path only
-   * while that measured cheaper, and otherwise recomputes for the next 16
-   * updates (reason KBISIM_MAINT_COST) before trying the frontier path again.
+   * later update; the handle's first frontier update, which allocates that
+   * path's scratch, is not timed): after one timed update on each, it takes
+   * the frontier path only while that measured cheaper, and otherwise
+   * recomputes for the next 16 updates (reason KBISIM_MAINT_COST) before
+   * trying the frontier path again.
    * 2 = the frontier path whenever it applies, without timing. */
   int maintain;
   /* Key words a hub bucket holds at most (out-degree > 4096: the hub's keys

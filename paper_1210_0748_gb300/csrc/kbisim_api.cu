@@ -978,7 +978,12 @@ int kbisim_update(kbisim_handle* h, const kbisim_batch* b, uint32_t k, kbisim_re
       avg = n ? 0.5 * (avg + x) : x;
       ++n;
     };
-    if (tried || m.incremental) fold(m.ms_inc, m.n_inc, call_ms * per);
+    if (tried || m.incremental) {
+      // the handle's first frontier update allocates that path's scratch:
+      // not a sample of its steady cost
+      if (m.inc_warm) fold(m.ms_inc, m.n_inc, call_ms * per);
+      m.inc_warm = true;
+    }
     else if (m.reason == KBISIM_MAINT_COST || m.reason == KBISIM_MAINT_NO_STORE) fold(m.ms_rec, m.n_rec, call_ms * per);
   }
   if (st.ok() && missing_deletes) *missing_deletes = missing;

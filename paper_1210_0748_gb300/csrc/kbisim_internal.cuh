@@ -217,6 +217,7 @@ struct MaintState {
   double ms_inc = 0, ms_rec = 0;
   uint32_t n_inc = 0, n_rec = 0;
   uint32_t cost_skip = 0;
+  bool inc_warm = false;  // a frontier update has run on this handle (later ones are timed)
 };
 
 struct Store;

@@ -2256,9 +2256,10 @@ Status run_signatures(Store& s, const SigArgs& a) {
     };
     if (!s.tune_now) return run_hubs();
     // tuning (once per handle, on a full round from level 2 on): each bucket
-    // size runs the hub pass twice, the second time timed (the first settles
-    // bucket growth); the faster size is kept.  Every pass writes the same
-    // signatures, so the round's result is the last pass's.
+    // size runs the hub pass once, timed with the repeats its overflows need
+    // (a repeat runs only the hubs that overflowed); the faster size is kept.
+    // Every pass writes the same signatures, so the round's result is the
+    // last pass's.
     const uint32_t sizes[2] = {(uint32_t)kHubUcapMax, (uint32_t)kHubUcapMax / 2};
     // bucket growth is learned per size: each starts from the growth before
     // tuning, and the chosen size keeps its own
@@ -2283,7 +2284,6 @@ Status run_signatures(Store& s, const SigArgs& a) {
       }
       s.hub_ucap = sizes[c];
       if (!(st = hub_layout(s)).ok()) break;
-      if (!(st = run_hubs()).ok()) break;
       cudaEventRecord(ev[0], s.stream);
       if (!(st = run_hubs()).ok()) break;
       cudaEventRecord(ev[1], s.stream);

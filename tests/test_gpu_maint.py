@@ -191,11 +191,12 @@ def test_long_signatures_in_the_store():
 
 
 def test_timed_choice_between_the_paths():
-    """maintain=True times both paths on the handle: the first update takes
-    the frontier path, the second recomputes to compare (reason "cost"), and
-    later ones take whichever measured cheaper, trying the frontier path again
-    after 16 recomputations.  Every level equals a handle that always
-    recomputes, and the last ones the oracle."""
+    """maintain=True times both paths on the handle: the first two updates
+    take the frontier path (the first, which allocates that path's scratch,
+    is not timed), the third recomputes to compare (reason "cost"), and later
+    ones take whichever measured cheaper, trying the frontier path again after
+    16 recomputations.  Every level equals a handle that always recomputes,
+    and the last ones the oracle."""
     rng = np.random.default_rng(31)
     g = synth.config_single_large(scale=1 / 512, seed=8)  # 31K nodes, 500K edges
     mg = _mg(g)
@@ -214,10 +215,10 @@ def test_timed_choice_between_the_paths():
             for lev in range(k + 1):
                 assert np.array_equal(kb.pids(lev), plain.pids(lev)), (step, lev)
         assert_same(r1, kb.all_pids(k), mg.kbisim(k))
-    assert reasons[0] in ("incremental", "frontier"), reasons
-    assert reasons[1] == "cost", reasons
+    assert reasons[0] in ("incremental", "frontier") and reasons[1] in ("incremental", "frontier"), reasons
+    assert reasons[2] == "cost", reasons
     assert set(reasons) <= {"incremental", "frontier", "cost"}, reasons
     run = 0
-    for r in reasons[2:]:  # never more than 15 recomputations in a row on cost
+    for r in reasons[3:]:  # never more than 15 recomputations in a row on cost
         run = run + 1 if r == "cost" else 0
         assert run <= 15, reasons
