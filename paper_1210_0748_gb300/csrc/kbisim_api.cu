@@ -371,6 +371,11 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   if (m && (!g->dst || !g->edge_label)) return Status::Err(KBISIM_ERR_INVALID_ARG, "dst/edge_label is NULL");
   if (m && !g->offsets && !g->src) return Status::Err(KBISIM_ERR_INVALID_ARG, "need offsets or src");
   if (m && !n) return Status::Err(KBISIM_ERR_INVALID_ARG, "edges without nodes");
+  // the hubs' bucket growth of the graph held now, for hubs of the same
+  // original id and out-degree in the new one (a graph loaded again)
+  HubGrowth growth;
+  Status gs = save_hub_growth(s, &growth);
+  if (!gs.ok()) growth = HubGrowth();
   free_graph(s, s.budget == 0);
   Status st;
   const bool dev = g->on_device != 0;
@@ -471,7 +476,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
     return st;
   }
   s.has_graph = true;
-  return Status::Ok();
+  return restore_hub_growth(s, growth, true);
 }
 
 Status ensure_levels(Store& s, uint32_t k) {

@@ -420,10 +420,14 @@ Status compute_level0(Store& s);                  // pId_0 into level[0]
 Status build_chunk_lists(Store& s, bool fresh);
 struct HubGrowth {
   std::vector<uint32_t> orig, xbits, shift;
+  std::vector<uint64_t> deg;
   std::vector<uint8_t> force;
 };
 Status save_hub_growth(Store& s, HubGrowth* g);
-Status restore_hub_growth(Store& s, const HubGrowth& g);
+// same_degree: a hub takes the saved growth only if its out-degree is unchanged
+// (a newly loaded graph); otherwise any hub with the saved original id does
+// (the same graph after an update).
+Status restore_hub_growth(Store& s, const HubGrowth& g, bool same_degree);
 Status compute_round(Store& s, uint32_t i);       // pId_i from pId_{i-1}
 // Signatures of the nodes whose bit is set in fmask (bitmap over internal ids;
 // NULL = every node) from identifiers prev (internal order), as 64-bit

@@ -2337,12 +2337,15 @@ uint32_t bits_for(uint64_t v) {  // bits needed to represent values 0..v
 }  // namespace
 
 // Bucket growth of the hubs, keyed by original node id: a graph laid out
-// again after an update keeps what its hubs' buckets learned, instead of
-// overflowing and growing them again in the next refinement.
+// again after an update, or loaded again into the same handle, keeps what its
+// hubs' buckets learned, instead of overflowing and growing them again in the
+// next refinement.  Growth only sizes buckets: a wrong carry costs memory or
+// a repeat, never a result.
 Status save_hub_growth(Store& s, HubGrowth* g) {
   g->orig.clear();
   g->xbits.clear();
   g->shift.clear();
+  g->deg.clear();
   g->force.clear();
   if (!s.has_graph || !s.n_hub || s.h_hub_xbits.size() != s.n_hub) return Status::Ok();
   bool any = false;
@@ -2358,12 +2361,13 @@ Status save_hub_growth(Store& s, HubGrowth* g) {
       g->orig.push_back(p2o[i]);
       g->xbits.push_back(s.h_hub_xbits[i]);
       g->shift.push_back(s.h_hub_shift[i]);
+      g->deg.push_back(i < s.h_hub_deg.size() ? s.h_hub_deg[i] : 0);
       g->force.push_back(s.h_hub_force[i]);
     }
   return Status::Ok();
 }
 
-Status restore_hub_growth(Store& s, const HubGrowth& g) {
+Status restore_hub_growth(Store& s, const HubGrowth& g, bool same_degree) {
   if (g.orig.empty() || !s.has_graph || !s.n_hub) return Status::Ok();
   std::vector<uint32_t> p2o(s.n_hub);
   Status st = cuda_check(cudaMemcpyAsync(p2o.data(), ptr<uint32_t>(s.p2o) + s.class_start[kClassHub], s.n_hub * 4,
@@ -2380,6 +2384,7 @@ Status restore_hub_growth(Store& s, const HubGrowth& g) {
   for (uint64_t i = 0; i < s.n_hub; ++i) {
     const auto it = at.find(p2o[i]);
     if (it == at.end()) continue;
+    if (same_degree && (i >= s.h_hub_deg.size() || s.h_hub_deg[i] != g.deg[it->second])) continue;
     s.h_hub_xbits[i] = std::max(s.h_hub_xbits[i], g.xbits[it->second]);
     s.h_hub_shift[i] = std::max(s.h_hub_shift[i], g.shift[it->second]);
     s.h_hub_force[i] = std::max(s.h_hub_force[i], g.force[it->second]);

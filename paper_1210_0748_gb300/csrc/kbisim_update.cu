@@ -934,7 +934,7 @@ Status apply_batch(Store& s, const kbisim_batch* bt, uint64_t* missing_out) {
   HubGrowth g;
   Status st = save_hub_growth(s, &g);
   if (st.ok()) st = apply_batch_body(s, bt, missing_out);
-  if (st.ok()) st = restore_hub_growth(s, g);
+  if (st.ok()) st = restore_hub_growth(s, g, false);
   return st;
 }
 

@@ -467,6 +467,29 @@ def test_level0_label_table_and_general_path(labels):
     assert_same(res, pids, oracle_levels(g, 3))
 
 
+def test_reloads_keep_or_drop_hub_growth():
+    """A handle that loads a graph again keeps the bucket growth its hubs
+    learned (same original id and out-degree); a different graph in between
+    and the graph itself both give the oracle's levels every time."""
+    rng = np.random.default_rng(47)
+    n = 60_000
+    nl = (np.arange(n) % 500).astype(np.uint32)
+    c = np.arange(300_000)
+    a_dst = np.concatenate([(c % 500) + 500 * rng.integers(0, n // 500, c.size), np.full(9_000, 7)])
+    a_lab = np.concatenate([c // 500, np.zeros(9_000, np.int64)])
+    other = 100_000
+    src = np.concatenate([np.zeros(a_dst.size, np.uint32), rng.integers(1, n, other).astype(np.uint32)])
+    dst = np.concatenate([a_dst, rng.integers(0, n, other)]).astype(np.uint32)
+    lab = np.concatenate([a_lab, rng.integers(0, 3, other)]).astype(np.uint32)
+    ga = synth.from_coo(n, src, dst, lab, nl)
+    gb = synth.random_small_graph(20_000, 80_000, node_labels=3, edge_labels=3, seed=5)
+    ra, rb = oracle_levels(ga, 3), oracle_levels(gb, 3)
+    with KBisim() as kb:
+        for g, ref in ((ga, ra), (ga, ra), (gb, rb), (ga, ra)):
+            res = kb.build(g, 3)
+            assert_same(res, kb.all_pids(3), ref)
+
+
 def test_hub_repeat_keeps_the_other_hubs():
     """A hub whose heavy key overflows its bucket is redone alone (the repeat
     runs only the hubs that overflowed); two other hubs, finished in the first
