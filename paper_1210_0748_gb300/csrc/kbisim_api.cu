@@ -358,6 +358,35 @@ struct Temps {
   explicit Temps(Store& st) : use(st, kCacheStage), b(st.stage) {}
 };
 
+// The side stream and its two events, made once per handle.
+Status ensure_side(Store& s) {
+  if (s.side) return Status::Ok();
+  Status st = cuda_check(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking), "side stream");
+  if (st.ok()) st = cuda_check(cudaEventCreateWithFlags(&s.ev_copied, cudaEventDisableTiming), "event");
+  if (st.ok()) st = cuda_check(cudaEventCreateWithFlags(&s.ev_labels, cudaEventDisableTiming), "event");
+  if (!st.ok()) {
+    if (s.ev_copied) cudaEventDestroy(s.ev_copied);
+    if (s.side) cudaStreamDestroy(s.side);
+    s.ev_copied = nullptr;
+    s.side = nullptr;
+  }
+  return st;
+}
+
+// The handle's stream waits for the edge labels copied on the side stream;
+// their maximum then decides the label width.
+Status await_side_labels(Store& s) {
+  Status st = cuda_check(cudaStreamWaitEvent(s.stream, s.ev_labels, 0), "wait for labels");
+  unsigned int maxlab = 0;
+  if (st.ok())
+    st = cuda_check(cudaMemcpyAsync(&maxlab, s.lab_max_dev, 4, cudaMemcpyDeviceToHost, s.stream), "label max");
+  if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  if (!st.ok()) return st;
+  s.label8 = maxlab < 256;
+  s.label_bits = bits_needed(maxlab);
+  return Status::Ok();
+}
+
 // Load: bring the graph to the device as a CSR in original ids (copying host
 // inputs, or grouping COO edges by source with a counting sort), validate it,
 // then relabel it into the store's internal layout.
@@ -373,6 +402,7 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   if (m && !n) return Status::Err(KBISIM_ERR_INVALID_ARG, "edges without nodes");
   // the hubs' bucket growth of the graph held now, for hubs of the same
   // original id and out-degree in the new one (a graph loaded again)
+  if (s.side) cudaStreamSynchronize(s.side);  // a failed load's label copy may still run
   HubGrowth growth;
   Status gs = save_hub_growth(s, &growth);
   if (!gs.ok()) growth = HubGrowth();
@@ -396,9 +426,13 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   const void* lab_in = g->edge_label;
   const uint32_t* dst_in = g->dst;
   const uint32_t* src_in = g->src;
+  // host CSR input: the edge labels are copied last, on the side stream, so
+  // that the copy overlaps the validation and the node phase of the
+  // relabelling (which need targets and offsets only)
+  const bool overlap = !dev && m && g->offsets && ensure_side(s).ok();
   if (!dev && m) {
     if (!(st = ensure(s, lab_b, m * w)).ok()) return st;
-    if (!(st = copy_in(s, lab_b.p, g->edge_label, m * w, false)).ok()) return st;
+    if (!overlap && !(st = copy_in(s, lab_b.p, g->edge_label, m * w, false)).ok()) return st;
     lab_in = lab_b.p;
     if (!(st = ensure(s, dst_b, m * 4)).ok()) return st;
     if (!(st = copy_in(s, dst_b.p, g->dst, m * 4, false)).ok()) return st;
@@ -410,29 +444,38 @@ Status load_graph(Store& s, const kbisim_graph* g) {
     }
   }
   unsigned int* d_max = reinterpret_cast<unsigned int*>(err + 4);
-  if (m) {
+  // offsets in original ids
+  const uint64_t* off0 = g->offsets;
+  if (g->offsets && !dev) {
+    if (!(st = ensure(s, off_b, (n + 1) * 8)).ok()) return st;
+    if (!(st = copy_in(s, off_b.p, g->offsets, (n + 1) * 8, false)).ok()) return st;
+    off0 = ptr<uint64_t>(off_b);
+  }
+  auto label_max = [&](cudaStream_t q) {
     const unsigned gb = grid(s, m, 256);
-    if (w == 1) k_label_max<uint8_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint8_t*>(lab_in), d_max);
-    else if (w == 2) k_label_max<uint16_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint16_t*>(lab_in), d_max);
-    else k_label_max<uint32_t><<<gb, 256, 0, s.stream>>>(m, static_cast<const uint32_t*>(lab_in), d_max);
+    if (w == 1) k_label_max<uint8_t><<<gb, 256, 0, q>>>(m, static_cast<const uint8_t*>(lab_in), d_max);
+    else if (w == 2) k_label_max<uint16_t><<<gb, 256, 0, q>>>(m, static_cast<const uint16_t*>(lab_in), d_max);
+    else k_label_max<uint32_t><<<gb, 256, 0, q>>>(m, static_cast<const uint32_t*>(lab_in), d_max);
+  };
+  if (overlap) {  // after the copies on the handle's stream: labels, then their maximum
+    cudaEventRecord(s.ev_copied, s.stream);
+    cudaStreamWaitEvent(s.side, s.ev_copied, 0);
+    st = cuda_check(cudaMemcpyAsync(lab_b.p, g->edge_label, m * w, cudaMemcpyHostToDevice, s.side), "copy in");
+    if (!st.ok()) return st;
+    label_max(s.side);
+    cudaEventRecord(s.ev_labels, s.side);
+  }
+  if (m) {
+    if (!overlap) label_max(s.stream);
     k_check_ids<<<grid(s, m, 256), 256, 0, s.stream>>>(m, n, dst_in, err);
     if (!g->offsets) k_check_ids<<<grid(s, m, 256), 256, 0, s.stream>>>(m, n, src_in, err);
   }
-  // offsets in original ids
-  const uint64_t* off0 = g->offsets;
-  if (g->offsets) {
-    if (!dev) {
-      if (!(st = ensure(s, off_b, (n + 1) * 8)).ok()) return st;
-      if (!(st = copy_in(s, off_b.p, g->offsets, (n + 1) * 8, false)).ok()) return st;
-      off0 = ptr<uint64_t>(off_b);
-    }
-    if (n) k_check_offsets<<<grid(s, n, 256), 256, 0, s.stream>>>(n, m, off0, err);
-  }
+  if (g->offsets && n) k_check_offsets<<<grid(s, n, 256), 256, 0, s.stream>>>(n, m, off0, err);
   uint32_t hv[8] = {0};
   if (!(st = cuda_check(cudaMemcpyAsync(hv, err, 32, cudaMemcpyDeviceToHost, s.stream), "validate")).ok()) return st;
   if (!(st = cuda_check(cudaStreamSynchronize(s.stream), "sync")).ok()) return st;
   if (hv[0]) return Status::Err(KBISIM_ERR_INVALID_ARG, "invalid graph: node id >= num_nodes or bad offsets");
-  const unsigned int maxlab = hv[4];
+  const unsigned int maxlab = hv[4];  // (with the side copy: read again by await_side_labels)
   if (!g->offsets) {
     // COO: counting sort by source into temporary CSR buffers
     Buf &csr_dst = t.b[7], &csr_lab = t.b[8];
@@ -471,7 +514,14 @@ Status load_graph(Store& s, const kbisim_graph* g) {
   s.m = m;
   s.label8 = maxlab < 256;
   s.label_bits = bits_needed(maxlab);
-  if (!(st = relabel_graph(s, off0, dst_in, lab_in, nlab0, nullptr, w)).ok()) {
+  if (overlap) {
+    s.await_labels = await_side_labels;
+    s.lab_max_dev = d_max;
+  }
+  st = relabel_graph(s, off0, dst_in, lab_in, nlab0, nullptr, w);
+  s.await_labels = nullptr;
+  if (overlap) cudaStreamSynchronize(s.side);  // (done already unless the relabelling failed early)
+  if (!st.ok()) {
     free_graph(s, s.budget == 0);
     return st;
   }
@@ -745,6 +795,12 @@ void kbisim_destroy(kbisim_handle* h) {
   kb::release(s, s.d_scalars);
   kb::release(s, s.d_err);
   if (s.h_scalars.p) cudaFreeHost(s.h_scalars.p);
+  if (s.side) {
+    cudaStreamSynchronize(s.side);
+    cudaEventDestroy(s.ev_copied);
+    cudaEventDestroy(s.ev_labels);
+    cudaStreamDestroy(s.side);
+  }
   kb::timer_destroy(s);
   delete h;
 }

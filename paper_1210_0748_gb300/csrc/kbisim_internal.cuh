@@ -351,6 +351,14 @@ struct Store {
   bool tune_now = false;
   float hub_tune_ms[2] = {0, 0};  // measured hub pass of each size (4096, 2048)
 
+  // a load from host memory copies the edge labels on a second stream while
+  // the relabelling's node phase runs; relabel_graph calls await_labels (if
+  // set) before it needs them (and the label width they decide)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_copied = nullptr, ev_labels = nullptr;
+  Status (*await_labels)(Store&) = nullptr;
+  const unsigned int* lab_max_dev = nullptr;
+
   size_t bytes_held = 0;
   uint32_t busy = 0;           // scratch groups (kCache*) in use by the running call
   KernelTimer* timer = nullptr;

@@ -1888,9 +1888,9 @@ Status read_scalars(Store& s, uint64_t* out) {
   return Status::Ok();
 }
 
-// Checked mode: run a check kernel's verdict to the host.  Returns CHECKED if
+// Checked mode: bring a check kernel's outcome to the host.  Returns CHECKED if
 // an index check failed (the kernels that would use the array are not run).
-Status checked_verdict(Store& s, const char* what) {
+Status checked_outcome(Store& s, const char* what) {
   uint32_t e = 0;
   Status st = launch_check(what);
   if (st.ok()) st = cuda_check(cudaMemcpyAsync(&e, s.d_err.p, 4, cudaMemcpyDeviceToHost, s.stream), what);
@@ -1904,7 +1904,7 @@ Status check_below(Store& s, const uint32_t* a, uint64_t n, uint64_t bound, cons
   if (!n) return Status::Ok();
   const unsigned g = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sm_count(s.device) * 16);
   k_check_below<<<g, 256, 0, s.stream>>>(a, n, bound, ptr<uint32_t>(s.d_err));
-  return checked_verdict(s, what);
+  return checked_outcome(s, what);
 }
 
 uint64_t table_capacity(uint64_t n) {
@@ -2526,7 +2526,6 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   if (st.ok()) st = ensure(s, s.offsets, (n + 1) * 8);
   if (st.ok()) st = ensure(s, s.nlabel, std::max<uint64_t>(1, n) * 4);
   if (st.ok()) st = ensure(s, s.dst, std::max<uint64_t>(1, m) * 4);
-  if (st.ok()) st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4));
   if (!st.ok()) return fail(st);
   const unsigned gb = (unsigned)std::min<uint64_t>(grid_for(n, 256), (uint64_t)sms * 32);
   if (n) {
@@ -2544,6 +2543,9 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
   s.n_alone = 0;
   if (!(st = build_chunk_lists(s, true)).ok()) return st;
+  // the edge labels (and with them the label width) from here on
+  if (s.await_labels && !(st = s.await_labels(s)).ok()) return st;
+  if (!(st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4))).ok()) return st;
   if (n && m) {
     if (s.label8) {
       uint8_t* lab = ptr<uint8_t>(s.elabel);
@@ -2757,7 +2759,7 @@ Status check_round_inputs(Store& s, uint32_t i) {
   if (s.n) {
     const unsigned g = (unsigned)std::min<uint64_t>(grid_for(s.n, 256), (uint64_t)sm_count(s.device) * 16);
     k_check_offsets_mono<<<g, 256, 0, s.stream>>>(ptr<uint64_t>(s.offsets), s.n, s.m, ptr<uint32_t>(s.d_err));
-    st = checked_verdict(s, "edge offsets");
+    st = checked_outcome(s, "edge offsets");
   }
   if (st.ok()) st = check_below(s, dst, s.m, s.n, "edge targets");
   if (s.fault_corrupt_dst && s.m) {
