@@ -108,7 +108,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-clocks", action="store_true")
-    p.add_argument("--hub-bucket-keys", type=int, default=0, choices=[0, 2048, 4096],
+    p.add_argument("--hub-bucket-keys", type=int, default=0, choices=[0, 2048, 4096, 8192],
                    help="hub bucket size (0 = tuned by the library on the first refinement)")
     p.add_argument("--workload", default="single", choices=["single", "batched", "large", "serve", "update"],
                    help="single: the 16M/256M graph (the headline line); batched: 4096 graphs "

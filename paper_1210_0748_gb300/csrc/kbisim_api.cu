@@ -738,7 +738,8 @@ int kbisim_create(kbisim_handle** h, const kbisim_options* opt) {
   if (opt) o = *opt; else kbisim_default_options(&o);
   if (o.hash_bits == 0 || o.hash_bits > 64) return KBISIM_ERR_INVALID_ARG;
   if (o.maintain < 0 || o.maintain > 2) return KBISIM_ERR_INVALID_ARG;
-  if (o.hub_bucket_keys != 0 && o.hub_bucket_keys != 2048 && o.hub_bucket_keys != 4096) return KBISIM_ERR_INVALID_ARG;
+  if (o.hub_bucket_keys != 0 && o.hub_bucket_keys != 2048 && o.hub_bucket_keys != 4096 && o.hub_bucket_keys != 8192)
+    return KBISIM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();

@@ -343,13 +343,13 @@ struct Store {
   uint32_t fault_timeout_round = 0;
   bool fault_corrupt_dst = false;
 
-  // hub bucket size (key words at most per bucket: 2048 or 4096) and its
+  // hub bucket size (key words at most per bucket: 2048, 4096 or 8192) and its
   // tuning: 1 = the next full round from level 2 on times both sizes and
   // keeps the faster, 2 = chosen (tuned, or fixed by options.hub_bucket_keys)
   uint32_t hub_ucap = 4096;
   int hub_tune = 1;
   bool tune_now = false;
-  float hub_tune_ms[2] = {0, 0};  // measured hub pass of each size (4096, 2048)
+  float hub_tune_ms[3] = {0, 0, 0};  // measured hub pass of each size (4096, 2048, 8192)
 
   // a load from host memory copies the edge labels on a second stream while
   // the relabelling's node phase runs; relabel_graph calls await_labels (if

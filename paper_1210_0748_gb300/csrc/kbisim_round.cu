@@ -714,7 +714,11 @@ __device__ __forceinline__ void hub_fail(const SigArgs& a, const HubArgs& h, uin
   atomicOr(a.err, e);
 }
 
-constexpr int kHubUcapMax = 4096;      // key words per bucket at most (the larger bucket variant)
+// Key words a hub bucket holds at most: the sizes options.hub_bucket_keys
+// accepts; the first is the size before tuning, and the tuning compares the
+// first two (8192 measured slower on every workload here once bucket growth
+// had settled, while its first pass, with fewer overflows, times faster).
+constexpr int kHubUcaps[3] = {4096, 2048, 8192};
 constexpr int kHubSmemBuckets = 1024;  // per-chunk bucket counts in shared memory up to this many buckets
 constexpr int kHubSample = 128;        // keys sampled per hub to choose its chunk pass
 constexpr int kHubSamplePairs = 16;    // equal sampled pairs from which a hub keeps the chunk set
@@ -905,14 +909,15 @@ constexpr int kBucketThreads = 256, kBucketItems = 8;
 template <typename K, int UCAP>
 struct BucketSmem {
   K set[2 * UCAP];
-  K uniq[UCAP];
-  uint32_t cnt, empty, full, lo, hi, last;
-  unsigned long long obase;
+  uint32_t empty, full, lo, hi;
 };
 
 // One CTA per hub bucket (grid-stride): distinct keys of the bucket into a
-// shared set and list, then appended at the hub's CSR offset, their term
-// sums added to the hub's.
+// shared set; a warp appends the keys it finds fresh straight after the
+// hub's keys written so far (one reservation per warp step on the hub's
+// counter) and adds their term sums to the bucket's, which go to the hub's
+// at the end.  If the set fills, the host repeats the hub with more buckets
+// (its counter restarts from zero, so the keys written are written again).
 template <typename K, int UCAP>
 __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -954,13 +959,14 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
       for (uint32_t i = tid; i < hcap * sizeof(K) / 16; i += kBucketThreads) s4[i] = ones;
     }
     if (tid == 0) {
-      sm.cnt = 0;
       sm.empty = 0;
       sm.full = 0;
       sm.lo = 0;
       sm.hi = 0;
     }
     __syncthreads();
+    K* hout = out + a.off[p];
+    unsigned long long* hcur = &h.hub_cur[hub];
     for (uint32_t i0 = 0; i0 < n; i0 += kBucketThreads * kBucketItems) {
       if (i0) {
 #pragma unroll
@@ -988,47 +994,28 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
         }
         const unsigned fm = __ballot_sync(kFull, fresh);
         if (fm == 0u) continue;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&sm.cnt, (uint32_t)__popc(fm));
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(hcur, (unsigned long long)__popc(fm));
+        const uint64_t tm = fresh ? elem_term(k, a.seed) : 0ull;
         base = __shfl_sync(kFull, base, 0);
-        const uint32_t q = base + __popc(fm & lanes_below(lane));
-        if (fresh) {
-          if (q < (uint32_t)UCAP) sm.uniq[q] = k; else sm.full = 1u;
+        if (fresh) hout[base + __popc(fm & lanes_below(lane))] = k;
+        const uint32_t lo = __reduce_add_sync(kFull, (uint32_t)tm);
+        const uint32_t hi = __reduce_add_sync(kFull, (uint32_t)(tm >> 32));
+        if (lane == 0) {
+          atomicAdd(&sm.lo, lo);
+          atomicAdd(&sm.hi, hi);
         }
       }
     }
     if (b + gridDim.x < n_buckets) fetch(b + gridDim.x);
     __syncthreads();
-    if (sm.full) {  // more distinct keys than the set holds: the host adds buckets
-      if (tid == 0) hub_fail(a, h, hub, kErrHubSet);
-      __syncthreads();
-      continue;
-    }
-    // the output reservation is in flight while the term sums are formed;
-    // the hub's count and hash are written by k_hub_finish
-    const uint32_t U = sm.cnt;
-    if (tid == 0) sm.obase = atomicAdd(&h.hub_cur[hub], (unsigned long long)U);
-    uint32_t lo = 0, hi = 0;
-    for (uint32_t i = tid; i < U; i += kBucketThreads) {
-      const uint64_t tm = elem_term(sm.uniq[i], a.seed);
-      lo += (uint32_t)tm;
-      hi += (uint32_t)(tm >> 32);
-    }
-    lo = __reduce_add_sync(kFull, lo);
-    hi = __reduce_add_sync(kFull, hi);
-    if (lane == 0) {
-      atomicAdd(&sm.lo, lo);
-      atomicAdd(&sm.hi, hi);
-    }
-    __syncthreads();
-    const uint64_t off = a.off[p] + sm.obase;
-    for (uint32_t i = tid; i < U; i += kBucketThreads) out[off + i] = sm.uniq[i];
     if (tid == 0) {
-      atomicAdd(&h.hub_term[2 * hub], sm.lo);
+      if (sm.full) hub_fail(a, h, hub, kErrHubSet);  // more distinct keys than the set holds: the host adds buckets
+      atomicAdd(&h.hub_term[2 * hub], sm.lo);      // (a failed hub's sums are cleared before its repeat)
       atomicAdd(&h.hub_term[2 * hub + 1], sm.hi);
     }
-    // no barrier here: the next bucket's first barrier comes before anything
-    // this bucket's output reads is written again
+    // no barrier here: thread 0 alone reads the bucket's totals, and the next
+    // bucket's first barrier comes before anything is written to them again
   }
 }
 
@@ -1858,11 +1845,14 @@ Status set_smem_attrs_for() {
 
   if (e == cudaSuccess) e = set_smem_attrs_label<uint32_t, K>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcapMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BucketSmem<K, kHubUcapMax>));
+    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcaps[0]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BucketSmem<K, kHubUcaps[0]>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcapMax / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BucketSmem<K, kHubUcapMax / 2>));
+    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcaps[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BucketSmem<K, kHubUcaps[1]>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_hub_bucket<K, kHubUcaps[2]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BucketSmem<K, kHubUcaps[2]>));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_verify_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)verify_ws_bytes<K>());
@@ -2121,6 +2111,14 @@ Status hub_layout(Store& s) {
   return cuda_check(cudaStreamSynchronize(s.stream), "hub layout");
 }
 
+// The bucket pass with buckets of at most U key words: one resident wave of CTAs.
+template <typename K, int U>
+void launch_hub_bucket(Store& s, const SigArgs& a, const HubArgs& h, int sms) {
+  const unsigned g = (unsigned)std::min<uint64_t>(
+      s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
+  k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(a, h, s.n_hub_buckets);
+}
+
 template <typename LabelT, typename K>
 Status run_signatures(Store& s, const SigArgs& a) {
   Status st;
@@ -2200,17 +2198,9 @@ Status run_signatures(Store& s, const SigArgs& a) {
           k_hub_sample<LabelT, K><<<(unsigned)((s.n_hub + 7) / 8), 256, 0, s.stream>>>(ah, h, s.n_hub);
           k_hub_chunk<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, hub_chunk_smem<K>(), s.stream>>>(ah, h);
           k_hub_scatter<LabelT, K><<<(unsigned)s.n_hub_chunks, kChunkThreads, 0, s.stream>>>(ah, h);
-          if (s.hub_ucap == (uint32_t)kHubUcapMax) {
-            constexpr int U = kHubUcapMax;
-            const unsigned g = (unsigned)std::min<uint64_t>(
-                s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
-            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(ah, h, s.n_hub_buckets);
-          } else {
-            constexpr int U = kHubUcapMax / 2;
-            const unsigned g = (unsigned)std::min<uint64_t>(
-                s.n_hub_buckets, resident_blocks(k_hub_bucket<K, U>, kBucketThreads, sizeof(BucketSmem<K, U>), sms));
-            k_hub_bucket<K, U><<<g, kBucketThreads, sizeof(BucketSmem<K, U>), s.stream>>>(ah, h, s.n_hub_buckets);
-          }
+          if (s.hub_ucap == (uint32_t)kHubUcaps[1]) launch_hub_bucket<K, kHubUcaps[1]>(s, ah, h, sms);
+          else if (s.hub_ucap == (uint32_t)kHubUcaps[2]) launch_hub_bucket<K, kHubUcaps[2]>(s, ah, h, sms);
+          else launch_hub_bucket<K, kHubUcaps[0]>(s, ah, h, sms);
           k_hub_finish<<<(unsigned)((s.n_hub + 255) / 256), 256, 0, s.stream>>>(ah, h, s.n_hub);
         }
         if (!(st = launch_check("hub kernels")).ok()) return st;
@@ -2260,45 +2250,46 @@ Status run_signatures(Store& s, const SigArgs& a) {
     // (a repeat runs only the hubs that overflowed); the faster size is kept.
     // Every pass writes the same signatures, so the round's result is the
     // last pass's.
-    const uint32_t sizes[2] = {(uint32_t)kHubUcapMax, (uint32_t)kHubUcapMax / 2};
+    constexpr int kSizes = 2;
     // bucket growth is learned per size: each starts from the growth before
     // tuning, and the chosen size keeps its own
     const std::vector<uint32_t> x0 = s.h_hub_xbits, sh0 = s.h_hub_shift;
     const std::vector<uint8_t> f0 = s.h_hub_force;
-    std::vector<uint32_t> x1, sh1;
-    std::vector<uint8_t> f1;
+    std::vector<uint32_t> xs[kSizes], shs[kSizes];
+    std::vector<uint8_t> fs[kSizes];
     cudaEvent_t ev[2];
     if (!(st = cuda_check(cudaEventCreate(&ev[0]), "event")).ok()) return st;
     if (!(st = cuda_check(cudaEventCreate(&ev[1]), "event")).ok()) {
       cudaEventDestroy(ev[0]);
       return st;
     }
-    for (int c = 0; c < 2 && st.ok(); ++c) {
-      if (c == 1) {
-        x1.swap(s.h_hub_xbits);
-        sh1.swap(s.h_hub_shift);
-        f1.swap(s.h_hub_force);
-        s.h_hub_xbits = x0;
-        s.h_hub_shift = sh0;
-        s.h_hub_force = f0;
-      }
-      s.hub_ucap = sizes[c];
+    for (int c = 0; c < kSizes && st.ok(); ++c) {
+      s.h_hub_xbits = x0;
+      s.h_hub_shift = sh0;
+      s.h_hub_force = f0;
+      s.hub_ucap = (uint32_t)kHubUcaps[c];
       if (!(st = hub_layout(s)).ok()) break;
       cudaEventRecord(ev[0], s.stream);
       if (!(st = run_hubs()).ok()) break;
       cudaEventRecord(ev[1], s.stream);
       if (!(st = cuda_check(cudaEventSynchronize(ev[1]), "event")).ok()) break;
       cudaEventElapsedTime(&s.hub_tune_ms[c], ev[0], ev[1]);
+      xs[c] = s.h_hub_xbits;
+      shs[c] = s.h_hub_shift;
+      fs[c] = s.h_hub_force;
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     if (!st.ok()) return st;
     s.hub_tune = 2;
-    if (s.hub_tune_ms[0] <= s.hub_tune_ms[1]) {
-      s.hub_ucap = sizes[0];
-      s.h_hub_xbits.swap(x1);
-      s.h_hub_shift.swap(sh1);
-      s.h_hub_force.swap(f1);
+    int best = 0;
+    for (int c = 1; c < kSizes; ++c)
+      if (s.hub_tune_ms[c] < s.hub_tune_ms[best]) best = c;
+    if (best != kSizes - 1) {
+      s.hub_ucap = (uint32_t)kHubUcaps[best];
+      s.h_hub_xbits.swap(xs[best]);
+      s.h_hub_shift.swap(shs[best]);
+      s.h_hub_force.swap(fs[best]);
       if (!(st = hub_layout(s)).ok()) return st;
     }
   }

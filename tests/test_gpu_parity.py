@@ -427,7 +427,8 @@ def test_hubs_with_distinct_keys():
     assert all(pids[lev][0] == pids[lev][1] for lev in range(pids.shape[0]))
 
 
-@pytest.mark.parametrize("heavy,ucap", [(10_000, 0), (30_000, 0), (10_000, 2048), (30_000, 2048), (30_000, 4096)])
+@pytest.mark.parametrize("heavy,ucap", [(10_000, 0), (30_000, 0), (10_000, 2048), (30_000, 2048), (30_000, 4096),
+                                        (30_000, 8192)])
 def test_hub_with_one_heavy_key_among_distinct_keys(heavy, ucap):
     """A 1M-edge hub whose keys are all distinct but one, which makes up 1% or
     3% of its edges: a key sample finds few repeats, so the hub skips the chunk
@@ -532,9 +533,9 @@ def test_grouping_with_a_block_of_a_million_nodes():
     assert_same(res, pids, oracle_levels(g, 3))
 
 
-@pytest.mark.parametrize("ucap", [0, 2048, 4096])
+@pytest.mark.parametrize("ucap", [0, 2048, 4096, 8192])
 def test_hub_bucket_sizes(ucap):
-    """Both hub bucket sizes (2048 and 4096 key words), and the size tuned in
+    """Each hub bucket size (2048, 4096 and 8192 key words), and the size tuned in
     the first round from level 2 on (which runs the hub pass with each size,
     the round keeping the last pass's signatures), give the oracle's levels on
     every degree tier, and a later refinement of the handle too."""
