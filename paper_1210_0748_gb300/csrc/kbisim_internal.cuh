@@ -201,6 +201,7 @@ struct MaintState {
   Buf cmp_info;                     // uint64 x 3 per pending comparison
   Buf big;                          // uint2 (node, label): long signatures copied by their own CTA
   Buf huge;                         // uint2 (node, label): the longest, copied by every CTA of a grid
+  Buf coarse;                       // bit w: word w of the changed bitmap is non-zero
   // last update
   int incremental = 0;              // 1 = frontier path, 0 = full recomputation
   int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)

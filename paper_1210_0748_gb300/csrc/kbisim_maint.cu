@@ -546,38 +546,67 @@ __global__ void k_assign(const uint32_t* list, uint64_t count, const uint32_t* r
   }
 }
 
-// Next frontier: seeds | changed | parents of changed nodes.  Out-degree <=
-// 64: one thread per node; larger: one warp per node.
-__global__ void k_frontier_small(uint64_t n_small, const uint64_t* off, const uint32_t* dst, const uint32_t* changed,
-                                 uint32_t* next) {
-  GRID_STRIDE(p, n_small) {
-    bool hit = false;
-    for (uint64_t e = off[p]; e < off[p + 1] && !hit; ++e) hit = bit(changed, dst[e]);
-    if (hit) set_bit(next, p);
+// Next frontier: seeds | changed | parents of changed nodes (a node is a
+// parent of a changed node if one of its out-edges points to it).
+// The parents by one pass over all edges, streamed in order: a coarse
+// bitmap (bit w set iff word w of `changed` is non-zero, 1 bit per 32 nodes;
+// 62.5 KB at 16M nodes, so it stays in L1) decides most edges without touching
+// the changed bitmap.  A warp takes kPullItems runs of 32 consecutive edges at
+// a time, all their target loads in flight together; in a run with a hit,
+// lane 0 finds the source of the run's first edge by binary search over the
+// offsets and each hit lane walks on from there (its edge lies at most 31
+// edges further), and lanes with the same source set its bit once.
+__global__ void k_changed_words(const uint32_t* changed, uint64_t words, uint32_t* coarse) {
+  GRID_STRIDE(w, words) {
+    if (changed[w]) atomicOr(&coarse[w >> 5], 1u << (w & 31));
   }
 }
-__global__ void k_frontier_large(uint64_t p0, uint64_t p1, const uint64_t* off, const uint32_t* dst,
-                                 const uint32_t* changed, uint32_t* next) {
+
+__device__ __forceinline__ uint64_t source_of(const uint64_t* off, uint64_t n, uint64_t e) {
+  uint64_t lo = 0, hi = n;  // off[lo] <= e < off[hi]: lo ends as the node whose edges hold e
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kPullItems = 8;
+
+__global__ void k_frontier_pull(uint64_t m, uint64_t n, const uint64_t* off, const uint32_t* dst,
+                                const uint32_t* changed, const uint32_t* coarse, uint32_t* next) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t p = p0 + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); p < p1; p += warps) {
-    bool hit = false;
-    for (uint64_t e = off[p] + lane; e < off[p + 1]; e += 32) {
-      hit |= bit(changed, dst[e]);
-      if (__any_sync(kFullMask, hit)) break;
+  constexpr uint64_t kSpan = 32 * kPullItems;
+  for (uint64_t base = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * kSpan; base < m;
+       base += warps * kSpan) {
+    uint32_t t[kPullItems];
+#pragma unroll
+    for (int r = 0; r < kPullItems; ++r) {
+      const uint64_t e = base + 32 * r + lane;
+      t[r] = e < m ? __ldg(dst + e) : 0xFFFFFFFFu;
     }
-    if (__any_sync(kFullMask, hit) && lane == 0) set_bit(next, p);
-  }
-}
-// Hubs, one CTA per chunk of the hub's edges.
-__global__ void k_frontier_hub(const uint4* chunks, uint64_t nchunks, uint64_t hub_first, const uint32_t* dst,
-                               const uint32_t* changed, uint32_t* next) {
-  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const uint4 q = chunks[c];
-    const uint64_t b = ((uint64_t)q.z << 32) | q.y;
-    bool hit = false;
-    for (uint32_t i = threadIdx.x; i < q.w; i += blockDim.x) hit |= bit(changed, dst[b + i]);
-    if (__syncthreads_or(hit) && threadIdx.x == 0) set_bit(next, hub_first + q.x);
+#pragma unroll
+    for (int r = 0; r < kPullItems; ++r) {
+      const uint64_t e = base + 32 * r + lane;
+      bool hit = false;
+      if (t[r] != 0xFFFFFFFFu) {
+        const uint32_t w = t[r] >> 5;
+        hit = ((__ldg(coarse + (w >> 5)) >> (w & 31)) & 1u) && bit(changed, t[r]);
+      }
+      const unsigned hm = __ballot_sync(kFullMask, hit);
+      if (!hm) continue;
+      uint64_t p0 = 0;
+      if (lane == 0) p0 = source_of(off, n, base + 32 * r);
+      p0 = __shfl_sync(kFullMask, p0, 0);
+      if (hit) {  // every lane of hm is here
+        uint64_t p = p0;
+        while (off[p + 1] <= e) ++p;  // ends: off[n] = m > e
+        const unsigned same = __match_any_sync(hm, p);
+        if (lane == (uint32_t)(__ffs(same) - 1) && !bit(next, p)) set_bit(next, p);
+      }
+    }
   }
 }
 
@@ -889,7 +918,7 @@ void maint_release(Store& s) {
   for (MaintLevel& L : m.lv) release_level(s, L);
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge};
+              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge, &m.coarse};
   for (Buf* x : b) release(s, *x);
   m.valid = false;
   m.k = 0;
@@ -993,19 +1022,16 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
     if (j == m.k) break;
     // next frontier: seeds | changed | parents of changed
     cudaMemsetAsync(m.fnext.p, 0, words * 4, s.stream);
-    const uint64_t n_small = s.class_start[kClassWarp];
-    if (n_small)
-      k_frontier_small<<<grid_for(s, n_small, kThreads), kThreads, 0, s.stream>>>(
-          n_small, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
-    const uint64_t hub_first = s.class_start[kClassHub];
-    if (hub_first > n_small)
-      k_frontier_large<<<(unsigned)s.sms * 16, kThreads, 0, s.stream>>>(n_small, hub_first, ptr<uint64_t>(s.offsets),
-                                                                       ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
-                                                                       ptr<uint32_t>(m.fnext));
-    if (s.n_hub_chunks)
-      k_frontier_hub<<<(unsigned)std::min<uint64_t>(s.n_hub_chunks, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
-          ptr<uint4>(s.hub_chunks), s.n_hub_chunks, hub_first, ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
-          ptr<uint32_t>(m.fnext));
+    if (s.m) {
+      const uint64_t cwords = (words + 31) / 32;
+      if (!(st = ensure(s, m.coarse, cwords * 4)).ok()) return st;
+      cudaMemsetAsync(m.coarse.p, 0, cwords * 4, s.stream);
+      k_changed_words<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.changed), words,
+                                                                            ptr<uint32_t>(m.coarse));
+      k_frontier_pull<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(s.m, n, ptr<uint64_t>(s.offsets),
+                                                                     ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
+                                                                     ptr<uint32_t>(m.coarse), ptr<uint32_t>(m.fnext));
+    }
     k_or3<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(words, ptr<uint32_t>(m.seeds),
                                                                     ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));
     std::swap(m.fmask, m.fnext);

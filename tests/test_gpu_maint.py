@@ -222,3 +222,28 @@ def test_timed_choice_between_the_paths():
     for r in reasons[3:]:  # never more than 15 recomputations in a row on cost
         run = run + 1 if r == "cost" else 0
         assert run <= 15, reasons
+
+
+def test_frontier_path_on_a_power_law_graph_all_levels():
+    """The frontier path on the 250K-node power-law graph (every degree class,
+    hubs, targets of in-degree in the thousands), batches of 200 edges: after
+    every batch all levels equal those of a handle that recomputes, which the
+    other tests tie to the oracle."""
+    rng = np.random.default_rng(57)
+    g = synth.config_single_large(scale=1 / 64, seed=11)
+    mg = _mg(g)
+    k = 3
+    with KBisim(maintain="always") as kb, KBisim(maintain=False) as plain:
+        kb.build(g, k)
+        plain.build(g, k)
+        inc = 0
+        for step in range(6):
+            add, ins, dels = _random_batch(rng, mg, 100, 100, labels=32, node_labels=16)
+            mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+            r1, _ = kb.update(k, ins=ins, dels=dels)
+            r2, _ = plain.update(k, ins=ins, dels=dels)
+            inc += kb.update_info()["incremental"]
+            assert list(r1.counts) == list(r2.counts)
+            for lev in range(k + 1):
+                assert np.array_equal(kb.pids(lev), plain.pids(lev)), (step, lev)
+        assert inc >= 4
