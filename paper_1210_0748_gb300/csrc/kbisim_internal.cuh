@@ -114,12 +114,19 @@ struct KeyOps<uint64_t> {
   }
 };
 
-// Per-element hash term: the SplitMix64 output function of (key + seed).  A
-// set's term sum adds the two 32-bit halves of the terms separately (each
-// modulo 2^32), so kernels can accumulate it with 32-bit adds in any order.
+// Per-element hash term.  A set's term sum adds the two 32-bit halves of the
+// terms separately (each modulo 2^32), so kernels can accumulate it with
+// 32-bit adds in any order.  64-bit words: the SplitMix64 output function of
+// (key + seed).  32-bit words: each half is the MurmurHash3 finalizer of the
+// word combined with one half of the seed (two 32-bit mixes cost about half
+// the instructions of one 64-bit mix; the hash only routes nodes to candidate
+// groups, and equality is always decided by exact comparison).
 template <typename K>
 __host__ __device__ __forceinline__ uint64_t elem_term(K key, uint64_t seed) {
   return mix64((uint64_t)key + seed);
+}
+__host__ __device__ __forceinline__ uint64_t elem_term(uint32_t key, uint64_t seed) {
+  return ((uint64_t)mix32(key ^ (uint32_t)(seed >> 32) ^ 0x9e3779b9u) << 32) | mix32(key + (uint32_t)seed);
 }
 
 // Sum of two packed term sums, half by half.
