@@ -919,7 +919,7 @@ struct BucketSmem {
 // at the end.  If the set fills, the host repeats the hub with more buckets
 // (its counter restarts from zero, so the keys written are written again).
 template <typename K, int UCAP>
-__global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
+__global__ void __launch_bounds__(kBucketThreads, sizeof(K) == 4 ? 6 : 3) k_hub_bucket(SigArgs a, HubArgs h, uint64_t n_buckets) {
   extern __shared__ __align__(16) char smem_raw[];
   BucketSmem<K, UCAP>& sm = *reinterpret_cast<BucketSmem<K, UCAP>*>(smem_raw);
   const uint32_t tid = threadIdx.x, lane = tid & 31;
@@ -975,13 +975,18 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
           kk[t] = i < n ? tmp[i] : (K)0;
         }
       }
-#pragma unroll 1
-      for (int t = 0; t < kBucketItems; ++t) {
-        if (i0 + (uint32_t)t * kBucketThreads >= n) break;  // the same for the whole CTA
-        const uint32_t i = i0 + tid + t * kBucketThreads;
-        const K k = kk[0];
+      // the keys of kBucketItems steps are inserted first; then the warp
+      // takes the places of all its fresh keys with one reservation on the
+      // hub's counter (its latency paid once, not per step) and adds their
+      // term sums once
+      unsigned fms[kBucketItems];
+      uint32_t lo = 0, hi = 0, total = 0;
 #pragma unroll
-        for (int q = 0; q + 1 < kBucketItems; ++q) kk[q] = kk[q + 1];
+      for (int t = 0; t < kBucketItems; ++t) {
+        fms[t] = 0u;
+        if (i0 + (uint32_t)t * kBucketThreads >= n) continue;  // the same for the whole CTA
+        const uint32_t i = i0 + tid + t * kBucketThreads;
+        const K k = kk[t];
         bool fresh = false;
         if (i < n) {
           if (k == KeyOps<K>::kEmpty) {
@@ -992,15 +997,25 @@ __global__ void __launch_bounds__(kBucketThreads) k_hub_bucket(SigArgs a, HubArg
             if (r < 0) sm.full = 1u;
           }
         }
-        const unsigned fm = __ballot_sync(kFull, fresh);
-        if (fm == 0u) continue;
+        fms[t] = __ballot_sync(kFull, fresh);
+        total += __popc(fms[t]);
+        if (fresh) {
+          const uint64_t tm = elem_term(k, a.seed);
+          lo += (uint32_t)tm;
+          hi += (uint32_t)(tm >> 32);
+        }
+      }
+      if (total) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(hcur, (unsigned long long)__popc(fm));
-        const uint64_t tm = fresh ? elem_term(k, a.seed) : 0ull;
+        if (lane == 0) base = atomicAdd(hcur, (unsigned long long)total);
         base = __shfl_sync(kFull, base, 0);
-        if (fresh) hout[base + __popc(fm & lanes_below(lane))] = k;
-        const uint32_t lo = __reduce_add_sync(kFull, (uint32_t)tm);
-        const uint32_t hi = __reduce_add_sync(kFull, (uint32_t)(tm >> 32));
+#pragma unroll
+        for (int t = 0; t < kBucketItems; ++t) {
+          if ((fms[t] >> lane) & 1u) hout[base + __popc(fms[t] & lanes_below(lane))] = kk[t];
+          base += __popc(fms[t]);
+        }
+        lo = __reduce_add_sync(kFull, lo);
+        hi = __reduce_add_sync(kFull, hi);
         if (lane == 0) {
           atomicAdd(&sm.lo, lo);
           atomicAdd(&sm.hi, hi);
