@@ -599,7 +599,7 @@ def main():
         barrier()
         t0 = time.perf_counter()
         e2e_rounds = 0
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, min(args.steps, 10))
         for _ in range(e2e_steps):
             r = kb2.build(host_g, K_ROUNDS)
             kb2._check(kb2._lib.kbisim_pids(kb2._h, K_ROUNDS, out_np.ctypes.data, 0))
