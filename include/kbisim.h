@@ -117,8 +117,11 @@ typedef struct {
    * again, level by level, against per-level signature stores kept in the
    * handle; 0 = kbisim_update recomputes every level.  Results are identical.
    * The stores are made at the first update after a build (a cost of about
-   * one signature pass per level) and take about 12 bytes per edge and 16 per
-   * node per maintained level.  The handle times both paths (host clock, per
+   * one signature pass per level) and take, per maintained level, about 24
+   * bytes per distinct element of the stored signatures (up to one per edge:
+   * the element pool keeps room for three times the stored elements, for the
+   * signatures later updates add) and about 84 bytes per node (labels, and a
+   * table twice as large as the number of labels).  The handle times both paths (host clock, per
    * maintained level, building the stores not included: they serve every
    * later update; the handle's first frontier update, which allocates that
    * path's scratch, is not timed): after one timed update on each, it takes
