@@ -226,6 +226,11 @@ struct MaintState {
   uint32_t n_inc = 0, n_rec = 0;
   uint32_t cost_skip = 0;
   bool inc_warm = false;  // a frontier update has run on this handle (later ones are timed)
+  // width of the element words the stores are built from: 32-bit when edge
+  // label bits + pbits fit (pbits covers the node labels, which are the level-0
+  // labels, and twice the node count, which bounds every later label)
+  bool key32 = false;
+  uint32_t pbits = 32;
 };
 
 struct Store;

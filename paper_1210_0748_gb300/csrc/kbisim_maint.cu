@@ -148,11 +148,18 @@ struct StoreArgs {
 
 struct NodeSig {
   const uint64_t* off;      // CSR offsets (internal ids)
-  const uint64_t* sigkey;   // element words of each node at its CSR offset
+  const uint64_t* sigkey;   // element words of each node at its CSR offset (64-bit keys)
+  const uint32_t* sigkey32; //   or these, when the stores use 32-bit keys (then sigkey is null)
   const uint32_t* ucnt;
   const uint64_t* hash;
   const uint32_t* prev;     // labels of the level below, internal order (first component)
 };
+
+// Element word i of the signature words (32-bit keys are widened; the stores
+// keep 64-bit words either way).
+__device__ __forceinline__ uint64_t sig_word(const NodeSig& g, uint64_t i) {
+  return g.sigkey32 ? (uint64_t)g.sigkey32[i] : g.sigkey[i];
+}
 
 // Claim a table slot for hash h and label b (the signature is already stored).
 __device__ bool store_slot(const StoreArgs& a, uint64_t h, uint32_t b) {
@@ -186,8 +193,8 @@ __device__ void store_signature(const StoreArgs& a, const NodeSig& g, uint64_t p
     return;
   }
   if (U <= kInlineCopy) {
-    const uint64_t* src = g.sigkey + g.off[p];
-    for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = src[i];
+    const uint64_t o = g.off[p];
+    for (uint32_t i = lane; i < U; i += 32) a.pool[base + i] = sig_word(g, o + i);
   } else if (lane == 0) {
     big[atomicAdd(n_big, 1ull)] = make_uint2((uint32_t)p, b);
   }
@@ -215,9 +222,9 @@ __global__ void k_copy_big(StoreArgs a, NodeSig g, const uint2* big, uint64_t n_
       if (threadIdx.x == 0) huge[atomicAdd(n_huge, 1ull)] = e;
       continue;
     }
-    const uint64_t* src = g.sigkey + g.off[e.x];
+    const uint64_t o = g.off[e.x];
     unsigned long long* dstp = a.pool + a.soff[e.y];
-    for (uint32_t i = threadIdx.x; i < U; i += blockDim.x) dstp[i] = src[i];
+    for (uint32_t i = threadIdx.x; i < U; i += blockDim.x) dstp[i] = sig_word(g, o + i);
   }
 }
 
@@ -228,9 +235,9 @@ __global__ void k_copy_huge(StoreArgs a, NodeSig g, const uint2* huge, const uns
     const uint2 e = huge[q];
     const uint64_t U = a.scount[e.y];
     const uint64_t lo = U * blockIdx.x / gridDim.x, hi = U * (blockIdx.x + 1) / gridDim.x;
-    const uint64_t* src = g.sigkey + g.off[e.x];
+    const uint64_t o = g.off[e.x];
     unsigned long long* dstp = a.pool + a.soff[e.y];
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dstp[i] = src[i];
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dstp[i] = sig_word(g, o + i);
   }
 }
 
@@ -267,8 +274,8 @@ __global__ void k_store_heads(StoreArgs a, NodeSig g, uint64_t n_alive, const ui
     const uint32_t U = g.ucnt[p];
     const unsigned long long base = woff[p];
     if (U <= kBuildInlineCopy) {
-      const uint64_t* src = g.sigkey + g.off[p];
-      for (uint32_t i = 0; i < U; ++i) a.pool[base + i] = src[i];
+      const uint64_t o = g.off[p];
+      for (uint32_t i = 0; i < U; ++i) a.pool[base + i] = sig_word(g, o + i);
     } else {
       big[atomicAdd(n_big, 1ull)] = make_uint2((uint32_t)p, b);
     }
@@ -297,7 +304,7 @@ __global__ void k_head_words(uint64_t n_alive, uint64_t n, const uint32_t* p2o, 
 // among the stored ones (both lists are duplicate-free).
 __device__ bool warp_same_set(const StoreArgs& a, const NodeSig& g, uint64_t p, uint32_t b, uint32_t U) {
   const uint32_t lane = threadIdx.x & 31;
-  const uint64_t mine = lane < U ? g.sigkey[g.off[p] + lane] : 0ull;
+  const uint64_t mine = lane < U ? sig_word(g, g.off[p] + lane) : 0ull;
   const uint64_t stored = lane < U ? a.pool[a.soff[b] + lane] : 0ull;
   bool found = lane >= U;
   for (uint32_t j = 0; j < U; ++j) found |= __shfl_sync(kFullMask, stored, j) == mine;
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeS
     const uint32_t p = l.heads[e.x], b = e.y;
     const uint32_t U = g.ucnt[p];
     if (U > kCmpChunk) continue;  // compared by k_big_* through a set in global memory
-    const uint64_t* mine = g.sigkey + g.off[p];
+    const uint64_t mo = g.off[p];
     const unsigned long long* stored = a.pool + a.soff[b];
     uint32_t found = 0;
     for (uint32_t c0 = 0; c0 < U; c0 += kCmpChunk) {
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeS
       }
       __syncthreads();
       for (uint32_t i = threadIdx.x; i < U; i += kCmpThreads) {
-        const unsigned long long k = mine[i];
+        const unsigned long long k = sig_word(g, mo + i);
         uint32_t s = (uint32_t)(mix64(k) & (kCmpSlots - 1));
         for (int t = 0; t < kCmpSlots; ++t) {
           const unsigned long long cur = set[s];
@@ -415,7 +422,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_long_compare(StoreArgs a, NodeS
       uint32_t extra = 0;
       bool mine_has = false, stored_has = false;
       for (uint32_t i = 0; i < U; ++i) {
-        mine_has |= mine[i] == kEmpty64;
+        mine_has |= sig_word(g, mo + i) == kEmpty64;
         stored_has |= stored[i] == kEmpty64;
       }
       if (mine_has && stored_has) extra = 1;
@@ -445,11 +452,11 @@ __global__ void k_big_insert(const unsigned long long* stored, uint32_t U, unsig
   }
 }
 
-__global__ void k_big_lookup(const uint64_t* mine, uint32_t U, const unsigned long long* set, uint64_t smask,
+__global__ void k_big_lookup(NodeSig g, uint64_t mo, uint32_t U, const unsigned long long* set, uint64_t smask,
                              unsigned int* flags) {
   unsigned int found = 0;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < U; i += (uint64_t)gridDim.x * blockDim.x) {
-    const unsigned long long k = mine[i];
+    const unsigned long long k = sig_word(g, mo + i);
     if (k == kEmpty64) {
       found += flags[0];
       continue;
@@ -673,7 +680,8 @@ StoreArgs store_args(Store& s, MaintLevel& L) {
 NodeSig node_sig(Store& s) {
   NodeSig g;
   g.off = ptr<uint64_t>(s.offsets);
-  g.sigkey = ptr<uint64_t>(s.sigkey);
+  g.sigkey = s.mt.key32 ? nullptr : ptr<uint64_t>(s.sigkey);
+  g.sigkey32 = s.mt.key32 ? ptr<uint32_t>(s.sigkey) : nullptr;
   g.ucnt = ptr<uint32_t>(s.ucnt);
   g.hash = ptr<uint64_t>(s.hash);
   g.prev = ptr<uint32_t>(s.mt.prev_int);
@@ -872,7 +880,7 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
       cudaMemsetAsync(flags, 0, 8, s.stream);
       const unsigned gb = grid_for(s, U, kThreads);
       k_big_insert<<<gb, kThreads, 0, s.stream>>>(ptr<unsigned long long>(L.pool) + soff, U, set, slots - 1, flags);
-      k_big_lookup<<<gb, kThreads, 0, s.stream>>>(ptr<uint64_t>(s.sigkey) + noff, U, set, slots - 1, flags);
+      k_big_lookup<<<gb, kThreads, 0, s.stream>>>(node_sig(s), noff, U, set, slots - 1, flags);
       k_big_result<<<1, 1, 0, s.stream>>>(flags, U, match + q);
       if (!(st = cuda_check(cudaGetLastError(), "long compare")).ok()) return st;
     }
@@ -924,12 +932,55 @@ void maint_release(Store& s) {
   m.k = 0;
 }
 
+// Largest node label of the alive nodes (internal order: alive ones first).
+__global__ void k_max_node_label(uint64_t n_alive, const uint32_t* nlabel, unsigned int* out) {
+  unsigned int mx = 0;
+  GRID_STRIDE(p, n_alive) mx = max(mx, nlabel[p]);
+  mx = __reduce_max_sync(kFullMask, mx);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+Status max_node_label(Store& s, uint32_t* out) {
+  unsigned long long* sc = ptr<unsigned long long>(s.mt.misc);
+  cudaMemsetAsync(sc + 13, 0, 8, s.stream);
+  k_max_node_label<<<grid_for(s, std::max<uint64_t>(s.n_alive, 1), kThreads), kThreads, 0, s.stream>>>(
+      s.n_alive, ptr<uint32_t>(s.nlabel), reinterpret_cast<unsigned int*>(sc + 13));
+  uint64_t v = 0;
+  Status st = cuda_check(cudaGetLastError(), "node labels");
+  if (st.ok()) st = sync_read(s, &v, sc + 13, 8, "node labels");
+  *out = (uint32_t)v;
+  return st;
+}
+
+uint32_t bits_of(uint64_t v) {  // bits for values 0..v
+  uint32_t b = 1;
+  while (b < 64 && (v >> b)) ++b;
+  return b;
+}
+
+// The labels a store's keys carry fit its pbits: node labels (level 0) and
+// original ids (every later label, < n).
+Status labels_fit(Store& s, bool* fit) {
+  uint32_t mx = 0;
+  Status st = max_node_label(s, &mx);
+  if (!st.ok()) return st;
+  const uint64_t top = std::max<uint64_t>((uint64_t)mx, std::max<uint64_t>(s.n, 1) - 1);
+  *fit = bits_of(top) <= s.mt.pbits && s.label_bits + s.mt.pbits <= 32;
+  return Status::Ok();
+}
+
 Status maint_build(Store& s, uint32_t k) {
   MaintState& m = s.mt;
   m.valid = false;
   if (!s.has_levels) return Status::Err(KBISIM_ERR_STATE, "no computed levels");
   Status st;
   if (!(st = ensure_common(s)).ok()) return st;
+  {  // the stores' key width: 32-bit words when labels up to twice the node count fit
+    uint32_t mx = 0;
+    if (!(st = max_node_label(s, &mx)).ok()) return st;
+    m.pbits = bits_of(std::max<uint64_t>((uint64_t)mx, 2 * std::max<uint64_t>(s.n, 1) - 1));
+    m.key32 = s.label_bits + m.pbits <= 32;
+  }
   for (size_t j = k + 1; j < m.lv.size(); ++j) release_level(s, m.lv[j]);
   m.lv.resize(k + 1);
   const uint64_t n = s.n;
@@ -966,6 +1017,15 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
   const uint64_t n0 = s.n;
   if (!(st = apply_batch(s, b, missing)).ok()) return st;
   *done = true;  // from here on the graph is the updated one
+  if (m.key32 && (s.n > n0 || s.label_bits + m.pbits > 32)) {  // new nodes or wider labels may no longer fit
+    bool fit = true;
+    if (!(st = labels_fit(s, &fit)).ok()) return st;
+    if (!fit) {
+      m.valid = false;
+      m.reason = KBISIM_MAINT_CAPACITY;
+      return Status::Ok();
+    }
+  }
   m.incremental = 0;
   m.frontier_nodes = 0;
   m.levels = 0;

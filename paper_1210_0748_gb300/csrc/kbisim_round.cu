@@ -2846,6 +2846,10 @@ Status masked_signatures(Store& s, const uint32_t* prev, const uint32_t* fmask) 
   a.mask = s.hash_mask;
   a.err = ptr<uint32_t>(s.d_err);
   a.fmask = fmask;
+  if (s.mt.key32) {  // labels below 2^pbits (the stores' width)
+    a.pbits = (int)s.mt.pbits;
+    return s.label8 ? run_signatures<uint8_t, uint32_t>(s, a) : run_signatures<uint32_t, uint32_t>(s, a);
+  }
   a.pbits = 32;
   return s.label8 ? run_signatures<uint8_t, uint64_t>(s, a) : run_signatures<uint32_t, uint64_t>(s, a);
 }
@@ -2866,7 +2870,7 @@ Status group_list(Store& s, const uint32_t* list, uint64_t count, const uint32_t
   g.read_first = 0;
   VerifyArgs v;
   v.mode = 1;
-  v.key64 = 1;
+  v.key64 = s.mt.key32 ? 0 : 1;
   v.nlabel = ptr<uint32_t>(s.nlabel);
   v.prev = prev;
   v.ucnt = ptr<uint32_t>(s.ucnt);

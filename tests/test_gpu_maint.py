@@ -247,3 +247,35 @@ def test_frontier_path_on_a_power_law_graph_all_levels():
             for lev in range(k + 1):
                 assert np.array_equal(kb.pids(lev), plain.pids(lev)), (step, lev)
         assert inc >= 4
+
+
+def test_store_key_widths():
+    """The stores use 32-bit element words when node labels and twice the
+    node count fit beside the edge label bits, 64-bit words otherwise: node
+    labels up to 2^31 take the 64-bit words; a small graph that gains nodes
+    until they no longer fit switches back once and rebuilds its stores.  Every
+    batch equals the oracle."""
+    rng = np.random.default_rng(61)
+    g = synth.random_small_graph(3000, 12_000, node_labels=3, edge_labels=3, seed=3)
+    wide = rng.integers(0, 2**31, g.num_nodes).astype(np.uint32)
+    g = synth.from_coo(g.num_nodes, g.src(), g.dst, g.edge_label, wide)
+    mg = _mg(g)
+    with KBisim(maintain="always") as kb:
+        kb.build(g, 3)
+        for _ in range(4):
+            add, ins, dels = _random_batch(rng, mg, 6, 3)
+            mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+            res, _ = kb.update(3, ins=ins, dels=dels)
+            assert_same(res, kb.all_pids(3), mg.kbisim(3))
+    small = synth.random_small_graph(50, 150, node_labels=2, edge_labels=2, seed=4)
+    mg = _mg(small)
+    reasons = []
+    with KBisim(maintain="always") as kb:
+        kb.build(small, 3)
+        for step in range(6):
+            add, ins, dels = _random_batch(rng, mg, 4, 2, n_add=30, labels=2, node_labels=2)
+            mg.apply(add, list(zip(*ins)), list(zip(*dels)))
+            res, _ = kb.update(3, add_node_label=add, ins=ins, dels=dels)
+            reasons.append(kb.update_info()["reason"])
+            assert_same(res, kb.all_pids(3), mg.kbisim(3))
+    assert "capacity" in reasons, reasons
