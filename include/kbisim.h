@@ -44,7 +44,9 @@
  *    report KBISIM_ERR_TIMEOUT; KBISIM_FAULT_CORRUPT_DST=1 (checked mode only)
  *    sets one stored edge target to num_nodes before each round, which the
  *    checked-mode index check reports as KBISIM_ERR_CHECKED (the value is put
- *    back before the call returns).
+ *    back before the call returns); KBISIM_FAULT_STORE_ROOM=W builds the
+ *    signature stores of incremental maintenance with W words of room beyond
+ *    their signatures (default 4M), so that the next updates grow them.
  *  - Inputs are borrowed for the duration of the call only; the library
  *    copies what it keeps.  Results live in the handle and stay valid until
  *    the next call that loads, refines, extends or updates the handle, or

@@ -36,7 +36,10 @@ Status cuda_check(cudaError_t e, const char* what) {
 //   KBISIM_FAULT_CORRUPT_DST=1    with options.checked only: one stored edge
 //                                 target is set to num_nodes (one past the
 //                                 last node) before each round, which the
-//                                 checked-mode index check must report.
+//                                 checked-mode index check must report;
+//   KBISIM_FAULT_STORE_ROOM=W     the signature stores of maintenance are
+//                                 built with W pool words of room (default
+//                                 4M), so that the next updates grow them.
 void read_fault_hooks(Store& s) {
   const char* a = std::getenv("KBISIM_FAULT_ALLOC");
   s.fault_alloc = (a && *a) ? std::strtol(a, nullptr, 10) : -1;
@@ -44,6 +47,8 @@ void read_fault_hooks(Store& s) {
   s.fault_timeout_round = (t && *t) ? (uint32_t)std::strtoul(t, nullptr, 10) : 0u;
   const char* c = std::getenv("KBISIM_FAULT_CORRUPT_DST");
   s.fault_corrupt_dst = s.checked && c && *c == '1';
+  const char* r = std::getenv("KBISIM_FAULT_STORE_ROOM");
+  s.store_room = (r && *r) ? (uint64_t)std::strtoull(r, nullptr, 10) : (uint64_t)(4u << 20);
 }
 
 Status ensure(Store& s, Buf& b, size_t bytes) {

@@ -351,10 +351,13 @@ struct Store {
   // Host-side fault injection for tests (read from the environment at every
   // mutating call, see read_fault_hooks): allocations that succeed before one
   // fails (-1 = off), the round that reports a timeout (0 = off), and, in
-  // checked mode only, one edge target set out of range before each round.
+  // checked mode only, one edge target set out of range before each round;
+  // and the pool words of room a signature store is built with beyond its
+  // signatures' words (smaller: the next updates grow the store).
   long fault_alloc = -1;
   uint32_t fault_timeout_round = 0;
   bool fault_corrupt_dst = false;
+  uint64_t store_room = 4u << 20;
 
   // hub bucket size (key words at most per bucket: 2048, 4096 or 8192) and its
   // tuning: 1 = the next full round from level 2 on times both sizes and

@@ -671,7 +671,7 @@ StoreArgs store_args(Store& s, MaintLevel& L) {
   a.soff = ptr<unsigned long long>(L.soff);
   a.pool = ptr<unsigned long long>(L.pool);
   a.ctr = ptr<unsigned long long>(L.ctr);
-  a.lcap = L.lcap;
+  a.lcap = s.mt.key32 ? std::min<uint64_t>(L.lcap, 1ull << s.mt.pbits) : L.lcap;  // labels fit the element words
   a.pcap = L.pcap;
   a.err = ptr<uint32_t>(s.d_err);
   return a;
@@ -766,7 +766,7 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = scan_u64(s, reinterpret_cast<uint64_t*>(woff), n + 1)).ok()) return st;
   uint64_t words = 0;
   if (!(st = sync_read(s, &words, woff + n, 8, "store size")).ok()) return st;
-  L.pcap = 3 * words + (4u << 20);  // room for the signatures later updates add
+  L.pcap = 3 * words + s.store_room;  // room for the signatures later updates add (then grown)
   L.tcap = pow2_at_least(2 * L.lcap);
   if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
   if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
@@ -799,13 +799,101 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   return Status::Ok();
 }
 
-// Heads of the frontier groups (rep[p] == p), listed.
-__global__ void k_group_heads(const uint32_t* list, uint64_t count, const uint32_t* rep, uint32_t* heads,
-                              unsigned long long* n) {
+// Heads of the frontier groups (rep[p] == p), listed, and their element
+// counts summed (the most pool words the level's new signatures can take).
+__global__ void k_group_heads(const uint32_t* list, uint64_t count, const uint32_t* rep, const uint32_t* ucnt,
+                              uint32_t* heads, unsigned long long* n, unsigned long long* words) {
   GRID_STRIDE(i, count) {
     const uint32_t p = list[i];
-    if (rep[p] == p) heads[atomicAdd(n, 1ull)] = p;
+    if (rep[p] == p) {
+      heads[atomicAdd(n, 1ull)] = p;
+      atomicAdd(words, (unsigned long long)ucnt[p]);
+    }
   }
+}
+
+// Every occupied slot of a table into the (larger, empty) table of a.
+__global__ void k_rehash(const unsigned long long* okey, const uint32_t* oval, uint64_t ocap, StoreArgs a) {
+  GRID_STRIDE(i, ocap) {
+    const unsigned long long h = okey[i];
+    if (h != kEmpty64 && !store_slot(a, h, oval[i])) atomicOr(a.err, 1u);
+  }
+}
+
+bool no_room(const Status& st) {
+  return st.code == KBISIM_ERR_BUDGET || st.code == KBISIM_ERR_OUT_OF_MEMORY;
+}
+
+// Room in S_j for `labels` labels and `words` pool words: the label arrays,
+// the table (kept at most half full) and the pool grow, keeping what they
+// hold.  *fits is false when the labels would not fit the element words of
+// the level above, or the device has no room (the caller recomputes).
+Status reserve_store(Store& s, MaintLevel& L, uint64_t used_labels, uint64_t labels, uint64_t used_words,
+                     uint64_t words, bool* fits) {
+  MaintState& m = s.mt;
+  const uint64_t limit = m.key32 ? (1ull << m.pbits) : (uint64_t)kNone32;
+  Status st;
+  if (labels > limit) {
+    *fits = false;
+    return Status::Ok();
+  }
+  if (labels > L.lcap) {
+    const uint64_t lcap = std::min<uint64_t>(pow2_at_least(2 * labels), limit);
+    if ((st = grow_keep(s, L.sfirst, lcap * 4, used_labels * 4)).ok() &&
+        (st = grow_keep(s, L.scount, lcap * 4, used_labels * 4)).ok())
+      st = grow_keep(s, L.soff, lcap * 8, used_labels * 8);
+    if (!st.ok()) {
+      if (!no_room(st)) return st;
+      *fits = false;
+      return Status::Ok();
+    }
+    L.lcap = lcap;
+  }
+  if (2 * labels > L.tcap) {
+    const uint64_t tcap = pow2_at_least(4 * labels);
+    Buf nk, nv;
+    if ((st = ensure(s, nk, tcap * 8)).ok()) st = ensure(s, nv, tcap * 4);
+    if (!st.ok()) {
+      release(s, nk);
+      release(s, nv);
+      if (!no_room(st)) return st;
+      *fits = false;
+      return Status::Ok();
+    }
+    cudaMemsetAsync(nk.p, 0xFF, tcap * 8, s.stream);
+    cudaMemsetAsync(nv.p, 0xFF, tcap * 4, s.stream);
+    StoreArgs a = store_args(s, L);
+    a.tkey = ptr<unsigned long long>(nk);
+    a.tval = ptr<uint32_t>(nv);
+    a.tmask = tcap - 1;
+    cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
+    k_rehash<<<grid_for(s, L.tcap, kThreads), kThreads, 0, s.stream>>>(ptr<unsigned long long>(L.tkey),
+                                                                      ptr<uint32_t>(L.tval), L.tcap, a);
+    uint32_t e = 0;
+    if ((st = cuda_check(cudaGetLastError(), "rehash")).ok()) st = sync_read(s, &e, s.d_err.p, 4, "rehash");
+    if (st.ok() && (e & 1u)) st = Status::Err(KBISIM_ERR_TIMEOUT, "signature table rehash found no slot");
+    if (!st.ok()) {
+      release(s, nk);
+      release(s, nv);
+      return st;
+    }
+    release(s, L.tkey);
+    release(s, L.tval);
+    L.tkey = nk;
+    L.tval = nv;
+    L.tcap = tcap;
+  }
+  if (words > L.pcap) {
+    const uint64_t pcap = words + std::max<uint64_t>(words / 2, 4u << 20);
+    st = grow_keep(s, L.pool, pcap * 8, used_words * 8);
+    if (!st.ok()) {
+      if (!no_room(st)) return st;
+      *fits = false;
+      return Status::Ok();
+    }
+    L.pcap = pcap;
+  }
+  return Status::Ok();
 }
 
 // One level of an update: the frontier (fmask) gets its labels of level j.
@@ -829,12 +917,18 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   uint32_t* heads = match + cnt;
   uint32_t* retry = heads + cnt;
   unsigned long long* sc = ptr<unsigned long long>(m.misc);
-  cudaMemsetAsync(sc, 0, 32, s.stream);
-  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
-  k_group_heads<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep), heads, sc);
-  uint64_t nheads = 0;
+  cudaMemsetAsync(sc, 0, 48, s.stream);
+  k_group_heads<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep),
+                                                                        ptr<uint32_t>(s.ucnt), heads, sc, sc + 5);
+  cudaMemcpyAsync(sc + 6, L.ctr.p, 16, cudaMemcpyDeviceToDevice, s.stream);
+  uint64_t hv8[8] = {};
   if (!(st = cuda_check(cudaGetLastError(), "group heads")).ok()) return st;
-  if (!(st = sync_read(s, &nheads, sc, 8, "group heads")).ok()) return st;
+  if (!(st = sync_read(s, hv8, sc, 64, "group heads")).ok()) return st;
+  const uint64_t nheads = hv8[0];
+  // every head may store a new signature: [6] labels handed out, [7] pool words used
+  if (!(st = reserve_store(s, L, hv8[6], hv8[6] + nheads, hv8[7], hv8[7] + hv8[5], fits)).ok()) return st;
+  if (!*fits) return Status::Ok();
+  cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
   LookupArgs la;
   la.heads = heads;
   la.start = nullptr;

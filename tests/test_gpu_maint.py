@@ -279,3 +279,36 @@ def test_store_key_widths():
             reasons.append(kb.update_info()["reason"])
             assert_same(res, kb.all_pids(3), mg.kbisim(3))
     assert "capacity" in reasons, reasons
+
+
+@pytest.mark.parametrize("wide", [False, True])
+def test_stores_grow_during_updates(monkeypatch, wide):
+    """Stores built with 64 words of room (KBISIM_FAULT_STORE_ROOM) on a graph
+    of few blocks take a batch that gives 3000 nodes new signatures: the pool
+    and the label arrays grow and the table is rehashed, keeping what they
+    hold, and the update stays on the frontier path; a second batch takes
+    500 of those nodes back to no out-edges, signatures stored at the build.
+    With 32-bit element words (node labels 5/1) and 64-bit ones (node labels
+    near 2^31 beside 8-bit edge labels); every batch equals the oracle."""
+    monkeypatch.setenv("KBISIM_FAULT_STORE_ROOM", "64")
+    rng = np.random.default_rng(71)
+    n = 40_000
+    nl = np.where(np.arange(n) % 2 == 0, 5, (2**31 - 3) if wide else 1).astype(np.uint32)
+    src = np.arange(100, dtype=np.uint32)
+    g = synth.from_coo(n, src, src + 1, np.full(100, 255, np.uint32), nl)  # edge labels of 8 bits from the start
+    mg = _mg(g)
+    k = 3
+    srcs = rng.permutation(np.arange(200, n))[:3000].astype(np.uint32)
+    a = (np.arange(3000) % 256).astype(np.uint32)
+    b = ((np.arange(3000) // 256 + a + 1) % 256).astype(np.uint32)
+    first = (np.concatenate([srcs, srcs]), rng.integers(0, n, 6000).astype(np.uint32), np.concatenate([a, b]))
+    pick = np.concatenate([np.arange(500), 3000 + np.arange(500)])
+    again = tuple(x[pick] for x in first)  # 500 nodes back to no out-edges
+    with KBisim(maintain="always") as kb:
+        kb.build(g, k)
+        for ins, dels in ((first, ()), ((), again)):
+            mg.apply(ins=list(zip(*ins)) if ins else [], dels=list(zip(*dels)) if dels else [])
+            res, _ = kb.update(k, ins=ins, dels=dels)
+            info = kb.update_info()
+            assert info["incremental"], info
+            assert_same(res, kb.all_pids(k), mg.kbisim(k))
