@@ -180,7 +180,10 @@ struct ManyState {
 // table from signature hash to label plus, per label, the signature itself
 // (first component, element count, element words in a pool).  A label keeps
 // its meaning across updates, so a node whose signature does not change keeps
-// its label, and only changed labels propagate to parents (Algorithm 3).
+// its label, and only changed labels propagate to parents (Algorithm 3).  A
+// block all of whose members take one new signature that no label holds keeps
+// its label too (the partition of the level is unchanged): the label is
+// pointed at the new signature, and the old entry no longer matches anything.
 struct MaintLevel {
   Buf lab;                  // uint32 [n] label of each node, original order (kDead: deleted)
   Buf tkey;                 // uint64 [tcap] signature hash of each slot (all ones: empty)
@@ -188,8 +191,10 @@ struct MaintLevel {
   Buf sfirst, scount;       // uint32 [lcap] first component and element count of each label's signature
   Buf soff;                 // uint64 [lcap] first element word of each label in pool
   Buf pool;                 // uint64 [pcap] element words of the stored signatures
+  Buf cnt;                  // uint32 [lcap] nodes holding each label
   Buf ctr;                  // uint64 [2] labels handed out, pool words used
   uint64_t tcap = 0, lcap = 0, pcap = 0;
+  uint64_t entries = 0;     // table slots taken (those of re-pointed labels included)
 };
 
 struct MaintState {
@@ -209,6 +214,9 @@ struct MaintState {
   Buf big;                          // uint2 (node, label): long signatures copied by their own CTA
   Buf huge;                         // uint2 (node, label): the longest, copied by every CTA of a grid
   Buf coarse;                       // bit w: word w of the changed bitmap is non-zero
+  Buf gold, gsize;                  // uint32 [n] per frontier group head: its members' old label,
+                                    // member count (top bit: members of several old labels)
+  Buf hit;                          // bitmap over labels: matched by a head in this level's lookups
   // last update
   int incremental = 0;              // 1 = frontier path, 0 = full recomputation
   int reason = 0;                   // why the last update recomputed everything (KBISIM_MAINT_*)

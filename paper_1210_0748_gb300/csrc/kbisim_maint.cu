@@ -315,7 +315,9 @@ __device__ bool warp_same_set(const StoreArgs& a, const NodeSig& g, uint64_t p, 
 // heads: (node, first slot to probe).  A stored signature with the same hash,
 // first component and count is compared here when it has at most 32 elements;
 // longer ones go to `pend` (node, label, slot) for k_long_compare.  A head
-// whose probe reaches an empty slot stores its signature under a new label.
+// whose probe reaches an empty slot is listed in `missed`; k_assign_missed
+// gives those their labels once every lookup of the level is done (distinct
+// heads have distinct signatures, so no head could find another's).
 struct LookupArgs {
   const uint32_t* heads;    // node ids
   const unsigned long long* start;  // per head: slot to start at, or all ones for the home slot
@@ -325,6 +327,9 @@ struct LookupArgs {
   unsigned long long* n_pend;
   uint2* big;               // new signatures copied by k_copy_big (node, label)
   unsigned long long* n_big;
+  uint32_t* missed;         // heads whose signature no label holds
+  unsigned long long* n_missed;
+  uint32_t* hit;            // bitmap over labels: found by some head
 };
 
 __global__ void k_lookup(StoreArgs a, NodeSig g, LookupArgs l) {
@@ -352,14 +357,35 @@ __global__ void k_lookup(StoreArgs a, NodeSig g, LookupArgs l) {
         break;
       }
       if (warp_same_set(a, g, p, b, U)) {
-        if (lane == 0) l.newlab[p] = b;
+        if (lane == 0) {
+          l.newlab[p] = b;
+          set_bit(l.hit, b);
+        }
         done = true;
       }
     }
-    if (done) continue;
-    // not in S_j: a new label
+    if (!done && lane == 0) l.missed[atomicAdd(l.n_missed, 1ull)] = p;  // not in S_j
+  }
+}
+
+// Labels of the heads no label matched (one warp per head).  A head keeps its
+// members' old label B when the group is all of B (every member had label B,
+// and as many as B has nodes) and no head found B in this level: B's block is
+// unchanged as a set, it only takes the new signature, so B is pointed at it.
+// Any other head gets a new label.  Each B is all of at most one group, so no
+// two heads take the same label.
+__global__ void k_assign_missed(StoreArgs a, NodeSig g, LookupArgs l, uint64_t n_missed, const uint32_t* gold,
+                                const uint32_t* gsize, const uint32_t* cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < n_missed; i += warps) {
+    const uint32_t p = l.missed[i];
     uint32_t b = 0;
-    if (lane == 0) b = (uint32_t)atomicAdd(&a.ctr[0], 1ull);
+    if (lane == 0) {
+      const uint32_t B = gold[p], sz = gsize[p];
+      const bool keep = B != kNone32 && !(sz >> 31) && sz == cnt[B] && !bit(l.hit, B);
+      b = keep ? B : (uint32_t)atomicAdd(&a.ctr[0], 1ull);
+    }
     b = __shfl_sync(kFullMask, b, 0);
     store_signature(a, g, p, b, l.big, l.n_big);
     if (lane == 0) l.newlab[p] = b;
@@ -502,6 +528,7 @@ __global__ void k_resolve(LookupArgs l, uint64_t n_pend, const uint32_t* match, 
     const uint32_t p = l.heads[e.x];
     if (match[q]) {
       l.newlab[p] = e.y;
+      set_bit(l.hit, e.y);
     } else {
       const unsigned long long r = atomicAdd(n_retry, 1ull);
       retry_heads[r] = p;
@@ -539,18 +566,27 @@ __global__ void k_seed_new(uint64_t n0, uint64_t n1, const uint32_t* o2p, uint32
 }
 
 // Labels of level j for the frontier: a head's new label goes to every node
-// of its group; nodes whose label changed are marked.
+// of its group; nodes whose label changed are marked and counted, and the
+// labels' node counts follow.
 __global__ void k_assign(const uint32_t* list, uint64_t count, const uint32_t* rep, const uint32_t* newlab,
-                         const uint32_t* p2o, uint32_t* lab, uint32_t* changed) {
+                         const uint32_t* p2o, uint32_t* lab, uint32_t* changed, uint32_t* cnt,
+                         unsigned long long* n_changed) {
+  unsigned int nc = 0;
   GRID_STRIDE(i, count) {
     const uint32_t p = list[i];
     const uint32_t b = newlab[rep[p]];
     const uint32_t o = p2o[p];
-    if (lab[o] != b) {
+    const uint32_t old = lab[o];
+    if (old != b) {
       lab[o] = b;
       set_bit(changed, p);
+      if (old != kNone32) atomicSub(&cnt[old], 1u);
+      atomicAdd(&cnt[b], 1u);
+      ++nc;
     }
   }
+  nc = __reduce_add_sync(kFullMask, nc);
+  if ((threadIdx.x & 31) == 0 && nc) atomicAdd(n_changed, (unsigned long long)nc);
 }
 
 // Next frontier: seeds | changed | parents of changed nodes (a node is a
@@ -582,7 +618,9 @@ __device__ __forceinline__ uint64_t source_of(const uint64_t* off, uint64_t n, u
 constexpr int kPullItems = 8;
 
 __global__ void k_frontier_pull(uint64_t m, uint64_t n, const uint64_t* off, const uint32_t* dst,
-                                const uint32_t* changed, const uint32_t* coarse, uint32_t* next) {
+                                const uint32_t* changed, const uint32_t* coarse, const unsigned long long* n_changed,
+                                uint32_t* next) {
+  if (*n_changed == 0) return;  // no label changed: no parents to add
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   constexpr uint64_t kSpan = 32 * kPullItems;
@@ -754,9 +792,11 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = masked_signatures(s, ptr<uint32_t>(m.prev_int), nullptr)).ok()) return st;
   L.lcap = pow2_at_least(2 * labels + 1024);
   if (!(st = ensure(s, m.minid, L.lcap * 4)).ok()) return st;
+  if (!(st = ensure(s, L.cnt, L.lcap * 4)).ok()) return st;
   cudaMemsetAsync(m.minid.p, 0xFF, L.lcap * 4, s.stream);
+  cudaMemsetAsync(L.cnt.p, 0, L.lcap * 4, s.stream);
   k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, ptr<uint32_t>(L.lab), ptr<uint32_t>(m.minid),
-                                                                      nullptr);
+                                                                      ptr<uint32_t>(L.cnt));
   if (!(st = ensure(s, m.woff, (n + 1) * 8)).ok()) return st;
   unsigned long long* woff = ptr<unsigned long long>(m.woff);
   k_head_words<<<grid_for(s, n + 1, kThreads), kThreads, 0, s.stream>>>(na, n, ptr<uint32_t>(s.p2o),
@@ -768,6 +808,7 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
   if (!(st = sync_read(s, &words, woff + n, 8, "store size")).ok()) return st;
   L.pcap = 3 * words + s.store_room;  // room for the signatures later updates add (then grown)
   L.tcap = pow2_at_least(2 * L.lcap);
+  L.entries = labels;
   if (!(st = ensure(s, L.tkey, L.tcap * 8)).ok()) return st;
   if (!(st = ensure(s, L.tval, L.tcap * 4)).ok()) return st;
   if (!(st = ensure(s, L.sfirst, L.lcap * 4)).ok()) return st;
@@ -800,15 +841,31 @@ Status build_level_store(Store& s, uint32_t j, uint64_t labels) {
 }
 
 // Heads of the frontier groups (rep[p] == p), listed, and their element
-// counts summed (the most pool words the level's new signatures can take).
+// counts summed (the most pool words the level's new signatures can take);
+// each head's old label starts its group's record (k_group_stats).
 __global__ void k_group_heads(const uint32_t* list, uint64_t count, const uint32_t* rep, const uint32_t* ucnt,
-                              uint32_t* heads, unsigned long long* n, unsigned long long* words) {
+                              const uint32_t* p2o, const uint32_t* lab, uint32_t* heads, unsigned long long* n,
+                              unsigned long long* words, uint32_t* gold, uint32_t* gsize) {
   GRID_STRIDE(i, count) {
     const uint32_t p = list[i];
     if (rep[p] == p) {
       heads[atomicAdd(n, 1ull)] = p;
       atomicAdd(words, (unsigned long long)ucnt[p]);
+      gold[p] = lab[p2o[p]];
+      gsize[p] = 0;
     }
+  }
+}
+
+// Per frontier group: how many members, and whether they all had the head's
+// old label (top bit of gsize set otherwise).
+__global__ void k_group_stats(const uint32_t* list, uint64_t count, const uint32_t* rep, const uint32_t* p2o,
+                              const uint32_t* lab, const uint32_t* gold, uint32_t* gsize) {
+  GRID_STRIDE(i, count) {
+    const uint32_t p = list[i];
+    const uint32_t h = rep[p];
+    if (lab[p2o[p]] != gold[h]) atomicOr(&gsize[h], 0x80000000u);
+    atomicAdd(&gsize[h], 1u);
   }
 }
 
@@ -824,12 +881,13 @@ bool no_room(const Status& st) {
   return st.code == KBISIM_ERR_BUDGET || st.code == KBISIM_ERR_OUT_OF_MEMORY;
 }
 
-// Room in S_j for `labels` labels and `words` pool words: the label arrays,
-// the table (kept at most half full) and the pool grow, keeping what they
-// hold.  *fits is false when the labels would not fit the element words of
-// the level above, or the device has no room (the caller recomputes).
+// Room in S_j for `labels` labels, `words` pool words and `entries` table
+// slots: the label arrays, the table (kept at most half full) and the pool
+// grow, keeping what they hold (new labels' node counts start at zero).
+// *fits is false when the labels would not fit the element words of the
+// level above, or the device has no room (the caller recomputes).
 Status reserve_store(Store& s, MaintLevel& L, uint64_t used_labels, uint64_t labels, uint64_t used_words,
-                     uint64_t words, bool* fits) {
+                     uint64_t words, uint64_t entries, bool* fits) {
   MaintState& m = s.mt;
   const uint64_t limit = m.key32 ? (1ull << m.pbits) : (uint64_t)kNone32;
   Status st;
@@ -840,17 +898,19 @@ Status reserve_store(Store& s, MaintLevel& L, uint64_t used_labels, uint64_t lab
   if (labels > L.lcap) {
     const uint64_t lcap = std::min<uint64_t>(pow2_at_least(2 * labels), limit);
     if ((st = grow_keep(s, L.sfirst, lcap * 4, used_labels * 4)).ok() &&
-        (st = grow_keep(s, L.scount, lcap * 4, used_labels * 4)).ok())
+        (st = grow_keep(s, L.scount, lcap * 4, used_labels * 4)).ok() &&
+        (st = grow_keep(s, L.cnt, lcap * 4, used_labels * 4)).ok())
       st = grow_keep(s, L.soff, lcap * 8, used_labels * 8);
     if (!st.ok()) {
       if (!no_room(st)) return st;
       *fits = false;
       return Status::Ok();
     }
+    cudaMemsetAsync(ptr<uint32_t>(L.cnt) + used_labels, 0, (lcap - used_labels) * 4, s.stream);
     L.lcap = lcap;
   }
-  if (2 * labels > L.tcap) {
-    const uint64_t tcap = pow2_at_least(4 * labels);
+  if (2 * entries > L.tcap) {
+    const uint64_t tcap = pow2_at_least(4 * entries);
     Buf nk, nv;
     if ((st = ensure(s, nk, tcap * 8)).ok()) st = ensure(s, nv, tcap * 4);
     if (!st.ok()) {
@@ -907,27 +967,42 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   if (!(st = masked_signatures(s, ptr<uint32_t>(m.prev_int), ptr<uint32_t>(m.fmask))).ok()) return st;
   if (!(st = group_list(s, list, count, ptr<uint32_t>(m.prev_int))).ok()) return st;
   // heads of the frontier groups (rep[p] == p) look up S_j; scratch of the
-  // lookup: pending long compares, restart slots, results, heads, retries
+  // lookup: pending long compares, restart slots, results, heads, retries,
+  // heads no label matched
   const size_t cnt = std::max<uint64_t>(count, 1);
-  if (!(st = ensure(s, m.pend, cnt * (sizeof(uint4) + 8 + 8 + 4 + 4 + 4))).ok()) return st;
+  if (!(st = ensure(s, m.pend, cnt * (sizeof(uint4) + 8 + 8 + 4 + 4 + 4 + 4))).ok()) return st;
   uint4* pend = ptr<uint4>(m.pend);
   unsigned long long* start = reinterpret_cast<unsigned long long*>(pend + cnt);
   uint2* big = reinterpret_cast<uint2*>(start + cnt);
   uint32_t* match = reinterpret_cast<uint32_t*>(big + cnt);
   uint32_t* heads = match + cnt;
   uint32_t* retry = heads + cnt;
+  uint32_t* missed = retry + cnt;
+  const uint64_t nn = std::max<uint64_t>(s.n, 1);
+  if (!(st = ensure(s, m.gold, nn * 4)).ok()) return st;
+  if (!(st = ensure(s, m.gsize, nn * 4)).ok()) return st;
+  uint32_t* gold = ptr<uint32_t>(m.gold);
+  uint32_t* gsize = ptr<uint32_t>(m.gsize);
   unsigned long long* sc = ptr<unsigned long long>(m.misc);
   cudaMemsetAsync(sc, 0, 48, s.stream);
-  k_group_heads<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep),
-                                                                        ptr<uint32_t>(s.ucnt), heads, sc, sc + 5);
+  k_group_heads<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(
+      list, count, ptr<uint32_t>(s.rep), ptr<uint32_t>(s.ucnt), ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab), heads, sc,
+      sc + 5, gold, gsize);
+  k_group_stats<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep),
+                                                                        ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
+                                                                        gold, gsize);
   cudaMemcpyAsync(sc + 6, L.ctr.p, 16, cudaMemcpyDeviceToDevice, s.stream);
   uint64_t hv8[8] = {};
   if (!(st = cuda_check(cudaGetLastError(), "group heads")).ok()) return st;
   if (!(st = sync_read(s, hv8, sc, 64, "group heads")).ok()) return st;
   const uint64_t nheads = hv8[0];
   // every head may store a new signature: [6] labels handed out, [7] pool words used
-  if (!(st = reserve_store(s, L, hv8[6], hv8[6] + nheads, hv8[7], hv8[7] + hv8[5], fits)).ok()) return st;
+  if (!(st = reserve_store(s, L, hv8[6], hv8[6] + nheads, hv8[7], hv8[7] + hv8[5], L.entries + nheads, fits)).ok())
+    return st;
   if (!*fits) return Status::Ok();
+  const uint64_t hwords = L.lcap / 32 + 1;
+  if (!(st = ensure(s, m.hit, hwords * 4)).ok()) return st;
+  cudaMemsetAsync(m.hit.p, 0, hwords * 4, s.stream);
   cudaMemsetAsync(s.d_err.p, 0, 4, s.stream);
   LookupArgs la;
   la.heads = heads;
@@ -938,17 +1013,21 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   la.n_pend = sc + 1;
   la.big = big;
   la.n_big = sc + 3;
+  la.missed = missed;
+  la.n_missed = sc + 4;  // zeroed above, summed over the passes
+  la.hit = ptr<uint32_t>(m.hit);
   const StoreArgs sa = store_args(s, L);
   const NodeSig ns = node_sig(s);
+  uint64_t n_missed = 0;
   for (int pass = 0; la.count; ++pass) {
     if (pass > 64) return Status::Err(KBISIM_ERR_TIMEOUT, "signature lookup made no progress");
-    cudaMemsetAsync(sc + 1, 0, 24, s.stream);  // [1] pending, [2] retries, [3] long copies
+    cudaMemsetAsync(sc + 1, 0, 16, s.stream);  // [1] pending, [2] retries
     k_lookup<<<(unsigned)std::min<uint64_t>((la.count + 7) / 8, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(sa, ns,
                                                                                                             la);
-    uint64_t hv[3] = {0, 0, 0};
+    uint64_t hv[4] = {0, 0, 0, 0};  // [0] pending, [3] missed so far
     if (!(st = cuda_check(cudaGetLastError(), "lookup")).ok()) return st;
-    if (!(st = sync_read(s, hv, sc + 1, 24, "lookup")).ok()) return st;
-    if (!(st = copy_long_signatures(s, sa, ns, big, hv[2])).ok()) return st;
+    if (!(st = sync_read(s, hv, sc + 1, 32, "lookup")).ok()) return st;
+    n_missed = hv[3];
     const uint64_t np = hv[0];
     if (!np) break;
     k_long_compare<<<(unsigned)std::min<uint64_t>(np, (uint64_t)s.sms * 4), kCmpThreads, 0, s.stream>>>(sa, ns, la, np,
@@ -989,6 +1068,16 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
     la.start = start;
     la.count = nr;
   }
+  if (n_missed) {  // their labels: kept by unchanged blocks, else new; then their signatures stored
+    cudaMemsetAsync(sc + 3, 0, 8, s.stream);
+    k_assign_missed<<<(unsigned)std::min<uint64_t>((n_missed + 7) / 8, (uint64_t)s.sms * 8), kThreads, 0, s.stream>>>(
+        sa, ns, la, n_missed, gold, gsize, ptr<uint32_t>(L.cnt));
+    uint64_t nb = 0;
+    if (!(st = cuda_check(cudaGetLastError(), "new labels")).ok()) return st;
+    if (!(st = sync_read(s, &nb, sc + 3, 8, "new labels")).ok()) return st;
+    if (!(st = copy_long_signatures(s, sa, ns, big, nb)).ok()) return st;
+    L.entries += n_missed;
+  }
   uint32_t e = 0;
   if (!(st = sync_read(s, &e, s.d_err.p, 4, "store")).ok()) return st;
   if (e & 1u) {
@@ -997,16 +1086,16 @@ Status update_level(Store& s, uint32_t j, uint64_t count, bool* fits) {
   }
   const uint64_t words = s.n / 32 + 1;
   cudaMemsetAsync(m.changed.p, 0, words * 4, s.stream);
-  k_assign<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(list, count, ptr<uint32_t>(s.rep),
-                                                                    ptr<uint32_t>(m.newlab), ptr<uint32_t>(s.p2o),
-                                                                    ptr<uint32_t>(L.lab), ptr<uint32_t>(m.changed));
+  k_assign<<<grid_for(s, count, kThreads), kThreads, 0, s.stream>>>(
+      list, count, ptr<uint32_t>(s.rep), ptr<uint32_t>(m.newlab), ptr<uint32_t>(s.p2o), ptr<uint32_t>(L.lab),
+      ptr<uint32_t>(m.changed), ptr<uint32_t>(L.cnt), sc + 11);
   return cuda_check(cudaGetLastError(), "assign labels");
 }
 
 }  // namespace
 
 void release_level(Store& s, MaintLevel& L) {
-  Buf* b[] = {&L.lab, &L.tkey, &L.tval, &L.sfirst, &L.scount, &L.soff, &L.pool, &L.ctr};
+  Buf* b[] = {&L.lab, &L.tkey, &L.tval, &L.sfirst, &L.scount, &L.soff, &L.pool, &L.cnt, &L.ctr};
   for (Buf* x : b) release(s, *x);
 }
 
@@ -1020,7 +1109,8 @@ void maint_release(Store& s) {
   for (MaintLevel& L : m.lv) release_level(s, L);
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge, &m.coarse};
+              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge, &m.coarse,
+              &m.gold, &m.gsize, &m.hit};
   for (Buf* x : b) release(s, *x);
   m.valid = false;
   m.k = 0;
@@ -1151,6 +1241,7 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
   for (uint32_t j = 1; j <= m.k && fits; ++j) {
     // frontier of level j: count, switch back when large, list
     cudaMemsetAsync(sc + 8, 0, 16, s.stream);
+    cudaMemsetAsync(sc + 11, 0, 8, s.stream);  // labels changed at this level (k_assign)
     k_popc_sum<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.fmask), words, sc + 8);
     uint64_t count = 0;
     if (!(st = cuda_check(cudaGetLastError(), "frontier")).ok()) return st;
@@ -1182,9 +1273,9 @@ Status maint_update(Store& s, const kbisim_batch* b, uint32_t k, uint64_t* missi
       cudaMemsetAsync(m.coarse.p, 0, cwords * 4, s.stream);
       k_changed_words<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(m.changed), words,
                                                                             ptr<uint32_t>(m.coarse));
-      k_frontier_pull<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(s.m, n, ptr<uint64_t>(s.offsets),
-                                                                     ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed),
-                                                                     ptr<uint32_t>(m.coarse), ptr<uint32_t>(m.fnext));
+      k_frontier_pull<<<(unsigned)s.sms * 8, kThreads, 0, s.stream>>>(
+          s.m, n, ptr<uint64_t>(s.offsets), ptr<uint32_t>(s.dst), ptr<uint32_t>(m.changed), ptr<uint32_t>(m.coarse),
+          sc + 11, ptr<uint32_t>(m.fnext));
     }
     k_or3<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(words, ptr<uint32_t>(m.seeds),
                                                                     ptr<uint32_t>(m.changed), ptr<uint32_t>(m.fnext));

@@ -312,3 +312,61 @@ def test_stores_grow_during_updates(monkeypatch, wide):
             info = kb.update_info()
             assert info["incremental"], info
             assert_same(res, kb.all_pids(k), mg.kbisim(k))
+
+
+def _update_both(kb, mg, k, ins=(), dels=()):
+    """One batch through the handle and the oracle; the handle's levels must
+    equal the oracle's and the update must take the frontier path."""
+    arr = lambda t: tuple(np.array(x, np.uint32) for x in zip(*t)) if t else ()
+    mg.apply(ins=ins, dels=dels)
+    res, _ = kb.update(k, ins=arr(ins), dels=arr(dels))
+    info = kb.update_info()
+    assert info["incremental"], info
+    assert_same(res, kb.all_pids(k), mg.kbisim(k))
+    return info
+
+
+def test_unchanged_blocks_keep_their_labels():
+    """A block all of whose nodes take one new signature that no label holds
+    keeps its label, so nothing propagates to its parents: on a graph whose
+    node labels are all distinct (every block a single node) an inserted edge
+    leaves the frontier at its source on every level.  A block that moves
+    whole keeps its label; a block that splits does not; and a block whose
+    old signature another frontier node takes in the same level gets a new
+    label.  Every batch equals the oracle."""
+    rng = np.random.default_rng(83)
+    n, k = 1000, 4
+    edges = [(int(a), int(l), int(b)) for a, l, b in zip(rng.integers(0, n, 4000), rng.integers(0, 3, 4000),
+                                                       rng.integers(0, n, 4000))]
+    g = graph_from_edges(n, np.arange(n, dtype=np.uint32), edges)
+    mg = _mg(g)
+    with KBisim(maintain="always") as kb:
+        kb.build(g, k)
+        info = _update_both(kb, mg, k, ins=[(5, 17, 2)])
+        assert info["frontier_nodes"] == k, info  # the source alone, on each level
+        info = _update_both(kb, mg, k, dels=[(5, 17, 2)])
+        assert info["frontier_nodes"] == k, info
+    # nodes 0..3 share node label 1, 4 and 5 label 2; 6 is the parent of 0
+    # and 1.  Level 1: {0, 1} one block (one edge of label 0 to a label-2
+    # node), {2} (label 1), {3} (labels 0 and 1).  Batches as (src, dst, label).
+    lab = np.array([1, 1, 1, 1, 2, 2, 3, 4], np.uint32)
+    base = [(0, 0, 4), (1, 0, 5), (2, 1, 4), (3, 0, 4), (3, 1, 5), (6, 0, 0), (6, 1, 1), (7, 0, 2)]
+    steps = [
+        dict(ins=[(0, 4, 2), (1, 5, 2)]),         # {0, 1} moves whole to a signature no label holds
+        dict(ins=[(0, 4, 1)]),                    # {0, 1} splits
+        dict(ins=[(2, 4, 0)], dels=[(3, 5, 1)]),  # 2 takes {3}'s signature, 3 a signature no label holds
+        dict(ins=[(7, 2, 1)], dels=[(2, 4, 1)]),  # 2 takes 3's new one
+    ]
+    g = graph_from_edges(8, lab, base)
+    mg = _mg(g)
+    with KBisim(maintain="always") as kb:
+        kb.build(g, 3)
+        for st in steps:
+            _update_both(kb, mg, 3, **st)
+    # the hit rule: {x} moves to a new signature while z takes x's old one
+    lab = np.array([1, 1, 2, 2], np.uint32)
+    g = graph_from_edges(4, lab, [(0, 0, 2), (1, 1, 3)])  # x = 0: (1, {(0, 2)}); z = 1: (1, {(1, 2)})
+    mg = _mg(g)
+    with KBisim(maintain="always") as kb:
+        kb.build(g, 2)
+        _update_both(kb, mg, 2, ins=[(0, 2, 3), (1, 3, 0)], dels=[(1, 3, 1)])  # x: new; z: x's old
