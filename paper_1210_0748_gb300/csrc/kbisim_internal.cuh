@@ -205,7 +205,7 @@ struct MaintState {
   Buf list, pend;                   // uint32 frontier list; pending head lookups
   Buf prev_int;                     // uint32 [n] labels of the level below, internal order
   Buf newlab;                       // uint32 [n] label found for each frontier head (internal id)
-  Buf minid, cnt;                   // uint32 [lcap] canonical renumbering from labels
+  Buf minid;                        // uint32 [lcap] smallest original id of each label
   Buf src;                          // uint32 staged sources of the batch's edges
   Buf misc;                         // uint64 scalars
   Buf woff;                         // uint64 [n + 1] pool offsets of the heads' signatures (build)

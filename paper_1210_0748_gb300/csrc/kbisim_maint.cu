@@ -748,17 +748,15 @@ Status canonical_from_labels(Store& s, uint32_t j, uint32_t* pid, uint64_t* bloc
   const uint64_t n = s.n, words = n / 32 + 1;
   Status st;
   if (!(st = ensure(s, m.minid, L.lcap * 4)).ok()) return st;
-  if (!(st = ensure(s, m.cnt, L.lcap * 4)).ok()) return st;
   if (!(st = ensure(s, s.hbits, words * 4 + 16)).ok()) return st;
   if (!(st = ensure(s, s.hword, words * 8)).ok()) return st;
   cudaMemsetAsync(m.minid.p, 0xFF, L.lcap * 4, s.stream);
-  cudaMemsetAsync(m.cnt.p, 0, L.lcap * 4, s.stream);
   cudaMemsetAsync(s.hbits.p, 0, words * 4, s.stream);
   unsigned long long* sc = ptr<unsigned long long>(m.misc);
   cudaMemsetAsync(sc + 4, 0, 8, s.stream);
   const uint32_t* lab = ptr<uint32_t>(L.lab);
-  k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, lab, ptr<uint32_t>(m.minid),
-                                                                      ptr<uint32_t>(m.cnt));
+  // the labels' node counts are kept by the store build and every assignment
+  k_label_heads<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, lab, ptr<uint32_t>(m.minid), nullptr);
   k_label_head_bits<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(n, lab, ptr<uint32_t>(m.minid),
                                                                           ptr<uint32_t>(s.hbits));
   k_word_popc<<<grid_for(s, words, kThreads), kThreads, 0, s.stream>>>(ptr<uint32_t>(s.hbits), words,
@@ -766,7 +764,7 @@ Status canonical_from_labels(Store& s, uint32_t j, uint32_t* pid, uint64_t* bloc
   if (!(st = cuda_check(cudaGetLastError(), "canonical ids")).ok()) return st;
   if (!(st = scan_u64(s, ptr<uint64_t>(s.hword), words)).ok()) return st;
   k_label_pid<<<grid_for(s, n, kThreads), kThreads, 0, s.stream>>>(
-      n, s.n_alive, ptr<uint32_t>(s.p2o), lab, ptr<uint32_t>(m.minid), ptr<uint32_t>(m.cnt), ptr<uint32_t>(s.hbits),
+      n, s.n_alive, ptr<uint32_t>(s.p2o), lab, ptr<uint32_t>(m.minid), ptr<uint32_t>(L.cnt), ptr<uint32_t>(s.hbits),
       ptr<uint64_t>(s.hword), pid, alone ? ptr<uint8_t>(s.alone) : nullptr, sc + 4);
   if (!(st = cuda_check(cudaGetLastError(), "canonical ids")).ok()) return st;
   uint64_t tail[2] = {0, 0};
@@ -1109,7 +1107,7 @@ void maint_release(Store& s) {
   for (MaintLevel& L : m.lv) release_level(s, L);
   m.lv.clear();
   Buf* b[] = {&m.fmask, &m.fnext, &m.changed, &m.seeds, &m.list, &m.pend, &m.prev_int, &m.newlab,
-              &m.minid, &m.cnt, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge, &m.coarse,
+              &m.minid, &m.src, &m.misc, &m.woff, &m.cmp, &m.cmp_info, &m.big, &m.huge, &m.coarse,
               &m.gold, &m.gsize, &m.hit};
   for (Buf* x : b) release(s, *x);
   m.valid = false;

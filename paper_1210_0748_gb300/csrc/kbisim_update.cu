@@ -431,7 +431,11 @@ __global__ void k_claim_deletes(uint64_t k, const uint32_t* ds, const uint32_t* 
 }
 
 // Deletions whose source is a hub: one CTA per deletion scans the hub's
-// segment a block of edges at a time.
+// segment, kClaimItems blocks of edges at a time with all their loads in
+// flight (a hub holds up to millions of edges, and a copy of the triple may
+// lie anywhere in it).
+constexpr int kClaimItems = 8;
+
 template <typename LabelT>
 __global__ void __launch_bounds__(1024) k_claim_deletes_hub(uint64_t k, const uint32_t* ds, const uint32_t* dt,
                                                             const uint32_t* dl, uint64_t n0, const uint64_t* off,
@@ -445,26 +449,43 @@ __global__ void __launch_bounds__(1024) k_claim_deletes_hub(uint64_t k, const ui
     if (threadIdx.x == 0) done = 0;
     __syncthreads();
     const uint64_t e1 = off[p + 1];
-    for (uint64_t e0 = off[p]; e0 < e1; e0 += blockDim.x) {
-      const uint64_t e = e0 + threadIdx.x;
-      const bool cand = e < e1 && dst[e] == t && (uint32_t)lab[e] == l;
-      // candidates take turns in lane order within the block until one claims
-      if (__syncthreads_or(cand)) {
-        for (uint32_t w = 0; w < blockDim.x; w += 32) {
+    for (uint64_t e0 = off[p]; e0 < e1; e0 += (uint64_t)blockDim.x * kClaimItems) {
+      uint32_t tv[kClaimItems], lv[kClaimItems];
+#pragma unroll
+      for (int r = 0; r < kClaimItems; ++r) {
+        const uint64_t e = e0 + (uint64_t)r * blockDim.x + threadIdx.x;
+        tv[r] = e < e1 ? dst[e] : 0u;
+        lv[r] = e < e1 ? (uint32_t)lab[e] : 0u;
+      }
+      uint32_t cm = 0;  // bit r: this thread's edge of block r is a copy of the triple
+#pragma unroll
+      for (int r = 0; r < kClaimItems; ++r) {
+        const uint64_t e = e0 + (uint64_t)r * blockDim.x + threadIdx.x;
+        if (e < e1 && tv[r] == t && lv[r] == l) cm |= 1u << r;
+      }
+      // candidates take turns, block by block and in lane order within a
+      // block, until one claims (`done` is read after a barrier: uniform)
+      if (__syncthreads_or(cm != 0)) {
+        for (int r = 0; r < kClaimItems; ++r) {
           if (done) break;
-          if (threadIdx.x >= w && threadIdx.x < w + 32) {
-            unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-            while (m && !done) {
-              const int j = __ffs(m) - 1;
-              m &= m - 1;
-              if ((threadIdx.x & 31) == (uint32_t)j) {
-                const uint64_t ej = e;
-                if (!((atomicOr(&claimed[ej >> 5], 1u << (ej & 31)) >> (ej & 31)) & 1u)) done = 1;
+          const bool cand = (cm >> r) & 1u;
+          const uint64_t e = e0 + (uint64_t)r * blockDim.x + threadIdx.x;
+          if (!__syncthreads_or(cand)) continue;
+          for (uint32_t w = 0; w < blockDim.x; w += 32) {
+            if (done) break;
+            if (threadIdx.x >= w && threadIdx.x < w + 32) {
+              unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+              while (m && !done) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                if ((threadIdx.x & 31) == (uint32_t)j) {
+                  if (!((atomicOr(&claimed[e >> 5], 1u << (e & 31)) >> (e & 31)) & 1u)) done = 1;
+                }
+                __syncwarp();
               }
-              __syncwarp();
             }
+            __syncthreads();
           }
-          __syncthreads();
         }
       }
       __syncthreads();

@@ -370,3 +370,33 @@ def test_unchanged_blocks_keep_their_labels():
     with KBisim(maintain="always") as kb:
         kb.build(g, 2)
         _update_both(kb, mg, 2, ins=[(0, 2, 3), (1, 3, 0)], dels=[(1, 3, 1)])  # x: new; z: x's old
+
+
+def test_deletions_on_a_long_hub():
+    """Deletions whose source is a hub of 40K edges over 600 distinct triples
+    (about 67 copies each, spread over the whole segment): repeated deletions
+    of one triple claim distinct copies, deletions beyond a triple's copies
+    count as missing, and the levels equal the oracle, on both update paths."""
+    rng = np.random.default_rng(97)
+    n = 3000
+    t = rng.integers(0, 200, 40_000).astype(np.uint32)
+    l = rng.integers(0, 3, 40_000).astype(np.uint32)
+    other = 9000
+    src = np.concatenate([np.full(t.size, 5, np.uint32), rng.integers(0, n, other).astype(np.uint32)])
+    dst = np.concatenate([t, rng.integers(0, n, other).astype(np.uint32)])
+    lab = np.concatenate([l, rng.integers(0, 3, other).astype(np.uint32)])
+    g = synth.from_coo(n, src, dst, lab, rng.integers(0, 3, n).astype(np.uint32))
+    for maintain in ("always", False):
+        mg = _mg(g)
+        with KBisim(maintain=maintain) as kb:
+            kb.build(g, 3)
+            for step in range(3):
+                pick = rng.integers(0, 40_000, 150)
+                reps = 1 + (np.arange(pick.size) % 3) * 40  # 1, 41 or 81 deletions of a triple
+                ds = np.repeat(np.full(pick.size, 5, np.uint32), reps)
+                dt = np.repeat(t[pick], reps)
+                dl = np.repeat(l[pick], reps)
+                want = mg.apply(dels=list(zip(ds, dt, dl)))
+                res, missing = kb.update(3, dels=(ds, dt, dl))
+                assert missing == want and want > 0, (missing, want)
+                assert_same(res, kb.all_pids(3), mg.kbisim(3))
