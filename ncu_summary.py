@@ -114,6 +114,35 @@ def summarise(launches, rounds: int):
     return per_kernel, total_t, per_call
 
 
+def per_round(launches):
+    """Time of each kernel class per level of the last refinement: level 0,
+    then one column per round.  A round starts at its first signature kernel
+    after the previous level's renumbering."""
+    first = max((i for i, (_, n, _) in enumerate(launches) if n.startswith(("k_label_hash", "k_l0_collect"))),
+                default=0)
+    cols = [collections.defaultdict(float)]
+    in_sig = False
+    for _, name, m in launches[first:]:
+        cls = class_of(name) or "other"
+        if cls.startswith("sig") and not in_sig:
+            cols.append(collections.defaultdict(float))
+        in_sig = cls.startswith("sig")
+        cols[-1][cls] += m.get("gpu__time_duration.sum", 0.0)
+    return cols
+
+
+def round_table(cols):
+    """Markdown table of per_round's columns (ms)."""
+    order = ["label_group", "sig_small", "sig_medium", "sig_hub", "group", "verify", "renumber", "other"]
+    names = ["level 0"] + ["round %d" % i for i in range(1, len(cols))]
+    lines = ["| class | " + " | ".join(names) + " |", "|---|" + "---:|" * len(cols)]
+    for c in order:
+        if any(c in col for col in cols):
+            lines.append("| %s | " % c + " | ".join("%.3f" % (col.get(c, 0.0) * 1e3) for col in cols) + " |")
+    lines.append("| total | " + " | ".join("%.3f" % (sum(col.values()) * 1e3) for col in cols) + " |")
+    return lines
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
@@ -135,6 +164,8 @@ def main():
     for name, (n, t, b) in sorted(per_kernel.items(), key=lambda kv: -kv[1][1]):
         lines.append("| `%s` | %d | %.3f | %.1f%% |" % (name, n, t * 1e3, 100 * t / total_t) +
                      (" %.1f |" % (b / 1e6) if dram else ""))
+    lines += ["", "Per level (ms, same launches; a round is its signatures, grouping, verification and renumbering):",
+              ""] + round_table(per_round(launches))
     if dram:
         lines += ["", "DRAM bytes per call of each kernel class (per round for signatures, per level otherwise):",
                   ""]

@@ -75,3 +75,19 @@ def test_traffic_record_and_digest(tmp_path, monkeypatch):
     # the digest covers the round-kernel sources only and is stable
     assert ncu_summary.source_digest() == ncu_summary.source_digest()
     assert set(ncu_summary.ROUND_SOURCES) == {"kbisim_round.cu", "kbisim_internal.cuh"}
+
+
+def test_per_round_split(tmp_path):
+    path = tmp_path / "launches.csv"
+    _write(path, [("k_check_ids", 5000, 1e9, 0)] + _refinement(10) + _refinement(1))
+    cols = ncu_summary.per_round(ncu_summary.load(str(path)))
+    # level 0 of the last refinement, then its two rounds
+    assert len(cols) == 3
+    assert abs(cols[0]["label_group"] - 1000e-9) < 1e-15 and abs(cols[0]["group"] - 2000e-9) < 1e-15
+    for c in cols[1:]:
+        assert abs(c["sig_small"] - 3000e-9) < 1e-15
+        assert abs(c["sig_hub"] - 1200e-9) < 1e-15
+        assert abs(c["renumber"] - 400e-9) < 1e-15
+    lines = ncu_summary.round_table(cols)
+    assert lines[0] == "| class | level 0 | round 1 | round 2 |"
+    assert lines[-1].startswith("| total | 0.003 | 0.008 | 0.008 |")
