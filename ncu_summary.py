@@ -152,6 +152,9 @@ def main():
     ap.add_argument("--command", default="")
     ap.add_argument("--md", help="write the per-kernel table here")
     ap.add_argument("--traffic", help="write the per-class DRAM bytes record here")
+    ap.add_argument("--units", action="store_true",
+                    help="store the (edges, nodes) each class processes on the profiled workload (the bench's "
+                         "single-graph generator at --scale) in the traffic record, for scaling to other sizes")
     a = ap.parse_args()
     launches = load(a.csv)
     per_kernel, total_t, per_call = summarise(launches, a.rounds)
@@ -181,6 +184,10 @@ def main():
         rec = {"source_sha256": source_digest(), "scale": a.scale, "workload": a.workload,
                "command": a.command, "rounds": a.rounds,
                "dram_bytes_per_round": {c: round(b) for c, b in per_call.items()}}
+        if a.units:
+            import bench
+            g, _ = bench.workload(a.scale)
+            rec["class_units"] = {c: {"edges": e, "nodes": n} for c, (e, n) in bench.class_units(g).items()}
         with open(a.traffic, "w") as f:
             json.dump(rec, f, indent=1)
             f.write("\n")

@@ -92,7 +92,10 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // and then passed through a bijective mix, so equal words <=> equal elements.
 // A node's signature set is stored as its distinct words in arbitrary order
 // (sets are compared as sets); the mix spreads the words uniformly, which the
-// hash sets and the hub buckets rely on for balance.
+// hash sets and the hub buckets rely on for balance.  The 32-bit mix is a
+// multiplication by an odd constant (every input bit reaches the high bits,
+// which pick set regions and hub buckets) followed by folding the high half
+// into the low half (which pick home slots in power-of-two sets).
 template <typename K>
 struct KeyOps;
 
@@ -101,7 +104,8 @@ struct KeyOps<uint32_t> {
   static constexpr uint32_t kEmpty = 0xFFFFFFFFu;
   static constexpr int kBits = 32;
   __device__ __forceinline__ static uint32_t make(uint32_t label, uint32_t pid, int pbits) {
-    return mix32((label << pbits) | pid);
+    const uint32_t x = ((label << pbits) | pid) * 0x9e3779b1u;
+    return x ^ (x >> 16);
   }
 };
 
@@ -117,16 +121,19 @@ struct KeyOps<uint64_t> {
 // Per-element hash term.  A set's term sum adds the two 32-bit halves of the
 // terms separately (each modulo 2^32), so kernels can accumulate it with
 // 32-bit adds in any order.  64-bit words: the SplitMix64 output function of
-// (key + seed).  32-bit words: each half is the MurmurHash3 finalizer of the
-// word combined with one half of the seed (two 32-bit mixes cost about half
-// the instructions of one 64-bit mix; the hash only routes nodes to candidate
-// groups, and equality is always decided by exact comparison).
+// (key + seed).  32-bit words, which are already the output of a mixing
+// bijection of (label, identifier): the low half is the word plus half of the
+// seed, the high half the word times (word xor the other half of the seed,
+// made odd), so the two halves of a set's sum are its first moment and a
+// quadratic one.  Three integer operations instead of two 32-bit mixes; the
+// hash only routes nodes to candidate groups, and equality is always decided
+// by exact comparison.
 template <typename K>
 __host__ __device__ __forceinline__ uint64_t elem_term(K key, uint64_t seed) {
   return mix64((uint64_t)key + seed);
 }
 __host__ __device__ __forceinline__ uint64_t elem_term(uint32_t key, uint64_t seed) {
-  return ((uint64_t)mix32(key ^ (uint32_t)(seed >> 32) ^ 0x9e3779b9u) << 32) | mix32(key + (uint32_t)seed);
+  return ((uint64_t)(key * ((key ^ (uint32_t)(seed >> 32)) | 1u)) << 32) | (key + (uint32_t)seed);
 }
 
 // Sum of two packed term sums, half by half.

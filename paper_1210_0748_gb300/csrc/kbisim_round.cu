@@ -800,8 +800,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_chunk(SigArgs a, HubArgs 
 
 // Hub pieces without the chunk-level set, for hubs whose keys rarely repeat
 // (k_hub_sample): the keys of a chunk go straight to the hub's buckets
-// (ranked per bucket in shared memory, one global reservation per bucket), and
-// the bucket pass removes every duplicate.
+// (ranked per bucket in shared memory, one global reservation per bucket,
+// then ordered by bucket in shared memory so that each bucket's keys are
+// stored as one run), and the bucket pass removes every duplicate.
 
 // One warp per hub: kHubSample keys at an even stride over the hub's edges.
 // Among S samples from U equally frequent distinct keys about S(S-1)/2 / U
@@ -835,10 +836,44 @@ __global__ void __launch_bounds__(256) k_hub_sample(SigArgs a, HubArgs h, uint64
   pairs = __reduce_add_sync(kFull, pairs);
   if (lane == 0) h.mode[hub] = (!h.force[hub] && pairs < (uint32_t)kHubSamplePairs) ? 1 : 0;
 }
+// Exclusive prefix sums of v[0..n) in place (n <= 2 * NT), by the whole CTA;
+// wsum holds NT / 32 words.  Ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void cta_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* wsum) {
+  static_assert(NT % 32 == 0 && NT / 32 <= 32, "one warp scans the warp totals");
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t a = 2 * tid < n ? v[2 * tid] : 0u, b = 2 * tid + 1 < n ? v[2 * tid + 1] : 0u;
+  uint32_t x = a + b;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < (uint32_t)(NT / 32) ? wsum[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, t, d);
+      if (lane >= (uint32_t)d) t += y;
+    }
+    if (lane < (uint32_t)(NT / 32)) wsum[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t before = (w ? wsum[w - 1] : 0u) + x - (a + b);
+  if (2 * tid < n) v[2 * tid] = before;
+  if (2 * tid + 1 < n) v[2 * tid + 1] = before + a;
+  __syncthreads();
+}
+
 template <typename LabelT, typename K>
 __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArgs h) {
   __shared__ uint32_t bcnt[kHubSmemBuckets];
   __shared__ uint32_t bpos[kHubSmemBuckets];
+  __shared__ uint32_t lstart[kHubSmemBuckets];
+  __shared__ uint32_t wsum[kChunkThreads / 32];
+  __shared__ K stage[kHubChunk];
   const uint4 c = h.chunks[blockIdx.x];
   const uint32_t hub = c.x;
   if (!h.mode[hub]) return;  // this hub's chunks run k_hub_chunk
@@ -868,20 +903,35 @@ __global__ void __launch_bounds__(kChunkThreads) k_hub_scatter(SigArgs a, HubArg
       rank[t] = in_smem ? atomicAdd(&bcnt[b], 1u) : atomicAdd(&cur[b], 1u);
     }
   }
-  if (in_smem) {
-    __syncthreads();
-    for (uint32_t b = tid; b < nb; b += kChunkThreads) {
-      const uint32_t n_b = bcnt[b];
-      bpos[b] = n_b ? atomicAdd(&cur[b], n_b) : 0u;
-    }
-    __syncthreads();
-  }
+  if (!in_smem) {
 #pragma unroll
-  for (int t = 0; t < kChunkItems; ++t) {
-    if (tid + t * kChunkThreads >= E) continue;
-    const uint32_t b = hub_bucket(key[t], bits);
-    const uint32_t q = in_smem ? bpos[b] + rank[t] : rank[t];
-    if (q < cap) tmp[(uint64_t)b * cap + q] = key[t];
+    for (int t = 0; t < kChunkItems; ++t) {
+      if (tid + t * kChunkThreads >= E) continue;
+      const uint32_t b = hub_bucket(key[t], bits);
+      if (rank[t] < cap) tmp[(uint64_t)b * cap + rank[t]] = key[t];
+      else hub_fail(a, h, hub, kErrHubOverflow);
+    }
+    return;
+  }
+  __syncthreads();
+  for (uint32_t b = tid; b < nb; b += kChunkThreads) {
+    const uint32_t n_b = bcnt[b];
+    bpos[b] = n_b ? atomicAdd(&cur[b], n_b) : 0u;
+    lstart[b] = n_b;
+  }
+  __syncthreads();
+  // the chunk's keys ordered by bucket in shared memory, so that each
+  // bucket's keys leave as one run of consecutive words
+  cta_exclusive_scan<kChunkThreads>(lstart, nb, wsum);
+#pragma unroll
+  for (int t = 0; t < kChunkItems; ++t)
+    if (tid + t * kChunkThreads < E) stage[lstart[hub_bucket(key[t], bits)] + rank[t]] = key[t];
+  __syncthreads();
+  for (uint32_t i = tid; i < E; i += kChunkThreads) {
+    const K k = stage[i];
+    const uint32_t b = hub_bucket(k, bits);
+    const uint32_t q = bpos[b] + (i - lstart[b]);
+    if (q < cap) tmp[(uint64_t)b * cap + q] = k;
     else hub_fail(a, h, hub, kErrHubOverflow);
   }
 }
