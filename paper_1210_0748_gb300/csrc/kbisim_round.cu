@@ -1472,27 +1472,53 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint64_t* bsum, uin
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Every alive node takes its head's block id; deleted nodes get kDead.
+// Every alive node takes its head's block id; deleted nodes get kDead.  A
+// thread takes kFillItems nodes at a time and issues each step's loads for
+// all of them together (representatives; their original ids; the bitmap
+// words), so the three dependent gathers of a node overlap with the others'.
+constexpr int kFillItems = 4;
+
 __global__ void k_pid_fill(RankArgs r) {
   unsigned int n_alone = 0, mx = 0;
   unsigned long long keys = 0;
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < r.n;
-       p += (uint64_t)gridDim.x * blockDim.x) {
-    if (p < r.n_alive) {
-      if (r.ucnt) {
-        const uint32_t q = r.ucnt[p];
-        keys += q;
-        mx = max(mx, q);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p0 < r.n; p0 += stride * kFillItems) {
+    uint32_t h[kFillItems], o[kFillItems], hb[kFillItems];
+    uint64_t hw[kFillItems];
+    bool live[kFillItems];
+#pragma unroll
+    for (int t = 0; t < kFillItems; ++t) {
+      const uint64_t p = p0 + (uint64_t)t * stride;
+      live[t] = p < r.n_alive;
+      if (live[t]) h[t] = r.rep[p];
+    }
+#pragma unroll
+    for (int t = 0; t < kFillItems; ++t)
+      if (live[t]) o[t] = r.p2o[h[t]];
+#pragma unroll
+    for (int t = 0; t < kFillItems; ++t) {
+      if (live[t]) {
+        hw[t] = r.hword[o[t] >> 5];
+        hb[t] = r.hbits[o[t] >> 5];
       }
-      const uint32_t h = r.rep[p];
-      const uint32_t o = r.p2o[h];
-      const uint32_t w = o >> 5;
-      r.pid[p] = (uint32_t)r.hword[w] + (uint32_t)__popc(r.hbits[w] & ((1u << (o & 31)) - 1u));
-      const bool al = h == (uint32_t)p && !r.member[p];
-      r.alone[p] = al ? 1 : 0;
-      n_alone += al ? 1u : 0u;
-    } else {
-      r.pid[p] = kDead;
+    }
+#pragma unroll
+    for (int t = 0; t < kFillItems; ++t) {
+      const uint64_t p = p0 + (uint64_t)t * stride;
+      if (p >= r.n) break;
+      if (live[t]) {
+        if (r.ucnt) {
+          const uint32_t q = r.ucnt[p];
+          keys += q;
+          mx = max(mx, q);
+        }
+        r.pid[p] = (uint32_t)hw[t] + (uint32_t)__popc(hb[t] & ((1u << (o[t] & 31)) - 1u));
+        const bool al = h[t] == (uint32_t)p && !r.member[p];
+        r.alone[p] = al ? 1 : 0;
+        n_alone += al ? 1u : 0u;
+      } else {
+        r.pid[p] = kDead;
+      }
     }
   }
   n_alone = __reduce_add_sync(kFull, n_alone);
