@@ -2337,11 +2337,16 @@ Status run_signatures(Store& s, const SigArgs& a) {
     };
     if (!s.tune_now) return run_hubs();
     // tuning (once per handle, on a full round from level 2 on): each bucket
-    // size runs the hub pass once, timed with the repeats its overflows need
-    // (a repeat runs only the hubs that overflowed); the faster size is kept.
-    // Every pass writes the same signatures, so the round's result is the
-    // last pass's.
+    // size runs the hub pass twice, the sizes alternating, each pass timed
+    // with the repeats its overflows need (a repeat runs only the hubs that
+    // overflowed).  A size's second pass starts from the bucket growth its
+    // first pass learned and finds the round's data in L2 as the first passes
+    // left it, so the second passes compare the sizes as the later rounds run
+    // them; the first size (the default) is kept unless another is faster by
+    // more than kHubTuneMargin.  Every pass writes the same signatures, so the
+    // round's result is the last pass's.
     constexpr int kSizes = 2;
+    constexpr float kHubTuneMargin = 0.05f;
     // bucket growth is learned per size: each starts from the growth before
     // tuning, and the chosen size keeps its own
     const std::vector<uint32_t> x0 = s.h_hub_xbits, sh0 = s.h_hub_shift;
@@ -2354,20 +2359,22 @@ Status run_signatures(Store& s, const SigArgs& a) {
       cudaEventDestroy(ev[0]);
       return st;
     }
-    for (int c = 0; c < kSizes && st.ok(); ++c) {
-      s.h_hub_xbits = x0;
-      s.h_hub_shift = sh0;
-      s.h_hub_force = f0;
-      s.hub_ucap = (uint32_t)kHubUcaps[c];
-      if (!(st = hub_layout(s)).ok()) break;
-      cudaEventRecord(ev[0], s.stream);
-      if (!(st = run_hubs()).ok()) break;
-      cudaEventRecord(ev[1], s.stream);
-      if (!(st = cuda_check(cudaEventSynchronize(ev[1]), "event")).ok()) break;
-      cudaEventElapsedTime(&s.hub_tune_ms[c], ev[0], ev[1]);
-      xs[c] = s.h_hub_xbits;
-      shs[c] = s.h_hub_shift;
-      fs[c] = s.h_hub_force;
+    for (int rep = 0; rep < 2 && st.ok(); ++rep) {
+      for (int c = 0; c < kSizes && st.ok(); ++c) {
+        s.h_hub_xbits = rep ? xs[c] : x0;
+        s.h_hub_shift = rep ? shs[c] : sh0;
+        s.h_hub_force = rep ? fs[c] : f0;
+        s.hub_ucap = (uint32_t)kHubUcaps[c];
+        if (!(st = hub_layout(s)).ok()) break;
+        cudaEventRecord(ev[0], s.stream);
+        if (!(st = run_hubs()).ok()) break;
+        cudaEventRecord(ev[1], s.stream);
+        if (!(st = cuda_check(cudaEventSynchronize(ev[1]), "event")).ok()) break;
+        cudaEventElapsedTime(&s.hub_tune_ms[c], ev[0], ev[1]);
+        xs[c] = s.h_hub_xbits;
+        shs[c] = s.h_hub_shift;
+        fs[c] = s.h_hub_force;
+      }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
@@ -2375,7 +2382,7 @@ Status run_signatures(Store& s, const SigArgs& a) {
     s.hub_tune = 2;
     int best = 0;
     for (int c = 1; c < kSizes; ++c)
-      if (s.hub_tune_ms[c] < s.hub_tune_ms[best]) best = c;
+      if (s.hub_tune_ms[c] < s.hub_tune_ms[best] * (1.0f - kHubTuneMargin)) best = c;
     if (best != kSizes - 1) {
       s.hub_ucap = (uint32_t)kHubUcaps[best];
       s.h_hub_xbits.swap(xs[best]);
