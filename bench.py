@@ -600,15 +600,37 @@ def main():
         t0 = time.perf_counter()
         e2e_rounds = 0
         e2e_steps = max(1, min(args.steps, 10))
+        marks = [t0]
         for _ in range(e2e_steps):
-            r = kb2.build(host_g, K_ROUNDS)
+            r = kb2.build(host_g, K_ROUNDS)  # returns once the counts are on the host
             kb2._check(kb2._lib.kbisim_pids(kb2._h, K_ROUNDS, out_np.ctypes.data, 0))
             e2e_rounds += r.rounds_run
+            marks.append(time.perf_counter())
         dt = max_over_ranks(time.perf_counter() - t0)
         h2d = sum(v.numel() * v.element_size() for v in pin.values())
+        per_build = np.diff(np.array(marks)) * 1000.0
         line["e2e"] = {"value": job_value(E * e2e_rounds, world, dt * 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": N * 4 + 8 * (K_ROUNDS + 1),
-                       "ms_per_step": 1000 * dt / e2e_steps}
+                       "ms_per_step": 1000 * dt / e2e_steps,
+                       "ms_per_build": {"min": float(per_build.min()), "median": float(np.median(per_build)),
+                                        "max": float(per_build.max())}}
+        # where a build's time goes: three more builds, each phase timed on its own
+        # (outside the timed region above)
+        phases = {"load": [], "refine": [], "pids_to_host": []}
+        for _ in range(3):
+            a0 = time.perf_counter()
+            kb2.load(host_g)
+            torch.cuda.synchronize(local_rank)
+            a1 = time.perf_counter()
+            kb2.refine(K_ROUNDS)
+            torch.cuda.synchronize(local_rank)
+            a2 = time.perf_counter()
+            kb2._check(kb2._lib.kbisim_pids(kb2._h, K_ROUNDS, out_np.ctypes.data, 0))
+            a3 = time.perf_counter()
+            phases["load"].append(a1 - a0)
+            phases["refine"].append(a2 - a1)
+            phases["pids_to_host"].append(a3 - a2)
+        line["e2e"]["phase_ms_median"] = {k: 1000.0 * float(np.median(v)) for k, v in phases.items()}
         kb2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.scale)
