@@ -2488,7 +2488,16 @@ Status restore_hub_growth(Store& s, const HubGrowth& g, bool same_degree) {
 // Work lists made from the offsets of the degree classes: hub chunks and the
 // hubs' bucket layout, and the chunks of whole nodes for out-degree 33..4096.
 // `fresh`: a new graph (bucket growth learned on the previous one is dropped).
-Status build_chunk_lists(Store& s, bool fresh) {
+// Offsets of the out-degree 33..4096 nodes, copied to the host for the chunk
+// plan, and the class bounds they cover.
+struct MidPlan {
+  std::vector<uint64_t> moff;
+  uint64_t mf = 0, mw = 0, mb = 0, me = 0;
+};
+
+// Hub chunk lists and layout, and the copy of the offsets the chunk plan of
+// the out-degree 33..4096 nodes needs (made with the hub offsets' copy).
+Status chunk_lists_hubs(Store& s, bool fresh, MidPlan* mp) {
   Status st;
   // hubs: a contiguous internal id range; their offsets come in one copy
   s.n_hub = s.class_start[kClassHub + 1] - s.class_start[kClassHub];
@@ -2537,19 +2546,35 @@ Status build_chunk_lists(Store& s, bool fresh) {
     if (!st.ok()) return st;
     if (!(st = hub_layout(s)).ok()) return st;
   }
-  // out-degree 33..4096: runs of whole nodes; 33..64 and 65..1024 in chunks
-  // of at most 1024 edges (128-thread CTAs), 1025..4096 in chunks of at most
-  // 4096 edges (512-thread CTAs)
-  s.n_mid_chunks[0] = s.n_mid_chunks[1] = s.n_mid_chunks[2] = 0;
-  const uint64_t mf = s.class_start[kSmallClasses - 1], mw = s.class_start[kClassWarp],
-                 mb = s.class_start[kClassBlock], me = s.class_start[kClassHub];
-  if (me > mf) {
-    std::vector<uint64_t> moff(me - mf + 1);
-    st = cuda_check(cudaMemcpyAsync(moff.data(), ptr<uint64_t>(s.offsets) + mf, (me - mf + 1) * 8,
-                                    cudaMemcpyDeviceToHost, s.stream), "chunk offsets");
+  // the out-degree 33..4096 nodes' offsets for their chunk plan
+  mp->mf = s.class_start[kSmallClasses - 1];
+  mp->mw = s.class_start[kClassWarp];
+  mp->mb = s.class_start[kClassBlock];
+  mp->me = s.class_start[kClassHub];
+  mp->moff.clear();
+  if (mp->me > mp->mf) {
+    mp->moff.resize(mp->me - mp->mf + 1);
+    st = cuda_check(cudaMemcpyAsync(mp->moff.data(), ptr<uint64_t>(s.offsets) + mp->mf,
+                                    (mp->me - mp->mf + 1) * 8, cudaMemcpyDeviceToHost, s.stream),
+                    "chunk offsets");
     if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
     if (!st.ok()) return st;
+  }
+  return Status::Ok();
+}
+
+// out-degree 33..4096: runs of whole nodes; 33..64 and 65..1024 in chunks
+// of at most 1024 edges (128-thread CTAs), 1025..4096 in chunks of at most
+// 4096 edges (512-thread CTAs).  A host loop over the nodes' offsets (about
+// 2 ms for 640K nodes), so a load runs it while the GPU relabels the edges.
+Status chunk_lists_mid(Store& s, const MidPlan& mp) {
+  Status st;
+  s.n_mid_chunks[0] = s.n_mid_chunks[1] = s.n_mid_chunks[2] = 0;
+  const uint64_t mf = mp.mf, mw = mp.mw, mb = mp.mb, me = mp.me;
+  if (me > mf) {
+    const std::vector<uint64_t>& moff = mp.moff;
     std::vector<uint2> mc;
+    mc.reserve((size_t)((moff[me - mf] - moff[0]) / 512 + (me - mf) / 16 + 16));
     auto pack = [&](uint64_t lo, uint64_t hi, uint64_t max_edges, uint64_t max_nodes) {
       for (uint64_t i = lo; i < hi;) {
         uint64_t j = i + 1;
@@ -2570,9 +2595,17 @@ Status build_chunk_lists(Store& s, bool fresh) {
     if (!(st = ensure(s, s.mid_chunks, mc.size() * sizeof(uint2))).ok()) return st;
     st = cuda_check(cudaMemcpyAsync(s.mid_chunks.p, mc.data(), mc.size() * sizeof(uint2), cudaMemcpyHostToDevice,
                                     s.stream), "medium chunks");
+    if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");  // mc is freed on return
     if (!st.ok()) return st;
   }
   return Status::Ok();
+}
+
+Status build_chunk_lists(Store& s, bool fresh) {
+  MidPlan mp;
+  Status st = chunk_lists_hubs(s, fresh, &mp);
+  if (st.ok()) st = chunk_lists_mid(s, mp);
+  return st;
 }
 
 
@@ -2631,7 +2664,8 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
   if (!st.ok()) return st;
   if (!(st = scan64(s, ptr<uint64_t>(s.offsets), n + 1, nullptr)).ok()) return st;
   s.n_alone = 0;
-  if (!(st = build_chunk_lists(s, true)).ok()) return st;
+  MidPlan mp;
+  if (!(st = chunk_lists_hubs(s, true, &mp)).ok()) return st;
   // the edge labels (and with them the label width) from here on
   if (s.await_labels && !(st = s.await_labels(s)).ok()) return st;
   if (!(st = ensure(s, s.elabel, std::max<uint64_t>(1, m) * (s.label8 ? 1 : 4))).ok()) return st;
@@ -2648,9 +2682,10 @@ Status relabel_graph(Store& s, const uint64_t* off0, const uint32_t* dst0, const
     }
   }
   st = launch_check("relabel edges");
+  // the medium chunk plan on the host while the GPU relabels the edges
+  if (st.ok()) st = chunk_lists_mid(s, mp);
   if (st.ok()) st = cuda_check(cudaStreamSynchronize(s.stream), "sync");
-  if (!st.ok()) return st;
-  return cuda_check(cudaStreamSynchronize(s.stream), "sync");
+  return st;
 }
 
 // ---- level 0 when few labels occur (Definition 2: pId_0 groups nodes by
