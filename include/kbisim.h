@@ -135,9 +135,10 @@ typedef struct {
   /* Key words a hub bucket holds at most (out-degree > 4096: the hub's keys
    * are split into buckets by key bits, each deduplicated by one CTA in
    * shared memory): 2048, 4096 or 8192; 0 (default) = tuned once per handle, in the
-   * first full round from level 2 on, by timing the hub pass with 4096 and
-   * with 2048 (kbisim_hub_bucket_keys reports the choice).  Results do not
-   * depend on it. */
+   * first full round from level 2 on, by timing the hub pass twice with 4096
+   * and twice with 2048, alternating, and comparing the second passes (2048 is
+   * kept only when more than 5% faster; kbisim_hub_bucket_keys reports the
+   * choice).  Results do not depend on it. */
   uint32_t hub_bucket_keys;
 } kbisim_options;
 
