@@ -91,3 +91,24 @@ def test_per_round_split(tmp_path):
     lines = ncu_summary.round_table(cols)
     assert lines[0] == "| class | level 0 | round 1 | round 2 |"
     assert lines[-1].startswith("| total | 0.003 | 0.008 | 0.008 |")
+
+
+def test_traffic_record_units(tmp_path, monkeypatch):
+    """--units stores the (edges, nodes) each kernel class processes on the
+    profiled workload, which bench.py scales the traffic by."""
+    import bench
+    from paper_1210_0748_gb300 import synth
+    g = synth.uniform_zipf_graph(2000, 40000, zipf_s=1.2, dmax=6000, node_labels=4, edge_labels=4, seed=5)
+    monkeypatch.setattr(bench, "workload", lambda scale, kind="single": (g, {}))
+    path = tmp_path / "launches.csv"
+    _write(path, _refinement(1))
+    rec = tmp_path / "traffic.json"
+    monkeypatch.setattr("sys.argv", ["ncu_summary", str(path), "--rounds", "2", "--scale", "0.5", "--units",
+                                     "--traffic", str(rec)])
+    ncu_summary.main()
+    r = json.loads(rec.read_text())
+    units = bench.class_units(g)
+    assert r["class_units"] == {c: {"edges": e, "nodes": n} for c, (e, n) in units.items()}
+    # every edge and node is in exactly one signature class
+    assert sum(r["class_units"][c]["edges"] for c in ("sig_small", "sig_medium", "sig_hub")) == g.num_edges
+    assert sum(r["class_units"][c]["nodes"] for c in ("sig_small", "sig_medium", "sig_hub")) == g.num_nodes
